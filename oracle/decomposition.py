@@ -1,0 +1,80 @@
+"""Multilevel overlapping decomposition (oracle side).
+
+§3 "Problem and model definition": levels l = 1..L, each covering the domain
+with J_l overlapping subdomains.  §4.1 "Domain decomposition": a uniform
+tensor grid of subdomains per level; in one dimension subdomain j has bounds
+mu_j -/+ (delta/2) * (spacing), half-width sigma = (x_max - x_min) / 2, with
+delta the width ratio.
+
+Readings (the paper is silent or ambiguous):
+* placement "cell" (default): centres are cell-centred,
+  mu_j = lo + (j + 1/2) * Delta with Delta = (hi - lo) / n;
+* placement "endpoint": centres equally spaced including both end points,
+  mu_j = lo + j * Delta with Delta = (hi - lo) / (n - 1) (a single subdomain
+  sits at the midpoint with Delta = hi - lo);
+* the end subdomains use the same spacing Delta on their outer side, so every
+  subdomain has sigma = delta * Delta / 2;
+* within a level, 2-D subdomains are numbered j = j_y * n + j_x (x fastest);
+* the column index of (level l, subdomain j, feature k) is
+  q = sum_{m<l} J_m K + j K + k  (§3 "Indexing conventions", 0-based here).
+
+Parity pinned through the window tests (partition of unity, support) and the
+closed-form column counts in tests/test_oracle_windows.py.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass
+from typing import List, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Level:
+    n: int                      # subdomains per dimension
+    mu: List[np.ndarray]        # per dimension: centres, shape (n,)
+    sigma: List[float]          # per dimension: half-width
+    col_offset: int             # first column index of this level
+    n_sub: int                  # J_l = n ** dim
+
+
+def build_levels(dim: int, lo, hi, levels, delta: float, K: int,
+                 placement: str = "cell") -> List[Level]:
+    out = []
+    off = 0
+    for n in levels:
+        mus, sigs = [], []
+        for i in range(dim):
+            if placement == "cell":
+                D = (hi[i] - lo[i]) / n
+                mus.append(lo[i] + (np.arange(n, dtype=np.float64) + 0.5) * D)
+            elif placement == "endpoint":
+                if n == 1:
+                    D = hi[i] - lo[i]
+                    mus.append(np.array([0.5 * (lo[i] + hi[i])]))
+                else:
+                    D = (hi[i] - lo[i]) / (n - 1)
+                    mus.append(lo[i] + np.arange(n, dtype=np.float64) * D)
+            else:
+                raise ValueError(f"unknown placement {placement!r}")
+            sigs.append(delta * D / 2.0)
+        J = n ** dim
+        out.append(Level(n=n, mu=mus, sigma=sigs, col_offset=off, n_sub=J))
+        off += J * K
+    return out
+
+
+def subdomain_multi_index(level: Level, dim: int, j: int) -> Tuple[int, ...]:
+    """Linear subdomain index j -> (j_x, j_y, ...) with x fastest."""
+    idx = []
+    for _ in range(dim):
+        idx.append(j % level.n)
+        j //= level.n
+    return tuple(idx)
+
+
+def all_subdomains(level: Level, dim: int):
+    """Iterate (j, (j_x, j_y, ...)) over the level in linear order."""
+    for j, rev in enumerate(itertools.product(range(level.n), repeat=dim)):
+        yield j, tuple(reversed(rev))
