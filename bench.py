@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the multilevel ELM-FBPINN hot path on one GB300 (per rank).
+
+One step = the whole path the paper times (basis construction, assembly of the
+global system and iterative solution, §4.1 "Optimisation and solvers"), plus
+the evaluation of u_hat and its error norms on the test points:
+
+    elmfb_create -> elmfb_assemble -> elmfb_solve -> elmfb_eval -> elmfb_error_norms
+
+on the 2-D multilevel Poisson workload (levels 1,2,4,8,16 per dimension,
+K = 128, 400^2 + 1600 collocation rows).  Inputs (points, right-hand sides,
+test points, reference values) are resident in HBM when the timed region
+starts; the e2e leg repeats the step from pinned host buffers with the copies
+inside the timed region.  The panels (1.1 GB) exceed L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead (the paper's protocol, on a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as WL  # noqa: E402
+
+METRIC = "ELM-FBPINN time-to-solution (s) at oracle-matched L2 error; assembly HBM GB/s"
+WORKLOADS = {
+    "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400"),
+    "dho_ml": (WL.config_dho_ml, "dho_L1-64_K96_N20000"),
+    "poisson1d": (WL.config_poisson1d, "poisson1d_J16_K64_N2000"),
+}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _golden(name):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_errors.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get(name)
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _sets(P, device):
+    import torch
+    sets = []
+    for rs in [P.interior] + list(P.boundary):
+        pts = torch.as_tensor(np.ascontiguousarray(rs.points, dtype=np.float64))
+        rhs = torch.as_tensor(np.ascontiguousarray(rs.rhs, dtype=np.float64))
+        if device == "pinned":
+            pts, rhs = pts.pin_memory(), rhs.pin_memory()
+        elif device is not None:
+            pts, rhs = pts.to(device), rhs.to(device)
+        sets.append(dict(points=pts, rhs=rhs, c0=rs.c0, c1=rs.c1, c2=rs.c2, weight=rs.weight,
+                         n=rs.points.shape[0]))
+    return sets
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2409_01949_gb300 as E
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    make, golden_name = WORKLOADS[args.workload]
+    P = make()
+    prec = {"fp64": E.FP64, "fp32": E.FP32}[args.precision]
+    stream = torch.cuda.current_stream()
+    opts = E.default_solve_opts(max_iter=args.max_iter, atol=args.tol, btol=args.tol,
+                                shift=args.shift, check_every=args.check_every)
+
+    sets_dev = _sets(P, dev)
+    xs_dev = torch.as_tensor(P.test_points).to(dev)
+    u_dev = torch.as_tensor(P.exact(P.test_points)).to(dev)
+    uh_dev = torch.empty(xs_dev.shape[0], dtype=torch.float64, device=dev)
+    kstats = {}
+    launches = [0]
+    last = {}
+
+    def step(sets, xs, u, uh, profile):
+        s = E.Solver.from_problem(P, precision=prec, stream=stream.cuda_stream)
+        if profile:
+            s.set_profiling(True)
+        s.assemble(sets)
+        info = s.solve(opts)
+        s.eval(xs, out=uh)
+        err = s.error_norms(uh, u)
+        if profile:
+            for k, (ms, n, by) in s.kernel_stats().items():
+                t = kstats.setdefault(k, [0.0, 0, by])
+                t[0] += ms
+                t[1] += n
+                t[2] = by
+            launches[0] += s.kernel_launches()
+        last.update(info=info, err=err, sizes=s.sizes(), stages=s.stage_times())
+        s.close()
+        return err
+
+    for _ in range(args.warmup):
+        step(sets_dev, xs_dev, u_dev, uh_dev, False)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(sets_dev, xs_dev, u_dev, uh_dev, True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+
+    # end-to-end through the public API from pinned host buffers
+    sets_h = _sets(P, "pinned")
+    xs_h = torch.as_tensor(P.test_points).pin_memory()
+    u_h = torch.as_tensor(P.exact(P.test_points)).pin_memory()
+    uh_h = torch.empty(xs_h.shape[0], dtype=torch.float64).pin_memory()
+    a_h = torch.empty(P.n_columns, dtype=torch.float64).pin_memory()
+    h2d = sum(s["points"].numel() * 8 + s["rhs"].numel() * 8 for s in sets_h) + \
+        xs_h.numel() * 8 + u_h.numel() * 8
+    d2h = uh_h.numel() * 8 + a_h.numel() * 8 + 3 * 8
+
+    def step_e2e():
+        s = E.Solver.from_problem(P, precision=prec, stream=stream.cuda_stream)
+        s.assemble(sets_h)
+        s.solve(opts)
+        s.eval(xs_h, out=uh_h)
+        s.error_norms(uh_h, u_h)
+        E.lib().elmfb_get_coeffs(s.h, a_h.data_ptr())
+        s.close()
+
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - e0) / args.steps
+    if ws > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = _peaks()
+    kern = {}
+    for k, (tms, n, by) in kstats.items():
+        avg = tms / max(n, 1)
+        kern[k] = {"launches_per_step": n / args.steps, "avg_ms": round(avg, 5),
+                   "share": None, "gbs": round(by / (avg * 1e-3) / 1e9, 1) if avg > 0 else None}
+    tot = sum(v[0] for v in kstats.values()) or 1.0
+    for k in kern:
+        kern[k]["share"] = round(kstats[k][0] / tot, 4)
+    dom = max(kstats, key=lambda k: kstats[k][0])
+    dms = kstats[dom][0] / kstats[dom][1]
+    ach = kstats[dom][2] / (dms * 1e-3) / 1e9
+    asm = kern.get("assemble_panels", {})
+    g = _golden(golden_name)
+    info, err, sz = last["info"], last["err"], last["sizes"]
+    line = {
+        "metric": METRIC,
+        "value": round(ms / 1000.0, 5),
+        "unit": "s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == E.FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": golden_name, "levels": list(P.levels), "features": P.features,
+                   "rows": P.n_rows, "columns": P.n_columns, "nnz_stored": int(sz.nnz),
+                   "solver": f"LSQR + block-Jacobi, tol {args.tol}, max_iter {args.max_iter}",
+                   "parallelism": f"replicas x{ws}", "l2_flush": "inputs larger than L2 (panels "
+                   f"{sz.panel_rows * P.features * (4 if prec == E.FP32 else 8) / 1e9:.2f} GB)"},
+        "solution": {"rel_l2": err["rel_l2"], "e_l1": err["e_l1"], "iterations": info.iterations,
+                     "oracle_lsqr15000_rel_l2": (g or {}).get("lsqr", {}).get("rel_l2"),
+                     "oracle_qr_rel_l2": (g or {}).get("qr", {}).get("rel_l2")},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                     "peak_kind": peak_kind},
+        "assembly": {"kernel": "assemble_panels", "achieved_gbs": asm.get("gbs"),
+                     "frac": round(asm["gbs"] / hbm, 4) if asm.get("gbs") else None,
+                     "avg_ms": asm.get("avg_ms")},
+        "kernels": kern,
+        "stages_ms": {k: round(v, 3) for k, v in last["stages"].items()},
+        "gpu_launches": int(launches[0]),
+        "e2e": {"value": round(e2e_s, 5), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(P, args)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(P, args):
+    """The FP64 oracle as it stands on a bounded sample, projected to the full paper protocol."""
+    from oracle import lstsq as OL
+    from oracle import system as OS
+    frac = args.cpu_row_stride
+    its = args.cpu_lsqr_its
+    rows = np.arange(0, P.n_rows, frac)
+    c0 = time.process_time()
+    w0 = time.perf_counter()
+    out = OS.assemble(P, rows=rows, fmt="csr")
+    t_as = time.perf_counter() - w0
+    w1 = time.perf_counter()
+    OL.lstsq_lsqr(out["M"], out["h"], iter_lim=its)
+    t_ls = time.perf_counter() - w1
+    wall = time.perf_counter() - w0
+    cpu = time.process_time() - c0
+    projected = t_as * frac + t_ls * frac * (15000.0 / its)
+    return {"value": round(projected, 2), "unit": "s", "cores": max(1, round(cpu / wall)),
+            "kind": "oracle",
+            "sample": f"every {frac}th row assembled ({t_as:.2f} s) and {its} LSQR iterations on "
+                      f"that sample ({t_ls:.2f} s); projected x{frac} rows and x{15000 // its} "
+                      f"iterations to the paper protocol (15000 LSQR iterations); host "
+                      f"{os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    make, golden_name = WORKLOADS[args.workload]
+    P = make()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(P, args)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.mean(c["value"] for c in vals)
+    cb = dict(vals[-1])
+    cb["value"] = round(v, 2)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(v * 1000.0, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": golden_name, "levels": list(P.levels), "features": P.features,
+                       "rows": P.n_rows, "columns": P.n_columns,
+                       "solver": "oracle: SciPy LSQR, 15000 iterations (paper protocol)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(v, 2), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poisson2d_ml", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--shift", type=float, default=1e-10)
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--cpu-row-stride", type=int, default=40)
+    ap.add_argument("--cpu-lsqr-its", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * elmfb.h -- C ABI of the GB300 multilevel ELM-FBPINN solver (arxiv 2409.01949).
+ *
+ * The method (paper §3): a linear PDE  N[u] = f  on interior collocation
+ * points and linear boundary conditions  B_b[u] = g_b  on boundary point sets
+ * are fitted by the multilevel random-feature model
+ *
+ *     u_hat(x) = (1/L) sum_l sum_j w_j^(l)(x) sum_k a_ljk phi_ljk(x)
+ *
+ * (Eq. multilevel_solution), whose hidden parameters are fixed, so the
+ * physics-informed loss (Eq. multilevel_loss) is the linear least-squares
+ * problem  min_a ||M a - h||  (Eq. multilevel_ls) with a block-sparse M
+ * (Eq. multilevel_domain_decomp).  This library creates the decomposition and
+ * random features, assembles M and h on the GPU, solves for a, and evaluates
+ * u_hat.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status, ELMFB_OK (0) on success.  On an
+ *     error the handle keeps a message readable through elmfb_last_error().
+ *   - Pointer arguments may be host or device memory (CUDA unified
+ *     addressing decides); they are borrowed for the duration of the call
+ *     and copied.  Outputs are caller-allocated.
+ *   - One handle is bound to one CUDA stream and one device; handles are not
+ *     thread-safe.  The handle owns all device memory it allocates and frees
+ *     it in elmfb_destroy().
+ *   - Indices are 0-based.  Column q of M is (level l, subdomain j, feature k)
+ *     with q = sum_{m<l} J_m K + j K + k (paper §3 "Indexing conventions");
+ *     2-D subdomains are numbered j = j_y n_l + j_x.  Rows of M are the
+ *     interior points in the order given, then each boundary set in order
+ *     (paper §3, rows of Eq. multilevel_ls).
+ */
+#ifndef ELMFB_H
+#define ELMFB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+enum {
+  ELMFB_OK = 0,
+  ELMFB_ERR_INVALID_ARG = 1,  /* bad size, pointer, or option                   */
+  ELMFB_ERR_OOM = 2,          /* device allocation failed                        */
+  ELMFB_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has details) */
+  ELMFB_ERR_STATE = 4,        /* call out of order (e.g. solve before assemble)   */
+  ELMFB_ERR_NOT_CONVERGED = 5,/* iteration cap reached; coefficients still valid  */
+  ELMFB_ERR_BREAKDOWN = 6,    /* factorisation pivot or Krylov scalar <= 0         */
+  ELMFB_ERR_NONFINITE = 7,    /* NaN/Inf produced (flag raised by a kernel)       */
+  ELMFB_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up               */
+  ELMFB_ERR_UNSUPPORTED = 9   /* size or feature outside the documented limits     */
+};
+
+/* ---- precision of the stored system (paper §4.1 states none) --------------- */
+enum {
+  ELMFB_FP64 = 0,   /* panels, Gram and solver vectors in FP64                  */
+  ELMFB_FP32 = 1,   /* panels FP32, FP64 solver vectors and reductions          */
+  ELMFB_MIXED = 2   /* FP32 panels + BF16 copy for tensor-core Gram blocks       */
+};
+
+/* ---- subdomain centre placement (paper §4.1 "Domain decomposition") -------- */
+enum {
+  ELMFB_PLACE_CELL = 0,     /* mu_j = lo + (j + 1/2) (hi - lo) / n              */
+  ELMFB_PLACE_ENDPOINT = 1  /* mu_j = lo + j (hi - lo) / (n - 1); n = 1: midpoint */
+};
+
+/* ---- solvers ---------------------------------------------------------------- */
+enum {
+  ELMFB_SOLVE_LSQR = 0,     /* right-preconditioned LSQR on M (paper §3, §4.1)   */
+  ELMFB_SOLVE_PCG = 1,      /* preconditioned CG on the Gram normal equations    */
+  ELMFB_SOLVE_FCG_GNN = 2   /* flexible CG with the learned preconditioner       */
+};
+
+/* ---- preconditioners --------------------------------------------------------- */
+enum {
+  ELMFB_PREC_NONE = 0,      /* plain LSQR, the paper's protocol                  */
+  ELMFB_PREC_BLOCK_JACOBI = 1 /* per-subdomain Cholesky of the shifted diagonal
+                               Gram block (not in the paper)                      */
+};
+
+typedef struct elmfb_ctx* elmfb_t;
+
+/* Decomposition and random features (paper §3 "Problem and model definition",
+ * §4.1 "Domain decomposition" and "weight initialisation").
+ *   dim          1 or 2
+ *   lo, hi       domain box [lo_i, hi_i] per dimension (entries >= dim ignored)
+ *   n_levels     L >= 1, at most ELMFB_MAX_LEVELS
+ *   levels       [n_levels] subdomains per dimension at each level (J_l = n^dim)
+ *   delta        width ratio delta > 1; half-width sigma = delta * spacing / 2
+ *   placement    ELMFB_PLACE_*
+ *   features     K >= 1 random features per subdomain, at most ELMFB_MAX_FEATURES
+ *   seed         SplitMix64 seed of the parameter stream
+ *   weight_scale a: every hidden weight and bias is drawn from U(-a, a)
+ *   precision    ELMFB_FP64 / ELMFB_FP32 / ELMFB_MIXED
+ * Parameter stream: output i of SplitMix64(seed) is
+ * mix(seed + (i+1) * 0x9E3779B97F4A7C15); column q draws outputs
+ * q*(dim+1)+p (p < dim: weight p, p = dim: bias); u = (z >> 40) * 2^-24,
+ * value = a (2u - 1).  The feature input is (x - mu_j) / sigma_j. */
+#define ELMFB_MAX_LEVELS 12
+#define ELMFB_MAX_FEATURES 256
+#define ELMFB_MAX_ROWSETS 16
+typedef struct {
+  int dim;
+  double lo[2];
+  double hi[2];
+  int n_levels;
+  int levels[ELMFB_MAX_LEVELS];
+  double delta;
+  int placement;
+  int features;
+  uint64_t seed;
+  double weight_scale;
+  int precision;
+} elmfb_config;
+
+/* Create a handle on the current CUDA device, bound to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Draws the random
+ * parameters (host, SplitMix64) and uploads the geometry tables.
+ * Errors: INVALID_ARG for an out-of-range field, OOM, CUDA. */
+int elmfb_create(elmfb_t* out, const elmfb_config* cfg, void* cuda_stream);
+
+/* Release every device buffer of the handle.  NULL is accepted. */
+void elmfb_destroy(elmfb_t h);
+
+/* Message of the last error on this handle ("" if none).  The string is owned
+ * by the handle and valid until the next call on it. */
+const char* elmfb_last_error(elmfb_t h);
+
+/* One block of rows of Eq. multilevel_ls.  The operator applied to the model
+ * is the constant-coefficient operator
+ *     Op[v] = c0 v + sum_i c1[i] d_i v + sum_i c2[i] d_ii v
+ * (paper §3: N and B_b linear).  The first row set of elmfb_assemble is the
+ * interior set N[u] = f, row scale 1/sqrt(N_I) ("Definition of vectors");
+ * every later set is a boundary set B_b[u] = g_b with penalty weight
+ * lambda_b > 0, row scale sqrt(lambda_b / N_B^(b)).
+ *   points  [n * dim] row-major FP64 coordinates, inside the domain box
+ *   rhs     [n] FP64 values of f or g_b at the points (unscaled)          */
+typedef struct {
+  int64_t n;
+  const double* points;
+  const double* rhs;
+  double c0;
+  double c1[2];
+  double c2[2];
+  double weight;      /* lambda_b; ignored for the interior set */
+} elmfb_rowset;
+
+/* Assemble M and h on the device (paper §3 "Definition of the system
+ * matrices": N_{n,q} = N[w_j phi_jk](x_n) / (sqrt(N_I) L), B_{p,q} =
+ * sqrt(lambda_b/N_B^(b)) B_b[w_j phi_jk](x_p) / L), applying the operator to
+ * w_j phi_jk analytically by the product rule.  Sorts rows by the cells of
+ * the common refinement of all subdomain supports and stores M as dense
+ * per-subdomain panels M_j = M restricted to I_j x K_j (Eq.
+ * multilevel_domain_decomp).  Replaces any previous system of the handle.
+ *   n_sets  1 .. ELMFB_MAX_ROWSETS; sets[0] is the interior set
+ * Errors: INVALID_ARG (empty interior set, points outside the box, bad sizes),
+ * UNSUPPORTED (a cell of the refinement holds more than 16384 points), OOM,
+ * CUDA.  Blocks until the assembly has finished on the handle's stream. */
+int elmfb_assemble(elmfb_t h, int n_sets, const elmfb_rowset* sets);
+
+/* Sizes of the handle's problem. */
+typedef struct {
+  int64_t n_columns;       /* N_Phi = K sum_l J_l                          */
+  int64_t n_rows;          /* N_I + N_B (0 before elmfb_assemble)           */
+  int64_t n_subdomains;    /* sum_l J_l                                     */
+  int64_t nnz;             /* stored panel entries, padding rows excluded   */
+  int64_t panel_rows;      /* stored panel rows including padding           */
+  int64_t n_cells;         /* cells of the common refinement of supports     */
+  int64_t n_gram_pairs;    /* subdomain pairs (i <= j) sharing a cell        */
+  int features;
+  int n_levels;
+  int dim;
+  int precision;
+} elmfb_sizes;
+int elmfb_get_sizes(elmfb_t h, elmfb_sizes* out);
+
+/* Fixed random parameters of every column (paper §3 Eq. shallow networks):
+ * W [N_Phi * dim] row-major, b [N_Phi].  Either pointer may be NULL. */
+int elmfb_get_params(elmfb_t h, double* W, double* b);
+
+/* Dense copy of selected rows of the assembled M and of h, for checking.
+ *   rows [n] row indices (paper order); out [n * N_Phi] row-major FP64;
+ *   h_out [n] or NULL.   Errors: STATE before assemble, INVALID_ARG. */
+int elmfb_get_rows(elmfb_t h, const int64_t* rows, int64_t n, double* out, double* h_out);
+
+/* Solver options and report. */
+typedef struct {
+  int method;          /* ELMFB_SOLVE_*                                       */
+  int preconditioner;  /* ELMFB_PREC_*                                        */
+  int max_iter;        /* iteration cap (the paper uses 15000)                */
+  double atol;         /* stop when ||M^T r|| <= atol ||M|| ||r|| (estimates) */
+  double btol;         /* stop when ||r|| <= btol ||h||; 0 disables both tests */
+  double shift;        /* Cholesky shift eps: G_jj + eps tr(G_jj)/K I          */
+  int check_every;     /* host checks convergence every this many iterations  */
+  int warm_start;      /* nonzero: start from the handle's current coefficients */
+} elmfb_solve_opts;
+
+typedef struct {
+  int status;                 /* ELMFB_OK or NOT_CONVERGED                     */
+  int iterations;
+  double residual_norm;       /* ||M a - h|| (LSQR estimate)                   */
+  double normal_residual_norm;/* ||M^T (M a - h)|| (estimate, preconditioned) */
+  double setup_ms;            /* preconditioner set-up time                    */
+  double solve_ms;            /* iteration time                                */
+} elmfb_solve_info;
+
+/* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
+ * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start. */
+void elmfb_default_solve_opts(elmfb_solve_opts* opts);
+
+/* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the
+ * paper uses LSQR, §3 and §4.1).  The result stays in the handle.
+ * Errors: STATE before assemble, BREAKDOWN, NONFINITE, INVALID_ARG.
+ * Returns NOT_CONVERGED (with valid coefficients) at the iteration cap. */
+int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info);
+
+/* Copy the coefficients a [N_Phi] out of / into the handle. */
+int elmfb_get_coeffs(elmfb_t h, double* a);
+int elmfb_set_coeffs(elmfb_t h, const double* a);
+
+/* Evaluate u_hat (paper Eq. multilevel_solution) at n points.
+ *   xs [n * dim] row-major FP64 inside the domain box; out [n] FP64. */
+int elmfb_eval(elmfb_t h, const double* xs, int64_t n, double* out);
+
+/* Error norms of u_hat against reference values, reduced on the device in
+ * FP64: out[0] = ||u_hat - u||_2 / ||u||_2, out[1] = e_L1 of paper Eq.
+ * l1_error (population standard deviation of u), out[2] = max |u_hat - u|. */
+int elmfb_error_norms(elmfb_t h, const double* u_hat, const double* u_ref, int64_t n,
+                      double* out3);
+
+/* Per-stage device times (ms) of the last calls, by CUDA events:
+ * [0] create upload, [1] cell sort, [2] panel assembly, [3] Gram,
+ * [4] preconditioner set-up, [5] iterations, [6] eval, [7] total assemble.  */
+#define ELMFB_N_STAGES 8
+int elmfb_stage_times(elmfb_t h, double* ms);
+
+/* Number of this library's kernels launched since the handle was created. */
+int64_t elmfb_kernel_launches(elmfb_t h);
+
+/* Per-kernel device timing.  With profiling on, the main kernels are
+ * bracketed by CUDA events on the handle's stream; elmfb_kernel_stats()
+ * synchronises the stream and returns, for up to `max` kernels, the name
+ * (static string), the summed device time (ms), the number of timed launches
+ * and the algorithmic bytes one launch must move (inputs read once, outputs
+ * written once; the roofline numerator).  Returns the number of kernels
+ * reported (>= 0) or a negative status.  elmfb_set_profiling(h, 1) clears the
+ * totals. */
+int elmfb_set_profiling(elmfb_t h, int on);
+int elmfb_kernel_stats(elmfb_t h, int max, const char** names, double* total_ms,
+                       int64_t* launches, double* bytes_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELMFB_H */

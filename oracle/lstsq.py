@@ -42,14 +42,47 @@ def lstsq_qr(M: np.ndarray, h: np.ndarray, rcond: float = 1e-13):
     return a, rank
 
 
-def lstsq_lsqr(M, h: np.ndarray, iter_lim: int = 15000, atol: float = 0.0, btol: float = 0.0):
+def _row_split_operator(M, threads: int):
+    """M as a LinearOperator whose products run on row blocks in threads.
+
+    Each output entry is the same CSR row sum as in the serial product (rows
+    of M for M x, rows of the CSR transpose for M^T y), so results are
+    bitwise those of the serial SciPy product.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+    M = sp.csr_matrix(M)
+    MT = M.T.tocsr()
+    ex = ThreadPoolExecutor(threads)
+
+    def parts(A):
+        b = np.linspace(0, A.shape[0], threads + 1).astype(np.int64)
+        return [(b[i], b[i + 1], A[b[i]:b[i + 1]]) for i in range(threads)]
+
+    pm, pt = parts(M), parts(MT)
+
+    def apply(ps, v, n):
+        out = np.empty(n)
+
+        def one(p):
+            out[p[0]:p[1]] = p[2] @ v
+        list(ex.map(one, ps))
+        return out
+
+    return spla.LinearOperator(M.shape, matvec=lambda v: apply(pm, v, M.shape[0]),
+                               rmatvec=lambda v: apply(pt, v, M.shape[1]), dtype=np.float64)
+
+
+def lstsq_lsqr(M, h: np.ndarray, iter_lim: int = 15000, atol: float = 0.0, btol: float = 0.0,
+               threads: int = 1):
     """SciPy LSQR, by default run for the full iteration budget as in the paper.
 
+    threads > 1 runs the matrix products on row blocks in threads (same values).
     Returns (a, info) with info = dict(istop, itn, r1norm, arnorm).
     """
     if not sp.issparse(M):
         M = sp.csr_matrix(M)
-    res = spla.lsqr(M, h, atol=atol, btol=btol, conlim=0.0, iter_lim=iter_lim)
+    A = _row_split_operator(M, threads) if threads > 1 else M
+    res = spla.lsqr(A, h, atol=atol, btol=btol, conlim=0.0, iter_lim=iter_lim)
     a, istop, itn, r1norm = res[0], res[1], res[2], res[3]
     return a, {"istop": int(istop), "itn": int(itn), "r1norm": float(r1norm),
                "arnorm": float(res[7])}

@@ -1,0 +1,303 @@
+"""Python binding of the GB300 multilevel ELM-FBPINN library (``libelmfb.so``).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  The binding fails loudly when the compiled library is missing; there
+is no CPU fallback.  Entry points carry the C names of ``include/elmfb.h``;
+``Solver`` is a small object wrapper over them.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); pointers are
+passed through unchanged and the library copies what it needs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libelmfb.so")
+
+# status codes (elmfb.h)
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_BREAKDOWN, \
+    ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(10)
+FP64, FP32, MIXED = 0, 1, 2
+PLACE_CELL, PLACE_ENDPOINT = 0, 1
+SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN = 0, 1, 2
+PREC_NONE, PREC_BLOCK_JACOBI = 0, 1
+MAX_LEVELS = 12
+MAX_ROWSETS = 16
+N_STAGES = 8
+STAGE_NAMES = ["create", "cell_sort", "assemble", "gram", "precond_setup", "iterate", "eval",
+               "assemble_total"]
+
+
+class ElmfbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"elmfb error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("lo", C.c_double * 2), ("hi", C.c_double * 2),
+                ("n_levels", C.c_int), ("levels", C.c_int * MAX_LEVELS), ("delta", C.c_double),
+                ("placement", C.c_int), ("features", C.c_int), ("seed", C.c_uint64),
+                ("weight_scale", C.c_double), ("precision", C.c_int)]
+
+
+class RowSet(C.Structure):
+    _fields_ = [("n", C.c_int64), ("points", C.c_void_p), ("rhs", C.c_void_p),
+                ("c0", C.c_double), ("c1", C.c_double * 2), ("c2", C.c_double * 2),
+                ("weight", C.c_double)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("n_columns", C.c_int64), ("n_rows", C.c_int64), ("n_subdomains", C.c_int64),
+                ("nnz", C.c_int64), ("panel_rows", C.c_int64), ("n_cells", C.c_int64),
+                ("n_gram_pairs", C.c_int64), ("features", C.c_int), ("n_levels", C.c_int),
+                ("dim", C.c_int), ("precision", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("method", C.c_int), ("preconditioner", C.c_int), ("max_iter", C.c_int),
+                ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
+                ("check_every", C.c_int), ("warm_start", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_norm", C.c_double),
+                ("normal_residual_norm", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGNATURES = {
+    "elmfb_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Config), C.c_void_p]),
+    "elmfb_destroy": (None, [C.c_void_p]),
+    "elmfb_last_error": (C.c_char_p, [C.c_void_p]),
+    "elmfb_assemble": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(RowSet)]),
+    "elmfb_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(Sizes)]),
+    "elmfb_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "elmfb_get_rows": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "elmfb_default_solve_opts": (None, [C.POINTER(SolveOpts)]),
+    "elmfb_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    "elmfb_get_coeffs": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "elmfb_set_coeffs": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "elmfb_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "elmfb_error_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "elmfb_stage_times": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "elmfb_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "elmfb_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "elmfb_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
+}
+
+
+def lib():
+    """Load ``libelmfb.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        l = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _ptr(x):
+    """(pointer, keepalive) for a numpy array or torch tensor (contiguous float64 / int64)."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):          # torch tensor
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, a
+
+
+def _check(h, rc, allow=(OK,)):
+    if rc not in allow:
+        msg = lib().elmfb_last_error(h).decode() if h else ""
+        raise ElmfbError(rc, msg)
+    return rc
+
+
+def default_solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().elmfb_default_solve_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One handle: create -> assemble -> solve -> eval."""
+
+    def __init__(self, dim, lo, hi, levels: Sequence[int], delta: float, features: int,
+                 seed: int = 0, weight_scale: float = 1.0, precision: int = FP64,
+                 placement: int = PLACE_CELL, stream: Optional[int] = None):
+        cfg = Config()
+        cfg.dim = dim
+        for i in range(dim):
+            cfg.lo[i] = float(lo[i])
+            cfg.hi[i] = float(hi[i])
+        if len(levels) > MAX_LEVELS:
+            raise ValueError("too many levels")
+        cfg.n_levels = len(levels)
+        for i, n in enumerate(levels):
+            cfg.levels[i] = int(n)
+        cfg.delta = float(delta)
+        cfg.placement = int(placement)
+        cfg.features = int(features)
+        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.weight_scale = float(weight_scale)
+        cfg.precision = int(precision)
+        self.h = C.c_void_p()
+        self._keep = []
+        _check(None, lib().elmfb_create(C.byref(self.h), C.byref(cfg), C.c_void_p(stream or 0)))
+        self.dim = dim
+
+    @classmethod
+    def from_problem(cls, problem, precision=FP64, stream=None):
+        place = PLACE_CELL if problem.placement == "cell" else PLACE_ENDPOINT
+        return cls(problem.dim, problem.lo, problem.hi, problem.levels, problem.delta,
+                   problem.features, problem.seed, problem.weight_scale, precision, place, stream)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().elmfb_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- assemble -------------------------------------------------------------
+    def assemble(self, sets):
+        """sets: list of dicts(points, rhs, c0, c1, c2, weight); sets[0] = interior."""
+        arr = (RowSet * len(sets))()
+        keep = []
+        for i, s in enumerate(sets):
+            pts, kp = _ptr(s["points"])
+            rhs, kr = _ptr(s["rhs"])
+            keep += [kp, kr]
+            arr[i].n = int(s["n"]) if "n" in s else int(len(s["rhs"]))
+            arr[i].points = pts
+            arr[i].rhs = rhs
+            arr[i].c0 = float(s.get("c0", 0.0))
+            for k in range(self.dim):
+                arr[i].c1[k] = float(s.get("c1", (0.0, 0.0))[k])
+                arr[i].c2[k] = float(s.get("c2", (0.0, 0.0))[k])
+            arr[i].weight = float(s.get("weight") or 0.0)
+        _check(self.h, lib().elmfb_assemble(self.h, len(sets), arr))
+
+    def assemble_problem(self, problem):
+        sets = []
+        for rs in [problem.interior] + list(problem.boundary):
+            sets.append(dict(points=np.ascontiguousarray(rs.points, dtype=np.float64),
+                             rhs=np.ascontiguousarray(rs.rhs, dtype=np.float64),
+                             c0=rs.c0, c1=rs.c1, c2=rs.c2, weight=rs.weight))
+        self.assemble(sets)
+
+    def sizes(self) -> Sizes:
+        s = Sizes()
+        _check(self.h, lib().elmfb_get_sizes(self.h, C.byref(s)))
+        return s
+
+    def params(self):
+        s = self.sizes()
+        W = np.zeros((s.n_columns, s.dim))
+        b = np.zeros(s.n_columns)
+        _check(self.h, lib().elmfb_get_params(self.h, W.ctypes.data, b.ctypes.data))
+        return W, b
+
+    def get_rows(self, rows):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        s = self.sizes()
+        out = np.zeros((rows.size, s.n_columns))
+        hh = np.zeros(rows.size)
+        _check(self.h, lib().elmfb_get_rows(self.h, rows.ctypes.data, rows.size,
+                                            out.ctypes.data, hh.ctypes.data))
+        return out, hh
+
+    # -- solve ----------------------------------------------------------------
+    def solve(self, opts: Optional[SolveOpts] = None, **kw) -> SolveInfo:
+        if opts is None:
+            opts = default_solve_opts(**kw)
+        info = SolveInfo()
+        _check(self.h, lib().elmfb_solve(self.h, C.byref(opts), C.byref(info)),
+               allow=(OK, ERR_NOT_CONVERGED))
+        return info
+
+    def coeffs(self):
+        a = np.zeros(self.sizes().n_columns)
+        _check(self.h, lib().elmfb_get_coeffs(self.h, a.ctypes.data))
+        return a
+
+    def set_coeffs(self, a):
+        p, k = _ptr(np.ascontiguousarray(a, dtype=np.float64))
+        _check(self.h, lib().elmfb_set_coeffs(self.h, p))
+
+    # -- eval -----------------------------------------------------------------
+    def eval(self, xs, out=None):
+        xs_c = np.ascontiguousarray(xs, dtype=np.float64) if not hasattr(xs, "data_ptr") else xs
+        n = xs_c.shape[0]
+        if out is None:
+            out = np.zeros(n)
+        px, kx = _ptr(xs_c)
+        po, ko = _ptr(out)
+        _check(self.h, lib().elmfb_eval(self.h, px, n, po))
+        return out
+
+    def error_norms(self, u_hat, u_ref):
+        out = np.zeros(3)
+        pu, ku = _ptr(u_hat if hasattr(u_hat, "data_ptr") else np.ascontiguousarray(u_hat, dtype=np.float64))
+        pr, kr = _ptr(u_ref if hasattr(u_ref, "data_ptr") else np.ascontiguousarray(u_ref, dtype=np.float64))
+        n = int(u_hat.shape[0])
+        _check(self.h, lib().elmfb_error_norms(self.h, pu, pr, n, out.ctypes.data))
+        return {"rel_l2": out[0], "e_l1": out[1], "max_abs": out[2]}
+
+    def stage_times(self):
+        out = np.zeros(N_STAGES)
+        _check(self.h, lib().elmfb_stage_times(self.h, out.ctypes.data))
+        return dict(zip(STAGE_NAMES, out.tolist()))
+
+    def kernel_launches(self) -> int:
+        return int(lib().elmfb_kernel_launches(self.h))
+
+    def set_profiling(self, on: bool = True):
+        _check(self.h, lib().elmfb_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{name: (total_ms, launches, algorithmic bytes per launch)} of the timed kernels."""
+        n = 32
+        names = (C.c_char_p * n)()
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        by = np.zeros(n)
+        k = lib().elmfb_kernel_stats(self.h, n, names, ms.ctypes.data, cnt.ctypes.data,
+                                     by.ctypes.data)
+        if k < 0:
+            _check(self.h, -k)
+        return {names[i].decode(): (float(ms[i]), int(cnt[i]), float(by[i])) for i in range(k)}

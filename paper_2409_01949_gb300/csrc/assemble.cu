@@ -1,0 +1,611 @@
+// System assembly: cell sort of the collocation rows (K0) and the fused panel
+// assembly kernel (K1).
+//
+// The paper defines every entry of M (§3 "Definition of the system matrices")
+//     M[r, q] = s_r / L * Op_r[w_j phi_jk](x_r)
+// with s_r = 1/sqrt(N_I) for interior rows and sqrt(lambda_b / N_B^(b)) for
+// boundary rows, w_j the normalised cos^2 window (§4.1 Eq. window_func) and
+// phi_jk = tanh(w . (x - mu_j)/sigma_j + b) (§3 shallow network, h = 1).  M is
+// nonzero only on I_j x K_j (Eq. multilevel_domain_decomp), so it is stored as
+// one dense row-major panel |I_j| x K per subdomain j.
+//
+// Panel rows are ordered cell-major: the rows of each cell of the common
+// refinement of all supports are contiguous and padded with zero rows to a
+// multiple of 16, in every panel that covers the cell.  A point's covering
+// subdomains, and its row offset inside each of their panels, then follow from
+// its cell alone.
+//
+// K1 evaluates the operator analytically.  With t = 1 - phi^2 and
+// d_i = w_i / sigma_i (= d s / d x_i),
+//     d_i phi = t d_i,    d_ii phi = -2 phi t d_i^2,
+// and the product rule of Op[w phi] collects into
+//     Op[w phi] = phi A + t sum_i beta_i d_i - 2 phi t sum_i gamma_i d_i^2
+// with per-(row, subdomain) A = c0 w + sum c1_i d_i w + sum c2_i d_ii w,
+// beta_i = c1_i w + 2 c2_i d_i w, gamma_i = c2_i w.  A warp computes these for
+// 32 rows (one row per lane), then broadcasts them while every lane evaluates
+// its own features of each row, so stores of a row are contiguous.
+//
+// Window factors use the half-angle form 1 + cos(theta) = 2 cos^2(theta/2):
+//     f = 4 c^4,  f' = -8 c^3 s g,  f'' = 4 c^2 (3 s^2 - c^2) g^2
+// with (s, c) = sincos(theta/2), g = pi/sigma, which keeps full relative
+// accuracy near the support edge (theta -> +-pi) where 1 + cos(theta) cancels;
+// there c = sin(pi u / 2) with the edge distance u = (sigma - |x - mu|)/sigma
+// formed in FP64.  The support test is |x - mu| < sigma in FP64, as in the
+// paper's open support.
+// tanh is formed from expm1: e = expm1(2|s|), phi = sign(s) e/(e+2) and
+// 1 - phi^2 = 4 (e+1)/(e+2)^2, free of cancellation for every s.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "elmfb_internal.cuh"
+
+namespace {
+
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
+
+__constant__ RowClass c_cls[kMaxClasses];
+
+// ------------------------------------------------------------------ K0 ------
+__global__ void k_cell_of_rows(const double* __restrict__ pts, int64_t n, int dim,
+                               const double* __restrict__ bnd, int nc0, int nc1,
+                               double lo0, double hi0, double lo1, double hi1,
+                               int* __restrict__ row_cell, int* __restrict__ count,
+                               int* __restrict__ flags) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int c[2] = {0, 0};
+  const int ncs[2] = {nc0, nc1};
+  const double los[2] = {lo0, lo1}, his[2] = {hi0, hi1};
+  const double* b = bnd;
+  for (int i = 0; i < dim; ++i) {
+    double x = pts[r * dim + i];
+    if (!(x >= los[i] && x <= his[i])) atomicOr(&flags[0], 1);  // outside the box / NaN
+    // last boundary <= x
+    int lo = 0, hi = ncs[i];  // search in b[0..nc]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (b[mid] <= x) lo = mid;
+      else hi = mid;
+    }
+    c[i] = lo;
+    b += ncs[i] + 1;
+  }
+  int cell = c[1] * nc0 + c[0];
+  row_cell[r] = cell;
+  atomicAdd(&count[cell], 1);
+}
+
+__global__ void k_scatter_rows(const int* __restrict__ row_cell, int64_t n,
+                               const int* __restrict__ cell_pstart, int* __restrict__ fill,
+                               int* __restrict__ sorted) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int c = row_cell[r];
+  int slot = atomicAdd(&fill[c], 1);
+  sorted[cell_pstart[c] + slot] = (int)r;
+}
+
+// One CTA per cell: order the cell's rows by their user index (rank sort in
+// shared memory), so the layout does not depend on atomic arrival order.
+__global__ void k_sort_cells(const int* __restrict__ count, const int* __restrict__ cell_pstart,
+                             int* __restrict__ sorted) {
+  extern __shared__ int sh[];
+  int c = blockIdx.x;
+  int n = count[c];
+  if (n <= 1) return;
+  int* seg = sorted + cell_pstart[c];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = seg[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int v = sh[i], rank = 0;
+    for (int j = 0; j < n; ++j) rank += sh[j] < v;
+    seg[rank] = v;
+  }
+}
+
+__global__ void k_gather_rows(const int* __restrict__ sorted, int64_t NR, int dim,
+                              const double* __restrict__ pts, const double* __restrict__ rhs,
+                              const int* __restrict__ cls_user, const int* __restrict__ row_cell,
+                              double* __restrict__ x, int* __restrict__ rcls,
+                              double* __restrict__ hvec, int* __restrict__ grow_cell,
+                              int* __restrict__ user_to_sorted, const int* __restrict__ cell_of_R) {
+  int64_t R = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= NR) return;
+  int r = sorted[R];
+  grow_cell[R] = cell_of_R[R];
+  if (r < 0) {
+    for (int i = 0; i < dim; ++i) x[R * dim + i] = 0.0;
+    rcls[R] = -1;
+    hvec[R] = 0.0;
+    return;
+  }
+  for (int i = 0; i < dim; ++i) x[R * dim + i] = pts[(int64_t)r * dim + i];
+  int k = cls_user[r];
+  rcls[R] = k;
+  // scaled right-hand side (§3 "Definition of vectors")
+  hvec[R] = rhs[r] * c_cls[k].hscale;
+  user_to_sorted[r] = (int)R;
+}
+
+__global__ void k_fill_cell_of_R(const int* __restrict__ cell_pstart, int n_cells,
+                                 int* __restrict__ cell_of_R) {
+  int c = blockIdx.x;
+  if (c >= n_cells) return;
+  for (int p = cell_pstart[c] + threadIdx.x; p < cell_pstart[c + 1]; p += blockDim.x)
+    cell_of_R[p] = c;
+}
+
+// ------------------------------------------------------------------ K1 ------
+template <class T> struct Math;
+template <> struct Math<float> {
+  static __device__ __forceinline__ void sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+  static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float pi() { return kPiF; }
+};
+template <> struct Math<double> {
+  static __device__ __forceinline__ void sincospi(double x, double* s, double* c) { ::sincospi(x, s, c); }
+  static __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double pi() { return kPiD; }
+};
+
+// tanh(s) and 1 - tanh(s)^2 from one expm1 (see file header)
+template <class T>
+__device__ __forceinline__ void tanh_pair(T s, T* phi, T* t) {
+  T as = fabs(s);
+  as = as < T(15) ? as : T(15);
+  T e = Math<T>::expm1(T(2) * as);
+  T r = Math<T>::rcp(e + T(2));
+  T p = e * r;
+  *phi = copysign(p, s);
+  *t = T(4) * (e + T(1)) * r * r;
+}
+
+// Normalised window of subdomain `own` and its derivatives at one point, from
+// the covering subdomains of its level (list [b, e) of cover_sub).
+template <class T>
+__device__ __forceinline__ void window_at(const double* x, int dim, const SubGeom* __restrict__ sub,
+                                          const int* __restrict__ cover_sub, int b, int e, int own,
+                                          T& om, T dom[2], T ddom[2], T xt_own[2]) {
+  T S = 0, dS[2] = {0, 0}, ddS[2] = {0, 0};
+  T wo = 0, dwo[2] = {0, 0}, ddwo[2] = {0, 0};
+  xt_own[0] = xt_own[1] = 0;
+  for (int k = b; k < e; ++k) {
+    int t = cover_sub[k];
+    const SubGeom g = sub[t];
+    T f[2], fp[2], fpp[2];
+    for (int i = 0; i < 2; ++i) {
+      f[i] = 1;
+      fp[i] = 0;
+      fpp[i] = 0;
+    }
+    for (int i = 0; i < dim; ++i) {
+      // support test and edge distance in FP64, exactly as |x - mu| < sigma
+      const double dx = x[i] - g.mu[i];
+      const double adx = fabs(dx);
+      const T inv_s = sizeof(T) == 8 ? (T)g.inv_sigma_d[i] : (T)g.inv_sigma[i];
+      const T xt = (T)dx * inv_s;
+      if (t == own) xt_own[i] = xt;
+      if (adx < g.sigma_d[i]) {
+        // half angle theta/2 = pi xt / 2: (sh, ch) = (sin, cos)(theta/2).  Near the
+        // edge use u = 1 - |xt| = (sigma - |dx|)/sigma formed in FP64, so
+        // ch = sin(pi u / 2) keeps its relative accuracy as ch -> 0.
+        T sh, ch;
+        const double ud = (g.sigma_d[i] - adx) * g.inv_sigma_d[i];
+        if (ud < 0.5) {
+          T su, cu;
+          Math<T>::sincospi(T(0.5) * (T)ud, &su, &cu);
+          ch = su;
+          sh = dx < 0.0 ? -cu : cu;
+        } else {
+          Math<T>::sincospi(T(0.5) * xt, &sh, &ch);
+        }
+        const T gg = Math<T>::pi() * inv_s;
+        const T c2 = ch * ch;
+        f[i] = T(4) * c2 * c2;
+        fp[i] = T(-8) * c2 * ch * sh * gg;
+        fpp[i] = T(4) * c2 * (T(3) * sh * sh - c2) * gg * gg;
+      } else {
+        f[i] = 0;
+        fp[i] = 0;
+        fpp[i] = 0;
+      }
+    }
+    T w = f[0] * f[1];
+    T dw[2], ddw[2];
+    dw[0] = fp[0] * f[1];
+    ddw[0] = fpp[0] * f[1];
+    dw[1] = f[0] * fp[1];
+    ddw[1] = f[0] * fpp[1];
+    S += w;
+    for (int i = 0; i < 2; ++i) {
+      dS[i] += dw[i];
+      ddS[i] += ddw[i];
+    }
+    if (t == own) {
+      wo = w;
+      for (int i = 0; i < 2; ++i) {
+        dwo[i] = dw[i];
+        ddwo[i] = ddw[i];
+      }
+    }
+  }
+  T iS = T(1) / S;
+  om = wo * iS;
+  for (int i = 0; i < 2; ++i) {
+    T a = dS[i] * iS;
+    dom[i] = (dwo[i] - wo * a) * iS;
+    ddom[i] = (ddwo[i] - T(2) * dwo[i] * a - wo * ddS[i] * iS + T(2) * wo * a * a) * iS;
+  }
+}
+
+template <class T, int FPL>
+__global__ void __launch_bounds__(128) k_assemble(
+    const int2* __restrict__ tiles, int64_t n_tiles, int dim, int K, int L,
+    const SubGeom* __restrict__ sub, const int* __restrict__ cover_sub,
+    const int* __restrict__ cover_start, const int* __restrict__ entry_cell,
+    const int* __restrict__ cell_level_off, const int* __restrict__ cell_count,
+    const int* __restrict__ cell_pstart, const int64_t* __restrict__ panel_off,
+    const double* __restrict__ xs, const int* __restrict__ rcls,
+    const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels) {
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= n_tiles) return;
+  const int2 tile = tiles[t];
+  const int e = tile.x, p0 = tile.y;
+  const int c = entry_cell[e];
+  const int s = cover_sub[e];
+  const SubGeom gs = sub[s];
+  const int lev = gs.level;
+  const int cnt = cell_count[c];
+  const int pad = cell_pstart[c + 1] - cell_pstart[c];
+  const int nrows = min(32, pad - p0);
+  const int64_t R0 = cell_pstart[c] + p0;
+  T* out = panels + (panel_off[s] + cover_start[e] + p0) * (int64_t)K;
+
+  // phase 1: lane = row
+  T A = 0, be0 = 0, be1 = 0, ga0 = 0, ga1 = 0, xt0 = 0, xt1 = 0;
+  const int p = p0 + lane;
+  if (lane < nrows && p < cnt) {
+    const int64_t R = R0 + lane;
+    double x[2] = {xs[R * dim], dim == 2 ? xs[R * dim + 1] : 0.0};
+    const int b = cell_level_off[(int64_t)c * (L + 1) + lev];
+    const int en = cell_level_off[(int64_t)c * (L + 1) + lev + 1];
+    T om, dom[2], ddom[2], xt[2];
+    window_at<T>(x, dim, sub, cover_sub, b, en, s, om, dom, ddom, xt);
+    const RowClass rc = c_cls[rcls[R]];
+    const T sc = (T)rc.scale;
+    A = sc * ((T)rc.c0 * om + (T)rc.c1[0] * dom[0] + (T)rc.c2[0] * ddom[0] +
+              (T)rc.c1[1] * dom[1] + (T)rc.c2[1] * ddom[1]);
+    be0 = sc * ((T)rc.c1[0] * om + T(2) * (T)rc.c2[0] * dom[0]);
+    be1 = sc * ((T)rc.c1[1] * om + T(2) * (T)rc.c2[1] * dom[1]);
+    ga0 = sc * (T)rc.c2[0] * om;
+    ga1 = sc * (T)rc.c2[1] * om;
+    xt0 = xt[0];
+    xt1 = xt[1];
+  }
+
+  // per-lane feature constants: features k = lane + 32 i
+  T w0[FPL], w1[FPL], bb[FPL], d0[FPL], d1[FPL];
+  const T is0 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[0] : (T)gs.inv_sigma[0];
+  const T is1 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[1] : (T)gs.inv_sigma[1];
+#pragma unroll
+  for (int i = 0; i < FPL; ++i) {
+    int k = lane + 32 * i;
+    if (k < K) {
+      int64_t q = (int64_t)s * K + k;
+      w0[i] = W[q * dim];
+      w1[i] = dim == 2 ? W[q * dim + 1] : T(0);
+      bb[i] = Bias[q];
+    } else {
+      w0[i] = w1[i] = bb[i] = 0;
+    }
+    d0[i] = w0[i] * is0;
+    d1[i] = w1[i] * is1;
+  }
+
+  // phase 2: broadcast one row at a time
+  for (int r = 0; r < nrows; ++r) {
+    const T rA = __shfl_sync(0xffffffffu, A, r);
+    const T rb0 = __shfl_sync(0xffffffffu, be0, r);
+    const T rb1 = __shfl_sync(0xffffffffu, be1, r);
+    const T rg0 = __shfl_sync(0xffffffffu, ga0, r);
+    const T rg1 = __shfl_sync(0xffffffffu, ga1, r);
+    const T rx0 = __shfl_sync(0xffffffffu, xt0, r);
+    const T rx1 = __shfl_sync(0xffffffffu, xt1, r);
+    T* orow = out + (int64_t)r * K;
+#pragma unroll
+    for (int i = 0; i < FPL; ++i) {
+      int k = lane + 32 * i;
+      if (k < K) {
+        T sarg = w0[i] * rx0 + w1[i] * rx1 + bb[i];
+        T phi, tt;
+        tanh_pair<T>(sarg, &phi, &tt);
+        T v = phi * rA + tt * (rb0 * d0[i] + rb1 * d1[i]) -
+              T(2) * phi * tt * (rg0 * d0[i] * d0[i] + rg1 * d1[i] * d1[i]);
+        orow[k] = v;
+      }
+    }
+  }
+}
+
+template <class T>
+void launch_assemble(elmfb_ctx* h) {
+  const int K = h->K;
+  const int fpl = (K + 31) / 32;
+  const int warps = 4;
+  const int64_t blocks = ceil_div(h->n_tiles, warps);
+  if (blocks == 0) return;
+  const T* W = sizeof(T) == 8 ? (const T*)h->d_W64.p : (const T*)h->d_W32.p;
+  const T* B = sizeof(T) == 8 ? (const T*)h->d_b64.p : (const T*)h->d_b32.p;
+#define ELMFB_K1(F)                                                                          \
+  case F:                                                                                    \
+    k_assemble<T, F><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(                        \
+        h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),          \
+        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),     \
+        h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(), h->d_cell_pstart.as<int>(), \
+        h->d_panel_off.as<int64_t>(), h->d_x.as<double>(), h->d_rcls.as<int>(), W, B,        \
+        (T*)h->d_panels.p);                                                                  \
+    break;
+  // algorithmic bytes: every panel entry written once, point data read once
+  prof_begin(h, KID_ASSEMBLE,
+             (double)h->NPR * K * sizeof(T) + (double)h->NR * (h->dim * 8.0 + 4.0));
+  switch (fpl) {
+    ELMFB_K1(1) ELMFB_K1(2) ELMFB_K1(3) ELMFB_K1(4) ELMFB_K1(5) ELMFB_K1(6) ELMFB_K1(7) ELMFB_K1(8)
+    default: ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "features > 256");
+  }
+#undef ELMFB_K1
+  prof_end(h, KID_ASSEMBLE);
+  check_launch("k_assemble");
+  count_launch(h);
+}
+
+// --------------------------------------------------------------- export -----
+template <class T>
+__global__ void k_export_rows(const int64_t* __restrict__ rows, int64_t n,
+                              const int* __restrict__ user_to_sorted,
+                              const int* __restrict__ grow_cell, const int* __restrict__ cell_pstart,
+                              const int* __restrict__ cover_off, const int* __restrict__ cover_sub,
+                              const int* __restrict__ cover_start,
+                              const int64_t* __restrict__ panel_off, const T* __restrict__ panels,
+                              int K, int64_t NPhi, const double* __restrict__ hvec,
+                              double* __restrict__ out, double* __restrict__ hout) {
+  int64_t i = blockIdx.x;
+  if (i >= n) return;
+  int R = user_to_sorted[rows[i]];
+  int c = grow_cell[R];
+  int p = R - cell_pstart[c];
+  if (threadIdx.x == 0 && hout) hout[i] = hvec[R];
+  for (int e = cover_off[c]; e < cover_off[c + 1]; ++e) {
+    int s = cover_sub[e];
+    const T* src = panels + (panel_off[s] + cover_start[e] + p) * (int64_t)K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+      out[i * NPhi + (int64_t)s * K + k] = (double)src[k];
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
+  cudaStream_t st = h->stream;
+  h->assembled = false;
+  h->have_coeffs = false;
+  const int dim = h->dim;
+  int64_t n = 0;
+  for (int b = 0; b < n_sets; ++b) {
+    if (sets[b].n < 0 || (sets[b].n > 0 && (!sets[b].points || !sets[b].rhs)))
+      ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "row set " + std::to_string(b) + ": bad pointers");
+    if (b > 0 && !(sets[b].weight > 0.0))
+      ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "boundary weight must be > 0");
+    n += sets[b].n;
+  }
+  if (sets[0].n < 1) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "empty interior set");
+  if (n >= (int64_t)1 << 31) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "more than 2^31 rows");
+  h->n_rows = n;
+
+  // row classes (§3: interior scale 1/sqrt(N_I), boundary sqrt(lambda_b / N_B^(b)); 1/L folded in)
+  h->n_classes = n_sets;
+  for (int b = 0; b < n_sets; ++b) {
+    RowClass rc{};
+    rc.c0 = sets[b].c0;
+    for (int i = 0; i < 2; ++i) {
+      rc.c1[i] = i < dim ? sets[b].c1[i] : 0.0;
+      rc.c2[i] = i < dim ? sets[b].c2[i] : 0.0;
+    }
+    double s = b == 0 ? 1.0 / std::sqrt((double)sets[0].n)
+                      : (sets[b].n > 0 ? std::sqrt(sets[b].weight / (double)sets[b].n) : 0.0);
+    rc.scale = s / h->L;
+    rc.hscale = s;
+    h->cls[b] = rc;
+  }
+  CUDA_CHECK(cudaMemcpyToSymbolAsync(c_cls, h->cls, sizeof(RowClass) * n_sets, 0,
+                                     cudaMemcpyHostToDevice, st));
+
+  stage_begin(h, 7);
+  stage_begin(h, 1);
+  // user-order inputs
+  h->d_pts_user.alloc(n * dim * sizeof(double), st);
+  h->d_rhs_user.alloc(n * sizeof(double), st);
+  h->d_cls_user.alloc(n * sizeof(int), st);
+  std::vector<int> cls_user(n);
+  {
+    int64_t off = 0;
+    for (int b = 0; b < n_sets; ++b) {
+      int64_t m = sets[b].n;
+      if (m == 0) continue;
+      CUDA_CHECK(cudaMemcpyAsync(h->d_pts_user.as<double>() + off * dim, sets[b].points,
+                                 m * dim * sizeof(double), cudaMemcpyDefault, st));
+      CUDA_CHECK(cudaMemcpyAsync(h->d_rhs_user.as<double>() + off, sets[b].rhs, m * sizeof(double),
+                                 cudaMemcpyDefault, st));
+      std::fill(cls_user.begin() + off, cls_user.begin() + off + m, b);
+      off += m;
+    }
+  }
+  CUDA_CHECK(cudaMemcpyAsync(h->d_cls_user.p, cls_user.data(), n * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+
+  // K0: cells
+  const int nc = h->n_cells;
+  h->d_row_cell.alloc(n * sizeof(int), st);
+  h->d_cell_count.alloc(nc * sizeof(int), st);
+  h->d_cell_fill.alloc(nc * sizeof(int), st);
+  CUDA_CHECK(cudaMemsetAsync(h->d_cell_count.p, 0, nc * sizeof(int), st));
+  CUDA_CHECK(cudaMemsetAsync(h->d_cell_fill.p, 0, nc * sizeof(int), st));
+  CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
+  k_cell_of_rows<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
+      h->d_pts_user.as<double>(), n, dim, h->d_bnd.as<double>(), h->nc[0], h->nc[1], h->cfg.lo[0],
+      h->cfg.hi[0], dim == 2 ? h->cfg.lo[1] : 0.0, dim == 2 ? h->cfg.hi[1] : 1.0,
+      h->d_row_cell.as<int>(), h->d_cell_count.as<int>(), h->d_flags.as<int>());
+  check_launch("k_cell_of_rows");
+  count_launch(h);
+  h->cell_count.resize(nc);
+  int flags[4];
+  CUDA_CHECK(cudaMemcpyAsync(h->cell_count.data(), h->d_cell_count.p, nc * sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  if (flags[0]) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "a collocation point lies outside the domain box");
+
+  // host: padded cell layout, panel offsets, tiles
+  h->cell_pstart.assign(nc + 1, 0);
+  int max_count = 0;
+  for (int c = 0; c < nc; ++c) {
+    int cnt = h->cell_count[c];
+    max_count = std::max(max_count, cnt);
+    h->cell_pstart[c + 1] = h->cell_pstart[c] + (int)ceil_div(cnt, kCellPad) * kCellPad;
+  }
+  if (max_count > kMaxCellPoints)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "a cell holds more than 16384 collocation points");
+  h->NR = h->cell_pstart[nc];
+  const int ne = (int)h->cover_sub.size();
+  h->cover_start.assign(ne, 0);
+  h->panel_off.assign(h->n_sub + 1, 0);
+  std::vector<int64_t> panel_len(h->n_sub, 0);
+  // cells are visited in increasing id (y-major), so each panel's rows are cell-major
+  for (int c = 0; c < nc; ++c) {
+    int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
+    for (int e = h->cover_off[c]; e < h->cover_off[c + 1]; ++e) {
+      int s = h->cover_sub[e];
+      h->cover_start[e] = (int)panel_len[s];
+      panel_len[s] += pad;
+    }
+  }
+  for (int s = 0; s < h->n_sub; ++s) h->panel_off[s + 1] = h->panel_off[s] + panel_len[s];
+  h->NPR = h->panel_off[h->n_sub];
+  if (h->NPR >= (int64_t)1 << 31) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "more than 2^31 panel rows");
+  h->nnz = 0;
+  std::vector<int2> tiles;
+  for (int e = 0; e < ne; ++e) {
+    int c = h->entry_cell[e];
+    int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
+    h->nnz += (int64_t)h->cell_count[c] * h->K;
+    for (int p = 0; p < pad; p += 32) tiles.push_back(make_int2(e, p));
+  }
+  h->n_tiles = (int64_t)tiles.size();
+  // Gram pair count: subdomain pairs (i <= j) that share a cell with points
+  {
+    std::vector<std::vector<int>> nb(h->n_sub);
+    for (int c = 0; c < nc; ++c) {
+      if (h->cell_count[c] == 0) continue;
+      for (int e = h->cover_off[c]; e < h->cover_off[c + 1]; ++e)
+        for (int f = e; f < h->cover_off[c + 1]; ++f) nb[h->cover_sub[e]].push_back(h->cover_sub[f]);
+    }
+    h->n_gram_pairs = 0;
+    for (auto& v : nb) {
+      std::sort(v.begin(), v.end());
+      h->n_gram_pairs += std::unique(v.begin(), v.end()) - v.begin();
+    }
+  }
+
+  auto up = [&](DevBuf& b, const void* src, size_t bytes) {
+    b.alloc(std::max<size_t>(bytes, 4), st);
+    if (bytes) CUDA_CHECK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
+  };
+  up(h->d_cell_pstart, h->cell_pstart.data(), (nc + 1) * sizeof(int));
+  up(h->d_cover_start, h->cover_start.data(), ne * sizeof(int));
+  up(h->d_panel_off, h->panel_off.data(), (h->n_sub + 1) * sizeof(int64_t));
+  up(h->d_tiles, tiles.data(), tiles.size() * sizeof(int2));
+
+  // K0: scatter into cells, deterministic order inside each cell, gather row data
+  const int64_t NR = h->NR;
+  h->d_sorted.alloc(NR * sizeof(int), st);
+  CUDA_CHECK(cudaMemsetAsync(h->d_sorted.p, 0xff, NR * sizeof(int), st));
+  k_scatter_rows<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
+      h->d_row_cell.as<int>(), n, h->d_cell_pstart.as<int>(), h->d_cell_fill.as<int>(),
+      h->d_sorted.as<int>());
+  check_launch("k_scatter_rows");
+  const size_t sort_smem = std::max(max_count, 1) * sizeof(int);
+  if (sort_smem > 48 * 1024)
+    CUDA_CHECK(cudaFuncSetAttribute(k_sort_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sort_smem));
+  prof_begin(h, KID_CELL_SORT, 8.0 * (double)NR);
+  k_sort_cells<<<nc, 256, sort_smem, st>>>(
+      h->d_cell_count.as<int>(), h->d_cell_pstart.as<int>(), h->d_sorted.as<int>());
+  prof_end(h, KID_CELL_SORT);
+  check_launch("k_sort_cells");
+  h->d_grow_cell.alloc(NR * sizeof(int), st);
+  h->d_x.alloc(NR * dim * sizeof(double), st);
+  h->d_rcls.alloc(NR * sizeof(int), st);
+  h->d_h.alloc(NR * sizeof(double), st);
+  h->d_u2s.alloc(n * sizeof(int), st);
+  h->d_tmp.alloc(NR * sizeof(int), st);
+  int* user_to_sorted = h->d_u2s.as<int>();
+  int* cell_of_R = h->d_tmp.as<int>();
+  k_fill_cell_of_R<<<nc, 128, 0, st>>>(h->d_cell_pstart.as<int>(), nc, cell_of_R);
+  check_launch("k_fill_cell_of_R");
+  k_gather_rows<<<(unsigned)ceil_div(NR, 256), 256, 0, st>>>(
+      h->d_sorted.as<int>(), NR, dim, h->d_pts_user.as<double>(), h->d_rhs_user.as<double>(),
+      h->d_cls_user.as<int>(), h->d_row_cell.as<int>(), h->d_x.as<double>(), h->d_rcls.as<int>(),
+      h->d_h.as<double>(), h->d_grow_cell.as<int>(), user_to_sorted, cell_of_R);
+  check_launch("k_gather_rows");
+  count_launch(h, 4);
+  stage_end(h, 1);
+
+  // K1: panels
+  stage_begin(h, 2);
+  h->d_panels.alloc(h->NPR * h->K * h->panel_elem(), st);
+  if (h->fp64()) launch_assemble<double>(h);
+  else launch_assemble<float>(h);
+  stage_end(h, 2);
+  stage_end(h, 7);
+  h->assembled = true;
+}
+
+void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, double* h_out) {
+  if (n == 0) return;
+  cudaStream_t st = h->stream;
+  DevBuf drows, dout, dh;
+  drows.alloc(n * sizeof(int64_t), st);
+  CUDA_CHECK(cudaMemcpyAsync(drows.p, rows, n * sizeof(int64_t), cudaMemcpyDefault, st));
+  {
+    std::vector<int64_t> hr(n);
+    CUDA_CHECK(cudaMemcpyAsync(hr.data(), drows.p, n * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    for (int64_t v : hr)
+      if (v < 0 || v >= h->n_rows) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "row index out of range");
+  }
+  dout.alloc(n * h->NPhi * sizeof(double), st);
+  dh.alloc(n * sizeof(double), st);
+  CUDA_CHECK(cudaMemsetAsync(dout.p, 0, n * h->NPhi * sizeof(double), st));
+  if (h->fp64())
+    k_export_rows<double><<<(unsigned)n, 128, 0, st>>>(
+        drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
+        h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
+        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), h->d_panels.as<double>(), h->K,
+        h->NPhi, h->d_h.as<double>(), dout.as<double>(), dh.as<double>());
+  else
+    k_export_rows<float><<<(unsigned)n, 128, 0, st>>>(
+        drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
+        h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
+        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), h->d_panels.as<float>(), h->K,
+        h->NPhi, h->d_h.as<double>(), dout.as<double>(), dh.as<double>());
+  check_launch("k_export_rows");
+  count_launch(h);
+  CUDA_CHECK(cudaMemcpyAsync(out, dout.p, n * h->NPhi * sizeof(double), cudaMemcpyDefault, st));
+  if (h_out) CUDA_CHECK(cudaMemcpyAsync(h_out, dh.p, n * sizeof(double), cudaMemcpyDefault, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}

@@ -1,0 +1,522 @@
+// Handle lifetime, geometry, random parameters and the thin ABI wrappers.
+//
+// Geometry follows the paper's §4.1 "Domain decomposition": per level a
+// uniform tensor grid of n^d subdomains with centres mu and half-width
+// sigma = delta * spacing / 2.  The random hidden parameters follow §4.1
+// "weight initialisation" (U(-a, a)), drawn from SplitMix64 (Steele, Lea &
+// Flood 2014) by the counter stream documented in elmfb.h.
+//
+// Besides the paper's quantities this file builds the "cells": the common
+// refinement of every subdomain support along each dimension.  Every cell lies
+// entirely inside or outside each support, so all points of a cell share one
+// set of covering subdomains; the row layout of the panels and the Gram pair
+// structure are built on it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "elmfb_internal.cuh"
+
+namespace {
+
+inline uint64_t splitmix64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+inline uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  return splitmix64_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+template <class F>
+int guarded(elmfb_ctx* h, F&& f) {
+  if (!h) return ELMFB_ERR_INVALID_ARG;
+  try {
+    CUDA_CHECK(cudaSetDevice(h->device));
+    h->err.clear();
+    f();
+    return ELMFB_OK;
+  } catch (const elmfb_error& e) {
+    h->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
+  }
+}
+
+void build_geometry(elmfb_ctx* h) {
+  const elmfb_config& c = h->cfg;
+  h->dim = c.dim;
+  h->L = c.n_levels;
+  h->K = c.features;
+  h->lev_n.assign(c.levels, c.levels + c.n_levels);
+  h->lev_sub_off.assign(h->L + 1, 0);
+  for (int l = 0; l < h->L; ++l) {
+    int J = 1;
+    for (int i = 0; i < h->dim; ++i) J *= h->lev_n[l];
+    h->lev_sub_off[l + 1] = h->lev_sub_off[l] + J;
+  }
+  h->n_sub = h->lev_sub_off[h->L];
+  h->NPhi = (int64_t)h->n_sub * h->K;
+
+  // centres and half-widths per level and dimension
+  std::vector<std::vector<double>> mu(h->L * 2);
+  std::vector<double> sig(h->L * 2, 0.0);
+  for (int l = 0; l < h->L; ++l) {
+    int n = h->lev_n[l];
+    for (int i = 0; i < h->dim; ++i) {
+      double lo = c.lo[i], hi = c.hi[i], D;
+      std::vector<double>& m = mu[l * 2 + i];
+      m.resize(n);
+      if (c.placement == ELMFB_PLACE_CELL) {
+        D = (hi - lo) / n;
+        for (int j = 0; j < n; ++j) m[j] = lo + (j + 0.5) * D;
+      } else {
+        if (n == 1) {
+          D = hi - lo;
+          m[0] = 0.5 * (lo + hi);
+        } else {
+          D = (hi - lo) / (n - 1);
+          for (int j = 0; j < n; ++j) m[j] = lo + j * D;
+        }
+      }
+      sig[l * 2 + i] = c.delta * D / 2.0;
+    }
+  }
+  h->sub.resize(h->n_sub);
+  for (int l = 0; l < h->L; ++l) {
+    int n = h->lev_n[l];
+    for (int j = h->lev_sub_off[l]; j < h->lev_sub_off[l + 1]; ++j) {
+      int loc = j - h->lev_sub_off[l];
+      int ji[2] = {loc % n, h->dim == 2 ? loc / n : 0};
+      SubGeom g{};
+      for (int i = 0; i < 2; ++i) {
+        if (i < h->dim) {
+          g.mu[i] = mu[l * 2 + i][ji[i]];
+          g.sigma_d[i] = sig[l * 2 + i];
+          g.inv_sigma_d[i] = 1.0 / sig[l * 2 + i];
+          g.inv_sigma[i] = (float)g.inv_sigma_d[i];
+        } else {
+          g.mu[i] = 0.0;
+          g.sigma_d[i] = 1.0;
+          g.inv_sigma_d[i] = 0.0;
+          g.inv_sigma[i] = 0.f;
+        }
+      }
+      g.level = l;
+      h->sub[j] = g;
+    }
+  }
+
+  // random parameters: column q draws outputs q*(d+1)+p
+  const int d = h->dim;
+  h->Wh.resize((size_t)h->NPhi * d);
+  h->bh.resize(h->NPhi);
+  const double a = c.weight_scale;
+  for (int64_t q = 0; q < h->NPhi; ++q) {
+    for (int p = 0; p <= d; ++p) {
+      uint64_t z = splitmix64_at(c.seed, (uint64_t)q * (d + 1) + p);
+      double u = (double)(z >> 40) * (1.0 / 16777216.0);
+      double v = a * (2.0 * u - 1.0);
+      if (p < d) h->Wh[q * d + p] = v;
+      else h->bh[q] = v;
+    }
+  }
+
+  // cells: common refinement of all supports, per dimension
+  for (int i = 0; i < 2; ++i) {
+    h->bnd[i].clear();
+    h->sub_c0[i].assign(h->n_sub, 0);
+    h->sub_c1[i].assign(h->n_sub, 1);
+    if (i >= h->dim) {
+      h->bnd[i] = {0.0, 1.0};
+      h->nc[i] = 1;
+      continue;
+    }
+    double lo = c.lo[i], hi = c.hi[i];
+    double tol = 1e-12 * (hi - lo);
+    std::vector<double> b = {lo, hi};
+    for (int l = 0; l < h->L; ++l)
+      for (double m : mu[l * 2 + i]) {
+        double e0 = m - sig[l * 2 + i], e1 = m + sig[l * 2 + i];
+        if (e0 > lo + tol && e0 < hi - tol) b.push_back(e0);
+        if (e1 > lo + tol && e1 < hi - tol) b.push_back(e1);
+      }
+    std::sort(b.begin(), b.end());
+    std::vector<double> u;
+    for (double v : b)
+      if (u.empty() || v > u.back() + tol) u.push_back(v);
+    u.back() = hi;
+    h->bnd[i] = u;
+    h->nc[i] = (int)u.size() - 1;
+    // cell range of each subdomain along this dimension
+    for (int s = 0; s < h->n_sub; ++s) {
+      int l = h->sub[s].level;
+      double e0 = h->sub[s].mu[i] - sig[l * 2 + i], e1 = h->sub[s].mu[i] + sig[l * 2 + i];
+      int c0 = h->nc[i], c1 = 0;
+      for (int cc = 0; cc < h->nc[i]; ++cc) {
+        if (u[cc] >= e0 - tol && u[cc + 1] <= e1 + tol) {
+          c0 = std::min(c0, cc);
+          c1 = std::max(c1, cc + 1);
+        }
+      }
+      if (c1 <= c0) c0 = c1 = 0;  // support misses the box entirely
+      h->sub_c0[i][s] = c0;
+      h->sub_c1[i][s] = c1;
+    }
+  }
+  h->n_cells = h->nc[0] * h->nc[1];
+
+  // covering index range per level, dimension and cell coordinate
+  std::vector<int> jlo((size_t)h->L * 2 * std::max(h->nc[0], h->nc[1])),
+      jhi(jlo.size());
+  auto rix = [&](int l, int i, int cc) { return ((size_t)l * 2 + i) * std::max(h->nc[0], h->nc[1]) + cc; };
+  for (int l = 0; l < h->L; ++l) {
+    int n = h->lev_n[l];
+    for (int i = 0; i < 2; ++i)
+      for (int cc = 0; cc < h->nc[i]; ++cc) {
+        int lo_j = n, hi_j = 0;
+        if (i >= h->dim) {
+          lo_j = 0;
+          hi_j = 1;
+        } else {
+          for (int j = 0; j < n; ++j) {
+            int s = h->lev_sub_off[l] + (i == 0 ? j : j * n);
+            if (cc >= h->sub_c0[i][s] && cc < h->sub_c1[i][s]) {
+              lo_j = std::min(lo_j, j);
+              hi_j = std::max(hi_j, j + 1);
+            }
+          }
+        }
+        if (hi_j <= lo_j)
+          ELMFB_THROW(ELMFB_ERR_INVALID_ARG,
+                      "level " + std::to_string(l) +
+                          " leaves part of the domain uncovered (width ratio too small)");
+        jlo[rix(l, i, cc)] = lo_j;
+        jhi[rix(l, i, cc)] = hi_j;
+      }
+  }
+  // covering subdomains per cell, grouped by level, increasing subdomain id
+  h->cover_off.assign(h->n_cells + 1, 0);
+  h->cell_level_off.assign((size_t)h->n_cells * (h->L + 1), 0);
+  h->cover_sub.clear();
+  h->max_cover = 0;
+  for (int cy = 0; cy < h->nc[1]; ++cy)
+    for (int cx = 0; cx < h->nc[0]; ++cx) {
+      int cell = cy * h->nc[0] + cx;
+      h->cover_off[cell] = (int)h->cover_sub.size();
+      for (int l = 0; l < h->L; ++l) {
+        h->cell_level_off[(size_t)cell * (h->L + 1) + l] = (int)h->cover_sub.size();
+        int n = h->lev_n[l];
+        for (int jy = jlo[rix(l, 1, cy)]; jy < jhi[rix(l, 1, cy)]; ++jy)
+          for (int jx = jlo[rix(l, 0, cx)]; jx < jhi[rix(l, 0, cx)]; ++jx)
+            h->cover_sub.push_back(h->lev_sub_off[l] + jy * n + jx);
+      }
+      h->cell_level_off[(size_t)cell * (h->L + 1) + h->L] = (int)h->cover_sub.size();
+      h->max_cover = std::max(h->max_cover, (int)h->cover_sub.size() - h->cover_off[cell]);
+    }
+  h->cover_off[h->n_cells] = (int)h->cover_sub.size();
+  h->entry_cell.resize(h->cover_sub.size());
+  for (int cell = 0; cell < h->n_cells; ++cell)
+    for (int e = h->cover_off[cell]; e < h->cover_off[cell + 1]; ++e) h->entry_cell[e] = cell;
+}
+
+template <class T>
+void upload(elmfb_ctx* h, DevBuf& b, const std::vector<T>& v) {
+  b.alloc(std::max<size_t>(v.size(), 1) * sizeof(T), h->stream);
+  if (!v.empty())
+    CUDA_CHECK(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                               h->stream));
+}
+
+}  // namespace
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    ELMFB_THROW(ELMFB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void stage_begin(elmfb_ctx* h, int s) { CUDA_CHECK(cudaEventRecord(h->st[s].a, h->stream)); }
+void stage_end(elmfb_ctx* h, int s) {
+  CUDA_CHECK(cudaEventRecord(h->st[s].b, h->stream));
+  CUDA_CHECK(cudaEventSynchronize(h->st[s].b));
+  float ms = 0.f;
+  CUDA_CHECK(cudaEventElapsedTime(&ms, h->st[s].a, h->st[s].b));
+  h->stage_ms[s] = ms;
+}
+
+namespace {
+cudaEvent_t prof_event(elmfb_ctx* h) {
+  if (!h->prof_pool.empty()) {
+    cudaEvent_t e = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CUDA_CHECK(cudaEventCreate(&e));
+  return e;
+}
+const char* kKernelNames[KID_COUNT] = {"assemble_panels", "gather_Mv",    "entry_MTu",
+                                       "panel_MTu",       "precond_apply", "lsqr_update",
+                                       "gram_diag",       "block_chol",   "gram_tc",
+                                       "cell_sort"};
+}  // namespace
+
+void prof_begin(elmfb_ctx* h, int kid, double bytes) {
+  if (!h->prof) return;
+  ProfRec r{kid, prof_event(h), prof_event(h)};
+  CUDA_CHECK(cudaEventRecord(r.a, h->stream));
+  h->prof_live.push_back(r);
+  h->prof_bytes[kid] = bytes;
+}
+
+void prof_end(elmfb_ctx* h, int kid) {
+  if (!h->prof) return;
+  for (auto it = h->prof_live.rbegin(); it != h->prof_live.rend(); ++it)
+    if (it->kid == kid) {
+      CUDA_CHECK(cudaEventRecord(it->b, h->stream));
+      break;
+    }
+  if (h->prof_live.size() > 4096) prof_harvest(h);
+}
+
+void prof_harvest(elmfb_ctx* h) {
+  if (h->prof_live.empty()) return;
+  CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  for (auto& r : h->prof_live) {
+    float ms = 0.f;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, r.a, r.b));
+    h->prof_ms[r.kid] += ms;
+    h->prof_n[r.kid] += 1;
+    h->prof_pool.push_back(r.a);
+    h->prof_pool.push_back(r.b);
+  }
+  h->prof_live.clear();
+}
+
+void upload_geometry(elmfb_ctx* h) {
+  upload(h, h->d_sub, h->sub);
+  std::vector<float> W32(h->Wh.begin(), h->Wh.end()), b32(h->bh.begin(), h->bh.end());
+  upload(h, h->d_W32, W32);
+  upload(h, h->d_b32, b32);
+  upload(h, h->d_W64, h->Wh);
+  upload(h, h->d_b64, h->bh);
+  std::vector<double> bnd(h->bnd[0]);
+  bnd.insert(bnd.end(), h->bnd[1].begin(), h->bnd[1].end());
+  upload(h, h->d_bnd, bnd);
+  upload(h, h->d_cover_off, h->cover_off);
+  upload(h, h->d_cover_sub, h->cover_sub);
+  upload(h, h->d_cell_level_off, h->cell_level_off);
+  upload(h, h->d_entry_cell, h->entry_cell);
+  h->d_a.alloc(h->NPhi * sizeof(double), h->stream);
+  CUDA_CHECK(cudaMemsetAsync(h->d_a.p, 0, h->NPhi * sizeof(double), h->stream));
+  h->d_flags.alloc(16 * sizeof(int), h->stream);
+  CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), h->stream));
+}
+
+extern "C" {
+
+int elmfb_create(elmfb_t* out, const elmfb_config* cfg, void* cuda_stream) {
+  if (!out || !cfg) return ELMFB_ERR_INVALID_ARG;
+  *out = nullptr;
+  const elmfb_config& c = *cfg;
+  if (c.dim < 1 || c.dim > 2 || c.n_levels < 1 || c.n_levels > ELMFB_MAX_LEVELS ||
+      c.features < 1 || c.features > ELMFB_MAX_FEATURES || !(c.delta > 1.0) ||
+      (c.placement != ELMFB_PLACE_CELL && c.placement != ELMFB_PLACE_ENDPOINT) ||
+      c.precision < ELMFB_FP64 || c.precision > ELMFB_MIXED || !(c.weight_scale >= 0.0))
+    return ELMFB_ERR_INVALID_ARG;
+  for (int i = 0; i < c.dim; ++i)
+    if (!(c.hi[i] > c.lo[i])) return ELMFB_ERR_INVALID_ARG;
+  int64_t nsub = 0;
+  for (int l = 0; l < c.n_levels; ++l) {
+    if (c.levels[l] < 1 || c.levels[l] > 4096) return ELMFB_ERR_INVALID_ARG;
+    nsub += c.dim == 2 ? (int64_t)c.levels[l] * c.levels[l] : c.levels[l];
+  }
+  if (nsub * c.features > (int64_t)1 << 30) return ELMFB_ERR_UNSUPPORTED;
+  elmfb_ctx* h = new elmfb_ctx();
+  h->cfg = c;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&h->device);
+  int rc = guarded(h, [&] {
+    for (auto& s : h->st) {
+      CUDA_CHECK(cudaEventCreate(&s.a));
+      CUDA_CHECK(cudaEventCreate(&s.b));
+    }
+    stage_begin(h, 0);
+    build_geometry(h);
+    upload_geometry(h);
+    stage_end(h, 0);
+  });
+  if (rc != ELMFB_OK) {
+    elmfb_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return ELMFB_OK;
+}
+
+void elmfb_destroy(elmfb_t h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  for (auto& s : h->st) {
+    if (s.a) cudaEventDestroy(s.a);
+    if (s.b) cudaEventDestroy(s.b);
+  }
+  for (auto& r : h->prof_live) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
+  delete h;  // DevBuf destructors free device memory
+  cudaDeviceSynchronize();
+}
+
+const char* elmfb_last_error(elmfb_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int elmfb_assemble(elmfb_t h, int n_sets, const elmfb_rowset* sets) {
+  return guarded(h, [&] {
+    if (n_sets < 1 || n_sets > ELMFB_MAX_ROWSETS || !sets)
+      ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "n_sets must be in 1..16");
+    assemble_system(h, n_sets, sets);
+  });
+}
+
+int elmfb_get_sizes(elmfb_t h, elmfb_sizes* o) {
+  return guarded(h, [&] {
+    if (!o) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null output");
+    o->n_columns = h->NPhi;
+    o->n_rows = h->assembled ? h->n_rows : 0;
+    o->n_subdomains = h->n_sub;
+    o->nnz = h->assembled ? h->nnz : 0;
+    o->panel_rows = h->assembled ? h->NPR : 0;
+    o->n_cells = h->n_cells;
+    o->n_gram_pairs = h->n_gram_pairs;
+    o->features = h->K;
+    o->n_levels = h->L;
+    o->dim = h->dim;
+    o->precision = h->cfg.precision;
+  });
+}
+
+int elmfb_get_params(elmfb_t h, double* W, double* b) {
+  return guarded(h, [&] {
+    if (W)
+      CUDA_CHECK(cudaMemcpy(W, h->Wh.data(), h->Wh.size() * sizeof(double), cudaMemcpyDefault));
+    if (b)
+      CUDA_CHECK(cudaMemcpy(b, h->bh.data(), h->bh.size() * sizeof(double), cudaMemcpyDefault));
+  });
+}
+
+int elmfb_get_rows(elmfb_t h, const int64_t* rows, int64_t n, double* out, double* h_out) {
+  return guarded(h, [&] {
+    if (!h->assembled) ELMFB_THROW(ELMFB_ERR_STATE, "get_rows before assemble");
+    if (n < 0 || (n > 0 && (!rows || !out))) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad arguments");
+    export_rows(h, rows, n, out, h_out);
+  });
+}
+
+void elmfb_default_solve_opts(elmfb_solve_opts* o) {
+  if (!o) return;
+  o->method = ELMFB_SOLVE_LSQR;
+  o->preconditioner = ELMFB_PREC_BLOCK_JACOBI;
+  o->max_iter = 15000;
+  o->atol = 1e-10;
+  o->btol = 1e-10;
+  o->shift = 1e-12;
+  o->check_every = 50;
+  o->warm_start = 0;
+}
+
+int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info) {
+  int nc_status = ELMFB_OK;
+  int rc = guarded(h, [&] {
+    if (!h->assembled) ELMFB_THROW(ELMFB_ERR_STATE, "solve before assemble");
+    elmfb_solve_opts o;
+    elmfb_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.check_every < 1 || !(o.shift >= 0.0))
+      ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad solver options");
+    elmfb_solve_info inf{};
+    solve_system(h, &o, &inf);
+    h->have_coeffs = true;
+    nc_status = inf.status;
+    if (info) *info = inf;
+  });
+  if (rc != ELMFB_OK) return rc;
+  return nc_status;
+}
+
+int elmfb_get_coeffs(elmfb_t h, double* a) {
+  return guarded(h, [&] {
+    if (!a) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null output");
+    CUDA_CHECK(cudaMemcpyAsync(a, h->d_a.p, h->NPhi * sizeof(double), cudaMemcpyDefault,
+                               h->stream));
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  });
+}
+
+int elmfb_set_coeffs(elmfb_t h, const double* a) {
+  return guarded(h, [&] {
+    if (!a) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null input");
+    CUDA_CHECK(cudaMemcpyAsync(h->d_a.p, a, h->NPhi * sizeof(double), cudaMemcpyDefault,
+                               h->stream));
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    h->have_coeffs = true;
+  });
+}
+
+int elmfb_eval(elmfb_t h, const double* xs, int64_t n, double* out) {
+  return guarded(h, [&] {
+    if (n < 0 || (n > 0 && (!xs || !out))) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad arguments");
+    eval_model(h, xs, n, out);
+  });
+}
+
+int elmfb_error_norms(elmfb_t h, const double* uh, const double* ur, int64_t n, double* out3) {
+  return guarded(h, [&] {
+    if (n <= 0 || !uh || !ur || !out3) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad arguments");
+    error_norms(h, uh, ur, n, out3);
+  });
+}
+
+int elmfb_stage_times(elmfb_t h, double* ms) {
+  return guarded(h, [&] {
+    if (!ms) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null output");
+    for (int i = 0; i < ELMFB_N_STAGES; ++i) ms[i] = h->stage_ms[i];
+  });
+}
+
+int64_t elmfb_kernel_launches(elmfb_t h) { return h ? h->launches : -1; }
+
+int elmfb_set_profiling(elmfb_t h, int on) {
+  return guarded(h, [&] {
+    prof_harvest(h);
+    h->prof = on != 0;
+    for (int k = 0; k < KID_COUNT; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_n[k] = 0;
+    }
+  });
+}
+
+int elmfb_kernel_stats(elmfb_t h, int max, const char** names, double* total_ms, int64_t* launches,
+                       double* bytes_per_launch) {
+  int count = 0;
+  int rc = guarded(h, [&] {
+    prof_harvest(h);
+    for (int k = 0; k < KID_COUNT && count < max; ++k) {
+      if (h->prof_n[k] == 0) continue;
+      if (names) names[count] = kKernelNames[k];
+      if (total_ms) total_ms[count] = h->prof_ms[k];
+      if (launches) launches[count] = h->prof_n[k];
+      if (bytes_per_launch) bytes_per_launch[count] = h->prof_bytes[k];
+      ++count;
+    }
+  });
+  return rc == ELMFB_OK ? count : -rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// Internal declarations of the GB300 ELM-FBPINN library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/elmfb.h"
+
+#define ELMFB_LIKELY(x) __builtin_expect(!!(x), 1)
+
+// ---------------------------------------------------------------------------
+// error plumbing: every ABI entry point catches elmfb_error and stores the
+// message in the handle.
+// ---------------------------------------------------------------------------
+struct elmfb_error {
+  int code;
+  std::string msg;
+};
+
+#define ELMFB_THROW(code, msg) throw elmfb_error{(code), (msg)}
+#define CUDA_CHECK(call)                                                          \
+  do {                                                                            \
+    cudaError_t e__ = (call);                                                     \
+    if (e__ != cudaSuccess)                                                       \
+      throw elmfb_error{e__ == cudaErrorMemoryAllocation ? ELMFB_ERR_OOM : ELMFB_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e__)};     \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffer owned by the handle (stream-ordered allocation)
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t n, cudaStream_t stream) {
+    if (n <= bytes && p) return;
+    release();
+    s = stream;
+    if (n == 0) return;
+    CUDA_CHECK(cudaMallocAsync(&p, n, stream));
+    bytes = n;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Limits of one cell of the common refinement (points per cell) and of the
+// number of covering subdomains per cell.
+constexpr int kCellPad = 16;            // cell row groups are padded to this multiple
+constexpr int kMaxCellPoints = 16384;   // per-cell sort limit
+constexpr int kMaxClasses = ELMFB_MAX_ROWSETS;
+
+// Row class (interior or boundary set): operator coefficients and row scale
+// already divided by L.
+struct RowClass {
+  double c0, c1[2], c2[2];
+  double scale;   // row scale / L (entries of M)
+  double hscale;  // row scale (entries of h)
+};
+
+// Per-subdomain geometry as used on the device.
+struct SubGeom {
+  double mu[2];
+  double sigma_d[2];      // half-width sigma
+  double inv_sigma_d[2];  // 1 / sigma in FP64
+  float inv_sigma[2];     // 1 / sigma in FP32
+  int level;
+  int pad_;
+};
+
+struct Stage {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
+// kernels with device timing (elmfb_kernel_stats)
+enum KernelId {
+  KID_ASSEMBLE = 0, KID_GATHER, KID_ENTRY_T, KID_PANEL_T, KID_PRECOND, KID_UPDATE,
+  KID_GRAM_DIAG, KID_BLOCK_CHOL, KID_GRAM_TC, KID_CELL_SORT, KID_COUNT
+};
+struct ProfRec {
+  int kid;
+  cudaEvent_t a, b;
+};
+
+struct elmfb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  elmfb_config cfg{};
+  std::string err;
+  int64_t launches = 0;
+
+  // geometry (host)
+  int dim = 1, L = 1, K = 1, n_sub = 0;
+  int64_t NPhi = 0;
+  std::vector<int> lev_n, lev_sub_off;  // [L], [L+1]
+  std::vector<SubGeom> sub;             // [n_sub]
+  std::vector<double> Wh, bh;           // [NPhi*dim], [NPhi]
+  std::vector<double> bnd[2];           // cell boundaries per dimension
+  int nc[2] = {1, 1};
+  int n_cells = 0;
+  std::vector<int> sub_c0[2], sub_c1[2];  // [n_sub] cell range per dimension
+  std::vector<int> cover_off;             // [n_cells+1]
+  std::vector<int> cover_sub;             // [n_entries] covering subdomains per cell
+  std::vector<int> cell_level_off;        // [n_cells*(L+1)]
+  int max_cover = 0;
+
+  // device copies of the geometry
+  DevBuf d_sub, d_W32, d_b32, d_W64, d_b64, d_bnd, d_cover_off, d_cover_sub, d_cell_level_off;
+
+  // assembled system
+  bool assembled = false;
+  int n_classes = 0;
+  RowClass cls[kMaxClasses];
+  int64_t n_rows = 0;           // user rows
+  int64_t NR = 0;               // padded sorted rows
+  int64_t NPR = 0;              // panel rows (padded)
+  int64_t nnz = 0;
+  std::vector<int> cell_count, cell_pstart;   // [n_cells], [n_cells+1]
+  std::vector<int64_t> panel_off;             // [n_sub+1]
+  std::vector<int> cover_start;               // [n_entries] panel-local first row of the cell
+  std::vector<int> row_class_of_set;          // per user row set: class id
+  int64_t n_gram_pairs = 0;
+
+  DevBuf d_pts_user, d_rhs_user, d_cls_user;  // user order
+  DevBuf d_row_cell, d_cell_count, d_cell_fill, d_cell_pstart;
+  DevBuf d_sorted;      // [NR] user row of each sorted row (-1 = padding)
+  DevBuf d_x;           // [NR*dim] coordinates (sorted order)
+  DevBuf d_rcls;        // [NR] class (sorted order; -1 padding)
+  DevBuf d_h;           // [NR] scaled rhs (sorted order)
+  DevBuf d_grow_cell;   // [NR] cell of each sorted row
+  DevBuf d_u2s;         // [n_rows] sorted position of each user row
+  DevBuf d_cover_start, d_panel_off;
+  DevBuf d_panels;      // [NPR*K] FP64 or FP32
+  DevBuf d_tiles;       // assembly / transpose-product tiles: (entry, first row)
+  int64_t n_tiles = 0;
+  std::vector<int> entry_cell;   // [n_entries]
+  DevBuf d_entry_cell;
+  DevBuf d_flags;       // device status flags (int[4])
+
+  // solution
+  DevBuf d_a;           // [NPhi] FP64
+  bool have_coeffs = false;
+
+  // solver work buffers
+  DevBuf d_u, d_v, d_w, d_x_sol, d_tmp, d_partial, d_scal, d_R, d_ptile, d_gpart;
+
+  // stage timers
+  Stage st[ELMFB_N_STAGES];
+  double stage_ms[ELMFB_N_STAGES] = {0};
+
+  // per-kernel profiling
+  bool prof = false;
+  std::vector<ProfRec> prof_live;       // recorded, not yet harvested
+  std::vector<cudaEvent_t> prof_pool;   // free events
+  double prof_ms[KID_COUNT] = {0};
+  int64_t prof_n[KID_COUNT] = {0};
+  double prof_bytes[KID_COUNT] = {0};   // algorithmic bytes per launch (last launch)
+
+  bool fp64() const { return cfg.precision == ELMFB_FP64; }
+  size_t panel_elem() const { return fp64() ? 8 : 4; }
+};
+
+// stage timing helpers
+void stage_begin(elmfb_ctx* h, int s);
+void stage_end(elmfb_ctx* h, int s);   // records; time read lazily
+void stage_collect(elmfb_ctx* h);
+
+// assembly (assemble.cu)
+void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets);
+void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, double* h_out);
+
+// solve (solve.cu)
+void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
+
+// eval (eval.cu)
+void eval_model(elmfb_ctx* h, const double* xs, int64_t n, double* out);
+void error_norms(elmfb_ctx* h, const double* uh, const double* ur, int64_t n, double* out3);
+
+// per-kernel profiling (no-ops when h->prof is false)
+void prof_begin(elmfb_ctx* h, int kid, double bytes);
+void prof_end(elmfb_ctx* h, int kid);
+void prof_harvest(elmfb_ctx* h);
+
+// helpers
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline void count_launch(elmfb_ctx* h, int n = 1) { h->launches += n; }
+void check_launch(const char* what);

@@ -1,0 +1,669 @@
+// Least-squares solve of min ||M a - h|| (paper Eq. multilevel_ls).
+//
+// The paper's solver is LSQR (§3 last paragraph; §4.1 "Optimisation and
+// solvers": SciPy LSQR, up to 15000 iterations).  This file runs LSQR
+// (Paige & Saunders, ACM TOMS 8(1), 1982, the bidiagonalisation recurrences
+// and the stopping estimates of its §5-6) on the GPU with an optional
+// right preconditioner that the paper does not use: block-Jacobi over
+// subdomains, P = blockdiag(R_j^{-1}) with R_j^T R_j = G_jj + eps tr(G_jj)/K I
+// the shifted Cholesky factor of the diagonal Gram block G_jj = M_j^T M_j.
+// LSQR then runs on A = M P and returns a = P y.
+//
+// Data flow of one iteration (all scalars stay on the device):
+//   k_precond     t_j = R_j^{-1} v_j                       (block per subdomain)
+//   k_gather      u' = M t - alpha u  and ||u'||^2 partials  (warp per row; M read
+//                 through the per-cell list of covering panels, no atomics)
+//   k_entry_T     partial_e = sum_p P[rho(e,p)]^T u'[R(e,p)] (block per (cell, panel))
+//   k_panel_T     v' = R_j^{-T} (sum_e partial_e) / beta - beta v, ||v'||^2 partials
+//   k_update      scalar recurrence (redundantly per block), x, w, v, u updates
+// Every reduction is a fixed-order two-stage sum, so results are bitwise
+// reproducible from run to run.
+#include <algorithm>
+#include <cmath>
+
+#include "elmfb_internal.cuh"
+
+namespace {
+
+constexpr int kGatherBlocks = 1216;   // 152 SMs x 8
+constexpr int kGatherThreads = 256;
+constexpr int kScal = 32;             // device scalar slots
+
+// scalar slots in d_scal: [0, 16) committed values read by the kernels of an
+// iteration, [16, 32) staged values written by k_panel_T / k_update; k_precond
+// (first kernel of the next iteration) commits staged -> committed.
+constexpr int kStage = 16;
+enum {
+  S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
+  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO
+};
+
+template <class T>
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide fixed-order sum; every thread gets the result
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum<double>(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += sh[i];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------ Gram diag -----
+// partial sums of the upper triangle of P^T P over one chunk of panel rows
+template <class T, int NACC>
+__global__ void __launch_bounds__(256) k_gram_diag_partial(const T* __restrict__ panels, int K,
+                                                            const int4* __restrict__ chunks,
+                                                            double* __restrict__ partial) {
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);   // [16][K]
+  const int4 ch = chunks[blockIdx.x];     // (panel, row0, nrows, -)
+  const int KT = K * (K + 1) / 2;
+  int ij[NACC];   // (i << 16) | j, or -1
+  double acc[NACC];
+#pragma unroll
+  for (int a = 0; a < NACC; ++a) {
+    int idx = threadIdx.x + a * blockDim.x;
+    acc[a] = 0.0;
+    if (idx < KT) {
+      // row-major upper triangle: find (i, j), j >= i
+      int i = 0, rem = idx;
+      while (rem >= K - i) {
+        rem -= K - i;
+        ++i;
+      }
+      ij[a] = (i << 16) | (i + rem);
+    } else {
+      ij[a] = -1;
+    }
+  }
+  const T* base = panels + (int64_t)ch.y * K;
+  for (int r0 = 0; r0 < ch.z; r0 += 16) {
+    const int nr = min(16, ch.z - r0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 16 * K; t += blockDim.x) {
+      int r = t / K;
+      sm[t] = r < nr ? base[(int64_t)(r0 + r) * K + (t - r * K)] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) {
+      if (ij[a] < 0) continue;
+      const int i = ij[a] >> 16, j = ij[a] & 0xffff;
+      T s = 0;
+#pragma unroll 4
+      for (int r = 0; r < 16; ++r) s += sm[r * K + i] * sm[r * K + j];
+      acc[a] += (double)s;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NACC; ++a) {
+    int idx = threadIdx.x + a * blockDim.x;
+    if (idx < KT) partial[(int64_t)blockIdx.x * KT + idx] = acc[a];
+  }
+}
+
+// One block per subdomain: sum the chunk partials, shift, Cholesky
+// (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
+// column-major.  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
+__global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ partial,
+                                                     const int* __restrict__ chunk_off, int K,
+                                                     double shift, double* __restrict__ Xr,
+                                                     double* __restrict__ Xc,
+                                                     int* __restrict__ flags,
+                                                     double* __restrict__ gdiag_out) {
+  extern __shared__ double G[];   // [K][K] lower used
+  __shared__ double red[32];
+  __shared__ double diag0[128];
+  __shared__ int fail;
+  const int s = blockIdx.x;
+  const int KT = K * (K + 1) / 2;
+  const int c0 = chunk_off[s], c1 = chunk_off[s + 1];
+  // assemble full symmetric G
+  for (int idx = threadIdx.x; idx < KT; idx += blockDim.x) {
+    double v = 0.0;
+    for (int c = c0; c < c1; ++c) v += partial[(int64_t)c * KT + idx];
+    int i = 0, rem = idx;
+    while (rem >= K - i) {
+      rem -= K - i;
+      ++i;
+    }
+    int j = i + rem;
+    G[i * K + j] = v;
+    G[j * K + i] = v;
+  }
+  __syncthreads();
+  if (gdiag_out) {
+    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x)
+      gdiag_out[(int64_t)s * K * K + idx] = G[idx];
+  }
+  double tr = 0.0;
+  {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      v += G[i * K + i];
+      diag0[i] = G[i * K + i];
+    }
+    tr = block_sum(v, red);
+  }
+  double eps = shift;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    if (attempt > 0) {
+      // restore the lower triangle from the (untouched) upper triangle
+      for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+        int i = idx / K, j = idx % K;
+        if (i > j) G[i * K + j] = G[j * K + i];
+        else if (i == j) G[i * K + i] = diag0[i];
+      }
+      eps = eps > 0.0 ? eps * 100.0 : 1e-14;
+    }
+    const double add = eps * tr / K + (tr == 0.0 ? 1.0 : 0.0);
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += blockDim.x) G[i * K + i] += add;
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+      if (threadIdx.x == 0) {
+        double d = G[k * K + k];
+        if (!(d > 0.0)) fail = 1;
+        G[k * K + k] = sqrt(d > 0.0 ? d : 1.0);
+      }
+      __syncthreads();
+      if (fail) break;
+      const double piv = G[k * K + k];
+      for (int i = k + 1 + threadIdx.x; i < K; i += blockDim.x) G[i * K + k] /= piv;
+      __syncthreads();
+      const int m = K - k - 1;
+      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        int i = k + 1 + idx / m, j = k + 1 + idx % m;
+        if (j <= i) G[i * K + j] -= G[i * K + k] * G[j * K + k];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!fail) break;
+  }
+  if (fail) {
+    if (threadIdx.x == 0) atomicOr(&flags[1], 1);
+    return;
+  }
+  // X = L^{-1}: thread per column j, forward substitution
+  double* xr = Xr + (int64_t)s * K * K;
+  double* xc = Xc + (int64_t)s * K * K;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) {
+      xr[i * K + j] = 0.0;
+      xc[j * K + i] = 0.0;
+    }
+    for (int i = j; i < K; ++i) {
+      double sum = i == j ? 1.0 : 0.0;
+      for (int m = j; m < i; ++m) sum -= G[i * K + m] * xr[m * K + j];
+      double v = sum / G[i * K + i];
+      xr[i * K + j] = v;   // X_ij row-major
+      xc[j * K + i] = v;   // X_ij column-major
+    }
+  }
+}
+
+// t_j = R_j^{-1} v_j = X_j^T v_j  (t_i = sum_{m>=i} X_mi v_m); identity if no preconditioner
+__global__ void k_precond(const double* __restrict__ Xr, const double* __restrict__ v, int K,
+                          double* __restrict__ t, int identity, double* __restrict__ scal) {
+  extern __shared__ double vs[];
+  const int s = blockIdx.x;
+  if (s == 0 && threadIdx.x < kStage) scal[threadIdx.x] = scal[kStage + threadIdx.x];
+  const double* vv = v + (int64_t)s * K;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) vs[i] = vv[i];
+  __syncthreads();
+  const double* X = Xr + (int64_t)s * K * K;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double acc;
+    if (identity) {
+      acc = vs[i];
+    } else {
+      acc = 0.0;
+      for (int m = i; m < K; ++m) acc += X[m * K + i] * vs[m];
+    }
+    t[(int64_t)s * K + i] = acc;
+  }
+}
+
+// u'_R = sum over covering panels of P[rho] . t_s  - alpha * u_R / beta_prev
+// (u is stored unnormalised; u_norm = u / beta_prev).  mode 1: u' = h - M t.
+template <class T>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(
+    const T* __restrict__ panels, const double* __restrict__ tvec, int K, int64_t NR,
+    const int* __restrict__ grow_cell, const int* __restrict__ cell_pstart,
+    const int* __restrict__ cell_count, const int* __restrict__ cover_off,
+    const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
+    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    double* __restrict__ u, const double* __restrict__ hvec, int mode,
+    double* __restrict__ norm_partial) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double coef = 0.0;
+  if (mode == 0) {
+    const double beta = scal[S_BETA];
+    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+  }
+  double nrm = 0.0;
+  for (int64_t R = wg; R < NR; R += warps) {
+    const int c = grow_cell[R];
+    const int p = (int)(R - cell_pstart[c]);
+    double y = 0.0;
+    if (p < cell_count[c]) {
+      for (int e = cover_off[c]; e < cover_off[c + 1]; ++e) {
+        const int s = cover_sub[e];
+        const T* row = panels + (panel_off[s] + cover_start[e] + p) * (int64_t)K;
+        const double* tv = tvec + (int64_t)s * K;
+        T part = 0;
+        for (int k = lane; k < K; k += 32) part += row[k] * (T)tv[k];
+        if (sizeof(T) == 8) y += warp_sum<double>((double)part);
+        else y += (double)warp_sumf((float)part);
+      }
+      double out;
+      if (mode == 0) out = y - coef * u[R];
+      else out = hvec[R] - y;
+      if (lane == 0) u[R] = out;
+      nrm += out * out;
+    }
+  }
+  // lane 0 holds the warp's sum
+  nrm = __shfl_sync(0xffffffffu, nrm, 0);
+  double tot = block_sum(lane == 0 ? nrm : 0.0, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+}
+
+// partial_e[k] = sum_p P[rho(e,p)][k] u[R(e,p)]  (one block per (cell, panel) entry)
+template <class T>
+__global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
+                                                 const double* __restrict__ u, int K,
+                                                 const int* __restrict__ entry_cell,
+                                                 const int* __restrict__ cover_sub,
+                                                 const int* __restrict__ cover_start,
+                                                 const int* __restrict__ cell_pstart,
+                                                 const int* __restrict__ cell_count,
+                                                 const int64_t* __restrict__ panel_off,
+                                                 double* __restrict__ partial) {
+  extern __shared__ double us[];
+  const int e = blockIdx.x;
+  const int c = entry_cell[e];
+  const int cnt = cell_count[c];
+  const int64_t R0 = cell_pstart[c];
+  const int s = cover_sub[e];
+  const T* base = panels + (panel_off[s] + cover_start[e]) * (int64_t)K;
+  double* out = partial + (int64_t)e * K;
+  if (cnt == 0) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = 0.0;
+    return;
+  }
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) us[p] = u[R0 + p];
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double acc = 0.0;
+    if (sizeof(T) == 8) {
+      for (int p = 0; p < cnt; ++p) acc += (double)base[(int64_t)p * K + k] * us[p];
+    } else {
+      float a32 = 0.f;
+      int p = 0;
+      for (; p < cnt; ++p) {
+        a32 += (float)base[(int64_t)p * K + k] * (float)us[p];
+        if ((p & 31) == 31) {
+          acc += a32;
+          a32 = 0.f;
+        }
+      }
+      acc += a32;
+    }
+    out[k] = acc;
+  }
+}
+
+// v'_j = X_j z_j / beta - beta v_j with z_j = sum of the entry partials of panel j
+// (X_j = R_j^{-T}); writes v' (unnormalised) and ||v'||^2 per block.
+__global__ void k_panel_T(const double* __restrict__ partial, const int* __restrict__ pent_off,
+                          const int* __restrict__ pent, const double* __restrict__ Xc, int K,
+                          const double* __restrict__ beta_partial, int n_beta_partial,
+                          double* __restrict__ v, double* __restrict__ scal, int identity,
+                          int init, double* __restrict__ norm_partial) {
+  extern __shared__ double zs[];
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  // beta = sqrt(sum of gather partials), same fixed order in every block
+  double b2 = 0.0;
+  for (int i = 0; i < n_beta_partial; ++i) b2 += beta_partial[i];
+  const double beta = sqrt(b2);
+  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double z = 0.0;
+    for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) z += partial[(int64_t)pent[q] * K + k];
+    zs[k] = z * ib;
+  }
+  __syncthreads();
+  const double* X = Xc + (int64_t)s * K * K;
+  double nrm = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double acc;
+    if (identity) {
+      acc = zs[i];
+    } else {
+      acc = 0.0;
+      for (int m = 0; m <= i; ++m) acc += X[m * K + i] * zs[m];   // X_im, column-major
+    }
+    double vold = init ? 0.0 : v[(int64_t)s * K + i];
+    double vn = acc - beta * vold;
+    v[(int64_t)s * K + i] = vn;
+    nrm += vn * vn;
+  }
+  double tot = block_sum(nrm, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;   // staged beta_{i+1}
+}
+
+// LSQR scalar recurrence + vector updates.  Every block recomputes the scalars
+// (identical fixed-order sums); block 0 commits them.
+__global__ void k_update(double* __restrict__ scal, const double* __restrict__ alpha_partial,
+                         int n_alpha_partial, double* __restrict__ v, double* __restrict__ w,
+                         double* __restrict__ x, int64_t N, int init) {
+  double a2 = 0.0;
+  for (int i = 0; i < n_alpha_partial; ++i) a2 += alpha_partial[i];
+  const double alpha = sqrt(a2);
+  const double beta = scal[kStage + S_BETA];   // beta_{i+1}
+  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  double phi_rho = 0.0, theta_rho = 0.0;
+  double rhobar_new = 0.0, phibar_new = 0.0, anorm2 = scal[S_ANORM2], arnorm = 0.0;
+  if (init) {
+    // beta_1 u_1 = b, alpha_1 v_1 = A^T u_1, w_1 = v_1, phibar_1 = beta_1, rhobar_1 = alpha_1
+    rhobar_new = alpha;
+    phibar_new = beta;
+    anorm2 = alpha * alpha;
+    arnorm = alpha * beta;
+  } else {
+    const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
+    const double rho = sqrt(rhobar * rhobar + beta * beta);
+    const double c = rho > 0.0 ? rhobar / rho : 1.0;
+    const double sn = rho > 0.0 ? beta / rho : 0.0;
+    const double theta = sn * alpha;
+    rhobar_new = -c * alpha;
+    const double phi = c * phibar;
+    phibar_new = sn * phibar;
+    phi_rho = rho > 0.0 ? phi / rho : 0.0;
+    theta_rho = rho > 0.0 ? theta / rho : 0.0;
+    anorm2 += alpha * alpha + beta * beta;
+    arnorm = phibar_new * alpha * fabs(c);
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double vn = v[i] * ia;   // v_{i+1}
+    if (init) {
+      w[i] = vn;
+      x[i] = 0.0;
+    } else {
+      const double wi = w[i];
+      x[i] += phi_rho * wi;
+      w[i] = vn - theta_rho * wi;
+    }
+    v[i] = vn;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double* sg = scal + kStage;
+    sg[S_ALPHA] = alpha;
+    sg[S_BETA] = beta;
+    sg[S_RHOBAR] = rhobar_new;
+    sg[S_PHIBAR] = phibar_new;
+    sg[S_ANORM2] = anorm2;
+    sg[S_RNORM] = phibar_new;
+    sg[S_ARNORM] = arnorm;
+    sg[S_BNORM] = init ? beta : scal[S_BNORM];
+    sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
+    sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_add_to(double* __restrict__ a, const double* __restrict__ d, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] += d[i];
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+namespace {
+
+struct SolveLayout {
+  int n_chunks = 0;
+  std::vector<int4> chunks;
+  std::vector<int> chunk_off;
+  std::vector<int> pent_off, pent;
+};
+
+template <class T>
+void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity) {
+  cudaStream_t st = h->stream;
+  const int K = h->K;
+  const int64_t KK = (int64_t)K * K;
+  h->d_R.alloc(2 * h->n_sub * KK * sizeof(double), st);
+  if (identity) return;
+  if (K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up supports K <= 128");
+  // chunks of at most 512 panel rows
+  std::vector<int4> chunks;
+  std::vector<int> chunk_off(h->n_sub + 1, 0);
+  for (int s = 0; s < h->n_sub; ++s) {
+    chunk_off[s] = (int)chunks.size();
+    for (int64_t r = h->panel_off[s]; r < h->panel_off[s + 1]; r += 512)
+      chunks.push_back(make_int4(s, (int)r, (int)std::min<int64_t>(512, h->panel_off[s + 1] - r), 0));
+  }
+  chunk_off[h->n_sub] = (int)chunks.size();
+  const int KT = K * (K + 1) / 2;
+  DevBuf dch, dcoff;
+  dch.alloc(std::max<size_t>(chunks.size(), 1) * sizeof(int4), st);
+  dcoff.alloc(chunk_off.size() * sizeof(int), st);
+  CUDA_CHECK(cudaMemcpyAsync(dch.p, chunks.data(), chunks.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(dcoff.p, chunk_off.data(), chunk_off.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+  h->d_gpart.alloc(std::max<size_t>(chunks.size(), 1) * KT * sizeof(double), st);
+  const int nacc = (KT + 255) / 256;
+  const size_t smem = 16 * K * sizeof(T);
+  if (!chunks.empty()) {
+    prof_begin(h, KID_GRAM_DIAG,
+               (double)h->NPR * K * sizeof(T) + (double)chunks.size() * KT * sizeof(double));
+#define ELMFB_GD(N)                                                                         \
+  if (nacc <= N) {                                                                          \
+    k_gram_diag_partial<T, N><<<(unsigned)chunks.size(), 256, smem, st>>>(                  \
+        (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>());               \
+  } else
+    ELMFB_GD(1) ELMFB_GD(2) ELMFB_GD(4) ELMFB_GD(8) ELMFB_GD(16) ELMFB_GD(33)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "K too large for the diagonal Gram kernel");
+#undef ELMFB_GD
+    prof_end(h, KID_GRAM_DIAG);
+    check_launch("k_gram_diag_partial");
+    count_launch(h);
+  }
+  const size_t csm = (size_t)KK * sizeof(double);
+  CUDA_CHECK(cudaFuncSetAttribute(k_block_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)std::max<size_t>(csm, 48 * 1024)));
+  CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
+  prof_begin(h, KID_BLOCK_CHOL,
+             (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
+  k_block_chol<<<h->n_sub, 256, csm, st>>>(h->d_gpart.as<double>(), dcoff.as<int>(), K, shift,
+                                           h->d_R.as<double>(), h->d_R.as<double>() + h->n_sub * KK,
+                                           h->d_flags.as<int>(), nullptr);
+  prof_end(h, KID_BLOCK_CHOL);
+  check_launch("k_block_chol");
+  count_launch(h);
+  int flags[4];
+  CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  if (flags[1]) ELMFB_THROW(ELMFB_ERR_BREAKDOWN, "block Cholesky failed after shift increases");
+}
+
+template <class T>
+void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
+  cudaStream_t st = h->stream;
+  const int K = h->K;
+  const int64_t N = h->NPhi;
+  const int64_t KK = (int64_t)K * K;
+  const bool identity = o->preconditioner == ELMFB_PREC_NONE;
+
+  stage_begin(h, 4);
+  block_jacobi_setup<T>(h, o->shift, identity);
+  stage_end(h, 4);
+  info->setup_ms = h->stage_ms[4];
+
+  // panel -> entries (cell order)
+  const int ne = (int)h->cover_sub.size();
+  std::vector<int> pent_off(h->n_sub + 1, 0), pent(ne);
+  for (int e = 0; e < ne; ++e) pent_off[h->cover_sub[e] + 1]++;
+  for (int s = 0; s < h->n_sub; ++s) pent_off[s + 1] += pent_off[s];
+  {
+    std::vector<int> fill(pent_off.begin(), pent_off.end() - 1);
+    for (int e = 0; e < ne; ++e) pent[fill[h->cover_sub[e]]++] = e;
+  }
+  DevBuf dpo, dpe;
+  dpo.alloc(pent_off.size() * sizeof(int), st);
+  dpe.alloc(std::max(ne, 1) * sizeof(int), st);
+  CUDA_CHECK(cudaMemcpyAsync(dpo.p, pent_off.data(), pent_off.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(dpe.p, pent.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st));
+
+  h->d_u.alloc(h->NR * sizeof(double), st);
+  h->d_v.alloc(N * sizeof(double), st);
+  h->d_w.alloc(N * sizeof(double), st);
+  h->d_x_sol.alloc(N * sizeof(double), st);
+  h->d_tmp.alloc(std::max<int64_t>(N, h->NR) * sizeof(double), st);
+  h->d_partial.alloc((int64_t)ne * K * sizeof(double), st);
+  h->d_scal.alloc(2 * kScal * sizeof(double), st);
+  h->d_ptile.alloc((kGatherBlocks + h->n_sub + 8) * sizeof(double), st);
+  double* gpart = h->d_ptile.as<double>();
+  double* vpart = gpart + kGatherBlocks;
+  CUDA_CHECK(cudaMemsetAsync(h->d_scal.p, 0, 2 * kScal * sizeof(double), st));
+
+  const T* P = (const T*)h->d_panels.p;
+  double* scal = h->d_scal.as<double>();
+  const double* Xr = h->d_R.as<double>();
+  const double* Xc = h->d_R.as<double>() + h->n_sub * KK;
+  int pblock = std::min(std::max(32, ((K + 31) / 32) * 32), 256);
+  size_t emax = 0;
+  for (int c = 0; c < h->n_cells; ++c) emax = std::max<size_t>(emax, h->cell_count[c]);
+  const size_t esm = std::max<size_t>(emax, 1) * sizeof(double);
+  if (esm > 48 * 1024)
+    CUDA_CHECK(cudaFuncSetAttribute(k_entry_T<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)esm));
+  const int upd_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
+
+  const double panel_bytes = (double)h->NPR * K * sizeof(T);
+  auto gather = [&](const double* t, int mode) {
+    prof_begin(h, KID_GATHER, panel_bytes + 16.0 * h->NR + 8.0 * N);
+    k_gather<T><<<kGatherBlocks, kGatherThreads, 0, st>>>(
+        P, t, K, h->NR, h->d_grow_cell.as<int>(), h->d_cell_pstart.as<int>(),
+        h->d_cell_count.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
+        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(),
+        h->d_h.as<double>(), mode, gpart);
+    prof_end(h, KID_GATHER);
+  };
+  auto transpose_step = [&](int init) {
+    prof_begin(h, KID_ENTRY_T, panel_bytes + 8.0 * h->NR + 8.0 * ne * K);
+    k_entry_T<T><<<ne, 128, esm, st>>>(P, h->d_u.as<double>(), K, h->d_entry_cell.as<int>(),
+                                        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),
+                                        h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),
+                                        h->d_panel_off.as<int64_t>(), h->d_partial.as<double>());
+    prof_end(h, KID_ENTRY_T);
+    prof_begin(h, KID_PANEL_T, 8.0 * ne * K + (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
+    k_panel_T<<<h->n_sub, pblock, K * sizeof(double), st>>>(
+        h->d_partial.as<double>(), dpo.as<int>(), dpe.as<int>(), Xc, K, gpart, kGatherBlocks,
+        h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart);
+    prof_end(h, KID_PANEL_T);
+    prof_begin(h, KID_UPDATE, 48.0 * N);
+    k_update<<<upd_blocks, 256, 0, st>>>(scal, vpart, h->n_sub, h->d_v.as<double>(),
+                                         h->d_w.as<double>(), h->d_x_sol.as<double>(), N, init);
+    prof_end(h, KID_UPDATE);
+  };
+
+  stage_begin(h, 5);
+  // start: b = h (cold) or h - M a0 (warm start)
+  if (o->warm_start) {
+    gather(h->d_a.as<double>(), 1);
+  } else {
+    // u' = h: gather with t = 0 in mode 1 gives h - 0
+    CUDA_CHECK(cudaMemsetAsync(h->d_tmp.p, 0, N * sizeof(double), st));
+    gather(h->d_tmp.as<double>(), 1);
+  }
+  transpose_step(1);
+  count_launch(h, 4);
+  check_launch("lsqr init");
+
+  int it = 0;
+  int status = ELMFB_ERR_NOT_CONVERGED;
+  double sc[kScal];
+  const int max_it = o->max_iter;
+  while (it < max_it) {
+    int batch = std::min(o->check_every, max_it - it);
+    for (int b = 0; b < batch; ++b) {
+      prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
+      k_precond<<<h->n_sub, pblock, K * sizeof(double), st>>>(Xr, h->d_v.as<double>(), K,
+                                                               h->d_tmp.as<double>(), identity,
+                                                               scal);
+      prof_end(h, KID_PRECOND);
+      gather(h->d_tmp.as<double>(), 0);
+      transpose_step(0);
+    }
+    count_launch(h, 5 * batch);
+    it += batch;
+    check_launch("lsqr iteration");
+    CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (sc[S_BAD] != 0.0) ELMFB_THROW(ELMFB_ERR_NONFINITE, "non-finite LSQR scalar");
+    const double anorm = std::sqrt(sc[S_ANORM2]);
+    const double rn = sc[S_RNORM], arn = sc[S_ARNORM];
+    const bool t1 = o->btol > 0.0 && rn <= o->btol * sc[S_BNORM];
+    const bool t2 = o->atol > 0.0 && anorm > 0.0 && rn > 0.0 && arn <= o->atol * anorm * rn;
+    if (t1 || t2 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0) {
+      status = ELMFB_OK;
+      break;
+    }
+  }
+  // a = (a0 +) P y
+  k_precond<<<h->n_sub, pblock, K * sizeof(double), st>>>(Xr, h->d_x_sol.as<double>(), K,
+                                                           h->d_tmp.as<double>(), identity, scal);
+  if (o->warm_start)
+    k_add_to<<<upd_blocks, 256, 0, st>>>(h->d_a.as<double>(), h->d_tmp.as<double>(), N);
+  else
+    CUDA_CHECK(cudaMemcpyAsync(h->d_a.p, h->d_tmp.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                               st));
+  count_launch(h, 2);
+  check_launch("lsqr finish");
+  CUDA_CHECK(cudaMemcpyAsync(sc, scal, kStage * sizeof(double), cudaMemcpyDeviceToHost, st));
+  stage_end(h, 5);
+  info->status = status;
+  info->iterations = it;
+  info->residual_norm = sc[S_RNORM];
+  info->normal_residual_norm = sc[S_ARNORM];
+  info->solve_ms = h->stage_ms[5];
+}
+
+}  // namespace
+
+void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
+  if (o->method != ELMFB_SOLVE_LSQR)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "solver method not available in this build");
+  if (o->preconditioner != ELMFB_PREC_NONE && o->preconditioner != ELMFB_PREC_BLOCK_JACOBI)
+    ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "unknown preconditioner");
+  if (h->fp64()) lsqr<double>(h, o, info);
+  else lsqr<float>(h, o, info);
+}

@@ -53,3 +53,11 @@ def test_exact_recovery_of_planted_solution():
     X = P.test_points
     u_star = E.u_hat(P, a_star, X)
     assert np.allclose(E.u_hat(P, a, X), u_star, atol=1e-6 * np.abs(u_star).max())
+
+
+def test_threaded_lsqr_is_bitwise_serial():
+    P = WL.dho(levels=(1, 2, 4), features=8, n_interior=300, omega0=8.0)
+    out = S.assemble(P, fmt="csr")
+    a1, _ = LS.lstsq_lsqr(out["M"], out["h"], iter_lim=200)
+    a4, _ = LS.lstsq_lsqr(out["M"], out["h"], iter_lim=200, threads=4)
+    assert np.array_equal(a1, a4)
