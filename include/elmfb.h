@@ -250,6 +250,31 @@ int elmfb_set_profiling(elmfb_t h, int on);
 int elmfb_kernel_stats(elmfb_t h, int max, const char** names, double* total_ms,
                        int64_t* launches, double* bytes_per_launch);
 
+/* Error norms that allocate nothing.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory when they need the
+ * result -- for example because their framework's memory pool already holds
+ * the device, or because they run where calling an allocator is not allowed.
+ * It computes the same three numbers as elmfb_error_norms() (relative L2,
+ * e_L1 with the population standard deviation, max |u_hat - u_ref|) but needs
+ * no handle, makes no staging copies and calls no allocating routine.
+ *   u_hat, u_ref  [n] FP64 in device (or managed) memory; host pointers are
+ *                 rejected with ELMFB_ERR_INVALID_ARG
+ *   n             1 .. ELMFB_NOALLOC_MAX_POINTS; larger n returns
+ *                 ELMFB_ERR_UNSUPPORTED before anything runs
+ *   out3          [3] host memory
+ *   cuda_stream   stream to run on (cudaStream_t, NULL = default stream);
+ *                 the call synchronises it before returning
+ * Scratch: a fixed 12 KB array in the library's device globals, one per
+ * device, held until the process exits.  The first call on a device looks up
+ * that array's device address (one-time set-up with the device current), so
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU race and must be ordered by the
+ * caller.  Returns ELMFB_OK, INVALID_ARG, UNSUPPORTED or CUDA; there is no
+ * handle, so no message is kept. */
+#define ELMFB_NOALLOC_MAX_POINTS ((int64_t)1 << 24)
+int elmfb_error_norms_noalloc(const double* u_hat, const double* u_ref, int64_t n, double* out3,
+                              void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,8 @@ _SIGNATURES = {
     "elmfb_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "elmfb_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "elmfb_error_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                            C.c_void_p]),
 }
 
 
