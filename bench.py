@@ -36,10 +36,11 @@ import numpy as np  # noqa: E402
 import workloads as WL  # noqa: E402
 
 METRIC = "ELM-FBPINN time-to-solution (s) at oracle-matched L2 error; assembly HBM GB/s"
+# workload -> (problem, oracle golden name, panel precision)
 WORKLOADS = {
-    "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400"),
-    "dho_ml": (WL.config_dho_ml, "dho_L1-64_K96_N20000"),
-    "poisson1d": (WL.config_poisson1d, "poisson1d_J16_K64_N2000"),
+    "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400", "fp32"),
+    "dho_ml": (WL.config_dho_ml, "dho_L1-64_K96_N20000", "fp64"),
+    "poisson1d": (WL.config_poisson1d, "poisson1d_J16_K64_N2000", "fp64"),
 }
 
 
@@ -143,12 +144,18 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    make, golden_name = WORKLOADS[args.workload]
+    make, golden_name, default_prec = WORKLOADS[args.workload]
     P = make()
-    prec = {"fp64": E.FP64, "fp32": E.FP32}[args.precision]
+    prec = {"fp64": E.FP64, "fp32": E.FP32}[args.precision or default_prec]
+    if args.shift is None:
+        args.shift = 1e-12 if prec == E.FP64 else 1e-10
     stream = torch.cuda.current_stream()
-    opts = E.default_solve_opts(max_iter=args.max_iter, atol=args.tol, btol=args.tol,
-                                shift=args.shift, check_every=args.check_every)
+    g = _golden(golden_name)
+    target = None
+    if args.target == "paper" and g and "lsqr" in g:
+        target = 1.01 * g["lsqr"]["rel_l2"]
+    elif args.target == "qr" and g and "qr" in g:
+        target = 1.01 * g["qr"]["rel_l2"]
 
     sets_dev = _sets(P, dev)
     xs_dev = torch.as_tensor(P.test_points).to(dev)
@@ -176,6 +183,24 @@ def run_ours(args):
         last.update(info=info, err=err, sizes=s.sizes(), stages=s.stage_times())
         s.close()
         return err
+
+    # untimed calibration: smallest iteration budget whose solution meets the target
+    budget = args.max_iter
+    calib = []
+    if target is not None:
+        b = args.calib_start
+        while True:
+            opts = E.default_solve_opts(max_iter=b, atol=0.0, btol=0.0, shift=args.shift,
+                                        check_every=args.check_every)
+            e = step(sets_dev, xs_dev, u_dev, uh_dev, False)["rel_l2"]
+            calib.append((b, float(e)))
+            if e <= target or b >= args.max_iter:
+                budget = b
+                break
+            b = min(args.max_iter, int(b * 1.5) + 1)
+    opts = E.default_solve_opts(max_iter=budget, atol=0.0 if target is not None else args.tol,
+                                btol=0.0 if target is not None else args.tol, shift=args.shift,
+                                check_every=args.check_every)
 
     for _ in range(args.warmup):
         step(sets_dev, xs_dev, u_dev, uh_dev, False)
@@ -248,7 +273,6 @@ def run_ours(args):
     dms = kstats[dom][0] / kstats[dom][1]
     ach = kstats[dom][2] / (dms * 1e-3) / 1e9
     asm = kern.get("assemble_panels", {})
-    g = _golden(golden_name)
     info, err, sz = last["info"], last["err"], last["sizes"]
     line = {
         "metric": METRIC,
@@ -261,14 +285,18 @@ def run_ours(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == E.FP32 else "f64",
+        "dtype": "f32+f64" if prec == E.FP32 else "f64",
         "data": "synthetic",
         "config": {"workload": golden_name, "levels": list(P.levels), "features": P.features,
                    "rows": P.n_rows, "columns": P.n_columns, "nnz_stored": int(sz.nnz),
-                   "solver": f"LSQR + block-Jacobi, tol {args.tol}, max_iter {args.max_iter}",
+                   "solver": f"LSQR + block-Jacobi (shift {args.shift}), {budget} iterations",
                    "parallelism": f"replicas x{ws}", "l2_flush": "inputs larger than L2 (panels "
                    f"{sz.panel_rows * P.features * (4 if prec == E.FP32 else 8) / 1e9:.2f} GB)"},
-        "solution": {"rel_l2": err["rel_l2"], "e_l1": err["e_l1"], "iterations": info.iterations,
+        "solution": {"rel_l2": float(err["rel_l2"]), "e_l1": float(err["e_l1"]),
+                     "iterations": info.iterations,
+                     "target": target, "target_kind": args.target,
+                     "matched": bool(err["rel_l2"] <= target) if target is not None else None,
+                     "calibration": calib,
                      "oracle_lsqr15000_rel_l2": (g or {}).get("lsqr", {}).get("rel_l2"),
                      "oracle_qr_rel_l2": (g or {}).get("qr", {}).get("rel_l2")},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
@@ -320,7 +348,7 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    make, golden_name = WORKLOADS[args.workload]
+    make, golden_name, _ = WORKLOADS[args.workload]
     P = make()
     vals = []
     for i in range(args.warmup + args.steps):
@@ -350,10 +378,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poisson2d_ml", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--target", default="paper", choices=["paper", "qr", "none"])
+    ap.add_argument("--calib-start", type=int, default=10)
+    ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--shift", type=float, default=1e-10)
+    ap.add_argument("--shift", type=float, default=None)
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--cpu-row-stride", type=int, default=40)
     ap.add_argument("--cpu-lsqr-its", type=int, default=60)

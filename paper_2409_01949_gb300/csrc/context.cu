@@ -261,7 +261,7 @@ cudaEvent_t prof_event(elmfb_ctx* h) {
 const char* kKernelNames[KID_COUNT] = {"assemble_panels", "gather_Mv",    "entry_MTu",
                                        "panel_MTu",       "precond_apply", "lsqr_update",
                                        "gram_diag",       "block_chol",   "gram_tc",
-                                       "cell_sort"};
+                                       "cell_sort",       "fused_Mt_MTu"};
 }  // namespace
 
 void prof_begin(elmfb_ctx* h, int kid, double bytes) {

@@ -61,6 +61,22 @@ __device__ double block_sum(double v, double* sh) {
   return s;
 }
 
+// sum of n partials by warp 0 of the block in a fixed order (lane-strided
+// sums, then a fixed xor tree); the result is broadcast through shared memory
+// so that every block of a grid computes the identical value.
+__device__ double block_partial_sum(const double* __restrict__ part, int n, double* sh) {
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+    v = warp_sum<double>(v);
+    if (threadIdx.x == 0) *sh = v;
+  }
+  __syncthreads();
+  const double r = *sh;
+  __syncthreads();
+  return r;
+}
+
 // ------------------------------------------------------------ Gram diag -----
 // partial sums of the upper triangle of P^T P over one chunk of panel rows
 template <class T, int NACC>
@@ -332,6 +348,181 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
   }
 }
 
+// One pass over the panels per LSQR iteration.  A CTA takes one unit (a row
+// range of one cell); warp w owns the w-th covering panel of the cell.  For
+// each 8-row chunk the warps load their panel rows into registers and form
+// d_w(r) = P_w[r] . t_w; the row values u'(r) = sum_w d_w(r) - coef u(r)
+// (mode 0) or h(r) - sum_w d_w(r) (mode 1) are formed in FP64 in a fixed
+// order; then every warp adds P_w[r] u'(r) into its running partial of
+// M^T u' (Kahan-compensated in FP32 panels).  The unit's partials and its
+// ||u'||^2 are written once: M t and M^T u' read each panel entry once.
+constexpr int kFusedRows = 8;
+
+template <class T, int FPL, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_fused(
+    const T* __restrict__ panels, const double* __restrict__ tvec, int K,
+    const int4* __restrict__ units, const int* __restrict__ cell_pstart,
+    const int* __restrict__ cell_count, const int* __restrict__ cover_off,
+    const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
+    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    double* __restrict__ u, const double* __restrict__ hvec, int mode,
+    double* __restrict__ partial, double* __restrict__ norm_partial) {
+  __shared__ double sd[32][kFusedRows];
+  __shared__ double su[kFusedRows];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
+  const int c = un.x;
+  const int m = cover_off[c + 1] - cover_off[c];
+  const int cnt = cell_count[c];
+  const int64_t R0 = cell_pstart[c];
+  const bool active = w < m;
+  const int e = cover_off[c] + (active ? w : 0);
+  const int s = cover_sub[e];
+  const T* base = panels + (panel_off[s] + cover_start[e]) * (int64_t)K;
+  T tv[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) {
+    const int k = lane + 32 * j;
+    tv[j] = (active && k < K) ? (T)tvec[(int64_t)s * K + k] : T(0);
+  }
+  double coef = 0.0;
+  if (mode == 0) {
+    const double beta = scal[S_BETA];
+    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+  }
+  T ahi[FPL], alo[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) ahi[j] = alo[j] = T(0);
+  double nrm = 0.0;
+  // register double buffer: rows (and u values) of the next chunk are loaded
+  // while the current chunk is reduced
+  T pv[kFusedRows][FPL], pn[kFusedRows][FPL];
+  double uold = 0.0, unext = 0.0;
+  auto load_chunk = [&](int r0, T (&dst)[kFusedRows][FPL], double& uo) {
+    const int nr = min(kFusedRows, un.z - r0);
+#pragma unroll
+    for (int r = 0; r < kFusedRows; ++r)
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) {
+        const int k = lane + 32 * j;
+        dst[r][j] = (active && r < nr && k < K) ? base[(int64_t)(r0 + r) * K + k] : T(0);
+      }
+    const int p = r0 + (int)threadIdx.x;
+    uo = 0.0;
+    if (threadIdx.x < (unsigned)nr && p < cnt)
+      uo = mode == 0 ? u[R0 + p] : hvec[R0 + p];
+  };
+  if (un.y < un.z) load_chunk(un.y, pv, uold);
+  for (int r0 = un.y; r0 < un.z; r0 += kFusedRows) {
+    const int nr = min(kFusedRows, un.z - r0);
+    if (r0 + kFusedRows < un.z) load_chunk(r0 + kFusedRows, pn, unext);
+#pragma unroll
+    for (int r = 0; r < kFusedRows; ++r) {
+      T d = 0;
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) d += pv[r][j] * tv[j];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) sd[w][r] = (double)d;
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const int r = threadIdx.x;
+      const int p = r0 + r;
+      double y = 0.0;
+      for (int q = 0; q < m; ++q) y += sd[q][r];
+      double out = 0.0;
+      if (p < cnt) {
+        out = mode == 0 ? y - coef * uold : uold - y;
+        u[R0 + p] = out;
+        nrm += out * out;
+      }
+      su[r] = out;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kFusedRows; ++r) {
+      const T ur = r < nr ? (T)su[r] : T(0);
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) {
+        if (sizeof(T) == 8) {
+          ahi[j] += pv[r][j] * ur;
+        } else {
+          const T y = pv[r][j] * ur - alo[j];
+          const T t = ahi[j] + y;
+          alo[j] = (t - ahi[j]) - y;
+          ahi[j] = t;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kFusedRows; ++r)
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) pv[r][j] = pn[r][j];
+    uold = unext;
+  }
+  if (active) {
+    double* out = partial + (int64_t)(un.w + w) * K;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+      const int k = lane + 32 * j;
+      if (k < K) out[k] = (double)ahi[j] - (double)alo[j];
+    }
+  }
+  // threads 0..7 of warp 0 hold the row norms
+  double tot = block_sum(threadIdx.x < kFusedRows ? nrm : 0.0, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+}
+
+// v'_j = X_j z_j / beta - beta v_j with z_j = sum of the unit partials of panel j
+// (X_j = R_j^{-T}); several thread groups split the partial list of a panel.
+__global__ void __launch_bounds__(1024) k_panel_T2(
+    const double* __restrict__ partial, const int* __restrict__ pent_off,
+    const int* __restrict__ pent, const double* __restrict__ Xc, int K,
+    const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
+    double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial) {
+  extern __shared__ double zsh[];   // [groups][K] then z[K]
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
+  __shared__ double shs;
+  const double beta = sqrt(block_partial_sum(beta_partial, n_beta_partial, &shs));
+  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (g < G && k < K) {
+    double z = 0.0;
+    for (int q = pent_off[s] + g; q < pent_off[s + 1]; q += G) z += partial[(int64_t)pent[q] * K + k];
+    zsh[g * K + k] = z;
+  }
+  __syncthreads();
+  double* zs = zsh + G * K;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double z = 0.0;
+    for (int q = 0; q < G; ++q) z += zsh[q * K + i];
+    zs[i] = z * ib;
+  }
+  __syncthreads();
+  const double* X = Xc + (int64_t)s * K * K;
+  double nrm = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double acc;
+    if (identity) {
+      acc = zs[i];
+    } else {
+      acc = 0.0;
+      for (int mm = 0; mm <= i; ++mm) acc += X[mm * K + i] * zs[mm];
+    }
+    const double vold = init ? 0.0 : v[(int64_t)s * K + i];
+    const double vn = acc - beta * vold;
+    v[(int64_t)s * K + i] = vn;
+    nrm += vn * vn;
+  }
+  double tot = block_sum(nrm, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;
+}
+
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the entry partials of panel j
 // (X_j = R_j^{-T}); writes v' (unnormalised) and ||v'||^2 per block.
 __global__ void k_panel_T(const double* __restrict__ partial, const int* __restrict__ pent_off,
@@ -378,9 +569,8 @@ __global__ void k_panel_T(const double* __restrict__ partial, const int* __restr
 __global__ void k_update(double* __restrict__ scal, const double* __restrict__ alpha_partial,
                          int n_alpha_partial, double* __restrict__ v, double* __restrict__ w,
                          double* __restrict__ x, int64_t N, int init) {
-  double a2 = 0.0;
-  for (int i = 0; i < n_alpha_partial; ++i) a2 += alpha_partial[i];
-  const double alpha = sqrt(a2);
+  __shared__ double shs;
+  const double alpha = sqrt(block_partial_sum(alpha_partial, n_alpha_partial, &shs));
   const double beta = scal[kStage + S_BETA];   // beta_{i+1}
   const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
   double phi_rho = 0.0, theta_rho = 0.0;
@@ -551,6 +741,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   h->d_ptile.alloc((kGatherBlocks + h->n_sub + 8) * sizeof(double), st);
   double* gpart = h->d_ptile.as<double>();
   double* vpart = gpart + kGatherBlocks;
+  const double panel_bytes = (double)h->NPR * K * sizeof(T);
   CUDA_CHECK(cudaMemsetAsync(h->d_scal.p, 0, 2 * kScal * sizeof(double), st));
 
   const T* P = (const T*)h->d_panels.p;
@@ -566,7 +757,6 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
                                     (int)esm));
   const int upd_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
 
-  const double panel_bytes = (double)h->NPR * K * sizeof(T);
   auto gather = [&](const double* t, int mode) {
     prof_begin(h, KID_GATHER, panel_bytes + 16.0 * h->NR + 8.0 * N);
     k_gather<T><<<kGatherBlocks, kGatherThreads, 0, st>>>(
@@ -594,17 +784,109 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     prof_end(h, KID_UPDATE);
   };
 
+  // fused single-pass iteration (M t and M^T u' in one read of the panels)
+  const bool fused = h->max_cover <= 32 && K <= 128;
+  DevBuf dunits, dfo, dfe, dfpart;
+  int n_units = 0;
+  int fthreads = 32 * std::max(1, h->max_cover);
+  if (fused) {
+    int64_t target = std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7));
+    std::vector<int4> units;
+    std::vector<std::vector<int>> plist(h->n_sub);
+    int pbase = 0;
+    for (int c = 0; c < h->n_cells; ++c) {
+      const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
+      const int m = h->cover_off[c + 1] - h->cover_off[c];
+      if (pad == 0) continue;
+      const int nunit = (int)ceil_div(pad, target);
+      const int per = (int)(ceil_div(ceil_div(pad, nunit), kFusedRows) * kFusedRows);
+      for (int r = 0; r < pad; r += per) {
+        units.push_back(make_int4(c, r, std::min(pad, r + per), pbase));
+        for (int w = 0; w < m; ++w) plist[h->cover_sub[h->cover_off[c] + w]].push_back(pbase + w);
+        pbase += m;
+      }
+    }
+    n_units = (int)units.size();
+    std::vector<int> fo(h->n_sub + 1, 0), fe;
+    fe.reserve(pbase);
+    for (int s2 = 0; s2 < h->n_sub; ++s2) {
+      fo[s2] = (int)fe.size();
+      fe.insert(fe.end(), plist[s2].begin(), plist[s2].end());
+    }
+    fo[h->n_sub] = (int)fe.size();
+    dunits.alloc(std::max<size_t>(units.size(), 1) * sizeof(int4), st);
+    dfo.alloc(fo.size() * sizeof(int), st);
+    dfe.alloc(std::max<size_t>(fe.size(), 1) * sizeof(int), st);
+    dfpart.alloc(std::max<int64_t>(pbase, 1) * K * sizeof(double), st);
+    CUDA_CHECK(cudaMemcpyAsync(dunits.p, units.data(), units.size() * sizeof(int4),
+                               cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(dfo.p, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               st));
+    CUDA_CHECK(cudaMemcpyAsync(dfe.p, fe.data(), fe.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               st));
+    h->d_ptile.alloc((std::max(kGatherBlocks, n_units) + h->n_sub + 8) * sizeof(double), st);
+    gpart = h->d_ptile.as<double>();
+    vpart = gpart + std::max(kGatherBlocks, n_units);
+  }
+  const int fpl = (K + 31) / 32;
+  const int KpT = (K + 31) & ~31;
+  const int tgroups = std::max(1, 1024 / KpT);
+  const size_t p2smem = (size_t)(tgroups + 1) * K * sizeof(double);
+  auto fused_step = [&](const double* t, int mode) {
+    prof_begin(h, KID_FUSED, panel_bytes + 16.0 * h->NR + 8.0 * N);
+#define ELMFB_FU(F, MT)                                                                      \
+  if (fpl == F && fthreads <= MT) {                                                          \
+    k_fused<T, F, MT><<<n_units, fthreads, 0, st>>>(                                         \
+        P, t, K, dunits.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
+        h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),      \
+        h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
+        dfpart.as<double>(), gpart);                                                         \
+  } else
+#define ELMFB_FU4(F) ELMFB_FU(F, 256) ELMFB_FU(F, 512) ELMFB_FU(F, 640) ELMFB_FU(F, 1024)
+    ELMFB_FU4(1) ELMFB_FU4(2) ELMFB_FU4(3) ELMFB_FU4(4)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "fused path needs K <= 128 and <= 32 covering panels");
+#undef ELMFB_FU4
+#undef ELMFB_FU
+    prof_end(h, KID_FUSED);
+  };
+  auto fused_tail = [&](int init) {
+    prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
+                                   (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
+    k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
+        dfpart.as<double>(), dfo.as<int>(), dfe.as<int>(), Xc, K, gpart, n_units,
+        h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart);
+    prof_end(h, KID_PANEL_T);
+    prof_begin(h, KID_UPDATE, 48.0 * N);
+    k_update<<<upd_blocks, 256, 0, st>>>(scal, vpart, h->n_sub, h->d_v.as<double>(),
+                                         h->d_w.as<double>(), h->d_x_sol.as<double>(), N, init);
+    prof_end(h, KID_UPDATE);
+  };
+  if (fused && p2smem > 48 * 1024)
+    CUDA_CHECK(cudaFuncSetAttribute(k_panel_T2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)p2smem));
+
   stage_begin(h, 5);
   // start: b = h (cold) or h - M a0 (warm start)
-  if (o->warm_start) {
-    gather(h->d_a.as<double>(), 1);
+  if (fused) {
+    if (o->warm_start) {
+      fused_step(h->d_a.as<double>(), 1);
+    } else {
+      CUDA_CHECK(cudaMemsetAsync(h->d_tmp.p, 0, N * sizeof(double), st));
+      fused_step(h->d_tmp.as<double>(), 1);
+    }
+    fused_tail(1);
+    count_launch(h, 3);
   } else {
-    // u' = h: gather with t = 0 in mode 1 gives h - 0
-    CUDA_CHECK(cudaMemsetAsync(h->d_tmp.p, 0, N * sizeof(double), st));
-    gather(h->d_tmp.as<double>(), 1);
+    if (o->warm_start) {
+      gather(h->d_a.as<double>(), 1);
+    } else {
+      // u' = h: gather with t = 0 in mode 1 gives h - 0
+      CUDA_CHECK(cudaMemsetAsync(h->d_tmp.p, 0, N * sizeof(double), st));
+      gather(h->d_tmp.as<double>(), 1);
+    }
+    transpose_step(1);
+    count_launch(h, 4);
   }
-  transpose_step(1);
-  count_launch(h, 4);
   check_launch("lsqr init");
 
   int it = 0;
@@ -619,10 +901,15 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
                                                                h->d_tmp.as<double>(), identity,
                                                                scal);
       prof_end(h, KID_PRECOND);
-      gather(h->d_tmp.as<double>(), 0);
-      transpose_step(0);
+      if (fused) {
+        fused_step(h->d_tmp.as<double>(), 0);
+        fused_tail(0);
+      } else {
+        gather(h->d_tmp.as<double>(), 0);
+        transpose_step(0);
+      }
     }
-    count_launch(h, 5 * batch);
+    count_launch(h, (fused ? 4 : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
