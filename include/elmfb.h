@@ -168,6 +168,7 @@ typedef struct {
   int64_t panel_rows;      /* stored panel rows including padding           */
   int64_t n_cells;         /* cells of the common refinement of supports     */
   int64_t n_gram_pairs;    /* subdomain pairs (i <= j) sharing a cell        */
+  double gram_flops;       /* 2 K^2 x shared rows, summed over those pairs  */
   int features;
   int n_levels;
   int dim;
@@ -183,6 +184,20 @@ int elmfb_get_params(elmfb_t h, double* W, double* b);
  *   rows [n] row indices (paper order); out [n * N_Phi] row-major FP64;
  *   h_out [n] or NULL.   Errors: STATE before assemble, INVALID_ARG. */
 int elmfb_get_rows(elmfb_t h, const int64_t* rows, int64_t n, double* out, double* h_out);
+
+/* Gram blocks G_ij = M_i^T M_j of every subdomain pair (i <= j) whose
+ * supports share collocation points -- the normal-equations matrix of Eq.
+ * multilevel_ls with the block structure of Eq. multilevel_domain_decomp --
+ * computed on the tcgen05 tensor cores from BF16 copies of the panels with
+ * FP32 accumulation.  Needs ELMFB_MIXED precision and K <= 128 (UNSUPPORTED
+ * otherwise); STATE before assemble; TIMEOUT if a pipeline wait gave up.
+ * The blocks stay on the device (n_gram_pairs x K x K FP32). */
+int elmfb_compute_gram(elmfb_t h);
+
+/* Copy Gram blocks out: ij [2n] pairs (i, j) of subdomain indices (either
+ * order), out [n * K * K] FP64 row-major (row = feature of i, column =
+ * feature of j).  Blocks of pairs that share no rows are zero. */
+int elmfb_get_gram(elmfb_t h, int64_t n, const int* ij, double* out);
 
 /* Solver options and report. */
 typedef struct {

@@ -55,7 +55,8 @@ class RowSet(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("n_columns", C.c_int64), ("n_rows", C.c_int64), ("n_subdomains", C.c_int64),
                 ("nnz", C.c_int64), ("panel_rows", C.c_int64), ("n_cells", C.c_int64),
-                ("n_gram_pairs", C.c_int64), ("features", C.c_int), ("n_levels", C.c_int),
+                ("n_gram_pairs", C.c_int64), ("gram_flops", C.c_double), ("features", C.c_int),
+                ("n_levels", C.c_int),
                 ("dim", C.c_int), ("precision", C.c_int)]
 
 
@@ -95,6 +96,8 @@ _SIGNATURES = {
                                      C.c_void_p]),
     "elmfb_error_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                             C.c_void_p]),
+    "elmfb_compute_gram": (C.c_int, [C.c_void_p]),
+    "elmfb_get_gram": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -284,6 +287,17 @@ class Solver:
         out = np.zeros(N_STAGES)
         _check(self.h, lib().elmfb_stage_times(self.h, out.ctypes.data))
         return dict(zip(STAGE_NAMES, out.tolist()))
+
+    def compute_gram(self):
+        _check(self.h, lib().elmfb_compute_gram(self.h))
+
+    def gram_blocks(self, pairs):
+        """pairs: sequence of (i, j) subdomain indices -> array (n, K, K)."""
+        ij = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        K = self.sizes().features
+        out = np.zeros((ij.shape[0], K, K))
+        _check(self.h, lib().elmfb_get_gram(self.h, ij.shape[0], ij.ctypes.data, out.ctypes.data))
+        return out
 
     def kernel_launches(self) -> int:
         return int(lib().elmfb_kernel_launches(self.h))

@@ -66,7 +66,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB) or _stale(LIB, objs):
-        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcuda"])
+        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs])
     return LIB
 
 

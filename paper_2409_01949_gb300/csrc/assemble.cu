@@ -38,6 +38,8 @@
 #include <cmath>
 #include <numeric>
 
+#include <cuda_bf16.h>
+
 #include "elmfb_internal.cuh"
 
 namespace {
@@ -242,7 +244,7 @@ __device__ __forceinline__ void window_at(const double* x, int dim, const SubGeo
   }
 }
 
-template <class T, int FPL>
+template <class T, int FPL, bool WRITE_T>
 __global__ void __launch_bounds__(128) k_assemble(
     const int2* __restrict__ tiles, int64_t n_tiles, int dim, int K, int L,
     const SubGeom* __restrict__ sub, const int* __restrict__ cover_sub,
@@ -250,7 +252,9 @@ __global__ void __launch_bounds__(128) k_assemble(
     const int* __restrict__ cell_level_off, const int* __restrict__ cell_count,
     const int* __restrict__ cell_pstart, const int64_t* __restrict__ panel_off,
     const double* __restrict__ xs, const int* __restrict__ rcls,
-    const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels) {
+    const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels,
+    __nv_bfloat16* __restrict__ pt, int64_t NPR) {
+  extern __shared__ __nv_bfloat16 tsm[];   // WRITE_T: per warp [K][32]
   const int lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (t >= n_tiles) return;
@@ -327,7 +331,20 @@ __global__ void __launch_bounds__(128) k_assemble(
         T v = phi * rA + tt * (rb0 * d0[i] + rb1 * d1[i]) -
               T(2) * phi * tt * (rg0 * d0[i] * d0[i] + rg1 * d1[i] * d1[i]);
         orow[k] = v;
+        if (WRITE_T) tsm[((threadIdx.x >> 5) * K + k) * 32 + r] = __float2bfloat16_rn((float)v);
       }
+    }
+  }
+  if (WRITE_T) {
+    // feature-major BF16 copy: feature k, rows rho0 .. rho0+nrows in 16-byte pieces
+    __syncwarp();
+    const __nv_bfloat16* wt = tsm + (threadIdx.x >> 5) * K * 32;
+    const int64_t rho0 = panel_off[s] + cover_start[e] + p0;
+    const int pieces = nrows / 8;   // nrows is 16 or 32
+    for (int idx = lane; idx < K * pieces; idx += 32) {
+      const int k = idx / pieces, q = idx - k * pieces;
+      const uint4 val = *reinterpret_cast<const uint4*>(wt + k * 32 + q * 8);
+      *reinterpret_cast<uint4*>(pt + (int64_t)k * NPR + rho0 + q * 8) = val;
     }
   }
 }
@@ -341,18 +358,34 @@ void launch_assemble(elmfb_ctx* h) {
   if (blocks == 0) return;
   const T* W = sizeof(T) == 8 ? (const T*)h->d_W64.p : (const T*)h->d_W32.p;
   const T* B = sizeof(T) == 8 ? (const T*)h->d_b64.p : (const T*)h->d_b32.p;
+  const bool wt = h->cfg.precision == ELMFB_MIXED && sizeof(T) == 4;
+  const size_t tsm = wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0;
 #define ELMFB_K1(F)                                                                          \
   case F:                                                                                    \
-    k_assemble<T, F><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(                        \
-        h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),          \
-        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),     \
-        h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(), h->d_cell_pstart.as<int>(), \
-        h->d_panel_off.as<int64_t>(), h->d_x.as<double>(), h->d_rcls.as<int>(), W, B,        \
-        (T*)h->d_panels.p);                                                                  \
+    if (wt)                                                                                  \
+      k_assemble<T, F, true><<<(unsigned)blocks, warps * 32, tsm, h->stream>>>(              \
+          h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
+          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
+          h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
+          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
+          h->d_rcls.as<int>(), W, B, (T*)h->d_panels.p, h->d_pt.as<__nv_bfloat16>(), h->NPR); \
+    else                                                                                     \
+      k_assemble<T, F, false><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(               \
+          h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
+          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
+          h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
+          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
+          h->d_rcls.as<int>(), W, B, (T*)h->d_panels.p, nullptr, h->NPR);                    \
     break;
-  // algorithmic bytes: every panel entry written once, point data read once
+  // algorithmic bytes: every panel entry written once (twice in mixed precision:
+  // FP32 row-major and BF16 feature-major), point data read once
   prof_begin(h, KID_ASSEMBLE,
-             (double)h->NPR * K * sizeof(T) + (double)h->NR * (h->dim * 8.0 + 4.0));
+             (double)h->NPR * K * (sizeof(T) + (wt ? 2.0 : 0.0)) +
+                 (double)h->NR * (h->dim * 8.0 + 4.0));
+  if (tsm > 48 * 1024) {
+    if (wt)
+      ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "mixed precision supports K <= 128");
+  }
   switch (fpl) {
     ELMFB_K1(1) ELMFB_K1(2) ELMFB_K1(3) ELMFB_K1(4) ELMFB_K1(5) ELMFB_K1(6) ELMFB_K1(7) ELMFB_K1(8)
     default: ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "features > 256");
@@ -506,7 +539,13 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
     for (int p = 0; p < pad; p += 32) tiles.push_back(make_int2(e, p));
   }
   h->n_tiles = (int64_t)tiles.size();
-  // Gram pair count: subdomain pairs (i <= j) that share a cell with points
+  // Gram pair count: subdomain pairs (i <= j) that share a cell with points,
+  // and the algorithmic Gram flops 2 K^2 per shared row and pair
+  h->gram_flops = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double m = h->cover_off[c + 1] - h->cover_off[c];
+    h->gram_flops += 0.5 * m * (m + 1) * 2.0 * h->K * h->K * h->cell_count[c];
+  }
   {
     std::vector<std::vector<int>> nb(h->n_sub);
     for (int c = 0; c < nc; ++c) {
@@ -568,6 +607,13 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   // K1: panels
   stage_begin(h, 2);
   h->d_panels.alloc(h->NPR * h->K * h->panel_elem(), st);
+  h->gram_pair_ij.clear();
+  h->have_gram = false;
+  if (h->cfg.precision == ELMFB_MIXED) {
+    h->d_pt.alloc(h->NPR * h->K * 2, st);
+    // padding tail of 16-row tiles is written by the kernel; clear once for safety
+    CUDA_CHECK(cudaMemsetAsync(h->d_pt.p, 0, h->NPR * h->K * 2, st));
+  }
   if (h->fp64()) launch_assemble<double>(h);
   else launch_assemble<float>(h);
   stage_end(h, 2);

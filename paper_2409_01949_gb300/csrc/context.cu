@@ -394,6 +394,7 @@ int elmfb_get_sizes(elmfb_t h, elmfb_sizes* o) {
     o->panel_rows = h->assembled ? h->NPR : 0;
     o->n_cells = h->n_cells;
     o->n_gram_pairs = h->n_gram_pairs;
+    o->gram_flops = h->gram_flops;
     o->features = h->K;
     o->n_levels = h->L;
     o->dim = h->dim;

@@ -132,6 +132,7 @@ struct elmfb_ctx {
   std::vector<int> cover_start;               // [n_entries] panel-local first row of the cell
   std::vector<int> row_class_of_set;          // per user row set: class id
   int64_t n_gram_pairs = 0;
+  double gram_flops = 0.0;
 
   DevBuf d_pts_user, d_rhs_user, d_cls_user;  // user order
   DevBuf d_row_cell, d_cell_count, d_cell_fill, d_cell_pstart;
@@ -148,6 +149,13 @@ struct elmfb_ctx {
   std::vector<int> entry_cell;   // [n_entries]
   DevBuf d_entry_cell;
   DevBuf d_flags;       // device status flags (int[4])
+
+  // BF16 feature-major panel copy PT[k][rho] (mixed precision) and Gram blocks
+  DevBuf d_pt;
+  std::vector<std::pair<int, int>> gram_pair_ij;   // sorted (i <= j)
+  int64_t gram_runs = 0;
+  DevBuf d_gram_pairs, d_gram_runs, d_gram;        // d_gram: [pair][K][K] FP32
+  bool have_gram = false;
 
   // solution
   DevBuf d_a;           // [NPhi] FP64
@@ -180,6 +188,10 @@ void stage_collect(elmfb_ctx* h);
 // assembly (assemble.cu)
 void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets);
 void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, double* h_out);
+
+// tensor-core Gram (gram_tc.cu)
+void gram_build_pairs(elmfb_ctx* h);
+void gram_compute(elmfb_ctx* h);
 
 // solve (solve.cu)
 void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);

@@ -26,7 +26,7 @@ SMALL = {
     "dho_L1-8_K24": (lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000),
                      [E.FP64, E.FP32]),
     "poisson2d_L1-4_K64": (lambda: WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60,
-                                                n_boundary_side=60), [E.FP64, E.FP32]),
+                                                n_boundary_side=60), [E.FP64, E.FP32, E.MIXED]),
     "dho_paper_K12_delta2.9_endpoint": (WL.dho_paper_baseline, [E.FP64]),
     "poisson2d_delta2.9_K40": (lambda: WL.poisson2d(levels=(3, 5), features=40, n_side=50,
                                                     n_boundary_side=50, delta=2.9), [E.FP32]),
