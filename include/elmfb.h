@@ -209,6 +209,11 @@ typedef struct {
   double shift;        /* Cholesky shift eps: G_jj + eps tr(G_jj)/K I          */
   int check_every;     /* host checks convergence every this many iterations  */
   int warm_start;      /* nonzero: start from the handle's current coefficients */
+  int refine;          /* PCG: outer refinement steps (>= 1); each recomputes
+                          g = M^T (h - M a) from the panels and runs max_iter
+                          PCG iterations on the tensor-core Gram for the update */
+  double gram_shift;   /* PCG: Tikhonov shift mu, as a fraction of the mean
+                          Gram diagonal, added to the Gram operator          */
 } elmfb_solve_opts;
 
 typedef struct {
@@ -221,11 +226,16 @@ typedef struct {
 } elmfb_solve_info;
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
- * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start. */
+ * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
+ * gram_shift 0. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the
  * paper uses LSQR, §3 and §4.1).  The result stays in the handle.
+ * ELMFB_SOLVE_PCG (not in the paper) solves the normal equations instead:
+ * `refine` outer steps a += PCG(G_bf16 + mu I, M^T (h - M a)), each with
+ * max_iter PCG iterations preconditioned by the block-Jacobi factors; it
+ * needs ELMFB_MIXED precision (tensor-core Gram).
  * Errors: STATE before assemble, BREAKDOWN, NONFINITE, INVALID_ARG.
  * Returns NOT_CONVERGED (with valid coefficients) at the iteration cap. */
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info);

@@ -261,7 +261,7 @@ cudaEvent_t prof_event(elmfb_ctx* h) {
 const char* kKernelNames[KID_COUNT] = {"assemble_panels", "gather_Mv",    "entry_MTu",
                                        "panel_MTu",       "precond_apply", "lsqr_update",
                                        "gram_diag",       "block_chol",   "gram_tc",
-                                       "cell_sort",       "fused_Mt_MTu"};
+                                       "cell_sort",       "fused_Mt_MTu",  "gram_spmv"};
 }  // namespace
 
 void prof_begin(elmfb_ctx* h, int kid, double bytes) {
@@ -429,6 +429,8 @@ void elmfb_default_solve_opts(elmfb_solve_opts* o) {
   o->shift = 1e-12;
   o->check_every = 50;
   o->warm_start = 0;
+  o->refine = 1;
+  o->gram_shift = 0.0;
 }
 
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info) {
@@ -438,7 +440,8 @@ int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info)
     elmfb_solve_opts o;
     elmfb_default_solve_opts(&o);
     if (opts) o = *opts;
-    if (o.max_iter < 0 || o.check_every < 1 || !(o.shift >= 0.0))
+    if (o.max_iter < 0 || o.check_every < 1 || !(o.shift >= 0.0) || o.refine < 1 ||
+        !(o.gram_shift >= 0.0))
       ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad solver options");
     elmfb_solve_info inf{};
     solve_system(h, &o, &inf);

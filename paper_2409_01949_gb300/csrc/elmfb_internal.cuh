@@ -87,7 +87,7 @@ struct Stage {
 // kernels with device timing (elmfb_kernel_stats)
 enum KernelId {
   KID_ASSEMBLE = 0, KID_GATHER, KID_ENTRY_T, KID_PANEL_T, KID_PRECOND, KID_UPDATE,
-  KID_GRAM_DIAG, KID_BLOCK_CHOL, KID_GRAM_TC, KID_CELL_SORT, KID_FUSED, KID_COUNT
+  KID_GRAM_DIAG, KID_BLOCK_CHOL, KID_GRAM_TC, KID_CELL_SORT, KID_FUSED, KID_GSPMV, KID_COUNT
 };
 struct ProfRec {
   int kid;

@@ -641,6 +641,82 @@ struct SolveLayout {
   std::vector<int> pent_off, pent;
 };
 
+// Work plan of the fused pass: units (cell, row range, first partial) and, per
+// panel, the list of partial rows that sum to its part of M^T u'.
+struct FusedPlan {
+  DevBuf units, fo, fe, part;
+  int n_units = 0;
+  int threads = 0;
+};
+
+bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
+  const int K = h->K;
+  if (h->max_cover > 32 || K > 128) return false;
+  cudaStream_t st = h->stream;
+  fp.threads = 32 * std::max(1, h->max_cover);
+  const int64_t target = std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7));
+  std::vector<int4> units;
+  std::vector<std::vector<int>> plist(h->n_sub);
+  int pbase = 0;
+  for (int c = 0; c < h->n_cells; ++c) {
+    const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
+    const int m = h->cover_off[c + 1] - h->cover_off[c];
+    if (pad == 0) continue;
+    const int nunit = (int)ceil_div(pad, target);
+    const int per = (int)(ceil_div(ceil_div(pad, nunit), kFusedRows) * kFusedRows);
+    for (int r = 0; r < pad; r += per) {
+      units.push_back(make_int4(c, r, std::min(pad, r + per), pbase));
+      for (int w = 0; w < m; ++w) plist[h->cover_sub[h->cover_off[c] + w]].push_back(pbase + w);
+      pbase += m;
+    }
+  }
+  fp.n_units = (int)units.size();
+  std::vector<int> fo(h->n_sub + 1, 0), fe;
+  fe.reserve(pbase);
+  for (int s2 = 0; s2 < h->n_sub; ++s2) {
+    fo[s2] = (int)fe.size();
+    fe.insert(fe.end(), plist[s2].begin(), plist[s2].end());
+  }
+  fo[h->n_sub] = (int)fe.size();
+  fp.units.alloc(std::max<size_t>(units.size(), 1) * sizeof(int4), st);
+  fp.fo.alloc(fo.size() * sizeof(int), st);
+  fp.fe.alloc(std::max<size_t>(fe.size(), 1) * sizeof(int), st);
+  fp.part.alloc(std::max<int64_t>(pbase, 1) * K * sizeof(double), st);
+  CUDA_CHECK(cudaMemcpyAsync(fp.units.p, units.data(), units.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(fp.fo.p, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             st));
+  CUDA_CHECK(cudaMemcpyAsync(fp.fe.p, fe.data(), fe.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             st));
+  return true;
+}
+
+template <class T>
+void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double* scal,
+                  double* gpart) {
+  const int K = h->K;
+  const int fpl = (K + 31) / 32;
+  const int fthreads = fp.threads;
+  const T* P = (const T*)h->d_panels.p;
+  cudaStream_t st = h->stream;
+  prof_begin(h, KID_FUSED, (double)h->NPR * K * sizeof(T) + 16.0 * h->NR + 8.0 * h->NPhi);
+#define ELMFB_FU(F, MT)                                                                      \
+  if (fpl == F && fthreads <= MT) {                                                          \
+    k_fused<T, F, MT><<<fp.n_units, fthreads, 0, st>>>(                                      \
+        P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), \
+        h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),      \
+        h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
+        fp.part.as<double>(), gpart);                                                        \
+  } else
+#define ELMFB_FU4(F) ELMFB_FU(F, 256) ELMFB_FU(F, 512) ELMFB_FU(F, 640) ELMFB_FU(F, 1024)
+  ELMFB_FU4(1) ELMFB_FU4(2) ELMFB_FU4(3) ELMFB_FU4(4)
+  ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "fused path needs K <= 128 and <= 32 covering panels");
+#undef ELMFB_FU4
+#undef ELMFB_FU
+  prof_end(h, KID_FUSED);
+  count_launch(h);
+}
+
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity) {
   cudaStream_t st = h->stream;
@@ -785,69 +861,24 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   };
 
   // fused single-pass iteration (M t and M^T u' in one read of the panels)
-  const bool fused = h->max_cover <= 32 && K <= 128;
-  DevBuf dunits, dfo, dfe, dfpart;
-  int n_units = 0;
-  int fthreads = 32 * std::max(1, h->max_cover);
+  FusedPlan fp;
+  const bool fused = build_fused_plan(h, fp);
+  DevBuf& dunits = fp.units;
+  DevBuf& dfo = fp.fo;
+  DevBuf& dfe = fp.fe;
+  DevBuf& dfpart = fp.part;
+  const int n_units = fp.n_units;
+  const int fthreads = fp.threads;
   if (fused) {
-    int64_t target = std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7));
-    std::vector<int4> units;
-    std::vector<std::vector<int>> plist(h->n_sub);
-    int pbase = 0;
-    for (int c = 0; c < h->n_cells; ++c) {
-      const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
-      const int m = h->cover_off[c + 1] - h->cover_off[c];
-      if (pad == 0) continue;
-      const int nunit = (int)ceil_div(pad, target);
-      const int per = (int)(ceil_div(ceil_div(pad, nunit), kFusedRows) * kFusedRows);
-      for (int r = 0; r < pad; r += per) {
-        units.push_back(make_int4(c, r, std::min(pad, r + per), pbase));
-        for (int w = 0; w < m; ++w) plist[h->cover_sub[h->cover_off[c] + w]].push_back(pbase + w);
-        pbase += m;
-      }
-    }
-    n_units = (int)units.size();
-    std::vector<int> fo(h->n_sub + 1, 0), fe;
-    fe.reserve(pbase);
-    for (int s2 = 0; s2 < h->n_sub; ++s2) {
-      fo[s2] = (int)fe.size();
-      fe.insert(fe.end(), plist[s2].begin(), plist[s2].end());
-    }
-    fo[h->n_sub] = (int)fe.size();
-    dunits.alloc(std::max<size_t>(units.size(), 1) * sizeof(int4), st);
-    dfo.alloc(fo.size() * sizeof(int), st);
-    dfe.alloc(std::max<size_t>(fe.size(), 1) * sizeof(int), st);
-    dfpart.alloc(std::max<int64_t>(pbase, 1) * K * sizeof(double), st);
-    CUDA_CHECK(cudaMemcpyAsync(dunits.p, units.data(), units.size() * sizeof(int4),
-                               cudaMemcpyHostToDevice, st));
-    CUDA_CHECK(cudaMemcpyAsync(dfo.p, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice,
-                               st));
-    CUDA_CHECK(cudaMemcpyAsync(dfe.p, fe.data(), fe.size() * sizeof(int), cudaMemcpyHostToDevice,
-                               st));
     h->d_ptile.alloc((std::max(kGatherBlocks, n_units) + h->n_sub + 8) * sizeof(double), st);
     gpart = h->d_ptile.as<double>();
     vpart = gpart + std::max(kGatherBlocks, n_units);
   }
-  const int fpl = (K + 31) / 32;
   const int KpT = (K + 31) & ~31;
   const int tgroups = std::max(1, 1024 / KpT);
   const size_t p2smem = (size_t)(tgroups + 1) * K * sizeof(double);
   auto fused_step = [&](const double* t, int mode) {
-    prof_begin(h, KID_FUSED, panel_bytes + 16.0 * h->NR + 8.0 * N);
-#define ELMFB_FU(F, MT)                                                                      \
-  if (fpl == F && fthreads <= MT) {                                                          \
-    k_fused<T, F, MT><<<n_units, fthreads, 0, st>>>(                                         \
-        P, t, K, dunits.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
-        h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),      \
-        h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
-        dfpart.as<double>(), gpart);                                                         \
-  } else
-#define ELMFB_FU4(F) ELMFB_FU(F, 256) ELMFB_FU(F, 512) ELMFB_FU(F, 640) ELMFB_FU(F, 1024)
-    ELMFB_FU4(1) ELMFB_FU4(2) ELMFB_FU4(3) ELMFB_FU4(4)
-    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "fused path needs K <= 128 and <= 32 covering panels");
-#undef ELMFB_FU4
-#undef ELMFB_FU
-    prof_end(h, KID_FUSED);
+    launch_fused<T>(h, fp, t, mode, scal, gpart);
   };
   auto fused_tail = [&](int init) {
     prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
@@ -909,7 +940,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
         transpose_step(0);
       }
     }
-    count_launch(h, (fused ? 4 : 5) * batch);
+    count_launch(h, (fused ? 3 : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
@@ -944,9 +975,270 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   info->solve_ms = h->stage_ms[5];
 }
 
+
+// ------------------------------------------------------------------ PCG -----
+// Normal equations (G + mu I) a = g with G the tensor-core Gram (BF16 products,
+// FP32 blocks), block-Jacobi preconditioned; outer refinement steps recompute
+// g = M^T (h - M a) exactly from the panels with the fused pass.
+
+// per pair: y_i part = G_ij x_j, y_j part = G_ij^T x_i (FP32 products summed in
+// FP32 per row, stored FP64); one block per pair
+__global__ void __launch_bounds__(128) k_gspmv_pairs(const float* __restrict__ G,
+                                                     const int2* __restrict__ pij, int K,
+                                                     const double* __restrict__ x,
+                                                     double* __restrict__ part) {
+  __shared__ float xi[128], xj[128];
+  const int p = blockIdx.x;
+  const int2 ij = pij[p];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    xi[k] = (float)x[(int64_t)ij.x * K + k];
+    xj[k] = (float)x[(int64_t)ij.y * K + k];
+  }
+  __syncthreads();
+  const float* B = G + (int64_t)p * K * K;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* yi = part + (int64_t)p * 2 * K;
+  double* yj = yi + K;
+  // rows: warp per row, lanes along the row (coalesced)
+  for (int m = w; m < K; m += nw) {
+    float acc = 0.f;
+    for (int n = lane; n < K; n += 32) acc += B[(int64_t)m * K + n] * xj[n];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) yi[m] = (double)acc;
+  }
+  if (ij.x != ij.y) {
+    // columns: thread per column, loop over rows (coalesced across threads)
+    for (int n = threadIdx.x; n < K; n += blockDim.x) {
+      float acc = 0.f;
+      for (int m = 0; m < K; ++m) acc += B[(int64_t)m * K + n] * xi[m];
+      yj[n] = (double)acc;
+    }
+  }
+}
+
+// y_s = sum of its incident pair parts (fixed order) + mu x_s; partial x.y per block
+__global__ void k_gspmv_reduce(const double* __restrict__ part, const int* __restrict__ inc_off,
+                               const int* __restrict__ inc, int K, const double* __restrict__ x,
+                               double mu, double* __restrict__ y, double* __restrict__ dot_part) {
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  double d = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double acc = 0.0;
+    for (int q = inc_off[s]; q < inc_off[s + 1]; ++q) acc += part[(int64_t)inc[q] * K + k];
+    const double xv = x[(int64_t)s * K + k];
+    acc += mu * xv;
+    y[(int64_t)s * K + k] = acc;
+    d += xv * acc;
+  }
+  const double tot = block_sum(d, red);
+  if (threadIdx.x == 0) dot_part[s] = tot;
+}
+
+// z_s = X_s^T X_s r_s (= (G_ss + eps tr/K I)^{-1} r_s); partial r.z per block
+__global__ void k_bj_apply(const double* __restrict__ Xr, const double* __restrict__ Xc, int K,
+                           const double* __restrict__ r, double* __restrict__ z,
+                           double* __restrict__ dot_part) {
+  extern __shared__ double sh[];   // r[K], w[K]
+  __shared__ double red[32];
+  const int s = blockIdx.x;
+  double* rs = sh;
+  double* ws = sh + K;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) rs[i] = r[(int64_t)s * K + i];
+  __syncthreads();
+  const double* XC = Xc + (int64_t)s * K * K;   // XC[m*K + i] = X_im
+  const double* XR = Xr + (int64_t)s * K * K;   // XR[m*K + i] = X_mi
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double acc = 0.0;
+    for (int m = 0; m <= i; ++m) acc += XC[m * K + i] * rs[m];
+    ws[i] = acc;
+  }
+  __syncthreads();
+  double d = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double acc = 0.0;
+    for (int m = i; m < K; ++m) acc += XR[m * K + i] * ws[m];
+    z[(int64_t)s * K + i] = acc;
+    d += acc * rs[i];
+  }
+  const double tot = block_sum(d, red);
+  if (threadIdx.x == 0) dot_part[s] = tot;
+}
+
+// g_s = sum of the fused pass partials of panel s (M^T u' unscaled)
+__global__ void k_panel_sum(const double* __restrict__ partial, const int* __restrict__ pent_off,
+                            const int* __restrict__ pent, int K, double* __restrict__ g) {
+  const int s = blockIdx.x;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double acc = 0.0;
+    for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) acc += partial[(int64_t)pent[q] * K + k];
+    g[(int64_t)s * K + k] = acc;
+  }
+}
+
+// alpha = rz / p.q;  x += alpha p;  r -= alpha q   (rz in sc[slot])
+__global__ void k_pcg_axpy(const double* __restrict__ sc, int slot,
+                           const double* __restrict__ pq_part, int npart,
+                           const double* __restrict__ p, const double* __restrict__ q,
+                           double* __restrict__ x, double* __restrict__ r, int64_t N) {
+  __shared__ double shs;
+  const double pq = block_partial_sum(pq_part, npart, &shs);
+  const double rz = sc[slot];
+  const double alpha = pq > 0.0 ? rz / pq : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// beta = rz_new / rz;  p = z + beta p;  sc[slot ^ 1] = rz_new  (init: p = z)
+__global__ void k_pcg_pupdate(double* __restrict__ sc, int slot, const double* __restrict__ rz_part,
+                              int npart, const double* __restrict__ z, double* __restrict__ p,
+                              int64_t N, int init) {
+  __shared__ double shs;
+  const double rzn = block_partial_sum(rz_part, npart, &shs);
+  const double rz = sc[slot];
+  const double beta = (!init && rz > 0.0) ? rzn / rz : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[init ? slot : (slot ^ 1)] = rzn;
+}
+
+template <class T>
+void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
+  if (h->cfg.precision != ELMFB_MIXED)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "PCG on the tensor-core Gram needs ELMFB_MIXED precision");
+  cudaStream_t st = h->stream;
+  const int K = h->K;
+  const int64_t N = h->NPhi;
+  const int64_t KK = (int64_t)K * K;
+  stage_begin(h, 4);
+  block_jacobi_setup<T>(h, o->shift, false);
+  stage_end(h, 4);
+  if (!h->have_gram) gram_compute(h);
+  info->setup_ms = h->stage_ms[4] + h->stage_ms[3];
+  FusedPlan fp;
+  if (!build_fused_plan(h, fp))
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "PCG needs K <= 128 and <= 32 covering panels per cell");
+  // per-subdomain incident pair parts, in pair order
+  const int64_t np = h->n_gram_pairs;
+  std::vector<int2> pij(np);
+  std::vector<std::vector<int>> inc(h->n_sub);
+  for (int64_t p = 0; p < np; ++p) {
+    const auto ij = h->gram_pair_ij[p];
+    pij[p] = make_int2(ij.first, ij.second);
+    inc[ij.first].push_back((int)(2 * p));
+    if (ij.first != ij.second) inc[ij.second].push_back((int)(2 * p + 1));
+  }
+  std::vector<int> ioff(h->n_sub + 1, 0), ilist;
+  for (int s2 = 0; s2 < h->n_sub; ++s2) {
+    ioff[s2] = (int)ilist.size();
+    ilist.insert(ilist.end(), inc[s2].begin(), inc[s2].end());
+  }
+  ioff[h->n_sub] = (int)ilist.size();
+  // panel -> fused partial rows (for g)
+  DevBuf dpij, dioff, dilist, dpart2, dvec, dpartial, dsc;
+  auto up = [&](DevBuf& d, const void* src, size_t bytes) {
+    d.alloc(std::max<size_t>(bytes, 8), st);
+    if (bytes) CUDA_CHECK(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, st));
+  };
+  up(dpij, pij.data(), np * sizeof(int2));
+  up(dioff, ioff.data(), ioff.size() * sizeof(int));
+  up(dilist, ilist.data(), ilist.size() * sizeof(int));
+  dpart2.alloc(std::max<int64_t>(np, 1) * 2 * K * sizeof(double), st);
+  dvec.alloc(6 * N * sizeof(double), st);
+  double* x = dvec.as<double>();
+  double* r = x + N;
+  double* z = r + N;
+  double* pv = z + N;
+  double* q = pv + N;
+  double* g = q + N;
+  h->d_u.alloc(h->NR * sizeof(double), st);
+  h->d_tmp.alloc(std::max<int64_t>(N, h->NR) * sizeof(double), st);
+  const int nparts = std::max(fp.n_units, h->n_sub);
+  dpartial.alloc((size_t)(nparts + 2 * h->n_sub + 8) * sizeof(double), st);
+  double* gpart = dpartial.as<double>();
+  double* dot1 = gpart + nparts;
+  double* dot2 = dot1 + h->n_sub;
+  dsc.alloc(kScal * sizeof(double), st);
+  CUDA_CHECK(cudaMemsetAsync(dsc.p, 0, kScal * sizeof(double), st));
+  double* sc = dsc.as<double>();
+  const double* Xr = h->d_R.as<double>();
+  const double* Xc = h->d_R.as<double>() + h->n_sub * KK;
+  // mu as a fraction of the mean Gram diagonal (host estimate from the diagonal blocks)
+  double mu = 0.0;
+  if (o->gram_shift > 0.0) {
+    std::vector<float> blk(K * K);
+    double tr = 0.0;
+    for (int64_t p = 0; p < np; ++p)
+      if (pij[p].x == pij[p].y) {
+        CUDA_CHECK(cudaMemcpy(blk.data(), h->d_gram.as<float>() + p * KK, KK * sizeof(float),
+                              cudaMemcpyDeviceToHost));
+        for (int k = 0; k < K; ++k) tr += blk[k * K + k];
+      }
+    mu = o->gram_shift * tr / (double)N;
+  }
+  const int vb = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
+  const int pb = std::min(std::max(32, ((K + 31) / 32) * 32), 256);
+  const size_t fsz = 16;   // unused scalar slots of the fused kernel (mode 1 reads none)
+
+  stage_begin(h, 5);
+  if (!o->warm_start) CUDA_CHECK(cudaMemsetAsync(h->d_a.p, 0, N * sizeof(double), st));
+  int its = 0;
+  for (int ref = 0; ref < o->refine; ++ref) {
+    // g = M^T (h - M a), exact from the panels
+    launch_fused<T>(h, fp, h->d_a.as<double>(), 1, sc + fsz, gpart);
+    k_panel_sum<<<h->n_sub, pb, 0, st>>>(fp.part.as<double>(), fp.fo.as<int>(), fp.fe.as<int>(),
+                                         K, g);
+    // PCG from x = 0: r = g, z = P r, p = z
+    CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), st));
+    CUDA_CHECK(cudaMemcpyAsync(r, g, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_bj_apply<<<h->n_sub, pb, 2 * K * sizeof(double), st>>>(Xr, Xc, K, r, z, dot2);
+    k_pcg_pupdate<<<vb, 256, 0, st>>>(sc, 0, dot2, h->n_sub, z, pv, N, 1);
+    count_launch(h, 3);
+    for (int k = 0; k < o->max_iter; ++k) {
+      const int slot = k & 1;
+      prof_begin(h, KID_GSPMV, (double)np * KK * 4.0 + 16.0 * N);
+      k_gspmv_pairs<<<(unsigned)std::max<int64_t>(np, 1), 128, 0, st>>>(
+          h->d_gram.as<float>(), dpij.as<int2>(), K, pv, dpart2.as<double>());
+      k_gspmv_reduce<<<h->n_sub, pb, 0, st>>>(dpart2.as<double>(), dioff.as<int>(),
+                                              dilist.as<int>(), K, pv, mu, q, dot1);
+      prof_end(h, KID_GSPMV);
+      k_pcg_axpy<<<vb, 256, 0, st>>>(sc, slot, dot1, h->n_sub, pv, q, x, r, N);
+      k_bj_apply<<<h->n_sub, pb, 2 * K * sizeof(double), st>>>(Xr, Xc, K, r, z, dot2);
+      k_pcg_pupdate<<<vb, 256, 0, st>>>(sc, slot, dot2, h->n_sub, z, pv, N, 0);
+      count_launch(h, 5);
+      ++its;
+    }
+    k_add_to<<<vb, 256, 0, st>>>(h->d_a.as<double>(), x, N);
+    count_launch(h);
+    check_launch("pcg");
+  }
+  // final residual norm ||h - M a|| from the fused pass partials
+  launch_fused<T>(h, fp, h->d_a.as<double>(), 1, sc + fsz, gpart);
+  std::vector<double> gp(fp.n_units);
+  CUDA_CHECK(cudaMemcpyAsync(gp.data(), gpart, fp.n_units * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  stage_end(h, 5);
+  double rn = 0.0;
+  for (double v : gp) rn += v;
+  info->status = ELMFB_OK;
+  info->iterations = its;
+  info->residual_norm = std::sqrt(rn);
+  info->normal_residual_norm = NAN;
+  info->solve_ms = h->stage_ms[5];
+}
+
 }  // namespace
 
 void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
+  if (o->method == ELMFB_SOLVE_PCG) {
+    pcg_solve<float>(h, o, info);
+    return;
+  }
   if (o->method != ELMFB_SOLVE_LSQR)
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "solver method not available in this build");
   if (o->preconditioner != ELMFB_PREC_NONE && o->preconditioner != ELMFB_PREC_BLOCK_JACOBI)
