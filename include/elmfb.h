@@ -75,8 +75,9 @@ enum {
 /* ---- preconditioners --------------------------------------------------------- */
 enum {
   ELMFB_PREC_NONE = 0,      /* plain LSQR, the paper's protocol                  */
-  ELMFB_PREC_BLOCK_JACOBI = 1 /* per-subdomain Cholesky of the shifted diagonal
+  ELMFB_PREC_BLOCK_JACOBI = 1,/* per-subdomain Cholesky of the shifted diagonal
                                Gram block (not in the paper)                      */
+  ELMFB_PREC_BJ_GNN = 2     /* FCG only: block-Jacobi plus the learned correction */
 };
 
 typedef struct elmfb_ctx* elmfb_t;
@@ -239,6 +240,64 @@ void elmfb_default_solve_opts(elmfb_solve_opts* opts);
  * Errors: STATE before assemble, BREAKDOWN, NONFINITE, INVALID_ARG.
  * Returns NOT_CONVERGED (with valid coefficients) at the iteration cap. */
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info);
+
+/* ---- learned preconditioner (not in the paper) ------------------------------
+ * A message-passing network on the subdomain graph (nodes = subdomains, edges
+ * = pairs sharing collocation points): input layer K -> 64, three layers
+ * A_l[s] = relu(W_self A_{l-1}[s] + W_nb mean_{t in N(s)} A_{l-1}[t] + b),
+ * output layer 64 -> K.  ELMFB_SOLVE_FCG_GNN runs flexible CG on M^T M a =
+ * M^T h (operator applied through the panels) with z = B r + s N(B r / s),
+ * s = ||B r||, B the block-Jacobi factor, when preconditioner ==
+ * ELMFB_PREC_BJ_GNN (block-Jacobi alone otherwise).
+ * Weight layout: W_in (64 x K), b_in (64), then per layer W_self (64 x 64),
+ * W_nb (64 x 64), b (64), then W_out (K x 64), b_out (K); FP32 row-major. */
+int64_t elmfb_gnn_num_weights(elmfb_t h);
+/* neighbour lists: off [n_subdomains + 1], nb [n_edges] (either may be NULL) */
+int elmfb_gnn_graph(elmfb_t h, int* off, int* nb, int64_t* n_edges);
+int elmfb_gnn_set_weights(elmfb_t h, const float* w);
+int elmfb_gnn_get_weights(elmfb_t h, float* w);
+/* Forward pass on `batch` samples x [batch][n_subdomains][K]; with targets t
+ * and per-sample weights wb also the loss (1/batch) sum_b wb_b ||y_b - t_b||^2
+ * and, if grad != NULL, its gradient w.r.t. the weights (for checking). */
+int elmfb_gnn_eval(elmfb_t h, int batch, const float* x, const float* t, const float* wb,
+                   float* y, float* grad, double* loss);
+/* Train on pairs from block-Jacobi FCG solves of this system with n_rhs other
+ * right-hand sides rhs [n_rhs][n_rows] (unscaled, row order of assemble):
+ * solve_iters recorded iterations per solve (errors against the iterate
+ * after 2 solve_iters), `epochs` passes of Adam (learning rate lr) over
+ * mini-batches of 8; weights initialised from SplitMix64(seed) with a zero
+ * output layer.  loss2 [2] receives the first and last epoch losses. */
+int elmfb_gnn_train(elmfb_t h, int n_rhs, const double* rhs, int solve_iters, int epochs,
+                    double lr, uint64_t seed, double* loss2);
+
+/* ---- batched solves (not in the paper) ---------------------------------------
+ * Solve many independent instances: each item is a full problem (create
+ * config + row sets), optionally with evaluation points, an output buffer
+ * for u_hat and reference values for the error norms.  n_workers host
+ * threads, each with its own non-blocking stream, take the instances in
+ * decreasing order of estimated work; all use the same solver options.
+ * Results are identical to solving the instances one by one.  Returns the
+ * first non-OK instance status (NOT_CONVERGED counts as OK), else ELMFB_OK.
+ * Pointers may be host or device memory, as elsewhere. */
+typedef struct {
+  elmfb_config cfg;
+  int n_sets;
+  const elmfb_rowset* sets;
+  int64_t n_eval;             /* 0: no evaluation                        */
+  const double* eval_points;  /* [n_eval * dim]                          */
+  double* eval_out;           /* [n_eval] u_hat                          */
+  const double* eval_ref;     /* [n_eval] reference values, or NULL      */
+  double* coeffs_out;         /* [N_Phi] coefficients, or NULL           */
+} elmfb_batch_item;
+typedef struct {
+  int status;
+  int iterations;
+  double rel_l2, e_l1, max_abs;   /* NaN without eval_ref                */
+  double total_ms;                /* host wall time of the instance      */
+  int64_t launches;               /* kernels launched for the instance   */
+} elmfb_batch_result;
+int elmfb_batch_solve(int n, const elmfb_batch_item* items, const elmfb_solve_opts* opts,
+                      int n_workers, elmfb_batch_result* results);
 
 /* Copy the coefficients a [N_Phi] out of / into the handle. */
 int elmfb_get_coeffs(elmfb_t h, double* a);

@@ -1,0 +1,84 @@
+"""Graph network of the learned preconditioner (oracle side; not in the paper).
+
+The GPU library learns a correction to its block-Jacobi preconditioner with a
+message-passing network over the subdomain graph (nodes = subdomains, edges =
+subdomain pairs whose supports share collocation points).  This module is the
+plain FP64 definition of that network, used to check the GPU forward pass and
+its hand-written gradients.
+
+Network (per sample b, node s; H hidden channels, K features per subdomain):
+    A0[s]  = relu(W_in X[s] + b_in)
+    for l = 1, 2, 3:
+        agg[s] = mean_{t in N(s)} A_{l-1}[t]          (N(s): neighbours, s excluded)
+        A_l[s] = relu(W_self_l A_{l-1}[s] + W_nb_l agg[s] + b_l)
+    Y[s]   = W_out A3[s] + b_out
+Loss: L = (1/B) sum_b w_b sum_s ||Y_b[s] - T_b[s]||^2.
+
+Weight vector layout (the C ABI's): W_in (H x K), b_in (H), then for l = 1..3
+W_self_l (H x H), W_nb_l (H x H), b_l (H), then W_out (K x H), b_out (K), all
+row-major.
+
+Pinned by central finite differences of the loss (tests/test_oracle_gnn.py);
+parity unpinned against the paper, which has no such network.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_LAYERS = 3
+
+
+def n_weights(K: int, H: int = 64) -> int:
+    return H * K + H + N_LAYERS * (2 * H * H + H) + K * H + K
+
+
+def unpack(w: np.ndarray, K: int, H: int = 64):
+    w = np.asarray(w, dtype=np.float64)
+    o = 0
+
+    def take(n, shape):
+        nonlocal o
+        v = w[o:o + n].reshape(shape)
+        o += n
+        return v
+    P = {"W_in": take(H * K, (H, K)), "b_in": take(H, (H,))}
+    for l in range(N_LAYERS):
+        P[f"W_self{l}"] = take(H * H, (H, H))
+        P[f"W_nb{l}"] = take(H * H, (H, H))
+        P[f"b{l}"] = take(H, (H,))
+    P["W_out"] = take(K * H, (K, H))
+    P["b_out"] = take(K, (K,))
+    assert o == w.size
+    return P
+
+
+def forward(w, X, nbrs, K: int, H: int = 64):
+    """X: (B, n_nodes, K); nbrs: list of neighbour index arrays.  Returns Y (B, n, K)."""
+    P = unpack(w, K, H)
+    A = np.maximum(X @ P["W_in"].T + P["b_in"], 0.0)
+    for l in range(N_LAYERS):
+        agg = np.stack([A[:, nb, :].mean(axis=1) if len(nb) else np.zeros_like(A[:, 0, :])
+                        for nb in nbrs], axis=1)
+        A = np.maximum(A @ P[f"W_self{l}"].T + agg @ P[f"W_nb{l}"].T + P[f"b{l}"], 0.0)
+    return A @ P["W_out"].T + P["b_out"]
+
+
+def loss(w, X, T, wb, nbrs, K: int, H: int = 64) -> float:
+    Y = forward(w, X, nbrs, K, H)
+    per = ((Y - T) ** 2).sum(axis=(1, 2))
+    return float((np.asarray(wb) * per).sum() / X.shape[0])
+
+
+def fd_gradient(w, X, T, wb, nbrs, K: int, idx, H: int = 64, eps: float = 1e-6):
+    """Central differences of the loss w.r.t. the weights at indices idx."""
+    w = np.asarray(w, dtype=np.float64).copy()
+    g = np.zeros(len(idx))
+    for n, i in enumerate(idx):
+        old = w[i]
+        w[i] = old + eps
+        lp = loss(w, X, T, wb, nbrs, K, H)
+        w[i] = old - eps
+        lm = loss(w, X, T, wb, nbrs, K, H)
+        w[i] = old
+        g[n] = (lp - lm) / (2 * eps)
+    return g

@@ -25,7 +25,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_BREAKD
 FP64, FP32, MIXED = 0, 1, 2
 PLACE_CELL, PLACE_ENDPOINT = 0, 1
 SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN = 0, 1, 2
-PREC_NONE, PREC_BLOCK_JACOBI = 0, 1
+PREC_NONE, PREC_BLOCK_JACOBI, PREC_BJ_GNN = 0, 1, 2
 MAX_LEVELS = 12
 MAX_ROWSETS = 16
 N_STAGES = 8
@@ -67,6 +67,18 @@ class SolveOpts(C.Structure):
                 ("gram_shift", C.c_double)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("cfg", Config), ("n_sets", C.c_int), ("sets", C.c_void_p), ("n_eval", C.c_int64),
+                ("eval_points", C.c_void_p), ("eval_out", C.c_void_p), ("eval_ref", C.c_void_p),
+                ("coeffs_out", C.c_void_p)]
+
+
+class BatchResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("rel_l2", C.c_double),
+                ("e_l1", C.c_double), ("max_abs", C.c_double), ("total_ms", C.c_double),
+                ("launches", C.c_int64)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_norm", C.c_double),
                 ("normal_residual_norm", C.c_double), ("setup_ms", C.c_double),
@@ -98,6 +110,15 @@ _SIGNATURES = {
     "elmfb_error_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                             C.c_void_p]),
     "elmfb_compute_gram": (C.c_int, [C.c_void_p]),
+    "elmfb_batch_solve": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "elmfb_gnn_num_weights": (C.c_int64, [C.c_void_p]),
+    "elmfb_gnn_graph": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "elmfb_gnn_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "elmfb_gnn_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "elmfb_gnn_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "elmfb_gnn_train": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                  C.c_uint64, C.c_void_p]),
     "elmfb_get_gram": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
 }
 
@@ -147,6 +168,86 @@ def default_solve_opts(**kw) -> SolveOpts:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def make_config(dim, lo, hi, levels, delta, features, seed=0, weight_scale=1.0, precision=FP64,
+                placement=PLACE_CELL) -> Config:
+    cfg = Config()
+    cfg.dim = dim
+    for i in range(dim):
+        cfg.lo[i] = float(lo[i])
+        cfg.hi[i] = float(hi[i])
+    if len(levels) > MAX_LEVELS:
+        raise ValueError("too many levels")
+    cfg.n_levels = len(levels)
+    for i, n in enumerate(levels):
+        cfg.levels[i] = int(n)
+    cfg.delta = float(delta)
+    cfg.placement = int(placement)
+    cfg.features = int(features)
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.weight_scale = float(weight_scale)
+    cfg.precision = int(precision)
+    return cfg
+
+
+def config_of(problem, precision=FP64) -> Config:
+    place = PLACE_CELL if problem.placement == "cell" else PLACE_ENDPOINT
+    return make_config(problem.dim, problem.lo, problem.hi, problem.levels, problem.delta,
+                       problem.features, problem.seed, problem.weight_scale, precision, place)
+
+
+def _rowsets(problem, keep):
+    arr = (RowSet * (1 + len(problem.boundary)))()
+    for i, rs in enumerate([problem.interior] + list(problem.boundary)):
+        pts = np.ascontiguousarray(rs.points, dtype=np.float64)
+        rhs = np.ascontiguousarray(rs.rhs, dtype=np.float64)
+        keep += [pts, rhs]
+        arr[i].n = pts.shape[0]
+        arr[i].points = pts.ctypes.data
+        arr[i].rhs = rhs.ctypes.data
+        arr[i].c0 = float(rs.c0)
+        for k in range(problem.dim):
+            arr[i].c1[k] = float(rs.c1[k])
+            arr[i].c2[k] = float(rs.c2[k])
+        arr[i].weight = float(rs.weight or 0.0)
+    keep.append(arr)
+    return arr
+
+
+def batch_solve(problems, precision=FP32, n_workers=8, opts=None, evaluate=True, coeffs=False):
+    """Solve independent problems with elmfb_batch_solve.
+
+    Returns (results, u_hat list, coefficient list)."""
+    n = len(problems)
+    items = (BatchItem * n)()
+    keep = []
+    outs, cos = [], []
+    for i, P in enumerate(problems):
+        items[i].cfg = config_of(P, precision)
+        sets = _rowsets(P, keep)
+        items[i].n_sets = len(sets)
+        items[i].sets = C.cast(sets, C.c_void_p)
+        if evaluate:
+            X = np.ascontiguousarray(P.test_points, dtype=np.float64)
+            ref = np.ascontiguousarray(P.exact(P.test_points), dtype=np.float64)
+            out = np.zeros(X.shape[0])
+            keep += [X, ref]
+            items[i].n_eval = X.shape[0]
+            items[i].eval_points = X.ctypes.data
+            items[i].eval_out = out.ctypes.data
+            items[i].eval_ref = ref.ctypes.data
+            outs.append(out)
+        if coeffs:
+            a = np.zeros(P.n_columns)
+            items[i].coeffs_out = a.ctypes.data
+            cos.append(a)
+    res = (BatchResult * n)()
+    o = opts if opts is not None else default_solve_opts()
+    rc = lib().elmfb_batch_solve(n, items, C.byref(o), n_workers, res)
+    if rc not in (OK, ERR_NOT_CONVERGED):
+        raise ElmfbError(rc, "batch solve failed")
+    return list(res), outs, cos
 
 
 class Solver:
@@ -298,6 +399,50 @@ class Solver:
         K = self.sizes().features
         out = np.zeros((ij.shape[0], K, K))
         _check(self.h, lib().elmfb_get_gram(self.h, ij.shape[0], ij.ctypes.data, out.ctypes.data))
+        return out
+
+    # -- learned preconditioner ------------------------------------------------
+    def gnn_graph(self):
+        s = self.sizes()
+        ne = C.c_int64()
+        _check(self.h, lib().elmfb_gnn_graph(self.h, None, None, C.byref(ne)))
+        off = np.zeros(s.n_subdomains + 1, dtype=np.int32)
+        nb = np.zeros(max(ne.value, 1), dtype=np.int32)
+        _check(self.h, lib().elmfb_gnn_graph(self.h, off.ctypes.data, nb.ctypes.data, None))
+        return [nb[off[i]:off[i + 1]].copy() for i in range(s.n_subdomains)]
+
+    def gnn_num_weights(self) -> int:
+        return int(lib().elmfb_gnn_num_weights(self.h))
+
+    def gnn_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(self.h, lib().elmfb_gnn_set_weights(self.h, w.ctypes.data))
+
+    def gnn_get_weights(self):
+        w = np.zeros(self.gnn_num_weights(), dtype=np.float32)
+        _check(self.h, lib().elmfb_gnn_get_weights(self.h, w.ctypes.data))
+        return w
+
+    def gnn_eval(self, x, t=None, wb=None, grad=False):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        B = x.shape[0]
+        y = np.zeros_like(x)
+        g = np.zeros(self.gnn_num_weights(), dtype=np.float32) if grad else None
+        loss = C.c_double(0.0)
+        tp = np.ascontiguousarray(t, dtype=np.float32) if t is not None else None
+        wp = np.ascontiguousarray(wb, dtype=np.float32) if wb is not None else None
+        _check(self.h, lib().elmfb_gnn_eval(self.h, B, x.ctypes.data,
+                                            tp.ctypes.data if tp is not None else None,
+                                            wp.ctypes.data if wp is not None else None,
+                                            y.ctypes.data, g.ctypes.data if g is not None else None,
+                                            C.byref(loss)))
+        return y, g, loss.value
+
+    def gnn_train(self, rhs_list, solve_iters=30, epochs=20, lr=1e-3, seed=0):
+        R = np.ascontiguousarray(np.asarray(rhs_list, dtype=np.float64))
+        out = np.zeros(2)
+        _check(self.h, lib().elmfb_gnn_train(self.h, R.shape[0], R.ctypes.data, solve_iters,
+                                             epochs, lr, seed, out.ctypes.data))
         return out
 
     def kernel_launches(self) -> int:

@@ -47,7 +47,6 @@ namespace {
 constexpr float kPiF = 3.14159265358979323846f;
 constexpr double kPiD = 3.14159265358979323846;
 
-__constant__ RowClass c_cls[kMaxClasses];
 
 // ------------------------------------------------------------------ K0 ------
 __global__ void k_cell_of_rows(const double* __restrict__ pts, int64_t n, int dim,
@@ -107,7 +106,8 @@ __global__ void k_sort_cells(const int* __restrict__ count, const int* __restric
   }
 }
 
-__global__ void k_gather_rows(const int* __restrict__ sorted, int64_t NR, int dim,
+__global__ void k_gather_rows(const RowClass* __restrict__ c_cls, const int* __restrict__ sorted,
+                              int64_t NR, int dim,
                               const double* __restrict__ pts, const double* __restrict__ rhs,
                               const int* __restrict__ cls_user, const int* __restrict__ row_cell,
                               double* __restrict__ x, int* __restrict__ rcls,
@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(128) k_assemble(
     const int* __restrict__ cell_level_off, const int* __restrict__ cell_count,
     const int* __restrict__ cell_pstart, const int64_t* __restrict__ panel_off,
     const double* __restrict__ xs, const int* __restrict__ rcls,
+    const RowClass* __restrict__ c_cls,
     const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels,
     __nv_bfloat16* __restrict__ pt, int64_t NPR) {
   extern __shared__ __nv_bfloat16 tsm[];   // WRITE_T: per warp [K][32]
@@ -368,14 +369,16 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
           h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
-          h->d_rcls.as<int>(), W, B, (T*)h->d_panels.p, h->d_pt.as<__nv_bfloat16>(), h->NPR); \
+          h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p,             \
+          h->d_pt.as<__nv_bfloat16>(), h->NPR);                                              \
     else                                                                                     \
       k_assemble<T, F, false><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(               \
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
           h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
-          h->d_rcls.as<int>(), W, B, (T*)h->d_panels.p, nullptr, h->NPR);                    \
+          h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
+          h->NPR);                                                                           \
     break;
   // algorithmic bytes: every panel entry written once (twice in mixed precision:
   // FP32 row-major and BF16 feature-major), point data read once
@@ -455,8 +458,9 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
     rc.hscale = s;
     h->cls[b] = rc;
   }
-  CUDA_CHECK(cudaMemcpyToSymbolAsync(c_cls, h->cls, sizeof(RowClass) * n_sets, 0,
-                                     cudaMemcpyHostToDevice, st));
+  h->d_cls.alloc(sizeof(RowClass) * kMaxClasses, st);
+  CUDA_CHECK(cudaMemcpyAsync(h->d_cls.p, h->cls, sizeof(RowClass) * n_sets,
+                             cudaMemcpyHostToDevice, st));
 
   stage_begin(h, 7);
   stage_begin(h, 1);
@@ -597,7 +601,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   k_fill_cell_of_R<<<nc, 128, 0, st>>>(h->d_cell_pstart.as<int>(), nc, cell_of_R);
   check_launch("k_fill_cell_of_R");
   k_gather_rows<<<(unsigned)ceil_div(NR, 256), 256, 0, st>>>(
-      h->d_sorted.as<int>(), NR, dim, h->d_pts_user.as<double>(), h->d_rhs_user.as<double>(),
+      h->d_cls.as<RowClass>(), h->d_sorted.as<int>(), NR, dim, h->d_pts_user.as<double>(), h->d_rhs_user.as<double>(),
       h->d_cls_user.as<int>(), h->d_row_cell.as<int>(), h->d_x.as<double>(), h->d_rcls.as<int>(),
       h->d_h.as<double>(), h->d_grow_cell.as<int>(), user_to_sorted, cell_of_R);
   check_launch("k_gather_rows");
@@ -609,6 +613,9 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   h->d_panels.alloc(h->NPR * h->K * h->panel_elem(), st);
   h->gram_pair_ij.clear();
   h->have_gram = false;
+  h->gnn_off.clear();
+  h->gnn_nb.clear();
+  h->gnn_trained = false;
   if (h->cfg.precision == ELMFB_MIXED) {
     h->d_pt.alloc(h->NPR * h->K * 2, st);
     // padding tail of 16-row tiles is written by the kernel; clear once for safety

@@ -360,7 +360,8 @@ int elmfb_create(elmfb_t* out, const elmfb_config* cfg, void* cuda_stream) {
 void elmfb_destroy(elmfb_t h) {
   if (!h) return;
   cudaSetDevice(h->device);
-  cudaStreamSynchronize(h->stream);
+  cudaStream_t st = h->stream;
+  cudaStreamSynchronize(st);
   for (auto& s : h->st) {
     if (s.a) cudaEventDestroy(s.a);
     if (s.b) cudaEventDestroy(s.b);
@@ -370,8 +371,8 @@ void elmfb_destroy(elmfb_t h) {
     cudaEventDestroy(r.b);
   }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
-  delete h;  // DevBuf destructors free device memory
-  cudaDeviceSynchronize();
+  delete h;  // DevBuf destructors free device memory, ordered on the handle's stream
+  cudaStreamSynchronize(st);
 }
 
 const char* elmfb_last_error(elmfb_t h) { return h ? h->err.c_str() : "null handle"; }

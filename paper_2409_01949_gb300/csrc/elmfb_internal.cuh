@@ -135,6 +135,7 @@ struct elmfb_ctx {
   double gram_flops = 0.0;
 
   DevBuf d_pts_user, d_rhs_user, d_cls_user;  // user order
+  DevBuf d_cls;                                 // [kMaxClasses] RowClass table
   DevBuf d_row_cell, d_cell_count, d_cell_fill, d_cell_pstart;
   DevBuf d_sorted;      // [NR] user row of each sorted row (-1 = padding)
   DevBuf d_x;           // [NR*dim] coordinates (sorted order)
@@ -156,6 +157,11 @@ struct elmfb_ctx {
   int64_t gram_runs = 0;
   DevBuf d_gram_pairs, d_gram_runs, d_gram;        // d_gram: [pair][K][K] FP32
   bool have_gram = false;
+
+  // learned preconditioner: subdomain graph, weights, Adam moments, work buffers
+  std::vector<int> gnn_off, gnn_nb;
+  DevBuf d_gnn_off, d_gnn_nb, d_gnn_w, d_gnn_m, d_gnn_v, d_gnn_act, d_gnn_lp, d_gnn_dy;
+  bool gnn_trained = false;
 
   // solution
   DevBuf d_a;           // [NPhi] FP64
@@ -195,6 +201,27 @@ void gram_compute(elmfb_ctx* h);
 
 // solve (solve.cu)
 void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
+
+// Work plan of the fused pass: units (cell, row range, first partial) and, per
+// panel, the list of partial rows that sum to its part of M^T u'.
+struct FusedPlan {
+  DevBuf units, fo, fe, part;
+  int n_units = 0;
+  int threads = 0;
+};
+bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp);
+// mode 0: u' = M t - (alpha/beta) u (scal[0], scal[1]); mode 1: u' = h - M t.
+// Writes u', per-panel partials of M^T u' into fp.part and ||u'||^2 per unit.
+template <class T>
+void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double* scal,
+                  double* gpart);
+template <class T>
+void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
+void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials
+void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part);  // z = X^T X r
+
+// learned preconditioner (gnn.cu)
+void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
 
 // eval (eval.cu)
 void eval_model(elmfb_ctx* h, const double* xs, int64_t n, double* out);

@@ -147,16 +147,17 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 // cuTensorMapEncodeTiled from the driver, resolved at run time through the
 // runtime's entry-point query (the library does not link libcuda directly).
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // thread-safe one-time lookup (function-local static initialisation)
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                                cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
-      ELMFB_THROW(ELMFB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  if (!fn) ELMFB_THROW(ELMFB_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   return fn;
 }
 

@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(256) k_gram_diag_partial(const T* __restrict__
 // column-major.  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
 __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ partial,
                                                      const int* __restrict__ chunk_off, int K,
-                                                     double shift, double* __restrict__ Xr,
+                                                     double shift, double abs_shift,
+                                                     double* __restrict__ Xr,
                                                      double* __restrict__ Xc,
                                                      int* __restrict__ flags,
                                                      double* __restrict__ gdiag_out) {
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ p
       }
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
-    const double add = eps * tr / K + (tr == 0.0 ? 1.0 : 0.0);
+    const double add = eps * tr / K + abs_shift + (tr == 0.0 && abs_shift == 0.0 ? 1.0 : 0.0);
     if (threadIdx.x == 0) fail = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < K; i += blockDim.x) G[i * K + i] += add;
@@ -641,13 +642,7 @@ struct SolveLayout {
   std::vector<int> pent_off, pent;
 };
 
-// Work plan of the fused pass: units (cell, row range, first partial) and, per
-// panel, the list of partial rows that sum to its part of M^T u'.
-struct FusedPlan {
-  DevBuf units, fo, fe, part;
-  int n_units = 0;
-  int threads = 0;
-};
+}  // namespace
 
 bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   const int K = h->K;
@@ -718,7 +713,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
 }
 
 template <class T>
-void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity) {
+void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift) {
   cudaStream_t st = h->stream;
   const int K = h->K;
   const int64_t KK = (int64_t)K * K;
@@ -767,7 +762,8 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity) {
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
   k_block_chol<<<h->n_sub, 256, csm, st>>>(h->d_gpart.as<double>(), dcoff.as<int>(), K, shift,
-                                           h->d_R.as<double>(), h->d_R.as<double>() + h->n_sub * KK,
+                                           abs_shift, h->d_R.as<double>(),
+                                           h->d_R.as<double>() + h->n_sub * KK,
                                            h->d_flags.as<int>(), nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
@@ -777,6 +773,8 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity) {
   CUDA_CHECK(cudaStreamSynchronize(st));
   if (flags[1]) ELMFB_THROW(ELMFB_ERR_BREAKDOWN, "block Cholesky failed after shift increases");
 }
+
+namespace {
 
 template <class T>
 void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
@@ -1114,10 +1112,24 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   const int K = h->K;
   const int64_t N = h->NPhi;
   const int64_t KK = (int64_t)K * K;
-  stage_begin(h, 4);
-  block_jacobi_setup<T>(h, o->shift, false);
-  stage_end(h, 4);
   if (!h->have_gram) gram_compute(h);
+  const int64_t np_ = h->n_gram_pairs;
+  // mu as a fraction of the mean Gram diagonal (host estimate from the diagonal blocks)
+  double mu = 0.0;
+  if (o->gram_shift > 0.0) {
+    std::vector<float> blk(K * K);
+    double tr = 0.0;
+    for (int64_t p = 0; p < np_; ++p)
+      if (h->gram_pair_ij[p].first == h->gram_pair_ij[p].second) {
+        CUDA_CHECK(cudaMemcpy(blk.data(), h->d_gram.as<float>() + p * KK, KK * sizeof(float),
+                              cudaMemcpyDeviceToHost));
+        for (int k = 0; k < K; ++k) tr += blk[k * K + k];
+      }
+    mu = o->gram_shift * tr / (double)N;
+  }
+  stage_begin(h, 4);
+  block_jacobi_setup<T>(h, o->shift, false, mu);
+  stage_end(h, 4);
   info->setup_ms = h->stage_ms[4] + h->stage_ms[3];
   FusedPlan fp;
   if (!build_fused_plan(h, fp))
@@ -1167,19 +1179,6 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   double* sc = dsc.as<double>();
   const double* Xr = h->d_R.as<double>();
   const double* Xc = h->d_R.as<double>() + h->n_sub * KK;
-  // mu as a fraction of the mean Gram diagonal (host estimate from the diagonal blocks)
-  double mu = 0.0;
-  if (o->gram_shift > 0.0) {
-    std::vector<float> blk(K * K);
-    double tr = 0.0;
-    for (int64_t p = 0; p < np; ++p)
-      if (pij[p].x == pij[p].y) {
-        CUDA_CHECK(cudaMemcpy(blk.data(), h->d_gram.as<float>() + p * KK, KK * sizeof(float),
-                              cudaMemcpyDeviceToHost));
-        for (int k = 0; k < K; ++k) tr += blk[k * K + k];
-      }
-    mu = o->gram_shift * tr / (double)N;
-  }
   const int vb = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
   const int pb = std::min(std::max(32, ((K + 31) / 32) * 32), 256);
   const size_t fsz = 16;   // unused scalar slots of the fused kernel (mode 1 reads none)
@@ -1239,10 +1238,37 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
     pcg_solve<float>(h, o, info);
     return;
   }
+  if (o->method == ELMFB_SOLVE_FCG_GNN) {
+    fcg_solve(h, o, info);
+    return;
+  }
   if (o->method != ELMFB_SOLVE_LSQR)
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "solver method not available in this build");
   if (o->preconditioner != ELMFB_PREC_NONE && o->preconditioner != ELMFB_PREC_BLOCK_JACOBI)
-    ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "unknown preconditioner");
+    ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "LSQR takes no or block-Jacobi preconditioning");
   if (h->fp64()) lsqr<double>(h, o, info);
   else lsqr<float>(h, o, info);
+}
+
+template void launch_fused<float>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*);
+template void launch_fused<double>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*);
+template void block_jacobi_setup<float>(elmfb_ctx*, double, bool, double);
+template void block_jacobi_setup<double>(elmfb_ctx*, double, bool, double);
+
+void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g) {
+  const int pb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 256);
+  k_panel_sum<<<h->n_sub, pb, 0, h->stream>>>(fp.part.as<double>(), fp.fo.as<int>(),
+                                               fp.fe.as<int>(), h->K, g);
+  check_launch("k_panel_sum");
+  count_launch(h);
+}
+
+void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part) {
+  const int K = h->K;
+  const int64_t KK = (int64_t)K * K;
+  const int pb = std::min(std::max(32, ((K + 31) / 32) * 32), 256);
+  k_bj_apply<<<h->n_sub, pb, 2 * K * sizeof(double), h->stream>>>(
+      h->d_R.as<double>(), h->d_R.as<double>() + h->n_sub * KK, K, r, z, dot_part);
+  check_launch("k_bj_apply");
+  count_launch(h);
 }

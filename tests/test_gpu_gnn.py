@@ -1,0 +1,125 @@
+"""Learned preconditioner (graph network) and flexible CG (not in the paper).
+
+* the GPU network's forward pass and hand-written gradients against the
+  oracle's FP64 definition (oracle/gnn.py) with central finite differences,
+  on the subdomain graph derived by the oracle from its own M;
+* a network whose output layer is zero leaves FCG identical to block-Jacobi
+  FCG (the correction is exactly zero);
+* training on pairs from the method's own solves lowers the loss, and the
+  iterations FCG needs with and without the trained network are reported;
+* FCG's solution error against the paper protocol.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_2409_01949_gb300 as E
+import workloads as WL
+from oracle import gnn as OG
+from oracle import system as OS
+
+pytestmark = pytest.mark.gpu
+
+
+def _small():
+    return WL.poisson2d(levels=(1, 2, 3), features=8, n_side=20, n_boundary_side=10)
+
+
+def _oracle_graph(P):
+    M = OS.assemble(P, fmt="dense")["M"]
+    K = P.features
+    nz = np.abs(M).reshape(M.shape[0], P.n_subdomains, K).max(axis=2) > 0
+    share = (nz.T.astype(np.int64) @ nz.astype(np.int64)) > 0
+    return [np.array([t for t in range(P.n_subdomains) if t != s and share[s, t]])
+            for s in range(P.n_subdomains)]
+
+
+def test_gnn_forward_and_gradient_match_oracle():
+    P = _small()
+    K, H = P.features, 64
+    nbrs = _oracle_graph(P)
+    rng = np.random.default_rng(0)
+    w = (0.3 * rng.standard_normal(OG.n_weights(K, H))).astype(np.float32)
+    B = 2
+    X = rng.standard_normal((B, P.n_subdomains, K)).astype(np.float32)
+    T = rng.standard_normal((B, P.n_subdomains, K)).astype(np.float32)
+    wb = np.array([1.0, 0.5], dtype=np.float32)
+    with E.Solver.from_problem(P, precision=E.FP32) as s:
+        s.assemble_problem(P)
+        g_graph = s.gnn_graph()
+        assert all(np.array_equal(a, b) for a, b in zip(g_graph, nbrs))
+        s.gnn_set_weights(w)
+        Y, grad, loss = s.gnn_eval(X, T, wb, grad=True)
+    Yo = OG.forward(w.astype(np.float64), X.astype(np.float64), nbrs, K, H)
+    assert np.allclose(Y, Yo, rtol=1e-4, atol=1e-4 * np.abs(Yo).max())
+    Lo = OG.loss(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64), wb, nbrs, K, H)
+    assert loss == pytest.approx(Lo, rel=1e-4)
+    idx = np.unique(np.concatenate([rng.choice(w.size, 150, replace=False),
+                                    [0, w.size - 1, H * K, H * K + H]]))
+    gfd = OG.fd_gradient(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64), wb,
+                         nbrs, K, idx, H)
+    scale = max(np.abs(gfd).max(), 1e-12)
+    assert np.allclose(grad[idx], gfd, rtol=2e-3, atol=2e-3 * scale)
+
+
+def _fcg(P, prec, precond, iters, tol=0.0, weights=None, train=None):
+    with E.Solver.from_problem(P, precision=prec) as s:
+        s.assemble_problem(P)
+        if weights is not None:
+            s.gnn_set_weights(weights)
+        loss = None
+        if train is not None:
+            loss = s.gnn_train(*train)
+        info = s.solve(method=E.SOLVE_FCG_GNN, preconditioner=precond, max_iter=iters, btol=tol,
+                       shift=1e-10)
+        a = s.coeffs()
+        err = s.error_norms(s.eval(P.test_points), P.exact(P.test_points))["rel_l2"]
+    return info, a, err, loss
+
+
+def test_zero_network_equals_block_jacobi_fcg():
+    P = _small()
+    with E.Solver.from_problem(P) as s:
+        s.assemble_problem(P)
+        nw = s.gnn_num_weights()
+    w = np.random.default_rng(3).standard_normal(nw).astype(np.float32)
+    w[-(P.features * 64 + P.features):] = 0.0        # output layer and bias: correction = 0
+    i1, a1, e1, _ = _fcg(P, E.FP32, E.PREC_BLOCK_JACOBI, 25)
+    i2, a2, e2, _ = _fcg(P, E.FP32, E.PREC_BJ_GNN, 25, weights=w)
+    assert i1.iterations == i2.iterations == 25
+    assert np.array_equal(a1, a2)
+
+
+def _rhs_rows(P, seed):
+    """Right-hand side values (row order of assemble) of another manufactured solution."""
+    modes = WL.random_sine_modes(seed, n_modes=4, kmax=6)
+    Q = WL.poisson2d(levels=P.levels, features=P.features,
+                     n_side=int(round(math.sqrt(P.interior.points.shape[0]))),
+                     n_boundary_side=P.boundary[0].points.shape[0] // 4, modes=modes)
+    return np.concatenate([Q.interior.rhs, Q.boundary[0].rhs])
+
+
+def test_training_lowers_loss_and_reports_gain():
+    P = WL.poisson2d(levels=(1, 2, 4), features=32, n_side=40, n_boundary_side=40)
+    rhs = np.stack([_rhs_rows(P, s) for s in range(1, 5)])
+    tol = 1e-6
+    i_bj, _, e_bj, _ = _fcg(P, E.FP32, E.PREC_BLOCK_JACOBI, 400, tol)
+    i_gnn, _, e_gnn, loss = _fcg(P, E.FP32, E.PREC_BJ_GNN, 400, tol,
+                                 train=(rhs, 25, 30, 1e-3, 0))
+    print(f"training loss {loss[0]:.4f} -> {loss[1]:.4f}; FCG iterations to ||r||/||g|| <= {tol}: "
+          f"block-Jacobi {i_bj.iterations} (rel L2 {e_bj:.2e}), with the network "
+          f"{i_gnn.iterations} (rel L2 {e_gnn:.2e})")
+    assert loss[1] < loss[0]
+
+
+def test_fcg_block_jacobi_matches_paper_protocol_error():
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "oracle_errors.json")))["poisson2d_L1-4_K64_N60"]
+    P = WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60, n_boundary_side=60)
+    info, a, err, _ = _fcg(P, E.FP32, E.PREC_BLOCK_JACOBI, 3000, 1e-12)
+    print(f"FCG block-Jacobi rel L2 {err:.3e} after {info.iterations} its; "
+          f"oracle LSQR-15000 {g['lsqr']['rel_l2']:.3e}")
+    assert err <= 1.01 * g["lsqr"]["rel_l2"]

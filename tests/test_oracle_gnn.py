@@ -1,0 +1,55 @@
+"""Pins of the oracle's graph network (the learned preconditioner's definition).
+
+The network is not in the paper; it is pinned to mathematics: special cases
+with closed-form outputs (zero weights give the output bias; identical node
+inputs give identical outputs under mean aggregation) and central finite
+differences checked against a directional derivative of the loss.
+"""
+import numpy as np
+
+from oracle import gnn as G
+
+
+def _setup(seed=0, B=2, n=5, K=6, H=4):
+    rng = np.random.default_rng(seed)
+    w = 0.5 * rng.standard_normal(G.n_weights(K, H))
+    X = rng.standard_normal((B, n, K))
+    T = rng.standard_normal((B, n, K))
+    nbrs = [np.array([1, 2]), np.array([0]), np.array([0, 3]), np.array([2, 4]), np.array([3])]
+    return w, X, T, np.array([1.0, 0.5]), nbrs, K, H
+
+
+def test_weight_count_and_layout():
+    K, H = 7, 4
+    n = G.n_weights(K, H)
+    assert n == H * K + H + 3 * (2 * H * H + H) + K * H + K
+    P = G.unpack(np.arange(n, dtype=float), K, H)
+    assert P["W_in"][0, 0] == 0 and P["b_out"][-1] == n - 1
+
+
+def test_zero_weights_output_bias():
+    w, X, T, wb, nbrs, K, H = _setup()
+    w0 = np.zeros_like(w)
+    P = G.unpack(w0, K, H)
+    P["b_out"][:] = np.arange(K)       # view into w0
+    Y = G.forward(w0, X, nbrs, K, H)
+    assert np.allclose(Y, np.arange(K))
+
+
+def test_mean_aggregation_of_constant_features():
+    """All nodes equal: aggregation returns the same vector, so every node's output is equal."""
+    w, X, T, wb, nbrs, K, H = _setup()
+    Xc = np.repeat(X[:, :1, :], X.shape[1], axis=1)
+    Y = G.forward(w, Xc, nbrs, K, H)
+    assert np.allclose(Y, Y[:, :1, :])
+
+
+def test_fd_gradient_consistent_with_directional_derivative():
+    w, X, T, wb, nbrs, K, H = _setup(1)
+    idx = np.arange(0, G.n_weights(K, H), 7)
+    g = G.fd_gradient(w, X, T, wb, nbrs, K, idx, H)
+    d = np.zeros_like(w)
+    d[idx] = np.random.default_rng(2).standard_normal(idx.size)
+    e = 1e-5
+    dd = (G.loss(w + e * d, X, T, wb, nbrs, K, H) - G.loss(w - e * d, X, T, wb, nbrs, K, H)) / (2 * e)
+    assert abs(dd - g @ d[idx]) <= 1e-5 * max(1.0, abs(dd))
