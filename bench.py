@@ -319,6 +319,45 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """All instances of the uneven batched workload through elmfb_batch_solve."""
+    import torch
+
+    import paper_2409_01949_gb300 as E
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    specs = WL.batch_specs(args.batch_n, 0)
+    probs = [WL.batch_instance(sp, i, 0) for i, sp in enumerate(specs)]
+    opts = E.default_solve_opts(max_iter=args.batch_iters, atol=0.0, btol=0.0, shift=1e-10,
+                                check_every=args.batch_iters)
+    for _ in range(args.warmup):
+        E.batch_solve(probs[:16], precision=E.FP32, n_workers=args.batch_workers, opts=opts)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res, _, _ = E.batch_solve(probs, precision=E.FP32, n_workers=args.batch_workers, opts=opts)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    errs = np.array([r.rel_l2 for r in res])
+    line = {"metric": "batched time-to-solution (s) for all instances", "value": round(dt, 4),
+            "unit": "s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batch{args.batch_n}_uneven_poisson2d",
+                       "instances": len(probs), "rows": int(sum(P.n_rows for P in probs)),
+                       "columns": int(sum(P.n_columns for P in probs)),
+                       "solver": f"LSQR + block-Jacobi, {args.batch_iters} iterations each",
+                       "workers": args.batch_workers},
+            "instances_per_s": round(len(probs) / dt, 2),
+            "rel_l2": {"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
+                       "max": float(errs.max())},
+            "gpu_launches": int(sum(r.launches for r in res)),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(P, args):
     """The FP64 oracle as it stands on a bounded sample, projected to the full paper protocol."""
     from oracle import lstsq as OL
@@ -377,7 +416,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="poisson2d_ml", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="poisson2d_ml", choices=list(WORKLOADS) + ["batch"])
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--target", default="paper", choices=["paper", "qr", "none"])
     ap.add_argument("--calib-start", type=int, default=10)
@@ -388,7 +427,13 @@ def main():
     ap.add_argument("--cpu-row-stride", type=int, default=40)
     ap.add_argument("--cpu-lsqr-its", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--batch-iters", type=int, default=300)
+    ap.add_argument("--batch-workers", type=int, default=8)
     args = ap.parse_args()
+    if args.workload == "batch":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

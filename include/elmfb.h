@@ -156,8 +156,7 @@ typedef struct {
  * multilevel_domain_decomp).  Replaces any previous system of the handle.
  *   n_sets  1 .. ELMFB_MAX_ROWSETS; sets[0] is the interior set
  * Errors: INVALID_ARG (empty interior set, points outside the box, bad sizes),
- * UNSUPPORTED (a cell of the refinement holds more than 16384 points), OOM,
- * CUDA.  Blocks until the assembly has finished on the handle's stream. */
+ * UNSUPPORTED (2^31 or more rows or padded panel rows), OOM, CUDA.  Blocks until the assembly has finished on the handle's stream. */
 int elmfb_assemble(elmfb_t h, int n_sets, const elmfb_rowset* sets);
 
 /* Sizes of the handle's problem. */
@@ -295,6 +294,7 @@ typedef struct {
   double rel_l2, e_l1, max_abs;   /* NaN without eval_ref                */
   double total_ms;                /* host wall time of the instance      */
   int64_t launches;               /* kernels launched for the instance   */
+  char message[160];              /* the instance's last error text, or "" */
 } elmfb_batch_result;
 int elmfb_batch_solve(int n, const elmfb_batch_item* items, const elmfb_solve_opts* opts,
                       int n_workers, elmfb_batch_result* results);

@@ -76,7 +76,7 @@ class BatchItem(C.Structure):
 class BatchResult(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("rel_l2", C.c_double),
                 ("e_l1", C.c_double), ("max_abs", C.c_double), ("total_ms", C.c_double),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("message", C.c_char * 160)]
 
 
 class SolveInfo(C.Structure):
@@ -246,7 +246,9 @@ def batch_solve(problems, precision=FP32, n_workers=8, opts=None, evaluate=True,
     o = opts if opts is not None else default_solve_opts()
     rc = lib().elmfb_batch_solve(n, items, C.byref(o), n_workers, res)
     if rc not in (OK, ERR_NOT_CONVERGED):
-        raise ElmfbError(rc, "batch solve failed")
+        bad = [(i, r.status, r.message.decode(errors="replace")) for i, r in enumerate(res)
+               if r.status not in (OK, ERR_NOT_CONVERGED)]
+        raise ElmfbError(rc, f"batch solve failed: {len(bad)} instance(s), first {bad[:3]}")
     return list(res), outs, cos
 
 

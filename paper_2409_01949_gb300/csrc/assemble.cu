@@ -78,32 +78,102 @@ __global__ void k_cell_of_rows(const double* __restrict__ pts, int64_t n, int di
   atomicAdd(&count[cell], 1);
 }
 
-__global__ void k_scatter_rows(const int* __restrict__ row_cell, int64_t n,
-                               const int* __restrict__ cell_pstart, int* __restrict__ fill,
-                               int* __restrict__ sorted) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int c = row_cell[r];
-  int slot = atomicAdd(&fill[c], 1);
-  sorted[cell_pstart[c] + slot] = (int)r;
+// Stable LSD radix sort of the rows by cell id (8-bit digits), so rows of a
+// cell are ordered by their user index whatever the launch schedule; then
+// k_place_rows writes them into the padded cell layout.  A tile of kSortTile
+// rows is handled by one CTA: k_radix_hist counts its digits, k_radix_scan
+// turns the digit-major table into output offsets, k_radix_scatter moves the
+// tile 256 rows at a time, ranking equal digits by warp match and per-warp
+// counts so equal keys keep their order.
+constexpr int kSortTile = 4096;
+constexpr int kSortThreads = 256;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const int* __restrict__ keys,
+                                                             int64_t n, int shift,
+                                                             int* __restrict__ hist,
+                                                             int n_tiles) {
+  __shared__ int cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
+  const int64_t t1 = t0 + kSortTile < n ? t0 + kSortTile : n;
+  for (int64_t i = t0 + threadIdx.x; i < t1; i += kSortThreads)
+    atomicAdd(&cnt[(keys[i] >> shift) & 255], 1);
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// One CTA per cell: order the cell's rows by their user index (rank sort in
-// shared memory), so the layout does not depend on atomic arrival order.
-__global__ void k_sort_cells(const int* __restrict__ count, const int* __restrict__ cell_pstart,
-                             int* __restrict__ sorted) {
-  extern __shared__ int sh[];
-  int c = blockIdx.x;
-  int n = count[c];
-  if (n <= 1) return;
-  int* seg = sorted + cell_pstart[c];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sh[i] = seg[i];
+// exclusive scan of m ints in place, one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) k_radix_scan(int* __restrict__ a, int64_t m) {
+  __shared__ int part[1024];
+  const int64_t per = (m + 1023) / 1024;
+  const int64_t b0 = threadIdx.x * per;
+  const int64_t b1 = b0 + per < m ? b0 + per : m;
+  int sum = 0;
+  for (int64_t i = b0; i < b1; ++i) sum += a[i];
+  part[threadIdx.x] = sum;
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int v = sh[i], rank = 0;
-    for (int j = 0; j < n; ++j) rank += sh[j] < v;
-    seg[rank] = v;
+  for (int o = 1; o < 1024; o <<= 1) {
+    int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
   }
+  int run = part[threadIdx.x] - sum;
+  for (int64_t i = b0; i < b1; ++i) {
+    int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const int* __restrict__ keys_in, const int* __restrict__ vals_in, int64_t n, int shift,
+    const int* __restrict__ offs, int n_tiles, int* __restrict__ keys_out,
+    int* __restrict__ vals_out) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ int running[256];
+  __shared__ int wcount[W][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  running[threadIdx.x] = offs[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
+  const int64_t t1 = t0 + kSortTile < n ? t0 + kSortTile : n;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t c0 = t0; c0 < t1; c0 += kSortThreads) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) wcount[q][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = c0 + threadIdx.x;
+    const bool valid = i < t1;
+    const int key = valid ? keys_in[i] : 0;
+    const int val = valid ? (vals_in ? vals_in[i] : (int)i) : 0;
+    const int d = valid ? (key >> shift) & 255 : 256 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) wcount[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int pos = running[d] + rank;
+      for (int q = 0; q < w; ++q) pos += wcount[q][d];
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+    int add = 0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) add += wcount[q][threadIdx.x];
+    running[threadIdx.x] += add;
+  }
+}
+
+// sorted[cell_pstart[c] + j] = j-th row of cell c (keys sorted, ustart = unpadded starts)
+__global__ void k_place_rows(const int* __restrict__ keys, const int* __restrict__ vals,
+                             int64_t n, const int* __restrict__ ustart,
+                             const int* __restrict__ cell_pstart, int* __restrict__ sorted) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = keys[i];
+  sorted[cell_pstart[c] + (i - ustart[c])] = vals[i];
 }
 
 __global__ void k_gather_rows(const RowClass* __restrict__ c_cls, const int* __restrict__ sorted,
@@ -489,9 +559,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   const int nc = h->n_cells;
   h->d_row_cell.alloc(n * sizeof(int), st);
   h->d_cell_count.alloc(nc * sizeof(int), st);
-  h->d_cell_fill.alloc(nc * sizeof(int), st);
   CUDA_CHECK(cudaMemsetAsync(h->d_cell_count.p, 0, nc * sizeof(int), st));
-  CUDA_CHECK(cudaMemsetAsync(h->d_cell_fill.p, 0, nc * sizeof(int), st));
   CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
   k_cell_of_rows<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
       h->d_pts_user.as<double>(), n, dim, h->d_bnd.as<double>(), h->nc[0], h->nc[1], h->cfg.lo[0],
@@ -509,14 +577,10 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
 
   // host: padded cell layout, panel offsets, tiles
   h->cell_pstart.assign(nc + 1, 0);
-  int max_count = 0;
   for (int c = 0; c < nc; ++c) {
     int cnt = h->cell_count[c];
-    max_count = std::max(max_count, cnt);
     h->cell_pstart[c + 1] = h->cell_pstart[c] + (int)ceil_div(cnt, kCellPad) * kCellPad;
   }
-  if (max_count > kMaxCellPoints)
-    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "a cell holds more than 16384 collocation points");
   h->NR = h->cell_pstart[nc];
   const int ne = (int)h->cover_sub.size();
   h->cover_start.assign(ne, 0);
@@ -577,19 +641,42 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   const int64_t NR = h->NR;
   h->d_sorted.alloc(NR * sizeof(int), st);
   CUDA_CHECK(cudaMemsetAsync(h->d_sorted.p, 0xff, NR * sizeof(int), st));
-  k_scatter_rows<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
-      h->d_row_cell.as<int>(), n, h->d_cell_pstart.as<int>(), h->d_cell_fill.as<int>(),
-      h->d_sorted.as<int>());
-  check_launch("k_scatter_rows");
-  const size_t sort_smem = std::max(max_count, 1) * sizeof(int);
-  if (sort_smem > 48 * 1024)
-    CUDA_CHECK(cudaFuncSetAttribute(k_sort_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sort_smem));
-  prof_begin(h, KID_CELL_SORT, 8.0 * (double)NR);
-  k_sort_cells<<<nc, 256, sort_smem, st>>>(
-      h->d_cell_count.as<int>(), h->d_cell_pstart.as<int>(), h->d_sorted.as<int>());
-  prof_end(h, KID_CELL_SORT);
-  check_launch("k_sort_cells");
+  {
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < nc) ++bits;
+    const int passes = (bits + 7) / 8;
+    const int n_tiles = (int)ceil_div(n, kSortTile);
+    std::vector<int> ustart(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) ustart[c + 1] = ustart[c] + h->cell_count[c];
+    DevBuf ka, kb, va, vb, hist, dus;
+    ka.alloc(n * sizeof(int), st);
+    kb.alloc(n * sizeof(int), st);
+    va.alloc(n * sizeof(int), st);
+    vb.alloc(n * sizeof(int), st);
+    hist.alloc((size_t)n_tiles * 256 * sizeof(int), st);
+    up(dus, ustart.data(), (nc + 1) * sizeof(int));
+    prof_begin(h, KID_CELL_SORT, (16.0 * passes + 12.0) * (double)n + 4.0 * (double)NR);
+    const int* kin = h->d_row_cell.as<int>();
+    const int* vin = nullptr;
+    int* kout = ka.as<int>();
+    int* vout = va.as<int>();
+    for (int ps = 0; ps < passes; ++ps) {
+      k_radix_hist<<<n_tiles, kSortThreads, 0, st>>>(kin, n, 8 * ps, hist.as<int>(), n_tiles);
+      k_radix_scan<<<1, 1024, 0, st>>>(hist.as<int>(), (int64_t)n_tiles * 256);
+      k_radix_scatter<<<n_tiles, kSortThreads, 0, st>>>(kin, vin, n, 8 * ps, hist.as<int>(),
+                                                         n_tiles, kout, vout);
+      check_launch("k_radix_scatter");
+      kin = kout;
+      vin = vout;
+      kout = kout == ka.as<int>() ? kb.as<int>() : ka.as<int>();
+      vout = vout == va.as<int>() ? vb.as<int>() : va.as<int>();
+    }
+    k_place_rows<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
+        kin, vin, n, dus.as<int>(), h->d_cell_pstart.as<int>(), h->d_sorted.as<int>());
+    check_launch("k_place_rows");
+    prof_end(h, KID_CELL_SORT);
+    count_launch(h, 3 * passes + 1);
+  }
   h->d_grow_cell.alloc(NR * sizeof(int), st);
   h->d_x.alloc(NR * dim * sizeof(double), st);
   h->d_rcls.alloc(NR * sizeof(int), st);
@@ -605,7 +692,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
       h->d_cls_user.as<int>(), h->d_row_cell.as<int>(), h->d_x.as<double>(), h->d_rcls.as<int>(),
       h->d_h.as<double>(), h->d_grow_cell.as<int>(), user_to_sorted, cell_of_R);
   check_launch("k_gather_rows");
-  count_launch(h, 4);
+  count_launch(h, 2);
   stage_end(h, 1);
 
   // K1: panels

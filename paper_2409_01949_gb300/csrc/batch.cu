@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <thread>
 
 #include "elmfb_internal.cuh"
@@ -49,6 +50,7 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
       const auto t0 = std::chrono::steady_clock::now();
       elmfb_t h = nullptr;
       int rc = elmfb_create(&h, &it.cfg, st);
+      if (rc != ELMFB_OK) std::snprintf(res.message, sizeof(res.message), "create failed");
       if (rc == ELMFB_OK) rc = elmfb_assemble(h, it.n_sets, it.sets);
       elmfb_solve_info info{};
       if (rc == ELMFB_OK) {
@@ -70,6 +72,9 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
         }
       }
       if (h) {
+        if (rc != ELMFB_OK) {
+          std::snprintf(res.message, sizeof(res.message), "%s", elmfb_last_error(h));
+        }
         res.launches = elmfb_kernel_launches(h);
         elmfb_destroy(h);
       }

@@ -14,6 +14,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "elmfb_internal.cuh"
 
@@ -231,6 +234,18 @@ void upload(elmfb_ctx* h, DevBuf& b, const std::vector<T>& v) {
 }
 
 }  // namespace
+
+void ensure_dyn_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, func}];
+  if (bytes <= std::max<size_t>(cur, 48 * 1024)) return;  // 48 KB needs no opt-in
+  CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+}
 
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();

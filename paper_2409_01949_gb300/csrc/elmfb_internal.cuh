@@ -56,10 +56,8 @@ struct DevBuf {
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
-// Limits of one cell of the common refinement (points per cell) and of the
-// number of covering subdomains per cell.
+// Row padding of a cell of the common refinement and the row-class limit.
 constexpr int kCellPad = 16;            // cell row groups are padded to this multiple
-constexpr int kMaxCellPoints = 16384;   // per-cell sort limit
 constexpr int kMaxClasses = ELMFB_MAX_ROWSETS;
 
 // Row class (interior or boundary set): operator coefficients and row scale
@@ -136,7 +134,7 @@ struct elmfb_ctx {
 
   DevBuf d_pts_user, d_rhs_user, d_cls_user;  // user order
   DevBuf d_cls;                                 // [kMaxClasses] RowClass table
-  DevBuf d_row_cell, d_cell_count, d_cell_fill, d_cell_pstart;
+  DevBuf d_row_cell, d_cell_count, d_cell_pstart;
   DevBuf d_sorted;      // [NR] user row of each sorted row (-1 = padding)
   DevBuf d_x;           // [NR*dim] coordinates (sorted order)
   DevBuf d_rcls;        // [NR] class (sorted order; -1 padding)
@@ -236,3 +234,7 @@ void prof_harvest(elmfb_ctx* h);
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline void count_launch(elmfb_ctx* h, int n = 1) { h->launches += n; }
 void check_launch(const char* what);
+// Raise, never lower, a kernel's dynamic shared-memory limit on the current
+// device.  The attribute is process-wide, so handles solving concurrently in
+// other threads only ever see it grow.
+void ensure_dyn_smem(const void* func, size_t bytes);

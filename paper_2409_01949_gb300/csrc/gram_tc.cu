@@ -226,8 +226,7 @@ void gram_compute(elmfb_ctx* h) {
                                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     ELMFB_THROW(ELMFB_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-  CUDA_CHECK(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kGramSmem));
+  ensure_dyn_smem((const void*)k_gram_tc, kGramSmem);
   CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
   stage_begin(h, 3);
   // algorithmic work: 2 K^2 flops per shared row per pair; bytes: BF16 rows read once

@@ -19,9 +19,11 @@
 // Every reduction is a fixed-order two-stage sum, so results are bitwise
 // reproducible from run to run.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 
 #include "elmfb_internal.cuh"
+#include "sm100_ptx.cuh"
 
 namespace {
 
@@ -78,57 +80,91 @@ __device__ double block_partial_sum(const double* __restrict__ part, int n, doub
 }
 
 // ------------------------------------------------------------ Gram diag -----
-// partial sums of the upper triangle of P^T P over one chunk of panel rows
-template <class T, int NACC>
-__global__ void __launch_bounds__(256) k_gram_diag_partial(const T* __restrict__ panels, int K,
+// Partial sums of the upper triangle of P^T P over one chunk of panel rows.
+// Thread t owns the 4x4 tile (ti, tj), ti <= tj, of the Gram block: per row it
+// reads two float4 from shared memory and does 16 FMAs.  Products are summed
+// in FP32 over 16 rows, those sums Kahan-compensated in FP32 over the chunk,
+// and the result stored in FP64 (upper triangle, row-major, K(K+1)/2 values).
+template <class T>
+__global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__ panels, int K,
                                                             const int4* __restrict__ chunks,
                                                             double* __restrict__ partial) {
   extern __shared__ unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);   // [16][K]
+  T* sm = reinterpret_cast<T*>(smraw);   // [16][Kp]
   const int4 ch = chunks[blockIdx.x];     // (panel, row0, nrows, -)
-  const int KT = K * (K + 1) / 2;
-  int ij[NACC];   // (i << 16) | j, or -1
-  double acc[NACC];
-#pragma unroll
-  for (int a = 0; a < NACC; ++a) {
-    int idx = threadIdx.x + a * blockDim.x;
-    acc[a] = 0.0;
-    if (idx < KT) {
-      // row-major upper triangle: find (i, j), j >= i
-      int i = 0, rem = idx;
-      while (rem >= K - i) {
-        rem -= K - i;
-        ++i;
-      }
-      ij[a] = (i << 16) | (i + rem);
-    } else {
-      ij[a] = -1;
+  const int Kp = (K + 3) & ~3;
+  const int TT = Kp / 4;
+  const int ntiles = TT * (TT + 1) / 2;
+  int ti = -1, tj = -1;
+  if ((int)threadIdx.x < ntiles) {
+    int rem = threadIdx.x;
+    ti = 0;
+    while (rem >= TT - ti) {
+      rem -= TT - ti;
+      ++ti;
     }
+    tj = ti + rem;
   }
+  T acc[4][4], hi[4][4], lo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = T(0);
   const T* base = panels + (int64_t)ch.y * K;
   for (int r0 = 0; r0 < ch.z; r0 += 16) {
     const int nr = min(16, ch.z - r0);
     __syncthreads();
-    for (int t = threadIdx.x; t < 16 * K; t += blockDim.x) {
-      int r = t / K;
-      sm[t] = r < nr ? base[(int64_t)(r0 + r) * K + (t - r * K)] : T(0);
+    for (int t = threadIdx.x; t < 16 * Kp; t += blockDim.x) {
+      const int r = t / Kp, k = t - r * Kp;
+      sm[t] = (r < nr && k < K) ? base[(int64_t)(r0 + r) * K + k] : T(0);
     }
     __syncthreads();
+    if (ti < 0) continue;
 #pragma unroll
-    for (int a = 0; a < NACC; ++a) {
-      if (ij[a] < 0) continue;
-      const int i = ij[a] >> 16, j = ij[a] & 0xffff;
-      T s = 0;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
 #pragma unroll 4
-      for (int r = 0; r < 16; ++r) s += sm[r * K + i] * sm[r * K + j];
-      acc[a] += (double)s;
-    }
-  }
+    for (int r = 0; r < 16; ++r) {
+      T x[4], y[4];
 #pragma unroll
-  for (int a = 0; a < NACC; ++a) {
-    int idx = threadIdx.x + a * blockDim.x;
-    if (idx < KT) partial[(int64_t)blockIdx.x * KT + idx] = acc[a];
+      for (int a = 0; a < 4; ++a) {
+        x[a] = sm[r * Kp + 4 * ti + a];
+        y[a] = sm[r * Kp + 4 * tj + a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += x[a] * y[b];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (sizeof(T) == 8) {
+          hi[a][b] += acc[a][b];
+        } else {
+          const T yv = acc[a][b] - lo[a][b];
+          const T tv = hi[a][b] + yv;
+          lo[a][b] = (tv - hi[a][b]) - yv;
+          hi[a][b] = tv;
+        }
+      }
   }
+  if (ti < 0) return;
+  const int KT = K * (K + 1) / 2;
+  double* out = partial + (int64_t)blockIdx.x * KT;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * ti + a, j = 4 * tj + b;
+      if (i < K && j < K && j >= i) {
+        // row-major upper-triangle index of (i, j)
+        const int idx = i * K - i * (i - 1) / 2 + (j - i);
+        out[idx] = (double)hi[a][b] - (double)lo[a][b];
+      }
+    }
 }
 
 // One block per subdomain: sum the chunk partials, shift, Cholesky
@@ -234,25 +270,43 @@ __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ p
   }
 }
 
-// t_j = R_j^{-1} v_j = X_j^T v_j  (t_i = sum_{m>=i} X_mi v_m); identity if no preconditioner
-__global__ void k_precond(const double* __restrict__ Xr, const double* __restrict__ v, int K,
-                          double* __restrict__ t, int identity, double* __restrict__ scal) {
-  extern __shared__ double vs[];
+// t_j = R_j^{-1} v_j = X_j^T v_j per subdomain (t_i = sum_{m>=i} X_mi v_m; X_j lower
+// triangular, row-major; identity without a preconditioner).  The G
+// thread groups of the block split the inner sum into fixed slices, then one
+// pass adds the group sums in order (deterministic).  Block 0 commits the
+// staged LSQR scalars.
+__global__ void __launch_bounds__(1024) k_precond(const double* __restrict__ Xr,
+                                                  const double* __restrict__ v, int K,
+                                                  double* __restrict__ t, int identity,
+                                                  double* __restrict__ scal) {
+  extern __shared__ double psh[];   // vs[K] then part[G][K]
   const int s = blockIdx.x;
   if (s == 0 && threadIdx.x < kStage) scal[threadIdx.x] = scal[kStage + threadIdx.x];
   const double* vv = v + (int64_t)s * K;
+  if (identity) {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) t[(int64_t)s * K + i] = vv[i];
+    return;
+  }
+  double* vs = psh;
+  double* part = psh + K;
   for (int i = threadIdx.x; i < K; i += blockDim.x) vs[i] = vv[i];
   __syncthreads();
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
+  const int chunk = (K + G - 1) / G;
   const double* X = Xr + (int64_t)s * K * K;
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    double acc;
-    if (identity) {
-      acc = vs[i];
-    } else {
-      acc = 0.0;
-      for (int m = i; m < K; ++m) acc += X[m * K + i] * vs[m];
-    }
-    t[(int64_t)s * K + i] = acc;
+  if (g < G && i < K) {
+    double acc = 0.0;
+    const int m1 = min(K, (g + 1) * chunk);
+    for (int m = max(i, g * chunk); m < m1; ++m) acc += X[m * K + i] * vs[m];
+    part[g * K + i] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < G; ++q) acc += part[q * K + j];
+    t[(int64_t)s * K + j] = acc;
   }
 }
 
@@ -315,7 +369,6 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
                                                  const int* __restrict__ cell_count,
                                                  const int64_t* __restrict__ panel_off,
                                                  double* __restrict__ partial) {
-  extern __shared__ double us[];
   const int e = blockIdx.x;
   const int c = entry_cell[e];
   const int cnt = cell_count[c];
@@ -327,8 +380,7 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
     for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = 0.0;
     return;
   }
-  for (int p = threadIdx.x; p < cnt; p += blockDim.x) us[p] = u[R0 + p];
-  __syncthreads();
+  const double* us = u + R0;   // broadcast reads, cached
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
     if (sizeof(T) == 8) {
@@ -475,6 +527,181 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
   if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
 }
 
+// Same pass, pipelined through shared memory by bulk copies.  Chunks of
+// kPipeRows rows of every covering panel of the unit land in a ring of S
+// stages (lane w of warp 0 copies panel w's rows; one mbarrier per stage).  Iteration i of the loop
+//   - forms the per-panel dots of chunk i (FP32 or FP64 as the panels),
+//   - warp 0 sums them over the panels for chunk i-1 and forms
+//     u'_r = y_r - (alpha/beta) u_r (FP64, written to u),
+//   - all warps add P_w[r,:]^T u'_r of chunk i-2 into their partials,
+// with one barrier per iteration, after which the stage of chunk i-2 is
+// refilled.  FP64 work is confined to warp 0 (GB300's FP64 rate is a small
+// fraction of FP32).  Double-buffered dot and u' slots make the one barrier
+// sufficient: a slot is rewritten two iterations after it was filled, when
+// every reader has passed the barrier in between.  A wait that times out
+// raises flags[3].
+constexpr int kPipeRows = 4;
+constexpr int kPipeMaxStages = 8;
+
+// sum of 4 per-lane values over the warp; lane 8r holds the total of value r
+template <class T>
+__device__ __forceinline__ T warp_sum4(T v0, T v1, T v2, T v3, int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+  const T k0 = (b4 ? v2 : v0) + __shfl_xor_sync(0xffffffffu, b4 ? v0 : v2, 16);
+  const T k1 = (b4 ? v3 : v1) + __shfl_xor_sync(0xffffffffu, b4 ? v1 : v3, 16);
+  T k = (b3 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b3 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+template <class T, int FPL>
+__global__ void __launch_bounds__(1024, 1) k_fused_pipe(
+    const T* __restrict__ panels, const double* __restrict__ tvec, int K,
+    const int4* __restrict__ units, const int* __restrict__ cell_pstart,
+    const int* __restrict__ cell_count, const int* __restrict__ cover_off,
+    const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
+    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    double* __restrict__ u, const double* __restrict__ hvec, int mode,
+    double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
+    int* __restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char ring_raw[];
+  __shared__ __align__(8) uint64_t full[kPipeMaxStages];
+  __shared__ T sd[2][32][kPipeRows];
+  __shared__ T su[2][kPipeRows];
+  __shared__ double red[32];
+  T* ring = reinterpret_cast<T*>(ring_raw);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int4 un = units[blockIdx.x];
+  const int c = un.x;
+  const int m = cover_off[c + 1] - cover_off[c];
+  const int cnt = cell_count[c];
+  const int64_t R0 = cell_pstart[c];
+  const bool active = w < m;
+  const int s = cover_sub[cover_off[c] + (active ? w : 0)];
+  const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
+  const uint32_t copy_bytes = (uint32_t)(kPipeRows * K * sizeof(T));
+  const int nchunks = (un.z - un.y) / kPipeRows;
+  __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
+  if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; ++q) sm100::mbar_init(&full[q], 1);
+    sm100::fence_mbar_init();
+  }
+  __syncthreads();
+  // called by all lanes of warp 0: lane ww copies the chunk's rows of panel ww
+  auto issue = [&](int chunk) {
+    const int q = chunk % S;
+    if (lane == 0) sm100::mbar_arrive_expect_tx(&full[q], copy_bytes * (uint32_t)m);
+    __syncwarp();
+    if (lane < m)
+      sm100::bulk_load(ring + q * stage_elems + (int64_t)lane * kPipeRows * K,
+                       panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
+                       &full[q]);
+  };
+  if (w == 0)
+    for (int q = 0; q < S && q < nchunks; ++q) issue(q);
+  T tv[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) {
+    const int k = lane + 32 * j;
+    tv[j] = (active && k < K) ? (T)tvec[(int64_t)s * K + k] : T(0);
+  }
+  double coef = 0.0;
+  if (mode == 0) {
+    const double beta = scal[S_BETA];
+    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+  }
+  T ahi[FPL], alo[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) ahi[j] = alo[j] = T(0);
+  // warp 0, lane 8r + g: row r of a chunk, panel group g
+  const int yr = lane >> 3, yg = lane & 7;
+  double nrm = 0.0, uold = 0.0;
+  bool ok = true;
+  for (int i = 0; i < nchunks + 2; ++i) {
+    double unext = 0.0;
+    if (i < nchunks) {
+      if (w == 0 && yg == 0) {
+        const int p = un.y + i * kPipeRows + yr;
+        if (p < cnt) unext = mode == 0 ? u[R0 + p] : hvec[R0 + p];
+      }
+      if (!sm100::mbar_wait(&full[i % S], (i / S) & 1)) ok = false;
+      const T* sp = ring + (i % S) * stage_elems + (int64_t)w * kPipeRows * K;
+      T d[kPipeRows];
+#pragma unroll
+      for (int r = 0; r < kPipeRows; ++r) {
+        d[r] = T(0);
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+          const int k = lane + 32 * j;
+          d[r] += (active && k < K ? sp[r * K + k] : T(0)) * tv[j];
+        }
+      }
+      const T tot = warp_sum4(d[0], d[1], d[2], d[3], lane);
+      if (yg == 0) sd[i & 1][w][yr] = tot;
+    }
+    if (w == 0 && i >= 1 && i <= nchunks) {
+      const int b = (i - 1) & 1;
+      T part = T(0);
+      for (int q = yg; q < m; q += 8) part += sd[b][q][yr];
+      part += __shfl_xor_sync(0xffffffffu, part, 4);
+      part += __shfl_xor_sync(0xffffffffu, part, 2);
+      part += __shfl_xor_sync(0xffffffffu, part, 1);
+      if (yg == 0) {
+        const int p = un.y + (i - 1) * kPipeRows + yr;
+        double out = 0.0;
+        if (p < cnt) {
+          out = mode == 0 ? (double)part - coef * uold : uold - (double)part;
+          u[R0 + p] = out;
+          nrm += out * out;
+        }
+        su[b][yr] = (T)out;
+      }
+    }
+    if (i >= 2) {
+      const T* sp = ring + ((i - 2) % S) * stage_elems + (int64_t)w * kPipeRows * K;
+      const int b = i & 1;   // == (i - 2) & 1
+#pragma unroll
+      for (int r = 0; r < kPipeRows; ++r) {
+        const T ur = su[b][r];
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+          const int k = lane + 32 * j;
+          const T pvv = (active && k < K) ? sp[r * K + k] : T(0);
+          if (sizeof(T) == 8) {
+            ahi[j] += pvv * ur;
+          } else {
+            const T y = pvv * ur - alo[j];
+            const T t = ahi[j] + y;
+            alo[j] = (t - ahi[j]) - y;
+            ahi[j] = t;
+          }
+        }
+      }
+    }
+    uold = unext;
+    __syncthreads();
+    // every warp is past the update of chunk i-2: its stage can be refilled
+    if (w == 0 && i >= 2 && i - 2 + S < nchunks) {
+      sm100::fence_proxy_async_smem();
+      issue(i - 2 + S);
+    }
+  }
+  if (!ok && lane == 0) atomicOr(&flags[3], 1);
+  if (active) {
+    double* out = partial + (int64_t)(un.w + w) * K;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+      const int k = lane + 32 * j;
+      if (k < K) out[k] = (double)ahi[j] - (double)alo[j];
+    }
+  }
+  double tot = block_sum(w == 0 && yg == 0 ? nrm : 0.0, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+}
+
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the unit partials of panel j
 // (X_j = R_j^{-T}); several thread groups split the partial list of a panel.
 __global__ void __launch_bounds__(1024) k_panel_T2(
@@ -505,14 +732,24 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   }
   __syncthreads();
   const double* X = Xc + (int64_t)s * K * K;
+  if (!identity) {
+    // the groups split the sum over mm <= i into fixed slices
+    const int chunk = (K + G - 1) / G;
+    if (g < G && k < K) {
+      double acc = 0.0;
+      const int m1 = min(k + 1, (g + 1) * chunk);
+      for (int mm = g * chunk; mm < m1; ++mm) acc += X[mm * K + k] * zs[mm];
+      zsh[g * K + k] = acc;
+    }
+    __syncthreads();
+  }
   double nrm = 0.0;
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    double acc;
+    double acc = 0.0;
     if (identity) {
       acc = zs[i];
     } else {
-      acc = 0.0;
-      for (int mm = 0; mm <= i; ++mm) acc += X[mm * K + i] * zs[mm];
+      for (int q = 0; q < G; ++q) acc += zsh[q * K + i];
     }
     const double vold = init ? 0.0 : v[(int64_t)s * K + i];
     const double vn = acc - beta * vold;
@@ -695,6 +932,28 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
   const T* P = (const T*)h->d_panels.p;
   cudaStream_t st = h->stream;
   prof_begin(h, KID_FUSED, (double)h->NPR * K * sizeof(T) + 16.0 * h->NR + 8.0 * h->NPhi);
+  // bulk-copy ring: S stages of (covering panels x kPipeRows rows x K) elements
+  const int mmax = std::max(1, h->max_cover);
+  const size_t stage_bytes = (size_t)mmax * kPipeRows * K * sizeof(T);
+  const int S = (int)std::min<size_t>(kPipeMaxStages, (200 * 1024) / std::max<size_t>(stage_bytes, 1));
+  const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
+  // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
+  // ring needs two stages in use plus at least two in flight
+  if (S >= 4 && (K * sizeof(T)) % 16 == 0 && !(force_regs && force_regs[0] == '1')) {
+    const size_t smem = (size_t)S * stage_bytes;
+#define ELMFB_FT(F)                                                                            \
+  if (fpl == F) {                                                                              \
+    ensure_dyn_smem((const void*)k_fused_pipe<T, F>, smem);                                   \
+    k_fused_pipe<T, F><<<fp.n_units, fthreads, smem, st>>>(                                    \
+        P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
+        h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
+        h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
+        fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>());                           \
+  } else
+    ELMFB_FT(1) ELMFB_FT(2) ELMFB_FT(3) ELMFB_FT(4)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "fused path needs K <= 128");
+#undef ELMFB_FT
+  } else {
 #define ELMFB_FU(F, MT)                                                                      \
   if (fpl == F && fthreads <= MT) {                                                          \
     k_fused<T, F, MT><<<fp.n_units, fthreads, 0, st>>>(                                      \
@@ -708,6 +967,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
   ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "fused path needs K <= 128 and <= 32 covering panels");
 #undef ELMFB_FU4
 #undef ELMFB_FU
+  }
   prof_end(h, KID_FUSED);
   count_launch(h);
 }
@@ -738,26 +998,21 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   CUDA_CHECK(cudaMemcpyAsync(dcoff.p, chunk_off.data(), chunk_off.size() * sizeof(int),
                              cudaMemcpyHostToDevice, st));
   h->d_gpart.alloc(std::max<size_t>(chunks.size(), 1) * KT * sizeof(double), st);
-  const int nacc = (KT + 255) / 256;
-  const size_t smem = 16 * K * sizeof(T);
+  const int Kp4 = (K + 3) & ~3;
+  const int ntiles = (Kp4 / 4) * (Kp4 / 4 + 1) / 2;
+  const int gthreads = std::max(32, ((ntiles + 31) / 32) * 32);
+  const size_t smem = 16 * Kp4 * sizeof(T);
   if (!chunks.empty()) {
     prof_begin(h, KID_GRAM_DIAG,
                (double)h->NPR * K * sizeof(T) + (double)chunks.size() * KT * sizeof(double));
-#define ELMFB_GD(N)                                                                         \
-  if (nacc <= N) {                                                                          \
-    k_gram_diag_partial<T, N><<<(unsigned)chunks.size(), 256, smem, st>>>(                  \
-        (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>());               \
-  } else
-    ELMFB_GD(1) ELMFB_GD(2) ELMFB_GD(4) ELMFB_GD(8) ELMFB_GD(16) ELMFB_GD(33)
-    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "K too large for the diagonal Gram kernel");
-#undef ELMFB_GD
+    k_gram_diag_partial<T><<<(unsigned)chunks.size(), gthreads, smem, st>>>(
+        (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>());
     prof_end(h, KID_GRAM_DIAG);
     check_launch("k_gram_diag_partial");
     count_launch(h);
   }
   const size_t csm = (size_t)KK * sizeof(double);
-  CUDA_CHECK(cudaFuncSetAttribute(k_block_chol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)std::max<size_t>(csm, 48 * 1024)));
+  ensure_dyn_smem((const void*)k_block_chol, csm);
   CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
@@ -823,13 +1078,12 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const double* Xr = h->d_R.as<double>();
   const double* Xc = h->d_R.as<double>() + h->n_sub * KK;
   int pblock = std::min(std::max(32, ((K + 31) / 32) * 32), 256);
-  size_t emax = 0;
-  for (int c = 0; c < h->n_cells; ++c) emax = std::max<size_t>(emax, h->cell_count[c]);
-  const size_t esm = std::max<size_t>(emax, 1) * sizeof(double);
-  if (esm > 48 * 1024)
-    CUDA_CHECK(cudaFuncSetAttribute(k_entry_T<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)esm));
   const int upd_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
+  // k_precond: G groups of Kp threads split each X_j^T v_j sum
+  const int pc_Kp = (K + 31) & ~31;
+  const int pc_G = std::max(1, std::min(8, std::min(1024 / pc_Kp, K / 8)));
+  const int pc_threads = pc_G * pc_Kp;
+  const size_t pc_smem = (size_t)(K + pc_G * K) * sizeof(double);
 
   auto gather = [&](const double* t, int mode) {
     prof_begin(h, KID_GATHER, panel_bytes + 16.0 * h->NR + 8.0 * N);
@@ -842,7 +1096,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   };
   auto transpose_step = [&](int init) {
     prof_begin(h, KID_ENTRY_T, panel_bytes + 8.0 * h->NR + 8.0 * ne * K);
-    k_entry_T<T><<<ne, 128, esm, st>>>(P, h->d_u.as<double>(), K, h->d_entry_cell.as<int>(),
+    k_entry_T<T><<<ne, 128, 0, st>>>(P, h->d_u.as<double>(), K, h->d_entry_cell.as<int>(),
                                         h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),
                                         h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),
                                         h->d_panel_off.as<int64_t>(), h->d_partial.as<double>());
@@ -891,8 +1145,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     prof_end(h, KID_UPDATE);
   };
   if (fused && p2smem > 48 * 1024)
-    CUDA_CHECK(cudaFuncSetAttribute(k_panel_T2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)p2smem));
+    ensure_dyn_smem((const void*)k_panel_T2, p2smem);
 
   stage_begin(h, 5);
   // start: b = h (cold) or h - M a0 (warm start)
@@ -926,7 +1179,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     int batch = std::min(o->check_every, max_it - it);
     for (int b = 0; b < batch; ++b) {
       prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
-      k_precond<<<h->n_sub, pblock, K * sizeof(double), st>>>(Xr, h->d_v.as<double>(), K,
+      k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_v.as<double>(), K,
                                                                h->d_tmp.as<double>(), identity,
                                                                scal);
       prof_end(h, KID_PRECOND);
@@ -955,7 +1208,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     }
   }
   // a = (a0 +) P y
-  k_precond<<<h->n_sub, pblock, K * sizeof(double), st>>>(Xr, h->d_x_sol.as<double>(), K,
+  k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_x_sol.as<double>(), K,
                                                            h->d_tmp.as<double>(), identity, scal);
   if (o->warm_start)
     k_add_to<<<upd_blocks, 256, 0, st>>>(h->d_a.as<double>(), h->d_tmp.as<double>(), N);

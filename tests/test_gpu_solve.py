@@ -147,3 +147,22 @@ def test_fp32_panels_solution_vs_paper_protocol():
     print("fp64 / fp32 rel L2:", errs, "oracle LSQR-15000:", g["lsqr"]["rel_l2"])
     assert errs[E.FP64] <= 1.01 * g["lsqr"]["rel_l2"]
     assert errs[E.FP32] <= 1.01 * g["lsqr"]["rel_l2"]
+
+
+@pytest.mark.parametrize("prec", [E.FP32, E.FP64])
+@pytest.mark.parametrize("registers", ["0", "1"])
+def test_both_fused_pass_variants_meet_paper_protocol_error(prec, registers, monkeypatch):
+    """The fused LSQR pass has a shared-memory pipelined form (bulk copies,
+    FP32 sums of the per-panel dots for FP32 panels) and a register-load form
+    (the fallback when the ring does not fit); each meets the solution bar on
+    its own."""
+    g = _golden("poisson2d_L1-4_K64_N60")
+    P = WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60, n_boundary_side=60)
+    monkeypatch.setenv("ELMFB_FUSED_REGISTERS", registers)
+    with E.Solver.from_problem(P, precision=prec) as s:
+        s.assemble_problem(P)
+        info = s.solve(max_iter=4000, atol=1e-14, btol=1e-14, shift=1e-12)
+        err = s.error_norms(s.eval(P.test_points), P.exact(P.test_points))["rel_l2"]
+    print(f"registers={registers} prec={prec}: rel L2 {err:.3e} ({info.iterations} its); "
+          f"oracle LSQR-15000 {g['lsqr']['rel_l2']:.3e}")
+    assert err <= 1.01 * g["lsqr"]["rel_l2"]
