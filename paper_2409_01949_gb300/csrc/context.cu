@@ -241,10 +241,13 @@ void ensure_dyn_smem(const void* func, size_t bytes) {
   int dev = 0;
   CUDA_CHECK(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
+  // the default limit covers static plus dynamic memory, so opt in to at
+  // least 48 KB of dynamic memory whenever a kernel asks
+  const size_t want = std::max<size_t>(bytes, 48 * 1024);
   size_t& cur = limit[{dev, func}];
-  if (bytes <= std::max<size_t>(cur, 48 * 1024)) return;  // 48 KB needs no opt-in
-  CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  cur = bytes;
+  if (want <= cur) return;
+  CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want));
+  cur = want;
 }
 
 void check_launch(const char* what) {

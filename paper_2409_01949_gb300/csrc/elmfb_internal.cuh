@@ -204,15 +204,20 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
 // panel, the list of partial rows that sum to its part of M^T u'.
 struct FusedPlan {
   DevBuf units, fo, fe, part;
+  DevBuf tf;            // FP32 copy of t for FP32 panels
   int n_units = 0;
   int threads = 0;
+  bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
 };
 bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp);
 // mode 0: u' = M t - (alpha/beta) u (scal[0], scal[1]); mode 1: u' = h - M t.
-// Writes u', per-panel partials of M^T u' into fp.part and ||u'||^2 per unit.
+// Writes u', per-panel partials of M^T u' into fp.part (FP64 values for FP64
+// panels; compensated FP32 (hi, lo) pairs in the same 8 bytes for FP32
+// panels) and ||u'||^2 per unit.  tf: FP32 copy of t (FP32 panels), or null
+// to convert t here.
 template <class T>
 void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double* scal,
-                  double* gpart);
+                  double* gpart, const float* tf = nullptr);
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials

@@ -79,6 +79,28 @@ __device__ double block_partial_sum(const double* __restrict__ part, int n, doub
   return r;
 }
 
+// (s, c) += hi - lo in float-float arithmetic (TwoSum, then a fast
+// renormalisation; Dekker 1971 / Knuth TAOCP 4.2.2): FP32 pipes only, about
+// 2^-44 relative, used to sum compensated FP32 partials without FP64 work.
+__device__ __forceinline__ void ff_add(float& s, float& c, float hi, float lo) {
+  const float t = s + hi;
+  const float bp = t - s;
+  const float e = (s - (t - bp)) + (hi - bp);
+  c += e - lo;
+  s = t + c;
+  c = c - (s - t);
+}
+// FP32 (hi, lo) pair stored in the 8 bytes of partial idx
+__device__ __forceinline__ float2 partial_pair(const double* part, int64_t idx) {
+  return reinterpret_cast<const float2*>(part)[idx];
+}
+// FP32 copy of an FP64 vector (the fused pass's operand for FP32 panels)
+__global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 // ------------------------------------------------------------ Gram diag -----
 // Partial sums of the upper triangle of P^T P over one chunk of panel rows.
 // Thread t owns the 4x4 tile (ti, tj), ti <= tj, of the Gram block: per row it
@@ -167,9 +189,123 @@ __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__
     }
 }
 
+// Same partial sums with the rows staged by bulk copies: every chunk is a
+// whole number of 16-row groups of one panel (cells are padded to 16 rows),
+// so step q copies rows [16q, 16q + 16) of the chunk, contiguous in HBM, into
+// stage q % S of a ring (thread 0 issues; one mbarrier per stage), and the
+// stage is refilled after the barrier that ends its step.  Requires K
+// sizeof(T) to be a multiple of 16 bytes (rows stay 16-byte aligned) and
+// K % 4 == 0.  A wait that times out raises flags[3].
+constexpr int kDiagStages = 6;
+
+template <class T>
+__global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ panels, int K,
+                                                         const int4* __restrict__ chunks,
+                                                         double* __restrict__ partial,
+                                                         int* __restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* ring = reinterpret_cast<T*>(smraw);   // [kDiagStages][16][K]
+  __shared__ __align__(8) uint64_t full[kDiagStages];
+  const int4 ch = chunks[blockIdx.x];     // (panel, row0, nrows, -)
+  const int TT = K / 4;
+  const int ntiles = TT * (TT + 1) / 2;
+  int ti = -1, tj = -1;
+  if ((int)threadIdx.x < ntiles) {
+    int rem = threadIdx.x;
+    ti = 0;
+    while (rem >= TT - ti) {
+      rem -= TT - ti;
+      ++ti;
+    }
+    tj = ti + rem;
+  }
+  const int nsteps = ch.z / 16;
+  const uint32_t step_bytes = (uint32_t)(16 * K * sizeof(T));
+  const T* base = panels + (int64_t)ch.y * K;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kDiagStages; ++q) sm100::mbar_init(&full[q], 1);
+    sm100::fence_mbar_init();
+    for (int q = 0; q < kDiagStages && q < nsteps; ++q) {
+      sm100::mbar_arrive_expect_tx(&full[q], step_bytes);
+      sm100::bulk_load(ring + (int64_t)q * 16 * K, base + (int64_t)q * 16 * K, step_bytes,
+                       &full[q]);
+    }
+  }
+  __syncthreads();
+  T hi[4][4], lo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = T(0);
+  bool ok = true;
+  for (int q = 0; q < nsteps; ++q) {
+    const int st = q % kDiagStages;
+    if (!sm100::mbar_wait(&full[st], (q / kDiagStages) & 1)) ok = false;
+    const T* sm = ring + (int64_t)st * 16 * K;
+    if (ti >= 0) {
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 4
+      for (int r = 0; r < 16; ++r) {
+        T x[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          x[a] = sm[r * K + 4 * ti + a];
+          y[a] = sm[r * K + 4 * tj + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += x[a] * y[b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (sizeof(T) == 8) {
+            hi[a][b] += acc[a][b];
+          } else {
+            const T yv = acc[a][b] - lo[a][b];
+            const T tv = hi[a][b] + yv;
+            lo[a][b] = (tv - hi[a][b]) - yv;
+            hi[a][b] = tv;
+          }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + kDiagStages < nsteps) {
+      sm100::fence_proxy_async_smem();
+      sm100::mbar_arrive_expect_tx(&full[st], step_bytes);
+      sm100::bulk_load(ring + (int64_t)st * 16 * K, base + (int64_t)(q + kDiagStages) * 16 * K,
+                       step_bytes, &full[st]);
+    }
+  }
+  if (!ok) atomicOr(&flags[3], 1);
+  if (ti < 0) return;
+  const int KT = K * (K + 1) / 2;
+  double* out = partial + (int64_t)blockIdx.x * KT;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * ti + a, j = 4 * tj + b;
+      if (j >= i) {
+        const int idx = i * K - i * (i - 1) / 2 + (j - i);
+        out[idx] = (double)hi[a][b] - (double)lo[a][b];
+      }
+    }
+}
+
 // One block per subdomain: sum the chunk partials, shift, Cholesky
 // (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
 // column-major.  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
+// Right-looking factorisation with a 2-D split of the trailing update; the
+// inverse is formed in place in shared memory row by row (row i of X needs
+// row i of L and rows < i of X), two threads per column splitting each sum.
+// FP64 throughout: the blocks are as ill-conditioned as the shift allows.
 __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ partial,
                                                      const int* __restrict__ chunk_off, int K,
                                                      double shift, double abs_shift,
@@ -177,71 +313,73 @@ __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ p
                                                      double* __restrict__ Xc,
                                                      int* __restrict__ flags,
                                                      double* __restrict__ gdiag_out) {
-  extern __shared__ double G[];   // [K][K] lower used
+  extern __shared__ double G[];   // [K][K]
   __shared__ double red[32];
   __shared__ double diag0[128];
+  __shared__ double rpiv[128];    // 1 / L_kk
+  __shared__ double xrow[128];
   __shared__ int fail;
   const int s = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int KT = K * (K + 1) / 2;
   const int c0 = chunk_off[s], c1 = chunk_off[s + 1];
-  // assemble full symmetric G
-  for (int idx = threadIdx.x; idx < KT; idx += blockDim.x) {
+  // assemble the symmetric G from the upper-triangle partials
+  for (int idx = tid; idx < K * K; idx += nt) {
+    const int i = idx / K, j = idx - i * K;
+    if (j < i) continue;
+    const int pidx = i * K - i * (i - 1) / 2 + (j - i);
     double v = 0.0;
-    for (int c = c0; c < c1; ++c) v += partial[(int64_t)c * KT + idx];
-    int i = 0, rem = idx;
-    while (rem >= K - i) {
-      rem -= K - i;
-      ++i;
-    }
-    int j = i + rem;
+    for (int c = c0; c < c1; ++c) v += partial[(int64_t)c * KT + pidx];
     G[i * K + j] = v;
     G[j * K + i] = v;
   }
   __syncthreads();
   if (gdiag_out) {
-    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x)
-      gdiag_out[(int64_t)s * K * K + idx] = G[idx];
+    for (int idx = tid; idx < K * K; idx += nt) gdiag_out[(int64_t)s * K * K + idx] = G[idx];
   }
   double tr = 0.0;
   {
     double v = 0.0;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    for (int i = tid; i < K; i += nt) {
       v += G[i * K + i];
       diag0[i] = G[i * K + i];
     }
     tr = block_sum(v, red);
   }
+  // 2-D thread layout for the trailing update: 16 x (nt / 16)
+  const int tx = tid & 15, ty = tid >> 4, ny = nt >> 4;
   double eps = shift;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (attempt > 0) {
-      // restore the lower triangle from the (untouched) upper triangle
-      for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
-        int i = idx / K, j = idx % K;
+      // restore the lower triangle from the (untouched) strict upper triangle
+      for (int idx = tid; idx < K * K; idx += nt) {
+        const int i = idx / K, j = idx - i * K;
         if (i > j) G[i * K + j] = G[j * K + i];
         else if (i == j) G[i * K + i] = diag0[i];
       }
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
     const double add = eps * tr / K + abs_shift + (tr == 0.0 && abs_shift == 0.0 ? 1.0 : 0.0);
-    if (threadIdx.x == 0) fail = 0;
+    if (tid == 0) fail = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < K; i += blockDim.x) G[i * K + i] += add;
+    for (int i = tid; i < K; i += nt) G[i * K + i] += add;
     __syncthreads();
     for (int k = 0; k < K; ++k) {
-      if (threadIdx.x == 0) {
-        double d = G[k * K + k];
+      if (tid == 0) {
+        const double d = G[k * K + k];
         if (!(d > 0.0)) fail = 1;
-        G[k * K + k] = sqrt(d > 0.0 ? d : 1.0);
+        const double l = sqrt(d > 0.0 ? d : 1.0);
+        G[k * K + k] = l;
+        rpiv[k] = 1.0 / l;
       }
       __syncthreads();
       if (fail) break;
-      const double piv = G[k * K + k];
-      for (int i = k + 1 + threadIdx.x; i < K; i += blockDim.x) G[i * K + k] /= piv;
+      const double rp = rpiv[k];
+      for (int i = k + 1 + tid; i < K; i += nt) G[i * K + k] *= rp;
       __syncthreads();
-      const int m = K - k - 1;
-      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-        int i = k + 1 + idx / m, j = k + 1 + idx % m;
-        if (j <= i) G[i * K + j] -= G[i * K + k] * G[j * K + k];
+      for (int i = k + 1 + ty; i < K; i += ny) {
+        const double lik = G[i * K + k];
+        for (int j = k + 1 + tx; j <= i; j += 16) G[i * K + j] -= lik * G[j * K + k];
       }
       __syncthreads();
     }
@@ -249,42 +387,55 @@ __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ p
     if (!fail) break;
   }
   if (fail) {
-    if (threadIdx.x == 0) atomicOr(&flags[1], 1);
+    if (tid == 0) atomicOr(&flags[1], 1);
     return;
   }
-  // X = L^{-1}: thread per column j, forward substitution
+  // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
+  // Row i of L is read while row i of X is formed in xrow, then overwritten.
+  const int j = tid >> 1, half = tid & 1;
+  for (int i = 0; i < K; ++i) {
+    double acc = 0.0;
+    if (j < i) {
+      const int mid = j + (i - j + 1) / 2;
+      const int m0 = half ? mid : j, m1 = half ? i : mid;
+      for (int m = m0; m < m1; ++m) acc += G[i * K + m] * G[m * K + j];
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (half == 0 && j < i) xrow[j] = -acc * rpiv[i];
+    __syncthreads();
+    for (int q = tid; q <= i; q += nt) G[i * K + q] = q == i ? rpiv[i] : xrow[q];
+    __syncthreads();
+  }
   double* xr = Xr + (int64_t)s * K * K;
   double* xc = Xc + (int64_t)s * K * K;
-  for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    for (int i = 0; i < j; ++i) {
-      xr[i * K + j] = 0.0;
-      xc[j * K + i] = 0.0;
-    }
-    for (int i = j; i < K; ++i) {
-      double sum = i == j ? 1.0 : 0.0;
-      for (int m = j; m < i; ++m) sum -= G[i * K + m] * xr[m * K + j];
-      double v = sum / G[i * K + i];
-      xr[i * K + j] = v;   // X_ij row-major
-      xc[j * K + i] = v;   // X_ij column-major
-    }
+  for (int idx = tid; idx < K * K; idx += nt) {
+    const int i = idx / K, jj = idx - i * K;
+    const double v = jj <= i ? G[i * K + jj] : 0.0;
+    xr[idx] = v;                          // X_ij row-major
+    xc[(int64_t)jj * K + i] = v;          // X_ij column-major
   }
 }
 
 // t_j = R_j^{-1} v_j = X_j^T v_j per subdomain (t_i = sum_{m>=i} X_mi v_m; X_j lower
-// triangular, row-major; identity without a preconditioner).  The G
+// triangular, row-major; identity without a preconditioner); tf, if given,
+// receives an FP32 copy of t.  The G
 // thread groups of the block split the inner sum into fixed slices, then one
 // pass adds the group sums in order (deterministic).  Block 0 commits the
 // staged LSQR scalars.
 __global__ void __launch_bounds__(1024) k_precond(const double* __restrict__ Xr,
                                                   const double* __restrict__ v, int K,
                                                   double* __restrict__ t, int identity,
-                                                  double* __restrict__ scal) {
+                                                  double* __restrict__ scal,
+                                                  float* __restrict__ tf) {
   extern __shared__ double psh[];   // vs[K] then part[G][K]
   const int s = blockIdx.x;
   if (s == 0 && threadIdx.x < kStage) scal[threadIdx.x] = scal[kStage + threadIdx.x];
   const double* vv = v + (int64_t)s * K;
   if (identity) {
-    for (int i = threadIdx.x; i < K; i += blockDim.x) t[(int64_t)s * K + i] = vv[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      t[(int64_t)s * K + i] = vv[i];
+      if (tf) tf[(int64_t)s * K + i] = (float)vv[i];
+    }
     return;
   }
   double* vs = psh;
@@ -307,6 +458,7 @@ __global__ void __launch_bounds__(1024) k_precond(const double* __restrict__ Xr,
     double acc = 0.0;
     for (int q = 0; q < G; ++q) acc += part[q * K + j];
     t[(int64_t)s * K + j] = acc;
+    if (tf) tf[(int64_t)s * K + j] = (float)acc;
   }
 }
 
@@ -413,7 +565,7 @@ constexpr int kFusedRows = 8;
 
 template <class T, int FPL, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_fused(
-    const T* __restrict__ panels, const double* __restrict__ tvec, int K,
+    const T* __restrict__ panels, const T* __restrict__ tvec, int K,
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
     const int* __restrict__ cell_count, const int* __restrict__ cover_off,
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
@@ -437,10 +589,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
 #pragma unroll
   for (int j = 0; j < FPL; ++j) {
     const int k = lane + 32 * j;
-    tv[j] = (active && k < K) ? (T)tvec[(int64_t)s * K + k] : T(0);
+    tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : T(0);
   }
-  double coef = 0.0;
-  if (mode == 0) {
+  double coef = 0.0;   // used by warp 0 only (an FP64 division is costly)
+  if (mode == 0 && threadIdx.x < 32) {
     const double beta = scal[S_BETA];
     coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
   }
@@ -515,16 +667,23 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     uold = unext;
   }
   if (active) {
-    double* out = partial + (int64_t)(un.w + w) * K;
+    const int64_t base_idx = (int64_t)(un.w + w) * K;
 #pragma unroll
     for (int j = 0; j < FPL; ++j) {
       const int k = lane + 32 * j;
-      if (k < K) out[k] = (double)ahi[j] - (double)alo[j];
+      if (k >= K) continue;
+      if (sizeof(T) == 8)
+        partial[base_idx + k] = (double)ahi[j];
+      else
+        reinterpret_cast<float2*>(partial)[base_idx + k] =
+            make_float2((float)ahi[j], (float)alo[j]);
     }
   }
   // threads 0..7 of warp 0 hold the row norms
-  double tot = block_sum(threadIdx.x < kFusedRows ? nrm : 0.0, red);
-  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  if (threadIdx.x < 32) {   // the row norms live in warp 0
+    const double tot = warp_sum<double>(nrm);
+    if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  }
 }
 
 // Same pass, pipelined through shared memory by bulk copies.  Chunks of
@@ -535,13 +694,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
 //     u'_r = y_r - (alpha/beta) u_r (FP64, written to u),
 //   - all warps add P_w[r,:]^T u'_r of chunk i-2 into their partials,
 // with one barrier per iteration, after which the stage of chunk i-2 is
-// refilled.  FP64 work is confined to warp 0 (GB300's FP64 rate is a small
+// refilled.  The unit's u (or h) values arrive by one more bulk copy at the
+// start, so warp 0 never waits on a global load inside the loop.  Lane l
+// holds features k = l FPL + j, read from shared memory as one vector.  FP64 work is confined to warp 0 (GB300's FP64 rate is a small
 // fraction of FP32).  Double-buffered dot and u' slots make the one barrier
 // sufficient: a slot is rewritten two iterations after it was filled, when
 // every reader has passed the barrier in between.  A wait that times out
 // raises flags[3].
 constexpr int kPipeRows = 4;
 constexpr int kPipeMaxStages = 8;
+constexpr int kMaxUnitRows = 1024;   // rows of one unit (its u values are staged in smem)
 
 // sum of 4 per-lane values over the warp; lane 8r holds the total of value r
 template <class T>
@@ -556,9 +718,44 @@ __device__ __forceinline__ T warp_sum4(T v0, T v1, T v2, T v3, int lane) {
   return k;
 }
 
+// FPL consecutive elements p[0..FPL) into x (vector loads when the slice is
+// whole; zeros past rem elements otherwise).  p is aligned to the slice width.
+template <class T, int FPL>
+__device__ __forceinline__ void load_slice(const T* p, T (&x)[FPL], bool whole, int rem) {
+  if (whole) {
+    if constexpr (sizeof(T) * FPL == 16) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) x[j] = e[j];
+    } else if constexpr (sizeof(T) * FPL == 32) {
+      const float4 v0 = reinterpret_cast<const float4*>(p)[0];
+      const float4 v1 = reinterpret_cast<const float4*>(p)[1];
+      const T* e0 = reinterpret_cast<const T*>(&v0);
+      const T* e1 = reinterpret_cast<const T*>(&v1);
+#pragma unroll
+      for (int j = 0; j < FPL / 2; ++j) {
+        x[j] = e0[j];
+        x[j + FPL / 2] = e1[j];
+      }
+    } else if constexpr (sizeof(T) * FPL == 8) {
+      const float2 v = *reinterpret_cast<const float2*>(p);
+      const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) x[j] = e[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) x[j] = p[j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) x[j] = j < rem ? p[j] : T(0);
+  }
+}
+
 template <class T, int FPL>
 __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
-    const T* __restrict__ panels, const double* __restrict__ tvec, int K,
+    const T* __restrict__ panels, const T* __restrict__ tvec, int K,
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
     const int* __restrict__ cell_count, const int* __restrict__ cover_off,
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
@@ -568,48 +765,58 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];
+  __shared__ __align__(8) uint64_t ubar;
   __shared__ T sd[2][32][kPipeRows];
   __shared__ T su[2][kPipeRows];
-  __shared__ double red[32];
+  __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
   T* ring = reinterpret_cast<T*>(ring_raw);
+  const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
+  double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(T));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int4 un = units[blockIdx.x];
+  const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
   const int cnt = cell_count[c];
   const int64_t R0 = cell_pstart[c];
   const bool active = w < m;
   const int s = cover_sub[cover_off[c] + (active ? w : 0)];
-  const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
   const uint32_t copy_bytes = (uint32_t)(kPipeRows * K * sizeof(T));
-  const int nchunks = (un.z - un.y) / kPipeRows;
-  __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
+  const int nrows = un.z - un.y;
+  const int nchunks = nrows / kPipeRows;
   if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
   if (threadIdx.x == 0) {
     for (int q = 0; q < S; ++q) sm100::mbar_init(&full[q], 1);
+    sm100::mbar_init(&ubar, 1);
     sm100::fence_mbar_init();
+    // the unit's u (mode 0) or h (mode 1) values, read by warp 0 for u'
+    const uint32_t ub = (uint32_t)(nrows * sizeof(double));
+    sm100::mbar_arrive_expect_tx(&ubar, ub);
+    sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
   }
   __syncthreads();
   // called by all lanes of warp 0: lane ww copies the chunk's rows of panel ww
-  auto issue = [&](int chunk) {
-    const int q = chunk % S;
-    if (lane == 0) sm100::mbar_arrive_expect_tx(&full[q], copy_bytes * (uint32_t)m);
+  auto issue = [&](int chunk, int stage) {
+    if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
     __syncwarp();
     if (lane < m)
-      sm100::bulk_load(ring + q * stage_elems + (int64_t)lane * kPipeRows * K,
+      sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
                        panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
-                       &full[q]);
+                       &full[stage]);
   };
   if (w == 0)
-    for (int q = 0; q < S && q < nchunks; ++q) issue(q);
+    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+  // lane slice of the features: k = lane * FPL + j
+  const int k0 = lane * FPL;
+  const bool whole = k0 + FPL <= K;
+  const int rem = K - k0;
   T tv[FPL];
 #pragma unroll
   for (int j = 0; j < FPL; ++j) {
-    const int k = lane + 32 * j;
-    tv[j] = (active && k < K) ? (T)tvec[(int64_t)s * K + k] : T(0);
+    const int k = k0 + j;
+    tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : T(0);
   }
-  double coef = 0.0;
-  if (mode == 0) {
+  double coef = 0.0;   // used by warp 0 only (an FP64 division is costly)
+  if (mode == 0 && w == 0) {
     const double beta = scal[S_BETA];
     coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
   }
@@ -618,29 +825,28 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   for (int j = 0; j < FPL; ++j) ahi[j] = alo[j] = T(0);
   // warp 0, lane 8r + g: row r of a chunk, panel group g
   const int yr = lane >> 3, yg = lane & 7;
-  double nrm = 0.0, uold = 0.0;
+  double nrm = 0.0;
   bool ok = true;
+  if (w == 0 && !sm100::mbar_wait(&ubar, 0)) ok = false;
+  int st_i = 0, ph_i = 0;   // stage and phase parity of chunk i
+  int st_u = 0;             // stage of chunk i - 2
   for (int i = 0; i < nchunks + 2; ++i) {
-    double unext = 0.0;
     if (i < nchunks) {
-      if (w == 0 && yg == 0) {
-        const int p = un.y + i * kPipeRows + yr;
-        if (p < cnt) unext = mode == 0 ? u[R0 + p] : hvec[R0 + p];
-      }
-      if (!sm100::mbar_wait(&full[i % S], (i / S) & 1)) ok = false;
-      const T* sp = ring + (i % S) * stage_elems + (int64_t)w * kPipeRows * K;
-      T d[kPipeRows];
+      if (!sm100::mbar_wait(&full[st_i], ph_i)) ok = false;
+      if (active) {
+        const T* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
+        T d[kPipeRows];
 #pragma unroll
-      for (int r = 0; r < kPipeRows; ++r) {
-        d[r] = T(0);
+        for (int r = 0; r < kPipeRows; ++r) {
+          T x[FPL];
+          load_slice<T, FPL>(sp + r * K, x, whole, rem);
+          d[r] = T(0);
 #pragma unroll
-        for (int j = 0; j < FPL; ++j) {
-          const int k = lane + 32 * j;
-          d[r] += (active && k < K ? sp[r * K + k] : T(0)) * tv[j];
+          for (int j = 0; j < FPL; ++j) d[r] += x[j] * tv[j];
         }
+        const T tot = warp_sum4(d[0], d[1], d[2], d[3], lane);
+        if (yg == 0) sd[i & 1][w][yr] = tot;
       }
-      const T tot = warp_sum4(d[0], d[1], d[2], d[3], lane);
-      if (yg == 0) sd[i & 1][w][yr] = tot;
     }
     if (w == 0 && i >= 1 && i <= nchunks) {
       const int b = (i - 1) & 1;
@@ -650,56 +856,74 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
       part += __shfl_xor_sync(0xffffffffu, part, 2);
       part += __shfl_xor_sync(0xffffffffu, part, 1);
       if (yg == 0) {
-        const int p = un.y + (i - 1) * kPipeRows + yr;
+        const int pr = (i - 1) * kPipeRows + yr;   // row within the unit
         double out = 0.0;
-        if (p < cnt) {
-          out = mode == 0 ? (double)part - coef * uold : uold - (double)part;
-          u[R0 + p] = out;
+        if (un.y + pr < cnt) {
+          const double uo = us[pr];
+          out = mode == 0 ? (double)part - coef * uo : uo - (double)part;
+          u[R0 + un.y + pr] = out;
           nrm += out * out;
         }
         su[b][yr] = (T)out;
       }
     }
-    if (i >= 2) {
-      const T* sp = ring + ((i - 2) % S) * stage_elems + (int64_t)w * kPipeRows * K;
+    if (i >= 2 && active) {
+      const T* sp = ring + st_u * stage_elems + (int64_t)w * kPipeRows * K + k0;
       const int b = i & 1;   // == (i - 2) & 1
+      T acc[FPL];
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) acc[j] = T(0);
 #pragma unroll
       for (int r = 0; r < kPipeRows; ++r) {
         const T ur = su[b][r];
+        T x[FPL];
+        load_slice<T, FPL>(sp + r * K, x, whole, rem);
 #pragma unroll
-        for (int j = 0; j < FPL; ++j) {
-          const int k = lane + 32 * j;
-          const T pvv = (active && k < K) ? sp[r * K + k] : T(0);
-          if (sizeof(T) == 8) {
-            ahi[j] += pvv * ur;
-          } else {
-            const T y = pvv * ur - alo[j];
-            const T t = ahi[j] + y;
-            alo[j] = (t - ahi[j]) - y;
-            ahi[j] = t;
-          }
+        for (int j = 0; j < FPL; ++j) acc[j] += x[j] * ur;
+      }
+      // chunk sums added with compensation (FP32 panels)
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) {
+        if (sizeof(T) == 8) {
+          ahi[j] += acc[j];
+        } else {
+          const T y = acc[j] - alo[j];
+          const T t = ahi[j] + y;
+          alo[j] = (t - ahi[j]) - y;
+          ahi[j] = t;
         }
       }
     }
-    uold = unext;
     __syncthreads();
     // every warp is past the update of chunk i-2: its stage can be refilled
     if (w == 0 && i >= 2 && i - 2 + S < nchunks) {
       sm100::fence_proxy_async_smem();
-      issue(i - 2 + S);
+      issue(i - 2 + S, st_u);
+    }
+    if (i >= 2) st_u = st_u + 1 == S ? 0 : st_u + 1;
+    if (i < nchunks && ++st_i == S) {
+      st_i = 0;
+      ph_i ^= 1;
     }
   }
   if (!ok && lane == 0) atomicOr(&flags[3], 1);
   if (active) {
-    double* out = partial + (int64_t)(un.w + w) * K;
+    const int64_t base_idx = (int64_t)(un.w + w) * K;
 #pragma unroll
     for (int j = 0; j < FPL; ++j) {
-      const int k = lane + 32 * j;
-      if (k < K) out[k] = (double)ahi[j] - (double)alo[j];
+      const int k = k0 + j;
+      if (k >= K) continue;
+      if (sizeof(T) == 8)
+        partial[base_idx + k] = (double)ahi[j];
+      else
+        reinterpret_cast<float2*>(partial)[base_idx + k] =
+            make_float2((float)ahi[j], (float)alo[j]);
     }
   }
-  double tot = block_sum(w == 0 && yg == 0 ? nrm : 0.0, red);
-  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  if (threadIdx.x < 32) {   // the row norms live in warp 0
+    const double tot = warp_sum<double>(nrm);
+    if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  }
 }
 
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the unit partials of panel j
@@ -708,7 +932,8 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
     const double* __restrict__ partial, const int* __restrict__ pent_off,
     const int* __restrict__ pent, const double* __restrict__ Xc, int K,
     const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
-    double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial) {
+    double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial,
+    int pairs) {
   extern __shared__ double zsh[];   // [groups][K] then z[K]
   __shared__ double red[32];
   const int s = blockIdx.x;
@@ -720,7 +945,17 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
   if (g < G && k < K) {
     double z = 0.0;
-    for (int q = pent_off[s] + g; q < pent_off[s + 1]; q += G) z += partial[(int64_t)pent[q] * K + k];
+    if (pairs) {
+      float zs_hi = 0.f, zs_lo = 0.f;
+      for (int q = pent_off[s] + g; q < pent_off[s + 1]; q += G) {
+        const float2 pr = partial_pair(partial, (int64_t)pent[q] * K + k);
+        ff_add(zs_hi, zs_lo, pr.x, pr.y);
+      }
+      z = (double)zs_hi + (double)zs_lo;
+    } else {
+      for (int q = pent_off[s] + g; q < pent_off[s + 1]; q += G)
+        z += partial[(int64_t)pent[q] * K + k];
+    }
     zsh[g * K + k] = z;
   }
   __syncthreads();
@@ -886,7 +1121,8 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   if (h->max_cover > 32 || K > 128) return false;
   cudaStream_t st = h->stream;
   fp.threads = 32 * std::max(1, h->max_cover);
-  const int64_t target = std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7));
+  const int64_t target =
+      std::min<int64_t>(kMaxUnitRows, std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7)));
   std::vector<int4> units;
   std::vector<std::vector<int>> plist(h->n_sub);
   int pbase = 0;
@@ -914,6 +1150,8 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   fp.fo.alloc(fo.size() * sizeof(int), st);
   fp.fe.alloc(std::max<size_t>(fe.size(), 1) * sizeof(int), st);
   fp.part.alloc(std::max<int64_t>(pbase, 1) * K * sizeof(double), st);
+  fp.pairs = !h->fp64();
+  if (fp.pairs) fp.tf.alloc(std::max<int64_t>(h->NPhi, 1) * sizeof(float), st);
   CUDA_CHECK(cudaMemcpyAsync(fp.units.p, units.data(), units.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, st));
   CUDA_CHECK(cudaMemcpyAsync(fp.fo.p, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -924,23 +1162,36 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
 }
 
 template <class T>
-void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double* scal,
-                  double* gpart) {
+void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, double* scal,
+                  double* gpart, const float* tf) {
   const int K = h->K;
   const int fpl = (K + 31) / 32;
   const int fthreads = fp.threads;
   const T* P = (const T*)h->d_panels.p;
   cudaStream_t st = h->stream;
+  // the pass reads t in the panels' precision
+  const T* t = reinterpret_cast<const T*>(t64);
+  if (sizeof(T) == 4) {
+    if (!tf) {
+      k_to_float<<<(unsigned)std::min<int64_t>(ceil_div(h->NPhi, 256), 1216), 256, 0, st>>>(
+          t64, fp.tf.as<float>(), h->NPhi);
+      count_launch(h);
+      tf = fp.tf.as<float>();
+    }
+    t = reinterpret_cast<const T*>(tf);
+  }
   prof_begin(h, KID_FUSED, (double)h->NPR * K * sizeof(T) + 16.0 * h->NR + 8.0 * h->NPhi);
   // bulk-copy ring: S stages of (covering panels x kPipeRows rows x K) elements
   const int mmax = std::max(1, h->max_cover);
   const size_t stage_bytes = (size_t)mmax * kPipeRows * K * sizeof(T);
-  const int S = (int)std::min<size_t>(kPipeMaxStages, (200 * 1024) / std::max<size_t>(stage_bytes, 1));
+  const size_t u_bytes = kMaxUnitRows * sizeof(double);
+  const int S = (int)std::min<size_t>(kPipeMaxStages,
+                                      (200 * 1024 - u_bytes) / std::max<size_t>(stage_bytes, 1));
   const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
   // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
   // ring needs two stages in use plus at least two in flight
   if (S >= 4 && (K * sizeof(T)) % 16 == 0 && !(force_regs && force_regs[0] == '1')) {
-    const size_t smem = (size_t)S * stage_bytes;
+    const size_t smem = (size_t)S * stage_bytes + u_bytes;
 #define ELMFB_FT(F)                                                                            \
   if (fpl == F) {                                                                              \
     ensure_dyn_smem((const void*)k_fused_pipe<T, F>, smem);                                   \
@@ -972,6 +1223,10 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
   count_launch(h);
 }
 
+// rows per diagonal-Gram chunk: fewer, larger chunks keep the triangular
+// partials (K(K+1)/2 doubles per chunk) small next to the panel reads
+constexpr int kDiagChunk = 2048;
+
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift) {
   cudaStream_t st = h->stream;
@@ -980,13 +1235,14 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   h->d_R.alloc(2 * h->n_sub * KK * sizeof(double), st);
   if (identity) return;
   if (K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up supports K <= 128");
-  // chunks of at most 512 panel rows
+  // chunks of at most 2048 panel rows
   std::vector<int4> chunks;
   std::vector<int> chunk_off(h->n_sub + 1, 0);
   for (int s = 0; s < h->n_sub; ++s) {
     chunk_off[s] = (int)chunks.size();
-    for (int64_t r = h->panel_off[s]; r < h->panel_off[s + 1]; r += 512)
-      chunks.push_back(make_int4(s, (int)r, (int)std::min<int64_t>(512, h->panel_off[s + 1] - r), 0));
+    for (int64_t r = h->panel_off[s]; r < h->panel_off[s + 1]; r += kDiagChunk)
+      chunks.push_back(
+          make_int4(s, (int)r, (int)std::min<int64_t>(kDiagChunk, h->panel_off[s + 1] - r), 0));
   }
   chunk_off[h->n_sub] = (int)chunks.size();
   const int KT = K * (K + 1) / 2;
@@ -1002,18 +1258,26 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   const int ntiles = (Kp4 / 4) * (Kp4 / 4 + 1) / 2;
   const int gthreads = std::max(32, ((ntiles + 31) / 32) * 32);
   const size_t smem = 16 * Kp4 * sizeof(T);
+  CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
   if (!chunks.empty()) {
     prof_begin(h, KID_GRAM_DIAG,
                (double)h->NPR * K * sizeof(T) + (double)chunks.size() * KT * sizeof(double));
-    k_gram_diag_partial<T><<<(unsigned)chunks.size(), gthreads, smem, st>>>(
-        (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>());
+    if (K % 4 == 0 && (K * sizeof(T)) % 16 == 0) {
+      const size_t psmem = (size_t)kDiagStages * 16 * K * sizeof(T);
+      ensure_dyn_smem((const void*)k_gram_diag_pipe<T>, psmem);
+      k_gram_diag_pipe<T><<<(unsigned)chunks.size(), gthreads, psmem, st>>>(
+          (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>(),
+          h->d_flags.as<int>());
+    } else {
+      k_gram_diag_partial<T><<<(unsigned)chunks.size(), gthreads, smem, st>>>(
+          (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>());
+    }
     prof_end(h, KID_GRAM_DIAG);
     check_launch("k_gram_diag_partial");
     count_launch(h);
   }
   const size_t csm = (size_t)KK * sizeof(double);
   ensure_dyn_smem((const void*)k_block_chol, csm);
-  CUDA_CHECK(cudaMemsetAsync(h->d_flags.p, 0, 16 * sizeof(int), st));
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
   k_block_chol<<<h->n_sub, 256, csm, st>>>(h->d_gpart.as<double>(), dcoff.as<int>(), K, shift,
@@ -1026,6 +1290,7 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   int flags[4];
   CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaStreamSynchronize(st));
+  if (flags[3]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "diagonal Gram: a copy wait timed out");
   if (flags[1]) ELMFB_THROW(ELMFB_ERR_BREAKDOWN, "block Cholesky failed after shift increases");
 }
 
@@ -1129,15 +1394,15 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const int KpT = (K + 31) & ~31;
   const int tgroups = std::max(1, 1024 / KpT);
   const size_t p2smem = (size_t)(tgroups + 1) * K * sizeof(double);
-  auto fused_step = [&](const double* t, int mode) {
-    launch_fused<T>(h, fp, t, mode, scal, gpart);
+  auto fused_step = [&](const double* t, int mode, const float* tf = nullptr) {
+    launch_fused<T>(h, fp, t, mode, scal, gpart, tf);
   };
   auto fused_tail = [&](int init) {
     prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
                                    (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
     k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
         dfpart.as<double>(), dfo.as<int>(), dfe.as<int>(), Xc, K, gpart, n_units,
-        h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart);
+        h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N);
     k_update<<<upd_blocks, 256, 0, st>>>(scal, vpart, h->n_sub, h->d_v.as<double>(),
@@ -1179,12 +1444,12 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     int batch = std::min(o->check_every, max_it - it);
     for (int b = 0; b < batch; ++b) {
       prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
-      k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_v.as<double>(), K,
-                                                               h->d_tmp.as<double>(), identity,
-                                                               scal);
+      k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
+          Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal,
+          fused && fp.pairs ? fp.tf.as<float>() : nullptr);
       prof_end(h, KID_PRECOND);
       if (fused) {
-        fused_step(h->d_tmp.as<double>(), 0);
+        fused_step(h->d_tmp.as<double>(), 0, fp.pairs ? fp.tf.as<float>() : nullptr);
         fused_tail(0);
       } else {
         gather(h->d_tmp.as<double>(), 0);
@@ -1196,7 +1461,10 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
                                st));
+    int dflags[4];
+    CUDA_CHECK(cudaMemcpyAsync(dflags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
+    if (dflags[3]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "fused LSQR pass: a copy wait timed out");
     if (sc[S_BAD] != 0.0) ELMFB_THROW(ELMFB_ERR_NONFINITE, "non-finite LSQR scalar");
     const double anorm = std::sqrt(sc[S_ANORM2]);
     const double rn = sc[S_RNORM], arn = sc[S_ARNORM];
@@ -1209,7 +1477,8 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   }
   // a = (a0 +) P y
   k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_x_sol.as<double>(), K,
-                                                           h->d_tmp.as<double>(), identity, scal);
+                                                    h->d_tmp.as<double>(), identity, scal,
+                                                    nullptr);
   if (o->warm_start)
     k_add_to<<<upd_blocks, 256, 0, st>>>(h->d_a.as<double>(), h->d_tmp.as<double>(), N);
   else
@@ -1318,14 +1587,25 @@ __global__ void k_bj_apply(const double* __restrict__ Xr, const double* __restri
 
 // g_s = sum of the fused pass partials of panel s (M^T u' unscaled)
 __global__ void k_panel_sum(const double* __restrict__ partial, const int* __restrict__ pent_off,
-                            const int* __restrict__ pent, int K, double* __restrict__ g) {
+                            const int* __restrict__ pent, int K, double* __restrict__ g,
+                            int pairs) {
   const int s = blockIdx.x;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
-    for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) acc += partial[(int64_t)pent[q] * K + k];
+    if (pairs) {
+      float hi = 0.f, lo = 0.f;
+      for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) {
+        const float2 pr = partial_pair(partial, (int64_t)pent[q] * K + k);
+        ff_add(hi, lo, pr.x, pr.y);
+      }
+      acc = (double)hi + (double)lo;
+    } else {
+      for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) acc += partial[(int64_t)pent[q] * K + k];
+    }
     g[(int64_t)s * K + k] = acc;
   }
 }
+
 
 // alpha = rz / p.q;  x += alpha p;  r -= alpha q   (rz in sc[slot])
 __global__ void k_pcg_axpy(const double* __restrict__ sc, int slot,
@@ -1443,7 +1723,7 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
     // g = M^T (h - M a), exact from the panels
     launch_fused<T>(h, fp, h->d_a.as<double>(), 1, sc + fsz, gpart);
     k_panel_sum<<<h->n_sub, pb, 0, st>>>(fp.part.as<double>(), fp.fo.as<int>(), fp.fe.as<int>(),
-                                         K, g);
+                                         K, g, fp.pairs ? 1 : 0);
     // PCG from x = 0: r = g, z = P r, p = z
     CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), st));
     CUDA_CHECK(cudaMemcpyAsync(r, g, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1503,15 +1783,17 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
   else lsqr<float>(h, o, info);
 }
 
-template void launch_fused<float>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*);
-template void launch_fused<double>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*);
+template void launch_fused<float>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
+                                  const float*);
+template void launch_fused<double>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
+                                   const float*);
 template void block_jacobi_setup<float>(elmfb_ctx*, double, bool, double);
 template void block_jacobi_setup<double>(elmfb_ctx*, double, bool, double);
 
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g) {
   const int pb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 256);
   k_panel_sum<<<h->n_sub, pb, 0, h->stream>>>(fp.part.as<double>(), fp.fo.as<int>(),
-                                               fp.fe.as<int>(), h->K, g);
+                                               fp.fe.as<int>(), h->K, g, fp.pairs ? 1 : 0);
   check_launch("k_panel_sum");
   count_launch(h);
 }
