@@ -614,19 +614,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
     const double m = h->cover_off[c + 1] - h->cover_off[c];
     h->gram_flops += 0.5 * m * (m + 1) * 2.0 * h->K * h->K * h->cell_count[c];
   }
-  {
-    std::vector<std::vector<int>> nb(h->n_sub);
-    for (int c = 0; c < nc; ++c) {
-      if (h->cell_count[c] == 0) continue;
-      for (int e = h->cover_off[c]; e < h->cover_off[c + 1]; ++e)
-        for (int f = e; f < h->cover_off[c + 1]; ++f) nb[h->cover_sub[e]].push_back(h->cover_sub[f]);
-    }
-    h->n_gram_pairs = 0;
-    for (auto& v : nb) {
-      std::sort(v.begin(), v.end());
-      h->n_gram_pairs += std::unique(v.begin(), v.end()) - v.begin();
-    }
-  }
+  h->n_gram_pairs = -1;   // counted when asked for (count_gram_pairs)
 
   auto up = [&](DevBuf& b, const void* src, size_t bytes) {
     b.alloc(std::max<size_t>(bytes, 4), st);
@@ -713,6 +701,22 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   stage_end(h, 2);
   stage_end(h, 7);
   h->assembled = true;
+}
+
+// subdomain pairs (i <= j) that share a cell with points
+int64_t count_gram_pairs(const elmfb_ctx* h) {
+  std::vector<std::vector<int>> nb(h->n_sub);
+  for (int c = 0; c < h->n_cells; ++c) {
+    if (h->cell_count[c] == 0) continue;
+    for (int e = h->cover_off[c]; e < h->cover_off[c + 1]; ++e)
+      for (int f = e; f < h->cover_off[c + 1]; ++f) nb[h->cover_sub[e]].push_back(h->cover_sub[f]);
+  }
+  int64_t n = 0;
+  for (auto& v : nb) {
+    std::sort(v.begin(), v.end());
+    n += std::unique(v.begin(), v.end()) - v.begin();
+  }
+  return n;
 }
 
 void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, double* h_out) {

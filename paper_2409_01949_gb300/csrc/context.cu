@@ -412,7 +412,8 @@ int elmfb_get_sizes(elmfb_t h, elmfb_sizes* o) {
     o->nnz = h->assembled ? h->nnz : 0;
     o->panel_rows = h->assembled ? h->NPR : 0;
     o->n_cells = h->n_cells;
-    o->n_gram_pairs = h->n_gram_pairs;
+    if (h->assembled && h->n_gram_pairs < 0) h->n_gram_pairs = count_gram_pairs(h);
+    o->n_gram_pairs = h->assembled ? h->n_gram_pairs : 0;
     o->gram_flops = h->gram_flops;
     o->features = h->K;
     o->n_levels = h->L;

@@ -239,6 +239,7 @@ void prof_harvest(elmfb_ctx* h);
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline void count_launch(elmfb_ctx* h, int n = 1) { h->launches += n; }
 void check_launch(const char* what);
+int64_t count_gram_pairs(const elmfb_ctx* h);   // pairs (i <= j) sharing a cell with points
 // Raise, never lower, a kernel's dynamic shared-memory limit on the current
 // device.  The attribute is process-wide, so handles solving concurrently in
 // other threads only ever see it grow.

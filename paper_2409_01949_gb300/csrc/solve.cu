@@ -50,17 +50,24 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
-// block-wide fixed-order sum; every thread gets the result
+// block-wide fixed-order sum; every thread gets the result.  Warp 0 alone
+// reduces the per-warp sums (FP64 work in every thread is costly on GB300,
+// whose FP64 rate is 1/64 of FP32).
 __device__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_sum<double>(v);
   __syncthreads();
   if (lane == 0) sh[wid] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += sh[i];
+  if (wid == 0) {
+    double s = lane < nw ? sh[lane] : 0.0;
+    s = warp_sum<double>(s);
+    if (lane == 0) sh[32] = s;
+  }
   __syncthreads();
-  return s;
+  const double r = sh[32];
+  __syncthreads();
+  return r;
 }
 
 // sum of n partials by warp 0 of the block in a fixed order (lane-strided
@@ -299,14 +306,16 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
     }
 }
 
+constexpr int kCholThreads = 512;   // 4 per column of X at K = 128
+
 // One block per subdomain: sum the chunk partials, shift, Cholesky
 // (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
 // column-major.  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
 // Right-looking factorisation with a 2-D split of the trailing update; the
 // inverse is formed in place in shared memory row by row (row i of X needs
-// row i of L and rows < i of X), two threads per column splitting each sum.
+// row i of L and rows < i of X), four threads per column splitting each sum.
 // FP64 throughout: the blocks are as ill-conditioned as the shift allows.
-__global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ partial,
+__global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __restrict__ partial,
                                                      const int* __restrict__ chunk_off, int K,
                                                      double shift, double abs_shift,
                                                      double* __restrict__ Xr,
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ p
                                                      int* __restrict__ flags,
                                                      double* __restrict__ gdiag_out) {
   extern __shared__ double G[];   // [K][K]
-  __shared__ double red[32];
+  __shared__ double red[33];
   __shared__ double diag0[128];
   __shared__ double rpiv[128];    // 1 / L_kk
   __shared__ double xrow[128];
@@ -392,16 +401,17 @@ __global__ void __launch_bounds__(256) k_block_chol(const double* __restrict__ p
   }
   // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
   // Row i of L is read while row i of X is formed in xrow, then overwritten.
-  const int j = tid >> 1, half = tid & 1;
+  const int j = tid >> 2, part = tid & 3;   // 4 threads per column
   for (int i = 0; i < K; ++i) {
     double acc = 0.0;
     if (j < i) {
-      const int mid = j + (i - j + 1) / 2;
-      const int m0 = half ? mid : j, m1 = half ? i : mid;
-      for (int m = m0; m < m1; ++m) acc += G[i * K + m] * G[m * K + j];
+      const int len = i - j, step = (len + 3) >> 2;
+      const int m1 = min(i, j + (part + 1) * step);
+      for (int m = j + part * step; m < m1; ++m) acc += G[i * K + m] * G[m * K + j];
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (half == 0 && j < i) xrow[j] = -acc * rpiv[i];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (part == 0 && j < i) xrow[j] = -acc * rpiv[i];
     __syncthreads();
     for (int q = tid; q <= i; q += nt) G[i * K + q] = q == i ? rpiv[i] : xrow[q];
     __syncthreads();
@@ -473,7 +483,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(
     const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ norm_partial) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -574,7 +584,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     double* __restrict__ partial, double* __restrict__ norm_partial) {
   __shared__ double sd[32][kFusedRows];
   __shared__ double su[kFusedRows];
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
   const int c = un.x;
@@ -686,21 +696,23 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
   }
 }
 
-// Same pass, pipelined through shared memory by bulk copies.  Chunks of
-// kPipeRows rows of every covering panel of the unit land in a ring of S
-// stages (lane w of warp 0 copies panel w's rows; one mbarrier per stage).  Iteration i of the loop
-//   - forms the per-panel dots of chunk i (FP32 or FP64 as the panels),
-//   - warp 0 sums them over the panels for chunk i-1 and forms
+// Same pass, pipelined through shared memory by bulk copies.  Warp w < m
+// owns covering panel w of the unit; one extra control warp issues the
+// copies (lane w copies panel w's rows) and forms u'.  Chunks of kPipeRows
+// rows of every covering panel land in a ring of S stages, one mbarrier per
+// stage.  Iteration i of the loop
+//   - panel warps form the per-panel dots of chunk i (FP32 or FP64 as the
+//     panels) and add P_w[r,:]^T u'_r of chunk i-2 into their partials,
+//   - the control warp sums the dots of chunk i-1 over the panels and forms
 //     u'_r = y_r - (alpha/beta) u_r (FP64, written to u),
-//   - all warps add P_w[r,:]^T u'_r of chunk i-2 into their partials,
 // with one barrier per iteration, after which the stage of chunk i-2 is
-// refilled.  The unit's u (or h) values arrive by one more bulk copy at the
-// start, so warp 0 never waits on a global load inside the loop.  Lane l
-// holds features k = l FPL + j, read from shared memory as one vector.  FP64 work is confined to warp 0 (GB300's FP64 rate is a small
-// fraction of FP32).  Double-buffered dot and u' slots make the one barrier
+// refilled.  Double-buffered dot and u' slots make the one barrier
 // sufficient: a slot is rewritten two iterations after it was filled, when
-// every reader has passed the barrier in between.  A wait that times out
-// raises flags[3].
+// every reader has passed the barrier in between.  The unit's u (or h)
+// values arrive by one more bulk copy at the start, so no global load sits
+// inside the loop.  FP64 work is confined to the control warp (GB300's FP64
+// rate is 1/64 of FP32).  Lane l holds features k = l FPL + j, read from
+// shared memory as one vector.  A wait that times out raises flags[3].
 constexpr int kPipeRows = 4;
 constexpr int kPipeMaxStages = 8;
 constexpr int kMaxUnitRows = 1024;   // rows of one unit (its u values are staged in smem)
@@ -773,6 +785,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(T));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cw = (blockDim.x >> 5) - 1;   // control warp: copies, u', norms
   const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
@@ -794,7 +807,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
   }
   __syncthreads();
-  // called by all lanes of warp 0: lane ww copies the chunk's rows of panel ww
+  // called by all lanes of the control warp: lane ww copies the chunk's rows of panel ww
   auto issue = [&](int chunk, int stage) {
     if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
     __syncwarp();
@@ -803,7 +816,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
                        panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
                        &full[stage]);
   };
-  if (w == 0)
+  if (w == cw)
     for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
   // lane slice of the features: k = lane * FPL + j
   const int k0 = lane * FPL;
@@ -815,23 +828,23 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     const int k = k0 + j;
     tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : T(0);
   }
-  double coef = 0.0;   // used by warp 0 only (an FP64 division is costly)
-  if (mode == 0 && w == 0) {
+  double coef = 0.0;   // used by the control warp only (an FP64 division is costly)
+  if (mode == 0 && w == cw) {
     const double beta = scal[S_BETA];
     coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
   }
   T ahi[FPL], alo[FPL];
 #pragma unroll
   for (int j = 0; j < FPL; ++j) ahi[j] = alo[j] = T(0);
-  // warp 0, lane 8r + g: row r of a chunk, panel group g
+  // control warp, lane 8r + g: row r of a chunk, panel group g
   const int yr = lane >> 3, yg = lane & 7;
   double nrm = 0.0;
   bool ok = true;
-  if (w == 0 && !sm100::mbar_wait(&ubar, 0)) ok = false;
+  if (w == cw && !sm100::mbar_wait(&ubar, 0)) ok = false;
   int st_i = 0, ph_i = 0;   // stage and phase parity of chunk i
   int st_u = 0;             // stage of chunk i - 2
   for (int i = 0; i < nchunks + 2; ++i) {
-    if (i < nchunks) {
+    if (i < nchunks && w != cw) {
       if (!sm100::mbar_wait(&full[st_i], ph_i)) ok = false;
       if (active) {
         const T* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
@@ -848,7 +861,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
         if (yg == 0) sd[i & 1][w][yr] = tot;
       }
     }
-    if (w == 0 && i >= 1 && i <= nchunks) {
+    if (w == cw && i >= 1 && i <= nchunks) {
       const int b = (i - 1) & 1;
       T part = T(0);
       for (int q = yg; q < m; q += 8) part += sd[b][q][yr];
@@ -896,7 +909,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     }
     __syncthreads();
     // every warp is past the update of chunk i-2: its stage can be refilled
-    if (w == 0 && i >= 2 && i - 2 + S < nchunks) {
+    if (w == cw && i >= 2 && i - 2 + S < nchunks) {
       sm100::fence_proxy_async_smem();
       issue(i - 2 + S, st_u);
     }
@@ -920,9 +933,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
             make_float2((float)ahi[j], (float)alo[j]);
     }
   }
-  if (threadIdx.x < 32) {   // the row norms live in warp 0
+  if (w == cw) {   // the row norms live in the control warp
     const double tot = warp_sum<double>(nrm);
-    if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+    if (lane == 0) norm_partial[blockIdx.x] = tot;
   }
 }
 
@@ -935,14 +948,20 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
     double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial,
     int pairs) {
   extern __shared__ double zsh[];   // [groups][K] then z[K]
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int s = blockIdx.x;
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
-  __shared__ double shs;
-  const double beta = sqrt(block_partial_sum(beta_partial, n_beta_partial, &shs));
-  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  __shared__ double shs, sh_beta, sh_ib;
+  const double b2 = block_partial_sum(beta_partial, n_beta_partial, &shs);
+  if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
+    const double bt = sqrt(b2);
+    sh_beta = bt;
+    sh_ib = bt > 0.0 ? 1.0 / bt : 0.0;
+  }
+  __syncthreads();
+  const double beta = sh_beta, ib = sh_ib;
   if (g < G && k < K) {
     double z = 0.0;
     if (pairs) {
@@ -1004,7 +1023,7 @@ __global__ void k_panel_T(const double* __restrict__ partial, const int* __restr
                           double* __restrict__ v, double* __restrict__ scal, int identity,
                           int init, double* __restrict__ norm_partial) {
   extern __shared__ double zs[];
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int s = blockIdx.x;
   // beta = sqrt(sum of gather partials), same fixed order in every block
   double b2 = 0.0;
@@ -1043,31 +1062,42 @@ __global__ void k_update(double* __restrict__ scal, const double* __restrict__ a
                          int n_alpha_partial, double* __restrict__ v, double* __restrict__ w,
                          double* __restrict__ x, int64_t N, int init) {
   __shared__ double shs;
-  const double alpha = sqrt(block_partial_sum(alpha_partial, n_alpha_partial, &shs));
+  __shared__ double shv[4];   // ia, phi_rho, theta_rho (scalars formed by one thread)
+  const double a2 = block_partial_sum(alpha_partial, n_alpha_partial, &shs);
   const double beta = scal[kStage + S_BETA];   // beta_{i+1}
-  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-  double phi_rho = 0.0, theta_rho = 0.0;
+  double alpha = 0.0, ia = 0.0, phi_rho = 0.0, theta_rho = 0.0;
   double rhobar_new = 0.0, phibar_new = 0.0, anorm2 = scal[S_ANORM2], arnorm = 0.0;
-  if (init) {
-    // beta_1 u_1 = b, alpha_1 v_1 = A^T u_1, w_1 = v_1, phibar_1 = beta_1, rhobar_1 = alpha_1
-    rhobar_new = alpha;
-    phibar_new = beta;
-    anorm2 = alpha * alpha;
-    arnorm = alpha * beta;
-  } else {
-    const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
-    const double rho = sqrt(rhobar * rhobar + beta * beta);
-    const double c = rho > 0.0 ? rhobar / rho : 1.0;
-    const double sn = rho > 0.0 ? beta / rho : 0.0;
-    const double theta = sn * alpha;
-    rhobar_new = -c * alpha;
-    const double phi = c * phibar;
-    phibar_new = sn * phibar;
-    phi_rho = rho > 0.0 ? phi / rho : 0.0;
-    theta_rho = rho > 0.0 ? theta / rho : 0.0;
-    anorm2 += alpha * alpha + beta * beta;
-    arnorm = phibar_new * alpha * fabs(c);
+  if (threadIdx.x == 0) {   // one thread: the recurrence needs FP64 sqrt / divisions
+    alpha = sqrt(a2);
+    ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    if (init) {
+      // beta_1 u_1 = b, alpha_1 v_1 = A^T u_1, w_1 = v_1, phibar_1 = beta_1, rhobar_1 = alpha_1
+      rhobar_new = alpha;
+      phibar_new = beta;
+      anorm2 = alpha * alpha;
+      arnorm = alpha * beta;
+    } else {
+      const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
+      const double rho = sqrt(rhobar * rhobar + beta * beta);
+      const double c = rho > 0.0 ? rhobar / rho : 1.0;
+      const double sn = rho > 0.0 ? beta / rho : 0.0;
+      const double theta = sn * alpha;
+      rhobar_new = -c * alpha;
+      const double phi = c * phibar;
+      phibar_new = sn * phibar;
+      phi_rho = rho > 0.0 ? phi / rho : 0.0;
+      theta_rho = rho > 0.0 ? theta / rho : 0.0;
+      anorm2 += alpha * alpha + beta * beta;
+      arnorm = phibar_new * alpha * fabs(c);
+    }
+    shv[0] = ia;
+    shv[1] = phi_rho;
+    shv[2] = theta_rho;
   }
+  __syncthreads();
+  ia = shv[0];
+  phi_rho = shv[1];
+  theta_rho = shv[2];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double vn = v[i] * ia;   // v_{i+1}
@@ -1190,12 +1220,14 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
   const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
   // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
   // ring needs two stages in use plus at least two in flight
-  if (S >= 4 && (K * sizeof(T)) % 16 == 0 && !(force_regs && force_regs[0] == '1')) {
+  const int pthreads = fthreads + 32;   // covering-panel warps + the control warp
+  if (S >= 4 && pthreads <= 1024 && (K * sizeof(T)) % 16 == 0 &&
+      !(force_regs && force_regs[0] == '1')) {
     const size_t smem = (size_t)S * stage_bytes + u_bytes;
 #define ELMFB_FT(F)                                                                            \
   if (fpl == F) {                                                                              \
     ensure_dyn_smem((const void*)k_fused_pipe<T, F>, smem);                                   \
-    k_fused_pipe<T, F><<<fp.n_units, fthreads, smem, st>>>(                                    \
+    k_fused_pipe<T, F><<<fp.n_units, pthreads, smem, st>>>(                                    \
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
         h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
@@ -1280,7 +1312,7 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   ensure_dyn_smem((const void*)k_block_chol, csm);
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
-  k_block_chol<<<h->n_sub, 256, csm, st>>>(h->d_gpart.as<double>(), dcoff.as<int>(), K, shift,
+  k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(h->d_gpart.as<double>(), dcoff.as<int>(), K, shift,
                                            abs_shift, h->d_R.as<double>(),
                                            h->d_R.as<double>() + h->n_sub * KK,
                                            h->d_flags.as<int>(), nullptr);
@@ -1540,7 +1572,7 @@ __global__ void __launch_bounds__(128) k_gspmv_pairs(const float* __restrict__ G
 __global__ void k_gspmv_reduce(const double* __restrict__ part, const int* __restrict__ inc_off,
                                const int* __restrict__ inc, int K, const double* __restrict__ x,
                                double mu, double* __restrict__ y, double* __restrict__ dot_part) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int s = blockIdx.x;
   double d = 0.0;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -1560,7 +1592,7 @@ __global__ void k_bj_apply(const double* __restrict__ Xr, const double* __restri
                            const double* __restrict__ r, double* __restrict__ z,
                            double* __restrict__ dot_part) {
   extern __shared__ double sh[];   // r[K], w[K]
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int s = blockIdx.x;
   double* rs = sh;
   double* ws = sh + K;
@@ -1612,10 +1644,11 @@ __global__ void k_pcg_axpy(const double* __restrict__ sc, int slot,
                            const double* __restrict__ pq_part, int npart,
                            const double* __restrict__ p, const double* __restrict__ q,
                            double* __restrict__ x, double* __restrict__ r, int64_t N) {
-  __shared__ double shs;
+  __shared__ double shs, sha;
   const double pq = block_partial_sum(pq_part, npart, &shs);
-  const double rz = sc[slot];
-  const double alpha = pq > 0.0 ? rz / pq : 0.0;
+  if (threadIdx.x == 0) sha = pq > 0.0 ? sc[slot] / pq : 0.0;   // one FP64 division
+  __syncthreads();
+  const double alpha = sha;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
@@ -1627,10 +1660,14 @@ __global__ void k_pcg_axpy(const double* __restrict__ sc, int slot,
 __global__ void k_pcg_pupdate(double* __restrict__ sc, int slot, const double* __restrict__ rz_part,
                               int npart, const double* __restrict__ z, double* __restrict__ p,
                               int64_t N, int init) {
-  __shared__ double shs;
+  __shared__ double shs, shb;
   const double rzn = block_partial_sum(rz_part, npart, &shs);
-  const double rz = sc[slot];
-  const double beta = (!init && rz > 0.0) ? rzn / rz : 0.0;
+  if (threadIdx.x == 0) {   // one FP64 division
+    const double rz = sc[slot];
+    shb = (!init && rz > 0.0) ? rzn / rz : 0.0;
+  }
+  __syncthreads();
+  const double beta = shb;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
