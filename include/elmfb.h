@@ -56,7 +56,12 @@ enum {
 enum {
   ELMFB_FP64 = 0,   /* panels, Gram and solver vectors in FP64                  */
   ELMFB_FP32 = 1,   /* panels FP32, FP64 solver vectors and reductions          */
-  ELMFB_MIXED = 2   /* FP32 panels + BF16 copy for tensor-core Gram blocks       */
+  ELMFB_MIXED = 2,  /* FP32 panels + BF16 copy for tensor-core Gram blocks       */
+  ELMFB_DF32 = 3    /* panels as FP32 pairs (hi + lo, ~48-bit significand, same
+                       8 bytes as FP64), products and sums in float-float
+                       arithmetic on the FP32 pipes; entries evaluated in FP64.
+                       The solvers need K a multiple of 4, K <= 128 and <= 31
+                       covering panels per cell (else UNSUPPORTED)            */
 };
 
 /* ---- subdomain centre placement (paper §4.1 "Domain decomposition") -------- */
@@ -93,7 +98,7 @@ typedef struct elmfb_ctx* elmfb_t;
  *   features     K >= 1 random features per subdomain, at most ELMFB_MAX_FEATURES
  *   seed         SplitMix64 seed of the parameter stream
  *   weight_scale a: every hidden weight and bias is drawn from U(-a, a)
- *   precision    ELMFB_FP64 / ELMFB_FP32 / ELMFB_MIXED
+ *   precision    ELMFB_FP64 / ELMFB_FP32 / ELMFB_MIXED / ELMFB_DF32
  * Parameter stream: output i of SplitMix64(seed) is
  * mix(seed + (i+1) * 0x9E3779B97F4A7C15); column q draws outputs
  * q*(dim+1)+p (p < dim: weight p, p = dim: bias); u = (z >> 40) * 2^-24,

@@ -314,7 +314,8 @@ __device__ __forceinline__ void window_at(const double* x, int dim, const SubGeo
   }
 }
 
-template <class T, int FPL, bool WRITE_T>
+// SPLIT (T = double): store each entry as an FP32 pair hi + lo (ELMFB_DF32).
+template <class T, int FPL, bool WRITE_T, bool SPLIT>
 __global__ void __launch_bounds__(128) k_assemble(
     const int2* __restrict__ tiles, int64_t n_tiles, int dim, int K, int L,
     const SubGeom* __restrict__ sub, const int* __restrict__ cover_sub,
@@ -401,7 +402,13 @@ __global__ void __launch_bounds__(128) k_assemble(
         tanh_pair<T>(sarg, &phi, &tt);
         T v = phi * rA + tt * (rb0 * d0[i] + rb1 * d1[i]) -
               T(2) * phi * tt * (rg0 * d0[i] * d0[i] + rg1 * d1[i] * d1[i]);
-        orow[k] = v;
+        if (SPLIT) {
+          const float hi = __double2float_rn((double)v);
+          reinterpret_cast<float2*>(orow)[k] =
+              make_float2(hi, __double2float_rn((double)v - (double)hi));
+        } else {
+          orow[k] = v;
+        }
         if (WRITE_T) tsm[((threadIdx.x >> 5) * K + k) * 32 + r] = __float2bfloat16_rn((float)v);
       }
     }
@@ -430,19 +437,28 @@ void launch_assemble(elmfb_ctx* h) {
   const T* W = sizeof(T) == 8 ? (const T*)h->d_W64.p : (const T*)h->d_W32.p;
   const T* B = sizeof(T) == 8 ? (const T*)h->d_b64.p : (const T*)h->d_b32.p;
   const bool wt = h->cfg.precision == ELMFB_MIXED && sizeof(T) == 4;
+  const bool split = h->df32() && sizeof(T) == 8;
   const size_t tsm = wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0;
 #define ELMFB_K1(F)                                                                          \
   case F:                                                                                    \
     if (wt)                                                                                  \
-      k_assemble<T, F, true><<<(unsigned)blocks, warps * 32, tsm, h->stream>>>(              \
+      k_assemble<T, F, true, false><<<(unsigned)blocks, warps * 32, tsm, h->stream>>>(       \
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
           h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p,             \
           h->d_pt.as<__nv_bfloat16>(), h->NPR);                                              \
+    else if (split)                                                                          \
+      k_assemble<T, F, false, true><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(         \
+          h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
+          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
+          h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
+          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
+          h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
+          h->NPR);                                                                           \
     else                                                                                     \
-      k_assemble<T, F, false><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(               \
+      k_assemble<T, F, false, false><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(        \
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
@@ -470,6 +486,10 @@ void launch_assemble(elmfb_ctx* h) {
 }
 
 // --------------------------------------------------------------- export -----
+__device__ __forceinline__ double value_of(float v) { return (double)v; }
+__device__ __forceinline__ double value_of(double v) { return v; }
+__device__ __forceinline__ double value_of(df2 v) { return (double)v.hi + (double)v.lo; }
+
 template <class T>
 __global__ void k_export_rows(const int64_t* __restrict__ rows, int64_t n,
                               const int* __restrict__ user_to_sorted,
@@ -489,7 +509,7 @@ __global__ void k_export_rows(const int64_t* __restrict__ rows, int64_t n,
     int s = cover_sub[e];
     const T* src = panels + (panel_off[s] + cover_start[e] + p) * (int64_t)K;
     for (int k = threadIdx.x; k < K; k += blockDim.x)
-      out[i * NPhi + (int64_t)s * K + k] = (double)src[k];
+      out[i * NPhi + (int64_t)s * K + k] = value_of(src[k]);
   }
 }
 
@@ -696,7 +716,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
     // padding tail of 16-row tiles is written by the kernel; clear once for safety
     CUDA_CHECK(cudaMemsetAsync(h->d_pt.p, 0, h->NPR * h->K * 2, st));
   }
-  if (h->fp64()) launch_assemble<double>(h);
+  if (h->eval64()) launch_assemble<double>(h);
   else launch_assemble<float>(h);
   stage_end(h, 2);
   stage_end(h, 7);
@@ -735,7 +755,13 @@ void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, doub
   dout.alloc(n * h->NPhi * sizeof(double), st);
   dh.alloc(n * sizeof(double), st);
   CUDA_CHECK(cudaMemsetAsync(dout.p, 0, n * h->NPhi * sizeof(double), st));
-  if (h->fp64())
+  if (h->df32())
+    k_export_rows<df2><<<(unsigned)n, 128, 0, st>>>(
+        drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
+        h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
+        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), h->d_panels.as<df2>(), h->K,
+        h->NPhi, h->d_h.as<double>(), dout.as<double>(), dh.as<double>());
+  else if (h->fp64())
     k_export_rows<double><<<(unsigned)n, 128, 0, st>>>(
         drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
         h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),

@@ -181,7 +181,10 @@ struct elmfb_ctx {
   double prof_bytes[KID_COUNT] = {0};   // algorithmic bytes per launch (last launch)
 
   bool fp64() const { return cfg.precision == ELMFB_FP64; }
-  size_t panel_elem() const { return fp64() ? 8 : 4; }
+  bool df32() const { return cfg.precision == ELMFB_DF32; }
+  // entries evaluated in FP64 (FP64 panels, or FP32 pairs split from FP64)
+  bool eval64() const { return fp64() || df32(); }
+  size_t panel_elem() const { return eval64() ? 8 : 4; }
 };
 
 // stage timing helpers
@@ -202,9 +205,16 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
 
 // Work plan of the fused pass: units (cell, row range, first partial) and, per
 // panel, the list of partial rows that sum to its part of M^T u'.
+// Panel element of ELMFB_DF32: an FP32 pair, value hi + lo (|lo| <= ulp(hi)/2).
+struct __align__(8) df2 {
+  float hi, lo;
+};
+
 struct FusedPlan {
   DevBuf units, fo, fe, part;
   DevBuf tf;            // FP32 copy of t for FP32 panels
+  DevBuf pch, pco, csum;   // per-panel slices of the partial list and their sums
+  int n_pchunks = 0;
   int n_units = 0;
   int threads = 0;
   bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
@@ -213,13 +223,14 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp);
 // mode 0: u' = M t - (alpha/beta) u (scal[0], scal[1]); mode 1: u' = h - M t.
 // Writes u', per-panel partials of M^T u' into fp.part (FP64 values for FP64
 // panels; compensated FP32 (hi, lo) pairs in the same 8 bytes for FP32
-// panels) and ||u'||^2 per unit.  tf: FP32 copy of t (FP32 panels), or null
-// to convert t here.
+// panels) and ||u'||^2 per unit.  tf: FP32 copy of t (FP32 panels) or FP32
+// pairs (DF32 panels), or null to convert t here.
 template <class T>
 void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double* scal,
-                  double* gpart, const float* tf = nullptr);
+                  double* gpart, const void* tf = nullptr);
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
+void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp);   // fixed slices of each panel's partials
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials
 void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part);  // z = X^T X r
 

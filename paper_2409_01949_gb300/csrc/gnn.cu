@@ -408,13 +408,15 @@ struct Fcg {
   }
   // y = M^T M v   (fused pass with coef 0: u' = M v, then the panel sums)
   void normal_op(const double* v, double* y) {
-    if (h->fp64()) launch_fused<double>(h, fp, v, 0, sc.as<double>(), gpart.as<double>());
+    if (h->df32()) launch_fused<df2>(h, fp, v, 0, sc.as<double>(), gpart.as<double>());
+    else if (h->fp64()) launch_fused<double>(h, fp, v, 0, sc.as<double>(), gpart.as<double>());
     else launch_fused<float>(h, fp, v, 0, sc.as<double>(), gpart.as<double>());
     panel_sum(h, fp, y);
   }
   // g = M^T h(sorted) for the handle's current h vector
   void rhs() {
-    if (h->fp64()) launch_fused<double>(h, fp, x, 1, sc.as<double>(), gpart.as<double>());
+    if (h->df32()) launch_fused<df2>(h, fp, x, 1, sc.as<double>(), gpart.as<double>());
+    else if (h->fp64()) launch_fused<double>(h, fp, x, 1, sc.as<double>(), gpart.as<double>());
     else launch_fused<float>(h, fp, x, 1, sc.as<double>(), gpart.as<double>());
     panel_sum(h, fp, g);
   }
@@ -491,7 +493,8 @@ void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
     ELMFB_THROW(ELMFB_ERR_STATE, "learned preconditioner requested before elmfb_gnn_train / "
                                  "elmfb_gnn_set_weights");
   stage_begin(h, 4);
-  if (h->fp64()) block_jacobi_setup<double>(h, o->shift, false);
+  if (h->df32()) block_jacobi_setup<df2>(h, o->shift, false);
+  else if (h->fp64()) block_jacobi_setup<double>(h, o->shift, false);
   else block_jacobi_setup<float>(h, o->shift, false);
   stage_end(h, 4);
   info->setup_ms = h->stage_ms[4];
@@ -611,7 +614,8 @@ int elmfb_gnn_train(elmfb_t h, int n_rhs, const double* rhs, int solve_iters, in
     cudaStream_t st = h->stream;
     const int K = h->K;
     const int64_t N = h->NPhi;
-    if (h->fp64()) block_jacobi_setup<double>(h, 1e-12, false);
+    if (h->df32()) block_jacobi_setup<df2>(h, 1e-12, false);
+    else if (h->fp64()) block_jacobi_setup<double>(h, 1e-12, false);
     else block_jacobi_setup<float>(h, 1e-10, false);
     gnn_alloc(h);
     // initial weights: He-uniform from SplitMix64 (seeded), biases zero; output layer zero so

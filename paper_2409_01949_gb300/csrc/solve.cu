@@ -20,6 +20,7 @@
 // reproducible from run to run.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 #include <cmath>
 
 #include "elmfb_internal.cuh"
@@ -107,6 +108,92 @@ __global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, 
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
+
+// FP32-pair copy of an FP64 vector (the fused pass's operand for DF32 panels)
+__global__ void k_to_df(const double* __restrict__ x, float2* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float hi = __double2float_rn(x[i]);
+    y[i] = make_float2(hi, __double2float_rn(x[i] - (double)hi));
+  }
+}
+
+// ------------------------------------------------------ float-float (DF32) ---
+// Error-free transformations on the FP32 pipes (Dekker 1971; Knuth TAOCP
+// 4.2.2; the FMA form of the exact product): a value is a pair hi + lo.
+// __fmul_rn / __fadd_rn keep the compiler from contracting a product into a
+// following add, which would break the exactness of the transformations.
+
+// (S, C) += (xh + xl) (yh + yl), renormalised (|C| <= ulp(S) / 2); the
+// xl yl term (below 2^-48 relative) is dropped.
+__device__ __forceinline__ void df_acc(float& S, float& C, float xh, float xl, float yh,
+                                       float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, fmaf(xl, yh, e));
+  const float s = __fadd_rn(S, p);
+  const float bp = __fadd_rn(s, -S);
+  const float t = __fadd_rn(__fadd_rn(S, -__fadd_rn(s, -bp)), __fadd_rn(p, -bp));
+  C = __fadd_rn(C, __fadd_rn(t, e));
+  S = __fadd_rn(s, C);
+  C = __fadd_rn(C, -__fadd_rn(S, -s));
+}
+
+// (ah + al) + (bh + bl), renormalised
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bp = __fadd_rn(s, -a.x);
+  float t = __fadd_rn(__fadd_rn(a.x, -__fadd_rn(s, -bp)), __fadd_rn(b.x, -bp));
+  t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, t);
+  return make_float2(hi, __fadd_rn(t, -__fadd_rn(hi, -s)));
+}
+
+__device__ __forceinline__ float2 df_shfl_xor(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// FP64 value split into an FP32 pair
+__device__ __forceinline__ float2 df_split(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+// sum of 4 per-lane pairs over the warp; lane 8r holds the total of pair r
+__device__ __forceinline__ float2 warp_sum4_df(float2 v0, float2 v1, float2 v2, float2 v3,
+                                               int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+  const float2 k0 = df_add(b4 ? v2 : v0, df_shfl_xor(b4 ? v0 : v2, 16));
+  const float2 k1 = df_add(b4 ? v3 : v1, df_shfl_xor(b4 ? v1 : v3, 16));
+  float2 k = df_add(b3 ? k1 : k0, df_shfl_xor(b3 ? k0 : k1, 8));
+  k = df_add(k, df_shfl_xor(k, 4));
+  k = df_add(k, df_shfl_xor(k, 2));
+  k = df_add(k, df_shfl_xor(k, 1));
+  return k;
+}
+
+// FPL consecutive pairs p[0..FPL) (vector loads when whole; zeros past rem)
+template <int FPL>
+__device__ __forceinline__ void load_slice_df(const float2* p, float2 (&x)[FPL], bool whole,
+                                              int rem) {
+  if (whole) {
+    if constexpr (FPL % 2 == 0) {
+#pragma unroll
+      for (int j = 0; j < FPL; j += 2) {
+        const float4 v = reinterpret_cast<const float4*>(p)[j / 2];
+        x[j] = make_float2(v.x, v.y);
+        x[j + 1] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) x[j] = p[j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) x[j] = j < rem ? p[j] : make_float2(0.f, 0.f);
+  }
+}
+
 
 // ------------------------------------------------------------ Gram diag -----
 // Partial sums of the upper triangle of P^T P over one chunk of panel rows.
@@ -306,6 +393,92 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
     }
 }
 
+// Diagonal Gram partials of DF32 panels: k_gram_diag_pipe's pipeline, every
+// product and sum in float-float arithmetic (4x4 tile of pair accumulators
+// per thread), FP64 result.  Requires K % 4 == 0.
+__global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restrict__ panels,
+                                                            int K, const int4* __restrict__ chunks,
+                                                            double* __restrict__ partial,
+                                                            int* __restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float2* ring = reinterpret_cast<float2*>(smraw);   // [kDiagStages][16][K]
+  __shared__ __align__(8) uint64_t full[kDiagStages];
+  const int4 ch = chunks[blockIdx.x];
+  const int TT = K / 4;
+  const int ntiles = TT * (TT + 1) / 2;
+  int ti = -1, tj = -1;
+  if ((int)threadIdx.x < ntiles) {
+    int rem = threadIdx.x;
+    ti = 0;
+    while (rem >= TT - ti) {
+      rem -= TT - ti;
+      ++ti;
+    }
+    tj = ti + rem;
+  }
+  const int nsteps = ch.z / 16;
+  const uint32_t step_bytes = (uint32_t)(16 * K * sizeof(float2));
+  const float2* base = panels + (int64_t)ch.y * K;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kDiagStages; ++q) sm100::mbar_init(&full[q], 1);
+    sm100::fence_mbar_init();
+    for (int q = 0; q < kDiagStages && q < nsteps; ++q) {
+      sm100::mbar_arrive_expect_tx(&full[q], step_bytes);
+      sm100::bulk_load(ring + (int64_t)q * 16 * K, base + (int64_t)q * 16 * K, step_bytes,
+                       &full[q]);
+    }
+  }
+  __syncthreads();
+  float S[4][4], C[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) S[a][b] = C[a][b] = 0.f;
+  bool ok = true;
+  int st = 0, ph = 0;
+  for (int q = 0; q < nsteps; ++q) {
+    if (!sm100::mbar_wait(&full[st], ph)) ok = false;
+    const float2* sm = ring + (int64_t)st * 16 * K;
+    if (ti >= 0) {
+#pragma unroll 2
+      for (int r = 0; r < 16; ++r) {
+        float2 x[4], y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          x[a] = sm[r * K + 4 * ti + a];
+          y[a] = sm[r * K + 4 * tj + a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) df_acc(S[a][b], C[a][b], x[a].x, x[a].y, y[b].x, y[b].y);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + kDiagStages < nsteps) {
+      sm100::fence_proxy_async_smem();
+      sm100::mbar_arrive_expect_tx(&full[st], step_bytes);
+      sm100::bulk_load(ring + (int64_t)st * 16 * K, base + (int64_t)(q + kDiagStages) * 16 * K,
+                       step_bytes, &full[st]);
+    }
+    if (++st == kDiagStages) {
+      st = 0;
+      ph ^= 1;
+    }
+  }
+  if (!ok) atomicOr(&flags[3], 1);
+  if (ti < 0) return;
+  const int KT = K * (K + 1) / 2;
+  double* out = partial + (int64_t)blockIdx.x * KT;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * ti + a, j = 4 * tj + b;
+      if (j >= i) out[i * K - i * (i - 1) / 2 + (j - i)] = (double)S[a][b] + (double)C[a][b];
+    }
+}
+
 constexpr int kCholThreads = 512;   // 4 per column of X at K = 128
 
 // One block per subdomain: sum the chunk partials, shift, Cholesky
@@ -426,9 +599,19 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   }
 }
 
+// low-precision copy of an FP64 value: kind 1 FP32, kind 2 FP32 pair (hi, lo)
+__device__ __forceinline__ void store_low(void* dst, int kind, int64_t i, double v) {
+  if (kind == 1) {
+    static_cast<float*>(dst)[i] = (float)v;
+  } else if (kind == 2) {
+    const float hi = __double2float_rn(v);
+    static_cast<float2*>(dst)[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
 // t_j = R_j^{-1} v_j = X_j^T v_j per subdomain (t_i = sum_{m>=i} X_mi v_m; X_j lower
-// triangular, row-major; identity without a preconditioner); tf, if given,
-// receives an FP32 copy of t.  The G
+// triangular, row-major; identity without a preconditioner); tlow receives a
+// low-precision copy of t (store_low kind; 0 = none).  The G
 // thread groups of the block split the inner sum into fixed slices, then one
 // pass adds the group sums in order (deterministic).  Block 0 commits the
 // staged LSQR scalars.
@@ -436,7 +619,7 @@ __global__ void __launch_bounds__(1024) k_precond(const double* __restrict__ Xr,
                                                   const double* __restrict__ v, int K,
                                                   double* __restrict__ t, int identity,
                                                   double* __restrict__ scal,
-                                                  float* __restrict__ tf) {
+                                                  void* __restrict__ tlow, int low_kind) {
   extern __shared__ double psh[];   // vs[K] then part[G][K]
   const int s = blockIdx.x;
   if (s == 0 && threadIdx.x < kStage) scal[threadIdx.x] = scal[kStage + threadIdx.x];
@@ -444,7 +627,7 @@ __global__ void __launch_bounds__(1024) k_precond(const double* __restrict__ Xr,
   if (identity) {
     for (int i = threadIdx.x; i < K; i += blockDim.x) {
       t[(int64_t)s * K + i] = vv[i];
-      if (tf) tf[(int64_t)s * K + i] = (float)vv[i];
+      store_low(tlow, low_kind, (int64_t)s * K + i, vv[i]);
     }
     return;
   }
@@ -468,7 +651,7 @@ __global__ void __launch_bounds__(1024) k_precond(const double* __restrict__ Xr,
     double acc = 0.0;
     for (int q = 0; q < G; ++q) acc += part[q * K + j];
     t[(int64_t)s * K + j] = acc;
-    if (tf) tf[(int64_t)s * K + j] = (float)acc;
+    store_low(tlow, low_kind, (int64_t)s * K + j, acc);
   }
 }
 
@@ -939,12 +1122,200 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   }
 }
 
-// v'_j = X_j z_j / beta - beta v_j with z_j = sum of the unit partials of panel j
-// (X_j = R_j^{-T}); several thread groups split the partial list of a panel.
+// The fused LSQR pass of k_fused_pipe for DF32 panels: identical pipeline,
+// with every product and sum of panel entries in float-float arithmetic
+// (about 15 FP32 operations per entry and product, against one FP64 FMA that
+// GB300 issues at 1/64 of the FP32 rate).  Partials are stored as pairs in
+// the hi - lo convention of the FP32 path.
+template <int FPL>
+__global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
+    const float2* __restrict__ panels, const float2* __restrict__ tvec, int K,
+    const int4* __restrict__ units, const int* __restrict__ cell_pstart,
+    const int* __restrict__ cell_count, const int* __restrict__ cover_off,
+    const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
+    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    double* __restrict__ u, const double* __restrict__ hvec, int mode,
+    double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
+    int* __restrict__ flags) {
+  extern __shared__ __align__(128) unsigned char ring_raw[];
+  __shared__ __align__(8) uint64_t full[kPipeMaxStages];
+  __shared__ __align__(8) uint64_t ubar;
+  __shared__ float2 sd[2][32][kPipeRows];
+  __shared__ float2 su[2][kPipeRows];
+  __shared__ int64_t srow[32];
+  float2* ring = reinterpret_cast<float2*>(ring_raw);
+  const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
+  double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(float2));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cw = (blockDim.x >> 5) - 1;
+  const int4 un = units[blockIdx.x];
+  const int c = un.x;
+  const int m = cover_off[c + 1] - cover_off[c];
+  const int cnt = cell_count[c];
+  const int64_t R0 = cell_pstart[c];
+  const bool active = w < m;
+  const int s = cover_sub[cover_off[c] + (active ? w : 0)];
+  const uint32_t copy_bytes = (uint32_t)(kPipeRows * K * sizeof(float2));
+  const int nrows = un.z - un.y;
+  const int nchunks = nrows / kPipeRows;
+  if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; ++q) sm100::mbar_init(&full[q], 1);
+    sm100::mbar_init(&ubar, 1);
+    sm100::fence_mbar_init();
+    const uint32_t ub = (uint32_t)(nrows * sizeof(double));
+    sm100::mbar_arrive_expect_tx(&ubar, ub);
+    sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
+  }
+  __syncthreads();
+  auto issue = [&](int chunk, int stage) {
+    if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
+    __syncwarp();
+    if (lane < m)
+      sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
+                       panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
+                       &full[stage]);
+  };
+  if (w == cw)
+    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+  const int k0 = lane * FPL;
+  const bool whole = k0 + FPL <= K;
+  const int rem = K - k0;
+  float2 tv[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) {
+    const int k = k0 + j;
+    tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : make_float2(0.f, 0.f);
+  }
+  double coef = 0.0;
+  if (mode == 0 && w == cw) {
+    const double beta = scal[S_BETA];
+    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+  }
+  float ah[FPL], al[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) ah[j] = al[j] = 0.f;
+  const int yr = lane >> 3, yg = lane & 7;
+  double nrm = 0.0;
+  bool ok = true;
+  if (w == cw && !sm100::mbar_wait(&ubar, 0)) ok = false;
+  int st_i = 0, ph_i = 0;
+  int st_u = 0;
+  for (int i = 0; i < nchunks + 2; ++i) {
+    if (i < nchunks && w != cw) {
+      if (!sm100::mbar_wait(&full[st_i], ph_i)) ok = false;
+      if (active) {
+        const float2* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
+        float2 d[kPipeRows];
+#pragma unroll
+        for (int r = 0; r < kPipeRows; ++r) {
+          float2 x[FPL];
+          load_slice_df<FPL>(sp + r * K, x, whole, rem);
+          float Sx = 0.f, Cx = 0.f;
+#pragma unroll
+          for (int j = 0; j < FPL; ++j) df_acc(Sx, Cx, x[j].x, x[j].y, tv[j].x, tv[j].y);
+          d[r] = make_float2(Sx, Cx);
+        }
+        const float2 tot = warp_sum4_df(d[0], d[1], d[2], d[3], lane);
+        if (yg == 0) sd[i & 1][w][yr] = tot;
+      }
+    }
+    if (w == cw && i >= 1 && i <= nchunks) {
+      const int b = (i - 1) & 1;
+      float2 part = make_float2(0.f, 0.f);
+      for (int q = yg; q < m; q += 8) part = df_add(part, sd[b][q][yr]);
+      part = df_add(part, df_shfl_xor(part, 4));
+      part = df_add(part, df_shfl_xor(part, 2));
+      part = df_add(part, df_shfl_xor(part, 1));
+      if (yg == 0) {
+        const int pr = (i - 1) * kPipeRows + yr;
+        double out = 0.0;
+        if (un.y + pr < cnt) {
+          const double y = (double)part.x + (double)part.y;
+          const double uo = us[pr];
+          out = mode == 0 ? y - coef * uo : uo - y;
+          u[R0 + un.y + pr] = out;
+          nrm += out * out;
+        }
+        su[b][yr] = df_split(out);
+      }
+    }
+    if (i >= 2 && active) {
+      const float2* sp = ring + st_u * stage_elems + (int64_t)w * kPipeRows * K + k0;
+      const int b = i & 1;
+#pragma unroll
+      for (int r = 0; r < kPipeRows; ++r) {
+        const float2 ur = su[b][r];
+        float2 x[FPL];
+        load_slice_df<FPL>(sp + r * K, x, whole, rem);
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) df_acc(ah[j], al[j], x[j].x, x[j].y, ur.x, ur.y);
+      }
+    }
+    __syncthreads();
+    if (w == cw && i >= 2 && i - 2 + S < nchunks) {
+      sm100::fence_proxy_async_smem();
+      issue(i - 2 + S, st_u);
+    }
+    if (i >= 2) st_u = st_u + 1 == S ? 0 : st_u + 1;
+    if (i < nchunks && ++st_i == S) {
+      st_i = 0;
+      ph_i ^= 1;
+    }
+  }
+  if (!ok && lane == 0) atomicOr(&flags[3], 1);
+  if (active) {
+    const int64_t base_idx = (int64_t)(un.w + w) * K;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+      const int k = k0 + j;
+      if (k < K) reinterpret_cast<float2*>(partial)[base_idx + k] = make_float2(ah[j], -al[j]);
+    }
+  }
+  if (w == cw) {
+    const double tot = warp_sum<double>(nrm);
+    if (lane == 0) norm_partial[blockIdx.x] = tot;
+  }
+}
+
+// Sum of one fixed slice of a panel's partials (at most kPanelChunk entries of
+// the panel's entry list), one thread per feature k.  FP32 (hi, lo) pairs are
+// summed in float-float arithmetic and stored as a pair in the same
+// convention (value hi - lo); FP64 partials are summed in FP64.
+constexpr int kPanelChunk = 32;
+
+__global__ void k_panel_chunks(const double* __restrict__ partial, const int* __restrict__ fe,
+                               const int2* __restrict__ pch, int K, double* __restrict__ csum,
+                               int pairs) {
+  __shared__ int ent[kPanelChunk];
+  const int2 ch = pch[blockIdx.x];
+  const int n = ch.y - ch.x;
+  if ((int)threadIdx.x < n) ent[threadIdx.x] = fe[ch.x + threadIdx.x];
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const int64_t out = (int64_t)blockIdx.x * K + k;
+    if (pairs) {
+      float hi = 0.f, lo = 0.f;
+#pragma unroll 8
+      for (int q = 0; q < n; ++q) {
+        const float2 pr = partial_pair(partial, (int64_t)ent[q] * K + k);
+        ff_add(hi, lo, pr.x, pr.y);
+      }
+      reinterpret_cast<float2*>(csum)[out] = make_float2(hi, -lo);
+    } else {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < n; ++q) acc += partial[(int64_t)ent[q] * K + k];
+      csum[out] = acc;
+    }
+  }
+}
+
+// v'_j = X_j z_j / beta - beta v_j with z_j = sum of the slice sums of panel j
+// (X_j = R_j^{-T}); several thread groups split the slice list of a panel.
 __global__ void __launch_bounds__(1024) k_panel_T2(
-    const double* __restrict__ partial, const int* __restrict__ pent_off,
-    const int* __restrict__ pent, const double* __restrict__ Xc, int K,
-    const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
+    const double* __restrict__ csum, const int* __restrict__ pco, const double* __restrict__ Xc,
+    int K, const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
     double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial,
     int pairs) {
   extern __shared__ double zsh[];   // [groups][K] then z[K]
@@ -966,14 +1337,13 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
     double z = 0.0;
     if (pairs) {
       float zs_hi = 0.f, zs_lo = 0.f;
-      for (int q = pent_off[s] + g; q < pent_off[s + 1]; q += G) {
-        const float2 pr = partial_pair(partial, (int64_t)pent[q] * K + k);
+      for (int q = pco[s] + g; q < pco[s + 1]; q += G) {
+        const float2 pr = partial_pair(csum, (int64_t)q * K + k);
         ff_add(zs_hi, zs_lo, pr.x, pr.y);
       }
       z = (double)zs_hi + (double)zs_lo;
     } else {
-      for (int q = pent_off[s] + g; q < pent_off[s + 1]; q += G)
-        z += partial[(int64_t)pent[q] * K + k];
+      for (int q = pco[s] + g; q < pco[s + 1]; q += G) z += csum[(int64_t)q * K + k];
     }
     zsh[g * K + k] = z;
   }
@@ -1181,7 +1551,30 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   fp.fe.alloc(std::max<size_t>(fe.size(), 1) * sizeof(int), st);
   fp.part.alloc(std::max<int64_t>(pbase, 1) * K * sizeof(double), st);
   fp.pairs = !h->fp64();
-  if (fp.pairs) fp.tf.alloc(std::max<int64_t>(h->NPhi, 1) * sizeof(float), st);
+  // fixed slices of at most kPanelChunk partials per panel: the big panels of
+  // the coarse levels (one partial per unit of every cell) are summed by many
+  // blocks, then each panel adds its few slice sums in order
+  {
+    std::vector<int2> pch;
+    std::vector<int> pco(h->n_sub + 1, 0);
+    for (int s2 = 0; s2 < h->n_sub; ++s2) {
+      pco[s2] = (int)pch.size();
+      for (int e0 = fo[s2]; e0 < fo[s2 + 1]; e0 += kPanelChunk)
+        pch.push_back(make_int2(e0, std::min(e0 + kPanelChunk, fo[s2 + 1])));
+    }
+    pco[h->n_sub] = (int)pch.size();
+    fp.n_pchunks = (int)pch.size();
+    fp.pch.alloc(std::max<size_t>(pch.size(), 1) * sizeof(int2), st);
+    fp.pco.alloc(pco.size() * sizeof(int), st);
+    fp.csum.alloc(std::max<size_t>(pch.size(), 1) * K * sizeof(double), st);
+    if (!pch.empty())
+      CUDA_CHECK(cudaMemcpyAsync(fp.pch.p, pch.data(), pch.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(fp.pco.p, pco.data(), pco.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, st));
+  }
+  if (fp.pairs)
+    fp.tf.alloc(std::max<int64_t>(h->NPhi, 1) * (h->df32() ? sizeof(float2) : sizeof(float)), st);
   CUDA_CHECK(cudaMemcpyAsync(fp.units.p, units.data(), units.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, st));
   CUDA_CHECK(cudaMemcpyAsync(fp.fo.p, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -1193,12 +1586,48 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
 
 template <class T>
 void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, double* scal,
-                  double* gpart, const float* tf) {
+                  double* gpart, const void* tlow) {
   const int K = h->K;
   const int fpl = (K + 31) / 32;
   const int fthreads = fp.threads;
-  const T* P = (const T*)h->d_panels.p;
   cudaStream_t st = h->stream;
+  if constexpr (std::is_same<T, df2>::value) {
+    // DF32 panels: the pass reads t as FP32 pairs
+    if (!tlow) {
+      k_to_df<<<(unsigned)std::min<int64_t>(ceil_div(h->NPhi, 256), 1216), 256, 0, st>>>(
+          t64, fp.tf.as<float2>(), h->NPhi);
+      count_launch(h);
+      tlow = fp.tf.p;
+    }
+    const int mmax = std::max(1, h->max_cover);
+    const size_t stage_bytes = (size_t)mmax * kPipeRows * K * sizeof(float2);
+    const size_t u_bytes = kMaxUnitRows * sizeof(double);
+    const int S = (int)std::min<size_t>(kPipeMaxStages,
+                                        (200 * 1024 - u_bytes) / std::max<size_t>(stage_bytes, 1));
+    const int pthreads = fthreads + 32;
+    if (S < 4 || pthreads > 1024 || K % 2 != 0 || fpl > 4)
+      ELMFB_THROW(ELMFB_ERR_UNSUPPORTED,
+                  "DF32 needs K even, K <= 128 and <= 31 covering panels per cell");
+    const size_t smem = (size_t)S * stage_bytes + u_bytes;
+    prof_begin(h, KID_FUSED, (double)h->NPR * K * 8.0 + 16.0 * h->NR + 8.0 * h->NPhi);
+#define ELMFB_FD(F)                                                                             \
+  if (fpl == F) {                                                                               \
+    ensure_dyn_smem((const void*)k_fused_pipe_df<F>, smem);                                     \
+    k_fused_pipe_df<F><<<fp.n_units, pthreads, smem, st>>>(                                     \
+        h->d_panels.as<float2>(), (const float2*)tlow, K, fp.units.as<int4>(),                  \
+        h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), h->d_cover_off.as<int>(),        \
+        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(),    \
+        scal, h->d_u.as<double>(), h->d_h.as<double>(), mode, fp.part.as<double>(), gpart, S,   \
+        mmax, h->d_flags.as<int>());                                                            \
+  }
+    ELMFB_FD(1) ELMFB_FD(2) ELMFB_FD(3) ELMFB_FD(4)
+#undef ELMFB_FD
+    prof_end(h, KID_FUSED);
+    count_launch(h);
+    return;
+  } else {
+  const T* P = (const T*)h->d_panels.p;
+  const float* tf = (const float*)tlow;
   // the pass reads t in the panels' precision
   const T* t = reinterpret_cast<const T*>(t64);
   if (sizeof(T) == 4) {
@@ -1253,6 +1682,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
   }
   prof_end(h, KID_FUSED);
   count_launch(h);
+  }
 }
 
 // rows per diagonal-Gram chunk: fewer, larger chunks keep the triangular
@@ -1294,7 +1724,14 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   if (!chunks.empty()) {
     prof_begin(h, KID_GRAM_DIAG,
                (double)h->NPR * K * sizeof(T) + (double)chunks.size() * KT * sizeof(double));
-    if (K % 4 == 0 && (K * sizeof(T)) % 16 == 0) {
+    if constexpr (std::is_same<T, df2>::value) {
+      if (K % 4 != 0) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "DF32 block-Jacobi set-up needs K % 4 == 0");
+      const size_t psmem = (size_t)kDiagStages * 16 * K * sizeof(float2);
+      ensure_dyn_smem((const void*)k_gram_diag_pipe_df, psmem);
+      k_gram_diag_pipe_df<<<(unsigned)chunks.size(), gthreads, psmem, st>>>(
+          h->d_panels.as<float2>(), K, dch.as<int4>(), h->d_gpart.as<double>(),
+          h->d_flags.as<int>());
+    } else if (K % 4 == 0 && (K * sizeof(T)) % 16 == 0) {
       const size_t psmem = (size_t)kDiagStages * 16 * K * sizeof(T);
       ensure_dyn_smem((const void*)k_gram_diag_pipe<T>, psmem);
       k_gram_diag_pipe<T><<<(unsigned)chunks.size(), gthreads, psmem, st>>>(
@@ -1383,21 +1820,27 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const size_t pc_smem = (size_t)(K + pc_G * K) * sizeof(double);
 
   auto gather = [&](const double* t, int mode) {
-    prof_begin(h, KID_GATHER, panel_bytes + 16.0 * h->NR + 8.0 * N);
-    k_gather<T><<<kGatherBlocks, kGatherThreads, 0, st>>>(
-        P, t, K, h->NR, h->d_grow_cell.as<int>(), h->d_cell_pstart.as<int>(),
-        h->d_cell_count.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
-        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(),
-        h->d_h.as<double>(), mode, gpart);
-    prof_end(h, KID_GATHER);
+    if constexpr (std::is_same<T, df2>::value) {
+      ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "DF32 runs the fused pass only");
+    } else {
+      prof_begin(h, KID_GATHER, panel_bytes + 16.0 * h->NR + 8.0 * N);
+      k_gather<T><<<kGatherBlocks, kGatherThreads, 0, st>>>(
+          P, t, K, h->NR, h->d_grow_cell.as<int>(), h->d_cell_pstart.as<int>(),
+          h->d_cell_count.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
+          h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(),
+          h->d_h.as<double>(), mode, gpart);
+      prof_end(h, KID_GATHER);
+    }
   };
   auto transpose_step = [&](int init) {
-    prof_begin(h, KID_ENTRY_T, panel_bytes + 8.0 * h->NR + 8.0 * ne * K);
-    k_entry_T<T><<<ne, 128, 0, st>>>(P, h->d_u.as<double>(), K, h->d_entry_cell.as<int>(),
-                                        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),
-                                        h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),
-                                        h->d_panel_off.as<int64_t>(), h->d_partial.as<double>());
-    prof_end(h, KID_ENTRY_T);
+    if constexpr (!std::is_same<T, df2>::value) {
+      prof_begin(h, KID_ENTRY_T, panel_bytes + 8.0 * h->NR + 8.0 * ne * K);
+      k_entry_T<T><<<ne, 128, 0, st>>>(P, h->d_u.as<double>(), K, h->d_entry_cell.as<int>(),
+                                          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),
+                                          h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),
+                                          h->d_panel_off.as<int64_t>(), h->d_partial.as<double>());
+      prof_end(h, KID_ENTRY_T);
+    }
     prof_begin(h, KID_PANEL_T, 8.0 * ne * K + (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
     k_panel_T<<<h->n_sub, pblock, K * sizeof(double), st>>>(
         h->d_partial.as<double>(), dpo.as<int>(), dpe.as<int>(), Xc, K, gpart, kGatherBlocks,
@@ -1426,15 +1869,18 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const int KpT = (K + 31) & ~31;
   const int tgroups = std::max(1, 1024 / KpT);
   const size_t p2smem = (size_t)(tgroups + 1) * K * sizeof(double);
-  auto fused_step = [&](const double* t, int mode, const float* tf = nullptr) {
+  auto fused_step = [&](const double* t, int mode, const void* tf = nullptr) {
     launch_fused<T>(h, fp, t, mode, scal, gpart, tf);
   };
+  // k_precond also writes the fused pass's low-precision copy of t
+  const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
   auto fused_tail = [&](int init) {
     prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
                                    (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
+    panel_chunk_sums(h, fp);
     k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
-        dfpart.as<double>(), dfo.as<int>(), dfe.as<int>(), Xc, K, gpart, n_units,
-        h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
+        fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, gpart, n_units, h->d_v.as<double>(),
+        scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N);
     k_update<<<upd_blocks, 256, 0, st>>>(scal, vpart, h->n_sub, h->d_v.as<double>(),
@@ -1454,7 +1900,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       fused_step(h->d_tmp.as<double>(), 1);
     }
     fused_tail(1);
-    count_launch(h, 3);
+    count_launch(h, 2);   // k_panel_T2, k_update (the others count themselves)
   } else {
     if (o->warm_start) {
       gather(h->d_a.as<double>(), 1);
@@ -1477,11 +1923,10 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     for (int b = 0; b < batch; ++b) {
       prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
       k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
-          Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal,
-          fused && fp.pairs ? fp.tf.as<float>() : nullptr);
+          Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, fp.tf.p, low_kind);
       prof_end(h, KID_PRECOND);
       if (fused) {
-        fused_step(h->d_tmp.as<double>(), 0, fp.pairs ? fp.tf.as<float>() : nullptr);
+        fused_step(h->d_tmp.as<double>(), 0, low_kind ? fp.tf.p : nullptr);
         fused_tail(0);
       } else {
         gather(h->d_tmp.as<double>(), 0);
@@ -1510,7 +1955,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   // a = (a0 +) P y
   k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_x_sol.as<double>(), K,
                                                     h->d_tmp.as<double>(), identity, scal,
-                                                    nullptr);
+                                                    nullptr, 0);
   if (o->warm_start)
     k_add_to<<<upd_blocks, 256, 0, st>>>(h->d_a.as<double>(), h->d_tmp.as<double>(), N);
   else
@@ -1618,21 +2063,20 @@ __global__ void k_bj_apply(const double* __restrict__ Xr, const double* __restri
 }
 
 // g_s = sum of the fused pass partials of panel s (M^T u' unscaled)
-__global__ void k_panel_sum(const double* __restrict__ partial, const int* __restrict__ pent_off,
-                            const int* __restrict__ pent, int K, double* __restrict__ g,
-                            int pairs) {
+__global__ void k_panel_sum(const double* __restrict__ csum, const int* __restrict__ pco, int K,
+                            double* __restrict__ g, int pairs) {
   const int s = blockIdx.x;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
     if (pairs) {
       float hi = 0.f, lo = 0.f;
-      for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) {
-        const float2 pr = partial_pair(partial, (int64_t)pent[q] * K + k);
+      for (int q = pco[s]; q < pco[s + 1]; ++q) {
+        const float2 pr = partial_pair(csum, (int64_t)q * K + k);
         ff_add(hi, lo, pr.x, pr.y);
       }
       acc = (double)hi + (double)lo;
     } else {
-      for (int q = pent_off[s]; q < pent_off[s + 1]; ++q) acc += partial[(int64_t)pent[q] * K + k];
+      for (int q = pco[s]; q < pco[s + 1]; ++q) acc += csum[(int64_t)q * K + k];
     }
     g[(int64_t)s * K + k] = acc;
   }
@@ -1759,8 +2203,9 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   for (int ref = 0; ref < o->refine; ++ref) {
     // g = M^T (h - M a), exact from the panels
     launch_fused<T>(h, fp, h->d_a.as<double>(), 1, sc + fsz, gpart);
-    k_panel_sum<<<h->n_sub, pb, 0, st>>>(fp.part.as<double>(), fp.fo.as<int>(), fp.fe.as<int>(),
-                                         K, g, fp.pairs ? 1 : 0);
+    panel_chunk_sums(h, fp);
+    k_panel_sum<<<h->n_sub, pb, 0, st>>>(fp.csum.as<double>(), fp.pco.as<int>(), K, g,
+                                         fp.pairs ? 1 : 0);
     // PCG from x = 0: r = g, z = P r, p = z
     CUDA_CHECK(cudaMemsetAsync(x, 0, N * sizeof(double), st));
     CUDA_CHECK(cudaMemcpyAsync(r, g, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1816,21 +2261,36 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "solver method not available in this build");
   if (o->preconditioner != ELMFB_PREC_NONE && o->preconditioner != ELMFB_PREC_BLOCK_JACOBI)
     ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "LSQR takes no or block-Jacobi preconditioning");
-  if (h->fp64()) lsqr<double>(h, o, info);
+  if (h->df32()) lsqr<df2>(h, o, info);
+  else if (h->fp64()) lsqr<double>(h, o, info);
   else lsqr<float>(h, o, info);
 }
 
 template void launch_fused<float>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
-                                  const float*);
+                                  const void*);
 template void launch_fused<double>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
-                                   const float*);
+                                   const void*);
+template void launch_fused<df2>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
+                                const void*);
 template void block_jacobi_setup<float>(elmfb_ctx*, double, bool, double);
 template void block_jacobi_setup<double>(elmfb_ctx*, double, bool, double);
+template void block_jacobi_setup<df2>(elmfb_ctx*, double, bool, double);
+
+void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp) {
+  if (fp.n_pchunks == 0) return;
+  const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
+  k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(fp.part.as<double>(), fp.fe.as<int>(),
+                                                      fp.pch.as<int2>(), h->K,
+                                                      fp.csum.as<double>(), fp.pairs ? 1 : 0);
+  check_launch("k_panel_chunks");
+  count_launch(h);
+}
 
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g) {
   const int pb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 256);
-  k_panel_sum<<<h->n_sub, pb, 0, h->stream>>>(fp.part.as<double>(), fp.fo.as<int>(),
-                                               fp.fe.as<int>(), h->K, g, fp.pairs ? 1 : 0);
+  panel_chunk_sums(h, fp);
+  k_panel_sum<<<h->n_sub, pb, 0, h->stream>>>(fp.csum.as<double>(), fp.pco.as<int>(), h->K, g,
+                                               fp.pairs ? 1 : 0);
   check_launch("k_panel_sum");
   count_launch(h);
 }

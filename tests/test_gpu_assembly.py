@@ -4,7 +4,8 @@ Tolerance on entries (paper §3 entries; precision reading): |M_gpu - M_oracle|
 <= tol * max(T, 1e-3 S), with T the largest magnitude sum of product-rule and
 quotient-rule terms over the K features of the same row and subdomain block
 (the oracle's ``bound``), S the largest T of that subdomain block over all
-rows, tol = 1e-12 for FP64 panels and 1e-6 for FP32 panels.  The 1e-3 S floor
+rows, tol = 1e-12 for FP64 and DF32 (FP32 pair) panels and 1e-6 for FP32
+panels.  The 1e-3 S floor
 covers points within rounding distance of a support edge, where the window and
 its derivatives vanish and an entry's relative value is not determined by the
 FP64 coordinates.
@@ -19,19 +20,21 @@ from oracle import system as OS
 
 pytestmark = pytest.mark.gpu
 
-TOL = {E.FP64: 1e-12, E.FP32: 1e-6, E.MIXED: 1e-6}
+TOL = {E.FP64: 1e-12, E.FP32: 1e-6, E.MIXED: 1e-6, E.DF32: 1e-12}
 
 SMALL = {
-    "poisson1d_full": (WL.config_poisson1d, [E.FP64, E.FP32]),
+    "poisson1d_full": (WL.config_poisson1d, [E.FP64, E.FP32, E.DF32]),
     "dho_L1-8_K24": (lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000),
-                     [E.FP64, E.FP32]),
+                     [E.FP64, E.FP32, E.DF32]),
     "poisson2d_L1-4_K64": (lambda: WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60,
-                                                n_boundary_side=60), [E.FP64, E.FP32, E.MIXED]),
+                                                n_boundary_side=60),
+                           [E.FP64, E.FP32, E.MIXED, E.DF32]),
     "dho_paper_K12_delta2.9_endpoint": (WL.dho_paper_baseline, [E.FP64]),
     "poisson2d_delta2.9_K40": (lambda: WL.poisson2d(levels=(3, 5), features=40, n_side=50,
                                                     n_boundary_side=50, delta=2.9), [E.FP32]),
     "poisson2d_ragged_K33": (lambda: WL.poisson2d(levels=(1, 3, 7), features=33, n_side=37,
-                                                  n_boundary_side=11), [E.FP64, E.FP32]),
+                                                  n_boundary_side=11),
+                            [E.FP64, E.FP32, E.DF32]),
 }
 
 

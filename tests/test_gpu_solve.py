@@ -51,13 +51,16 @@ def test_plain_lsqr_iterates_match_oracle_lsqr():
         assert np.linalg.norm(a - a_ref) <= 1e-10 * np.linalg.norm(a_ref)
 
 
-@pytest.mark.parametrize("name,make,prec", [
-    ("poisson1d_J16_K64_N2000", WL.config_poisson1d, E.FP64),
-    ("dho_L1-8_K24_N1000", lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000),
-     E.FP64),
+_SOLVE_CASES = [
+    ("poisson1d_J16_K64_N2000", WL.config_poisson1d),
+    ("dho_L1-8_K24_N1000", lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000)),
     ("poisson2d_L1-4_K64_N60", lambda: WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60,
-                                                    n_boundary_side=60), E.FP64),
-])
+                                                    n_boundary_side=60)),
+]
+
+
+@pytest.mark.parametrize("name,make,prec", [(n, m, p) for n, m in _SOLVE_CASES
+                                            for p in (E.FP64, E.DF32)])
 def test_block_jacobi_lsqr_matches_oracle_error(name, make, prec):
     g = _golden(name)
     P = make()
@@ -166,3 +169,15 @@ def test_both_fused_pass_variants_meet_paper_protocol_error(prec, registers, mon
     print(f"registers={registers} prec={prec}: rel L2 {err:.3e} ({info.iterations} its); "
           f"oracle LSQR-15000 {g['lsqr']['rel_l2']:.3e}")
     assert err <= 1.01 * g["lsqr"]["rel_l2"]
+
+
+def test_df32_solve_needs_features_multiple_of_four():
+    """The DF32 solvers need K a multiple of 4 (16-byte vector reads of FP32
+    pairs, 4x4 Gram tiles): K = 33 is rejected before any solver kernel runs;
+    the assembly itself works for any K."""
+    P = WL.poisson2d(levels=(1, 3), features=33, n_side=30, n_boundary_side=10)
+    with E.Solver.from_problem(P, precision=E.DF32) as s:
+        s.assemble_problem(P)
+        with pytest.raises(E.ElmfbError) as ei:
+            s.solve(max_iter=10)
+        assert ei.value.code == E.ERR_UNSUPPORTED
