@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
   bool ok = true;
   for (int q = 0; q < nsteps; ++q) {
     const int st = q % kDiagStages;
-    if (!sm100::mbar_wait(&full[st], (q / kDiagStages) & 1)) ok = false;
+    if (!sm100::mbar_wait(&full[st], (q / kDiagStages) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
     const T* sm = ring + (int64_t)st * 16 * K;
     if (ti >= 0) {
       T acc[4][4];
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
   bool ok = true;
   int st = 0, ph = 0;
   for (int q = 0; q < nsteps; ++q) {
-    if (!sm100::mbar_wait(&full[st], ph)) ok = false;
+    if (!sm100::mbar_wait(&full[st], ph, ok ? sm100::kSpinLimit : 4u)) ok = false;
     const float2* sm = ring + (int64_t)st * 16 * K;
     if (ti >= 0) {
 #pragma unroll 2
@@ -879,25 +879,30 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
   }
 }
 
-// Same pass, pipelined through shared memory by bulk copies.  Warp w < m
-// owns covering panel w of the unit; one extra control warp issues the
-// copies (lane w copies panel w's rows) and forms u'.  Chunks of kPipeRows
-// rows of every covering panel land in a ring of S stages, one mbarrier per
-// stage.  Iteration i of the loop
-//   - panel warps form the per-panel dots of chunk i (FP32 or FP64 as the
-//     panels) and add P_w[r,:]^T u'_r of chunk i-2 into their partials,
-//   - the control warp sums the dots of chunk i-1 over the panels and forms
-//     u'_r = y_r - (alpha/beta) u_r (FP64, written to u),
-// with one barrier per iteration, after which the stage of chunk i-2 is
-// refilled.  Double-buffered dot and u' slots make the one barrier
-// sufficient: a slot is rewritten two iterations after it was filled, when
-// every reader has passed the barrier in between.  The unit's u (or h)
-// values arrive by one more bulk copy at the start, so no global load sits
-// inside the loop.  FP64 work is confined to the control warp (GB300's FP64
-// rate is 1/64 of FP32).  Lane l holds features k = l FPL + j, read from
-// shared memory as one vector.  A wait that times out raises flags[3].
+// Same pass, pipelined through shared memory by bulk copies and specialised
+// warps.  Warp w < m owns covering panel w of the unit; one extra control
+// warp issues the copies (lane w copies panel w's rows) and forms u'.  Chunks
+// of kPipeRows rows of every covering panel land in a ring of S stages.
+// There is no block-wide barrier in the loop; mbarriers carry every
+// dependency:
+//   full[st]   chunk copied in (transaction bytes)
+//   dots[b]    every panel warp has written its dots of the chunk (slot b)
+//   u[b]       the control warp has written u' of the chunk (slot b)
+//   empty[st]  every panel warp has finished its update with the stage
+// Panel warp, chunk i: wait full, form the dots of chunk i, then wait u of
+// chunk i-1 and add P_w[r,:]^T u'_r of chunk i-1, then free its stage.
+// Control warp, chunk j: wait dots, sum them over the panels, form
+// u'_r = y_r - (alpha/beta) u_r in FP64 (written to u), then wait empty for
+// chunk j-1 and refill that stage with chunk j-1+S.  A warp cannot run two
+// phases ahead on any barrier: each wait is ordered behind the arrivals it
+// depends on (a panel warp's dots of chunk i+2 follow its wait for u' of
+// chunk i, which needs every dots arrival of chunk i).  The unit's u (or h)
+// values come in by one bulk copy, so no global load sits inside the loop.
+// FP64 work is confined to the control warp (GB300's FP64 rate is 1/64 of
+// FP32).  Lane l holds features k = l FPL + j, read from shared memory as one
+// vector.  Every wait is bounded; a timeout raises flags[3].
 constexpr int kPipeRows = 4;
-constexpr int kPipeMaxStages = 8;
+constexpr int kPipeMaxStages = 12;
 constexpr int kMaxUnitRows = 1024;   // rows of one unit (its u values are staged in smem)
 
 // sum of 4 per-lane values over the warp; lane 8r holds the total of value r
@@ -959,8 +964,11 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
     int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char ring_raw[];
-  __shared__ __align__(8) uint64_t full[kPipeMaxStages];
-  __shared__ __align__(8) uint64_t ubar;
+  __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
+  __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
+  __shared__ __align__(8) uint64_t dots_bar[2];             // dots of a chunk written
+  __shared__ __align__(8) uint64_t u_bar[2];                // u' of a chunk written
+  __shared__ __align__(8) uint64_t ubar;                    // the unit's u / h values in
   __shared__ T sd[2][32][kPipeRows];
   __shared__ T su[2][kPipeRows];
   __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
@@ -969,7 +977,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(T));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cw = (blockDim.x >> 5) - 1;   // control warp: copies, u', norms
-  const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
+  const int4 un = units[blockIdx.x];      // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
   const int cnt = cell_count[c];
@@ -981,78 +989,55 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const int nchunks = nrows / kPipeRows;
   if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
   if (threadIdx.x == 0) {
-    for (int q = 0; q < S; ++q) sm100::mbar_init(&full[q], 1);
+    for (int q = 0; q < S; ++q) {
+      sm100::mbar_init(&full[q], 1);
+      sm100::mbar_init(&empty[q], (uint32_t)m);
+    }
+    for (int b = 0; b < 2; ++b) {
+      sm100::mbar_init(&dots_bar[b], 4u * (uint32_t)m);   // lanes 0, 8, 16, 24 of each warp
+      sm100::mbar_init(&u_bar[b], 4u);
+    }
     sm100::mbar_init(&ubar, 1);
     sm100::fence_mbar_init();
-    // the unit's u (mode 0) or h (mode 1) values, read by warp 0 for u'
-    const uint32_t ub = (uint32_t)(nrows * sizeof(double));
-    sm100::mbar_arrive_expect_tx(&ubar, ub);
-    sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
   }
-  __syncthreads();
-  // called by all lanes of the control warp: lane ww copies the chunk's rows of panel ww
-  auto issue = [&](int chunk, int stage) {
-    if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
-    __syncwarp();
-    if (lane < m)
-      sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
-                       panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
-                       &full[stage]);
-  };
-  if (w == cw)
-    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
-  // lane slice of the features: k = lane * FPL + j
-  const int k0 = lane * FPL;
-  const bool whole = k0 + FPL <= K;
-  const int rem = K - k0;
-  T tv[FPL];
-#pragma unroll
-  for (int j = 0; j < FPL; ++j) {
-    const int k = k0 + j;
-    tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : T(0);
-  }
-  double coef = 0.0;   // used by the control warp only (an FP64 division is costly)
-  if (mode == 0 && w == cw) {
-    const double beta = scal[S_BETA];
-    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
-  }
-  T ahi[FPL], alo[FPL];
-#pragma unroll
-  for (int j = 0; j < FPL; ++j) ahi[j] = alo[j] = T(0);
-  // control warp, lane 8r + g: row r of a chunk, panel group g
-  const int yr = lane >> 3, yg = lane & 7;
-  double nrm = 0.0;
+  __syncthreads();   // the only block-wide barrier
   bool ok = true;
-  if (w == cw && !sm100::mbar_wait(&ubar, 0)) ok = false;
-  int st_i = 0, ph_i = 0;   // stage and phase parity of chunk i
-  int st_u = 0;             // stage of chunk i - 2
-  for (int i = 0; i < nchunks + 2; ++i) {
-    if (i < nchunks && w != cw) {
-      if (!sm100::mbar_wait(&full[st_i], ph_i)) ok = false;
-      if (active) {
-        const T* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
-        T d[kPipeRows];
-#pragma unroll
-        for (int r = 0; r < kPipeRows; ++r) {
-          T x[FPL];
-          load_slice<T, FPL>(sp + r * K, x, whole, rem);
-          d[r] = T(0);
-#pragma unroll
-          for (int j = 0; j < FPL; ++j) d[r] += x[j] * tv[j];
-        }
-        const T tot = warp_sum4(d[0], d[1], d[2], d[3], lane);
-        if (yg == 0) sd[i & 1][w][yr] = tot;
-      }
+  const int yr = lane >> 3, yg = lane & 7;
+
+  if (w == cw) {
+    // ---------------------------------------------------------- control warp
+    auto issue = [&](int chunk, int stage) {
+      if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
+      __syncwarp();
+      if (lane < m)
+        sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
+                         panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
+                         &full[stage]);
+    };
+    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+    if (lane == 0) {
+      const uint32_t ub = (uint32_t)(nrows * sizeof(double));
+      sm100::mbar_arrive_expect_tx(&ubar, ub);
+      sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
     }
-    if (w == cw && i >= 1 && i <= nchunks) {
-      const int b = (i - 1) & 1;
+    double coef = 0.0;
+    if (mode == 0) {
+      const double beta = scal[S_BETA];
+      coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+    }
+    if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
+    double nrm = 0.0;
+    int st_r = 0, ph_r = 0;   // stage / empty parity of chunk j - 1
+    for (int j = 0; j < nchunks; ++j) {
+      const int b = j & 1;
+      if (!sm100::mbar_wait(&dots_bar[b], (j >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
       T part = T(0);
       for (int q = yg; q < m; q += 8) part += sd[b][q][yr];
       part += __shfl_xor_sync(0xffffffffu, part, 4);
       part += __shfl_xor_sync(0xffffffffu, part, 2);
       part += __shfl_xor_sync(0xffffffffu, part, 1);
       if (yg == 0) {
-        const int pr = (i - 1) * kPipeRows + yr;   // row within the unit
+        const int pr = j * kPipeRows + yr;   // row within the unit
         double out = 0.0;
         if (un.y + pr < cnt) {
           const double uo = us[pr];
@@ -1061,71 +1046,116 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
           nrm += out * out;
         }
         su[b][yr] = (T)out;
+        sm100::mbar_arrive(&u_bar[b]);
       }
-    }
-    if (i >= 2 && active) {
-      const T* sp = ring + st_u * stage_elems + (int64_t)w * kPipeRows * K + k0;
-      const int b = i & 1;   // == (i - 2) & 1
-      T acc[FPL];
-#pragma unroll
-      for (int j = 0; j < FPL; ++j) acc[j] = T(0);
-#pragma unroll
-      for (int r = 0; r < kPipeRows; ++r) {
-        const T ur = su[b][r];
-        T x[FPL];
-        load_slice<T, FPL>(sp + r * K, x, whole, rem);
-#pragma unroll
-        for (int j = 0; j < FPL; ++j) acc[j] += x[j] * ur;
-      }
-      // chunk sums added with compensation (FP32 panels)
-#pragma unroll
-      for (int j = 0; j < FPL; ++j) {
-        if (sizeof(T) == 8) {
-          ahi[j] += acc[j];
-        } else {
-          const T y = acc[j] - alo[j];
-          const T t = ahi[j] + y;
-          alo[j] = (t - ahi[j]) - y;
-          ahi[j] = t;
+      // refill the stage of chunk j - 1 once every panel warp has updated with it
+      if (j >= 1) {
+        if (!sm100::mbar_wait(&empty[st_r], ph_r, ok ? sm100::kSpinLimit : 4u)) ok = false;
+        if (j - 1 + S < nchunks) {
+          sm100::fence_proxy_async_smem();
+          issue(j - 1 + S, st_r);
+        }
+        if (++st_r == S) {
+          st_r = 0;
+          ph_r ^= 1;
         }
       }
     }
-    __syncthreads();
-    // every warp is past the update of chunk i-2: its stage can be refilled
-    if (w == cw && i >= 2 && i - 2 + S < nchunks) {
-      sm100::fence_proxy_async_smem();
-      issue(i - 2 + S, st_u);
+    if (!ok && lane == 0) atomicOr(&flags[3], 1);
+    const double tot = warp_sum<double>(nrm);
+    if (lane == 0) norm_partial[blockIdx.x] = tot;
+    return;
+  }
+  if (!active) return;
+
+  // ------------------------------------------------------------ panel warps
+  const int k0 = lane * FPL;   // lane slice of the features: k = lane * FPL + j
+  const bool whole = k0 + FPL <= K;
+  const int rem = K - k0;
+  T tv[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) {
+    const int k = k0 + j;
+    tv[j] = k < K ? tvec[(int64_t)s * K + k] : T(0);
+  }
+  T ahi[FPL], alo[FPL];
+#pragma unroll
+  for (int j = 0; j < FPL; ++j) ahi[j] = alo[j] = T(0);
+  // update with chunk i (rows of stage st, u' slot i & 1), then free the stage
+  auto update = [&](int i, int st) {
+    const int b = i & 1;
+    if (!sm100::mbar_wait(&u_bar[b], (i >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
+    const T* sp = ring + st * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    T acc[FPL];
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) acc[j] = T(0);
+#pragma unroll
+    for (int r = 0; r < kPipeRows; ++r) {
+      const T ur = su[b][r];
+      T x[FPL];
+      load_slice<T, FPL>(sp + r * K, x, whole, rem);
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) acc[j] += x[j] * ur;
     }
-    if (i >= 2) st_u = st_u + 1 == S ? 0 : st_u + 1;
-    if (i < nchunks && ++st_i == S) {
+    // chunk sums added with compensation (FP32 panels)
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+      if (sizeof(T) == 8) {
+        ahi[j] += acc[j];
+      } else {
+        const T y = acc[j] - alo[j];
+        const T t = ahi[j] + y;
+        alo[j] = (t - ahi[j]) - y;
+        ahi[j] = t;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) sm100::mbar_arrive(&empty[st]);
+  };
+  int st_i = 0, ph_i = 0, st_prev = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    if (!sm100::mbar_wait(&full[st_i], ph_i, ok ? sm100::kSpinLimit : 4u)) ok = false;
+    const T* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    T d[kPipeRows];
+#pragma unroll
+    for (int r = 0; r < kPipeRows; ++r) {
+      T x[FPL];
+      load_slice<T, FPL>(sp + r * K, x, whole, rem);
+      d[r] = T(0);
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) d[r] += x[j] * tv[j];
+    }
+    const T tot = warp_sum4(d[0], d[1], d[2], d[3], lane);
+    if (yg == 0) {
+      sd[i & 1][w][yr] = tot;
+      sm100::mbar_arrive(&dots_bar[i & 1]);
+    }
+    if (i >= 1) update(i - 1, st_prev);
+    st_prev = st_i;
+    if (++st_i == S) {
       st_i = 0;
       ph_i ^= 1;
     }
   }
+  if (nchunks >= 1) update(nchunks - 1, st_prev);
   if (!ok && lane == 0) atomicOr(&flags[3], 1);
-  if (active) {
-    const int64_t base_idx = (int64_t)(un.w + w) * K;
+  const int64_t base_idx = (int64_t)(un.w + w) * K;
 #pragma unroll
-    for (int j = 0; j < FPL; ++j) {
-      const int k = k0 + j;
-      if (k >= K) continue;
-      if (sizeof(T) == 8)
-        partial[base_idx + k] = (double)ahi[j];
-      else
-        reinterpret_cast<float2*>(partial)[base_idx + k] =
-            make_float2((float)ahi[j], (float)alo[j]);
-    }
-  }
-  if (w == cw) {   // the row norms live in the control warp
-    const double tot = warp_sum<double>(nrm);
-    if (lane == 0) norm_partial[blockIdx.x] = tot;
+  for (int j = 0; j < FPL; ++j) {
+    const int k = k0 + j;
+    if (k >= K) continue;
+    if (sizeof(T) == 8)
+      partial[base_idx + k] = (double)ahi[j];
+    else
+      reinterpret_cast<float2*>(partial)[base_idx + k] =
+          make_float2((float)ahi[j], (float)alo[j]);
   }
 }
 
-// The fused LSQR pass of k_fused_pipe for DF32 panels: identical pipeline,
-// with every product and sum of panel entries in float-float arithmetic
-// (about 15 FP32 operations per entry and product, against one FP64 FMA that
-// GB300 issues at 1/64 of the FP32 rate).  Partials are stored as pairs in
+// The fused LSQR pass of k_fused_pipe for DF32 panels: identical warp roles
+// and barriers, with every product and sum of panel entries in float-float
+// arithmetic (about 15 FP32 operations per entry and product, against one
+// FP64 FMA that GB300 issues at 1/64 of the FP32 rate).  Partials are stored as pairs in
 // the hi - lo convention of the FP32 path.
 template <int FPL>
 __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
@@ -1138,17 +1168,20 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
     int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char ring_raw[];
-  __shared__ __align__(8) uint64_t full[kPipeMaxStages];
-  __shared__ __align__(8) uint64_t ubar;
+  __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
+  __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
+  __shared__ __align__(8) uint64_t dots_bar[2];             // dots of a chunk written
+  __shared__ __align__(8) uint64_t u_bar[2];                // u' of a chunk written
+  __shared__ __align__(8) uint64_t ubar;                    // the unit's u / h values in
   __shared__ float2 sd[2][32][kPipeRows];
   __shared__ float2 su[2][kPipeRows];
-  __shared__ int64_t srow[32];
+  __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
   float2* ring = reinterpret_cast<float2*>(ring_raw);
   const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(float2));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int cw = (blockDim.x >> 5) - 1;
-  const int4 un = units[blockIdx.x];
+  const int cw = (blockDim.x >> 5) - 1;   // control warp: copies, u', norms
+  const int4 un = units[blockIdx.x];      // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
   const int cnt = cell_count[c];
@@ -1160,75 +1193,55 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   const int nchunks = nrows / kPipeRows;
   if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
   if (threadIdx.x == 0) {
-    for (int q = 0; q < S; ++q) sm100::mbar_init(&full[q], 1);
+    for (int q = 0; q < S; ++q) {
+      sm100::mbar_init(&full[q], 1);
+      sm100::mbar_init(&empty[q], (uint32_t)m);
+    }
+    for (int b = 0; b < 2; ++b) {
+      sm100::mbar_init(&dots_bar[b], 4u * (uint32_t)m);   // lanes 0, 8, 16, 24 of each warp
+      sm100::mbar_init(&u_bar[b], 4u);
+    }
     sm100::mbar_init(&ubar, 1);
     sm100::fence_mbar_init();
-    const uint32_t ub = (uint32_t)(nrows * sizeof(double));
-    sm100::mbar_arrive_expect_tx(&ubar, ub);
-    sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
   }
-  __syncthreads();
-  auto issue = [&](int chunk, int stage) {
-    if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
-    __syncwarp();
-    if (lane < m)
-      sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
-                       panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
-                       &full[stage]);
-  };
-  if (w == cw)
-    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
-  const int k0 = lane * FPL;
-  const bool whole = k0 + FPL <= K;
-  const int rem = K - k0;
-  float2 tv[FPL];
-#pragma unroll
-  for (int j = 0; j < FPL; ++j) {
-    const int k = k0 + j;
-    tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : make_float2(0.f, 0.f);
-  }
-  double coef = 0.0;
-  if (mode == 0 && w == cw) {
-    const double beta = scal[S_BETA];
-    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
-  }
-  float ah[FPL], al[FPL];
-#pragma unroll
-  for (int j = 0; j < FPL; ++j) ah[j] = al[j] = 0.f;
-  const int yr = lane >> 3, yg = lane & 7;
-  double nrm = 0.0;
+  __syncthreads();   // the only block-wide barrier
   bool ok = true;
-  if (w == cw && !sm100::mbar_wait(&ubar, 0)) ok = false;
-  int st_i = 0, ph_i = 0;
-  int st_u = 0;
-  for (int i = 0; i < nchunks + 2; ++i) {
-    if (i < nchunks && w != cw) {
-      if (!sm100::mbar_wait(&full[st_i], ph_i)) ok = false;
-      if (active) {
-        const float2* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
-        float2 d[kPipeRows];
-#pragma unroll
-        for (int r = 0; r < kPipeRows; ++r) {
-          float2 x[FPL];
-          load_slice_df<FPL>(sp + r * K, x, whole, rem);
-          float Sx = 0.f, Cx = 0.f;
-#pragma unroll
-          for (int j = 0; j < FPL; ++j) df_acc(Sx, Cx, x[j].x, x[j].y, tv[j].x, tv[j].y);
-          d[r] = make_float2(Sx, Cx);
-        }
-        const float2 tot = warp_sum4_df(d[0], d[1], d[2], d[3], lane);
-        if (yg == 0) sd[i & 1][w][yr] = tot;
-      }
+  const int yr = lane >> 3, yg = lane & 7;
+
+  if (w == cw) {
+    // ---------------------------------------------------------- control warp
+    auto issue = [&](int chunk, int stage) {
+      if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
+      __syncwarp();
+      if (lane < m)
+        sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
+                         panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
+                         &full[stage]);
+    };
+    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+    if (lane == 0) {
+      const uint32_t ub = (uint32_t)(nrows * sizeof(double));
+      sm100::mbar_arrive_expect_tx(&ubar, ub);
+      sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
     }
-    if (w == cw && i >= 1 && i <= nchunks) {
-      const int b = (i - 1) & 1;
+    double coef = 0.0;
+    if (mode == 0) {
+      const double beta = scal[S_BETA];
+      coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+    }
+    if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
+    double nrm = 0.0;
+    int st_r = 0, ph_r = 0;   // stage / empty parity of chunk j - 1
+    for (int j = 0; j < nchunks; ++j) {
+      const int b = j & 1;
+      if (!sm100::mbar_wait(&dots_bar[b], (j >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
       float2 part = make_float2(0.f, 0.f);
       for (int q = yg; q < m; q += 8) part = df_add(part, sd[b][q][yr]);
       part = df_add(part, df_shfl_xor(part, 4));
       part = df_add(part, df_shfl_xor(part, 2));
       part = df_add(part, df_shfl_xor(part, 1));
       if (yg == 0) {
-        const int pr = (i - 1) * kPipeRows + yr;
+        const int pr = j * kPipeRows + yr;   // row within the unit
         double out = 0.0;
         if (un.y + pr < cnt) {
           const double y = (double)part.x + (double)part.y;
@@ -1238,43 +1251,90 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
           nrm += out * out;
         }
         su[b][yr] = df_split(out);
+        sm100::mbar_arrive(&u_bar[b]);
+      }
+      // refill the stage of chunk j - 1 once every panel warp has updated with it
+      if (j >= 1) {
+        if (!sm100::mbar_wait(&empty[st_r], ph_r, ok ? sm100::kSpinLimit : 4u)) ok = false;
+        if (j - 1 + S < nchunks) {
+          sm100::fence_proxy_async_smem();
+          issue(j - 1 + S, st_r);
+        }
+        if (++st_r == S) {
+          st_r = 0;
+          ph_r ^= 1;
+        }
       }
     }
-    if (i >= 2 && active) {
-      const float2* sp = ring + st_u * stage_elems + (int64_t)w * kPipeRows * K + k0;
-      const int b = i & 1;
+    if (!ok && lane == 0) atomicOr(&flags[3], 1);
+    const double tot = warp_sum<double>(nrm);
+    if (lane == 0) norm_partial[blockIdx.x] = tot;
+    return;
+  }
+  if (!active) return;
+
+  // ------------------------------------------------------------ panel warps
+  const int k0 = lane * FPL;   // lane slice of the features: k = lane * FPL + j
+  const bool whole = k0 + FPL <= K;
+  const int rem = K - k0;
+  float2 tv[FPL];
 #pragma unroll
-      for (int r = 0; r < kPipeRows; ++r) {
-        const float2 ur = su[b][r];
-        float2 x[FPL];
-        load_slice_df<FPL>(sp + r * K, x, whole, rem);
+  for (int j = 0; j < FPL; ++j) {
+    const int k = k0 + j;
+    tv[j] = k < K ? tvec[(int64_t)s * K + k] : make_float2(0.f, 0.f);
+  }
+  float ah[FPL], al[FPL];
 #pragma unroll
-        for (int j = 0; j < FPL; ++j) df_acc(ah[j], al[j], x[j].x, x[j].y, ur.x, ur.y);
-      }
+  for (int j = 0; j < FPL; ++j) ah[j] = al[j] = 0.f;
+  // update with chunk i (rows of stage st, u' slot i & 1), then free the stage
+  auto update = [&](int i, int st) {
+    const int b = i & 1;
+    if (!sm100::mbar_wait(&u_bar[b], (i >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
+    const float2* sp = ring + st * stage_elems + (int64_t)w * kPipeRows * K + k0;
+#pragma unroll
+    for (int r = 0; r < kPipeRows; ++r) {
+      const float2 ur = su[b][r];
+      float2 x[FPL];
+      load_slice_df<FPL>(sp + r * K, x, whole, rem);
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) df_acc(ah[j], al[j], x[j].x, x[j].y, ur.x, ur.y);
     }
-    __syncthreads();
-    if (w == cw && i >= 2 && i - 2 + S < nchunks) {
-      sm100::fence_proxy_async_smem();
-      issue(i - 2 + S, st_u);
+    __syncwarp();
+    if (lane == 0) sm100::mbar_arrive(&empty[st]);
+  };
+  int st_i = 0, ph_i = 0, st_prev = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    if (!sm100::mbar_wait(&full[st_i], ph_i, ok ? sm100::kSpinLimit : 4u)) ok = false;
+    const float2* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    float2 d[kPipeRows];
+#pragma unroll
+    for (int r = 0; r < kPipeRows; ++r) {
+      float2 x[FPL];
+      load_slice_df<FPL>(sp + r * K, x, whole, rem);
+      float Sx = 0.f, Cx = 0.f;
+#pragma unroll
+      for (int j = 0; j < FPL; ++j) df_acc(Sx, Cx, x[j].x, x[j].y, tv[j].x, tv[j].y);
+      d[r] = make_float2(Sx, Cx);
     }
-    if (i >= 2) st_u = st_u + 1 == S ? 0 : st_u + 1;
-    if (i < nchunks && ++st_i == S) {
+    const float2 tot = warp_sum4_df(d[0], d[1], d[2], d[3], lane);
+    if (yg == 0) {
+      sd[i & 1][w][yr] = tot;
+      sm100::mbar_arrive(&dots_bar[i & 1]);
+    }
+    if (i >= 1) update(i - 1, st_prev);
+    st_prev = st_i;
+    if (++st_i == S) {
       st_i = 0;
       ph_i ^= 1;
     }
   }
+  if (nchunks >= 1) update(nchunks - 1, st_prev);
   if (!ok && lane == 0) atomicOr(&flags[3], 1);
-  if (active) {
-    const int64_t base_idx = (int64_t)(un.w + w) * K;
+  const int64_t base_idx = (int64_t)(un.w + w) * K;
 #pragma unroll
-    for (int j = 0; j < FPL; ++j) {
-      const int k = k0 + j;
-      if (k < K) reinterpret_cast<float2*>(partial)[base_idx + k] = make_float2(ah[j], -al[j]);
-    }
-  }
-  if (w == cw) {
-    const double tot = warp_sum<double>(nrm);
-    if (lane == 0) norm_partial[blockIdx.x] = tot;
+  for (int j = 0; j < FPL; ++j) {
+    const int k = k0 + j;
+    if (k < K) reinterpret_cast<float2*>(partial)[base_idx + k] = make_float2(ah[j], -al[j]);
   }
 }
 
@@ -1584,6 +1644,18 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   return true;
 }
 
+// Shared memory for the fused pass's ring and staged u values, per CTA (one
+// CTA per SM).  ELMFB_FUSED_SMEM_KB overrides the default (a tuning knob; the
+// stage count changes timing only, never the arithmetic).
+static size_t fused_ring_budget() {
+  static const size_t kb = [] {
+    const char* e = getenv("ELMFB_FUSED_SMEM_KB");
+    const long v = e ? atol(e) : 0;
+    return (size_t)(v >= 64 && v <= 220 ? v : 200);
+  }();
+  return kb * 1024;
+}
+
 template <class T>
 void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, double* scal,
                   double* gpart, const void* tlow) {
@@ -1603,7 +1675,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     const size_t stage_bytes = (size_t)mmax * kPipeRows * K * sizeof(float2);
     const size_t u_bytes = kMaxUnitRows * sizeof(double);
     const int S = (int)std::min<size_t>(kPipeMaxStages,
-                                        (200 * 1024 - u_bytes) / std::max<size_t>(stage_bytes, 1));
+                                        (fused_ring_budget() - u_bytes) / std::max<size_t>(stage_bytes, 1));
     const int pthreads = fthreads + 32;
     if (S < 4 || pthreads > 1024 || K % 2 != 0 || fpl > 4)
       ELMFB_THROW(ELMFB_ERR_UNSUPPORTED,
@@ -1645,7 +1717,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
   const size_t stage_bytes = (size_t)mmax * kPipeRows * K * sizeof(T);
   const size_t u_bytes = kMaxUnitRows * sizeof(double);
   const int S = (int)std::min<size_t>(kPipeMaxStages,
-                                      (200 * 1024 - u_bytes) / std::max<size_t>(stage_bytes, 1));
+                                      (fused_ring_budget() - u_bytes) / std::max<size_t>(stage_bytes, 1));
   const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
   // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
   // ring needs two stages in use plus at least two in flight
