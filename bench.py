@@ -39,8 +39,10 @@ METRIC = "ELM-FBPINN time-to-solution (s) at oracle-matched L2 error; assembly H
 # workload -> (problem, oracle golden name, panel precision)
 WORKLOADS = {
     "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400", "fp32"),
-    "dho_ml": (WL.config_dho_ml, "dho_L1-64_K96_N20000", "fp64"),
-    "poisson1d": (WL.config_poisson1d, "poisson1d_J16_K64_N2000", "fp64"),
+    # FP64-accuracy workloads run FP32-pair (DF32) panels: FP32 storage is an
+    # accuracy floor for them, and GB300's FP64 rate is 1/64 of FP32
+    "dho_ml": (WL.config_dho_ml, "dho_L1-64_K96_N20000", "df32"),
+    "poisson1d": (WL.config_poisson1d, "poisson1d_J16_K64_N2000", "df32"),
     # a quarter-size case of the 2-D workload (same levels and K; inputs still
     # larger than L2) for ncu captures that must stay small
     "poisson2d_ml_n200": (lambda: WL.poisson2d(levels=(1, 2, 4, 8, 16), features=128, n_side=200,
