@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(128) k_assemble(
     const int* __restrict__ cover_start, const int* __restrict__ entry_cell,
     const int* __restrict__ cell_level_off, const int* __restrict__ cell_count,
     const int* __restrict__ cell_pstart, const int64_t* __restrict__ panel_off,
+    const int64_t* __restrict__ entry_base, const int* __restrict__ cover_off,
     const double* __restrict__ xs, const int* __restrict__ rcls,
     const RowClass* __restrict__ c_cls,
     const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels,
@@ -340,7 +341,9 @@ __global__ void __launch_bounds__(128) k_assemble(
   const int pad = cell_pstart[c + 1] - cell_pstart[c];
   const int nrows = min(32, pad - p0);
   const int64_t R0 = cell_pstart[c] + p0;
-  T* out = panels + (panel_off[s] + cover_start[e] + p0) * (int64_t)K;
+  // cell-interleaved storage: row p of entry e at element row entry_base[e] + p m_c
+  const int64_t rstride = (int64_t)(cover_off[c + 1] - cover_off[c]) * K;
+  T* out = panels + entry_base[e] * (int64_t)K + (int64_t)p0 * rstride;
 
   // phase 1: lane = row
   T A = 0, be0 = 0, be1 = 0, ga0 = 0, ga1 = 0, xt0 = 0, xt1 = 0;
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(128) k_assemble(
     const T rg1 = __shfl_sync(0xffffffffu, ga1, r);
     const T rx0 = __shfl_sync(0xffffffffu, xt0, r);
     const T rx1 = __shfl_sync(0xffffffffu, xt1, r);
-    T* orow = out + (int64_t)r * K;
+    T* orow = out + (int64_t)r * rstride;
 #pragma unroll
     for (int i = 0; i < FPL; ++i) {
       int k = lane + 32 * i;
@@ -446,7 +449,8 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
-          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
+          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
+          h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p,             \
           h->d_pt.as<__nv_bfloat16>(), h->NPR);                                              \
     else if (split)                                                                          \
@@ -454,7 +458,8 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
-          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
+          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
+          h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
           h->NPR);                                                                           \
     else                                                                                     \
@@ -462,7 +467,8 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
           h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
           h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
-          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(), h->d_x.as<double>(),     \
+          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
+          h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
           h->NPR);                                                                           \
     break;
@@ -496,7 +502,7 @@ __global__ void k_export_rows(const int64_t* __restrict__ rows, int64_t n,
                               const int* __restrict__ grow_cell, const int* __restrict__ cell_pstart,
                               const int* __restrict__ cover_off, const int* __restrict__ cover_sub,
                               const int* __restrict__ cover_start,
-                              const int64_t* __restrict__ panel_off, const T* __restrict__ panels,
+                              const int64_t* __restrict__ entry_base, const T* __restrict__ panels,
                               int K, int64_t NPhi, const double* __restrict__ hvec,
                               double* __restrict__ out, double* __restrict__ hout) {
   int64_t i = blockIdx.x;
@@ -507,7 +513,8 @@ __global__ void k_export_rows(const int64_t* __restrict__ rows, int64_t n,
   if (threadIdx.x == 0 && hout) hout[i] = hvec[R];
   for (int e = cover_off[c]; e < cover_off[c + 1]; ++e) {
     int s = cover_sub[e];
-    const T* src = panels + (panel_off[s] + cover_start[e] + p) * (int64_t)K;
+    const int64_t mc = cover_off[c + 1] - cover_off[c];
+    const T* src = panels + (entry_base[e] + (int64_t)p * mc) * (int64_t)K;
     for (int k = threadIdx.x; k < K; k += blockDim.x)
       out[i * NPhi + (int64_t)s * K + k] = value_of(src[k]);
   }
@@ -617,6 +624,16 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   }
   for (int s = 0; s < h->n_sub; ++s) h->panel_off[s + 1] = h->panel_off[s] + panel_len[s];
   h->NPR = h->panel_off[h->n_sub];
+  // cell-interleaved element rows (see elmfb_ctx::cell_eoff)
+  h->cell_eoff.assign(nc + 1, 0);
+  for (int c = 0; c < nc; ++c)
+    h->cell_eoff[c + 1] = h->cell_eoff[c] + (int64_t)(h->cell_pstart[c + 1] - h->cell_pstart[c]) *
+                                                (h->cover_off[c + 1] - h->cover_off[c]);
+  h->entry_base.assign(ne, 0);
+  for (int e = 0; e < ne; ++e) {
+    const int c = h->entry_cell[e];
+    h->entry_base[e] = h->cell_eoff[c] + (e - h->cover_off[c]);
+  }
   if (h->NPR >= (int64_t)1 << 31) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "more than 2^31 panel rows");
   h->nnz = 0;
   std::vector<int2> tiles;
@@ -643,6 +660,8 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   up(h->d_cell_pstart, h->cell_pstart.data(), (nc + 1) * sizeof(int));
   up(h->d_cover_start, h->cover_start.data(), ne * sizeof(int));
   up(h->d_panel_off, h->panel_off.data(), (h->n_sub + 1) * sizeof(int64_t));
+  up(h->d_cell_eoff, h->cell_eoff.data(), (nc + 1) * sizeof(int64_t));
+  up(h->d_entry_base, h->entry_base.data(), ne * sizeof(int64_t));
   up(h->d_tiles, tiles.data(), tiles.size() * sizeof(int2));
 
   // K0: scatter into cells, deterministic order inside each cell, gather row data
@@ -759,19 +778,19 @@ void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, doub
     k_export_rows<df2><<<(unsigned)n, 128, 0, st>>>(
         drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
         h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
-        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), h->d_panels.as<df2>(), h->K,
+        h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(), h->d_panels.as<df2>(), h->K,
         h->NPhi, h->d_h.as<double>(), dout.as<double>(), dh.as<double>());
   else if (h->fp64())
     k_export_rows<double><<<(unsigned)n, 128, 0, st>>>(
         drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
         h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
-        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), h->d_panels.as<double>(), h->K,
+        h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(), h->d_panels.as<double>(), h->K,
         h->NPhi, h->d_h.as<double>(), dout.as<double>(), dh.as<double>());
   else
     k_export_rows<float><<<(unsigned)n, 128, 0, st>>>(
         drows.as<int64_t>(), n, h->d_u2s.as<int>(), h->d_grow_cell.as<int>(),
         h->d_cell_pstart.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
-        h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), h->d_panels.as<float>(), h->K,
+        h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(), h->d_panels.as<float>(), h->K,
         h->NPhi, h->d_h.as<double>(), dout.as<double>(), dh.as<double>());
   check_launch("k_export_rows");
   count_launch(h);

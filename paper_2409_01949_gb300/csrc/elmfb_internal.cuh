@@ -141,8 +141,14 @@ struct elmfb_ctx {
   DevBuf d_h;           // [NR] scaled rhs (sorted order)
   DevBuf d_grow_cell;   // [NR] cell of each sorted row
   DevBuf d_u2s;         // [n_rows] sorted position of each user row
-  DevBuf d_cover_start, d_panel_off;
-  DevBuf d_panels;      // [NPR*K] FP64 or FP32
+  DevBuf d_cover_start, d_panel_off;   // per-panel row numbering (BF16 copy, Gram pairs)
+  // Panel storage is cell-interleaved: the rows of cell c start at element row
+  // cell_eoff[c]; row p holds the K entries of each of the cell's m_c covering
+  // panels in turn, so entry e = (c, panel w) row p sits at element row
+  // entry_base[e] + p m_c with entry_base[e] = cell_eoff[c] + w.
+  std::vector<int64_t> cell_eoff, entry_base;
+  DevBuf d_cell_eoff, d_entry_base;
+  DevBuf d_panels;      // [NPR*K] FP64, FP32 or FP32 pairs
   DevBuf d_tiles;       // assembly / transpose-product tiles: (entry, first row)
   int64_t n_tiles = 0;
   std::vector<int> entry_cell;   // [n_entries]

@@ -201,13 +201,35 @@ __device__ __forceinline__ void load_slice_df(const float2* p, float2 (&x)[FPL],
 // reads two float4 from shared memory and does 16 FMAs.  Products are summed
 // in FP32 over 16 rows, those sums Kahan-compensated in FP32 over the chunk,
 // and the result stored in FP64 (upper triangle, row-major, K(K+1)/2 values).
+// A diagonal-Gram chunk is a run of 16-row steps of one panel; step (e, p0)
+// covers rows p0 .. p0+15 of entry e (cell c, covering panel w), which sit at
+// element rows entry_base[e] + p m_c in the cell-interleaved storage.
+struct DiagStepRows {
+  int64_t row0;   // element row of the step's first row
+  int64_t mK;     // element stride between its rows (m_c K)
+};
+__device__ __forceinline__ DiagStepRows diag_step(const int2* __restrict__ steps,
+                                                  const int64_t* __restrict__ entry_base,
+                                                  const int* __restrict__ entry_cell,
+                                                  const int* __restrict__ cover_off, int q,
+                                                  int K) {
+  const int2 st = steps[q];
+  const int c = entry_cell[st.x];
+  const int64_t m = cover_off[c + 1] - cover_off[c];
+  return {entry_base[st.x] + (int64_t)st.y * m, m * K};
+}
+
 template <class T>
 __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__ panels, int K,
                                                             const int4* __restrict__ chunks,
+                                                            const int2* __restrict__ steps,
+                                                            const int64_t* __restrict__ entry_base,
+                                                            const int* __restrict__ entry_cell,
+                                                            const int* __restrict__ cover_off,
                                                             double* __restrict__ partial) {
   extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);   // [16][Kp]
-  const int4 ch = chunks[blockIdx.x];     // (panel, row0, nrows, -)
+  const int4 ch = chunks[blockIdx.x];     // (panel, first step, steps, -)
   const int Kp = (K + 3) & ~3;
   const int TT = Kp / 4;
   const int ntiles = TT * (TT + 1) / 2;
@@ -226,13 +248,13 @@ __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = T(0);
-  const T* base = panels + (int64_t)ch.y * K;
-  for (int r0 = 0; r0 < ch.z; r0 += 16) {
-    const int nr = min(16, ch.z - r0);
+  for (int q = 0; q < ch.z; ++q) {
+    const DiagStepRows sr = diag_step(steps, entry_base, entry_cell, cover_off, ch.y + q, K);
+    const T* base = panels + sr.row0 * K;
     __syncthreads();
     for (int t = threadIdx.x; t < 16 * Kp; t += blockDim.x) {
       const int r = t / Kp, k = t - r * Kp;
-      sm[t] = (r < nr && k < K) ? base[(int64_t)(r0 + r) * K + k] : T(0);
+      sm[t] = k < K ? base[(int64_t)r * sr.mK + k] : T(0);
     }
     __syncthreads();
     if (ti < 0) continue;
@@ -295,12 +317,16 @@ constexpr int kDiagStages = 6;
 template <class T>
 __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ panels, int K,
                                                          const int4* __restrict__ chunks,
+                                                         const int2* __restrict__ steps,
+                                                         const int64_t* __restrict__ entry_base,
+                                                         const int* __restrict__ entry_cell,
+                                                         const int* __restrict__ cover_off,
                                                          double* __restrict__ partial,
                                                          int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char smraw[];
   T* ring = reinterpret_cast<T*>(smraw);   // [kDiagStages][16][K]
   __shared__ __align__(8) uint64_t full[kDiagStages];
-  const int4 ch = chunks[blockIdx.x];     // (panel, row0, nrows, -)
+  const int4 ch = chunks[blockIdx.x];   // (panel, first step, steps, -)
   const int TT = K / 4;
   const int ntiles = TT * (TT + 1) / 2;
   int ti = -1, tj = -1;
@@ -313,18 +339,25 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
     }
     tj = ti + rem;
   }
-  const int nsteps = ch.z / 16;
+  const int nsteps = ch.z;
   const uint32_t step_bytes = (uint32_t)(16 * K * sizeof(T));
-  const T* base = panels + (int64_t)ch.y * K;
+  // warp 0: lane i copies row i of a step (rows are m_c K elements apart)
+  auto issue = [&](int q, int st) {
+    const DiagStepRows sr = diag_step(steps, entry_base, entry_cell, cover_off, ch.y + q, K);
+    if (threadIdx.x == 0) sm100::mbar_arrive_expect_tx(&full[st], step_bytes);
+    __syncwarp();
+    if (threadIdx.x < 16)
+      sm100::bulk_load(ring + ((int64_t)st * 16 + threadIdx.x) * K,
+                       panels + (sr.row0 * K + (int64_t)threadIdx.x * sr.mK),
+                       (uint32_t)(K * sizeof(T)), &full[st]);
+  };
   if (threadIdx.x == 0) {
     for (int q = 0; q < kDiagStages; ++q) sm100::mbar_init(&full[q], 1);
     sm100::fence_mbar_init();
-    for (int q = 0; q < kDiagStages && q < nsteps; ++q) {
-      sm100::mbar_arrive_expect_tx(&full[q], step_bytes);
-      sm100::bulk_load(ring + (int64_t)q * 16 * K, base + (int64_t)q * 16 * K, step_bytes,
-                       &full[q]);
-    }
   }
+  __syncwarp();
+  if (threadIdx.x < 32)
+    for (int q = 0; q < kDiagStages && q < nsteps; ++q) issue(q, q);
   __syncthreads();
   T hi[4][4], lo[4][4];
 #pragma unroll
@@ -370,11 +403,9 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && q + kDiagStages < nsteps) {
+    if (threadIdx.x < 32 && q + kDiagStages < nsteps) {
       sm100::fence_proxy_async_smem();
-      sm100::mbar_arrive_expect_tx(&full[st], step_bytes);
-      sm100::bulk_load(ring + (int64_t)st * 16 * K, base + (int64_t)(q + kDiagStages) * 16 * K,
-                       step_bytes, &full[st]);
+      issue(q + kDiagStages, st);
     }
   }
   if (!ok) atomicOr(&flags[3], 1);
@@ -398,12 +429,16 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
 // per thread), FP64 result.  Requires K % 4 == 0.
 __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restrict__ panels,
                                                             int K, const int4* __restrict__ chunks,
+                                                                   const int2* __restrict__ steps,
+                                                                   const int64_t* __restrict__ entry_base,
+                                                                   const int* __restrict__ entry_cell,
+                                                                   const int* __restrict__ cover_off,
                                                             double* __restrict__ partial,
                                                             int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char smraw[];
   float2* ring = reinterpret_cast<float2*>(smraw);   // [kDiagStages][16][K]
   __shared__ __align__(8) uint64_t full[kDiagStages];
-  const int4 ch = chunks[blockIdx.x];
+  const int4 ch = chunks[blockIdx.x];   // (panel, first step, steps, -)
   const int TT = K / 4;
   const int ntiles = TT * (TT + 1) / 2;
   int ti = -1, tj = -1;
@@ -416,18 +451,25 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
     }
     tj = ti + rem;
   }
-  const int nsteps = ch.z / 16;
+  const int nsteps = ch.z;
   const uint32_t step_bytes = (uint32_t)(16 * K * sizeof(float2));
-  const float2* base = panels + (int64_t)ch.y * K;
+  // warp 0: lane i copies row i of a step (rows are m_c K elements apart)
+  auto issue = [&](int q, int st) {
+    const DiagStepRows sr = diag_step(steps, entry_base, entry_cell, cover_off, ch.y + q, K);
+    if (threadIdx.x == 0) sm100::mbar_arrive_expect_tx(&full[st], step_bytes);
+    __syncwarp();
+    if (threadIdx.x < 16)
+      sm100::bulk_load(ring + ((int64_t)st * 16 + threadIdx.x) * K,
+                       panels + (sr.row0 * K + (int64_t)threadIdx.x * sr.mK),
+                       (uint32_t)(K * sizeof(float2)), &full[st]);
+  };
   if (threadIdx.x == 0) {
     for (int q = 0; q < kDiagStages; ++q) sm100::mbar_init(&full[q], 1);
     sm100::fence_mbar_init();
-    for (int q = 0; q < kDiagStages && q < nsteps; ++q) {
-      sm100::mbar_arrive_expect_tx(&full[q], step_bytes);
-      sm100::bulk_load(ring + (int64_t)q * 16 * K, base + (int64_t)q * 16 * K, step_bytes,
-                       &full[q]);
-    }
   }
+  __syncwarp();
+  if (threadIdx.x < 32)
+    for (int q = 0; q < kDiagStages && q < nsteps; ++q) issue(q, q);
   __syncthreads();
   float S[4][4], C[4][4];
 #pragma unroll
@@ -455,11 +497,9 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && q + kDiagStages < nsteps) {
+    if (threadIdx.x < 32 && q + kDiagStages < nsteps) {
       sm100::fence_proxy_async_smem();
-      sm100::mbar_arrive_expect_tx(&full[st], step_bytes);
-      sm100::bulk_load(ring + (int64_t)st * 16 * K, base + (int64_t)(q + kDiagStages) * 16 * K,
-                       step_bytes, &full[st]);
+      issue(q + kDiagStages, st);
     }
     if (++st == kDiagStages) {
       st = 0;
@@ -663,7 +703,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(
     const int* __restrict__ grow_cell, const int* __restrict__ cell_pstart,
     const int* __restrict__ cell_count, const int* __restrict__ cover_off,
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
-    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ norm_partial) {
   __shared__ double red[33];
@@ -683,7 +723,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(
     if (p < cell_count[c]) {
       for (int e = cover_off[c]; e < cover_off[c + 1]; ++e) {
         const int s = cover_sub[e];
-        const T* row = panels + (panel_off[s] + cover_start[e] + p) * (int64_t)K;
+        const T* row =
+            panels + (entry_base[e] + (int64_t)p * (cover_off[c + 1] - cover_off[c])) * (int64_t)K;
         const double* tv = tvec + (int64_t)s * K;
         T part = 0;
         for (int k = lane; k < K; k += 32) part += row[k] * (T)tv[k];
@@ -709,17 +750,18 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
                                                  const double* __restrict__ u, int K,
                                                  const int* __restrict__ entry_cell,
                                                  const int* __restrict__ cover_sub,
-                                                 const int* __restrict__ cover_start,
+                                                 const int* __restrict__ cover_off,
                                                  const int* __restrict__ cell_pstart,
                                                  const int* __restrict__ cell_count,
-                                                 const int64_t* __restrict__ panel_off,
+                                                 const int64_t* __restrict__ entry_base,
                                                  double* __restrict__ partial) {
   const int e = blockIdx.x;
   const int c = entry_cell[e];
   const int cnt = cell_count[c];
   const int64_t R0 = cell_pstart[c];
   const int s = cover_sub[e];
-  const T* base = panels + (panel_off[s] + cover_start[e]) * (int64_t)K;
+  const T* base = panels + entry_base[e] * (int64_t)K;
+  const int64_t rs = (int64_t)(cover_off[c + 1] - cover_off[c]) * K;   // row stride
   double* out = partial + (int64_t)e * K;
   if (cnt == 0) {
     for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = 0.0;
@@ -729,12 +771,12 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
     if (sizeof(T) == 8) {
-      for (int p = 0; p < cnt; ++p) acc += (double)base[(int64_t)p * K + k] * us[p];
+      for (int p = 0; p < cnt; ++p) acc += (double)base[(int64_t)p * rs + k] * us[p];
     } else {
       float a32 = 0.f;
       int p = 0;
       for (; p < cnt; ++p) {
-        a32 += (float)base[(int64_t)p * K + k] * (float)us[p];
+        a32 += (float)base[(int64_t)p * rs + k] * (float)us[p];
         if ((p & 31) == 31) {
           acc += a32;
           a32 = 0.f;
@@ -762,7 +804,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
     const int* __restrict__ cell_count, const int* __restrict__ cover_off,
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
-    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial) {
   __shared__ double sd[32][kFusedRows];
@@ -777,7 +819,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
   const bool active = w < m;
   const int e = cover_off[c] + (active ? w : 0);
   const int s = cover_sub[e];
-  const T* base = panels + (panel_off[s] + cover_start[e]) * (int64_t)K;
+  const T* base = panels + entry_base[e] * (int64_t)K;   // row r at base + r m K
+  const int64_t rs = (int64_t)m * K;
   T tv[FPL];
 #pragma unroll
   for (int j = 0; j < FPL; ++j) {
@@ -804,7 +847,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
 #pragma unroll
       for (int j = 0; j < FPL; ++j) {
         const int k = lane + 32 * j;
-        dst[r][j] = (active && r < nr && k < K) ? base[(int64_t)(r0 + r) * K + k] : T(0);
+        dst[r][j] = (active && r < nr && k < K) ? base[(int64_t)(r0 + r) * rs + k] : T(0);
       }
     const int p = r0 + (int)threadIdx.x;
     uo = 0.0;
@@ -959,7 +1002,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
     const int* __restrict__ cell_count, const int* __restrict__ cover_off,
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
-    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
     int* __restrict__ flags) {
@@ -971,7 +1014,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   __shared__ __align__(8) uint64_t ubar;                    // the unit's u / h values in
   __shared__ T sd[2][32][kPipeRows];
   __shared__ T su[2][kPipeRows];
-  __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
   T* ring = reinterpret_cast<T*>(ring_raw);
   const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(T));
@@ -987,7 +1029,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const uint32_t copy_bytes = (uint32_t)(kPipeRows * K * sizeof(T));
   const int nrows = un.z - un.y;
   const int nchunks = nrows / kPipeRows;
-  if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
+  // the unit's rows of all m covering panels form one contiguous block
+  // (cell-interleaved storage): chunk q = element rows base_row + q kPipeRows m ...
+  const int64_t base_row = entry_base[cover_off[c]] + (int64_t)un.y * m;
   if (threadIdx.x == 0) {
     for (int q = 0; q < S; ++q) {
       sm100::mbar_init(&full[q], 1);
@@ -1007,12 +1051,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   if (w == cw) {
     // ---------------------------------------------------------- control warp
     auto issue = [&](int chunk, int stage) {
-      if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
-      __syncwarp();
-      if (lane < m)
-        sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
-                         panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
-                         &full[stage]);
+      if (lane == 0) {
+        sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
+        sm100::bulk_load(ring + stage * stage_elems,
+                         panels + (base_row + (int64_t)chunk * kPipeRows * m) * K,
+                         copy_bytes * (uint32_t)m, &full[stage]);
+      }
     };
     for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
     if (lane == 0) {
@@ -1085,7 +1129,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   auto update = [&](int i, int st) {
     const int b = i & 1;
     if (!sm100::mbar_wait(&u_bar[b], (i >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
-    const T* sp = ring + st * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    const T* sp = ring + st * stage_elems + (int64_t)w * K + k0;   // row r at + r m K
     T acc[FPL];
 #pragma unroll
     for (int j = 0; j < FPL; ++j) acc[j] = T(0);
@@ -1093,7 +1137,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     for (int r = 0; r < kPipeRows; ++r) {
       const T ur = su[b][r];
       T x[FPL];
-      load_slice<T, FPL>(sp + r * K, x, whole, rem);
+      load_slice<T, FPL>(sp + (int64_t)r * m * K, x, whole, rem);
 #pragma unroll
       for (int j = 0; j < FPL; ++j) acc[j] += x[j] * ur;
     }
@@ -1115,12 +1159,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   int st_i = 0, ph_i = 0, st_prev = 0;
   for (int i = 0; i < nchunks; ++i) {
     if (!sm100::mbar_wait(&full[st_i], ph_i, ok ? sm100::kSpinLimit : 4u)) ok = false;
-    const T* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    const T* sp = ring + st_i * stage_elems + (int64_t)w * K + k0;   // row r at + r m K
     T d[kPipeRows];
 #pragma unroll
     for (int r = 0; r < kPipeRows; ++r) {
       T x[FPL];
-      load_slice<T, FPL>(sp + r * K, x, whole, rem);
+      load_slice<T, FPL>(sp + (int64_t)r * m * K, x, whole, rem);
       d[r] = T(0);
 #pragma unroll
       for (int j = 0; j < FPL; ++j) d[r] += x[j] * tv[j];
@@ -1163,7 +1207,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
     const int* __restrict__ cell_count, const int* __restrict__ cover_off,
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
-    const int64_t* __restrict__ panel_off, const double* __restrict__ scal,
+    const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
     int* __restrict__ flags) {
@@ -1175,7 +1219,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   __shared__ __align__(8) uint64_t ubar;                    // the unit's u / h values in
   __shared__ float2 sd[2][32][kPipeRows];
   __shared__ float2 su[2][kPipeRows];
-  __shared__ int64_t srow[32];   // first panel row of the unit, per covering panel
   float2* ring = reinterpret_cast<float2*>(ring_raw);
   const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(float2));
@@ -1191,7 +1234,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   const uint32_t copy_bytes = (uint32_t)(kPipeRows * K * sizeof(float2));
   const int nrows = un.z - un.y;
   const int nchunks = nrows / kPipeRows;
-  if (active && lane == 0) srow[w] = panel_off[s] + cover_start[cover_off[c] + w] + un.y;
+  // the unit's rows of all m covering panels form one contiguous block
+  // (cell-interleaved storage): chunk q = element rows base_row + q kPipeRows m ...
+  const int64_t base_row = entry_base[cover_off[c]] + (int64_t)un.y * m;
   if (threadIdx.x == 0) {
     for (int q = 0; q < S; ++q) {
       sm100::mbar_init(&full[q], 1);
@@ -1211,12 +1256,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   if (w == cw) {
     // ---------------------------------------------------------- control warp
     auto issue = [&](int chunk, int stage) {
-      if (lane == 0) sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
-      __syncwarp();
-      if (lane < m)
-        sm100::bulk_load(ring + stage * stage_elems + (int64_t)lane * kPipeRows * K,
-                         panels + (srow[lane] + (int64_t)chunk * kPipeRows) * K, copy_bytes,
-                         &full[stage]);
+      if (lane == 0) {
+        sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
+        sm100::bulk_load(ring + stage * stage_elems,
+                         panels + (base_row + (int64_t)chunk * kPipeRows * m) * K,
+                         copy_bytes * (uint32_t)m, &full[stage]);
+      }
     };
     for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
     if (lane == 0) {
@@ -1290,12 +1335,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   auto update = [&](int i, int st) {
     const int b = i & 1;
     if (!sm100::mbar_wait(&u_bar[b], (i >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
-    const float2* sp = ring + st * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    const float2* sp = ring + st * stage_elems + (int64_t)w * K + k0;   // row r at + r m K
 #pragma unroll
     for (int r = 0; r < kPipeRows; ++r) {
       const float2 ur = su[b][r];
       float2 x[FPL];
-      load_slice_df<FPL>(sp + r * K, x, whole, rem);
+      load_slice_df<FPL>(sp + (int64_t)r * m * K, x, whole, rem);
 #pragma unroll
       for (int j = 0; j < FPL; ++j) df_acc(ah[j], al[j], x[j].x, x[j].y, ur.x, ur.y);
     }
@@ -1305,12 +1350,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   int st_i = 0, ph_i = 0, st_prev = 0;
   for (int i = 0; i < nchunks; ++i) {
     if (!sm100::mbar_wait(&full[st_i], ph_i, ok ? sm100::kSpinLimit : 4u)) ok = false;
-    const float2* sp = ring + st_i * stage_elems + (int64_t)w * kPipeRows * K + k0;
+    const float2* sp = ring + st_i * stage_elems + (int64_t)w * K + k0;   // row r at + r m K
     float2 d[kPipeRows];
 #pragma unroll
     for (int r = 0; r < kPipeRows; ++r) {
       float2 x[FPL];
-      load_slice_df<FPL>(sp + r * K, x, whole, rem);
+      load_slice_df<FPL>(sp + (int64_t)r * m * K, x, whole, rem);
       float Sx = 0.f, Cx = 0.f;
 #pragma unroll
       for (int j = 0; j < FPL; ++j) df_acc(Sx, Cx, x[j].x, x[j].y, tv[j].x, tv[j].y);
@@ -1688,7 +1733,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     k_fused_pipe_df<F><<<fp.n_units, pthreads, smem, st>>>(                                     \
         h->d_panels.as<float2>(), (const float2*)tlow, K, fp.units.as<int4>(),                  \
         h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), h->d_cover_off.as<int>(),        \
-        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(),    \
+        h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(),    \
         scal, h->d_u.as<double>(), h->d_h.as<double>(), mode, fp.part.as<double>(), gpart, S,   \
         mmax, h->d_flags.as<int>());                                                            \
   }
@@ -1731,7 +1776,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     k_fused_pipe<T, F><<<fp.n_units, pthreads, smem, st>>>(                                    \
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
-        h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
+        h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
         fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>());                           \
   } else
     ELMFB_FT(1) ELMFB_FT(2) ELMFB_FT(3) ELMFB_FT(4)
@@ -1743,7 +1788,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     k_fused<T, F, MT><<<fp.n_units, fthreads, 0, st>>>(                                      \
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),      \
-        h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
+        h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
         fp.part.as<double>(), gpart);                                                        \
   } else
 #define ELMFB_FU4(F) ELMFB_FU(F, 256) ELMFB_FU(F, 512) ELMFB_FU(F, 640) ELMFB_FU(F, 1024)
@@ -1769,22 +1814,43 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   h->d_R.alloc(2 * h->n_sub * KK * sizeof(double), st);
   if (identity) return;
   if (K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up supports K <= 128");
-  // chunks of at most 2048 panel rows
+  // chunks of at most 2048 rows of one panel, as 16-row steps (entry, first
+  // row) taken cell by cell in the cell-interleaved storage
+  const int ne = (int)h->cover_sub.size();
+  std::vector<std::vector<int>> pent(h->n_sub);
+  for (int e = 0; e < ne; ++e) pent[h->cover_sub[e]].push_back(e);
   std::vector<int4> chunks;
+  std::vector<int2> steps;
   std::vector<int> chunk_off(h->n_sub + 1, 0);
+  constexpr int kStepsPerChunk = kDiagChunk / 16;
   for (int s = 0; s < h->n_sub; ++s) {
     chunk_off[s] = (int)chunks.size();
-    for (int64_t r = h->panel_off[s]; r < h->panel_off[s + 1]; r += kDiagChunk)
-      chunks.push_back(
-          make_int4(s, (int)r, (int)std::min<int64_t>(kDiagChunk, h->panel_off[s + 1] - r), 0));
+    int first = (int)steps.size();
+    for (int e : pent[s]) {
+      const int c = h->entry_cell[e];
+      const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
+      for (int p0 = 0; p0 < pad; p0 += 16) {
+        steps.push_back(make_int2(e, p0));
+        if ((int)steps.size() - first == kStepsPerChunk) {
+          chunks.push_back(make_int4(s, first, kStepsPerChunk, 0));
+          first = (int)steps.size();
+        }
+      }
+    }
+    if ((int)steps.size() > first)
+      chunks.push_back(make_int4(s, first, (int)steps.size() - first, 0));
   }
   chunk_off[h->n_sub] = (int)chunks.size();
   const int KT = K * (K + 1) / 2;
-  DevBuf dch, dcoff;
+  DevBuf dch, dcoff, dsteps;
   dch.alloc(std::max<size_t>(chunks.size(), 1) * sizeof(int4), st);
   dcoff.alloc(chunk_off.size() * sizeof(int), st);
+  dsteps.alloc(std::max<size_t>(steps.size(), 1) * sizeof(int2), st);
   CUDA_CHECK(cudaMemcpyAsync(dch.p, chunks.data(), chunks.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, st));
+  if (!steps.empty())
+    CUDA_CHECK(cudaMemcpyAsync(dsteps.p, steps.data(), steps.size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, st));
   CUDA_CHECK(cudaMemcpyAsync(dcoff.p, chunk_off.data(), chunk_off.size() * sizeof(int),
                              cudaMemcpyHostToDevice, st));
   h->d_gpart.alloc(std::max<size_t>(chunks.size(), 1) * KT * sizeof(double), st);
@@ -1801,17 +1867,21 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
       const size_t psmem = (size_t)kDiagStages * 16 * K * sizeof(float2);
       ensure_dyn_smem((const void*)k_gram_diag_pipe_df, psmem);
       k_gram_diag_pipe_df<<<(unsigned)chunks.size(), gthreads, psmem, st>>>(
-          h->d_panels.as<float2>(), K, dch.as<int4>(), h->d_gpart.as<double>(),
-          h->d_flags.as<int>());
+          h->d_panels.as<float2>(), K, dch.as<int4>(), dsteps.as<int2>(),
+          h->d_entry_base.as<int64_t>(), h->d_entry_cell.as<int>(), h->d_cover_off.as<int>(),
+          h->d_gpart.as<double>(), h->d_flags.as<int>());
     } else if (K % 4 == 0 && (K * sizeof(T)) % 16 == 0) {
       const size_t psmem = (size_t)kDiagStages * 16 * K * sizeof(T);
       ensure_dyn_smem((const void*)k_gram_diag_pipe<T>, psmem);
       k_gram_diag_pipe<T><<<(unsigned)chunks.size(), gthreads, psmem, st>>>(
-          (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>(),
-          h->d_flags.as<int>());
+          (const T*)h->d_panels.p, K, dch.as<int4>(), dsteps.as<int2>(),
+          h->d_entry_base.as<int64_t>(), h->d_entry_cell.as<int>(), h->d_cover_off.as<int>(),
+          h->d_gpart.as<double>(), h->d_flags.as<int>());
     } else {
       k_gram_diag_partial<T><<<(unsigned)chunks.size(), gthreads, smem, st>>>(
-          (const T*)h->d_panels.p, K, dch.as<int4>(), h->d_gpart.as<double>());
+          (const T*)h->d_panels.p, K, dch.as<int4>(), dsteps.as<int2>(),
+          h->d_entry_base.as<int64_t>(), h->d_entry_cell.as<int>(), h->d_cover_off.as<int>(),
+          h->d_gpart.as<double>());
     }
     prof_end(h, KID_GRAM_DIAG);
     check_launch("k_gram_diag_partial");
@@ -1899,7 +1969,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       k_gather<T><<<kGatherBlocks, kGatherThreads, 0, st>>>(
           P, t, K, h->NR, h->d_grow_cell.as<int>(), h->d_cell_pstart.as<int>(),
           h->d_cell_count.as<int>(), h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(),
-          h->d_cover_start.as<int>(), h->d_panel_off.as<int64_t>(), scal, h->d_u.as<double>(),
+          h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(),
           h->d_h.as<double>(), mode, gpart);
       prof_end(h, KID_GATHER);
     }
@@ -1908,9 +1978,9 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     if constexpr (!std::is_same<T, df2>::value) {
       prof_begin(h, KID_ENTRY_T, panel_bytes + 8.0 * h->NR + 8.0 * ne * K);
       k_entry_T<T><<<ne, 128, 0, st>>>(P, h->d_u.as<double>(), K, h->d_entry_cell.as<int>(),
-                                          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),
+                                          h->d_cover_sub.as<int>(), h->d_cover_off.as<int>(),
                                           h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),
-                                          h->d_panel_off.as<int64_t>(), h->d_partial.as<double>());
+                                          h->d_entry_base.as<int64_t>(), h->d_partial.as<double>());
       prof_end(h, KID_ENTRY_T);
     }
     prof_begin(h, KID_PANEL_T, 8.0 * ne * K + (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
