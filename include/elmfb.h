@@ -336,6 +336,16 @@ int64_t elmfb_kernel_launches(elmfb_t h);
  * reported (>= 0) or a negative status.  elmfb_set_profiling(h, 1) clears the
  * totals. */
 int elmfb_set_profiling(elmfb_t h, int on);
+/* Profiling restricted to one kernel, named as elmfb_kernel_stats() names it
+ * (e.g. "fused_Mt_MTu"): the other kernels run without events around them.
+ * Clears the totals.  INVALID_ARG for an unknown name. */
+int elmfb_set_profiling_only(elmfb_t h, const char* kernel);
+
+/* Device memory of destroyed handles stays cached in the library's
+ * stream-ordered pool on each device, so that the next handle reuses it
+ * without returning memory to the system at every synchronisation.  This call
+ * synchronises the device (-1: the current one) and releases that cache. */
+int elmfb_trim_memory(int device);
 int elmfb_kernel_stats(elmfb_t h, int max, const char** names, double* total_ms,
                        int64_t* launches, double* bytes_per_launch);
 

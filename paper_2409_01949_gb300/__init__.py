@@ -105,6 +105,8 @@ _SIGNATURES = {
     "elmfb_stage_times": (C.c_int, [C.c_void_p, C.c_void_p]),
     "elmfb_kernel_launches": (C.c_int64, [C.c_void_p]),
     "elmfb_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "elmfb_set_profiling_only": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "elmfb_trim_memory": (C.c_int, [C.c_int]),
     "elmfb_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
     "elmfb_error_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
@@ -213,6 +215,13 @@ def _rowsets(problem, keep):
         arr[i].weight = float(rs.weight or 0.0)
     keep.append(arr)
     return arr
+
+
+def trim_memory(device: int = -1):
+    """Release the device memory cached in the library's pool."""
+    rc = lib().elmfb_trim_memory(device)
+    if rc != OK:
+        raise ElmfbError(rc, "trim_memory failed")
 
 
 def batch_solve(problems, precision=FP32, n_workers=8, opts=None, evaluate=True, coeffs=False):
@@ -452,6 +461,10 @@ class Solver:
 
     def set_profiling(self, on: bool = True):
         _check(self.h, lib().elmfb_set_profiling(self.h, 1 if on else 0))
+
+    def set_profiling_only(self, kernel: str):
+        """Time only the named kernel (names as kernel_stats() reports them)."""
+        _check(self.h, lib().elmfb_set_profiling_only(self.h, kernel.encode()))
 
     def kernel_stats(self):
         """{name: (total_ms, launches, algorithmic bytes per launch)} of the timed kernels."""

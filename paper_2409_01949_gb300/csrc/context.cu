@@ -235,6 +235,26 @@ void upload(elmfb_ctx* h, DevBuf& b, const std::vector<T>& v) {
 
 }  // namespace
 
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  CUDA_CHECK(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = UINT64_MAX;
+  CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pools[dev] = pool;
+  return pool;
+}
+
 void ensure_dyn_smem(const void* func, size_t bytes) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> limit;
@@ -283,7 +303,7 @@ const char* kKernelNames[KID_COUNT] = {"assemble_panels", "gather_Mv",    "entry
 }  // namespace
 
 void prof_begin(elmfb_ctx* h, int kid, double bytes) {
-  if (!h->prof) return;
+  if (!h->prof || !((h->prof_mask >> kid) & 1)) return;
   ProfRec r{kid, prof_event(h), prof_event(h)};
   CUDA_CHECK(cudaEventRecord(r.a, h->stream));
   h->prof_live.push_back(r);
@@ -291,7 +311,7 @@ void prof_begin(elmfb_ctx* h, int kid, double bytes) {
 }
 
 void prof_end(elmfb_ctx* h, int kid) {
-  if (!h->prof) return;
+  if (!h->prof || !((h->prof_mask >> kid) & 1)) return;
   for (auto it = h->prof_live.rbegin(); it != h->prof_live.rend(); ++it)
     if (it->kid == kid) {
       CUDA_CHECK(cudaEventRecord(it->b, h->stream));
@@ -515,10 +535,45 @@ int elmfb_stage_times(elmfb_t h, double* ms) {
 
 int64_t elmfb_kernel_launches(elmfb_t h) { return h ? h->launches : -1; }
 
+int elmfb_trim_memory(int device) {
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return ELMFB_ERR_CUDA;
+  if (device < 0) device = cur;
+  if (cudaSetDevice(device) != cudaSuccess) return ELMFB_ERR_INVALID_ARG;
+  int rc = ELMFB_OK;
+  try {
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemPoolTrimTo(library_pool(), 0) != cudaSuccess)
+      rc = ELMFB_ERR_CUDA;
+  } catch (...) {
+    rc = ELMFB_ERR_CUDA;
+  }
+  cudaSetDevice(cur);
+  return rc;
+}
+
+int elmfb_set_profiling_only(elmfb_t h, const char* kernel) {
+  return guarded(h, [&] {
+    if (!kernel) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null kernel name");
+    int kid = -1;
+    for (int k = 0; k < KID_COUNT; ++k)
+      if (std::strcmp(kernel, kKernelNames[k]) == 0) kid = k;
+    if (kid < 0) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "unknown kernel name");
+    prof_harvest(h);
+    h->prof = true;
+    h->prof_mask = uint64_t(1) << kid;
+    for (int k = 0; k < KID_COUNT; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_n[k] = 0;
+    }
+  });
+}
+
 int elmfb_set_profiling(elmfb_t h, int on) {
   return guarded(h, [&] {
     prof_harvest(h);
     h->prof = on != 0;
+    h->prof_mask = ~uint64_t(0);
     for (int k = 0; k < KID_COUNT; ++k) {
       h->prof_ms[k] = 0.0;
       h->prof_n[k] = 0;

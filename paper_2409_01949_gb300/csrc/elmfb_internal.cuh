@@ -29,6 +29,12 @@ struct elmfb_error {
                         std::string(#call) + ": " + cudaGetErrorString(e__)};     \
   } while (0)
 
+// The library's stream-ordered memory pool on the current device.  Freed
+// blocks stay cached in it (release threshold: never), so that handles made
+// one after another reuse device memory instead of returning it to the system
+// at every stream synchronisation; elmfb_trim_memory() hands it back.
+cudaMemPool_t library_pool();
+
 // ---------------------------------------------------------------------------
 // device buffer owned by the handle (stream-ordered allocation)
 // ---------------------------------------------------------------------------
@@ -50,7 +56,7 @@ struct DevBuf {
     release();
     s = stream;
     if (n == 0) return;
-    CUDA_CHECK(cudaMallocAsync(&p, n, stream));
+    CUDA_CHECK(cudaMallocFromPoolAsync(&p, n, library_pool(), stream));
     bytes = n;
   }
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
@@ -180,6 +186,7 @@ struct elmfb_ctx {
 
   // per-kernel profiling
   bool prof = false;
+  uint64_t prof_mask = ~uint64_t(0);   // kernels timed when prof is on (bit = KernelId)
   std::vector<ProfRec> prof_live;       // recorded, not yet harvested
   std::vector<cudaEvent_t> prof_pool;   // free events
   double prof_ms[KID_COUNT] = {0};
