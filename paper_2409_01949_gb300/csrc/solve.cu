@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
                                                      double* __restrict__ Xr,
                                                      double* __restrict__ Xc,
                                                      int* __restrict__ flags,
-                                                     double* __restrict__ gdiag_out) {
+                                                     double* __restrict__ gdiag_out,
+                                                     float2* __restrict__ xr2,
+                                                     float2* __restrict__ xc2) {
   extern __shared__ double G[];   // [K][K]
   __shared__ double red[33];
   __shared__ double diag0[128];
@@ -636,6 +638,11 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
     const double v = jj <= i ? G[i * K + jj] : 0.0;
     xr[idx] = v;                          // X_ij row-major
     xc[(int64_t)jj * K + i] = v;          // X_ij column-major
+    if (xr2) {                            // the same as FP32 pairs
+      const float2 p = df_split(v);
+      xr2[(int64_t)s * K * K + idx] = p;
+      xc2[(int64_t)s * K * K + (int64_t)jj * K + i] = p;
+    }
   }
 }
 
@@ -1490,6 +1497,129 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;
 }
 
+// k_precond with X_j held as FP32 pairs (FP32 and DF32 panels): the products
+// and sums of t_j = X_j^T v_j run in float-float arithmetic on the FP32 pipes
+// (about 2^-48 relative), so that the only FP64 work left is splitting v_j
+// and forming t_j.  Same group split and fixed summation order as k_precond.
+__global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ Xr2,
+                                                     const double* __restrict__ v, int K,
+                                                     double* __restrict__ t, int identity,
+                                                     double* __restrict__ scal,
+                                                     void* __restrict__ tlow, int low_kind) {
+  extern __shared__ double psh[];   // vs[K] then part[G][K], here as FP32 pairs
+  const int s = blockIdx.x;
+  if (s == 0 && threadIdx.x < kStage) scal[threadIdx.x] = scal[kStage + threadIdx.x];
+  const double* vv = v + (int64_t)s * K;
+  if (identity) {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      t[(int64_t)s * K + i] = vv[i];
+      store_low(tlow, low_kind, (int64_t)s * K + i, vv[i]);
+    }
+    return;
+  }
+  float2* vs = reinterpret_cast<float2*>(psh);
+  float2* part = vs + K;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) vs[i] = df_split(vv[i]);
+  __syncthreads();
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
+  const int chunk = (K + G - 1) / G;
+  const float2* X = Xr2 + (int64_t)s * K * K;
+  if (g < G && i < K) {
+    float S = 0.f, C = 0.f;
+    const int m1 = min(K, (g + 1) * chunk);
+    for (int m = max(i, g * chunk); m < m1; ++m) {
+      const float2 x = X[m * K + i];
+      df_acc(S, C, x.x, x.y, vs[m].x, vs[m].y);
+    }
+    part[g * K + i] = make_float2(S, C);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    float2 a = part[j];
+    for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
+    const double acc = (double)a.x + (double)a.y;
+    t[(int64_t)s * K + j] = acc;
+    store_low(tlow, low_kind, (int64_t)s * K + j, acc);
+  }
+}
+
+// k_panel_T2 for FP32-pair partials with X_j held as FP32 pairs: the slice
+// sums, the scaling by 1/beta and X_j z_j run in float-float arithmetic;
+// FP64 is left for beta, v' = X_j z_j - beta v_j and its norm.
+__global__ void __launch_bounds__(1024) k_panel_T2_df(
+    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xc2,
+    int K, const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
+    double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial) {
+  extern __shared__ double zsh[];   // [groups][K] then z[K], here as FP32 pairs
+  __shared__ double red[33];
+  const int s = blockIdx.x;
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
+  __shared__ double shs, sh_beta;
+  __shared__ float2 sh_ib;
+  const double b2 = block_partial_sum(beta_partial, n_beta_partial, &shs);
+  if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
+    const double bt = sqrt(b2);
+    sh_beta = bt;
+    sh_ib = df_split(bt > 0.0 ? 1.0 / bt : 0.0);
+  }
+  __syncthreads();
+  const double beta = sh_beta;
+  const float2 ib = sh_ib;
+  float2* part = reinterpret_cast<float2*>(zsh);
+  float2* zs = part + G * K;
+  if (g < G && k < K) {
+    float hi = 0.f, lo = 0.f;
+    for (int q = pco[s] + g; q < pco[s + 1]; q += G) {
+      const float2 pr = partial_pair(csum, (int64_t)q * K + k);
+      ff_add(hi, lo, pr.x, pr.y);
+    }
+    part[g * K + k] = make_float2(hi, lo);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    float2 z = part[i];
+    for (int q = 1; q < G; ++q) z = df_add(z, part[q * K + i]);
+    float S = 0.f, C = 0.f;
+    df_acc(S, C, z.x, z.y, ib.x, ib.y);
+    zs[i] = make_float2(S, C);
+  }
+  __syncthreads();
+  const float2* X = Xc2 + (int64_t)s * K * K;
+  if (!identity) {
+    // the groups split the sum over mm <= i into fixed slices
+    const int chunk = (K + G - 1) / G;
+    if (g < G && k < K) {
+      float S = 0.f, C = 0.f;
+      const int m1 = min(k + 1, (g + 1) * chunk);
+      for (int mm = g * chunk; mm < m1; ++mm) {
+        const float2 x = X[mm * K + k];
+        df_acc(S, C, x.x, x.y, zs[mm].x, zs[mm].y);
+      }
+      part[g * K + k] = make_float2(S, C);
+    }
+    __syncthreads();
+  }
+  double nrm = 0.0;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    float2 a = identity ? zs[i] : part[i];
+    if (!identity)
+      for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + i]);
+    const double acc = (double)a.x + (double)a.y;
+    const double vold = init ? 0.0 : v[(int64_t)s * K + i];
+    const double vn = acc - beta * vold;
+    v[(int64_t)s * K + i] = vn;
+    nrm += vn * vn;
+  }
+  double tot = block_sum(nrm, red);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
+  if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;
+}
+
+
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the entry partials of panel j
 // (X_j = R_j^{-T}); writes v' (unnormalised) and ||v'||^2 per block.
 __global__ void k_panel_T(const double* __restrict__ partial, const int* __restrict__ pent_off,
@@ -1891,10 +2021,14 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   ensure_dyn_smem((const void*)k_block_chol, csm);
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
-  k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(h->d_gpart.as<double>(), dcoff.as<int>(), K, shift,
-                                           abs_shift, h->d_R.as<double>(),
-                                           h->d_R.as<double>() + h->n_sub * KK,
-                                           h->d_flags.as<int>(), nullptr);
+  // FP32 and DF32 panels apply X_j in float-float arithmetic: keep a pair copy
+  const bool pairs_x = !std::is_same<T, double>::value;
+  if (pairs_x) h->d_R2.alloc(2 * h->n_sub * KK * sizeof(float2), st);
+  k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(
+      h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
+      h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr,
+      pairs_x ? h->d_R2.as<float2>() : nullptr,
+      pairs_x ? h->d_R2.as<float2>() + h->n_sub * KK : nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
@@ -2014,15 +2148,25 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   auto fused_step = [&](const double* t, int mode, const void* tf = nullptr) {
     launch_fused<T>(h, fp, t, mode, scal, gpart, tf);
   };
+  // FP32 and DF32 panels apply X_j as FP32 pairs (block_jacobi_setup keeps a
+  // pair copy); the fused path's partials are then pairs too
+  const bool xpairs = !std::is_same<T, double>::value && fused && fp.pairs && !identity;
+  const float2* Xr2 = xpairs ? h->d_R2.as<float2>() : nullptr;
+  const float2* Xc2 = xpairs ? h->d_R2.as<float2>() + h->n_sub * KK : nullptr;
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
   auto fused_tail = [&](int init) {
     prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
                                    (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
     panel_chunk_sums(h, fp);
-    k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
-        fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, gpart, n_units, h->d_v.as<double>(),
-        scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
+    if (xpairs)
+      k_panel_T2_df<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
+          fp.csum.as<double>(), fp.pco.as<int>(), Xc2, K, gpart, n_units, h->d_v.as<double>(),
+          scal, identity ? 1 : 0, init, vpart);
+    else
+      k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
+          fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, gpart, n_units, h->d_v.as<double>(),
+          scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N);
     k_update<<<upd_blocks, 256, 0, st>>>(scal, vpart, h->n_sub, h->d_v.as<double>(),
@@ -2064,8 +2208,13 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     int batch = std::min(o->check_every, max_it - it);
     for (int b = 0; b < batch; ++b) {
       prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
-      k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
-          Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, fp.tf.p, low_kind);
+      if (xpairs)
+        k_precond_df<<<h->n_sub, pc_threads, pc_smem, st>>>(
+            Xr2, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, fp.tf.p,
+            low_kind);
+      else
+        k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
+            Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, fp.tf.p, low_kind);
       prof_end(h, KID_PRECOND);
       if (fused) {
         fused_step(h->d_tmp.as<double>(), 0, low_kind ? fp.tf.p : nullptr);
@@ -2095,9 +2244,14 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     }
   }
   // a = (a0 +) P y
-  k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_x_sol.as<double>(), K,
-                                                    h->d_tmp.as<double>(), identity, scal,
-                                                    nullptr, 0);
+  if (xpairs)
+    k_precond_df<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr2, h->d_x_sol.as<double>(), K,
+                                                         h->d_tmp.as<double>(), identity, scal,
+                                                         nullptr, 0);
+  else
+    k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr, h->d_x_sol.as<double>(), K,
+                                                      h->d_tmp.as<double>(), identity, scal,
+                                                      nullptr, 0);
   if (o->warm_start)
     k_add_to<<<upd_blocks, 256, 0, st>>>(h->d_a.as<double>(), h->d_tmp.as<double>(), N);
   else
