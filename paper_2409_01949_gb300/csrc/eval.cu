@@ -1,8 +1,9 @@
 // Model evaluation and error norms.
 //
 // u_hat(x) = (1/L) sum_l sum_j w_j(x) sum_k a_ljk phi_ljk(x)   (paper Eq.
-// multilevel_solution), evaluated in FP64: one warp per point, lanes over the
-// features of each covering subdomain.  The covering subdomains of a point are
+// multilevel_solution), evaluated in FP64: one warp per point.  Lane j forms
+// the window of covering subdomain j, the lanes then share the features of
+// each covering subdomain.  The covering subdomains of a point are
 // those of its cell (the common refinement of all supports).
 //
 // Error norms (paper Eq. l1_error): e_L1 = sum |u_hat - u| / (M std(u)) with
@@ -60,7 +61,49 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ xs, int
     bb += ncs[i] + 1;
   }
   const int cell = c[1] * nc0 + c[0];
-  double total = 0.0;
+  const int e0 = cell_level_off[(int64_t)cell * (L + 1)];
+  const int m = cell_level_off[(int64_t)cell * (L + 1) + L] - e0;
+  if (m <= 32) {
+    // lane j takes covering entry e0 + j: its window factor (FP64 sin/cos, so
+    // once per entry instead of once per lane and entry) and scaled input
+    double wj = 0.0, xj[2] = {0.0, 0.0};
+    int lvl = -1, sj = 0;
+    if (lane < m) {
+      sj = cover_sub[e0 + lane];
+      const SubGeom g = sub[sj];
+      lvl = g.level;
+      wj = 1.0;
+      for (int i = 0; i < dim; ++i) {
+        xj[i] = (x[i] - g.mu[i]) * g.inv_sigma_d[i];
+        wj *= factor(x[i] - g.mu[i], g.sigma_d[i], g.inv_sigma_d[i]);
+      }
+    }
+    // partition of unity per level: S_l = sum of the level's factors
+    double Sj = 0.0;
+    for (int l = 0; l < L; ++l) {
+      const double S = warp_sum_d(lvl == l ? wj : 0.0);
+      if (lvl == l) Sj = S;
+    }
+    const double cj = (Sj > 0.0 && wj != 0.0) ? wj / Sj : 0.0;
+    // each lane sums its features over the entries; one reduction at the end
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double cw = __shfl_sync(0xffffffffu, cj, j);
+      if (cw == 0.0) continue;   // warp-uniform
+      const int s = __shfl_sync(0xffffffffu, sj, j);
+      const double x0 = __shfl_sync(0xffffffffu, xj[0], j);
+      const double x1 = __shfl_sync(0xffffffffu, xj[1], j);
+      for (int f = lane; f < K; f += 32) {
+        const int64_t q = (int64_t)s * K + f;
+        const double arg = W[q * dim] * x0 + (dim == 2 ? W[q * dim + 1] * x1 : 0.0) + B[q];
+        acc += cw * (a[q] * tanh(arg));
+      }
+    }
+    const double total = warp_sum_d(acc);
+    if (lane == 0) out[pt] = total / L;
+    return;
+  }
+  double total = 0.0;   // more than 32 covering subdomains: entry by entry
   for (int l = 0; l < L; ++l) {
     const int b = cell_level_off[(int64_t)cell * (L + 1) + l];
     const int e = cell_level_off[(int64_t)cell * (L + 1) + l + 1];
