@@ -37,6 +37,10 @@ import workloads as WL  # noqa: E402
 
 METRIC = "ELM-FBPINN time-to-solution (s) at oracle-matched L2 error; assembly HBM GB/s"
 DOMINANT = "fused_Mt_MTu"   # the LSQR pass: the largest share of a step
+# DRAM bytes (read + write) per algorithmic byte of the FP32-panel fused pass,
+# from the ncu capture summarised in profiles/k_fused_pipe_poisson2d_L1-16_K128_N200.md
+# (a quarter-size case of the same kernel; its traffic grows with the panel bytes)
+FUSED_FP32_TRAFFIC_PER_BYTE = (346.5 + 12.1) / 346.4
 # workload -> (problem, oracle golden name, panel precision)
 WORKLOADS = {
     "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400", "fp32"),
@@ -323,7 +327,11 @@ def run_ours(args):
                      "oracle_lsqr15000_rel_l2": (g or {}).get("lsqr", {}).get("rel_l2"),
                      "oracle_qr_rel_l2": (g or {}).get("qr", {}).get("rel_l2")},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(ach / hbm, 4),
+                     "traffic": (round(kstats[dom][2] * FUSED_FP32_TRAFFIC_PER_BYTE)
+                                 if prec == E.FP32 else None),
+                     "traffic_note": ("DRAM bytes per launch scaled from the ncu capture of the "
+                                      "200x200 case" if prec == E.FP32 else None),
                      "peak_kind": peak_kind},
         "assembly": {"kernel": "assemble_panels", "achieved_gbs": asm.get("gbs"),
                      "frac": round(asm["gbs"] / hbm, 4) if asm.get("gbs") else None,

@@ -244,7 +244,10 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
                   double* gpart, const void* tf = nullptr);
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
-void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp);   // fixed slices of each panel's partials
+// fixed slices of each panel's partials; with beta_partial also beta^2 into the
+// staged scalar slot that k_panel_T2 reads
+void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial = nullptr,
+                      int n_beta = 0, double* scal = nullptr);
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials
 void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part);  // z = X^T X r
 

@@ -38,7 +38,8 @@ constexpr int kScal = 32;             // device scalar slots
 constexpr int kStage = 16;
 enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
-  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO
+  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO,
+  S_BSQ   // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
 };
 
 template <class T>
@@ -1398,8 +1399,17 @@ constexpr int kPanelChunk = 32;
 
 __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __restrict__ fe,
                                const int2* __restrict__ pch, int K, double* __restrict__ csum,
-                               int pairs) {
+                               int pairs, const double* __restrict__ beta_partial, int n_beta,
+                               double* __restrict__ scal) {
   __shared__ int ent[kPanelChunk];
+  // block 0, warp 0: beta^2 = sum of the norm partials, once for every panel
+  // block of k_panel_T2 (same fixed order as block_partial_sum)
+  if (beta_partial && blockIdx.x == 0 && threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n_beta; i += 32) v += beta_partial[i];
+    v = warp_sum<double>(v);
+    if (threadIdx.x == 0) scal[kStage + S_BSQ] = v;
+  }
   const int2 ch = pch[blockIdx.x];
   const int n = ch.y - ch.x;
   if ((int)threadIdx.x < n) ent[threadIdx.x] = fe[ch.x + threadIdx.x];
@@ -1436,10 +1446,9 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
-  __shared__ double shs, sh_beta, sh_ib;
-  const double b2 = block_partial_sum(beta_partial, n_beta_partial, &shs);
+  __shared__ double sh_beta, sh_ib;
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
-    const double bt = sqrt(b2);
+    const double bt = sqrt(scal[kStage + S_BSQ]);   // k_panel_chunks formed beta^2
     sh_beta = bt;
     sh_ib = bt > 0.0 ? 1.0 / bt : 0.0;
   }
@@ -1558,11 +1567,10 @@ __global__ void __launch_bounds__(1024) k_panel_T2_df(
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
-  __shared__ double shs, sh_beta;
+  __shared__ double sh_beta;
   __shared__ float2 sh_ib;
-  const double b2 = block_partial_sum(beta_partial, n_beta_partial, &shs);
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
-    const double bt = sqrt(b2);
+    const double bt = sqrt(scal[kStage + S_BSQ]);   // k_panel_chunks formed beta^2
     sh_beta = bt;
     sh_ib = df_split(bt > 0.0 ? 1.0 / bt : 0.0);
   }
@@ -2091,7 +2099,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const int upd_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
   // k_precond: G groups of Kp threads split each X_j^T v_j sum
   const int pc_Kp = (K + 31) & ~31;
-  const int pc_G = std::max(1, std::min(8, std::min(1024 / pc_Kp, K / 8)));
+  const int pc_G = std::max(1, std::min(8, std::min(256 / pc_Kp, K / 8)));
   const int pc_threads = pc_G * pc_Kp;
   const size_t pc_smem = (size_t)(K + pc_G * K) * sizeof(double);
 
@@ -2143,7 +2151,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     vpart = gpart + std::max(kGatherBlocks, n_units);
   }
   const int KpT = (K + 31) & ~31;
-  const int tgroups = std::max(1, 1024 / KpT);
+  const int tgroups = std::max(1, 256 / KpT);   // small blocks: every panel resident at once
   const size_t p2smem = (size_t)(tgroups + 1) * K * sizeof(double);
   auto fused_step = [&](const double* t, int mode, const void* tf = nullptr) {
     launch_fused<T>(h, fp, t, mode, scal, gpart, tf);
@@ -2158,7 +2166,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   auto fused_tail = [&](int init) {
     prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
                                    (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
-    panel_chunk_sums(h, fp);
+    panel_chunk_sums(h, fp, gpart, n_units, scal);
     if (xpairs)
       k_panel_T2_df<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
           fp.csum.as<double>(), fp.pco.as<int>(), Xc2, K, gpart, n_units, h->d_v.as<double>(),
@@ -2572,12 +2580,13 @@ template void block_jacobi_setup<float>(elmfb_ctx*, double, bool, double);
 template void block_jacobi_setup<double>(elmfb_ctx*, double, bool, double);
 template void block_jacobi_setup<df2>(elmfb_ctx*, double, bool, double);
 
-void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp) {
+void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, int n_beta,
+                      double* scal) {
   if (fp.n_pchunks == 0) return;
   const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
-  k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(fp.part.as<double>(), fp.fe.as<int>(),
-                                                      fp.pch.as<int2>(), h->K,
-                                                      fp.csum.as<double>(), fp.pairs ? 1 : 0);
+  k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(
+      fp.part.as<double>(), fp.fe.as<int>(), fp.pch.as<int2>(), h->K, fp.csum.as<double>(),
+      fp.pairs ? 1 : 0, beta_partial, n_beta, scal);
   check_launch("k_panel_chunks");
   count_launch(h);
 }
