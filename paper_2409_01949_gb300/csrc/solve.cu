@@ -2099,7 +2099,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const int upd_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
   // k_precond: G groups of Kp threads split each X_j^T v_j sum
   const int pc_Kp = (K + 31) & ~31;
-  const int pc_G = std::max(1, std::min(8, std::min(256 / pc_Kp, K / 8)));
+  const int pc_G = std::max(1, std::min(8, std::min(1024 / pc_Kp, K / 8)));
   const int pc_threads = pc_G * pc_Kp;
   const size_t pc_smem = (size_t)(K + pc_G * K) * sizeof(double);
 
@@ -2151,7 +2151,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     vpart = gpart + std::max(kGatherBlocks, n_units);
   }
   const int KpT = (K + 31) & ~31;
-  const int tgroups = std::max(1, 256 / KpT);   // small blocks: every panel resident at once
+  const int tgroups = std::max(1, 1024 / KpT);
   const size_t p2smem = (size_t)(tgroups + 1) * K * sizeof(double);
   auto fused_step = [&](const double* t, int mode, const void* tf = nullptr) {
     launch_fused<T>(h, fp, t, mode, scal, gpart, tf);
