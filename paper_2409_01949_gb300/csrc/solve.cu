@@ -837,8 +837,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
   }
   double coef = 0.0;   // used by warp 0 only (an FP64 division is costly)
   if (mode == 0 && threadIdx.x < 32) {
-    const double beta = scal[S_BETA];
-    coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+    const double beta = scal[kStage + S_BETA];   // staged by k_update_precond
+    coef = beta > 0.0 ? scal[kStage + S_ALPHA] / beta : 0.0;
   }
   T ahi[FPL], alo[FPL];
 #pragma unroll
@@ -1074,8 +1074,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     }
     double coef = 0.0;
     if (mode == 0) {
-      const double beta = scal[S_BETA];
-      coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+      const double beta = scal[kStage + S_BETA];   // staged by k_update_precond
+      coef = beta > 0.0 ? scal[kStage + S_ALPHA] / beta : 0.0;
     }
     if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
     double nrm = 0.0;
@@ -1279,8 +1279,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     }
     double coef = 0.0;
     if (mode == 0) {
-      const double beta = scal[S_BETA];
-      coef = beta > 0.0 ? scal[S_ALPHA] / beta : 0.0;
+      const double beta = scal[kStage + S_BETA];   // staged by k_update_precond
+      coef = beta > 0.0 ? scal[kStage + S_ALPHA] / beta : 0.0;
     }
     if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
     double nrm = 0.0;
@@ -1402,8 +1402,12 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
                                int pairs, const double* __restrict__ beta_partial, int n_beta,
                                double* __restrict__ scal) {
   __shared__ int ent[kPanelChunk];
-  // block 0, warp 0: beta^2 = sum of the norm partials, once for every panel
-  // block of k_panel_T2 (same fixed order as block_partial_sum)
+  // block 0, LSQR: commit the scalars staged by k_update_precond (no kernel
+  // of the iteration reads the committed slots before this point), then
+  // warp 0 forms beta^2 = sum of the norm partials, once for every panel block
+  // of k_panel_T2 (same fixed order as block_partial_sum)
+  if (beta_partial && blockIdx.x == 0 && threadIdx.x < kStage && threadIdx.x != S_BSQ)
+    scal[threadIdx.x] = scal[kStage + threadIdx.x];
   if (beta_partial && blockIdx.x == 0 && threadIdx.x < 32) {
     double v = 0.0;
     for (int i = threadIdx.x; i < n_beta; i += 32) v += beta_partial[i];
@@ -1739,6 +1743,138 @@ __global__ void k_update(double* __restrict__ scal, const double* __restrict__ a
   }
 }
 
+// The fused path's k_update merged with the next iteration's k_precond, one
+// block per subdomain: alpha = ||v'|| (every block sums the norm partials in
+// the same fixed order; thread 0 runs the recurrence and block 0 stages the
+// scalars, as k_update), then the block updates v, w, x on its K entries and
+// forms t_s = X_s^T v_s for the next fused pass (float-float with FP32-pair X
+// for FP32 / DF32 panels, else FP64), with t's low-precision copy.  The
+// committed scalars are read here and committed later by k_panel_chunks, so
+// no block of this kernel overwrites what another block reads.
+__global__ void __launch_bounds__(1024) k_update_precond(
+    double* __restrict__ scal, const double* __restrict__ alpha_partial, int n_alpha_partial,
+    double* __restrict__ v, double* __restrict__ w, double* __restrict__ x, int K, int init,
+    int identity, const double* __restrict__ Xr, const float2* __restrict__ Xr2,
+    double* __restrict__ t, void* __restrict__ tlow, int low_kind) {
+  extern __shared__ double psh[];   // vs[K] then part[G][K] (FP32 pairs with Xr2)
+  __shared__ double shs;
+  __shared__ double shv[4];
+  const int s = blockIdx.x;
+  const double a2 = block_partial_sum(alpha_partial, n_alpha_partial, &shs);
+  const double beta = scal[kStage + S_BETA];   // beta_{i+1}
+  double alpha = 0.0, ia = 0.0, phi_rho = 0.0, theta_rho = 0.0;
+  double rhobar_new = 0.0, phibar_new = 0.0, anorm2 = scal[S_ANORM2], arnorm = 0.0;
+  if (threadIdx.x == 0) {   // one thread: the recurrence needs FP64 sqrt / divisions
+    alpha = sqrt(a2);
+    ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    if (init) {
+      rhobar_new = alpha;
+      phibar_new = beta;
+      anorm2 = alpha * alpha;
+      arnorm = alpha * beta;
+    } else {
+      const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
+      const double rho = sqrt(rhobar * rhobar + beta * beta);
+      const double c = rho > 0.0 ? rhobar / rho : 1.0;
+      const double sn = rho > 0.0 ? beta / rho : 0.0;
+      const double theta = sn * alpha;
+      rhobar_new = -c * alpha;
+      const double phi = c * phibar;
+      phibar_new = sn * phibar;
+      phi_rho = rho > 0.0 ? phi / rho : 0.0;
+      theta_rho = rho > 0.0 ? theta / rho : 0.0;
+      anorm2 += alpha * alpha + beta * beta;
+      arnorm = phibar_new * alpha * fabs(c);
+    }
+    shv[0] = ia;
+    shv[1] = phi_rho;
+    shv[2] = theta_rho;
+  }
+  __syncthreads();
+  ia = shv[0];
+  phi_rho = shv[1];
+  theta_rho = shv[2];
+  const int64_t o = (int64_t)s * K;
+  double* vs = psh;
+  float2* vs2 = reinterpret_cast<float2*>(psh);
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double vn = v[o + i] * ia;   // v_{i+1}
+    if (init) {
+      w[o + i] = vn;
+      x[o + i] = 0.0;
+    } else {
+      const double wi = w[o + i];
+      x[o + i] += phi_rho * wi;
+      w[o + i] = vn - theta_rho * wi;
+    }
+    v[o + i] = vn;
+    if (identity) {
+      t[o + i] = vn;
+      store_low(tlow, low_kind, o + i, vn);
+    } else if (Xr2) {
+      vs2[i] = df_split(vn);
+    } else {
+      vs[i] = vn;
+    }
+  }
+  if (s == 0 && threadIdx.x == 0) {
+    double* sg = scal + kStage;
+    sg[S_ALPHA] = alpha;
+    sg[S_BETA] = beta;
+    sg[S_RHOBAR] = rhobar_new;
+    sg[S_PHIBAR] = phibar_new;
+    sg[S_ANORM2] = anorm2;
+    sg[S_RNORM] = phibar_new;
+    sg[S_ARNORM] = arnorm;
+    sg[S_BNORM] = init ? beta : scal[S_BNORM];
+    sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
+    sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
+  }
+  if (identity) return;
+  __syncthreads();
+  // t_s = X_s^T v_s: G groups split each sum into fixed slices (as k_precond)
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
+  const int chunk = (K + G - 1) / G;
+  const int m1 = min(K, (g + 1) * chunk);
+  if (Xr2) {
+    float2* part = vs2 + K;
+    const float2* X = Xr2 + (int64_t)s * K * K;
+    if (g < G && i < K) {
+      float S = 0.f, C = 0.f;
+      for (int m = max(i, g * chunk); m < m1; ++m) {
+        const float2 xv = X[m * K + i];
+        df_acc(S, C, xv.x, xv.y, vs2[m].x, vs2[m].y);
+      }
+      part[g * K + i] = make_float2(S, C);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      float2 a = part[j];
+      for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
+      const double acc = (double)a.x + (double)a.y;
+      t[o + j] = acc;
+      store_low(tlow, low_kind, o + j, acc);
+    }
+  } else {
+    double* part = vs + K;
+    const double* X = Xr + (int64_t)s * K * K;
+    if (g < G && i < K) {
+      double acc = 0.0;
+      for (int m = max(i, g * chunk); m < m1; ++m) acc += X[m * K + i] * vs[m];
+      part[g * K + i] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < G; ++q) acc += part[q * K + j];
+      t[o + j] = acc;
+      store_low(tlow, low_kind, o + j, acc);
+    }
+  }
+}
+
 __global__ void k_add_to(double* __restrict__ a, const double* __restrict__ d, int64_t N) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -1764,8 +1900,15 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   if (h->max_cover > 32 || K > 128) return false;
   cudaStream_t st = h->stream;
   fp.threads = 32 * std::max(1, h->max_cover);
-  const int64_t target =
+  // rows per work unit: about NR / 608 (4 waves of CTAs); ELMFB_FUSED_UNIT_ROWS
+  // overrides it (a tuning knob: units change the timing, not the arithmetic
+  // order within a row)
+  int64_t target =
       std::min<int64_t>(kMaxUnitRows, std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7)));
+  if (const char* e = getenv("ELMFB_FUSED_UNIT_ROWS")) {
+    const long v = atol(e);
+    if (v >= 8 && v <= kMaxUnitRows) target = v & ~7L;
+  }
   std::vector<int4> units;
   std::vector<std::vector<int>> plist(h->n_sub);
   int pbase = 0;
@@ -2176,9 +2319,10 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
           fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, gpart, n_units, h->d_v.as<double>(),
           scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
-    prof_begin(h, KID_UPDATE, 48.0 * N);
-    k_update<<<upd_blocks, 256, 0, st>>>(scal, vpart, h->n_sub, h->d_v.as<double>(),
-                                         h->d_w.as<double>(), h->d_x_sol.as<double>(), N, init);
+    prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : (xpairs ? 4.0 : 8.0) * h->n_sub * KK));
+    k_update_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
+        scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(), h->d_x_sol.as<double>(),
+        K, init, identity ? 1 : 0, Xr, Xr2, h->d_tmp.as<double>(), fp.tf.p, low_kind);
     prof_end(h, KID_UPDATE);
   };
   if (fused && p2smem > 48 * 1024)
@@ -2215,24 +2359,22 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   while (it < max_it) {
     int batch = std::min(o->check_every, max_it - it);
     for (int b = 0; b < batch; ++b) {
-      prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
-      if (xpairs)
-        k_precond_df<<<h->n_sub, pc_threads, pc_smem, st>>>(
-            Xr2, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, fp.tf.p,
-            low_kind);
-      else
-        k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
-            Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, fp.tf.p, low_kind);
-      prof_end(h, KID_PRECOND);
       if (fused) {
+        // t (and its low-precision copy) come from the previous k_update_precond
         fused_step(h->d_tmp.as<double>(), 0, low_kind ? fp.tf.p : nullptr);
         fused_tail(0);
       } else {
+        prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
+        k_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
+            Xr, h->d_v.as<double>(), K, h->d_tmp.as<double>(), identity, scal, nullptr, 0);
+        prof_end(h, KID_PRECOND);
         gather(h->d_tmp.as<double>(), 0);
         transpose_step(0);
       }
     }
-    count_launch(h, (fused ? 3 : 5) * batch);
+    // fused: k_panel_T2 + k_update_precond (the fused pass and the slice sums
+    // count themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
+    count_launch(h, (fused ? 2 : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
