@@ -179,7 +179,7 @@ struct elmfb_ctx {
 
   // solver work buffers
   DevBuf d_u, d_v, d_w, d_x_sol, d_tmp, d_partial, d_scal, d_R, d_ptile, d_gpart;
-  DevBuf d_R2;   // X_j as FP32 pairs (row- then column-major), FP32 and DF32 panels
+  DevBuf d_R2;   // X_j as FP32 pairs, packed lower triangle per panel (FP32 and DF32 panels)
 
   // stage timers
   Stage st[ELMFB_N_STAGES];

@@ -160,6 +160,14 @@ __device__ __forceinline__ float2 df_split(double v) {
   return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
+// X_j as FP32 pairs (FP32 and DF32 panels), packed lower triangle: row m of
+// panel j holds X_mi, i = 0..m, from pair m (m + 1) / 2 on.  Panels are
+// tri_pairs(K) pairs apart (an even count, so that each one starts on a
+// 16-byte boundary and moves into shared memory as one bulk copy).
+__host__ __device__ __forceinline__ int64_t tri_pairs(int K) {
+  return ((int64_t)K * (K + 1) / 2 + 1) & ~int64_t(1);
+}
+
 // sum of 4 per-lane pairs over the warp; lane 8r holds the total of pair r
 __device__ __forceinline__ float2 warp_sum4_df(float2 v0, float2 v1, float2 v2, float2 v3,
                                                int lane) {
@@ -524,7 +532,7 @@ constexpr int kCholThreads = 512;   // 4 per column of X at K = 128
 
 // One block per subdomain: sum the chunk partials, shift, Cholesky
 // (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
-// column-major.  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
+// column-major (and, given xtri, as the packed pair triangle).  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
 // Right-looking factorisation with a 2-D split of the trailing update; the
 // inverse is formed in place in shared memory row by row (row i of X needs
 // row i of L and rows < i of X), four threads per column splitting each sum.
@@ -536,8 +544,7 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
                                                      double* __restrict__ Xc,
                                                      int* __restrict__ flags,
                                                      double* __restrict__ gdiag_out,
-                                                     float2* __restrict__ xr2,
-                                                     float2* __restrict__ xc2) {
+                                                     float2* __restrict__ xtri) {
   extern __shared__ double G[];   // [K][K]
   __shared__ double red[33];
   __shared__ double diag0[128];
@@ -639,11 +646,8 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
     const double v = jj <= i ? G[i * K + jj] : 0.0;
     xr[idx] = v;                          // X_ij row-major
     xc[(int64_t)jj * K + i] = v;          // X_ij column-major
-    if (xr2) {                            // the same as FP32 pairs
-      const float2 p = df_split(v);
-      xr2[(int64_t)s * K * K + idx] = p;
-      xc2[(int64_t)s * K * K + (int64_t)jj * K + i] = p;
-    }
+    if (xtri && jj <= i)                  // the triangle again, as packed FP32 pairs
+      xtri[(int64_t)s * tri_pairs(K) + i * (i + 1) / 2 + jj] = df_split(v);
   }
 }
 
@@ -953,6 +957,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
 // FP32).  Lane l holds features k = l FPL + j, read from shared memory as one
 // vector.  Every wait is bounded; a timeout raises flags[3].
 constexpr int kPipeRows = 4;
+// k_fused_pipe takes 4 or 8 rows a chunk: both divide every unit (units are
+// multiples of kFusedRows rows, cells multiples of kCellPad)
+static_assert(kFusedRows % 8 == 0 && kCellPad % 8 == 0, "fused chunks must divide the units");
 constexpr int kPipeMaxStages = 12;
 constexpr int kMaxUnitRows = 1024;   // rows of one unit (its u values are staged in smem)
 
@@ -1004,7 +1011,7 @@ __device__ __forceinline__ void load_slice(const T* p, T (&x)[FPL], bool whole, 
   }
 }
 
-template <class T, int FPL>
+template <class T, int FPL, int kRows>
 __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     const T* __restrict__ panels, const T* __restrict__ tvec, int K,
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
@@ -1020,10 +1027,10 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   __shared__ __align__(8) uint64_t dots_bar[2];             // dots of a chunk written
   __shared__ __align__(8) uint64_t u_bar[2];                // u' of a chunk written
   __shared__ __align__(8) uint64_t ubar;                    // the unit's u / h values in
-  __shared__ T sd[2][32][kPipeRows];
-  __shared__ T su[2][kPipeRows];
+  __shared__ T sd[2][32][kRows];
+  __shared__ T su[2][kRows];
   T* ring = reinterpret_cast<T*>(ring_raw);
-  const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
+  const int64_t stage_elems = (int64_t)mmax * kRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(T));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cw = (blockDim.x >> 5) - 1;   // control warp: copies, u', norms
@@ -1034,11 +1041,11 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const int64_t R0 = cell_pstart[c];
   const bool active = w < m;
   const int s = cover_sub[cover_off[c] + (active ? w : 0)];
-  const uint32_t copy_bytes = (uint32_t)(kPipeRows * K * sizeof(T));
+  const uint32_t copy_bytes = (uint32_t)(kRows * K * sizeof(T));
   const int nrows = un.z - un.y;
-  const int nchunks = nrows / kPipeRows;
+  const int nchunks = nrows / kRows;
   // the unit's rows of all m covering panels form one contiguous block
-  // (cell-interleaved storage): chunk q = element rows base_row + q kPipeRows m ...
+  // (cell-interleaved storage): chunk q = element rows base_row + q kRows m ...
   const int64_t base_row = entry_base[cover_off[c]] + (int64_t)un.y * m;
   if (threadIdx.x == 0) {
     for (int q = 0; q < S; ++q) {
@@ -1046,15 +1053,17 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
       sm100::mbar_init(&empty[q], (uint32_t)m);
     }
     for (int b = 0; b < 2; ++b) {
-      sm100::mbar_init(&dots_bar[b], 4u * (uint32_t)m);   // lanes 0, 8, 16, 24 of each warp
-      sm100::mbar_init(&u_bar[b], 4u);
+      sm100::mbar_init(&dots_bar[b], (uint32_t)(kRows * m));   // one arrival per row and warp
+      sm100::mbar_init(&u_bar[b], (uint32_t)kRows);
     }
     sm100::mbar_init(&ubar, 1);
     sm100::fence_mbar_init();
   }
   __syncthreads();   // the only block-wide barrier
   bool ok = true;
-  const int yr = lane >> 3, yg = lane & 7;
+  // control warp: kYG lanes (panel groups) per row of a chunk
+  constexpr int kYG = 32 / kRows;
+  const int yr = lane / kYG, yg = lane % kYG;
 
   if (w == cw) {
     // ---------------------------------------------------------- control warp
@@ -1062,7 +1071,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
       if (lane == 0) {
         sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
         sm100::bulk_load(ring + stage * stage_elems,
-                         panels + (base_row + (int64_t)chunk * kPipeRows * m) * K,
+                         panels + (base_row + (int64_t)chunk * kRows * m) * K,
                          copy_bytes * (uint32_t)m, &full[stage]);
       }
     };
@@ -1084,12 +1093,11 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
       const int b = j & 1;
       if (!sm100::mbar_wait(&dots_bar[b], (j >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
       T part = T(0);
-      for (int q = yg; q < m; q += 8) part += sd[b][q][yr];
-      part += __shfl_xor_sync(0xffffffffu, part, 4);
-      part += __shfl_xor_sync(0xffffffffu, part, 2);
-      part += __shfl_xor_sync(0xffffffffu, part, 1);
+      for (int q = yg; q < m; q += kYG) part += sd[b][q][yr];
+#pragma unroll
+      for (int o = kYG / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
       if (yg == 0) {
-        const int pr = j * kPipeRows + yr;   // row within the unit
+        const int pr = j * kRows + yr;   // row within the unit
         double out = 0.0;
         if (un.y + pr < cnt) {
           const double uo = us[pr];
@@ -1142,7 +1150,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
 #pragma unroll
     for (int j = 0; j < FPL; ++j) acc[j] = T(0);
 #pragma unroll
-    for (int r = 0; r < kPipeRows; ++r) {
+    for (int r = 0; r < kRows; ++r) {
       const T ur = su[b][r];
       T x[FPL];
       load_slice<T, FPL>(sp + (int64_t)r * m * K, x, whole, rem);
@@ -1168,19 +1176,23 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   for (int i = 0; i < nchunks; ++i) {
     if (!sm100::mbar_wait(&full[st_i], ph_i, ok ? sm100::kSpinLimit : 4u)) ok = false;
     const T* sp = ring + st_i * stage_elems + (int64_t)w * K + k0;   // row r at + r m K
-    T d[kPipeRows];
+    T d[kRows];
 #pragma unroll
-    for (int r = 0; r < kPipeRows; ++r) {
+    for (int r = 0; r < kRows; ++r) {
       T x[FPL];
       load_slice<T, FPL>(sp + (int64_t)r * m * K, x, whole, rem);
       d[r] = T(0);
 #pragma unroll
       for (int j = 0; j < FPL; ++j) d[r] += x[j] * tv[j];
     }
-    const T tot = warp_sum4(d[0], d[1], d[2], d[3], lane);
-    if (yg == 0) {
-      sd[i & 1][w][yr] = tot;
-      sm100::mbar_arrive(&dots_bar[i & 1]);
+    // butterflies of 4 rows: lane 8r holds row 4h + r of group h
+#pragma unroll
+    for (int h4 = 0; h4 < kRows / 4; ++h4) {
+      const T tot = warp_sum4(d[4 * h4], d[4 * h4 + 1], d[4 * h4 + 2], d[4 * h4 + 3], lane);
+      if ((lane & 7) == 0) {
+        sd[i & 1][w][4 * h4 + (lane >> 3)] = tot;
+        sm100::mbar_arrive(&dots_bar[i & 1]);
+      }
     }
     if (i >= 1) update(i - 1, st_prev);
     st_prev = st_i;
@@ -1510,11 +1522,12 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;
 }
 
-// k_precond with X_j held as FP32 pairs (FP32 and DF32 panels): the products
-// and sums of t_j = X_j^T v_j run in float-float arithmetic on the FP32 pipes
-// (about 2^-48 relative), so that the only FP64 work left is splitting v_j
-// and forming t_j.  Same group split and fixed summation order as k_precond.
-__global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ Xr2,
+// k_precond with X_j held as the packed pair triangle (FP32 and DF32 panels):
+// the products and sums of t_j = X_j^T v_j run in float-float arithmetic on
+// the FP32 pipes (about 2^-48 relative), so that the only FP64 work left is
+// splitting v_j and forming t_j.  Same group split and fixed summation order
+// as k_precond.
+__global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ Xt,
                                                      const double* __restrict__ v, int K,
                                                      double* __restrict__ t, int identity,
                                                      double* __restrict__ scal,
@@ -1538,12 +1551,12 @@ __global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ 
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
   const int chunk = (K + G - 1) / G;
-  const float2* X = Xr2 + (int64_t)s * K * K;
+  const float2* X = Xt + (int64_t)s * tri_pairs(K);
   if (g < G && i < K) {
     float S = 0.f, C = 0.f;
     const int m1 = min(K, (g + 1) * chunk);
     for (int m = max(i, g * chunk); m < m1; ++m) {
-      const float2 x = X[m * K + i];
+      const float2 x = X[m * (m + 1) / 2 + i];
       df_acc(S, C, x.x, x.y, vs[m].x, vs[m].y);
     }
     part[g * K + i] = make_float2(S, C);
@@ -1558,33 +1571,75 @@ __global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ 
   }
 }
 
-// k_panel_T2 for FP32-pair partials with X_j held as FP32 pairs: the slice
-// sums, the scaling by 1/beta and X_j z_j run in float-float arithmetic;
-// FP64 is left for beta, v' = X_j z_j - beta v_j and its norm.
-__global__ void __launch_bounds__(1024) k_panel_T2_df(
-    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xc2,
-    int K, const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
-    double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial) {
-  extern __shared__ double zsh[];   // [groups][K] then z[K], here as FP32 pairs
+// Block size of the kernels that apply the packed pair triangle: 512 threads
+// and about 70 KB of shared memory at K = 128, three blocks per SM, so that
+// every panel of the 2-D workloads (a few hundred) runs in one wave.
+constexpr int kTriThreads = 512;
+
+// Shared memory of those kernels: the triangle, a K-vector of pairs, G x K
+// group partials and the copy's mbarrier.
+static size_t tri_smem_bytes(int K) {
+  const int Kp = (K + 31) & ~31;
+  const int G = kTriThreads / Kp;
+  return (size_t)(tri_pairs(K) + K + (int64_t)G * K) * sizeof(float2) + 16;
+}
+
+// One bulk copy of panel s's triangle into shared memory (thread 0 issues it;
+// the caller's next __syncthreads publishes the mbarrier's initialisation).
+__device__ __forceinline__ void tri_fetch(float2* Xs, const float2* __restrict__ Xt, int s, int K,
+                                          uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    const int64_t P = tri_pairs(K);
+    sm100::mbar_init(bar, 1);
+    sm100::fence_mbar_init();
+    sm100::mbar_arrive_expect_tx(bar, (uint32_t)(P * sizeof(float2)));
+    sm100::bulk_load(Xs, Xt + (int64_t)s * P, (uint32_t)(P * sizeof(float2)), bar);
+  }
+}
+
+// Bounded wait for tri_fetch's copy.  On a timeout flags[3] is raised and the
+// block waits once more (bounded) for the copy still in flight, then goes on
+// with whatever arrived; the host turns the flag into ELMFB_ERR_TIMEOUT.
+__device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags) {
+  if (!sm100::mbar_wait(bar, 0)) {
+    if (threadIdx.x == 0) atomicOr(&flags[3], 1);
+    sm100::mbar_wait(bar, 0);
+  }
+}
+
+// k_panel_T2 for FP32-pair partials with X_j as the packed pair triangle: the
+// slice sums, the scaling by 1/beta and y = X_j z_j run in float-float
+// arithmetic; FP64 is left for beta, v' = y - beta v_j and its norm.  The
+// triangle arrives by one bulk copy issued at the start, so it streams in
+// while the slice sums run.  y_k = sum_{m<=k} X_km z_m: each warp takes rows
+// k = w, w + nw, ... four at a time, its lanes the terms m = l, l + 32, ...,
+// and one warp_sum4_df per four rows (a fixed order, so the result does not
+// depend on timing).
+__global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
+    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
+    int K, double* __restrict__ v, double* __restrict__ scal, int init,
+    double* __restrict__ norm_partial, int* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char trsm[];   // X, z, part[G][K], mbarrier
   __shared__ double red[33];
+  __shared__ double sh_beta;
+  __shared__ float2 sh_ib;
   const int s = blockIdx.x;
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
-  __shared__ double sh_beta;
-  __shared__ float2 sh_ib;
+  float2* Xs = reinterpret_cast<float2*>(trsm);
+  float2* zs = Xs + tri_pairs(K);
+  float2* part = zs + K;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
+  tri_fetch(Xs, Xt, s, K, bar);
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
     const double bt = sqrt(scal[kStage + S_BSQ]);   // k_panel_chunks formed beta^2
     sh_beta = bt;
     sh_ib = df_split(bt > 0.0 ? 1.0 / bt : 0.0);
   }
-  __syncthreads();
-  const double beta = sh_beta;
-  const float2 ib = sh_ib;
-  float2* part = reinterpret_cast<float2*>(zsh);
-  float2* zs = part + G * K;
   if (g < G && k < K) {
     float hi = 0.f, lo = 0.f;
+#pragma unroll 4
     for (int q = pco[s] + g; q < pco[s + 1]; q += G) {
       const float2 pr = partial_pair(csum, (int64_t)q * K + k);
       ff_add(hi, lo, pr.x, pr.y);
@@ -1592,6 +1647,8 @@ __global__ void __launch_bounds__(1024) k_panel_T2_df(
     part[g * K + k] = make_float2(hi, lo);
   }
   __syncthreads();
+  const double beta = sh_beta;
+  const float2 ib = sh_ib;
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
     float2 z = part[i];
     for (int q = 1; q < G; ++q) z = df_add(z, part[q * K + i]);
@@ -1600,27 +1657,29 @@ __global__ void __launch_bounds__(1024) k_panel_T2_df(
     zs[i] = make_float2(S, C);
   }
   __syncthreads();
-  const float2* X = Xc2 + (int64_t)s * K * K;
-  if (!identity) {
-    // the groups split the sum over mm <= i into fixed slices
-    const int chunk = (K + G - 1) / G;
-    if (g < G && k < K) {
+  tri_wait(bar, flags);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float2* ys = part;   // the group partials are consumed
+  for (int k0 = wid; k0 < K; k0 += 4 * nw) {
+    float2 acc[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int kr = k0 + r * nw;
       float S = 0.f, C = 0.f;
-      const int m1 = min(k + 1, (g + 1) * chunk);
-      for (int mm = g * chunk; mm < m1; ++mm) {
-        const float2 x = X[mm * K + k];
-        df_acc(S, C, x.x, x.y, zs[mm].x, zs[mm].y);
+      if (kr < K) {
+        const float2* row = Xs + kr * (kr + 1) / 2;
+        for (int m = lane; m <= kr; m += 32) df_acc(S, C, row[m].x, row[m].y, zs[m].x, zs[m].y);
       }
-      part[g * K + k] = make_float2(S, C);
+      acc[r] = make_float2(S, C);
     }
-    __syncthreads();
+    const float2 tot = warp_sum4_df(acc[0], acc[1], acc[2], acc[3], lane);
+    const int kr = k0 + (lane >> 3) * nw;
+    if ((lane & 7) == 0 && kr < K) ys[kr] = tot;
   }
+  __syncthreads();
   double nrm = 0.0;
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    float2 a = identity ? zs[i] : part[i];
-    if (!identity)
-      for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + i]);
-    const double acc = (double)a.x + (double)a.y;
+    const double acc = (double)ys[i].x + (double)ys[i].y;
     const double vold = init ? 0.0 : v[(int64_t)s * K + i];
     const double vn = acc - beta * vold;
     v[(int64_t)s * K + i] = vn;
@@ -1743,20 +1802,19 @@ __global__ void k_update(double* __restrict__ scal, const double* __restrict__ a
   }
 }
 
-// The fused path's k_update merged with the next iteration's k_precond, one
-// block per subdomain: alpha = ||v'|| (every block sums the norm partials in
-// the same fixed order; thread 0 runs the recurrence and block 0 stages the
-// scalars, as k_update), then the block updates v, w, x on its K entries and
-// forms t_s = X_s^T v_s for the next fused pass (float-float with FP32-pair X
-// for FP32 / DF32 panels, else FP64), with t's low-precision copy.  The
-// committed scalars are read here and committed later by k_panel_chunks, so
-// no block of this kernel overwrites what another block reads.
-__global__ void __launch_bounds__(1024) k_update_precond(
-    double* __restrict__ scal, const double* __restrict__ alpha_partial, int n_alpha_partial,
-    double* __restrict__ v, double* __restrict__ w, double* __restrict__ x, int K, int init,
-    int identity, const double* __restrict__ Xr, const float2* __restrict__ Xr2,
-    double* __restrict__ t, void* __restrict__ tlow, int low_kind) {
-  extern __shared__ double psh[];   // vs[K] then part[G][K] (FP32 pairs with Xr2)
+// One LSQR step on panel s's K entries (Paige & Saunders 1982: the plane
+// rotation from rhobar, beta and alpha, then the v, w, x updates): alpha =
+// ||v'|| (every block sums the norm partials in the same fixed order; thread 0
+// runs the recurrence, block 0 stages the scalars, as k_update).  sink(i, v_i)
+// receives each normalised v entry.  The committed scalars are read here and
+// committed later by k_panel_chunks, so no block overwrites what another
+// block reads.  Ends with a __syncthreads.
+template <class Sink>
+__device__ __forceinline__ void lsqr_step_panel(double* __restrict__ scal,
+                                                const double* __restrict__ alpha_partial,
+                                                int n_alpha_partial, double* __restrict__ v,
+                                                double* __restrict__ w, double* __restrict__ x,
+                                                int K, int init, Sink sink) {
   __shared__ double shs;
   __shared__ double shv[4];
   const int s = blockIdx.x;
@@ -1789,14 +1847,25 @@ __global__ void __launch_bounds__(1024) k_update_precond(
     shv[0] = ia;
     shv[1] = phi_rho;
     shv[2] = theta_rho;
+    if (s == 0) {
+      double* sg = scal + kStage;
+      sg[S_ALPHA] = alpha;
+      sg[S_BETA] = beta;
+      sg[S_RHOBAR] = rhobar_new;
+      sg[S_PHIBAR] = phibar_new;
+      sg[S_ANORM2] = anorm2;
+      sg[S_RNORM] = phibar_new;
+      sg[S_ARNORM] = arnorm;
+      sg[S_BNORM] = init ? beta : scal[S_BNORM];
+      sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
+      sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
+    }
   }
   __syncthreads();
   ia = shv[0];
   phi_rho = shv[1];
   theta_rho = shv[2];
   const int64_t o = (int64_t)s * K;
-  double* vs = psh;
-  float2* vs2 = reinterpret_cast<float2*>(psh);
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
     const double vn = v[o + i] * ia;   // v_{i+1}
     if (init) {
@@ -1808,70 +1877,98 @@ __global__ void __launch_bounds__(1024) k_update_precond(
       w[o + i] = vn - theta_rho * wi;
     }
     v[o + i] = vn;
-    if (identity) {
-      t[o + i] = vn;
-      store_low(tlow, low_kind, o + i, vn);
-    } else if (Xr2) {
-      vs2[i] = df_split(vn);
-    } else {
-      vs[i] = vn;
-    }
+    sink(i, vn);
   }
-  if (s == 0 && threadIdx.x == 0) {
-    double* sg = scal + kStage;
-    sg[S_ALPHA] = alpha;
-    sg[S_BETA] = beta;
-    sg[S_RHOBAR] = rhobar_new;
-    sg[S_PHIBAR] = phibar_new;
-    sg[S_ANORM2] = anorm2;
-    sg[S_RNORM] = phibar_new;
-    sg[S_ARNORM] = arnorm;
-    sg[S_BNORM] = init ? beta : scal[S_BNORM];
-    sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
-    sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
-  }
-  if (identity) return;
   __syncthreads();
+}
+
+// The fused path's k_update merged with the next iteration's k_precond, one
+// block per subdomain, FP64 X (FP64 panels) or no preconditioner: the LSQR
+// step, then t_s = X_s^T v_s for the next fused pass, with t's low-precision
+// copy.
+__global__ void __launch_bounds__(1024) k_update_precond(
+    double* __restrict__ scal, const double* __restrict__ alpha_partial, int n_alpha_partial,
+    double* __restrict__ v, double* __restrict__ w, double* __restrict__ x, int K, int init,
+    int identity, const double* __restrict__ Xr, double* __restrict__ t,
+    void* __restrict__ tlow, int low_kind) {
+  extern __shared__ double psh[];   // vs[K] then part[G][K]
+  const int64_t o = (int64_t)blockIdx.x * K;
+  double* vs = psh;
+  lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
+                  [&](int i, double vn) {
+                    if (identity) {
+                      t[o + i] = vn;
+                      store_low(tlow, low_kind, o + i, vn);
+                    } else {
+                      vs[i] = vn;
+                    }
+                  });
+  if (identity) return;
   // t_s = X_s^T v_s: G groups split each sum into fixed slices (as k_precond)
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
   const int chunk = (K + G - 1) / G;
   const int m1 = min(K, (g + 1) * chunk);
-  if (Xr2) {
-    float2* part = vs2 + K;
-    const float2* X = Xr2 + (int64_t)s * K * K;
-    if (g < G && i < K) {
-      float S = 0.f, C = 0.f;
-      for (int m = max(i, g * chunk); m < m1; ++m) {
-        const float2 xv = X[m * K + i];
-        df_acc(S, C, xv.x, xv.y, vs2[m].x, vs2[m].y);
-      }
-      part[g * K + i] = make_float2(S, C);
+  double* part = vs + K;
+  const double* X = Xr + (int64_t)blockIdx.x * K * K;
+  if (g < G && i < K) {
+    double acc = 0.0;
+    for (int m = max(i, g * chunk); m < m1; ++m) acc += X[m * K + i] * vs[m];
+    part[g * K + i] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < G; ++q) acc += part[q * K + j];
+    t[o + j] = acc;
+    store_low(tlow, low_kind, o + j, acc);
+  }
+}
+
+// k_update_precond for FP32 and DF32 panels: X_s as the packed pair triangle,
+// fetched by one bulk copy issued before the LSQR step so that it streams in
+// meanwhile; t_s = X_s^T v_s in float-float arithmetic.  t_i = sum_{m>=i}
+// X_mi v_m: G groups of Kp threads take fixed slices of the rows m, lane i
+// column i; all lanes of a warp walk the same rows (contiguous in shared
+// memory), those with i > m idle; then one pass adds the group sums in order.
+__global__ void __launch_bounds__(kTriThreads, 3) k_update_precond_tri(
+    double* __restrict__ scal, const double* __restrict__ alpha_partial, int n_alpha_partial,
+    double* __restrict__ v, double* __restrict__ w, double* __restrict__ x, int K, int init,
+    const float2* __restrict__ Xt, double* __restrict__ t, void* __restrict__ tlow,
+    int low_kind, int* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char trsm[];   // X, v, part[G][K], mbarrier
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  float2* Xs = reinterpret_cast<float2*>(trsm);
+  float2* vs = Xs + tri_pairs(K);
+  float2* part = vs + K;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
+  tri_fetch(Xs, Xt, blockIdx.x, K, bar);
+  lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
+                  [&](int i, double vn) { vs[i] = df_split(vn); });
+  tri_wait(bar, flags);
+  const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
+  const int chunk = (K + G - 1) / G;
+  const int m0 = g * chunk, m1 = min(K, m0 + chunk);
+  if (g < G && i < K) {
+    float S = 0.f, C = 0.f;
+    const int wlo = (i & ~31);   // rows below the warp's first column hold nothing for it
+#pragma unroll 4
+    for (int m = max(m0, wlo); m < m1; ++m) {
+      const float2 xv = Xs[m * (m + 1) / 2 + i];
+      if (m >= i) df_acc(S, C, xv.x, xv.y, vs[m].x, vs[m].y);
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-      float2 a = part[j];
-      for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
-      const double acc = (double)a.x + (double)a.y;
-      t[o + j] = acc;
-      store_low(tlow, low_kind, o + j, acc);
-    }
-  } else {
-    double* part = vs + K;
-    const double* X = Xr + (int64_t)s * K * K;
-    if (g < G && i < K) {
-      double acc = 0.0;
-      for (int m = max(i, g * chunk); m < m1; ++m) acc += X[m * K + i] * vs[m];
-      part[g * K + i] = acc;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < K; j += blockDim.x) {
-      double acc = 0.0;
-      for (int q = 0; q < G; ++q) acc += part[q * K + j];
-      t[o + j] = acc;
-      store_low(tlow, low_kind, o + j, acc);
-    }
+    part[g * K + i] = make_float2(S, C);
+  }
+  __syncthreads();
+  const int64_t o = (int64_t)blockIdx.x * K;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    float2 a = part[j];
+    for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
+    const double acc = (double)a.x + (double)a.y;
+    t[o + j] = acc;
+    store_low(tlow, low_kind, o + j, acc);
   }
 }
 
@@ -1971,13 +2068,14 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
 }
 
 // Shared memory for the fused pass's ring and staged u values, per CTA (one
-// CTA per SM).  ELMFB_FUSED_SMEM_KB overrides the default (a tuning knob; the
-// stage count changes timing only, never the arithmetic).
+// CTA per SM): 220 KB, or ELMFB_FUSED_SMEM_KB (a tuning knob; the stage count
+// changes timing only, but a budget without room for three 8-row stages makes
+// the pass take 4-row chunks, which group the compensated sums differently).
 static size_t fused_ring_budget() {
   static const size_t kb = [] {
     const char* e = getenv("ELMFB_FUSED_SMEM_KB");
     const long v = e ? atol(e) : 0;
-    return (size_t)(v >= 64 && v <= 220 ? v : 200);
+    return (size_t)(v >= 64 && v <= 220 ? v : 220);
   }();
   return kb * 1024;
 }
@@ -2040,29 +2138,41 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
   prof_begin(h, KID_FUSED, (double)h->NPR * K * sizeof(T) + 16.0 * h->NR + 8.0 * h->NPhi);
   // bulk-copy ring: S stages of (covering panels x kPipeRows rows x K) elements
   const int mmax = std::max(1, h->max_cover);
-  const size_t stage_bytes = (size_t)mmax * kPipeRows * K * sizeof(T);
   const size_t u_bytes = kMaxUnitRows * sizeof(double);
-  const int S = (int)std::min<size_t>(kPipeMaxStages,
-                                      (fused_ring_budget() - u_bytes) / std::max<size_t>(stage_bytes, 1));
+  auto stages_for = [&](int r) {
+    const size_t sb = std::max<size_t>((size_t)mmax * r * K * sizeof(T), 1);
+    return (int)std::min<size_t>(kPipeMaxStages, (fused_ring_budget() - u_bytes) / sb);
+  };
+  // rows per chunk: 8 while the ring still holds three such stages (fewer,
+  // larger copies and half the per-chunk synchronisation; on the 2-D
+  // workload's 17 covering panels a pass drops from 0.26 to 0.20 ms), else 4.
+  // ELMFB_FUSED_ROWS=4 forces 4 (it changes the grouping of the compensated
+  // sums, not the order of the terms within a row).
+  const char* erows = getenv("ELMFB_FUSED_ROWS");
+  const int rows = ((erows && atoi(erows) == 4) || stages_for(8) < 3) ? 4 : 8;
+  const size_t stage_bytes = (size_t)mmax * rows * K * sizeof(T);
+  const int S = stages_for(rows);
   const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
   // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
-  // ring needs two stages in use plus at least two in flight
+  // ring needs the two stages in use plus at least one in flight
   const int pthreads = fthreads + 32;   // covering-panel warps + the control warp
-  if (S >= 4 && pthreads <= 1024 && (K * sizeof(T)) % 16 == 0 &&
+  if (S >= 3 && pthreads <= 1024 && (K * sizeof(T)) % 16 == 0 &&
       !(force_regs && force_regs[0] == '1')) {
     const size_t smem = (size_t)S * stage_bytes + u_bytes;
-#define ELMFB_FT(F)                                                                            \
-  if (fpl == F) {                                                                              \
-    ensure_dyn_smem((const void*)k_fused_pipe<T, F>, smem);                                   \
-    k_fused_pipe<T, F><<<fp.n_units, pthreads, smem, st>>>(                                    \
+#define ELMFB_FTR(F, R)                                                                        \
+  if (fpl == F && rows == R) {                                                                 \
+    ensure_dyn_smem((const void*)k_fused_pipe<T, F, R>, smem);                                \
+    k_fused_pipe<T, F, R><<<fp.n_units, pthreads, smem, st>>>(                                 \
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
         h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
         fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>());                           \
   } else
+#define ELMFB_FT(F) ELMFB_FTR(F, 4) ELMFB_FTR(F, 8)
     ELMFB_FT(1) ELMFB_FT(2) ELMFB_FT(3) ELMFB_FT(4)
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "fused path needs K <= 128");
 #undef ELMFB_FT
+#undef ELMFB_FTR
   } else {
 #define ELMFB_FU(F, MT)                                                                      \
   if (fpl == F && fthreads <= MT) {                                                          \
@@ -2174,12 +2284,11 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
   // FP32 and DF32 panels apply X_j in float-float arithmetic: keep a pair copy
   const bool pairs_x = !std::is_same<T, double>::value;
-  if (pairs_x) h->d_R2.alloc(2 * h->n_sub * KK * sizeof(float2), st);
+  if (pairs_x) h->d_R2.alloc(h->n_sub * tri_pairs(K) * sizeof(float2), st);
   k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(
       h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
       h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr,
-      pairs_x ? h->d_R2.as<float2>() : nullptr,
-      pairs_x ? h->d_R2.as<float2>() + h->n_sub * KK : nullptr);
+      pairs_x ? h->d_R2.as<float2>() : nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
@@ -2302,31 +2411,43 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   // FP32 and DF32 panels apply X_j as FP32 pairs (block_jacobi_setup keeps a
   // pair copy); the fused path's partials are then pairs too
   const bool xpairs = !std::is_same<T, double>::value && fused && fp.pairs && !identity;
-  const float2* Xr2 = xpairs ? h->d_R2.as<float2>() : nullptr;
-  const float2* Xc2 = xpairs ? h->d_R2.as<float2>() + h->n_sub * KK : nullptr;
+  const float2* Xt = xpairs ? h->d_R2.as<float2>() : nullptr;
+  const size_t tsmem = tri_smem_bytes(K);
+  const double tri_bytes = 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
   auto fused_tail = [&](int init) {
-    prof_begin(h, KID_PANEL_T, 8.0 * (double)dfpart.bytes / 8.0 +
-                                   (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
+    // algorithmic bytes: the partials, X's triangle (8 bytes a value), v read and written
+    prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + (identity ? 0.0 : tri_bytes) + 16.0 * N);
     panel_chunk_sums(h, fp, gpart, n_units, scal);
     if (xpairs)
-      k_panel_T2_df<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xc2, K, gpart, n_units, h->d_v.as<double>(),
-          scal, identity ? 1 : 0, init, vpart);
+      k_panel_T2_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
+          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(), scal, init, vpart,
+          h->d_flags.as<int>());
     else
       k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
           fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, gpart, n_units, h->d_v.as<double>(),
           scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
-    prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : (xpairs ? 4.0 : 8.0) * h->n_sub * KK));
-    k_update_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
-        scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(), h->d_x_sol.as<double>(),
-        K, init, identity ? 1 : 0, Xr, Xr2, h->d_tmp.as<double>(), fp.tf.p, low_kind);
+    prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : tri_bytes));
+    if (xpairs)
+      k_update_precond_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
+          scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
+          h->d_x_sol.as<double>(), K, init, Xt, h->d_tmp.as<double>(), fp.tf.p, low_kind,
+          h->d_flags.as<int>());
+    else
+      k_update_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
+          scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
+          h->d_x_sol.as<double>(), K, init, identity ? 1 : 0, Xr, h->d_tmp.as<double>(), fp.tf.p,
+          low_kind);
     prof_end(h, KID_UPDATE);
   };
   if (fused && p2smem > 48 * 1024)
     ensure_dyn_smem((const void*)k_panel_T2, p2smem);
+  if (xpairs) {
+    ensure_dyn_smem((const void*)k_panel_T2_tri, tsmem);
+    ensure_dyn_smem((const void*)k_update_precond_tri, tsmem);
+  }
 
   stage_begin(h, 5);
   // start: b = h (cold) or h - M a0 (warm start)
@@ -2395,7 +2516,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   }
   // a = (a0 +) P y
   if (xpairs)
-    k_precond_df<<<h->n_sub, pc_threads, pc_smem, st>>>(Xr2, h->d_x_sol.as<double>(), K,
+    k_precond_df<<<h->n_sub, pc_threads, pc_smem, st>>>(Xt, h->d_x_sol.as<double>(), K,
                                                          h->d_tmp.as<double>(), identity, scal,
                                                          nullptr, 0);
   else

@@ -51,6 +51,42 @@ def test_plain_lsqr_iterates_match_oracle_lsqr():
         assert np.linalg.norm(a - a_ref) <= 1e-10 * np.linalg.norm(a_ref)
 
 
+@pytest.mark.parametrize("prec", [E.FP64, E.DF32])
+@pytest.mark.parametrize("levels,K", [((1, 2, 4), 32), ((1, 2), 64), ((1, 2), 128)])
+def test_block_jacobi_lsqr_iterates_match_preconditioned_lsqr(prec, levels, K):
+    """With the block-Jacobi preconditioner the GPU runs LSQR on M P, P =
+    diag_j R_j^{-1} with R_j^T R_j = G_jj + shift tr(G_jj)/K I and G_jj =
+    M_j^T M_j (M_j: the K columns of subdomain j), and returns a = P y.  Its
+    first iterates match SciPy's LSQR run on the same operator, built here in
+    FP64 from the oracle's M.  This checks the preconditioner's set-up and its
+    application inside the LSQR loop (both triangular products, the slice sums
+    of M^T u, the update) value by value, for three block geometries.  The
+    shift (1e-4) bounds cond(G_jj + shift) near 3e5, so that rounding-level
+    differences in G_jj stay near 1e-10 in the iterates."""
+    P = WL.poisson2d(levels=levels, features=K, n_side=40, n_boundary_side=40)
+    ref = OS.assemble(P, fmt="dense")
+    M, h = ref["M"], ref["h"]
+    shift = 1e-4
+    n = M.shape[1]
+    Pm = np.zeros((n, n))
+    for j in range(n // K):
+        Mj = M[:, j * K:(j + 1) * K]
+        G = Mj.T @ Mj
+        L = np.linalg.cholesky(G + shift * np.trace(G) / K * np.eye(K))
+        Pm[j * K:(j + 1) * K, j * K:(j + 1) * K] = np.linalg.inv(L.T)
+    A = M @ Pm
+    for k in (1, 2, 3):
+        a_ref = Pm @ spla.lsqr(A, h, atol=0, btol=0, conlim=0, iter_lim=k)[0]
+        with E.Solver.from_problem(P, precision=prec) as s:
+            s.assemble_problem(P)
+            info = s.solve(max_iter=k, atol=0.0, btol=0.0, check_every=1, shift=shift)
+            a = s.coeffs()
+        assert info.iterations == k
+        err = np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)
+        print(f"K={K} prec={prec} iterate {k}: relative difference {err:.2e}")
+        assert err <= 1e-8
+
+
 _SOLVE_CASES = [
     ("poisson1d_J16_K64_N2000", WL.config_poisson1d),
     ("dho_L1-8_K24_N1000", lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000)),
@@ -153,20 +189,23 @@ def test_fp32_panels_solution_vs_paper_protocol():
 
 
 @pytest.mark.parametrize("prec", [E.FP32, E.FP64])
-@pytest.mark.parametrize("registers", ["0", "1"])
-def test_both_fused_pass_variants_meet_paper_protocol_error(prec, registers, monkeypatch):
-    """The fused LSQR pass has a shared-memory pipelined form (bulk copies,
-    FP32 sums of the per-panel dots for FP32 panels) and a register-load form
-    (the fallback when the ring does not fit); each meets the solution bar on
-    its own."""
+@pytest.mark.parametrize("variant", ["pipe8", "pipe4", "registers"])
+def test_both_fused_pass_variants_meet_paper_protocol_error(prec, variant, monkeypatch):
+    """The fused LSQR pass has a shared-memory pipelined form (bulk copies of
+    8-row chunks, or 4-row chunks when three 8-row stages do not fit; FP32
+    sums of the per-panel dots for FP32 panels) and a register-load form (the
+    fallback when the ring does not fit); each meets the solution bar on its
+    own."""
     g = _golden("poisson2d_L1-4_K64_N60")
     P = WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60, n_boundary_side=60)
-    monkeypatch.setenv("ELMFB_FUSED_REGISTERS", registers)
+    monkeypatch.setenv("ELMFB_FUSED_REGISTERS", "1" if variant == "registers" else "0")
+    if variant == "pipe4":
+        monkeypatch.setenv("ELMFB_FUSED_ROWS", "4")
     with E.Solver.from_problem(P, precision=prec) as s:
         s.assemble_problem(P)
         info = s.solve(max_iter=4000, atol=1e-14, btol=1e-14, shift=1e-12)
         err = s.error_norms(s.eval(P.test_points), P.exact(P.test_points))["rel_l2"]
-    print(f"registers={registers} prec={prec}: rel L2 {err:.3e} ({info.iterations} its); "
+    print(f"{variant} prec={prec}: rel L2 {err:.3e} ({info.iterations} its); "
           f"oracle LSQR-15000 {g['lsqr']['rel_l2']:.3e}")
     assert err <= 1.01 * g["lsqr"]["rel_l2"]
 
