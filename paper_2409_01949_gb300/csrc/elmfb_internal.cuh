@@ -186,6 +186,9 @@ struct elmfb_ctx {
   double stage_ms[ELMFB_N_STAGES] = {0};
 
   // per-kernel profiling
+  // other handles run kernels at the same time (batch workers): no
+  // cooperative launches, whose grid barrier needs every block co-resident
+  bool concurrent = false;
   bool prof = false;
   uint64_t prof_mask = ~uint64_t(0);   // kernels timed when prof is on (bit = KernelId)
   std::vector<ProfRec> prof_live;       // recorded, not yet harvested
@@ -228,7 +231,9 @@ struct FusedPlan {
   DevBuf units, fo, fe, part;
   DevBuf tf;            // FP32 copy of t for FP32 panels
   DevBuf pch, pco, csum;   // per-panel slices of the partial list and their sums
+  DevBuf bsq;              // slice sums of the per-unit ||u'||^2 partials (LSQR beta^2)
   int n_pchunks = 0;
+  int n_bsq = 0;
   int n_units = 0;
   int threads = 0;
   bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
@@ -244,8 +249,9 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
                   double* gpart, const void* tf = nullptr);
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
-// fixed slices of each panel's partials; with beta_partial also beta^2 into the
-// staged scalar slot that k_panel_T2 reads
+// fixed slices of each panel's partials; with beta_partial (LSQR) also the
+// slice sums of beta_partial into fp.bsq, from which the panel kernels form
+// beta^2, and the commit of the staged scalars
 void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial = nullptr,
                       int n_beta = 0, double* scal = nullptr);
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials

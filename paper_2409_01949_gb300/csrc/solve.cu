@@ -38,8 +38,7 @@ constexpr int kScal = 32;             // device scalar slots
 constexpr int kStage = 16;
 enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
-  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO,
-  S_BSQ   // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
+  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO
 };
 
 template <class T>
@@ -1409,22 +1408,27 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
 // convention (value hi - lo); FP64 partials are summed in FP64.
 constexpr int kPanelChunk = 32;
 
+// Slices of the fused pass's ||u'||^2 partials (one per work unit) that
+// k_panel_chunks adds, so that the panel kernels form beta^2 from a few sums.
+constexpr int kBetaSlice = 32;
+
 __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __restrict__ fe,
                                const int2* __restrict__ pch, int K, double* __restrict__ csum,
                                int pairs, const double* __restrict__ beta_partial, int n_beta,
-                               double* __restrict__ scal) {
+                               double* __restrict__ scal, double* __restrict__ bsq) {
   __shared__ int ent[kPanelChunk];
-  // block 0, LSQR: commit the scalars staged by k_update_precond (no kernel
-  // of the iteration reads the committed slots before this point), then
-  // warp 0 forms beta^2 = sum of the norm partials, once for every panel block
-  // of k_panel_T2 (same fixed order as block_partial_sum)
-  if (beta_partial && blockIdx.x == 0 && threadIdx.x < kStage && threadIdx.x != S_BSQ)
+  // LSQR: block 0 commits the scalars staged by the previous update (no kernel
+  // of the iteration reads the committed slots before this point); warp 0 of
+  // block b adds slice b of the ||u'||^2 partials (a fixed xor tree), so that
+  // no block carries a long serial sum
+  if (beta_partial && blockIdx.x == 0 && threadIdx.x < kStage)
     scal[threadIdx.x] = scal[kStage + threadIdx.x];
-  if (beta_partial && blockIdx.x == 0 && threadIdx.x < 32) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n_beta; i += 32) v += beta_partial[i];
-    v = warp_sum<double>(v);
-    if (threadIdx.x == 0) scal[kStage + S_BSQ] = v;
+  if (beta_partial && threadIdx.x < 32) {
+    for (int b = blockIdx.x; b * kBetaSlice < n_beta; b += gridDim.x) {
+      const int i = b * kBetaSlice + threadIdx.x;
+      const double v = warp_sum<double>(i < n_beta ? beta_partial[i] : 0.0);
+      if (threadIdx.x == 0) bsq[b] = v;
+    }
   }
   const int2 ch = pch[blockIdx.x];
   const int n = ch.y - ch.x;
@@ -1449,11 +1453,23 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
   }
 }
 
+// beta^2 = the sum of the n slice sums written by k_panel_chunks, added by
+// warp 0 in a fixed order (so every block of a grid forms the same value);
+// valid in warp 0, 0 elsewhere
+__device__ __forceinline__ double beta2_from_slices(const double* __restrict__ bsq, int n) {
+  double v = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < n; i += 32) v += bsq[i];
+    v = warp_sum<double>(v);
+  }
+  return v;
+}
+
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the slice sums of panel j
 // (X_j = R_j^{-T}); several thread groups split the slice list of a panel.
 __global__ void __launch_bounds__(1024) k_panel_T2(
     const double* __restrict__ csum, const int* __restrict__ pco, const double* __restrict__ Xc,
-    int K, const double* __restrict__ beta_partial, int n_beta_partial, double* __restrict__ v,
+    int K, const double* __restrict__ bsq, int n_bsq, double* __restrict__ v,
     double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial,
     int pairs) {
   extern __shared__ double zsh[];   // [groups][K] then z[K]
@@ -1463,8 +1479,9 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
   __shared__ double sh_beta, sh_ib;
+  const double b2 = beta2_from_slices(bsq, n_bsq);
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
-    const double bt = sqrt(scal[kStage + S_BSQ]);   // k_panel_chunks formed beta^2
+    const double bt = sqrt(b2);
     sh_beta = bt;
     sh_ib = bt > 0.0 ? 1.0 / bt : 0.0;
   }
@@ -1607,19 +1624,19 @@ __device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags)
   }
 }
 
-// k_panel_T2 for FP32-pair partials with X_j as the packed pair triangle: the
-// slice sums, the scaling by 1/beta and y = X_j z_j run in float-float
-// arithmetic; FP64 is left for beta, v' = y - beta v_j and its norm.  The
-// triangle arrives by one bulk copy issued at the start, so it streams in
-// while the slice sums run.  y_k = sum_{m<=k} X_km z_m: each warp takes rows
-// k = w, w + nw, ... four at a time, its lanes the terms m = l, l + 32, ...,
-// and one warp_sum4_df per four rows (a fixed order, so the result does not
-// depend on timing).
-__global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
-    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
-    int K, double* __restrict__ v, double* __restrict__ scal, int init,
-    double* __restrict__ norm_partial, int* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char trsm[];   // X, z, part[G][K], mbarrier
+// First half of the LSQR tail for FP32-pair partials with X_j as the packed
+// pair triangle (Xs, fetched by tri_fetch): beta from the slice sums, z_j =
+// the sum of panel j's slice sums, scaled by 1/beta, y = X_j z_j, v' = y -
+// beta v_j (written to v), in float-float arithmetic except beta, v' and its
+// norm.  y_k = sum_{m<=k} X_km z_m: each warp takes rows k = w, w + nw, ...
+// four at a time, its lanes the terms m = l, l + 32, ..., one warp_sum4_df per
+// four rows (a fixed order).  Returns ||v'||^2 of the panel in every thread;
+// block 0 stages beta.
+__device__ double tail_v_tri(const double* __restrict__ csum, const int* __restrict__ pco,
+                             int K, const double* __restrict__ bsq, int n_bsq,
+                             double* __restrict__ v, double* __restrict__ scal, int init,
+                             const float2* Xs, float2* zs, float2* part, uint64_t* bar,
+                             int* __restrict__ flags) {
   __shared__ double red[33];
   __shared__ double sh_beta;
   __shared__ float2 sh_ib;
@@ -1627,13 +1644,9 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
-  float2* Xs = reinterpret_cast<float2*>(trsm);
-  float2* zs = Xs + tri_pairs(K);
-  float2* part = zs + K;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
-  tri_fetch(Xs, Xt, s, K, bar);
+  const double b2 = beta2_from_slices(bsq, n_bsq);
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
-    const double bt = sqrt(scal[kStage + S_BSQ]);   // k_panel_chunks formed beta^2
+    const double bt = sqrt(b2);
     sh_beta = bt;
     sh_ib = df_split(bt > 0.0 ? 1.0 / bt : 0.0);
   }
@@ -1685,11 +1698,75 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
     v[(int64_t)s * K + i] = vn;
     nrm += vn * vn;
   }
-  double tot = block_sum(nrm, red);
-  if (threadIdx.x == 0) norm_partial[blockIdx.x] = tot;
   if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;
+  return block_sum(nrm, red);
 }
 
+// Second half's product for the packed pair triangle: t_s = X_s^T v_s (v_s as
+// pairs in vs) in float-float arithmetic, with t's low-precision copy.
+// t_i = sum_{m>=i} X_mi v_m: G groups of Kp threads take fixed slices of the
+// rows m, lane i column i; all lanes of a warp walk the same rows (contiguous
+// in shared memory), those with i > m idle; then one pass adds the group sums
+// in order.
+__device__ void tail_t_tri(int K, const float2* Xs, const float2* vs, float2* part,
+                           double* __restrict__ t, void* __restrict__ tlow, int low_kind) {
+  const int Kp = (K + 31) & ~31;
+  const int G = blockDim.x / Kp;
+  const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
+  const int chunk = (K + G - 1) / G;
+  const int m0 = g * chunk, m1 = min(K, m0 + chunk);
+  if (g < G && i < K) {
+    float S = 0.f, C = 0.f;
+    const int wlo = (i & ~31);   // rows below the warp's first column hold nothing for it
+#pragma unroll 4
+    for (int m = max(m0, wlo); m < m1; ++m) {
+      const float2 xv = Xs[m * (m + 1) / 2 + i];
+      if (m >= i) df_acc(S, C, xv.x, xv.y, vs[m].x, vs[m].y);
+    }
+    part[g * K + i] = make_float2(S, C);
+  }
+  __syncthreads();
+  const int64_t o = (int64_t)blockIdx.x * K;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    float2 a = part[j];
+    for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
+    const double acc = (double)a.x + (double)a.y;
+    t[o + j] = acc;
+    store_low(tlow, low_kind, o + j, acc);
+  }
+}
+
+// Shared-memory layout of the packed-triangle kernels: X, a K-vector of
+// pairs, part[G][K], the mbarrier.
+struct TriSmem {
+  float2* Xs;
+  float2* vec;
+  float2* part;
+  uint64_t* bar;
+  __device__ TriSmem(unsigned char* raw, int K) {
+    const int G = blockDim.x / ((K + 31) & ~31);
+    Xs = reinterpret_cast<float2*>(raw);
+    vec = Xs + tri_pairs(K);
+    part = vec + K;
+    bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
+  }
+};
+
+// k_panel_T2 for FP32-pair partials with X_j as the packed pair triangle
+// (tail_v_tri; the triangle's bulk copy is issued first, so it streams in
+// while the slice sums run).
+__global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
+    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
+    int K, const double* __restrict__ bsq, int n_bsq, double* __restrict__ v,
+    double* __restrict__ scal, int init, double* __restrict__ norm_partial,
+    int* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char trsm[];
+  TriSmem sm(trsm, K);
+  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
+  const double nrm = tail_v_tri(csum, pco, K, bsq, n_bsq, v, scal, init, sm.Xs, sm.vec, sm.part,
+                                sm.bar, flags);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
+}
 
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the entry partials of panel j
 // (X_j = R_j^{-T}); writes v' (unnormalised) and ||v'||^2 per block.
@@ -1804,8 +1881,9 @@ __global__ void k_update(double* __restrict__ scal, const double* __restrict__ a
 
 // One LSQR step on panel s's K entries (Paige & Saunders 1982: the plane
 // rotation from rhobar, beta and alpha, then the v, w, x updates): alpha =
-// ||v'|| (every block sums the norm partials in the same fixed order; thread 0
-// runs the recurrence, block 0 stages the scalars, as k_update).  sink(i, v_i)
+// ||v'|| (every block sums the norm partials in the same fixed order, with all
+// its threads; thread 0 runs the recurrence, block 0 stages the scalars, as
+// k_update).  sink(i, v_i)
 // receives each normalised v entry.  The committed scalars are read here and
 // committed later by k_panel_chunks, so no block overwrites what another
 // block reads.  Ends with a __syncthreads.
@@ -1815,11 +1893,16 @@ __device__ __forceinline__ void lsqr_step_panel(double* __restrict__ scal,
                                                 int n_alpha_partial, double* __restrict__ v,
                                                 double* __restrict__ w, double* __restrict__ x,
                                                 int K, int init, Sink sink) {
-  __shared__ double shs;
+  __shared__ double red[33];
   __shared__ double shv[4];
   const int s = blockIdx.x;
-  const double a2 = block_partial_sum(alpha_partial, n_alpha_partial, &shs);
-  const double beta = scal[kStage + S_BETA];   // beta_{i+1}
+  // alpha^2: thread-strided sums of the partials, then block_sum (a fixed
+  // order, the same in every block); L2 loads, since in a cooperative launch
+  // other blocks wrote the partials and beta in this kernel
+  double a2 = 0.0;
+  for (int i = threadIdx.x; i < n_alpha_partial; i += blockDim.x) a2 += __ldcg(alpha_partial + i);
+  a2 = block_sum(a2, red);
+  const double beta = __ldcg(scal + kStage + S_BETA);   // beta_{i+1}
   double alpha = 0.0, ia = 0.0, phi_rho = 0.0, theta_rho = 0.0;
   double rhobar_new = 0.0, phibar_new = 0.0, anorm2 = scal[S_ANORM2], arnorm = 0.0;
   if (threadIdx.x == 0) {   // one thread: the recurrence needs FP64 sqrt / divisions
@@ -1928,48 +2011,77 @@ __global__ void __launch_bounds__(1024) k_update_precond(
 
 // k_update_precond for FP32 and DF32 panels: X_s as the packed pair triangle,
 // fetched by one bulk copy issued before the LSQR step so that it streams in
-// meanwhile; t_s = X_s^T v_s in float-float arithmetic.  t_i = sum_{m>=i}
-// X_mi v_m: G groups of Kp threads take fixed slices of the rows m, lane i
-// column i; all lanes of a warp walk the same rows (contiguous in shared
-// memory), those with i > m idle; then one pass adds the group sums in order.
+// meanwhile; t_s = X_s^T v_s by tail_t_tri.
 __global__ void __launch_bounds__(kTriThreads, 3) k_update_precond_tri(
     double* __restrict__ scal, const double* __restrict__ alpha_partial, int n_alpha_partial,
     double* __restrict__ v, double* __restrict__ w, double* __restrict__ x, int K, int init,
     const float2* __restrict__ Xt, double* __restrict__ t, void* __restrict__ tlow,
     int low_kind, int* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char trsm[];   // X, v, part[G][K], mbarrier
-  const int Kp = (K + 31) & ~31;
-  const int G = blockDim.x / Kp;
-  float2* Xs = reinterpret_cast<float2*>(trsm);
-  float2* vs = Xs + tri_pairs(K);
-  float2* part = vs + K;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
-  tri_fetch(Xs, Xt, blockIdx.x, K, bar);
+  extern __shared__ __align__(16) unsigned char trsm[];
+  TriSmem sm(trsm, K);
+  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
+  float2* vs = sm.vec;
   lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
                   [&](int i, double vn) { vs[i] = df_split(vn); });
-  tri_wait(bar, flags);
-  const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
-  const int chunk = (K + G - 1) / G;
-  const int m0 = g * chunk, m1 = min(K, m0 + chunk);
-  if (g < G && i < K) {
-    float S = 0.f, C = 0.f;
-    const int wlo = (i & ~31);   // rows below the warp's first column hold nothing for it
-#pragma unroll 4
-    for (int m = max(m0, wlo); m < m1; ++m) {
-      const float2 xv = Xs[m * (m + 1) / 2 + i];
-      if (m >= i) df_acc(S, C, xv.x, xv.y, vs[m].x, vs[m].y);
+  tri_wait(sm.bar, flags);
+  tail_t_tri(K, sm.Xs, vs, sm.part, t, tlow, low_kind);
+}
+
+// Grid-wide barrier of a cooperative launch (every block co-resident), by
+// generation counting: thread 0 of each block reads the generation, arrives
+// on the counter (release fence first); the last to arrive resets the counter
+// and advances the generation; the others poll it (acquire fence after).  The
+// poll is bounded: after kGridSpinLimit rounds the block raises flags[3] and
+// goes on (the host turns the flag into ELMFB_ERR_TIMEOUT and resets the
+// counter before the next solve).  gbar = {counter, generation}.
+constexpr uint32_t kGridSpinLimit = 1u << 22;   // x ~100 ns: well under a second
+
+__device__ __forceinline__ void grid_sync(unsigned int* gbar, int* __restrict__ flags) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = gbar + 1;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
+      atomicExch(gbar, 0u);
+      __threadfence();
+      atomicAdd(gbar + 1, 1u);
+    } else {
+      uint32_t n = 0;
+      while (*gen == g0) {
+        if (++n > kGridSpinLimit) {
+          atomicOr(&flags[3], 1);
+          break;
+        }
+        __nanosleep(64);
+      }
     }
-    part[g * K + i] = make_float2(S, C);
+    __threadfence();
   }
   __syncthreads();
-  const int64_t o = (int64_t)blockIdx.x * K;
-  for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    float2 a = part[j];
-    for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
-    const double acc = (double)a.x + (double)a.y;
-    t[o + j] = acc;
-    store_low(tlow, low_kind, o + j, acc);
-  }
+}
+
+// The whole LSQR tail in one cooperative launch, one block per panel (FP32
+// and DF32 panels): tail_v_tri (v' and its norm partial), a grid barrier,
+// then the LSQR step (lsqr_step_panel: alpha from all the partials) and t_s =
+// X_s^T v_s.  The triangle is fetched once and serves both products.
+__global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
+    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
+    int K, const double* __restrict__ bsq, int n_bsq, double* __restrict__ v,
+    double* __restrict__ w, double* __restrict__ x, double* __restrict__ scal, int init,
+    double* __restrict__ norm_partial, double* __restrict__ t, void* __restrict__ tlow,
+    int low_kind, unsigned int* __restrict__ gbar, int* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char trsm[];
+  TriSmem sm(trsm, K);
+  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
+  const double nrm = tail_v_tri(csum, pco, K, bsq, n_bsq, v, scal, init, sm.Xs, sm.vec, sm.part,
+                                sm.bar, flags);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
+  grid_sync(gbar, flags);
+  float2* vs = sm.vec;   // z is consumed
+  lsqr_step_panel(scal, norm_partial, gridDim.x, v, w, x, K, init,
+                  [&](int i, double vn) { vs[i] = df_split(vn); });
+  tail_t_tri(K, sm.Xs, vs, sm.part, t, tlow, low_kind);
 }
 
 __global__ void k_add_to(double* __restrict__ a, const double* __restrict__ d, int64_t N) {
@@ -2047,6 +2159,9 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
     }
     pco[h->n_sub] = (int)pch.size();
     fp.n_pchunks = (int)pch.size();
+    fp.n_bsq = (int)ceil_div(std::max(fp.n_units, 1), kBetaSlice);
+    fp.bsq.alloc(fp.n_bsq * sizeof(double), st);
+    CUDA_CHECK(cudaMemsetAsync(fp.bsq.p, 0, fp.n_bsq * sizeof(double), st));
     fp.pch.alloc(std::max<size_t>(pch.size(), 1) * sizeof(int2), st);
     fp.pco.alloc(pco.size() * sizeof(int), st);
     fp.csum.alloc(std::max<size_t>(pch.size(), 1) * K * sizeof(double), st);
@@ -2416,18 +2531,68 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const double tri_bytes = 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
+  // FP32 / DF32 panels: the whole tail (k_panel_T2 + k_update_precond) as one
+  // cooperative launch when every panel's block is co-resident (one wave);
+  // ELMFB_LSQR_TAIL=split keeps the two kernels (a switch for tests)
+  bool coop = false;
+  DevBuf gbar;   // the tail's grid barrier: {counter, generation}
+  if (xpairs) {
+    ensure_dyn_smem((const void*)k_lsqr_tail_tri, tsmem);
+    int dev = 0, nsm = 0, coop_ok = 0, per_sm = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
+    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_tail_tri,
+                                                             kTriThreads, tsmem));
+    const char* e = getenv("ELMFB_LSQR_TAIL");
+    coop = coop_ok && !h->concurrent && (int64_t)per_sm * nsm >= h->n_sub && !(e && e[0] == 's');
+    if (coop) {
+      gbar.alloc(2 * sizeof(unsigned int), st);
+      CUDA_CHECK(cudaMemsetAsync(gbar.p, 0, 2 * sizeof(unsigned int), st));
+    }
+  }
+  const int tail_launches = coop ? 1 : 2;   // besides k_panel_chunks (counted by itself)
   auto fused_tail = [&](int init) {
+    if (coop) {
+      // panel_MTu: the slice sums (the partials read, the slice sums written);
+      // lsqr_update: the rest (slice sums, X's triangle once, v, w, x, t)
+      const double csum_bytes = 8.0 * fp.n_pchunks * K;
+      prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + csum_bytes);
+      panel_chunk_sums(h, fp, gpart, n_units, scal);
+      prof_end(h, KID_PANEL_T);
+      prof_begin(h, KID_UPDATE, csum_bytes + tri_bytes + 64.0 * N);
+      const double* a_csum = fp.csum.as<double>();
+      const int* a_pco = fp.pco.as<int>();
+      const float2* a_Xt = Xt;
+      int a_K = K, a_nbsq = fp.n_bsq, a_init = init, a_low = low_kind;
+      const double* a_bsq = fp.bsq.as<double>();
+      double* a_v = h->d_v.as<double>();
+      double* a_w = h->d_w.as<double>();
+      double* a_x = h->d_x_sol.as<double>();
+      double* a_scal = scal;
+      double* a_np = vpart;
+      double* a_t = h->d_tmp.as<double>();
+      void* a_tlow = fp.tf.p;
+      unsigned int* a_gbar = gbar.as<unsigned int>();
+      int* a_flags = h->d_flags.as<int>();
+      void* args[] = {&a_csum, &a_pco, &a_Xt, &a_K,    &a_bsq,  &a_nbsq, &a_v,    &a_w,    &a_x,
+                      &a_scal, &a_init, &a_np, &a_t, &a_tlow, &a_low,  &a_gbar, &a_flags};
+      CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_lsqr_tail_tri, dim3(h->n_sub),
+                                             dim3(kTriThreads), args, tsmem, st));
+      prof_end(h, KID_UPDATE);
+      return;
+    }
     // algorithmic bytes: the partials, X's triangle (8 bytes a value), v read and written
     prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + (identity ? 0.0 : tri_bytes) + 16.0 * N);
     panel_chunk_sums(h, fp, gpart, n_units, scal);
     if (xpairs)
       k_panel_T2_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(), scal, init, vpart,
-          h->d_flags.as<int>());
+          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, fp.bsq.as<double>(), fp.n_bsq,
+          h->d_v.as<double>(), scal, init, vpart, h->d_flags.as<int>());
     else
       k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, gpart, n_units, h->d_v.as<double>(),
-          scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
+          fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, fp.bsq.as<double>(), fp.n_bsq,
+          h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : tri_bytes));
     if (xpairs)
@@ -2459,7 +2624,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       fused_step(h->d_tmp.as<double>(), 1);
     }
     fused_tail(1);
-    count_launch(h, 2);   // k_panel_T2, k_update (the others count themselves)
+    count_launch(h, tail_launches);   // the tail kernels (the others count themselves)
   } else {
     if (o->warm_start) {
       gather(h->d_a.as<double>(), 1);
@@ -2493,9 +2658,9 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
         transpose_step(0);
       }
     }
-    // fused: k_panel_T2 + k_update_precond (the fused pass and the slice sums
-    // count themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
-    count_launch(h, (fused ? 2 : 5) * batch);
+    // fused: the tail kernels (the fused pass and the slice sums count
+    // themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
+    count_launch(h, (fused ? tail_launches : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
@@ -2503,7 +2668,9 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     int dflags[4];
     CUDA_CHECK(cudaMemcpyAsync(dflags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
-    if (dflags[3]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "fused LSQR pass: a copy wait timed out");
+    if (dflags[3])
+      ELMFB_THROW(ELMFB_ERR_TIMEOUT,
+                  "LSQR iteration: an on-device wait (bulk copy or grid barrier) timed out");
     if (sc[S_BAD] != 0.0) ELMFB_THROW(ELMFB_ERR_NONFINITE, "non-finite LSQR scalar");
     const double anorm = std::sqrt(sc[S_ANORM2]);
     const double rn = sc[S_RNORM], arn = sc[S_ARNORM];
@@ -2849,7 +3016,7 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, i
   const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
   k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(
       fp.part.as<double>(), fp.fe.as<int>(), fp.pch.as<int2>(), h->K, fp.csum.as<double>(),
-      fp.pairs ? 1 : 0, beta_partial, n_beta, scal);
+      fp.pairs ? 1 : 0, beta_partial, n_beta, scal, fp.bsq.as<double>());
   check_launch("k_panel_chunks");
   count_launch(h);
 }
