@@ -241,15 +241,8 @@ void elmfb_default_solve_opts(elmfb_solve_opts* opts);
  * `refine` outer steps a += PCG(G_bf16 + mu I, M^T (h - M a)), each with
  * max_iter PCG iterations preconditioned by the block-Jacobi factors; it
  * needs ELMFB_MIXED precision (tensor-core Gram).
- * With FP32 or DF32 panels the end of each LSQR iteration (the
- * preconditioner's two triangular products and the LSQR update) runs as one
- * cooperative launch with a grid-wide barrier when one block per subdomain
- * fits the GPU at once; environment ELMFB_LSQR_TAIL=split runs it as two
- * kernels instead.  The barrier needs every block of the launch resident:
- * callers that solve on several handles of one GPU at the same time should
- * set ELMFB_LSQR_TAIL=split (elmfb_batch_solve does this for its handles).
  * Errors: STATE before assemble, BREAKDOWN, NONFINITE, INVALID_ARG; TIMEOUT
- * when an on-device wait (a bulk copy, the grid barrier) ran out.
+ * when an on-device wait for a bulk copy ran out.
  * Returns NOT_CONVERGED (with valid coefficients) at the iteration cap. */
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info);
 

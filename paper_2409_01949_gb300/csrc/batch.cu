@@ -51,7 +51,6 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
       elmfb_t h = nullptr;
       int rc = elmfb_create(&h, &it.cfg, st);
       if (rc != ELMFB_OK) std::snprintf(res.message, sizeof(res.message), "create failed");
-      if (rc == ELMFB_OK) h->concurrent = true;
       if (rc == ELMFB_OK) rc = elmfb_assemble(h, it.n_sets, it.sets);
       elmfb_solve_info info{};
       if (rc == ELMFB_OK) {

@@ -186,9 +186,6 @@ struct elmfb_ctx {
   double stage_ms[ELMFB_N_STAGES] = {0};
 
   // per-kernel profiling
-  // other handles run kernels at the same time (batch workers): no
-  // cooperative launches, whose grid barrier needs every block co-resident
-  bool concurrent = false;
   bool prof = false;
   uint64_t prof_mask = ~uint64_t(0);   // kernels timed when prof is on (bit = KernelId)
   std::vector<ProfRec> prof_live;       // recorded, not yet harvested

@@ -1897,12 +1897,11 @@ __device__ __forceinline__ void lsqr_step_panel(double* __restrict__ scal,
   __shared__ double shv[4];
   const int s = blockIdx.x;
   // alpha^2: thread-strided sums of the partials, then block_sum (a fixed
-  // order, the same in every block); L2 loads, since in a cooperative launch
-  // other blocks wrote the partials and beta in this kernel
+  // order, the same in every block)
   double a2 = 0.0;
-  for (int i = threadIdx.x; i < n_alpha_partial; i += blockDim.x) a2 += __ldcg(alpha_partial + i);
+  for (int i = threadIdx.x; i < n_alpha_partial; i += blockDim.x) a2 += alpha_partial[i];
   a2 = block_sum(a2, red);
-  const double beta = __ldcg(scal + kStage + S_BETA);   // beta_{i+1}
+  const double beta = scal[kStage + S_BETA];   // beta_{i+1}
   double alpha = 0.0, ia = 0.0, phi_rho = 0.0, theta_rho = 0.0;
   double rhobar_new = 0.0, phibar_new = 0.0, anorm2 = scal[S_ANORM2], arnorm = 0.0;
   if (threadIdx.x == 0) {   // one thread: the recurrence needs FP64 sqrt / divisions
@@ -2024,63 +2023,6 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_update_precond_tri(
   lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
                   [&](int i, double vn) { vs[i] = df_split(vn); });
   tri_wait(sm.bar, flags);
-  tail_t_tri(K, sm.Xs, vs, sm.part, t, tlow, low_kind);
-}
-
-// Grid-wide barrier of a cooperative launch (every block co-resident), by
-// generation counting: thread 0 of each block reads the generation, arrives
-// on the counter (release fence first); the last to arrive resets the counter
-// and advances the generation; the others poll it (acquire fence after).  The
-// poll is bounded: after kGridSpinLimit rounds the block raises flags[3] and
-// goes on (the host turns the flag into ELMFB_ERR_TIMEOUT and resets the
-// counter before the next solve).  gbar = {counter, generation}.
-constexpr uint32_t kGridSpinLimit = 1u << 22;   // x ~100 ns: well under a second
-
-__device__ __forceinline__ void grid_sync(unsigned int* gbar, int* __restrict__ flags) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* gen = gbar + 1;
-    const unsigned int g0 = *gen;
-    __threadfence();
-    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
-      atomicExch(gbar, 0u);
-      __threadfence();
-      atomicAdd(gbar + 1, 1u);
-    } else {
-      uint32_t n = 0;
-      while (*gen == g0) {
-        if (++n > kGridSpinLimit) {
-          atomicOr(&flags[3], 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// The whole LSQR tail in one cooperative launch, one block per panel (FP32
-// and DF32 panels): tail_v_tri (v' and its norm partial), a grid barrier,
-// then the LSQR step (lsqr_step_panel: alpha from all the partials) and t_s =
-// X_s^T v_s.  The triangle is fetched once and serves both products.
-__global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
-    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
-    int K, const double* __restrict__ bsq, int n_bsq, double* __restrict__ v,
-    double* __restrict__ w, double* __restrict__ x, double* __restrict__ scal, int init,
-    double* __restrict__ norm_partial, double* __restrict__ t, void* __restrict__ tlow,
-    int low_kind, unsigned int* __restrict__ gbar, int* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char trsm[];
-  TriSmem sm(trsm, K);
-  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
-  const double nrm = tail_v_tri(csum, pco, K, bsq, n_bsq, v, scal, init, sm.Xs, sm.vec, sm.part,
-                                sm.bar, flags);
-  if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
-  grid_sync(gbar, flags);
-  float2* vs = sm.vec;   // z is consumed
-  lsqr_step_panel(scal, norm_partial, gridDim.x, v, w, x, K, init,
-                  [&](int i, double vn) { vs[i] = df_split(vn); });
   tail_t_tri(K, sm.Xs, vs, sm.part, t, tlow, low_kind);
 }
 
@@ -2531,57 +2473,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const double tri_bytes = 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
-  // FP32 / DF32 panels: the whole tail (k_panel_T2 + k_update_precond) as one
-  // cooperative launch when every panel's block is co-resident (one wave);
-  // ELMFB_LSQR_TAIL=split keeps the two kernels (a switch for tests)
-  bool coop = false;
-  DevBuf gbar;   // the tail's grid barrier: {counter, generation}
-  if (xpairs) {
-    ensure_dyn_smem((const void*)k_lsqr_tail_tri, tsmem);
-    int dev = 0, nsm = 0, coop_ok = 0, per_sm = 0;
-    CUDA_CHECK(cudaGetDevice(&dev));
-    CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_CHECK(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
-    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lsqr_tail_tri,
-                                                             kTriThreads, tsmem));
-    const char* e = getenv("ELMFB_LSQR_TAIL");
-    coop = coop_ok && !h->concurrent && (int64_t)per_sm * nsm >= h->n_sub && !(e && e[0] == 's');
-    if (coop) {
-      gbar.alloc(2 * sizeof(unsigned int), st);
-      CUDA_CHECK(cudaMemsetAsync(gbar.p, 0, 2 * sizeof(unsigned int), st));
-    }
-  }
-  const int tail_launches = coop ? 1 : 2;   // besides k_panel_chunks (counted by itself)
   auto fused_tail = [&](int init) {
-    if (coop) {
-      // panel_MTu: the slice sums (the partials read, the slice sums written);
-      // lsqr_update: the rest (slice sums, X's triangle once, v, w, x, t)
-      const double csum_bytes = 8.0 * fp.n_pchunks * K;
-      prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + csum_bytes);
-      panel_chunk_sums(h, fp, gpart, n_units, scal);
-      prof_end(h, KID_PANEL_T);
-      prof_begin(h, KID_UPDATE, csum_bytes + tri_bytes + 64.0 * N);
-      const double* a_csum = fp.csum.as<double>();
-      const int* a_pco = fp.pco.as<int>();
-      const float2* a_Xt = Xt;
-      int a_K = K, a_nbsq = fp.n_bsq, a_init = init, a_low = low_kind;
-      const double* a_bsq = fp.bsq.as<double>();
-      double* a_v = h->d_v.as<double>();
-      double* a_w = h->d_w.as<double>();
-      double* a_x = h->d_x_sol.as<double>();
-      double* a_scal = scal;
-      double* a_np = vpart;
-      double* a_t = h->d_tmp.as<double>();
-      void* a_tlow = fp.tf.p;
-      unsigned int* a_gbar = gbar.as<unsigned int>();
-      int* a_flags = h->d_flags.as<int>();
-      void* args[] = {&a_csum, &a_pco, &a_Xt, &a_K,    &a_bsq,  &a_nbsq, &a_v,    &a_w,    &a_x,
-                      &a_scal, &a_init, &a_np, &a_t, &a_tlow, &a_low,  &a_gbar, &a_flags};
-      CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_lsqr_tail_tri, dim3(h->n_sub),
-                                             dim3(kTriThreads), args, tsmem, st));
-      prof_end(h, KID_UPDATE);
-      return;
-    }
     // algorithmic bytes: the partials, X's triangle (8 bytes a value), v read and written
     prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + (identity ? 0.0 : tri_bytes) + 16.0 * N);
     panel_chunk_sums(h, fp, gpart, n_units, scal);
@@ -2624,7 +2516,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       fused_step(h->d_tmp.as<double>(), 1);
     }
     fused_tail(1);
-    count_launch(h, tail_launches);   // the tail kernels (the others count themselves)
+    count_launch(h, 2);   // k_panel_T2, k_update (the others count themselves)
   } else {
     if (o->warm_start) {
       gather(h->d_a.as<double>(), 1);
@@ -2658,9 +2550,9 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
         transpose_step(0);
       }
     }
-    // fused: the tail kernels (the fused pass and the slice sums count
-    // themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
-    count_launch(h, (fused ? tail_launches : 5) * batch);
+    // fused: k_panel_T2 + k_update_precond (the fused pass and the slice sums
+    // count themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
+    count_launch(h, (fused ? 2 : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,

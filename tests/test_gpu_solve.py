@@ -51,11 +51,9 @@ def test_plain_lsqr_iterates_match_oracle_lsqr():
         assert np.linalg.norm(a - a_ref) <= 1e-10 * np.linalg.norm(a_ref)
 
 
-@pytest.mark.parametrize("prec,tail", [(E.FP64, "default"), (E.DF32, "default"),
-                                       (E.DF32, "split")])
+@pytest.mark.parametrize("prec", [E.FP64, E.DF32])
 @pytest.mark.parametrize("levels,K", [((1, 2, 4), 32), ((1, 2), 64), ((1, 2), 128)])
-def test_block_jacobi_lsqr_iterates_match_preconditioned_lsqr(prec, tail, levels, K,
-                                                              monkeypatch):
+def test_block_jacobi_lsqr_iterates_match_preconditioned_lsqr(prec, levels, K):
     """With the block-Jacobi preconditioner the GPU runs LSQR on M P, P =
     diag_j R_j^{-1} with R_j^T R_j = G_jj + shift tr(G_jj)/K I and G_jj =
     M_j^T M_j (M_j: the K columns of subdomain j), and returns a = P y.  Its
@@ -64,11 +62,7 @@ def test_block_jacobi_lsqr_iterates_match_preconditioned_lsqr(prec, tail, levels
     application inside the LSQR loop (both triangular products, the slice sums
     of M^T u, the update) value by value, for three block geometries.  The
     shift (1e-4) bounds cond(G_jj + shift) near 3e5, so that rounding-level
-    differences in G_jj stay near 1e-10 in the iterates.  DF32 runs both forms
-    of the iteration's tail: one cooperative kernel with a grid barrier (the
-    default when every panel's block is co-resident) and two kernels."""
-    if tail == "split":
-        monkeypatch.setenv("ELMFB_LSQR_TAIL", "split")
+    differences in G_jj stay near 1e-10 in the iterates."""
     P = WL.poisson2d(levels=levels, features=K, n_side=40, n_boundary_side=40)
     ref = OS.assemble(P, fmt="dense")
     M, h = ref["M"], ref["h"]
@@ -89,7 +83,7 @@ def test_block_jacobi_lsqr_iterates_match_preconditioned_lsqr(prec, tail, levels
             a = s.coeffs()
         assert info.iterations == k
         err = np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)
-        print(f"K={K} prec={prec} tail={tail} iterate {k}: relative difference {err:.2e}")
+        print(f"K={K} prec={prec} iterate {k}: relative difference {err:.2e}")
         assert err <= 1e-8
 
 
