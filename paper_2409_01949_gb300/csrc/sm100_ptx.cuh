@@ -53,18 +53,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   return false;
 }
 
-// ------------------------------------------- programmatic dependent launch
-// A kernel launched with programmatic stream serialisation may start while the
-// previous kernel of its stream is still running.  pdl_wait blocks the calling
-// thread until that kernel has completed and its writes are visible;
-// pdl_trigger lets the next kernel launch once every block of this one has
-// triggered or exited.  Both are no-ops for a kernel launched without the
-// attribute.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // ---------------------------------------------------------------- TMA
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int32_t x,
                                             int32_t y, uint64_t* bar) {

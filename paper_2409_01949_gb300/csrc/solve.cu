@@ -1059,7 +1059,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     sm100::fence_mbar_init();
   }
   __syncthreads();   // the only block-wide barrier
-  sm100::pdl_trigger();
   bool ok = true;
   // control warp: kYG lanes (panel groups) per row of a chunk
   constexpr int kYG = 32 / kRows;
@@ -1076,9 +1075,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
       }
     };
     for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
-    // the panels and the unit tables are fixed during a solve; u, h, t and the
-    // scalars come from earlier kernels: wait for them only now
-    sm100::pdl_wait();
     if (lane == 0) {
       const uint32_t ub = (uint32_t)(nrows * sizeof(double));
       sm100::mbar_arrive_expect_tx(&ubar, ub);
@@ -1135,7 +1131,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const int k0 = lane * FPL;   // lane slice of the features: k = lane * FPL + j
   const bool whole = k0 + FPL <= K;
   const int rem = K - k0;
-  sm100::pdl_wait();   // t comes from the previous kernel
   T tv[FPL];
 #pragma unroll
   for (int j = 0; j < FPL; ++j) {
@@ -1274,7 +1269,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     sm100::fence_mbar_init();
   }
   __syncthreads();   // the only block-wide barrier
-  sm100::pdl_trigger();
   bool ok = true;
   const int yr = lane >> 3, yg = lane & 7;
 
@@ -1289,9 +1283,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
       }
     };
     for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
-    // the panels and the unit tables are fixed during a solve; u, h, t and the
-    // scalars come from earlier kernels: wait for them only now
-    sm100::pdl_wait();
     if (lane == 0) {
       const uint32_t ub = (uint32_t)(nrows * sizeof(double));
       sm100::mbar_arrive_expect_tx(&ubar, ub);
@@ -1350,7 +1341,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   const int k0 = lane * FPL;   // lane slice of the features: k = lane * FPL + j
   const bool whole = k0 + FPL <= K;
   const int rem = K - k0;
-  sm100::pdl_wait();   // t comes from the previous kernel
   float2 tv[FPL];
 #pragma unroll
   for (int j = 0; j < FPL; ++j) {
@@ -1427,11 +1417,6 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
                                int pairs, const double* __restrict__ beta_partial, int n_beta,
                                double* __restrict__ scal, double* __restrict__ bsq) {
   __shared__ int ent[kPanelChunk];
-  sm100::pdl_trigger();
-  const int2 ch = pch[blockIdx.x];   // the slice tables are fixed during a solve
-  const int n = ch.y - ch.x;
-  if ((int)threadIdx.x < n) ent[threadIdx.x] = fe[ch.x + threadIdx.x];
-  sm100::pdl_wait();   // the partials and the scalars come from earlier kernels
   // LSQR: block 0 commits the scalars staged by the previous update (no kernel
   // of the iteration reads the committed slots before this point); warp 0 of
   // block b adds slice b of the ||u'||^2 partials (a fixed xor tree), so that
@@ -1445,6 +1430,9 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
       if (threadIdx.x == 0) bsq[b] = v;
     }
   }
+  const int2 ch = pch[blockIdx.x];
+  const int n = ch.y - ch.x;
+  if ((int)threadIdx.x < n) ent[threadIdx.x] = fe[ch.x + threadIdx.x];
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const int64_t out = (int64_t)blockIdx.x * K + k;
@@ -1486,8 +1474,6 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
     int pairs) {
   extern __shared__ double zsh[];   // [groups][K] then z[K]
   __shared__ double red[33];
-  sm100::pdl_trigger();
-  sm100::pdl_wait();
   const int s = blockIdx.x;
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
@@ -1776,9 +1762,7 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
     int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char trsm[];
   TriSmem sm(trsm, K);
-  sm100::pdl_trigger();
-  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);   // X is fixed during a solve
-  sm100::pdl_wait();
+  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
   const double nrm = tail_v_tri(csum, pco, K, bsq, n_bsq, v, scal, init, sm.Xs, sm.vec, sm.part,
                                 sm.bar, flags);
   if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
@@ -1990,8 +1974,6 @@ __global__ void __launch_bounds__(1024) k_update_precond(
     int identity, const double* __restrict__ Xr, double* __restrict__ t,
     void* __restrict__ tlow, int low_kind) {
   extern __shared__ double psh[];   // vs[K] then part[G][K]
-  sm100::pdl_trigger();
-  sm100::pdl_wait();
   const int64_t o = (int64_t)blockIdx.x * K;
   double* vs = psh;
   lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
@@ -2036,9 +2018,7 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_update_precond_tri(
     int low_kind, int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char trsm[];
   TriSmem sm(trsm, K);
-  sm100::pdl_trigger();
-  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);   // X is fixed during a solve
-  sm100::pdl_wait();
+  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
   float2* vs = sm.vec;
   lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
                   [&](int i, double vn) { vs[i] = df_split(vn); });
@@ -2063,28 +2043,6 @@ struct SolveLayout {
   std::vector<int> chunk_off;
   std::vector<int> pent_off, pent;
 };
-
-// Launch of a kernel of the LSQR loop (the fused pass, the slice sums, the
-// tail) with programmatic stream serialisation: each of them calls pdl_wait
-// before it touches anything an earlier kernel writes, so that its prologue
-// (barrier set-up, bulk copies of the fixed panels or factors) overlaps the
-// previous kernel's last blocks.  ELMFB_PDL=0 launches them plainly.
-template <typename... KArgs, typename... Args>
-void launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
-              cudaStream_t st, Args... args) {
-  const char* e = getenv("ELMFB_PDL");
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = (e && e[0] == '0') ? 0 : 1;
-  CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, args...));
-}
 
 }  // namespace
 
@@ -2208,7 +2166,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
 #define ELMFB_FD(F)                                                                             \
   if (fpl == F) {                                                                               \
     ensure_dyn_smem((const void*)k_fused_pipe_df<F>, smem);                                     \
-    launch_k(k_fused_pipe_df<F>, fp.n_units, pthreads, smem, st,                                \
+    k_fused_pipe_df<F><<<fp.n_units, pthreads, smem, st>>>(                                     \
         h->d_panels.as<float2>(), (const float2*)tlow, K, fp.units.as<int4>(),                  \
         h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), h->d_cover_off.as<int>(),        \
         h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(),    \
@@ -2261,7 +2219,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
 #define ELMFB_FTR(F, R)                                                                        \
   if (fpl == F && rows == R) {                                                                 \
     ensure_dyn_smem((const void*)k_fused_pipe<T, F, R>, smem);                                \
-    launch_k(k_fused_pipe<T, F, R>, fp.n_units, pthreads, smem, st,                            \
+    k_fused_pipe<T, F, R><<<fp.n_units, pthreads, smem, st>>>(                                 \
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
         h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
@@ -2520,22 +2478,22 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + (identity ? 0.0 : tri_bytes) + 16.0 * N);
     panel_chunk_sums(h, fp, gpart, n_units, scal);
     if (xpairs)
-      launch_k(k_panel_T2_tri, h->n_sub, kTriThreads, tsmem, st,
+      k_panel_T2_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
           fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, fp.bsq.as<double>(), fp.n_bsq,
           h->d_v.as<double>(), scal, init, vpart, h->d_flags.as<int>());
     else
-      launch_k(k_panel_T2, h->n_sub, tgroups * KpT, p2smem, st,
+      k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
           fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, fp.bsq.as<double>(), fp.n_bsq,
           h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : tri_bytes));
     if (xpairs)
-      launch_k(k_update_precond_tri, h->n_sub, kTriThreads, tsmem, st,
+      k_update_precond_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
           scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
           h->d_x_sol.as<double>(), K, init, Xt, h->d_tmp.as<double>(), fp.tf.p, low_kind,
           h->d_flags.as<int>());
     else
-      launch_k(k_update_precond, h->n_sub, pc_threads, pc_smem, st,
+      k_update_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
           scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
           h->d_x_sol.as<double>(), K, init, identity ? 1 : 0, Xr, h->d_tmp.as<double>(), fp.tf.p,
           low_kind);
@@ -2948,7 +2906,7 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, i
                       double* scal) {
   if (fp.n_pchunks == 0) return;
   const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
-  launch_k(k_panel_chunks, fp.n_pchunks, tb, 0, h->stream,
+  k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(
       fp.part.as<double>(), fp.fe.as<int>(), fp.pch.as<int2>(), h->K, fp.csum.as<double>(),
       fp.pairs ? 1 : 0, beta_partial, n_beta, scal, fp.bsq.as<double>());
   check_launch("k_panel_chunks");
