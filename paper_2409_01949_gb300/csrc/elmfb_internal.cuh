@@ -228,9 +228,7 @@ struct FusedPlan {
   DevBuf units, fo, fe, part;
   DevBuf tf;            // FP32 copy of t for FP32 panels
   DevBuf pch, pco, csum;   // per-panel slices of the partial list and their sums
-  DevBuf bsq;              // slice sums of the per-unit ||u'||^2 partials (LSQR beta^2)
   int n_pchunks = 0;
-  int n_bsq = 0;
   int n_units = 0;
   int threads = 0;
   bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
@@ -247,8 +245,8 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double
 template <class T>
 void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
 // fixed slices of each panel's partials; with beta_partial (LSQR) also the
-// slice sums of beta_partial into fp.bsq, from which the panel kernels form
-// beta^2, and the commit of the staged scalars
+// commit of the staged scalars and beta^2 into the staged slot that the panel
+// kernels read
 void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial = nullptr,
                       int n_beta = 0, double* scal = nullptr);
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials

@@ -38,7 +38,8 @@ constexpr int kScal = 32;             // device scalar slots
 constexpr int kStage = 16;
 enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
-  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO
+  S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO,
+  S_BSQ   // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
 };
 
 template <class T>
@@ -527,14 +528,18 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
     }
 }
 
-constexpr int kCholThreads = 512;   // 4 per column of X at K = 128
+constexpr int kCholThreads = 512;   // 4 slices x 128 columns in the inverse
+static_assert(kCholThreads == 4 * 128, "k_block_chol's inverse maps 512 threads");
 
 // One block per subdomain: sum the chunk partials, shift, Cholesky
 // (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
 // column-major (and, given xtri, as the packed pair triangle).  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
-// Right-looking factorisation with a 2-D split of the trailing update; the
-// inverse is formed in place in shared memory row by row (row i of X needs
-// row i of L and rows < i of X), four threads per column splitting each sum.
+// Right-looking factorisation: column k, once scaled, is also copied to a
+// contiguous vector, and the trailing update runs one warp per row with the
+// lanes over columns, so that no shared-memory access strides by a row.  The
+// inverse is formed in place row by row (row i of X needs row i of L and rows
+// < i of X): lanes over columns j, four warp-uniform slices of the sum over m,
+// the slice sums added through shared memory in a fixed order.
 // FP64 throughout: the blocks are as ill-conditioned as the shift allows.
 __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __restrict__ partial,
                                                      const int* __restrict__ chunk_off, int K,
@@ -549,20 +554,40 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   __shared__ double diag0[128];
   __shared__ double rpiv[128];    // 1 / L_kk
   __shared__ double xrow[128];
+  __shared__ double colk[128];       // scaled column k of L
+  __shared__ double xpart[4][128];   // slice sums of a row of the inverse
   __shared__ int fail;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int KT = K * (K + 1) / 2;
   const int c0 = chunk_off[s], c1 = chunk_off[s + 1];
-  // assemble the symmetric G from the upper-triangle partials
-  for (int idx = tid; idx < K * K; idx += nt) {
-    const int i = idx / K, j = idx - i * K;
-    if (j < i) continue;
-    const int pidx = i * K - i * (i - 1) / 2 + (j - i);
-    double v = 0.0;
-    for (int c = c0; c < c1; ++c) v += partial[(int64_t)c * KT + pidx];
-    G[i * K + j] = v;
-    G[j * K + i] = v;
+  // assemble the symmetric G from the upper-triangle partials, chunk by chunk
+  // (each entry's sum runs over the chunks in order; a thread's entries of
+  // one chunk are loaded together)
+  constexpr int kPer = (128 * 129 / 2 + kCholThreads - 1) / kCholThreads;
+  double acc[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) acc[r] = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    const double* pc = partial + (int64_t)c * KT;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int pidx = tid + r * kCholThreads;
+      if (pidx < KT) acc[r] += pc[pidx];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    int pidx = tid + r * kCholThreads;
+    if (pidx >= KT) continue;
+    int i = 0;   // row of the packed upper-triangle index
+    while (pidx >= K - i) {
+      pidx -= K - i;
+      ++i;
+    }
+    const int j = i + pidx;
+    G[i * K + j] = acc[r];
+    G[j * K + i] = acc[r];
   }
   __syncthreads();
   if (gdiag_out) {
@@ -577,8 +602,8 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
     }
     tr = block_sum(v, red);
   }
-  // 2-D thread layout for the trailing update: 16 x (nt / 16)
-  const int tx = tid & 15, ty = tid >> 4, ny = nt >> 4;
+  // trailing update: warp wr takes rows k + 1 + wr, + nwr, ...; lanes the columns
+  const int lane = tid & 31, wr = tid >> 5, nwr = nt >> 5;
   double eps = shift;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (attempt > 0) {
@@ -606,11 +631,15 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
       __syncthreads();
       if (fail) break;
       const double rp = rpiv[k];
-      for (int i = k + 1 + tid; i < K; i += nt) G[i * K + k] *= rp;
+      for (int i = k + 1 + tid; i < K; i += nt) {
+        const double l = G[i * K + k] * rp;
+        G[i * K + k] = l;
+        colk[i] = l;
+      }
       __syncthreads();
-      for (int i = k + 1 + ty; i < K; i += ny) {
-        const double lik = G[i * K + k];
-        for (int j = k + 1 + tx; j <= i; j += 16) G[i * K + j] -= lik * G[j * K + k];
+      for (int i = k + 1 + wr; i < K; i += nwr) {
+        const double lik = colk[i];
+        for (int j = k + 1 + lane; j <= i; j += 32) G[i * K + j] -= lik * colk[j];
       }
       __syncthreads();
     }
@@ -623,17 +652,20 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   }
   // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
   // Row i of L is read while row i of X is formed in xrow, then overwritten.
-  const int j = tid >> 2, part = tid & 3;   // 4 threads per column
+  // Thread (p, j): column j, slice p of [0, i) (rows m < j of X hold no X_mj:
+  // the strict upper triangle of G is untouched, hence the m >= j test).
+  const int j = tid & 127, p = tid >> 7;   // 4 slices at 512 threads
   for (int i = 0; i < K; ++i) {
+    const int step = (i + 3) >> 2;
+    const int m0 = p * step, m1 = min(i, m0 + step);
     double acc = 0.0;
-    if (j < i) {
-      const int len = i - j, step = (len + 3) >> 2;
-      const int m1 = min(i, j + (part + 1) * step);
-      for (int m = j + part * step; m < m1; ++m) acc += G[i * K + m] * G[m * K + j];
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (part == 0 && j < i) xrow[j] = -acc * rpiv[i];
+    if (j < i)
+      for (int m = m0; m < m1; ++m)
+        if (m >= j) acc += G[i * K + m] * G[m * K + j];
+    xpart[p][j] = acc;
+    __syncthreads();
+    if (tid < i) xrow[tid] = -(((xpart[0][tid] + xpart[1][tid]) + xpart[2][tid]) + xpart[3][tid]) *
+                             rpiv[i];
     __syncthreads();
     for (int q = tid; q <= i; q += nt) G[i * K + q] = q == i ? rpiv[i] : xrow[q];
     __syncthreads();
@@ -1408,27 +1440,22 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
 // convention (value hi - lo); FP64 partials are summed in FP64.
 constexpr int kPanelChunk = 32;
 
-// Slices of the fused pass's ||u'||^2 partials (one per work unit) that
-// k_panel_chunks adds, so that the panel kernels form beta^2 from a few sums.
-constexpr int kBetaSlice = 32;
-
 __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __restrict__ fe,
                                const int2* __restrict__ pch, int K, double* __restrict__ csum,
                                int pairs, const double* __restrict__ beta_partial, int n_beta,
-                               double* __restrict__ scal, double* __restrict__ bsq) {
+                               double* __restrict__ scal) {
   __shared__ int ent[kPanelChunk];
-  // LSQR: block 0 commits the scalars staged by the previous update (no kernel
-  // of the iteration reads the committed slots before this point); warp 0 of
-  // block b adds slice b of the ||u'||^2 partials (a fixed xor tree), so that
-  // no block carries a long serial sum
-  if (beta_partial && blockIdx.x == 0 && threadIdx.x < kStage)
+  // block 0, LSQR: commit the scalars staged by the previous update (no kernel
+  // of the iteration reads the committed slots before this point), then
+  // warp 0 forms beta^2 = sum of the norm partials, once for every panel block
+  // of the next kernel (a fixed order)
+  if (beta_partial && blockIdx.x == 0 && threadIdx.x < kStage && threadIdx.x != S_BSQ)
     scal[threadIdx.x] = scal[kStage + threadIdx.x];
-  if (beta_partial && threadIdx.x < 32) {
-    for (int b = blockIdx.x; b * kBetaSlice < n_beta; b += gridDim.x) {
-      const int i = b * kBetaSlice + threadIdx.x;
-      const double v = warp_sum<double>(i < n_beta ? beta_partial[i] : 0.0);
-      if (threadIdx.x == 0) bsq[b] = v;
-    }
+  if (beta_partial && blockIdx.x == 0 && threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n_beta; i += 32) v += beta_partial[i];
+    v = warp_sum<double>(v);
+    if (threadIdx.x == 0) scal[kStage + S_BSQ] = v;
   }
   const int2 ch = pch[blockIdx.x];
   const int n = ch.y - ch.x;
@@ -1453,25 +1480,12 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
   }
 }
 
-// beta^2 = the sum of the n slice sums written by k_panel_chunks, added by
-// warp 0 in a fixed order (so every block of a grid forms the same value);
-// valid in warp 0, 0 elsewhere
-__device__ __forceinline__ double beta2_from_slices(const double* __restrict__ bsq, int n) {
-  double v = 0.0;
-  if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < n; i += 32) v += bsq[i];
-    v = warp_sum<double>(v);
-  }
-  return v;
-}
-
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the slice sums of panel j
 // (X_j = R_j^{-T}); several thread groups split the slice list of a panel.
 __global__ void __launch_bounds__(1024) k_panel_T2(
     const double* __restrict__ csum, const int* __restrict__ pco, const double* __restrict__ Xc,
-    int K, const double* __restrict__ bsq, int n_bsq, double* __restrict__ v,
-    double* __restrict__ scal, int identity, int init, double* __restrict__ norm_partial,
-    int pairs) {
+    int K, double* __restrict__ v, double* __restrict__ scal, int identity, int init,
+    double* __restrict__ norm_partial, int pairs) {
   extern __shared__ double zsh[];   // [groups][K] then z[K]
   __shared__ double red[33];
   const int s = blockIdx.x;
@@ -1479,9 +1493,8 @@ __global__ void __launch_bounds__(1024) k_panel_T2(
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
   __shared__ double sh_beta, sh_ib;
-  const double b2 = beta2_from_slices(bsq, n_bsq);
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
-    const double bt = sqrt(b2);
+    const double bt = sqrt(scal[kStage + S_BSQ]);   // k_panel_chunks formed beta^2
     sh_beta = bt;
     sh_ib = bt > 0.0 ? 1.0 / bt : 0.0;
   }
@@ -1625,7 +1638,8 @@ __device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags)
 }
 
 // First half of the LSQR tail for FP32-pair partials with X_j as the packed
-// pair triangle (Xs, fetched by tri_fetch): beta from the slice sums, z_j =
+// pair triangle (Xs, fetched by tri_fetch): beta (from beta^2 formed by
+// k_panel_chunks), z_j =
 // the sum of panel j's slice sums, scaled by 1/beta, y = X_j z_j, v' = y -
 // beta v_j (written to v), in float-float arithmetic except beta, v' and its
 // norm.  y_k = sum_{m<=k} X_km z_m: each warp takes rows k = w, w + nw, ...
@@ -1633,8 +1647,7 @@ __device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags)
 // four rows (a fixed order).  Returns ||v'||^2 of the panel in every thread;
 // block 0 stages beta.
 __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restrict__ pco,
-                             int K, const double* __restrict__ bsq, int n_bsq,
-                             double* __restrict__ v, double* __restrict__ scal, int init,
+                             int K, double* __restrict__ v, double* __restrict__ scal, int init,
                              const float2* Xs, float2* zs, float2* part, uint64_t* bar,
                              int* __restrict__ flags) {
   __shared__ double red[33];
@@ -1644,9 +1657,8 @@ __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restr
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
-  const double b2 = beta2_from_slices(bsq, n_bsq);
   if (threadIdx.x == 0) {   // one thread: FP64 sqrt / division are costly
-    const double bt = sqrt(b2);
+    const double bt = sqrt(scal[kStage + S_BSQ]);
     sh_beta = bt;
     sh_ib = df_split(bt > 0.0 ? 1.0 / bt : 0.0);
   }
@@ -1757,14 +1769,13 @@ struct TriSmem {
 // while the slice sums run).
 __global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
     const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
-    int K, const double* __restrict__ bsq, int n_bsq, double* __restrict__ v,
-    double* __restrict__ scal, int init, double* __restrict__ norm_partial,
-    int* __restrict__ flags) {
+    int K, double* __restrict__ v, double* __restrict__ scal, int init,
+    double* __restrict__ norm_partial, int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char trsm[];
   TriSmem sm(trsm, K);
   tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
-  const double nrm = tail_v_tri(csum, pco, K, bsq, n_bsq, v, scal, init, sm.Xs, sm.vec, sm.part,
-                                sm.bar, flags);
+  const double nrm = tail_v_tri(csum, pco, K, v, scal, init, sm.Xs, sm.vec, sm.part, sm.bar,
+                                flags);
   if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
 }
 
@@ -2101,9 +2112,6 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
     }
     pco[h->n_sub] = (int)pch.size();
     fp.n_pchunks = (int)pch.size();
-    fp.n_bsq = (int)ceil_div(std::max(fp.n_units, 1), kBetaSlice);
-    fp.bsq.alloc(fp.n_bsq * sizeof(double), st);
-    CUDA_CHECK(cudaMemsetAsync(fp.bsq.p, 0, fp.n_bsq * sizeof(double), st));
     fp.pch.alloc(std::max<size_t>(pch.size(), 1) * sizeof(int2), st);
     fp.pco.alloc(pco.size() * sizeof(int), st);
     fp.csum.alloc(std::max<size_t>(pch.size(), 1) * K * sizeof(double), st);
@@ -2479,12 +2487,12 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     panel_chunk_sums(h, fp, gpart, n_units, scal);
     if (xpairs)
       k_panel_T2_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, fp.bsq.as<double>(), fp.n_bsq,
-          h->d_v.as<double>(), scal, init, vpart, h->d_flags.as<int>());
+          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(), scal, init, vpart,
+          h->d_flags.as<int>());
     else
       k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, fp.bsq.as<double>(), fp.n_bsq,
-          h->d_v.as<double>(), scal, identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
+          fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, h->d_v.as<double>(), scal,
+          identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : tri_bytes));
     if (xpairs)
@@ -2908,7 +2916,7 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, i
   const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
   k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(
       fp.part.as<double>(), fp.fe.as<int>(), fp.pch.as<int2>(), h->K, fp.csum.as<double>(),
-      fp.pairs ? 1 : 0, beta_partial, n_beta, scal, fp.bsq.as<double>());
+      fp.pairs ? 1 : 0, beta_partial, n_beta, scal);
   check_launch("k_panel_chunks");
   count_launch(h);
 }
