@@ -181,12 +181,14 @@ def run_ours(args):
     last = {}
 
     def step(sets, xs, u, uh, profile, stats=None):
-        # profile: "fused" times only the dominant kernel (events around every
-        # kernel would add about 1000 event records to a step); "all" times every
-        # kernel, for the breakdown taken on an extra untimed step
+        # profile: "fused" times only the dominant kernel, every
+        # --roofline-stride-th launch of it (events around every kernel would add
+        # about 1000 event records to a step); "all" times every kernel, for the
+        # breakdown taken on an extra untimed step
         s = E.Solver.from_problem(P, precision=prec, stream=stream.cuda_stream)
         if profile == "fused":
             s.set_profiling_only(DOMINANT)
+            s.set_profiling_stride(args.roofline_stride)
         elif profile == "all":
             s.set_profiling(True)
         s.assemble(sets)
@@ -332,13 +334,16 @@ def run_ours(args):
                                  if prec == E.FP32 else None),
                      "traffic_note": ("DRAM bytes per launch scaled from the ncu capture of the "
                                       "200x200 case" if prec == E.FP32 else None),
-                     "peak_kind": peak_kind},
+                     "peak_kind": peak_kind,
+                     "timed_launches": int(kstats[dom][1]),
+                     "timed_every": args.roofline_stride},
         "assembly": {"kernel": "assemble_panels", "achieved_gbs": asm.get("gbs"),
                      "frac": round(asm["gbs"] / hbm, 4) if asm.get("gbs") else None,
                      "avg_ms": asm.get("avg_ms")},
         "kernels": kern,
         "kernels_note": "per-kernel times from one extra untimed step with every kernel "
-                        "timed; in the timed steps only the roofline kernel carries events",
+                        "timed; in the timed steps only the roofline kernel carries events, "
+                        "on every roofline.timed_every-th launch",
         "stages_ms": {k: round(v, 3) for k, v in last["stages"].items()},
         "gpu_launches": int(launches[0]),
         "e2e": {"value": round(e2e_s, 5), "unit": "s", "h2d_bytes_per_step": int(h2d),
@@ -460,6 +465,8 @@ def main():
     ap.add_argument("--cpu-row-stride", type=int, default=40)
     ap.add_argument("--cpu-lsqr-its", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roofline-stride", type=int, default=8,
+                    help="time every n-th launch of the roofline kernel in the timed steps")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-iters", type=int, default=300)
     ap.add_argument("--batch-workers", type=int, default=8)

@@ -341,6 +341,10 @@ int elmfb_set_profiling(elmfb_t h, int on);
  * (e.g. "fused_Mt_MTu"): the other kernels run without events around them.
  * Clears the totals.  INVALID_ARG for an unknown name. */
 int elmfb_set_profiling_only(elmfb_t h, const char* kernel);
+/* Time only every stride-th launch of each profiled kernel (stride >= 1; 1,
+ * the default, times every launch), so that a long run carries few events.
+ * INVALID_ARG for stride < 1. */
+int elmfb_set_profiling_stride(elmfb_t h, int stride);
 
 /* Device memory of destroyed handles stays cached in the library's
  * stream-ordered pool on each device, so that the next handle reuses it

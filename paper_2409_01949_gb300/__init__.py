@@ -106,6 +106,7 @@ _SIGNATURES = {
     "elmfb_kernel_launches": (C.c_int64, [C.c_void_p]),
     "elmfb_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "elmfb_set_profiling_only": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "elmfb_set_profiling_stride": (C.c_int, [C.c_void_p, C.c_int]),
     "elmfb_trim_memory": (C.c_int, [C.c_int]),
     "elmfb_kernel_stats": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
@@ -465,6 +466,10 @@ class Solver:
     def set_profiling_only(self, kernel: str):
         """Time only the named kernel (names as kernel_stats() reports them)."""
         _check(self.h, lib().elmfb_set_profiling_only(self.h, kernel.encode()))
+
+    def set_profiling_stride(self, stride: int):
+        """Time only every stride-th launch of each profiled kernel."""
+        _check(self.h, lib().elmfb_set_profiling_stride(self.h, int(stride)))
 
     def kernel_stats(self):
         """{name: (total_ms, launches, algorithmic bytes per launch)} of the timed kernels."""

@@ -304,6 +304,8 @@ const char* kKernelNames[KID_COUNT] = {"assemble_panels", "gather_Mv",    "entry
 
 void prof_begin(elmfb_ctx* h, int kid, double bytes) {
   if (!h->prof || !((h->prof_mask >> kid) & 1)) return;
+  h->prof_now[kid] = h->prof_seen[kid]++ % h->prof_stride == 0;
+  if (!h->prof_now[kid]) return;
   ProfRec r{kid, prof_event(h), prof_event(h)};
   CUDA_CHECK(cudaEventRecord(r.a, h->stream));
   h->prof_live.push_back(r);
@@ -311,7 +313,7 @@ void prof_begin(elmfb_ctx* h, int kid, double bytes) {
 }
 
 void prof_end(elmfb_ctx* h, int kid) {
-  if (!h->prof || !((h->prof_mask >> kid) & 1)) return;
+  if (!h->prof || !((h->prof_mask >> kid) & 1) || !h->prof_now[kid]) return;
   for (auto it = h->prof_live.rbegin(); it != h->prof_live.rend(); ++it)
     if (it->kid == kid) {
       CUDA_CHECK(cudaEventRecord(it->b, h->stream));
@@ -566,6 +568,14 @@ int elmfb_set_profiling_only(elmfb_t h, const char* kernel) {
       h->prof_ms[k] = 0.0;
       h->prof_n[k] = 0;
     }
+  });
+}
+
+int elmfb_set_profiling_stride(elmfb_t h, int stride) {
+  return guarded(h, [&] {
+    if (stride < 1) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "profiling stride must be >= 1");
+    h->prof_stride = stride;
+    for (int k = 0; k < KID_COUNT; ++k) h->prof_seen[k] = 0;
   });
 }
 

@@ -193,6 +193,9 @@ struct elmfb_ctx {
   double prof_ms[KID_COUNT] = {0};
   int64_t prof_n[KID_COUNT] = {0};
   double prof_bytes[KID_COUNT] = {0};   // algorithmic bytes per launch (last launch)
+  int prof_stride = 1;                  // time every prof_stride-th launch of a kernel
+  int64_t prof_seen[KID_COUNT] = {0};   // launches seen while profiling
+  bool prof_now[KID_COUNT] = {false};   // the current launch carries events
 
   bool fp64() const { return cfg.precision == ELMFB_FP64; }
   bool df32() const { return cfg.precision == ELMFB_DF32; }
