@@ -540,7 +540,12 @@ static_assert(kCholThreads == 4 * 128, "k_block_chol's inverse maps 512 threads"
 // inverse is formed in place row by row (row i of X needs row i of L and rows
 // < i of X): lanes over columns j, four warp-uniform slices of the sum over m,
 // the slice sums added through shared memory in a fixed order.
-// FP64 throughout: the blocks are as ill-conditioned as the shift allows.
+// The factorisation is FP64 throughout (the blocks are as ill-conditioned as
+// the shift allows).  kDfInv (FP32 and DF32 panels, whose solvers apply X as
+// FP32 pairs anyway): the inverse runs in float-float arithmetic on the FP32
+// pipes (GB300 issues FP64 FMAs at 1/64 of the FP32 rate), each finished row
+// of X stored as pairs over the row of L it replaces.
+template <bool kDfInv>
 __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __restrict__ partial,
                                                      const int* __restrict__ chunk_off, int K,
                                                      double shift, double abs_shift,
@@ -555,7 +560,8 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   __shared__ double rpiv[128];    // 1 / L_kk
   __shared__ double xrow[128];
   __shared__ double colk[128];       // scaled column k of L
-  __shared__ double xpart[4][128];   // slice sums of a row of the inverse
+  __shared__ double xpart[4][128];   // slice sums of a row of the inverse (pairs with kDfInv)
+  __shared__ float2 lrow2[128];      // kDfInv: row i of L as pairs
   __shared__ int fail;
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -655,9 +661,38 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   // Thread (p, j): column j, slice p of [0, i) (rows m < j of X hold no X_mj:
   // the strict upper triangle of G is untouched, hence the m >= j test).
   const int j = tid & 127, p = tid >> 7;   // 4 slices at 512 threads
+  float2* X2 = reinterpret_cast<float2*>(G);   // kDfInv: row m of X as pairs
   for (int i = 0; i < K; ++i) {
     const int step = (i + 3) >> 2;
     const int m0 = p * step, m1 = min(i, m0 + step);
+    if (kDfInv) {
+      for (int m = tid; m < i; m += nt) lrow2[m] = df_split(G[i * K + m]);
+      __syncthreads();
+      float S = 0.f, C = 0.f;
+      if (j < i)
+        for (int m = m0; m < m1; ++m)
+          if (m >= j) {
+            const float2 x = X2[m * K + j];
+            df_acc(S, C, lrow2[m].x, lrow2[m].y, x.x, x.y);
+          }
+      reinterpret_cast<float2*>(&xpart[0][0])[p * 128 + j] = make_float2(S, C);
+      __syncthreads();
+      if (tid <= i) {
+        const float2 rp = df_split(rpiv[i]);
+        float2 v = rp;
+        if (tid < i) {
+          const float2* xp = reinterpret_cast<const float2*>(&xpart[0][0]);
+          const float2 a =
+              df_add(df_add(df_add(xp[tid], xp[128 + tid]), xp[256 + tid]), xp[384 + tid]);
+          float Sv = 0.f, Cv = 0.f;
+          df_acc(Sv, Cv, a.x, a.y, rp.x, rp.y);
+          v = make_float2(-Sv, -Cv);
+        }
+        X2[i * K + tid] = v;
+      }
+      __syncthreads();
+      continue;
+    }
     double acc = 0.0;
     if (j < i)
       for (int m = m0; m < m1; ++m)
@@ -674,11 +709,21 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   double* xc = Xc + (int64_t)s * K * K;
   for (int idx = tid; idx < K * K; idx += nt) {
     const int i = idx / K, jj = idx - i * K;
-    const double v = jj <= i ? G[i * K + jj] : 0.0;
+    double v = 0.0;
+    float2 v2 = make_float2(0.f, 0.f);
+    if (jj <= i) {
+      if (kDfInv) {
+        v2 = X2[i * K + jj];
+        v = (double)v2.x + (double)v2.y;
+      } else {
+        v = G[i * K + jj];
+        v2 = df_split(v);
+      }
+    }
     xr[idx] = v;                          // X_ij row-major
     xc[(int64_t)jj * K + i] = v;          // X_ij column-major
     if (xtri && jj <= i)                  // the triangle again, as packed FP32 pairs
-      xtri[(int64_t)s * tri_pairs(K) + i * (i + 1) / 2 + jj] = df_split(v);
+      xtri[(int64_t)s * tri_pairs(K) + i * (i + 1) / 2 + jj] = v2;
   }
 }
 
@@ -2344,16 +2389,22 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
     count_launch(h);
   }
   const size_t csm = (size_t)KK * sizeof(double);
-  ensure_dyn_smem((const void*)k_block_chol, csm);
+  ensure_dyn_smem((const void*)k_block_chol<false>, csm);
+  ensure_dyn_smem((const void*)k_block_chol<true>, csm);
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
   // FP32 and DF32 panels apply X_j in float-float arithmetic: keep a pair copy
   const bool pairs_x = !std::is_same<T, double>::value;
   if (pairs_x) h->d_R2.alloc(h->n_sub * tri_pairs(K) * sizeof(float2), st);
-  k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(
-      h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
-      h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr,
-      pairs_x ? h->d_R2.as<float2>() : nullptr);
+  if (pairs_x)
+    k_block_chol<true><<<h->n_sub, kCholThreads, csm, st>>>(
+        h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
+        h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr,
+        h->d_R2.as<float2>());
+  else
+    k_block_chol<false><<<h->n_sub, kCholThreads, csm, st>>>(
+        h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
+        h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr, nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
