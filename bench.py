@@ -203,7 +203,11 @@ def run_ours(args):
                 t[2] = by
         if profile == "fused":
             launches[0] += s.kernel_launches()
-        last.update(info=info, err=err, sizes=s.sizes(), stages=s.stage_times())
+        last.update(info=info, err=err)
+        if profile is None or (profile == "all" and "stages" not in last):
+            # report-only queries (sizes() counts the Gram pairs on the host on
+            # first use): taken on the untimed steps, preferably one without events
+            last.update(sizes=s.sizes(), stages=s.stage_times())
         s.close()
         return err
 
