@@ -87,6 +87,31 @@ def test_block_jacobi_lsqr_iterates_match_preconditioned_lsqr(prec, levels, K):
         assert err <= 1e-8
 
 
+@pytest.mark.parametrize("prec", [E.FP64, E.FP32, E.DF32])
+def test_block_cholesky_retries_with_a_larger_shift(prec):
+    """Shift 0 on diagonal blocks of rank < K: the first factorisation meets a
+    non-positive pivot, so the set-up starts again from a fresh copy of the
+    block with the shift raised (1e-14 tr/K, then 100-fold), and the solve
+    proceeds with finite coefficients.  NumPy's Cholesky confirms on the
+    oracle's M that every block is singular at shift 0 and factorises at
+    1e-14 tr/K."""
+    K = 16
+    P = WL.poisson1d(levels=(2, 4), features=K, n_interior=16)
+    M = OS.assemble(P, fmt="dense")["M"]
+    for j in range(M.shape[1] // K):
+        Mj = M[:, j * K:(j + 1) * K]
+        G = Mj.T @ Mj
+        with pytest.raises(np.linalg.LinAlgError):
+            np.linalg.cholesky(G)
+        np.linalg.cholesky(G + 1e-14 * np.trace(G) / K * np.eye(K))
+    with E.Solver.from_problem(P, precision=prec) as s:
+        s.assemble_problem(P)
+        info = s.solve(max_iter=20, atol=0.0, btol=0.0, shift=0.0, check_every=10)
+        a = s.coeffs()
+    assert info.iterations == 20
+    assert np.all(np.isfinite(a))
+
+
 _SOLVE_CASES = [
     ("poisson1d_J16_K64_N2000", WL.config_poisson1d),
     ("dho_L1-8_K24_N1000", lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000)),
