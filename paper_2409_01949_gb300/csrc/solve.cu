@@ -644,17 +644,50 @@ __global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp
         break;
       }
       rp = __shfl_sync(FULL, rp, 0);
-      for (int i = k + 1 + lane; i < K; i += 32) {
-        const double l = P[i * (i + 1) / 2 + k] * rp;
-        P[i * (i + 1) / 2 + k] = l;
-        colk[i] = l;
+      // lane's columns c_g = k + 1 + lane + 32 g of the trailing matrix: their
+      // entries of column k, scaled, stay in registers for the update
+      double cg[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int c = k + 1 + lane + 32 * g;
+        cg[g] = 0.0;
+        if (c < K) {
+          const double l = P[c * (c + 1) / 2 + k] * rp;
+          P[c * (c + 1) / 2 + k] = l;
+          colk[c] = l;
+          cg[g] = l;
+        }
       }
       __syncwarp();
-#pragma unroll 4
-      for (int i = k + 1; i < K; ++i) {
-        const double li = colk[i];
-        double* row = P + i * (i + 1) / 2;
-        for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= li * colk[j];
+      // A_ij -= l_ik l_jk, k < j <= i: four rows at a time, all their loads
+      // before any store (the rows do not overlap, but the compiler cannot
+      // tell), so that the FP64 FMAs of a block issue back to back
+      const int ng = (K - k - 1 + 31) >> 5;   // column groups in use (warp-uniform)
+      for (int i0 = k + 1; i0 < K; i0 += 4) {
+        double v[4][4], li[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int i = i0 + r;
+          li[r] = i < K ? colk[i] : 0.0;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int c = k + 1 + lane + 32 * g;
+            v[r][g] = (g < ng && i < K && c <= i) ? P[i * (i + 1) / 2 + c] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int g = 0; g < 4; ++g) v[r][g] -= li[r] * cg[g];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int i = i0 + r;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int c = k + 1 + lane + 32 * g;
+            if (g < ng && i < K && c <= i) P[i * (i + 1) / 2 + c] = v[r][g];
+          }
+        }
       }
       __syncwarp();
     }
@@ -676,20 +709,25 @@ __global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp
       for (int m = lane; m < i; m += 32) lrow2[m] = df_split(Li[m]);
       __syncwarp();
       const float2 rp2 = df_split(rp);
+      // m outermost: the four column groups' sums are independent chains
+      float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int m = 0; m < i; ++m) {
+        const float2 l = lrow2[m];
+        const float2* xm = X2 + m * (m + 1) / 2;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int j = lane + 32 * g;
+          if (j <= m) {
+            const float2 x = xm[j];
+            df_acc(S[g], C[g], l.x, l.y, x.x, x.y);
+          }
+        }
+      }
       float2 xv[4];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        const int j = lane + 32 * g;
-        float S = 0.f, C = 0.f;
-        if (32 * g < i) {   // warp-uniform: some lane of the group has j < i
-          for (int m = 32 * g; m < i; ++m)
-            if (m >= j) {
-              const float2 x = X2[m * (m + 1) / 2 + j];
-              df_acc(S, C, lrow2[m].x, lrow2[m].y, x.x, x.y);
-            }
-        }
         float Sv = 0.f, Cv = 0.f;
-        df_acc(Sv, Cv, S, C, rp2.x, rp2.y);
+        df_acc(Sv, Cv, S[g], C[g], rp2.x, rp2.y);
         xv[g] = make_float2(-Sv, -Cv);
       }
       __syncwarp();
@@ -701,17 +739,20 @@ __global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp
       if (lane == 0) X2[i * (i + 1) / 2 + i] = rp2;
       __syncwarp();
     } else {
+      // m outermost: the four column groups' sums are independent chains
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int m = 0; m < i; ++m) {
+        const double l = Li[m];
+        const double* xm = P + m * (m + 1) / 2;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const int j = lane + 32 * g;
+          if (j <= m) acc[g] += l * xm[j];
+        }
+      }
       double xv[4];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const int j = lane + 32 * g;
-        double acc = 0.0;
-        if (32 * g < i) {   // warp-uniform: some lane of the group has j < i
-          for (int m = 32 * g; m < i; ++m)
-            if (m >= j) acc += Li[m] * P[m * (m + 1) / 2 + j];
-        }
-        xv[g] = -acc * rp;
-      }
+      for (int g = 0; g < 4; ++g) xv[g] = -acc[g] * rp;
       __syncwarp();
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
