@@ -644,50 +644,49 @@ __global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp
         break;
       }
       rp = __shfl_sync(FULL, rp, 0);
-      // lane's columns c_g = k + 1 + lane + 32 g of the trailing matrix: their
-      // entries of column k, scaled, stay in registers for the update
-      double cg[4];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const int c = k + 1 + lane + 32 * g;
-        cg[g] = 0.0;
-        if (c < K) {
-          const double l = P[c * (c + 1) / 2 + k] * rp;
-          P[c * (c + 1) / 2 + k] = l;
-          colk[c] = l;
-          cg[g] = l;
-        }
+      for (int c = k + 1 + lane; c < K; c += 32) {
+        const double l = P[c * (c + 1) / 2 + k] * rp;
+        P[c * (c + 1) / 2 + k] = l;
+        colk[c] = l;
       }
       __syncwarp();
-      // A_ij -= l_ik l_jk, k < j <= i: four rows at a time, all their loads
-      // before any store (the rows do not overlap, but the compiler cannot
-      // tell), so that the FP64 FMAs of a block issue back to back
-      const int ng = (K - k - 1 + 31) >> 5;   // column groups in use (warp-uniform)
-      for (int i0 = k + 1; i0 < K; i0 += 4) {
-        double v[4][4], li[4];
+      // A_ic -= l_ik l_ck over the trailing triangle k < c <= i < K, flattened
+      // so that every lane has work: pair q = a (a + 1) / 2 + b is row
+      // i = k + 1 + a, column c = k + 1 + b (b <= a); lane l takes q = l,
+      // l + 32, ..., four at a time, all four loads before their stores (the
+      // compiler cannot tell that the entries differ)
+      const int n = K - 1 - k;
+      const int T = n * (n + 1) / 2;
+      int ra = 0;
+      while ((ra + 1) * (ra + 2) / 2 <= lane) ++ra;
+      int rb = lane - ra * (ra + 1) / 2;
+      for (int q0 = lane; q0 < T; q0 += 128) {
+        int idx[4], ii[4], cc[4];
+        bool on[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int i = i0 + r;
-          li[r] = i < K ? colk[i] : 0.0;
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int c = k + 1 + lane + 32 * g;
-            v[r][g] = (g < ng && i < K && c <= i) ? P[i * (i + 1) / 2 + c] : 0.0;
+        for (int u = 0; u < 4; ++u) {
+          on[u] = q0 + 32 * u < T;
+          ii[u] = k + 1 + ra;
+          cc[u] = k + 1 + rb;
+          idx[u] = ii[u] * (ii[u] + 1) / 2 + cc[u];
+          rb += 32;   // the position 32 pairs on
+          while (rb > ra) {
+            rb -= ra + 1;
+            ++ra;
           }
         }
+        double v[4], li[4], lc[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int g = 0; g < 4; ++g) v[r][g] -= li[r] * cg[g];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int i = i0 + r;
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int c = k + 1 + lane + 32 * g;
-            if (g < ng && i < K && c <= i) P[i * (i + 1) / 2 + c] = v[r][g];
-          }
+        for (int u = 0; u < 4; ++u) {
+          v[u] = on[u] ? P[idx[u]] : 0.0;
+          li[u] = on[u] ? colk[ii[u]] : 0.0;
+          lc[u] = on[u] ? colk[cc[u]] : 0.0;
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] -= li[u] * lc[u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (on[u]) P[idx[u]] = v[u];
       }
       __syncwarp();
     }
