@@ -228,6 +228,25 @@ __device__ __forceinline__ DiagStepRows diag_step(const int2* __restrict__ steps
   return {entry_base[st.x] + (int64_t)st.y * m, m * K};
 }
 
+// Four consecutive elements from shared memory (16-byte aligned) as vector
+// loads: a lane's four scalars at a 16-byte lane stride would meet 4-way bank
+// conflicts, one 16-byte load per lane meets none.
+__device__ __forceinline__ void lds4(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&x)[4]) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+  x[0] = v0.x, x[1] = v0.y, x[2] = v1.x, x[3] = v1.y;
+}
+__device__ __forceinline__ void lds4(const float2* p, float2 (&x)[4]) {
+  const float4 v0 = reinterpret_cast<const float4*>(p)[0];
+  const float4 v1 = reinterpret_cast<const float4*>(p)[1];
+  x[0] = make_float2(v0.x, v0.y), x[1] = make_float2(v0.z, v0.w);
+  x[2] = make_float2(v1.x, v1.y), x[3] = make_float2(v1.z, v1.w);
+}
+
 template <class T>
 __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__ panels, int K,
                                                             const int4* __restrict__ chunks,
@@ -236,7 +255,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__
                                                             const int* __restrict__ entry_cell,
                                                             const int* __restrict__ cover_off,
                                                             double* __restrict__ partial) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);   // [16][Kp]
   const int4 ch = chunks[blockIdx.x];     // (panel, first step, steps, -)
   const int Kp = (K + 3) & ~3;
@@ -274,11 +293,8 @@ __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__
 #pragma unroll 4
     for (int r = 0; r < 16; ++r) {
       T x[4], y[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        x[a] = sm[r * Kp + 4 * ti + a];
-        y[a] = sm[r * Kp + 4 * tj + a];
-      }
+      lds4(sm + r * Kp + 4 * ti, x);
+      lds4(sm + r * Kp + 4 * tj, y);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -387,11 +403,8 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
 #pragma unroll 4
       for (int r = 0; r < 16; ++r) {
         T x[4], y[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          x[a] = sm[r * K + 4 * ti + a];
-          y[a] = sm[r * K + 4 * tj + a];
-        }
+        lds4(sm + r * K + 4 * ti, x);
+        lds4(sm + r * K + 4 * tj, y);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -494,11 +507,8 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
 #pragma unroll 2
       for (int r = 0; r < 16; ++r) {
         float2 x[4], y[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          x[a] = sm[r * K + 4 * ti + a];
-          y[a] = sm[r * K + 4 * tj + a];
-        }
+        lds4(sm + r * K + 4 * ti, x);
+        lds4(sm + r * K + 4 * tj, y);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -716,7 +726,7 @@ __global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const int j = lane + 32 * g;
-          if (j <= m) {
+          if (32 * g <= m && j <= m) {   // the first test is warp-uniform
             const float2 x = xm[j];
             df_acc(S[g], C[g], l.x, l.y, x.x, x.y);
           }
@@ -746,7 +756,7 @@ __global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const int j = lane + 32 * g;
-          if (j <= m) acc[g] += l * xm[j];
+          if (32 * g <= m && j <= m) acc[g] += l * xm[j];   // the first test is warp-uniform
         }
       }
       double xv[4];
