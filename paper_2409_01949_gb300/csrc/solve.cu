@@ -538,259 +538,157 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
     }
 }
 
-// Sum of each panel's diagonal-Gram chunk partials (upper-triangle order,
-// FP64) into its packed lower triangle G_s (row i from i (i + 1) / 2 on;
-// tri_pairs(K) doubles per panel, so that each panel starts 16-byte aligned):
-// one thread per entry, the chunks added in order.  grid = (entry blocks, panels).
-__global__ void k_gram_reduce(const double* __restrict__ partial, const int* __restrict__ chunk_off,
-                              int K, double* __restrict__ Gp) {
-  const int s = blockIdx.y;
+constexpr int kCholThreads = 512;   // 4 slices x 128 columns in the inverse
+static_assert(kCholThreads == 4 * 128, "k_block_chol's inverse maps 512 threads");
+
+// One block per subdomain: sum the chunk partials, shift, Cholesky
+// (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
+// column-major (and, given xtri, as the packed pair triangle).  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
+// Right-looking factorisation: column k, once scaled, is also copied to a
+// contiguous vector, and the trailing update runs one warp per row with the
+// lanes over columns, so that no shared-memory access strides by a row.  The
+// inverse is formed in place row by row (row i of X needs row i of L and rows
+// < i of X): lanes over columns j, four warp-uniform slices of the sum over m,
+// the slice sums added through shared memory in a fixed order.
+// FP64 throughout: the blocks are as ill-conditioned as the shift allows.
+__global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __restrict__ partial,
+                                                     const int* __restrict__ chunk_off, int K,
+                                                     double shift, double abs_shift,
+                                                     double* __restrict__ Xr,
+                                                     double* __restrict__ Xc,
+                                                     int* __restrict__ flags,
+                                                     double* __restrict__ gdiag_out,
+                                                     float2* __restrict__ xtri) {
+  extern __shared__ double G[];   // [K][K]
+  __shared__ double red[33];
+  __shared__ double diag0[128];
+  __shared__ double rpiv[128];    // 1 / L_kk
+  __shared__ double xrow[128];
+  __shared__ double colk[128];       // scaled column k of L
+  __shared__ double xpart[4][128];   // slice sums of a row of the inverse
+  __shared__ int fail;
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int KT = K * (K + 1) / 2;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= KT) return;
   const int c0 = chunk_off[s], c1 = chunk_off[s + 1];
-  double v = 0.0;
-#pragma unroll 8
-  for (int c = c0; c < c1; ++c) v += partial[(int64_t)c * KT + e];
-  int i = 0, r = e;   // e = i K - i (i - 1) / 2 + (j - i), i <= j
-  while (r >= K - i) {
-    r -= K - i;
-    ++i;
-  }
-  const int j = i + r;
-  Gp[(int64_t)s * tri_pairs(K) + j * (j + 1) / 2 + i] = v;
-}
-
-// Shared memory of k_block_chol: the packed triangle, column k of L, 1 / L_kk,
-// a row of L as pairs, the copy's mbarrier.
-static size_t chol_smem_bytes(int K) {
-  return (size_t)tri_pairs(K) * sizeof(double) + 3 * 128 * sizeof(double) + 16;
-}
-
-// One warp per subdomain (three per SM, so that a few hundred subdomains are
-// one wave; no block-wide barrier anywhere): G_s arrives by one bulk copy;
-// shift; Cholesky L L^T = G + eps tr/K I, right-looking, column k scaled by
-// lane-parallel rows and copied to a vector, the trailing update one row at
-// a time with the lanes over its columns; then X = L^{-1} in place, row by
-// row (row i of X needs row i of L and rows < i of X): lanes over columns j,
-// the sum over m taken in order, every lane of the warp on the same row m of
-// X (contiguous in shared memory), those with j > m idle.  R_j = L^T, so
-// R_j^{-1} = X^T and R_j^{-T} = X; X is stored row- and column-major in FP64
-// and, given xtri, as the packed pair triangle.  A failed factorisation
-// (non-positive pivot) starts again from a fresh copy of G_s with the shift
-// raised 100-fold, at most 8 times, then raises flags[1].
-// The factorisation is FP64 throughout (the blocks are as ill-conditioned as
-// the shift allows).  kDfInv (FP32 and DF32 panels, whose solvers apply X as
-// FP32 pairs anyway): the inverse runs in float-float arithmetic on the FP32
-// pipes (GB300 issues FP64 FMAs at 1/64 of the FP32 rate), each finished row
-// of X stored as pairs over the row of L it replaces.
-template <bool kDfInv>
-__global__ void __launch_bounds__(32) k_block_chol(const double* __restrict__ Gp, int K,
-                                                   double shift, double abs_shift,
-                                                   double* __restrict__ Xr,
-                                                   double* __restrict__ Xc,
-                                                   int* __restrict__ flags,
-                                                   float2* __restrict__ xtri) {
-  extern __shared__ __align__(16) unsigned char chsm[];
-  const int64_t PT = tri_pairs(K);
-  double* P = reinterpret_cast<double*>(chsm);   // packed lower triangle
-  double* colk = P + PT;                         // [128] scaled column k of L
-  double* rpv = colk + 128;                      // [128] 1 / L_kk
-  float2* lrow2 = reinterpret_cast<float2*>(rpv + 128);   // [128] row i of L as pairs
-  uint64_t* bar = reinterpret_cast<uint64_t*>(lrow2 + 128);
-  float2* X2 = reinterpret_cast<float2*>(P);     // kDfInv: rows of X as pairs
-  const int s = blockIdx.x, lane = threadIdx.x;
-  const unsigned FULL = 0xffffffffu;
-  const uint32_t bytes = (uint32_t)(PT * sizeof(double));
-  if (lane == 0) {
-    sm100::mbar_init(bar, 1);
-    sm100::fence_mbar_init();
-  }
-  __syncwarp();
-  uint32_t phase = 0;
-  bool ok = true;
-  auto fetch = [&]() {
-    sm100::fence_proxy_async_smem();   // every lane's earlier writes to P before the copy
-    __syncwarp();
-    if (lane == 0) {
-      sm100::mbar_arrive_expect_tx(bar, bytes);
-      sm100::bulk_load(P, Gp + (int64_t)s * PT, bytes, bar);
+  // assemble the symmetric G from the upper-triangle partials, chunk by chunk
+  // (each entry's sum runs over the chunks in order; a thread's entries of
+  // one chunk are loaded together)
+  constexpr int kPer = (128 * 129 / 2 + kCholThreads - 1) / kCholThreads;
+  double acc[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) acc[r] = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    const double* pc = partial + (int64_t)c * KT;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int pidx = tid + r * kCholThreads;
+      if (pidx < KT) acc[r] += pc[pidx];
     }
-    if (!sm100::mbar_wait(bar, phase)) {
-      ok = false;
-      sm100::mbar_wait(bar, phase);   // bounded: the copy may still be in flight
+  }
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    int pidx = tid + r * kCholThreads;
+    if (pidx >= KT) continue;
+    int i = 0;   // row of the packed upper-triangle index
+    while (pidx >= K - i) {
+      pidx -= K - i;
+      ++i;
     }
-    phase ^= 1;
-  };
-  fetch();
+    const int j = i + pidx;
+    G[i * K + j] = acc[r];
+    G[j * K + i] = acc[r];
+  }
+  __syncthreads();
+  if (gdiag_out) {
+    for (int idx = tid; idx < K * K; idx += nt) gdiag_out[(int64_t)s * K * K + idx] = G[idx];
+  }
   double tr = 0.0;
-  for (int i = lane; i < K; i += 32) tr += P[i * (i + 1) / 2 + i];
-  tr = warp_sum<double>(tr);
+  {
+    double v = 0.0;
+    for (int i = tid; i < K; i += nt) {
+      v += G[i * K + i];
+      diag0[i] = G[i * K + i];
+    }
+    tr = block_sum(v, red);
+  }
+  // trailing update: warp wr takes rows k + 1 + wr, + nwr, ...; lanes the columns
+  const int lane = tid & 31, wr = tid >> 5, nwr = nt >> 5;
   double eps = shift;
-  bool fail = true;
-  for (int attempt = 0; attempt < 8 && fail && ok; ++attempt) {
+  for (int attempt = 0; attempt < 8; ++attempt) {
     if (attempt > 0) {
-      fetch();
+      // restore the lower triangle from the (untouched) strict upper triangle
+      for (int idx = tid; idx < K * K; idx += nt) {
+        const int i = idx / K, j = idx - i * K;
+        if (i > j) G[i * K + j] = G[j * K + i];
+        else if (i == j) G[i * K + i] = diag0[i];
+      }
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
     const double add = eps * tr / K + abs_shift + (tr == 0.0 && abs_shift == 0.0 ? 1.0 : 0.0);
-    for (int i = lane; i < K; i += 32) P[i * (i + 1) / 2 + i] += add;
-    __syncwarp();
-    fail = false;
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int i = tid; i < K; i += nt) G[i * K + i] += add;
+    __syncthreads();
     for (int k = 0; k < K; ++k) {
-      double rp = 0.0;
-      int bad = 0;
-      if (lane == 0) {   // one lane: FP64 sqrt / division are costly
-        const double d = P[k * (k + 1) / 2 + k];
-        bad = !(d > 0.0);
-        const double l = sqrt(bad ? 1.0 : d);
-        P[k * (k + 1) / 2 + k] = l;
-        rp = 1.0 / l;
-        rpv[k] = rp;
+      if (tid == 0) {
+        const double d = G[k * K + k];
+        if (!(d > 0.0)) fail = 1;
+        const double l = sqrt(d > 0.0 ? d : 1.0);
+        G[k * K + k] = l;
+        rpiv[k] = 1.0 / l;
       }
-      bad = __shfl_sync(FULL, bad, 0);
-      if (bad) {
-        fail = true;
-        break;
+      __syncthreads();
+      if (fail) break;
+      const double rp = rpiv[k];
+      for (int i = k + 1 + tid; i < K; i += nt) {
+        const double l = G[i * K + k] * rp;
+        G[i * K + k] = l;
+        colk[i] = l;
       }
-      rp = __shfl_sync(FULL, rp, 0);
-      for (int c = k + 1 + lane; c < K; c += 32) {
-        const double l = P[c * (c + 1) / 2 + k] * rp;
-        P[c * (c + 1) / 2 + k] = l;
-        colk[c] = l;
+      __syncthreads();
+      for (int i = k + 1 + wr; i < K; i += nwr) {
+        const double lik = colk[i];
+        for (int j = k + 1 + lane; j <= i; j += 32) G[i * K + j] -= lik * colk[j];
       }
-      __syncwarp();
-      // A_ic -= l_ik l_ck over the trailing triangle k < c <= i < K, flattened
-      // so that every lane has work: pair q = a (a + 1) / 2 + b is row
-      // i = k + 1 + a, column c = k + 1 + b (b <= a); lane l takes q = l,
-      // l + 32, ..., four at a time, all four loads before their stores (the
-      // compiler cannot tell that the entries differ)
-      const int n = K - 1 - k;
-      const int T = n * (n + 1) / 2;
-      int ra = 0;
-      while ((ra + 1) * (ra + 2) / 2 <= lane) ++ra;
-      int rb = lane - ra * (ra + 1) / 2;
-      for (int q0 = lane; q0 < T; q0 += 128) {
-        int idx[4], ii[4], cc[4];
-        bool on[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          on[u] = q0 + 32 * u < T;
-          ii[u] = k + 1 + ra;
-          cc[u] = k + 1 + rb;
-          idx[u] = ii[u] * (ii[u] + 1) / 2 + cc[u];
-          rb += 32;   // the position 32 pairs on
-          while (rb > ra) {
-            rb -= ra + 1;
-            ++ra;
-          }
-        }
-        double v[4], li[4], lc[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          v[u] = on[u] ? P[idx[u]] : 0.0;
-          li[u] = on[u] ? colk[ii[u]] : 0.0;
-          lc[u] = on[u] ? colk[cc[u]] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] -= li[u] * lc[u];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (on[u]) P[idx[u]] = v[u];
-      }
-      __syncwarp();
+      __syncthreads();
     }
-  }
-  if (!ok) {
-    if (lane == 0) atomicOr(&flags[3], 1);
-    return;
+    __syncthreads();
+    if (!fail) break;
   }
   if (fail) {
-    if (lane == 0) atomicOr(&flags[1], 1);
+    if (tid == 0) atomicOr(&flags[1], 1);
     return;
   }
   // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
-  // Row i of L is read while row i of X is formed in registers, then written over it.
+  // Row i of L is read while row i of X is formed in xrow, then overwritten.
+  // Thread (p, j): column j, slice p of [0, i) (rows m < j of X hold no X_mj:
+  // the strict upper triangle of G is untouched, hence the m >= j test).
+  const int j = tid & 127, p = tid >> 7;   // 4 slices at 512 threads
   for (int i = 0; i < K; ++i) {
-    const double* Li = P + i * (i + 1) / 2;
-    const double rp = rpv[i];
-    if (kDfInv) {
-      for (int m = lane; m < i; m += 32) lrow2[m] = df_split(Li[m]);
-      __syncwarp();
-      const float2 rp2 = df_split(rp);
-      // m outermost: the four column groups' sums are independent chains
-      float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int m = 0; m < i; ++m) {
-        const float2 l = lrow2[m];
-        const float2* xm = X2 + m * (m + 1) / 2;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const int j = lane + 32 * g;
-          if (32 * g <= m && j <= m) {   // the first test is warp-uniform
-            const float2 x = xm[j];
-            df_acc(S[g], C[g], l.x, l.y, x.x, x.y);
-          }
-        }
-      }
-      float2 xv[4];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        float Sv = 0.f, Cv = 0.f;
-        df_acc(Sv, Cv, S[g], C[g], rp2.x, rp2.y);
-        xv[g] = make_float2(-Sv, -Cv);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const int j = lane + 32 * g;
-        if (j < i) X2[i * (i + 1) / 2 + j] = xv[g];
-      }
-      if (lane == 0) X2[i * (i + 1) / 2 + i] = rp2;
-      __syncwarp();
-    } else {
-      // m outermost: the four column groups' sums are independent chains
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int m = 0; m < i; ++m) {
-        const double l = Li[m];
-        const double* xm = P + m * (m + 1) / 2;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const int j = lane + 32 * g;
-          if (32 * g <= m && j <= m) acc[g] += l * xm[j];   // the first test is warp-uniform
-        }
-      }
-      double xv[4];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) xv[g] = -acc[g] * rp;
-      __syncwarp();
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        const int j = lane + 32 * g;
-        if (j < i) P[i * (i + 1) / 2 + j] = xv[g];
-      }
-      if (lane == 0) P[i * (i + 1) / 2 + i] = rp;
-      __syncwarp();
-    }
+    const int step = (i + 3) >> 2;
+    const int m0 = p * step, m1 = min(i, m0 + step);
+    double acc = 0.0;
+    if (j < i)
+      for (int m = m0; m < m1; ++m)
+        if (m >= j) acc += G[i * K + m] * G[m * K + j];
+    xpart[p][j] = acc;
+    __syncthreads();
+    if (tid < i) xrow[tid] = -(((xpart[0][tid] + xpart[1][tid]) + xpart[2][tid]) + xpart[3][tid]) *
+                             rpiv[i];
+    __syncthreads();
+    for (int q = tid; q <= i; q += nt) G[i * K + q] = q == i ? rpiv[i] : xrow[q];
+    __syncthreads();
   }
-  auto value = [&](int i, int jj) -> double {
-    if (jj > i) return 0.0;
-    const int q = i * (i + 1) / 2 + jj;
-    return kDfInv ? (double)X2[q].x + (double)X2[q].y : P[q];
-  };
   double* xr = Xr + (int64_t)s * K * K;
   double* xc = Xc + (int64_t)s * K * K;
-  for (int o = lane; o < K * K; o += 32) {
-    const int i = o / K, jj = o - i * K;
-    xr[o] = value(i, jj);   // X_ij row-major
-  }
-  for (int o = lane; o < K * K; o += 32) {
-    const int jj = o / K, i = o - jj * K;
-    xc[o] = value(i, jj);   // X_ij column-major
-  }
-  if (xtri) {   // the triangle again, as packed FP32 pairs
-    const int KT = K * (K + 1) / 2;
-    for (int q = lane; q < KT; q += 32)
-      xtri[(int64_t)s * PT + q] = kDfInv ? X2[q] : df_split(P[q]);
+  for (int idx = tid; idx < K * K; idx += nt) {
+    const int i = idx / K, jj = idx - i * K;
+    const double v = jj <= i ? G[i * K + jj] : 0.0;
+    xr[idx] = v;                          // X_ij row-major
+    xc[(int64_t)jj * K + i] = v;          // X_ij column-major
+    if (xtri && jj <= i)                  // the triangle again, as packed FP32 pairs
+      xtri[(int64_t)s * tri_pairs(K) + i * (i + 1) / 2 + jj] = df_split(v);
   }
 }
 
@@ -1573,20 +1471,29 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
   const int n = ch.y - ch.x;
   if ((int)threadIdx.x < n) ent[threadIdx.x] = fe[ch.x + threadIdx.x];
   __syncthreads();
+  // every load of the slice is issued before the first add (one round of L2
+  // latency instead of one per few partials); the adds keep the slice order
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const int64_t out = (int64_t)blockIdx.x * K + k;
     if (pairs) {
+      float2 pr[kPanelChunk];
+#pragma unroll
+      for (int q = 0; q < kPanelChunk; ++q)
+        pr[q] = q < n ? partial_pair(partial, (int64_t)ent[q] * K + k) : make_float2(0.f, 0.f);
       float hi = 0.f, lo = 0.f;
-#pragma unroll 8
-      for (int q = 0; q < n; ++q) {
-        const float2 pr = partial_pair(partial, (int64_t)ent[q] * K + k);
-        ff_add(hi, lo, pr.x, pr.y);
-      }
+#pragma unroll
+      for (int q = 0; q < kPanelChunk; ++q)
+        if (q < n) ff_add(hi, lo, pr[q].x, pr[q].y);
       reinterpret_cast<float2*>(csum)[out] = make_float2(hi, -lo);
     } else {
+      double pv[kPanelChunk];
+#pragma unroll
+      for (int q = 0; q < kPanelChunk; ++q)
+        pv[q] = q < n ? partial[(int64_t)ent[q] * K + k] : 0.0;
       double acc = 0.0;
-#pragma unroll 8
-      for (int q = 0; q < n; ++q) acc += partial[(int64_t)ent[q] * K + k];
+#pragma unroll
+      for (int q = 0; q < kPanelChunk; ++q)
+        if (q < n) acc += pv[q];
       csum[out] = acc;
     }
   }
@@ -2455,30 +2362,17 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
     check_launch("k_gram_diag_partial");
     count_launch(h);
   }
-  // the per-chunk partials summed into one packed triangle per panel, then
-  // the factorisation and inverse, one warp per panel
-  if (h->n_sub > 65535) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up: too many subdomains");
-  DevBuf dG;
-  dG.alloc((size_t)h->n_sub * tri_pairs(K) * sizeof(double), st);
+  const size_t csm = (size_t)KK * sizeof(double);
+  ensure_dyn_smem((const void*)k_block_chol, csm);
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
-  k_gram_reduce<<<dim3((unsigned)ceil_div(KT, 256), (unsigned)h->n_sub), 256, 0, st>>>(
-      h->d_gpart.as<double>(), dcoff.as<int>(), K, dG.as<double>());
-  count_launch(h);
-  const size_t csm = chol_smem_bytes(K);
-  ensure_dyn_smem((const void*)k_block_chol<false>, csm);
-  ensure_dyn_smem((const void*)k_block_chol<true>, csm);
   // FP32 and DF32 panels apply X_j in float-float arithmetic: keep a pair copy
   const bool pairs_x = !std::is_same<T, double>::value;
   if (pairs_x) h->d_R2.alloc(h->n_sub * tri_pairs(K) * sizeof(float2), st);
-  if (pairs_x)
-    k_block_chol<true><<<h->n_sub, 32, csm, st>>>(
-        dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
-        h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), h->d_R2.as<float2>());
-  else
-    k_block_chol<false><<<h->n_sub, 32, csm, st>>>(
-        dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
-        h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr);
+  k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(
+      h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
+      h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr,
+      pairs_x ? h->d_R2.as<float2>() : nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
