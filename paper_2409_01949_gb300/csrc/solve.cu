@@ -2105,15 +2105,6 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
       pbase += m;
     }
   }
-  // launch order: largest units (rows x covering panels) first, so that the
-  // last wave of the one-CTA-per-SM pass is made of the small ones; each unit
-  // keeps its partial slots (un.w), so only the order of the per-unit norm
-  // partials changes (a fixed order still)
-  std::stable_sort(units.begin(), units.end(), [&](const int4& x, const int4& y) {
-    const int64_t wx = (int64_t)(x.z - x.y) * (h->cover_off[x.x + 1] - h->cover_off[x.x]);
-    const int64_t wy = (int64_t)(y.z - y.y) * (h->cover_off[y.x + 1] - h->cover_off[y.x]);
-    return wx > wy;
-  });
   fp.n_units = (int)units.size();
   std::vector<int> fo(h->n_sub + 1, 0), fe;
   fe.reserve(pbase);
