@@ -237,7 +237,9 @@ struct FusedPlan {
   bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
 };
 bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp);
-// mode 0: u' = M t - (alpha/beta) u (scal[0], scal[1]); mode 1: u' = h - M t.
+// mode 0: u' = M t - (alpha/beta) u (staged alpha, beta); mode 1: u' = h - M t;
+// mode 2: u' = (M t) s - (alpha/beta) u with s the staged 1/alpha (t = P v',
+// v' = alpha v not yet normalised).
 // Writes u', per-panel partials of M^T u' into fp.part (FP64 values for FP64
 // panels; compensated FP32 (hi, lo) pairs in the same 8 bytes for FP32
 // panels) and ||u'||^2 per unit.  tf: FP32 copy of t (FP32 panels) or FP32

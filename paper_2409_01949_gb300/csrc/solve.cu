@@ -39,7 +39,8 @@ constexpr int kStage = 16;
 enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
   S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO,
-  S_BSQ   // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
+  S_BSQ,    // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
+  S_TSCALE  // 1/alpha: the fused pass's factor on M t' (mode 2, t' = P v' unnormalised)
 };
 
 template <class T>
@@ -845,7 +846,8 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
 // range of one cell); warp w owns the w-th covering panel of the cell.  For
 // each 8-row chunk the warps load their panel rows into registers and form
 // d_w(r) = P_w[r] . t_w; the row values u'(r) = sum_w d_w(r) - coef u(r)
-// (mode 0) or h(r) - sum_w d_w(r) (mode 1) are formed in FP64 in a fixed
+// (mode 0; mode 2: sum_w d_w(r) / alpha - coef u(r), t = P v' not yet
+// normalised) or h(r) - sum_w d_w(r) (mode 1) are formed in FP64 in a fixed
 // order; then every warp adds P_w[r] u'(r) into its running partial of
 // M^T u' (Kahan-compensated in FP32 panels).  The unit's partials and its
 // ||u'||^2 are written once: M t and M^T u' read each panel entry once.
@@ -880,10 +882,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     const int k = lane + 32 * j;
     tv[j] = (active && k < K) ? tvec[(int64_t)s * K + k] : T(0);
   }
-  double coef = 0.0;   // used by warp 0 only (an FP64 division is costly)
-  if (mode == 0 && threadIdx.x < 32) {
-    const double beta = scal[kStage + S_BETA];   // staged by k_update_precond
+  double coef = 0.0, ts = 1.0;   // used by warp 0 only (an FP64 division is costly)
+  if (mode != 1 && threadIdx.x < 32) {
+    const double beta = scal[kStage + S_BETA];   // staged by the previous LSQR update
     coef = beta > 0.0 ? scal[kStage + S_ALPHA] / beta : 0.0;
+    if (mode == 2) ts = scal[kStage + S_TSCALE];
   }
   T ahi[FPL], alo[FPL];
 #pragma unroll
@@ -905,7 +908,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     const int p = r0 + (int)threadIdx.x;
     uo = 0.0;
     if (threadIdx.x < (unsigned)nr && p < cnt)
-      uo = mode == 0 ? u[R0 + p] : hvec[R0 + p];
+      uo = mode != 1 ? u[R0 + p] : hvec[R0 + p];
   };
   if (un.y < un.z) load_chunk(un.y, pv, uold);
   for (int r0 = un.y; r0 < un.z; r0 += kFusedRows) {
@@ -927,7 +930,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
       for (int q = 0; q < m; ++q) y += sd[q][r];
       double out = 0.0;
       if (p < cnt) {
-        out = mode == 0 ? y - coef * uold : uold - y;
+        out = mode != 1 ? y * ts - coef * uold : uold - y;
         u[R0 + p] = out;
         nrm += out * out;
       }
@@ -1120,12 +1123,13 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     if (lane == 0) {
       const uint32_t ub = (uint32_t)(nrows * sizeof(double));
       sm100::mbar_arrive_expect_tx(&ubar, ub);
-      sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
+      sm100::bulk_load(us, (mode != 1 ? u : hvec) + R0 + un.y, ub, &ubar);
     }
-    double coef = 0.0;
-    if (mode == 0) {
-      const double beta = scal[kStage + S_BETA];   // staged by k_update_precond
+    double coef = 0.0, ts = 1.0;
+    if (mode != 1) {
+      const double beta = scal[kStage + S_BETA];   // staged by the previous LSQR update
       coef = beta > 0.0 ? scal[kStage + S_ALPHA] / beta : 0.0;
+      if (mode == 2) ts = scal[kStage + S_TSCALE];
     }
     if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
     double nrm = 0.0;
@@ -1142,7 +1146,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
         double out = 0.0;
         if (un.y + pr < cnt) {
           const double uo = us[pr];
-          out = mode == 0 ? (double)part - coef * uo : uo - (double)part;
+          out = mode != 1 ? (double)part * ts - coef * uo : uo - (double)part;
           u[R0 + un.y + pr] = out;
           nrm += out * out;
         }
@@ -1328,12 +1332,13 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     if (lane == 0) {
       const uint32_t ub = (uint32_t)(nrows * sizeof(double));
       sm100::mbar_arrive_expect_tx(&ubar, ub);
-      sm100::bulk_load(us, (mode == 0 ? u : hvec) + R0 + un.y, ub, &ubar);
+      sm100::bulk_load(us, (mode != 1 ? u : hvec) + R0 + un.y, ub, &ubar);
     }
-    double coef = 0.0;
-    if (mode == 0) {
-      const double beta = scal[kStage + S_BETA];   // staged by k_update_precond
+    double coef = 0.0, ts = 1.0;
+    if (mode != 1) {
+      const double beta = scal[kStage + S_BETA];   // staged by the previous LSQR update
       coef = beta > 0.0 ? scal[kStage + S_ALPHA] / beta : 0.0;
+      if (mode == 2) ts = scal[kStage + S_TSCALE];
     }
     if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
     double nrm = 0.0;
@@ -1352,7 +1357,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
         if (un.y + pr < cnt) {
           const double y = (double)part.x + (double)part.y;
           const double uo = us[pr];
-          out = mode == 0 ? y - coef * uo : uo - y;
+          out = mode != 1 ? y * ts - coef * uo : uo - y;
           u[R0 + un.y + pr] = out;
           nrm += out * out;
         }
@@ -1663,8 +1668,8 @@ __device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags)
 // beta v_j (written to v), in float-float arithmetic except beta, v' and its
 // norm.  y_k = sum_{m<=k} X_km z_m: each warp takes rows k = w, w + nw, ...
 // four at a time, its lanes the terms m = l, l + 32, ..., one warp_sum4_df per
-// four rows (a fixed order).  Returns ||v'||^2 of the panel in every thread;
-// block 0 stages beta.
+// four rows (a fixed order).  Returns ||v'||^2 of the panel in every thread
+// and leaves v' as pairs in zs; block 0 stages beta.
 __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restrict__ pco,
                              int K, double* __restrict__ v, double* __restrict__ scal, int init,
                              const float2* Xs, float2* zs, float2* part, uint64_t* bar,
@@ -1727,6 +1732,7 @@ __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restr
     const double vold = init ? 0.0 : v[(int64_t)s * K + i];
     const double vn = acc - beta * vold;
     v[(int64_t)s * K + i] = vn;
+    zs[i] = df_split(vn);   // z is consumed: v' as pairs for X^T v'
     nrm += vn * vn;
   }
   if (s == 0 && threadIdx.x == 0) scal[kStage + S_BETA] = beta;
@@ -1782,21 +1788,6 @@ struct TriSmem {
     bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
   }
 };
-
-// k_panel_T2 for FP32-pair partials with X_j as the packed pair triangle
-// (tail_v_tri; the triangle's bulk copy is issued first, so it streams in
-// while the slice sums run).
-__global__ void __launch_bounds__(kTriThreads, 3) k_panel_T2_tri(
-    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
-    int K, double* __restrict__ v, double* __restrict__ scal, int init,
-    double* __restrict__ norm_partial, int* __restrict__ flags) {
-  extern __shared__ __align__(16) unsigned char trsm[];
-  TriSmem sm(trsm, K);
-  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
-  const double nrm = tail_v_tri(csum, pco, K, v, scal, init, sm.Xs, sm.vec, sm.part, sm.bar,
-                                flags);
-  if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
-}
 
 // v'_j = X_j z_j / beta - beta v_j with z_j = sum of the entry partials of panel j
 // (X_j = R_j^{-T}); writes v' (unnormalised) and ||v'||^2 per block.
@@ -1909,6 +1900,56 @@ __global__ void k_update(double* __restrict__ scal, const double* __restrict__ a
   }
 }
 
+// One step of the LSQR recurrence (Paige & Saunders 1982, the plane rotation
+// from rhobar, beta and alpha) from alpha^2, beta_{i+1} and the committed
+// scalars; with `stage`, all scalars go to the staged slots (S_TSCALE = 1/alpha
+// included).  Returns 1/alpha, phi/rho and theta/rho (0 and 0 at the start).
+struct LsqrStep {
+  double ia, phi_rho, theta_rho;
+};
+__device__ LsqrStep lsqr_recurrence(double* __restrict__ scal, double a2, double beta, int init,
+                                    bool stage) {
+  const double alpha = sqrt(a2);
+  LsqrStep r{alpha > 0.0 ? 1.0 / alpha : 0.0, 0.0, 0.0};
+  double rhobar_new, phibar_new, anorm2, arnorm;
+  if (init) {
+    rhobar_new = alpha;
+    phibar_new = beta;
+    anorm2 = alpha * alpha;
+    arnorm = alpha * beta;
+  } else {
+    const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
+    const double rho = sqrt(rhobar * rhobar + beta * beta);
+    const double c = rho > 0.0 ? rhobar / rho : 1.0;
+    const double sn = rho > 0.0 ? beta / rho : 0.0;
+    const double theta = sn * alpha;
+    rhobar_new = -c * alpha;
+    const double phi = c * phibar;
+    phibar_new = sn * phibar;
+    r.phi_rho = rho > 0.0 ? phi / rho : 0.0;
+    r.theta_rho = rho > 0.0 ? theta / rho : 0.0;
+    anorm2 = scal[S_ANORM2] + alpha * alpha + beta * beta;
+    arnorm = phibar_new * alpha * fabs(c);
+  }
+  if (stage) {
+    double* sg = scal + kStage;
+    sg[S_ALPHA] = alpha;
+    sg[S_BETA] = beta;
+    sg[S_RHOBAR] = rhobar_new;
+    sg[S_PHIBAR] = phibar_new;
+    sg[S_ANORM2] = anorm2;
+    sg[S_RNORM] = phibar_new;
+    sg[S_ARNORM] = arnorm;
+    sg[S_BNORM] = init ? beta : scal[S_BNORM];
+    sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
+    sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
+    sg[S_PHI_RHO] = r.phi_rho;
+    sg[S_THETA_RHO] = r.theta_rho;
+    sg[S_TSCALE] = r.ia;
+  }
+  return r;
+}
+
 // One LSQR step on panel s's K entries (Paige & Saunders 1982: the plane
 // rotation from rhobar, beta and alpha, then the v, w, x updates): alpha =
 // ||v'|| (every block sums the norm partials in the same fixed order, with all
@@ -1932,51 +1973,16 @@ __device__ __forceinline__ void lsqr_step_panel(double* __restrict__ scal,
   for (int i = threadIdx.x; i < n_alpha_partial; i += blockDim.x) a2 += alpha_partial[i];
   a2 = block_sum(a2, red);
   const double beta = scal[kStage + S_BETA];   // beta_{i+1}
-  double alpha = 0.0, ia = 0.0, phi_rho = 0.0, theta_rho = 0.0;
-  double rhobar_new = 0.0, phibar_new = 0.0, anorm2 = scal[S_ANORM2], arnorm = 0.0;
   if (threadIdx.x == 0) {   // one thread: the recurrence needs FP64 sqrt / divisions
-    alpha = sqrt(a2);
-    ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-    if (init) {
-      rhobar_new = alpha;
-      phibar_new = beta;
-      anorm2 = alpha * alpha;
-      arnorm = alpha * beta;
-    } else {
-      const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
-      const double rho = sqrt(rhobar * rhobar + beta * beta);
-      const double c = rho > 0.0 ? rhobar / rho : 1.0;
-      const double sn = rho > 0.0 ? beta / rho : 0.0;
-      const double theta = sn * alpha;
-      rhobar_new = -c * alpha;
-      const double phi = c * phibar;
-      phibar_new = sn * phibar;
-      phi_rho = rho > 0.0 ? phi / rho : 0.0;
-      theta_rho = rho > 0.0 ? theta / rho : 0.0;
-      anorm2 += alpha * alpha + beta * beta;
-      arnorm = phibar_new * alpha * fabs(c);
-    }
-    shv[0] = ia;
-    shv[1] = phi_rho;
-    shv[2] = theta_rho;
-    if (s == 0) {
-      double* sg = scal + kStage;
-      sg[S_ALPHA] = alpha;
-      sg[S_BETA] = beta;
-      sg[S_RHOBAR] = rhobar_new;
-      sg[S_PHIBAR] = phibar_new;
-      sg[S_ANORM2] = anorm2;
-      sg[S_RNORM] = phibar_new;
-      sg[S_ARNORM] = arnorm;
-      sg[S_BNORM] = init ? beta : scal[S_BNORM];
-      sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
-      sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
-    }
+    const LsqrStep st = lsqr_recurrence(scal, a2, beta, init, s == 0);
+    shv[0] = st.ia;
+    shv[1] = st.phi_rho;
+    shv[2] = st.theta_rho;
   }
   __syncthreads();
-  ia = shv[0];
-  phi_rho = shv[1];
-  theta_rho = shv[2];
+  const double ia = shv[0];
+  const double phi_rho = shv[1];
+  const double theta_rho = shv[2];
   const int64_t o = (int64_t)s * K;
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
     const double vn = v[o + i] * ia;   // v_{i+1}
@@ -2038,22 +2044,70 @@ __global__ void __launch_bounds__(1024) k_update_precond(
   }
 }
 
-// k_update_precond for FP32 and DF32 panels: X_s as the packed pair triangle,
-// fetched by one bulk copy issued before the LSQR step so that it streams in
-// meanwhile; t_s = X_s^T v_s by tail_t_tri.
-__global__ void __launch_bounds__(kTriThreads, 3) k_update_precond_tri(
-    double* __restrict__ scal, const double* __restrict__ alpha_partial, int n_alpha_partial,
-    double* __restrict__ v, double* __restrict__ w, double* __restrict__ x, int K, int init,
-    const float2* __restrict__ Xt, double* __restrict__ t, void* __restrict__ tlow,
-    int low_kind, int* __restrict__ flags) {
+// The LSQR iteration's tail for FP32 and DF32 panels in one kernel, one block
+// per panel, with the update of the previous iteration deferred into it:
+//  1. x += (phi/rho) w, w = v - (theta/rho) w with v = v' / alpha (v' as the
+//     previous call left it; 1/alpha and the ratios from the committed
+//     scalars); not at the start of a solve, where w and x are zero and the
+//     ratios are staged as 0 (so the next call sets w = v_1);
+//  2. v'' = X z / beta - beta v, stored unnormalised, its norm partial
+//     (tail_v_tri; the triangle's bulk copy is issued first);
+//  3. t' = X^T v'' (tail_t_tri) for the next fused pass, which multiplies
+//     M t' by the staged 1/alpha (mode 2);
+//  4. the last block to finish (a counter, reset by that block) adds all
+//     norm partials with the whole block in a fixed order, runs the
+//     recurrence and stages every scalar.
+// The solve's end applies the last deferred x update (k_lsqr_finish).
+__global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
+    const double* __restrict__ csum, const int* __restrict__ pco, const float2* __restrict__ Xt,
+    int K, double* __restrict__ v, double* __restrict__ w, double* __restrict__ x,
+    double* __restrict__ scal, int init, double* __restrict__ norm_partial,
+    double* __restrict__ t, void* __restrict__ tlow, int low_kind,
+    unsigned int* __restrict__ counter, int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char trsm[];
+  __shared__ double red[33];
+  __shared__ int last;
   TriSmem sm(trsm, K);
   tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
-  float2* vs = sm.vec;
-  lsqr_step_panel(scal, alpha_partial, n_alpha_partial, v, w, x, K, init,
-                  [&](int i, double vn) { vs[i] = df_split(vn); });
-  tri_wait(sm.bar, flags);
-  tail_t_tri(K, sm.Xs, vs, sm.part, t, tlow, low_kind);
+  const int64_t o = (int64_t)blockIdx.x * K;
+  if (!init) {
+    const double ia = scal[S_TSCALE], pr = scal[S_PHI_RHO], tr = scal[S_THETA_RHO];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const double vn = v[o + i] * ia;
+      const double wi = w[o + i];
+      x[o + i] += pr * wi;
+      w[o + i] = vn - tr * wi;
+      v[o + i] = vn;
+    }
+  }
+  const double nrm = tail_v_tri(csum, pco, K, v, scal, init, sm.Xs, sm.vec, sm.part, sm.bar,
+                                flags);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
+  __syncthreads();
+  tail_t_tri(K, sm.Xs, sm.vec, sm.part, t, tlow, low_kind);
+  // the last block: alpha, the recurrence, the staged scalars
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a2 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) a2 += __ldcg(norm_partial + i);
+  a2 = block_sum(a2, red);
+  if (threadIdx.x == 0) {
+    lsqr_recurrence(scal, a2, sqrt(scal[kStage + S_BSQ]), init, true);
+    *counter = 0u;
+  }
+}
+
+// The last deferred update of k_lsqr_tail_tri: x += (phi/rho) w, ratio staged.
+__global__ void k_lsqr_finish(const double* __restrict__ scal, const double* __restrict__ w,
+                              double* __restrict__ x, int64_t N) {
+  const double pr = scal[kStage + S_PHI_RHO];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += pr * w[i];
 }
 
 __global__ void k_add_to(double* __restrict__ a, const double* __restrict__ d, int64_t N) {
@@ -2500,38 +2554,52 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const double tri_bytes = 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
+  // FP32 / DF32 panels: the whole tail in k_lsqr_tail_tri (the update deferred
+  // into the next call, t unnormalised, the fused pass in mode 2); w and x start
+  // at zero, the tail's block counter too
+  DevBuf dcount;
+  if (xpairs) {
+    ensure_dyn_smem((const void*)k_lsqr_tail_tri, tsmem);
+    dcount.alloc(sizeof(unsigned int), st);
+    CUDA_CHECK(cudaMemsetAsync(dcount.p, 0, sizeof(unsigned int), st));
+    CUDA_CHECK(cudaMemsetAsync(h->d_w.p, 0, N * sizeof(double), st));
+    CUDA_CHECK(cudaMemsetAsync(h->d_x_sol.p, 0, N * sizeof(double), st));
+  }
+  const int fmode = xpairs ? 2 : 0;              // the loop's fused-pass mode
+  const int tail_launches = xpairs ? 1 : 2;      // besides the slice sums (counted by themselves)
   auto fused_tail = [&](int init) {
+    if (xpairs) {
+      // panel_MTu: the slice sums; lsqr_update: the rest (slice sums, X's
+      // triangle, v, w, x, t read or written once)
+      const double csum_bytes = 8.0 * fp.n_pchunks * K;
+      prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + csum_bytes);
+      panel_chunk_sums(h, fp, gpart, n_units, scal);
+      prof_end(h, KID_PANEL_T);
+      prof_begin(h, KID_UPDATE, csum_bytes + tri_bytes + 72.0 * N);
+      k_lsqr_tail_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
+          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(),
+          h->d_w.as<double>(), h->d_x_sol.as<double>(), scal, init, vpart,
+          h->d_tmp.as<double>(), fp.tf.p, low_kind, dcount.as<unsigned int>(),
+          h->d_flags.as<int>());
+      prof_end(h, KID_UPDATE);
+      return;
+    }
     // algorithmic bytes: the partials, X's triangle (8 bytes a value), v read and written
     prof_begin(h, KID_PANEL_T, (double)dfpart.bytes + (identity ? 0.0 : tri_bytes) + 16.0 * N);
     panel_chunk_sums(h, fp, gpart, n_units, scal);
-    if (xpairs)
-      k_panel_T2_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(), scal, init, vpart,
-          h->d_flags.as<int>());
-    else
-      k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
-          fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, h->d_v.as<double>(), scal,
-          identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
+    k_panel_T2<<<h->n_sub, tgroups * KpT, p2smem, st>>>(
+        fp.csum.as<double>(), fp.pco.as<int>(), Xc, K, h->d_v.as<double>(), scal,
+        identity ? 1 : 0, init, vpart, fp.pairs ? 1 : 0);
     prof_end(h, KID_PANEL_T);
     prof_begin(h, KID_UPDATE, 48.0 * N + (identity ? 0.0 : tri_bytes));
-    if (xpairs)
-      k_update_precond_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
-          scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
-          h->d_x_sol.as<double>(), K, init, Xt, h->d_tmp.as<double>(), fp.tf.p, low_kind,
-          h->d_flags.as<int>());
-    else
-      k_update_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
-          scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
-          h->d_x_sol.as<double>(), K, init, identity ? 1 : 0, Xr, h->d_tmp.as<double>(), fp.tf.p,
-          low_kind);
+    k_update_precond<<<h->n_sub, pc_threads, pc_smem, st>>>(
+        scal, vpart, h->n_sub, h->d_v.as<double>(), h->d_w.as<double>(),
+        h->d_x_sol.as<double>(), K, init, identity ? 1 : 0, Xr, h->d_tmp.as<double>(), fp.tf.p,
+        low_kind);
     prof_end(h, KID_UPDATE);
   };
   if (fused && p2smem > 48 * 1024)
     ensure_dyn_smem((const void*)k_panel_T2, p2smem);
-  if (xpairs) {
-    ensure_dyn_smem((const void*)k_panel_T2_tri, tsmem);
-    ensure_dyn_smem((const void*)k_update_precond_tri, tsmem);
-  }
 
   stage_begin(h, 5);
   // start: b = h (cold) or h - M a0 (warm start)
@@ -2543,7 +2611,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       fused_step(h->d_tmp.as<double>(), 1);
     }
     fused_tail(1);
-    count_launch(h, 2);   // k_panel_T2, k_update (the others count themselves)
+    count_launch(h, tail_launches);
   } else {
     if (o->warm_start) {
       gather(h->d_a.as<double>(), 1);
@@ -2566,7 +2634,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     for (int b = 0; b < batch; ++b) {
       if (fused) {
         // t (and its low-precision copy) come from the previous k_update_precond
-        fused_step(h->d_tmp.as<double>(), 0, low_kind ? fp.tf.p : nullptr);
+        fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);
         fused_tail(0);
       } else {
         prof_begin(h, KID_PRECOND, (identity ? 0.0 : 8.0 * h->n_sub * KK) + 16.0 * N);
@@ -2577,9 +2645,9 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
         transpose_step(0);
       }
     }
-    // fused: k_panel_T2 + k_update_precond (the fused pass and the slice sums
-    // count themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
-    count_launch(h, (fused ? 2 : 5) * batch);
+    // fused: the tail kernels (the fused pass and the slice sums count
+    // themselves); else k_precond, k_gather, k_entry_T, k_panel_T, k_update
+    count_launch(h, (fused ? tail_launches : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
     CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
@@ -2600,7 +2668,12 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       break;
     }
   }
-  // a = (a0 +) P y
+  // a = (a0 +) P y, after the last deferred update of y (x here)
+  if (xpairs) {
+    k_lsqr_finish<<<upd_blocks, 256, 0, st>>>(scal, h->d_w.as<double>(), h->d_x_sol.as<double>(),
+                                               N);
+    count_launch(h);
+  }
   if (xpairs)
     k_precond_df<<<h->n_sub, pc_threads, pc_smem, st>>>(Xt, h->d_x_sol.as<double>(), K,
                                                          h->d_tmp.as<double>(), identity, scal,
