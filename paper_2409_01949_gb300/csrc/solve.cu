@@ -564,7 +564,6 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   __shared__ double red[33];
   __shared__ double diag0[128];
   __shared__ double rpiv[128];    // 1 / L_kk
-  __shared__ double xrow[128];
   __shared__ double colk[128];       // scaled column k of L
   __shared__ double xpart[4][128];   // slice sums of a row of the inverse
   __shared__ int fail;
@@ -627,19 +626,24 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
     const double add = eps * tr / K + abs_shift + (tr == 0.0 && abs_shift == 0.0 ? 1.0 : 0.0);
+    // pivot k: L_kk = sqrt(G_kk), 1 / L_kk (one thread: FP64 sqrt / division are costly)
+    auto pivot = [&](int k) {
+      const double d = G[k * K + k];
+      if (!(d > 0.0)) fail = 1;
+      const double l = sqrt(d > 0.0 ? d : 1.0);
+      G[k * K + k] = l;
+      rpiv[k] = 1.0 / l;
+    };
     if (tid == 0) fail = 0;
-    __syncthreads();
     for (int i = tid; i < K; i += nt) G[i * K + i] += add;
     __syncthreads();
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    // two barriers a step: the scaled column, then the trailing update.  The
+    // lane that updates G_{k+1,k+1} (warp 0's first row, lane 0) takes pivot
+    // k + 1 right away, so that its FP64 latency overlaps the other warps'
+    // updates instead of a phase of its own.
     for (int k = 0; k < K; ++k) {
-      if (tid == 0) {
-        const double d = G[k * K + k];
-        if (!(d > 0.0)) fail = 1;
-        const double l = sqrt(d > 0.0 ? d : 1.0);
-        G[k * K + k] = l;
-        rpiv[k] = 1.0 / l;
-      }
-      __syncthreads();
       if (fail) break;
       const double rp = rpiv[k];
       for (int i = k + 1 + tid; i < K; i += nt) {
@@ -651,6 +655,7 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
       for (int i = k + 1 + wr; i < K; i += nwr) {
         const double lik = colk[i];
         for (int j = k + 1 + lane; j <= i; j += 32) G[i * K + j] -= lik * colk[j];
+        if (i == k + 1 && lane == 0) pivot(k + 1);   // row k + 1 is final now
       }
       __syncthreads();
     }
@@ -662,7 +667,7 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
     return;
   }
   // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
-  // Row i of L is read while row i of X is formed in xrow, then overwritten.
+  // Row i of L is read while row i of X is formed, then overwritten.
   // Thread (p, j): column j, slice p of [0, i) (rows m < j of X hold no X_mj:
   // the strict upper triangle of G is untouched, hence the m >= j test).
   const int j = tid & 127, p = tid >> 7;   // 4 slices at 512 threads
@@ -674,11 +679,11 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
       for (int m = m0; m < m1; ++m)
         if (m >= j) acc += G[i * K + m] * G[m * K + j];
     xpart[p][j] = acc;
-    __syncthreads();
-    if (tid < i) xrow[tid] = -(((xpart[0][tid] + xpart[1][tid]) + xpart[2][tid]) + xpart[3][tid]) *
-                             rpiv[i];
-    __syncthreads();
-    for (int q = tid; q <= i; q += nt) G[i * K + q] = q == i ? rpiv[i] : xrow[q];
+    __syncthreads();   // row i of L has been read: its place takes row i of X
+    if (tid < i)
+      G[i * K + tid] = -(((xpart[0][tid] + xpart[1][tid]) + xpart[2][tid]) + xpart[3][tid]) * rpiv[i];
+    else if (tid == i)
+      G[i * K + i] = rpiv[i];
     __syncthreads();
   }
   double* xr = Xr + (int64_t)s * K * K;
