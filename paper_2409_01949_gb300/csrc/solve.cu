@@ -539,122 +539,132 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
     }
 }
 
+// Sum of each panel's diagonal-Gram chunk partials (upper-triangle order,
+// FP64) into its packed lower triangle G_s (row i from i (i + 1) / 2 on;
+// tri_pairs(K) doubles per panel, so that each panel starts 16-byte aligned):
+// one thread per entry, the chunks added in order.  grid = (entry blocks, panels).
+__global__ void k_gram_reduce(const double* __restrict__ partial, const int* __restrict__ chunk_off,
+                              int K, double* __restrict__ Gp) {
+  const int s = blockIdx.y;
+  const int KT = K * (K + 1) / 2;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= KT) return;
+  const int c0 = chunk_off[s], c1 = chunk_off[s + 1];
+  double v = 0.0;
+#pragma unroll 8
+  for (int c = c0; c < c1; ++c) v += partial[(int64_t)c * KT + e];
+  int i = 0, r = e;   // e = i K - i (i - 1) / 2 + (j - i), i <= j
+  while (r >= K - i) {
+    r -= K - i;
+    ++i;
+  }
+  const int j = i + r;
+  Gp[(int64_t)s * tri_pairs(K) + j * (j + 1) / 2 + i] = v;
+}
+
 constexpr int kCholThreads = 512;   // 4 slices x 128 columns in the inverse
 static_assert(kCholThreads == 4 * 128, "k_block_chol's inverse maps 512 threads");
 
-// One block per subdomain: sum the chunk partials, shift, Cholesky
-// (lower L with L L^T = G + eps tr/K I), X = L^{-1}; store X row- and
-// column-major (and, given xtri, as the packed pair triangle).  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
+// Shared memory of k_block_chol: the packed triangle, then the copy's mbarrier
+// (about 66 KB at K = 128: three blocks per SM, so that a few hundred
+// subdomains are one wave).
+static size_t chol_smem_bytes(int K) { return (size_t)tri_pairs(K) * sizeof(double) + 16; }
+
+__device__ __forceinline__ int trirow(int i) { return i * (i + 1) / 2; }
+
+// One block per subdomain: G_s (packed lower triangle, from k_gram_reduce)
+// by one bulk copy; shift; Cholesky (lower L with L L^T = G + eps tr/K I);
+// X = L^{-1} in place; X stored row- and column-major (and, given xtri, as
+// the packed pair triangle).  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
 // Right-looking factorisation: column k, once scaled, is also copied to a
 // contiguous vector, and the trailing update runs one warp per row with the
-// lanes over columns, so that no shared-memory access strides by a row.  The
-// inverse is formed in place row by row (row i of X needs row i of L and rows
-// < i of X): lanes over columns j, four warp-uniform slices of the sum over m,
-// the slice sums added through shared memory in a fixed order.
+// lanes over columns; the lane that finishes G_{k+1,k+1} takes pivot k + 1
+// at once, so a step has two barriers.  The inverse is formed in place row by
+// row (row i of X needs row i of L and rows < i of X): lanes over columns j,
+// four warp-uniform slices of the sum over m, the slice sums added in a fixed
+// order.  A non-positive pivot starts again from a fresh copy of G_s with the
+// shift raised 100-fold (at most 8 times), then raises flags[1].
 // FP64 throughout: the blocks are as ill-conditioned as the shift allows.
-__global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __restrict__ partial,
-                                                     const int* __restrict__ chunk_off, int K,
-                                                     double shift, double abs_shift,
-                                                     double* __restrict__ Xr,
-                                                     double* __restrict__ Xc,
-                                                     int* __restrict__ flags,
-                                                     double* __restrict__ gdiag_out,
-                                                     float2* __restrict__ xtri) {
-  extern __shared__ double G[];   // [K][K]
+__global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __restrict__ Gp,
+                                                                 int K, double shift,
+                                                                 double abs_shift,
+                                                                 double* __restrict__ Xr,
+                                                                 double* __restrict__ Xc,
+                                                                 int* __restrict__ flags,
+                                                                 float2* __restrict__ xtri) {
+  extern __shared__ __align__(16) unsigned char chsm[];
   __shared__ double red[33];
-  __shared__ double diag0[128];
-  __shared__ double rpiv[128];    // 1 / L_kk
+  __shared__ double rpiv[128];       // 1 / L_kk
   __shared__ double colk[128];       // scaled column k of L
   __shared__ double xpart[4][128];   // slice sums of a row of the inverse
   __shared__ int fail;
+  const int64_t PT = tri_pairs(K);
+  double* P = reinterpret_cast<double*>(chsm);   // packed lower triangle
+  uint64_t* bar = reinterpret_cast<uint64_t*>(P + PT);
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int KT = K * (K + 1) / 2;
-  const int c0 = chunk_off[s], c1 = chunk_off[s + 1];
-  // assemble the symmetric G from the upper-triangle partials, chunk by chunk
-  // (each entry's sum runs over the chunks in order; a thread's entries of
-  // one chunk are loaded together)
-  constexpr int kPer = (128 * 129 / 2 + kCholThreads - 1) / kCholThreads;
-  double acc[kPer];
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) acc[r] = 0.0;
-  for (int c = c0; c < c1; ++c) {
-    const double* pc = partial + (int64_t)c * KT;
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-      const int pidx = tid + r * kCholThreads;
-      if (pidx < KT) acc[r] += pc[pidx];
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) {
-    int pidx = tid + r * kCholThreads;
-    if (pidx >= KT) continue;
-    int i = 0;   // row of the packed upper-triangle index
-    while (pidx >= K - i) {
-      pidx -= K - i;
-      ++i;
-    }
-    const int j = i + pidx;
-    G[i * K + j] = acc[r];
-    G[j * K + i] = acc[r];
+  const uint32_t bytes = (uint32_t)(PT * sizeof(double));
+  if (tid == 0) {
+    sm100::mbar_init(bar, 1);
+    sm100::fence_mbar_init();
   }
   __syncthreads();
-  if (gdiag_out) {
-    for (int idx = tid; idx < K * K; idx += nt) gdiag_out[(int64_t)s * K * K + idx] = G[idx];
-  }
+  uint32_t phase = 0;
+  auto fetch = [&]() {
+    sm100::fence_proxy_async_smem();   // earlier writes to P before the copy
+    __syncthreads();
+    if (tid == 0) {
+      sm100::mbar_arrive_expect_tx(bar, bytes);
+      sm100::bulk_load(P, Gp + (int64_t)s * PT, bytes, bar);
+    }
+    if (!sm100::mbar_wait(bar, phase)) {   // bounded; the host reports ELMFB_ERR_TIMEOUT
+      atomicOr(&flags[3], 1);
+      sm100::mbar_wait(bar, phase);
+    }
+    phase ^= 1;
+  };
+  fetch();
   double tr = 0.0;
   {
     double v = 0.0;
-    for (int i = tid; i < K; i += nt) {
-      v += G[i * K + i];
-      diag0[i] = G[i * K + i];
-    }
+    for (int i = tid; i < K; i += nt) v += P[trirow(i) + i];
     tr = block_sum(v, red);
   }
   // trailing update: warp wr takes rows k + 1 + wr, + nwr, ...; lanes the columns
   const int lane = tid & 31, wr = tid >> 5, nwr = nt >> 5;
+  // pivot k: L_kk = sqrt(G_kk), 1 / L_kk (one thread: FP64 sqrt / division are costly)
+  auto pivot = [&](int k) {
+    const double d = P[trirow(k) + k];
+    if (!(d > 0.0)) fail = 1;
+    const double l = sqrt(d > 0.0 ? d : 1.0);
+    P[trirow(k) + k] = l;
+    rpiv[k] = 1.0 / l;
+  };
   double eps = shift;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (attempt > 0) {
-      // restore the lower triangle from the (untouched) strict upper triangle
-      for (int idx = tid; idx < K * K; idx += nt) {
-        const int i = idx / K, j = idx - i * K;
-        if (i > j) G[i * K + j] = G[j * K + i];
-        else if (i == j) G[i * K + i] = diag0[i];
-      }
+      fetch();
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
     const double add = eps * tr / K + abs_shift + (tr == 0.0 && abs_shift == 0.0 ? 1.0 : 0.0);
-    // pivot k: L_kk = sqrt(G_kk), 1 / L_kk (one thread: FP64 sqrt / division are costly)
-    auto pivot = [&](int k) {
-      const double d = G[k * K + k];
-      if (!(d > 0.0)) fail = 1;
-      const double l = sqrt(d > 0.0 ? d : 1.0);
-      G[k * K + k] = l;
-      rpiv[k] = 1.0 / l;
-    };
     if (tid == 0) fail = 0;
-    for (int i = tid; i < K; i += nt) G[i * K + i] += add;
+    for (int i = tid; i < K; i += nt) P[trirow(i) + i] += add;
     __syncthreads();
     if (tid == 0) pivot(0);
     __syncthreads();
-    // two barriers a step: the scaled column, then the trailing update.  The
-    // lane that updates G_{k+1,k+1} (warp 0's first row, lane 0) takes pivot
-    // k + 1 right away, so that its FP64 latency overlaps the other warps'
-    // updates instead of a phase of its own.
     for (int k = 0; k < K; ++k) {
       if (fail) break;
       const double rp = rpiv[k];
       for (int i = k + 1 + tid; i < K; i += nt) {
-        const double l = G[i * K + k] * rp;
-        G[i * K + k] = l;
+        const double l = P[trirow(i) + k] * rp;
+        P[trirow(i) + k] = l;
         colk[i] = l;
       }
       __syncthreads();
       for (int i = k + 1 + wr; i < K; i += nwr) {
         const double lik = colk[i];
-        for (int j = k + 1 + lane; j <= i; j += 32) G[i * K + j] -= lik * colk[j];
+        double* row = P + trirow(i);
+        for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * colk[j];
         if (i == k + 1 && lane == 0) pivot(k + 1);   // row k + 1 is final now
       }
       __syncthreads();
@@ -668,33 +678,38 @@ __global__ void __launch_bounds__(kCholThreads) k_block_chol(const double* __res
   }
   // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
   // Row i of L is read while row i of X is formed, then overwritten.
-  // Thread (p, j): column j, slice p of [0, i) (rows m < j of X hold no X_mj:
-  // the strict upper triangle of G is untouched, hence the m >= j test).
-  const int j = tid & 127, p = tid >> 7;   // 4 slices at 512 threads
+  // Thread (p, j): column j, slice p of [0, i); rows m < j hold no X_mj.
+  const int j = tid & 127, p = tid >> 7;
   for (int i = 0; i < K; ++i) {
     const int step = (i + 3) >> 2;
     const int m0 = p * step, m1 = min(i, m0 + step);
+    const double* Li = P + trirow(i);
     double acc = 0.0;
     if (j < i)
       for (int m = m0; m < m1; ++m)
-        if (m >= j) acc += G[i * K + m] * G[m * K + j];
+        if (m >= j) acc += Li[m] * P[trirow(m) + j];
     xpart[p][j] = acc;
     __syncthreads();   // row i of L has been read: its place takes row i of X
     if (tid < i)
-      G[i * K + tid] = -(((xpart[0][tid] + xpart[1][tid]) + xpart[2][tid]) + xpart[3][tid]) * rpiv[i];
+      P[trirow(i) + tid] =
+          -(((xpart[0][tid] + xpart[1][tid]) + xpart[2][tid]) + xpart[3][tid]) * rpiv[i];
     else if (tid == i)
-      G[i * K + i] = rpiv[i];
+      P[trirow(i) + i] = rpiv[i];
     __syncthreads();
   }
   double* xr = Xr + (int64_t)s * K * K;
   double* xc = Xc + (int64_t)s * K * K;
-  for (int idx = tid; idx < K * K; idx += nt) {
-    const int i = idx / K, jj = idx - i * K;
-    const double v = jj <= i ? G[i * K + jj] : 0.0;
-    xr[idx] = v;                          // X_ij row-major
-    xc[(int64_t)jj * K + i] = v;          // X_ij column-major
-    if (xtri && jj <= i)                  // the triangle again, as packed FP32 pairs
-      xtri[(int64_t)s * tri_pairs(K) + i * (i + 1) / 2 + jj] = df_split(v);
+  for (int o = tid; o < K * K; o += nt) {
+    const int i = o / K, jj = o - i * K;
+    xr[o] = jj <= i ? P[trirow(i) + jj] : 0.0;   // X_ij row-major
+  }
+  for (int o = tid; o < K * K; o += nt) {
+    const int jj = o / K, i = o - jj * K;
+    xc[o] = jj <= i ? P[trirow(i) + jj] : 0.0;   // X_ij column-major
+  }
+  if (xtri) {   // the triangle again, as packed FP32 pairs
+    const int KT = K * (K + 1) / 2;
+    for (int q = tid; q < KT; q += nt) xtri[(int64_t)s * PT + q] = df_split(P[q]);
   }
 }
 
@@ -2421,16 +2436,25 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
     check_launch("k_gram_diag_partial");
     count_launch(h);
   }
-  const size_t csm = (size_t)KK * sizeof(double);
-  ensure_dyn_smem((const void*)k_block_chol, csm);
+  // the chunk partials summed into one packed triangle per panel, then the
+  // factorisation and inverse from a bulk copy of it
+  if (h->n_sub > 65535)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up: too many subdomains");
+  DevBuf dG;
+  dG.alloc((size_t)h->n_sub * tri_pairs(K) * sizeof(double), st);
   prof_begin(h, KID_BLOCK_CHOL,
              (double)chunks.size() * KT * sizeof(double) + 2.0 * h->n_sub * KK * sizeof(double));
+  k_gram_reduce<<<dim3((unsigned)ceil_div(KT, 256), (unsigned)h->n_sub), 256, 0, st>>>(
+      h->d_gpart.as<double>(), dcoff.as<int>(), K, dG.as<double>());
+  count_launch(h);
+  const size_t csm = chol_smem_bytes(K);
+  ensure_dyn_smem((const void*)k_block_chol, csm);
   // FP32 and DF32 panels apply X_j in float-float arithmetic: keep a pair copy
   const bool pairs_x = !std::is_same<T, double>::value;
   if (pairs_x) h->d_R2.alloc(h->n_sub * tri_pairs(K) * sizeof(float2), st);
   k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(
-      h->d_gpart.as<double>(), dcoff.as<int>(), K, shift, abs_shift, h->d_R.as<double>(),
-      h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr,
+      dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
+      h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(),
       pairs_x ? h->d_R2.as<float2>() : nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
