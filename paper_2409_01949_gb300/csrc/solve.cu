@@ -584,7 +584,13 @@ __device__ __forceinline__ int trirow(int i) { return i * (i + 1) / 2; }
 // four warp-uniform slices of the sum over m, the slice sums added in a fixed
 // order.  A non-positive pivot starts again from a fresh copy of G_s with the
 // shift raised 100-fold (at most 8 times), then raises flags[1].
-// FP64 throughout: the blocks are as ill-conditioned as the shift allows.
+// The factorisation is FP64 (the blocks are as ill-conditioned as the shift
+// allows); with three blocks per SM it keeps GB300's FP64 pipe (1/64 of the
+// FP32 FMA rate) about 80% busy.  kDfInv (FP32 and DF32 panels, whose solvers
+// apply X as FP32 pairs anyway): the inverse runs in float-float arithmetic
+// on the FP32 pipes instead, each finished row of X stored as pairs over the
+// row of L it replaces.
+template <bool kDfInv>
 __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __restrict__ Gp,
                                                                  int K, double shift,
                                                                  double abs_shift,
@@ -596,10 +602,12 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
   __shared__ double red[33];
   __shared__ double rpiv[128];       // 1 / L_kk
   __shared__ double colk[128];       // scaled column k of L
-  __shared__ double xpart[4][128];   // slice sums of a row of the inverse
+  __shared__ double xpart[4][128];   // slice sums of a row of the inverse (pairs with kDfInv)
+  __shared__ float2 lrow2[128];      // kDfInv: row i of L as pairs
   __shared__ int fail;
   const int64_t PT = tri_pairs(K);
   double* P = reinterpret_cast<double*>(chsm);   // packed lower triangle
+  float2* X2 = reinterpret_cast<float2*>(chsm);  // kDfInv: rows of X as pairs
   uint64_t* bar = reinterpret_cast<uint64_t*>(P + PT);
   const int s = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -684,6 +692,34 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
     const int step = (i + 3) >> 2;
     const int m0 = p * step, m1 = min(i, m0 + step);
     const double* Li = P + trirow(i);
+    if (kDfInv) {
+      for (int m = tid; m < i; m += nt) lrow2[m] = df_split(Li[m]);
+      __syncthreads();
+      float S = 0.f, C = 0.f;
+      if (j < i)
+        for (int m = m0; m < m1; ++m)
+          if (m >= j) {
+            const float2 x = X2[trirow(m) + j];
+            df_acc(S, C, lrow2[m].x, lrow2[m].y, x.x, x.y);
+          }
+      float2* xp = reinterpret_cast<float2*>(&xpart[0][0]);
+      xp[p * 128 + j] = make_float2(S, C);
+      __syncthreads();   // row i of L has been read: its place takes row i of X
+      if (tid <= i) {
+        const float2 rp = df_split(rpiv[i]);
+        float2 v = rp;
+        if (tid < i) {
+          const float2 a =
+              df_add(df_add(df_add(xp[tid], xp[128 + tid]), xp[256 + tid]), xp[384 + tid]);
+          float Sv = 0.f, Cv = 0.f;
+          df_acc(Sv, Cv, a.x, a.y, rp.x, rp.y);
+          v = make_float2(-Sv, -Cv);
+        }
+        X2[trirow(i) + tid] = v;
+      }
+      __syncthreads();
+      continue;
+    }
     double acc = 0.0;
     if (j < i)
       for (int m = m0; m < m1; ++m)
@@ -699,17 +735,22 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
   }
   double* xr = Xr + (int64_t)s * K * K;
   double* xc = Xc + (int64_t)s * K * K;
+  auto xval = [&](int i, int jj) -> double {
+    if (jj > i) return 0.0;
+    const int q = trirow(i) + jj;
+    return kDfInv ? (double)X2[q].x + (double)X2[q].y : P[q];
+  };
   for (int o = tid; o < K * K; o += nt) {
     const int i = o / K, jj = o - i * K;
-    xr[o] = jj <= i ? P[trirow(i) + jj] : 0.0;   // X_ij row-major
+    xr[o] = xval(i, jj);   // X_ij row-major
   }
   for (int o = tid; o < K * K; o += nt) {
     const int jj = o / K, i = o - jj * K;
-    xc[o] = jj <= i ? P[trirow(i) + jj] : 0.0;   // X_ij column-major
+    xc[o] = xval(i, jj);   // X_ij column-major
   }
   if (xtri) {   // the triangle again, as packed FP32 pairs
     const int KT = K * (K + 1) / 2;
-    for (int q = tid; q < KT; q += nt) xtri[(int64_t)s * PT + q] = df_split(P[q]);
+    for (int q = tid; q < KT; q += nt) xtri[(int64_t)s * PT + q] = kDfInv ? X2[q] : df_split(P[q]);
   }
 }
 
@@ -2448,14 +2489,19 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
       h->d_gpart.as<double>(), dcoff.as<int>(), K, dG.as<double>());
   count_launch(h);
   const size_t csm = chol_smem_bytes(K);
-  ensure_dyn_smem((const void*)k_block_chol, csm);
+  ensure_dyn_smem((const void*)k_block_chol<false>, csm);
+  ensure_dyn_smem((const void*)k_block_chol<true>, csm);
   // FP32 and DF32 panels apply X_j in float-float arithmetic: keep a pair copy
   const bool pairs_x = !std::is_same<T, double>::value;
   if (pairs_x) h->d_R2.alloc(h->n_sub * tri_pairs(K) * sizeof(float2), st);
-  k_block_chol<<<h->n_sub, kCholThreads, csm, st>>>(
-      dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
-      h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(),
-      pairs_x ? h->d_R2.as<float2>() : nullptr);
+  if (pairs_x)
+    k_block_chol<true><<<h->n_sub, kCholThreads, csm, st>>>(
+        dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
+        h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), h->d_R2.as<float2>());
+  else
+    k_block_chol<false><<<h->n_sub, kCholThreads, csm, st>>>(
+        dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
+        h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
