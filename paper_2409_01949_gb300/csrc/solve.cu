@@ -577,9 +577,10 @@ __device__ __forceinline__ int trirow(int i) { return i * (i + 1) / 2; }
 // X = L^{-1} in place; X stored row- and column-major (and, given xtri, as
 // the packed pair triangle).  R_j = L^T, so R_j^{-1} = X^T and R_j^{-T} = X.
 // Right-looking factorisation: column k, once scaled, is also copied to a
-// contiguous vector, and the trailing update runs one warp per row with the
-// lanes over columns; the lane that finishes G_{k+1,k+1} takes pivot k + 1
-// at once, so a step has two barriers.  The inverse is formed in place row by
+// contiguous vector; the trailing update is spread over all threads pair by
+// pair (no idle lanes on the short rows: the FP64 pipe is the limit), and the
+// thread that finishes G_{k+1,k+1} takes pivot k + 1 at once, so a step has
+// two barriers.  The inverse is formed in place row by
 // row (row i of X needs row i of L and rows < i of X): lanes over columns j,
 // four warp-uniform slices of the sum over m, the slice sums added in a fixed
 // order.  A non-positive pivot starts again from a fresh copy of G_s with the
@@ -638,8 +639,6 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
     for (int i = tid; i < K; i += nt) v += P[trirow(i) + i];
     tr = block_sum(v, red);
   }
-  // trailing update: warp wr takes rows k + 1 + wr, + nwr, ...; lanes the columns
-  const int lane = tid & 31, wr = tid >> 5, nwr = nt >> 5;
   // pivot k: L_kk = sqrt(G_kk), 1 / L_kk (one thread: FP64 sqrt / division are costly)
   auto pivot = [&](int k) {
     const double d = P[trirow(k) + k];
@@ -669,11 +668,18 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
         colk[i] = l;
       }
       __syncthreads();
-      for (int i = k + 1 + wr; i < K; i += nwr) {
-        const double lik = colk[i];
-        double* row = P + trirow(i);
-        for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * colk[j];
-        if (i == k + 1 && lane == 0) pivot(k + 1);   // row k + 1 is final now
+      // pairs q of the trailing triangle k < c <= i < K (q = a (a + 1) / 2 + b:
+      // row i = k + 1 + a, column c = k + 1 + b), every thread busy; the thread
+      // with q = 0 finishes G_{k+1,k+1} and takes pivot k + 1 at once
+      const int n = K - 1 - k;
+      const int T = n * (n + 1) / 2;
+      for (int q = tid; q < T; q += nt) {
+        int a = (int)((__fsqrt_rn(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+        if ((a + 1) * (a + 2) / 2 <= q) ++a;
+        else if (a * (a + 1) / 2 > q) --a;
+        const int i = k + 1 + a, c = k + 1 + (q - a * (a + 1) / 2);
+        P[trirow(i) + c] -= colk[i] * colk[c];
+        if (q == 0) pivot(k + 1);
       }
       __syncthreads();
     }
