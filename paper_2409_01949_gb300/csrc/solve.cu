@@ -351,8 +351,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
                                                          int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char smraw[];
   T* ring = reinterpret_cast<T*>(smraw);   // [kDiagStages][16][K]
-  __shared__ __align__(8) uint64_t full[kDiagStages];    // step copied in
-  __shared__ __align__(8) uint64_t empty[kDiagStages];   // every warp done with the stage
+  __shared__ __align__(8) uint64_t full[kDiagStages];
   const int4 ch = chunks[blockIdx.x];   // (panel, first step, steps, -)
   const int TT = K / 4;
   const int ntiles = TT * (TT + 1) / 2;
@@ -379,10 +378,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
                        (uint32_t)(K * sizeof(T)), &full[st]);
   };
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kDiagStages; ++q) {
-      sm100::mbar_init(&full[q], 1);
-      sm100::mbar_init(&empty[q], blockDim.x >> 5);
-    }
+    for (int q = 0; q < kDiagStages; ++q) sm100::mbar_init(&full[q], 1);
     sm100::fence_mbar_init();
   }
   __syncwarp();
@@ -429,17 +425,10 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
           }
         }
     }
-    // this warp is done with the stage; warp 0 refills the stage of step q - 1
-    // once every warp is (no block-wide barrier: the warps drift apart by up
-    // to the ring's depth)
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) sm100::mbar_arrive(&empty[st]);
-    if (threadIdx.x < 32 && q >= 1 && q - 1 + kDiagStages < nsteps) {
-      const int sp = (q - 1) % kDiagStages;
-      if (!sm100::mbar_wait(&empty[sp], ((q - 1) / kDiagStages) & 1, ok ? sm100::kSpinLimit : 4u))
-        ok = false;
+    __syncthreads();
+    if (threadIdx.x < 32 && q + kDiagStages < nsteps) {
       sm100::fence_proxy_async_smem();
-      issue(q - 1 + kDiagStages, sp);
+      issue(q + kDiagStages, st);
     }
   }
   if (!ok) atomicOr(&flags[3], 1);
@@ -471,8 +460,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
                                                             int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char smraw[];
   float2* ring = reinterpret_cast<float2*>(smraw);   // [kDiagStages][16][K]
-  __shared__ __align__(8) uint64_t full[kDiagStages];    // step copied in
-  __shared__ __align__(8) uint64_t empty[kDiagStages];   // every warp done with the stage
+  __shared__ __align__(8) uint64_t full[kDiagStages];
   const int4 ch = chunks[blockIdx.x];   // (panel, first step, steps, -)
   const int TT = K / 4;
   const int ntiles = TT * (TT + 1) / 2;
@@ -499,10 +487,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
                        (uint32_t)(K * sizeof(float2)), &full[st]);
   };
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kDiagStages; ++q) {
-      sm100::mbar_init(&full[q], 1);
-      sm100::mbar_init(&empty[q], blockDim.x >> 5);
-    }
+    for (int q = 0; q < kDiagStages; ++q) sm100::mbar_init(&full[q], 1);
     sm100::fence_mbar_init();
   }
   __syncwarp();
@@ -531,16 +516,10 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe_df(const float2* __restr
           for (int b = 0; b < 4; ++b) df_acc(S[a][b], C[a][b], x[a].x, x[a].y, y[b].x, y[b].y);
       }
     }
-    // as k_gram_diag_pipe: arrive on the stage's empty barrier; warp 0
-    // refills the stage of step q - 1 once every warp is done with it
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) sm100::mbar_arrive(&empty[st]);
-    if (threadIdx.x < 32 && q >= 1 && q - 1 + kDiagStages < nsteps) {
-      const int sp = (q - 1) % kDiagStages;
-      if (!sm100::mbar_wait(&empty[sp], ((q - 1) / kDiagStages) & 1, ok ? sm100::kSpinLimit : 4u))
-        ok = false;
+    __syncthreads();
+    if (threadIdx.x < 32 && q + kDiagStages < nsteps) {
       sm100::fence_proxy_async_smem();
-      issue(q - 1 + kDiagStages, sp);
+      issue(q + kDiagStages, st);
     }
     if (++st == kDiagStages) {
       st = 0;
