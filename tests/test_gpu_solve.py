@@ -245,3 +245,25 @@ def test_df32_solve_needs_features_multiple_of_four():
         with pytest.raises(E.ElmfbError) as ei:
             s.solve(max_iter=10)
         assert ei.value.code == E.ERR_UNSUPPORTED
+
+
+def test_profiling_stride_times_every_nth_launch():
+    """elmfb_set_profiling_stride: with profiling restricted to the fused pass
+    and stride 4, the handle times launches 0, 4, 8, ... of that kernel only
+    (the bench times its roofline kernel this way); stride 0 is rejected."""
+    P = WL.poisson2d(levels=(1, 2), features=32, n_side=30, n_boundary_side=30)
+    with E.Solver.from_problem(P, precision=E.FP32) as s:
+        s.assemble_problem(P)
+        s.set_profiling_only("fused_Mt_MTu")
+        with pytest.raises(E.ElmfbError) as ei:
+            s.set_profiling_stride(0)
+        assert ei.value.code == E.ERR_INVALID_ARG
+        s.set_profiling_stride(4)
+        info = s.solve(max_iter=13, atol=0.0, btol=0.0, check_every=13)
+        stats = s.kernel_stats()
+    # one fused pass for the start plus one per iteration
+    passes = 1 + info.iterations
+    ms, timed, _ = stats["fused_Mt_MTu"]
+    assert timed == (passes + 3) // 4
+    assert ms > 0.0
+    assert set(stats) == {"fused_Mt_MTu"}
