@@ -211,20 +211,36 @@ def run_ours(args):
         s.close()
         return err
 
-    # untimed calibration: smallest iteration budget whose solution meets the target
+    # untimed calibration: the smallest iteration budget whose solution meets
+    # the target -- a geometric search for a passing budget, then bisection
+    # between the last failing and the first passing one
     budget = args.max_iter
     calib = []
+
+    def error_at(b):
+        nonlocal opts
+        opts = E.default_solve_opts(max_iter=b, atol=0.0, btol=0.0, shift=args.shift,
+                                    check_every=args.check_every)
+        e = float(step(sets_dev, xs_dev, u_dev, uh_dev, None)["rel_l2"])
+        calib.append((b, e))
+        return e
+
+    opts = None
     if target is not None:
-        b = args.calib_start
+        lo, b = 0, args.calib_start
         while True:
-            opts = E.default_solve_opts(max_iter=b, atol=0.0, btol=0.0, shift=args.shift,
-                                        check_every=args.check_every)
-            e = step(sets_dev, xs_dev, u_dev, uh_dev, None)["rel_l2"]
-            calib.append((b, float(e)))
-            if e <= target or b >= args.max_iter:
+            if error_at(b) <= target or b >= args.max_iter:
                 budget = b
                 break
+            lo = b
             b = min(args.max_iter, int(b * 1.5) + 1)
+        if calib[-1][1] <= target:
+            while budget - lo > 1:
+                mid = (lo + budget) // 2
+                if error_at(mid) <= target:
+                    budget = mid
+                else:
+                    lo = mid
     opts = E.default_solve_opts(max_iter=budget, atol=0.0 if target is not None else args.tol,
                                 btol=0.0 if target is not None else args.tol, shift=args.shift,
                                 check_every=args.check_every)
