@@ -343,6 +343,7 @@ def run_ours(args):
                    f"{sz.panel_rows * P.features * (4 if prec == E.FP32 else 8) / 1e9:.2f} GB)"},
         "solution": {"rel_l2": float(err["rel_l2"]), "e_l1": float(err["e_l1"]),
                      "iterations": info.iterations,
+                     "precond_retries": info.precond_retries,
                      "target": target, "target_kind": args.target,
                      "matched": bool(err["rel_l2"] <= target) if target is not None else None,
                      "calibration": calib,

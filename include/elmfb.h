@@ -228,6 +228,9 @@ typedef struct {
   double normal_residual_norm;/* ||M^T (M a - h)|| (estimate, preconditioned) */
   double setup_ms;            /* preconditioner set-up time                    */
   double solve_ms;            /* iteration time                                */
+  int precond_retries;        /* block-Jacobi: factorisations that met a
+                                 non-positive pivot and were redone with the
+                                 shift raised 100-fold (once per retry)        */
 } elmfb_solve_info;
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,

@@ -82,7 +82,7 @@ class BatchResult(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_norm", C.c_double),
                 ("normal_residual_norm", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double)]
+                ("solve_ms", C.c_double), ("precond_retries", C.c_int)]
 
 
 _lib = None

@@ -194,6 +194,7 @@ struct elmfb_ctx {
   int64_t prof_n[KID_COUNT] = {0};
   double prof_bytes[KID_COUNT] = {0};   // algorithmic bytes per launch (last launch)
   int prof_stride = 1;                  // time every prof_stride-th launch of a kernel
+  int bj_retries = 0;                   // block-Jacobi factorisations redone with a larger shift
   int64_t prof_seen[KID_COUNT] = {0};   // launches seen while profiling
   bool prof_now[KID_COUNT] = {false};   // the current launch carries events
 

@@ -498,6 +498,7 @@ void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   else block_jacobi_setup<float>(h, o->shift, false);
   stage_end(h, 4);
   info->setup_ms = h->stage_ms[4];
+  info->precond_retries = h->bj_retries;
   if (use_gnn) gnn_alloc(h);
   Fcg f{h};
   f.init();

@@ -584,7 +584,8 @@ __device__ __forceinline__ int trirow(int i) { return i * (i + 1) / 2; }
 // row (row i of X needs row i of L and rows < i of X): lanes over columns j,
 // four warp-uniform slices of the sum over m, the slice sums added in a fixed
 // order.  A non-positive pivot starts again from a fresh copy of G_s with the
-// shift raised 100-fold (at most 8 times), then raises flags[1].
+// shift raised 100-fold (at most 8 times; each retry counted in flags[4]),
+// then raises flags[1].
 // The factorisation is FP64 (the blocks are as ill-conditioned as the shift
 // allows); with three blocks per SM it keeps GB300's FP64 pipe (1/64 of the
 // FP32 FMA rate) about 80% busy.  kDfInv (FP32 and DF32 panels, whose solvers
@@ -650,6 +651,7 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
   double eps = shift;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (attempt > 0) {
+      if (tid == 0) atomicAdd(&flags[4], 1);   // retries, reported to the caller
       fetch();
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
@@ -2408,6 +2410,7 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   const int K = h->K;
   const int64_t KK = (int64_t)K * K;
   h->d_R.alloc(2 * h->n_sub * KK * sizeof(double), st);
+  h->bj_retries = 0;
   if (identity) return;
   if (K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up supports K <= 128");
   // chunks of at most 2048 rows of one panel, as 16-row steps (entry, first
@@ -2511,9 +2514,10 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
-  int flags[4];
-  CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int flags[5];
+  CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaStreamSynchronize(st));
+  h->bj_retries = flags[4];
   if (flags[3]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "block-Jacobi set-up: a copy wait timed out");
   if (flags[1]) ELMFB_THROW(ELMFB_ERR_BREAKDOWN, "block Cholesky failed after shift increases");
 }
@@ -2532,6 +2536,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   block_jacobi_setup<T>(h, o->shift, identity);
   stage_end(h, 4);
   info->setup_ms = h->stage_ms[4];
+  info->precond_retries = h->bj_retries;
 
   // panel -> entries (cell order)
   const int ne = (int)h->cover_sub.size();
@@ -2952,6 +2957,7 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   block_jacobi_setup<T>(h, o->shift, false, mu);
   stage_end(h, 4);
   info->setup_ms = h->stage_ms[4] + h->stage_ms[3];
+  info->precond_retries = h->bj_retries;
   FusedPlan fp;
   if (!build_fused_plan(h, fp))
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "PCG needs K <= 128 and <= 32 covering panels per cell");
