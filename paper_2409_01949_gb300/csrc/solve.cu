@@ -9,15 +9,22 @@
 // the shifted Cholesky factor of the diagonal Gram block G_jj = M_j^T M_j.
 // LSQR then runs on A = M P and returns a = P y.
 //
-// Data flow of one iteration (all scalars stay on the device):
-//   k_precond     t_j = R_j^{-1} v_j                       (block per subdomain)
-//   k_gather      u' = M t - alpha u  and ||u'||^2 partials  (warp per row; M read
-//                 through the per-cell list of covering panels, no atomics)
-//   k_entry_T     partial_e = sum_p P[rho(e,p)]^T u'[R(e,p)] (block per (cell, panel))
-//   k_panel_T     v' = R_j^{-T} (sum_e partial_e) / beta - beta v, ||v'||^2 partials
-//   k_update      scalar recurrence (redundantly per block), x, w, v, u updates
-// Every reduction is a fixed-order two-stage sum, so results are bitwise
-// reproducible from run to run.
+// Data flow of one iteration (all scalars stay on the device), fused path:
+//   k_fused_pipe    u' = M t - (alpha/beta) u, the per-unit partials of M^T u'
+//                   and the ||u'||^2 partials, in one read of the panels
+//                   (k_fused_pipe_df for DF32 panels, k_fused without a ring)
+//   k_panel_chunks  fixed slices of each panel's partials; block 0 commits the
+//                   staged scalars and forms beta^2
+//   FP32 / DF32 panels: k_lsqr_tail_tri -- the previous iteration's deferred
+//                   w / x update, v' = X z / beta - beta v, t' = X^T v' (the
+//                   next pass scales M t' by 1/alpha), the recurrence in the
+//                   last block to finish; k_lsqr_finish after the loop
+//   FP64 panels:    k_panel_T2 (v'), then k_update_precond (recurrence, v, w,
+//                   x, t = X^T v)
+// Without the fused plan (more than 32 covering panels or K > 128) an
+// iteration is k_precond, k_gather, k_entry_T, k_panel_T, k_update.
+// Every reduction is a fixed-order sum, so results are bitwise reproducible
+// from run to run.
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -33,8 +40,10 @@ constexpr int kGatherThreads = 256;
 constexpr int kScal = 32;             // device scalar slots
 
 // scalar slots in d_scal: [0, 16) committed values read by the kernels of an
-// iteration, [16, 32) staged values written by k_panel_T / k_update; k_precond
-// (first kernel of the next iteration) commits staged -> committed.
+// iteration, [16, 32) staged values written by the kernel that runs the
+// recurrence; the next iteration's first reader of committed values
+// (k_panel_chunks, or k_precond without the fused plan) commits staged ->
+// committed.
 constexpr int kStage = 16;
 enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
@@ -401,7 +410,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_pipe(const T* __restrict__ pa
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-#pragma unroll 4
+#pragma unroll 8
       for (int r = 0; r < 16; ++r) {
         T x[4], y[4];
         lds4(sm + r * K + 4 * ti, x);
@@ -2719,7 +2728,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     int batch = std::min(o->check_every, max_it - it);
     for (int b = 0; b < batch; ++b) {
       if (fused) {
-        // t (and its low-precision copy) come from the previous k_update_precond
+        // t (and its low-precision copy) come from the previous iteration's tail
         fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);
         fused_tail(0);
       } else {
