@@ -1766,7 +1766,7 @@ __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restr
   }
   if (g < G && k < K) {
     float hi = 0.f, lo = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int q = pco[s] + g; q < pco[s + 1]; q += G) {
       const float2 pr = partial_pair(csum, (int64_t)q * K + k);
       ff_add(hi, lo, pr.x, pr.y);
@@ -1998,14 +1998,15 @@ __device__ LsqrStep lsqr_recurrence(double* __restrict__ scal, double a2, double
   } else {
     const double rhobar = scal[S_RHOBAR], phibar = scal[S_PHIBAR];
     const double rho = sqrt(rhobar * rhobar + beta * beta);
-    const double c = rho > 0.0 ? rhobar / rho : 1.0;
-    const double sn = rho > 0.0 ? beta / rho : 0.0;
+    const double irho = rho > 0.0 ? 1.0 / rho : 0.0;   // one FP64 division, then products
+    const double c = rho > 0.0 ? rhobar * irho : 1.0;
+    const double sn = beta * irho;
     const double theta = sn * alpha;
     rhobar_new = -c * alpha;
     const double phi = c * phibar;
     phibar_new = sn * phibar;
-    r.phi_rho = rho > 0.0 ? phi / rho : 0.0;
-    r.theta_rho = rho > 0.0 ? theta / rho : 0.0;
+    r.phi_rho = phi * irho;
+    r.theta_rho = theta * irho;
     anorm2 = scal[S_ANORM2] + alpha * alpha + beta * beta;
     arnorm = phibar_new * alpha * fabs(c);
   }
