@@ -63,6 +63,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, device=None):
+    """The largest x over the ranks of the process group (one rank: x).
+
+    With N replicas (one per GPU, each solving the workload on its own) the
+    job's time is the slowest replica's: every rank passes its own time and
+    all receive the maximum."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -269,11 +285,8 @@ def run_ours(args):
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1) / args.steps
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, dev)
     if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
 
     # end-to-end through the public API from pinned host buffers
@@ -300,11 +313,7 @@ def run_ours(args):
     for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - e0) / args.steps
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / args.steps, dev)
 
     if rank != 0:
         if ws > 1:
