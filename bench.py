@@ -41,6 +41,9 @@ DOMINANT = "fused_Mt_MTu"   # the LSQR pass: the largest share of a step
 # from the ncu capture summarised in profiles/k_fused_pipe_poisson2d_L1-16_K128_N200.md
 # (a quarter-size case of the same kernel; its traffic grows with the panel bytes)
 FUSED_FP32_TRAFFIC_PER_BYTE = (346.5 + 12.5) / 346.4
+# the same for the DF32-panel pass (k_fused_pipe_df), from the full-size DHO
+# capture in profiles/k_fused_pipe_df_dho_L1-64_K96_N20000.md
+FUSED_DF32_TRAFFIC_PER_BYTE = 192.4 / 189.4
 # workload -> (problem, oracle golden name, panel precision)
 WORKLOADS = {
     "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400", "fp32"),
@@ -365,9 +368,13 @@ def run_ours(args):
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(ach / hbm, 4),
                      "traffic": (round(kstats[dom][2] * FUSED_FP32_TRAFFIC_PER_BYTE)
-                                 if prec == E.FP32 else None),
+                                 if prec == E.FP32 else
+                                 round(kstats[dom][2] * FUSED_DF32_TRAFFIC_PER_BYTE)
+                                 if prec == E.DF32 else None),
                      "traffic_note": ("DRAM bytes per launch scaled from the ncu capture of the "
-                                      "200x200 case" if prec == E.FP32 else None),
+                                      "200x200 case" if prec == E.FP32 else
+                                      "DRAM bytes per launch from the ncu capture of the DHO "
+                                      "workload" if prec == E.DF32 else None),
                      "peak_kind": peak_kind,
                      "timed_launches": int(kstats[dom][1]),
                      "timed_every": args.roofline_stride},

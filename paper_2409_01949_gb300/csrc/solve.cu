@@ -2214,11 +2214,19 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
   if (h->max_cover > 32 || K > 128) return false;
   cudaStream_t st = h->stream;
   fp.threads = 32 * std::max(1, h->max_cover);
-  // rows per work unit: about NR / 608 (4 waves of CTAs); ELMFB_FUSED_UNIT_ROWS
-  // overrides it (a tuning knob: units change the timing, not the arithmetic
-  // order within a row)
-  int64_t target =
-      std::min<int64_t>(kMaxUnitRows, std::max<int64_t>(8, (h->NR / 608) & ~int64_t(7)));
+  // rows per work unit: about NR / 608 (4 waves of one-CTA-per-SM units), but
+  // at least the rows of about 2 MB of covering panels, so that a unit's
+  // start-up (barrier set-up, the first copies in flight) stays small next to
+  // its stream.  2-D workload (17 panels of 128 FP32): 264 rows either way;
+  // DHO (13 panels of 96 DF32): 200 rather than 32 rows, one wave of whole
+  // cells, fused pass 75 -> 68 us.  ELMFB_FUSED_UNIT_ROWS overrides it (a
+  // tuning knob: units change the timing and the grouping of the Mᵀu partial
+  // sums, not the order of the terms within a row)
+  const double row_bytes =
+      (double)h->NPR / (double)std::max<int64_t>(h->NR, 1) * K * (double)h->panel_elem();
+  const int64_t by_bytes = (int64_t)((2.0 * 1024 * 1024) / std::max(row_bytes, 1.0));
+  int64_t target = std::min<int64_t>(
+      kMaxUnitRows, std::max<int64_t>(8, std::max(h->NR / 608, by_bytes) & ~int64_t(7)));
   if (const char* e = getenv("ELMFB_FUSED_UNIT_ROWS")) {
     const long v = atol(e);
     if (v >= 8 && v <= kMaxUnitRows) target = v & ~7L;
