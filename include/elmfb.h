@@ -60,7 +60,7 @@ enum {
   ELMFB_DF32 = 3    /* panels as FP32 pairs (hi + lo, ~48-bit significand, same
                        8 bytes as FP64), products and sums in float-float
                        arithmetic on the FP32 pipes; entries evaluated in FP64.
-                       The solvers need K a multiple of 4, K <= 128 and <= 31
+                       The solvers need K a multiple of 4, K <= 128 and <= 30
                        covering panels per cell (else UNSUPPORTED)            */
 };
 

@@ -1057,9 +1057,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
 }
 
 // Same pass, pipelined through shared memory by bulk copies and specialised
-// warps.  Warp w < m owns covering panel w of the unit; one extra control
-// warp issues the copies (lane w copies panel w's rows) and forms u'.  Chunks
-// of kPipeRows rows of every covering panel land in a ring of S stages.
+// warps.  Warp w < m owns covering panel w of the unit; one extra producer
+// warp issues the copies and one control warp forms u'.  Chunks of kPipeRows
+// rows of every covering panel land in a ring of S stages.
 // There is no block-wide barrier in the loop; mbarriers carry every
 // dependency:
 //   full[st]   chunk copied in (transaction bytes)
@@ -1069,8 +1069,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
 // Panel warp, chunk i: wait full, form the dots of chunk i, then wait u of
 // chunk i-1 and add P_w[r,:]^T u'_r of chunk i-1, then free its stage.
 // Control warp, chunk j: wait dots, sum them over the panels, form
-// u'_r = y_r - (alpha/beta) u_r in FP64 (written to u), then wait empty for
-// chunk j-1 and refill that stage with chunk j-1+S.  A warp cannot run two
+// u'_r = y_r - (alpha/beta) u_r in FP64 (written to u).  Producer warp,
+// chunk c >= S: wait empty for chunk c-S and refill that stage with chunk c,
+// so that a refill never waits behind the control warp's FP64 chain (which
+// had shortened the time a copy has to land).  A warp cannot run two
 // phases ahead on any barrier: each wait is ordered behind the arrivals it
 // depends on (a panel warp's dots of chunk i+2 follow its wait for u' of
 // chunk i, which needs every dots arrival of chunk i).  The unit's u (or h)
@@ -1155,7 +1157,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const int64_t stage_elems = (int64_t)mmax * kRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(T));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int cw = (blockDim.x >> 5) - 1;   // control warp: copies, u', norms
+  const int cw = (blockDim.x >> 5) - 1;   // control warp: u', norms
+  const int pw = cw - 1;                  // producer warp: the ring's copies
   const int4 un = units[blockIdx.x];      // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
@@ -1187,17 +1190,34 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   constexpr int kYG = 32 / kRows;
   const int yr = lane / kYG, yg = lane % kYG;
 
-  if (w == cw) {
-    // ---------------------------------------------------------- control warp
-    auto issue = [&](int chunk, int stage) {
-      if (lane == 0) {
+  if (w == pw) {
+    // --------------------------------------------------------- producer warp
+    // chunk c goes to stage c mod S once chunk c - S has left it (release
+    // number (c - S) / S of that stage's empty barrier)
+    if (lane == 0) {
+      auto issue = [&](int chunk, int stage) {
         sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
         sm100::bulk_load(ring + stage * stage_elems,
                          panels + (base_row + (int64_t)chunk * kRows * m) * K,
                          copy_bytes * (uint32_t)m, &full[stage]);
+      };
+      for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+      int st_r = 0, ph_r = 0;   // stage / empty parity of chunk c - S
+      for (int c = S; c < nchunks; ++c) {
+        if (!sm100::mbar_wait(&empty[st_r], ph_r, ok ? sm100::kSpinLimit : 4u)) ok = false;
+        sm100::fence_proxy_async_smem();
+        issue(c, st_r);
+        if (++st_r == S) {
+          st_r = 0;
+          ph_r ^= 1;
+        }
       }
-    };
-    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+      if (!ok) atomicOr(&flags[3], 1);
+    }
+    return;
+  }
+  if (w == cw) {
+    // ---------------------------------------------------------- control warp
     if (lane == 0) {
       const uint32_t ub = (uint32_t)(nrows * sizeof(double));
       sm100::mbar_arrive_expect_tx(&ubar, ub);
@@ -1211,7 +1231,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     }
     if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
     double nrm = 0.0;
-    int st_r = 0, ph_r = 0;   // stage / empty parity of chunk j - 1
     for (int j = 0; j < nchunks; ++j) {
       const int b = j & 1;
       if (!sm100::mbar_wait(&dots_bar[b], (j >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
@@ -1230,18 +1249,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
         }
         su[b][yr] = (T)out;
         sm100::mbar_arrive(&u_bar[b]);
-      }
-      // refill the stage of chunk j - 1 once every panel warp has updated with it
-      if (j >= 1) {
-        if (!sm100::mbar_wait(&empty[st_r], ph_r, ok ? sm100::kSpinLimit : 4u)) ok = false;
-        if (j - 1 + S < nchunks) {
-          sm100::fence_proxy_async_smem();
-          issue(j - 1 + S, st_r);
-        }
-        if (++st_r == S) {
-          st_r = 0;
-          ph_r ^= 1;
-        }
       }
     }
     if (!ok && lane == 0) atomicOr(&flags[3], 1);
@@ -1366,7 +1373,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   const int64_t stage_elems = (int64_t)mmax * kPipeRows * K;
   double* us = reinterpret_cast<double*>(ring_raw + (size_t)S * stage_elems * sizeof(float2));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int cw = (blockDim.x >> 5) - 1;   // control warp: copies, u', norms
+  const int cw = (blockDim.x >> 5) - 1;   // control warp: u', norms
+  const int pw = cw - 1;                  // producer warp: the ring's copies
   const int4 un = units[blockIdx.x];      // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
@@ -1396,17 +1404,34 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
   bool ok = true;
   const int yr = lane >> 3, yg = lane & 7;
 
-  if (w == cw) {
-    // ---------------------------------------------------------- control warp
-    auto issue = [&](int chunk, int stage) {
-      if (lane == 0) {
+  if (w == pw) {
+    // --------------------------------------------------------- producer warp
+    // chunk c goes to stage c mod S once chunk c - S has left it (release
+    // number (c - S) / S of that stage's empty barrier)
+    if (lane == 0) {
+      auto issue = [&](int chunk, int stage) {
         sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
         sm100::bulk_load(ring + stage * stage_elems,
                          panels + (base_row + (int64_t)chunk * kPipeRows * m) * K,
                          copy_bytes * (uint32_t)m, &full[stage]);
+      };
+      for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+      int st_r = 0, ph_r = 0;   // stage / empty parity of chunk c - S
+      for (int c = S; c < nchunks; ++c) {
+        if (!sm100::mbar_wait(&empty[st_r], ph_r, ok ? sm100::kSpinLimit : 4u)) ok = false;
+        sm100::fence_proxy_async_smem();
+        issue(c, st_r);
+        if (++st_r == S) {
+          st_r = 0;
+          ph_r ^= 1;
+        }
       }
-    };
-    for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
+      if (!ok) atomicOr(&flags[3], 1);
+    }
+    return;
+  }
+  if (w == cw) {
+    // ---------------------------------------------------------- control warp
     if (lane == 0) {
       const uint32_t ub = (uint32_t)(nrows * sizeof(double));
       sm100::mbar_arrive_expect_tx(&ubar, ub);
@@ -1420,7 +1445,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     }
     if (!sm100::mbar_wait(&ubar, 0, ok ? sm100::kSpinLimit : 4u)) ok = false;
     double nrm = 0.0;
-    int st_r = 0, ph_r = 0;   // stage / empty parity of chunk j - 1
     for (int j = 0; j < nchunks; ++j) {
       const int b = j & 1;
       if (!sm100::mbar_wait(&dots_bar[b], (j >> 1) & 1, ok ? sm100::kSpinLimit : 4u)) ok = false;
@@ -1441,18 +1465,6 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
         }
         su[b][yr] = df_split(out);
         sm100::mbar_arrive(&u_bar[b]);
-      }
-      // refill the stage of chunk j - 1 once every panel warp has updated with it
-      if (j >= 1) {
-        if (!sm100::mbar_wait(&empty[st_r], ph_r, ok ? sm100::kSpinLimit : 4u)) ok = false;
-        if (j - 1 + S < nchunks) {
-          sm100::fence_proxy_async_smem();
-          issue(j - 1 + S, st_r);
-        }
-        if (++st_r == S) {
-          st_r = 0;
-          ph_r ^= 1;
-        }
       }
     }
     if (!ok && lane == 0) atomicOr(&flags[3], 1);
@@ -2325,10 +2337,10 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     const size_t u_bytes = kMaxUnitRows * sizeof(double);
     const int S = (int)std::min<size_t>(kPipeMaxStages,
                                         (fused_ring_budget() - u_bytes) / std::max<size_t>(stage_bytes, 1));
-    const int pthreads = fthreads + 32;
+    const int pthreads = fthreads + 64;   // covering-panel warps + producer + control
     if (S < 4 || pthreads > 1024 || K % 2 != 0 || fpl > 4)
       ELMFB_THROW(ELMFB_ERR_UNSUPPORTED,
-                  "DF32 needs K even, K <= 128 and <= 31 covering panels per cell");
+                  "DF32 needs K even, K <= 128 and <= 30 covering panels per cell");
     const size_t smem = (size_t)S * stage_bytes + u_bytes;
     prof_begin(h, KID_FUSED, (double)h->NPR * K * 8.0 + 16.0 * h->NR + 8.0 * h->NPhi);
 #define ELMFB_FD(F)                                                                             \
@@ -2380,7 +2392,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
   const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
   // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
   // ring needs the two stages in use plus at least one in flight
-  const int pthreads = fthreads + 32;   // covering-panel warps + the control warp
+  const int pthreads = fthreads + 64;   // covering-panel warps + producer + control
   if (S >= 3 && pthreads <= 1024 && (K * sizeof(T)) % 16 == 0 &&
       !(force_regs && force_regs[0] == '1')) {
     const size_t smem = (size_t)S * stage_bytes + u_bytes;
