@@ -40,10 +40,10 @@ DOMINANT = "fused_Mt_MTu"   # the LSQR pass: the largest share of a step
 # DRAM bytes (read + write) per algorithmic byte of the FP32-panel fused pass,
 # from the ncu capture summarised in profiles/k_fused_pipe_poisson2d_L1-16_K128_N200.md
 # (a quarter-size case of the same kernel; its traffic grows with the panel bytes)
-FUSED_FP32_TRAFFIC_PER_BYTE = (346.5 + 12.5) / 346.4
+FUSED_FP32_TRAFFIC_PER_BYTE = (346.5 + 7.7) / 346.4
 # the same for the DF32-panel pass (k_fused_pipe_df), from the full-size DHO
 # capture in profiles/k_fused_pipe_df_dho_L1-64_K96_N20000.md
-FUSED_DF32_TRAFFIC_PER_BYTE = 192.9 / 189.4
+FUSED_DF32_TRAFFIC_PER_BYTE = 192.5 / 189.4
 # workload -> (problem, oracle golden name, panel precision)
 WORKLOADS = {
     "poisson2d_ml": (WL.config_poisson2d_ml, "poisson2d_L1-16_K128_N400", "fp32"),

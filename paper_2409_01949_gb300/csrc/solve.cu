@@ -1195,11 +1195,15 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     // chunk c goes to stage c mod S once chunk c - S has left it (release
     // number (c - S) / S of that stage's empty barrier)
     if (lane == 0) {
+      // the panels stream through once per pass: evict them first, so that
+      // the data the rest of the iteration reuses (the triangles X_j, the
+      // partials, the vectors: tens of MB) stays in L2
+      const uint64_t pol = sm100::l2_evict_first_policy();
       auto issue = [&](int chunk, int stage) {
         sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
-        sm100::bulk_load(ring + stage * stage_elems,
-                         panels + (base_row + (int64_t)chunk * kRows * m) * K,
-                         copy_bytes * (uint32_t)m, &full[stage]);
+        sm100::bulk_load_hint(ring + stage * stage_elems,
+                              panels + (base_row + (int64_t)chunk * kRows * m) * K,
+                              copy_bytes * (uint32_t)m, &full[stage], pol);
       };
       for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
       int st_r = 0, ph_r = 0;   // stage / empty parity of chunk c - S
@@ -1409,11 +1413,15 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     // chunk c goes to stage c mod S once chunk c - S has left it (release
     // number (c - S) / S of that stage's empty barrier)
     if (lane == 0) {
+      // the panels stream through once per pass: evict them first, so that
+      // the data the rest of the iteration reuses (the triangles X_j, the
+      // partials, the vectors: tens of MB) stays in L2
+      const uint64_t pol = sm100::l2_evict_first_policy();
       auto issue = [&](int chunk, int stage) {
         sm100::mbar_arrive_expect_tx(&full[stage], copy_bytes * (uint32_t)m);
-        sm100::bulk_load(ring + stage * stage_elems,
-                         panels + (base_row + (int64_t)chunk * kPipeRows * m) * K,
-                         copy_bytes * (uint32_t)m, &full[stage]);
+        sm100::bulk_load_hint(ring + stage * stage_elems,
+                              panels + (base_row + (int64_t)chunk * kPipeRows * m) * K,
+                              copy_bytes * (uint32_t)m, &full[stage], pol);
       };
       for (int q = 0; q < S && q < nchunks; ++q) issue(q, q);
       int st_r = 0, ph_r = 0;   // stage / empty parity of chunk c - S
