@@ -74,7 +74,11 @@ enum {
 enum {
   ELMFB_SOLVE_LSQR = 0,     /* right-preconditioned LSQR on M (paper §3, §4.1)   */
   ELMFB_SOLVE_PCG = 1,      /* preconditioned CG on the Gram normal equations    */
-  ELMFB_SOLVE_FCG_GNN = 2   /* flexible CG with the learned preconditioner       */
+  ELMFB_SOLVE_FCG_GNN = 2,  /* flexible CG with the learned preconditioner       */
+  ELMFB_SOLVE_QR = 3        /* dense Householder QR with column pivoting: the
+                               basic least-squares solution with the rank cut
+                               |R_kk| <= rcond |R_11|; needs the dense M (rows x
+                               (columns + 1) FP64) to fit in device memory     */
 };
 
 /* ---- preconditioners --------------------------------------------------------- */
@@ -219,6 +223,8 @@ typedef struct {
                           PCG iterations on the tensor-core Gram for the update */
   double gram_shift;   /* PCG: Tikhonov shift mu, as a fraction of the mean
                           Gram diagonal, added to the Gram operator          */
+  double rcond;        /* QR: rank cut, a column is dropped once the largest
+                          remaining column norm is <= rcond |R_11|           */
 } elmfb_solve_opts;
 
 typedef struct {
@@ -231,11 +237,18 @@ typedef struct {
   int precond_retries;        /* block-Jacobi: factorisations that met a
                                  non-positive pivot and were redone with the
                                  shift raised 100-fold (once per retry)        */
+  int rank;                   /* QR: numerical rank (pivots kept); else 0     */
+  double sigma_max;           /* extreme singular-value estimates of the
+                                 solved operator: LSQR, those of the Golub-
+                                 Kahan bidiagonal B_k of M P (sigma_max from
+                                 below, sigma_min from above: kappa(B_k) <=
+                                 kappa(M P)); QR, |R_11| and |R_rr|; else 0  */
+  double sigma_min;
 } elmfb_solve_info;
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
  * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
- * gram_shift 0. */
+ * gram_shift 0, rcond 1e-13. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the
@@ -244,10 +257,23 @@ void elmfb_default_solve_opts(elmfb_solve_opts* opts);
  * `refine` outer steps a += PCG(G_bf16 + mu I, M^T (h - M a)), each with
  * max_iter PCG iterations preconditioned by the block-Jacobi factors; it
  * needs ELMFB_MIXED precision (tensor-core Gram).
+ * ELMFB_SOLVE_QR (a direct solve; the paper's LSQR resolves the small
+ * singular directions only slowly) factors the dense M with column pivoting
+ * in FP64 and returns the basic solution of rank `rank`; info->iterations =
+ * rank, residual_norm = ||M a - h|| exactly.  UNSUPPORTED when the dense M
+ * does not fit in device memory.
  * Errors: STATE before assemble, BREAKDOWN, NONFINITE, INVALID_ARG; TIMEOUT
  * when an on-device wait for a bulk copy ran out.
  * Returns NOT_CONVERGED (with valid coefficients) at the iteration cap. */
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info);
+
+/* The Golub-Kahan bidiagonal of the last LSQR solve (Paige & Saunders 1982,
+ * their §3; M P with the solve's preconditioner P): alpha [k + 1] and
+ * beta [k + 1] with beta_1 = ||h||, B_k lower bidiagonal with alpha_1..alpha_k
+ * on its diagonal and beta_2..beta_{k+1} below it; k = the solve's
+ * iterations, recorded up to max_iter + 1 entries.  *k_out receives k; either
+ * array may be NULL; at most `max` entries of each are written. */
+int elmfb_get_bidiagonal(elmfb_t h, int64_t max, double* alpha, double* beta, int64_t* k_out);
 
 /* ---- learned preconditioner (not in the paper) ------------------------------
  * A message-passing network on the subdomain graph (nodes = subdomains, edges
@@ -364,8 +390,9 @@ int elmfb_kernel_stats(elmfb_t h, int max, const char** names, double* total_ms,
  * It computes the same three numbers as elmfb_error_norms() (relative L2,
  * e_L1 with the population standard deviation, max |u_hat - u_ref|) but needs
  * no handle, makes no staging copies and calls no allocating routine.
- *   u_hat, u_ref  [n] FP64 in device (or managed) memory; host pointers are
- *                 rejected with ELMFB_ERR_INVALID_ARG
+ *   u_hat, u_ref  [n] FP64 in the current device's memory (or managed
+ *                 memory), read in place; host pointers and memory of another
+ *                 device are rejected with ELMFB_ERR_INVALID_ARG
  *   n             1 .. ELMFB_NOALLOC_MAX_POINTS; larger n returns
  *                 ELMFB_ERR_UNSUPPORTED before anything runs
  *   out3          [3] host memory
@@ -373,11 +400,16 @@ int elmfb_kernel_stats(elmfb_t h, int max, const char** names, double* total_ms,
  *                 the call synchronises it before returning
  * Scratch: a fixed 12 KB array in the library's device globals, one per
  * device, held until the process exits.  The first call on a device looks up
- * that array's device address (one-time set-up with the device current), so
- * make that first call before any stream capture.  Every call shares the
- * array: calls that overlap on the GPU race and must be ordered by the
- * caller.  Returns ELMFB_OK, INVALID_ARG, UNSUPPORTED or CUDA; there is no
- * handle, so no message is kept. */
+ * that array's device address (one-time set-up with the device current) and
+ * caches it; after a cudaDeviceReset() of that device the cached address is
+ * stale, so do not call this entry point again in that process.  Every call
+ * shares the array: calls that overlap on the GPU race and must be ordered by
+ * the caller.  Each call copies the partial sums to host memory and
+ * synchronises the stream, so it cannot be called while that stream is being
+ * captured.  An error already pending from earlier CUDA runtime calls is
+ * reported as ELMFB_ERR_CUDA and left pending for its owner.  Returns
+ * ELMFB_OK, INVALID_ARG, UNSUPPORTED or CUDA; there is no handle, so no
+ * message is kept. */
 #define ELMFB_NOALLOC_MAX_POINTS ((int64_t)1 << 24)
 int elmfb_error_norms_noalloc(const double* u_hat, const double* u_ref, int64_t n, double* out3,
                               void* cuda_stream);

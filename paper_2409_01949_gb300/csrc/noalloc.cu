@@ -13,7 +13,9 @@
 // the process exits.  Every call shares it and it keeps the previous call's
 // contents; each pass writes every slot it later reads, so nothing needs
 // clearing.  Calls whose kernels overlap on the GPU (different streams, no
-// ordering) race on the array.
+// ordering) race on the array.  Its device address is looked up once per
+// device and cached; a cudaDeviceReset() reloads the module at another
+// address, so the cache does not survive a reset of that device.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -89,13 +91,17 @@ __global__ void k_na_pass2(const double* __restrict__ ur, int64_t n, double* __r
   }
 }
 
-bool is_device_pointer(const void* p) {
+// Device memory of device `dev` (the kernels read it in place, so memory of
+// another GPU is refused: without peer access it is not addressable here), or
+// managed memory.
+bool is_device_pointer(const void* p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();   // the lookup's own error, raised just now
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+  return a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -106,7 +112,9 @@ extern "C" int elmfb_error_norms_noalloc(const double* u_hat, const double* u_re
   if (n > ELMFB_NOALLOC_MAX_POINTS) return ELMFB_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ELMFB_ERR_CUDA;
-  if (!is_device_pointer(u_hat) || !is_device_pointer(u_ref)) return ELMFB_ERR_INVALID_ARG;
+  // an error left pending by earlier runtime calls is reported, not consumed
+  if (cudaPeekAtLastError() != cudaSuccess) return ELMFB_ERR_CUDA;
+  if (!is_device_pointer(u_hat, dev) || !is_device_pointer(u_ref, dev)) return ELMFB_ERR_INVALID_ARG;
   double* scratch = nullptr;
   {
     // one-time set-up per device, with that device current
@@ -114,7 +122,7 @@ extern "C" int elmfb_error_norms_noalloc(const double* u_hat, const double* u_re
     if (!g_scratch_addr[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
+        cudaGetLastError();   // the lookup's own error (none was pending before it)
         return ELMFB_ERR_CUDA;
       }
       g_scratch_addr[dev] = static_cast<double*>(p);
@@ -124,8 +132,9 @@ extern "C" int elmfb_error_norms_noalloc(const double* u_hat, const double* u_re
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nb = (int)std::min<int64_t>((n + kNaThreads - 1) / kNaThreads, kNaBlocks);
   k_na_pass1<<<nb, kNaThreads, 0, st>>>(u_hat, u_ref, n, scratch);
+  if (cudaPeekAtLastError() != cudaSuccess) return ELMFB_ERR_CUDA;
   k_na_pass2<<<nb, kNaThreads, 0, st>>>(u_ref, n, scratch, nb);
-  if (cudaGetLastError() != cudaSuccess) return ELMFB_ERR_CUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return ELMFB_ERR_CUDA;
   double part[kNaSlots];
   if (cudaMemcpyAsync(part, scratch, sizeof(part), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)

@@ -1,10 +1,20 @@
 """GPU parity of the least-squares solve, model evaluation and error norms.
 
-Solution parity (paper Eq. multilevel_ls solved by LSQR, §3 and §4.1): the
-GPU solution's relative L2 error against the closed-form solution must not
-exceed 1.01x the error of the oracle run with the paper's protocol (SciPy
-LSQR from zero, full 15000-iteration budget).  The oracle's column-pivoted QR
-minimiser is reported beside it as the best attainable error.
+Solution parity against the oracle's least-squares minimiser (Eq.
+multilevel_ls), wherever the dense system fits the oracle's memory: the GPU's
+column-pivoted QR solve (ELMFB_SOLVE_QR, the oracle's algorithm) must reach
+a relative L2 error against the closed-form solution of at most 1.01x the
+oracle's QR error, where that error is taken as the largest over the oracle's
+QR of the system in its own row order and in three shuffled row orders (row
+order changes no minimiser, only the FP64 rounding; two valid FP64 QRs of the
+1-D Poisson system differ by 5% in this error).
+
+The LSQR path (the paper's solver, §3 and §4.1) is held to the paper's own
+protocol: at most 1.01x the error of SciPy LSQR from zero run for the full
+15000-iteration budget; its iterates are compared with SciPy's.  The QR
+minimiser is out of reach of LSQR at these condition numbers (1e17 and
+more): it uses singular directions that the Krylov iteration resolves only
+after far more than 15000 steps.
 """
 import json
 import os
@@ -121,9 +131,88 @@ _SOLVE_CASES = [
 ]
 
 
+_QR_CASES = _SOLVE_CASES + [("dho_L1-64_K96_N20000", WL.config_dho_ml)]
+
+
+@pytest.mark.parametrize("name,make,prec", [(n, m, p) for n, m in _QR_CASES
+                                            for p in (E.FP64, E.DF32)])
+def test_solution_matches_oracle_qr_minimiser(name, make, prec):
+    """The GPU's column-pivoted QR on the assembled system reaches the
+    oracle's QR error (1.01x its largest value over row orders), with a
+    numerical rank within the oracle's range over those orders (+-2: a pivot
+    near the rank cut may fall either side of it)."""
+    g = _golden(name)
+    if "qr" not in g or "rel_l2_max_over_orders" not in g["qr"]:
+        pytest.skip(f"{name}: no QR entry over row orders in oracle_errors.json")
+    q = g["qr"]
+    P = make()
+    with E.Solver.from_problem(P, precision=prec) as s:
+        s.assemble_problem(P)
+        info = s.solve(method=E.SOLVE_QR)
+        uh = s.eval(P.test_points)
+        err = s.error_norms(uh, P.exact(P.test_points))
+    ranks = [q["rank"]] + [o["rank"] for o in q["orders"]]
+    print(f"{name} prec={prec}: gpu QR rel L2 {err['rel_l2']:.4e} rank {info.rank} "
+          f"({info.solve_ms:.1f} ms, residual {info.residual_norm:.4e}); oracle QR "
+          f"{q['rel_l2']:.4e}, max over orders {q['rel_l2_max_over_orders']:.4e}, "
+          f"ranks {ranks}, residual {q['residual']:.4e}")
+    assert err["rel_l2"] <= 1.01 * q["rel_l2_max_over_orders"]
+    assert min(ranks) - 2 <= info.rank <= max(ranks) + 2
+    assert info.residual_norm <= 1.01 * max([q["residual"]] + [o["residual"] for o in q["orders"]])
+
+
+def test_qr_full_rank_coefficients_match_oracle():
+    """A small full-rank system (kappa ~ 1e4): the least-squares solution is
+    unique, so the GPU QR's coefficients equal the oracle QR's."""
+    from oracle import lstsq as OL
+    P = WL.poisson1d(levels=(4,), features=4, n_interior=200, lam=100.0)
+    ref = OS.assemble(P, fmt="dense")
+    a_ref, rank = OL.lstsq_qr(ref["M"], ref["h"])
+    assert rank == P.n_columns
+    with E.Solver.from_problem(P, precision=E.FP64) as s:
+        s.assemble_problem(P)
+        info = s.solve(method=E.SOLVE_QR)
+        a = s.coeffs()
+    assert info.rank == rank and info.iterations == rank
+    assert np.linalg.norm(a - a_ref) <= 1e-11 * np.linalg.norm(a_ref)
+    assert info.residual_norm == pytest.approx(np.linalg.norm(ref["M"] @ a_ref - ref["h"]),
+                                               rel=1e-10)
+
+
+def test_qr_rank_deficient_fit_matches_oracle():
+    """Rank deficient (overlapping subdomains, 16 features each): the fitted
+    values M a and the residual are unique and match the oracle's."""
+    from oracle import lstsq as OL
+    P = WL.dho(levels=(1, 2, 4), features=16, n_interior=300, omega0=10.0)
+    ref = OS.assemble(P, fmt="dense")
+    M, h = ref["M"], ref["h"]
+    a_ref, rank = OL.lstsq_qr(M, h)
+    with E.Solver.from_problem(P, precision=E.FP64) as s:
+        s.assemble_problem(P)
+        info = s.solve(method=E.SOLVE_QR)
+        a = s.coeffs()
+    print(f"rank gpu {info.rank} oracle {rank} of {M.shape[1]}")
+    assert abs(info.rank - rank) <= 1
+    fit, fit_ref = M @ a, M @ a_ref
+    assert np.linalg.norm(fit - fit_ref) <= 1e-9 * np.linalg.norm(h)
+    assert np.linalg.norm(fit - h) == pytest.approx(np.linalg.norm(fit_ref - h), rel=1e-6)
+
+
+def test_qr_rejects_a_dense_matrix_beyond_device_memory():
+    """The 2-D multilevel Poisson workload at 400^2 (161,600 x 43,649 dense,
+    56 GB) fits a GB300; a 1024^2 grid with 4096 subdomains of 32 features
+    would not (1.1 TB): UNSUPPORTED before anything is allocated."""
+    P = WL.poisson2d(levels=(64,), features=32, n_side=1024, n_boundary_side=8)
+    with E.Solver.from_problem(P, precision=E.FP32) as s:
+        s.assemble_problem(P)
+        with pytest.raises(E.ElmfbError) as ei:
+            s.solve(method=E.SOLVE_QR)
+        assert ei.value.code == E.ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("name,make,prec", [(n, m, p) for n, m in _SOLVE_CASES
                                             for p in (E.FP64, E.DF32)])
-def test_block_jacobi_lsqr_matches_oracle_error(name, make, prec):
+def test_block_jacobi_lsqr_meets_paper_protocol_error(name, make, prec):
     g = _golden(name)
     P = make()
     with E.Solver.from_problem(P, precision=prec) as s:

@@ -53,3 +53,32 @@ def test_fd_gradient_consistent_with_directional_derivative():
     e = 1e-5
     dd = (G.loss(w + e * d, X, T, wb, nbrs, K, H) - G.loss(w - e * d, X, T, wb, nbrs, K, H)) / (2 * e)
     assert abs(dd - g @ d[idx]) <= 1e-5 * max(1.0, abs(dd))
+
+
+def test_hand_computed_forward_on_three_node_path():
+    """Path graph 0 - 1 - 2, K = 1, H = 2, one sample x = (1, -2, 3), integer
+    weights, written out by hand:
+      W_in = [1, -1]^T, b_in = (0, 1): A0 = (1,0), (0,3), (3,0) (the input
+      ReLU clips node 1's first and node 2's second channel);
+      every layer W_self = diag(1, 2), W_nb = [[0,1],[1,0]], b = (0, -1):
+      A1 = (4,0), (0,7), (6,0); A2 = (11,0), (0,18), (13,0);
+      A3 = (29,0), (0,47), (31,0) (means over neighbours; the -1 channel
+      clipped by the ReLU at nodes 0 and 2);
+      W_out = [1, -1], b_out = 0.5: Y = 29.5, -46.5, 31.5.
+    Swapping W_self and W_nb, a sum instead of a mean, or a dropped ReLU all
+    change Y."""
+    K, H = 1, 2
+    w = np.zeros(G.n_weights(K, H))
+    P = G.unpack(w, K, H)          # views into w
+    P["W_in"][:] = [[1.0], [-1.0]]
+    P["b_in"][:] = [0.0, 1.0]
+    for l in range(3):
+        P[f"W_self{l}"][:] = [[1.0, 0.0], [0.0, 2.0]]
+        P[f"W_nb{l}"][:] = [[0.0, 1.0], [1.0, 0.0]]
+        P[f"b{l}"][:] = [0.0, -1.0]
+    P["W_out"][:] = [[1.0, -1.0]]
+    P["b_out"][:] = [0.5]
+    X = np.array([[[1.0], [-2.0], [3.0]]])
+    nbrs = [np.array([1]), np.array([0, 2]), np.array([1])]
+    Y = G.forward(w, X, nbrs, K, H)
+    assert np.array_equal(Y[0, :, 0], [29.5, -46.5, 31.5])
