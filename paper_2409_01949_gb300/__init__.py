@@ -24,7 +24,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_BREAKD
     ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(10)
 FP64, FP32, MIXED, DF32 = 0, 1, 2, 3
 PLACE_CELL, PLACE_ENDPOINT = 0, 1
-SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN = 0, 1, 2
+SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN, SOLVE_QR = 0, 1, 2, 3
 PREC_NONE, PREC_BLOCK_JACOBI, PREC_BJ_GNN = 0, 1, 2
 MAX_LEVELS = 12
 MAX_ROWSETS = 16
@@ -64,7 +64,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int), ("preconditioner", C.c_int), ("max_iter", C.c_int),
                 ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
                 ("check_every", C.c_int), ("warm_start", C.c_int), ("refine", C.c_int),
-                ("gram_shift", C.c_double)]
+                ("gram_shift", C.c_double), ("rcond", C.c_double)]
 
 
 class BatchItem(C.Structure):
@@ -82,7 +82,8 @@ class BatchResult(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_norm", C.c_double),
                 ("normal_residual_norm", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double), ("precond_retries", C.c_int)]
+                ("solve_ms", C.c_double), ("precond_retries", C.c_int), ("rank", C.c_int),
+                ("sigma_max", C.c_double), ("sigma_min", C.c_double)]
 
 
 _lib = None
@@ -99,6 +100,8 @@ _SIGNATURES = {
     "elmfb_default_solve_opts": (None, [C.POINTER(SolveOpts)]),
     "elmfb_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "elmfb_get_coeffs": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "elmfb_get_bidiagonal": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
     "elmfb_set_coeffs": (C.c_int, [C.c_void_p, C.c_void_p]),
     "elmfb_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "elmfb_error_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
@@ -368,6 +371,17 @@ class Solver:
         _check(self.h, lib().elmfb_solve(self.h, C.byref(opts), C.byref(info)),
                allow=(OK, ERR_NOT_CONVERGED))
         return info
+
+    def bidiagonal(self):
+        """(alpha, beta) of the last LSQR solve's Golub-Kahan bidiagonal."""
+        k = C.c_int64()
+        _check(self.h, lib().elmfb_get_bidiagonal(self.h, 0, None, None, C.byref(k)))
+        n = k.value + 1
+        al = np.zeros(n)
+        be = np.zeros(n)
+        _check(self.h, lib().elmfb_get_bidiagonal(self.h, n, al.ctypes.data, be.ctypes.data,
+                                                  None))
+        return al, be
 
     def coeffs(self):
         a = np.zeros(self.sizes().n_columns)

@@ -473,6 +473,7 @@ void elmfb_default_solve_opts(elmfb_solve_opts* o) {
   o->warm_start = 0;
   o->refine = 1;
   o->gram_shift = 0.0;
+  o->rcond = 1e-13;
 }
 
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info) {
@@ -483,9 +484,11 @@ int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info)
     elmfb_default_solve_opts(&o);
     if (opts) o = *opts;
     if (o.max_iter < 0 || o.check_every < 1 || !(o.shift >= 0.0) || o.refine < 1 ||
-        !(o.gram_shift >= 0.0))
+        !(o.gram_shift >= 0.0) || !(o.rcond >= 0.0))
       ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad solver options");
     elmfb_solve_info inf{};
+    h->gk_alpha.clear();
+    h->gk_beta.clear();
     solve_system(h, &o, &inf);
     h->have_coeffs = true;
     nc_status = inf.status;
@@ -493,6 +496,19 @@ int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info)
   });
   if (rc != ELMFB_OK) return rc;
   return nc_status;
+}
+
+int elmfb_get_bidiagonal(elmfb_t h, int64_t max, double* alpha, double* beta, int64_t* k_out) {
+  return guarded(h, [&] {
+    if (max < 0) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "negative max");
+    const int64_t n = (int64_t)h->gk_alpha.size();
+    if (k_out) *k_out = n > 0 ? n - 1 : 0;
+    const int64_t c = std::min<int64_t>(n, max);
+    if (alpha && c > 0)
+      CUDA_CHECK(cudaMemcpy(alpha, h->gk_alpha.data(), c * sizeof(double), cudaMemcpyDefault));
+    if (beta && c > 0)
+      CUDA_CHECK(cudaMemcpy(beta, h->gk_beta.data(), c * sizeof(double), cudaMemcpyDefault));
+  });
 }
 
 int elmfb_get_coeffs(elmfb_t h, double* a) {

@@ -173,6 +173,9 @@ struct elmfb_ctx {
   DevBuf d_gnn_off, d_gnn_nb, d_gnn_w, d_gnn_m, d_gnn_v, d_gnn_act, d_gnn_lp, d_gnn_dy;
   bool gnn_trained = false;
 
+  // Golub-Kahan record of the last LSQR solve: alpha_1.., beta_1..
+  std::vector<double> gk_alpha, gk_beta;
+
   // solution
   DevBuf d_a;           // [NPhi] FP64
   bool have_coeffs = false;
@@ -220,6 +223,11 @@ void gram_compute(elmfb_ctx* h);
 
 // solve (solve.cu)
 void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
+// extreme singular values of the Golub-Kahan bidiagonal recorded as (alpha,
+// beta) pairs, k steps: out2[0] = sigma_max, out2[1] = sigma_min (device)
+void bidiag_extremes(elmfb_ctx* h, const double* gk, int k, double* out2);
+// dense column-pivoted QR solve (direct.cu)
+void qr_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
 
 // Work plan of the fused pass: units (cell, row range, first partial) and, per
 // panel, the list of partial rows that sum to its part of M^T u'.

@@ -49,8 +49,24 @@ enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
   S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO,
   S_BSQ,    // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
-  S_TSCALE  // 1/alpha: the fused pass's factor on M t' (mode 2, t' = P v' unnormalised)
+  S_TSCALE, // 1/alpha: the fused pass's factor on M t' (mode 2, t' = P v' unnormalised)
+  S_GKCAP   // capacity (entries) of the Golub-Kahan record after the 2 kScal slots
 };
+
+// Record alpha_{i+1}, beta_{i+1} of LSQR step i (i = the new iteration count;
+// 0 = the start: alpha_1, beta_1) after the scalar slots, while it fits: the
+// lower bidiagonal B_k of Golub-Kahan (Paige & Saunders 1982, §3), whose
+// extreme singular values estimate those of the operator.
+__device__ __forceinline__ void record_bidiagonal(double* __restrict__ scal, double iter,
+                                                  double alpha, double beta) {
+  const int cap = (int)scal[kStage + S_GKCAP];
+  const int it = (int)iter;
+  if (it >= 0 && it < cap) {
+    double* gk = scal + 2 * kScal;
+    gk[2 * it] = alpha;
+    gk[2 * it + 1] = beta;
+  }
+}
 
 template <class T>
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1995,6 +2011,7 @@ __global__ void k_update(double* __restrict__ scal, const double* __restrict__ a
     sg[S_BNORM] = init ? beta : scal[S_BNORM];
     sg[S_ITER] = scal[S_ITER] + (init ? 0.0 : 1.0);
     sg[S_BAD] = (scal[S_BAD] != 0.0 || !(alpha == alpha) || !(beta == beta)) ? 1.0 : 0.0;
+    record_bidiagonal(scal, sg[S_ITER], alpha, beta);
   }
 }
 
@@ -2045,6 +2062,7 @@ __device__ LsqrStep lsqr_recurrence(double* __restrict__ scal, double a2, double
     sg[S_PHI_RHO] = r.phi_rho;
     sg[S_THETA_RHO] = r.theta_rho;
     sg[S_TSCALE] = r.ia;
+    record_bidiagonal(scal, sg[S_ITER], alpha, beta);
   }
   return r;
 }
@@ -2562,6 +2580,73 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
 
 namespace {
 
+// Number of eigenvalues below lam of the Golub-Kahan tridiagonal of B_k: the
+// (2k+1) x (2k+1) symmetric matrix with zero diagonal and off-diagonal
+// alpha_1, beta_2, alpha_2, beta_3, ..., alpha_k, beta_{k+1}, whose eigenvalues
+// are +-sigma_i(B_k) and 0 (Golub & Kahan 1965).  Sturm sequence of the LDL^T
+// factorisation of T - lam I, tiny pivots replaced by -pivmin.
+__device__ int gk_sturm_count(const double* __restrict__ gk, int k, double lam, double pivmin) {
+  double d = -lam;
+  int cnt = d < 0.0;
+  for (int i = 0; i < 2 * k; ++i) {
+    const int j = i >> 1;
+    const double e = (i & 1) ? gk[2 * (j + 1) + 1] : gk[2 * j];   // beta_{j+2} : alpha_{j+1}
+    if (fabs(d) < pivmin) d = -pivmin;
+    d = -lam - e * e / d;
+    cnt += d < 0.0;
+  }
+  return cnt;
+}
+
+// Extreme singular values of B_k by multisection of the Sturm count (one warp,
+// 32 trial points per round; geometric spacing once the interval is off 0):
+// out[0] = sigma_max (the point where the count reaches 2k+1), out[1] =
+// sigma_min (where it reaches k+2).  k = 0: zeros.
+__global__ void k_bidiag_extremes(const double* __restrict__ gk, int k, double* __restrict__ out) {
+  const int lane = threadIdx.x;
+  if (k <= 0) {
+    if (lane < 2) out[lane] = 0.0;
+    return;
+  }
+  double bound = 0.0, emax2 = 0.0, eprev = 0.0;
+  for (int i = 0; i < 2 * k; ++i) {
+    const int j = i >> 1;
+    const double e = fabs((i & 1) ? gk[2 * (j + 1) + 1] : gk[2 * j]);
+    bound = fmax(bound, eprev + e);
+    eprev = e;
+    emax2 = fmax(emax2, e * e);
+  }
+  bound = fmax(bound, eprev) * (1.0 + 1e-12) + 1e-300;
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
+  for (int which = 0; which < 2; ++which) {
+    const int target = which == 0 ? 2 * k + 1 : k + 2;
+    double lo = 0.0, hi = bound;
+    for (int round = 0; round < 200 && hi > lo * (1.0 + 4e-16); ++round) {
+      const double f = (double)(lane + 1) / 33.0;
+      const double lam = lo > 0.0 ? lo * pow(hi / lo, f) : hi * f;
+      const bool below = gk_sturm_count(gk, k, lam, pivmin) < target;
+      const unsigned m = __ballot_sync(0xffffffffu, below);
+      // lanes 0..n-1 lie below the point; the new interval is [lam_{n-1}, lam_n]
+      const int nb = __popc(m);
+      const double l_lo = __shfl_sync(0xffffffffu, lam, nb > 0 ? nb - 1 : 0);
+      const double l_hi = __shfl_sync(0xffffffffu, lam, nb < 32 ? nb : 31);
+      if (nb > 0) lo = l_lo;
+      if (nb < 32) hi = l_hi;
+    }
+    if (lane == 0) out[which] = 0.5 * (lo + hi);
+  }
+}
+
+}  // namespace
+
+void bidiag_extremes(elmfb_ctx* h, const double* gk, int k, double* out2) {
+  k_bidiag_extremes<<<1, 32, 0, h->stream>>>(gk, k, out2);
+  check_launch("k_bidiag_extremes");
+  count_launch(h);
+}
+
+namespace {
+
 template <class T>
 void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   cudaStream_t st = h->stream;
@@ -2598,12 +2683,21 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   h->d_x_sol.alloc(N * sizeof(double), st);
   h->d_tmp.alloc(std::max<int64_t>(N, h->NR) * sizeof(double), st);
   h->d_partial.alloc((int64_t)ne * K * sizeof(double), st);
-  h->d_scal.alloc(2 * kScal * sizeof(double), st);
+  // scalar slots, then the Golub-Kahan record (alpha, beta) of steps 0..max_iter
+  const int gk_cap = o->max_iter + 1;
+  h->d_scal.alloc((2 * kScal + 2 * (size_t)gk_cap) * sizeof(double), st);
   h->d_ptile.alloc((kGatherBlocks + h->n_sub + 8) * sizeof(double), st);
   double* gpart = h->d_ptile.as<double>();
   double* vpart = gpart + kGatherBlocks;
   const double panel_bytes = (double)h->NPR * K * sizeof(T);
   CUDA_CHECK(cudaMemsetAsync(h->d_scal.p, 0, 2 * kScal * sizeof(double), st));
+  {
+    const double cap_d = (double)gk_cap;   // pageable: staged before the call returns
+    CUDA_CHECK(cudaMemcpyAsync(h->d_scal.as<double>() + S_GKCAP, &cap_d, sizeof(double),
+                               cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(h->d_scal.as<double>() + kStage + S_GKCAP, &cap_d, sizeof(double),
+                               cudaMemcpyHostToDevice, st));
+  }
 
   const T* P = (const T*)h->d_panels.p;
   double* scal = h->d_scal.as<double>();
@@ -2815,6 +2909,27 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   check_launch("lsqr finish");
   CUDA_CHECK(cudaMemcpyAsync(sc, scal, kStage * sizeof(double), cudaMemcpyDeviceToHost, st));
   stage_end(h, 5);
+  // the Golub-Kahan record and its extreme singular values (B_k, k = it)
+  const int gk_k = std::min(it, gk_cap - 1);
+  h->gk_alpha.assign(gk_k + 1, 0.0);
+  h->gk_beta.assign(gk_k + 1, 0.0);
+  {
+    std::vector<double> rec(2 * (size_t)(gk_k + 1));
+    DevBuf dsv;
+    dsv.alloc(2 * sizeof(double), st);
+    bidiag_extremes(h, scal + 2 * kScal, gk_k, dsv.as<double>());
+    double sv[2];
+    CUDA_CHECK(cudaMemcpyAsync(rec.data(), scal + 2 * kScal, rec.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(sv, dsv.p, sizeof(sv), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    for (int i = 0; i <= gk_k; ++i) {
+      h->gk_alpha[i] = rec[2 * i];
+      h->gk_beta[i] = rec[2 * i + 1];
+    }
+    info->sigma_max = sv[0];
+    info->sigma_min = sv[1];
+  }
   info->status = status;
   info->iterations = it;
   info->residual_norm = sc[S_RNORM];
@@ -3106,6 +3221,10 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
   }
   if (o->method == ELMFB_SOLVE_FCG_GNN) {
     fcg_solve(h, o, info);
+    return;
+  }
+  if (o->method == ELMFB_SOLVE_QR) {
+    qr_solve(h, o, info);
     return;
   }
   if (o->method != ELMFB_SOLVE_LSQR)
