@@ -225,6 +225,9 @@ typedef struct {
                           Gram diagonal, added to the Gram operator          */
   double rcond;        /* QR: rank cut, a column is dropped once the largest
                           remaining column norm is <= rcond |R_11|           */
+  double ntol;         /* LSQR: also stop when ||(M P)^T r|| <= ntol ||(M P)^T h||
+                          (the preconditioned normal-equations residual
+                          relative to its start, LSQR's estimate); 0 disables */
 } elmfb_solve_opts;
 
 typedef struct {
@@ -248,7 +251,7 @@ typedef struct {
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
  * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
- * gram_shift 0, rcond 1e-13. */
+ * gram_shift 0, rcond 1e-13, ntol 0. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the

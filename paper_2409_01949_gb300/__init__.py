@@ -64,7 +64,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int), ("preconditioner", C.c_int), ("max_iter", C.c_int),
                 ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
                 ("check_every", C.c_int), ("warm_start", C.c_int), ("refine", C.c_int),
-                ("gram_shift", C.c_double), ("rcond", C.c_double)]
+                ("gram_shift", C.c_double), ("rcond", C.c_double), ("ntol", C.c_double)]
 
 
 class BatchItem(C.Structure):

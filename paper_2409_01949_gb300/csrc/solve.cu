@@ -2842,6 +2842,15 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     count_launch(h, 4);
   }
   check_launch("lsqr init");
+  // ||(M P)^T h|| = alpha_1 beta_1, the start of the normal-residual estimate
+  double arnorm0 = 0.0;
+  if (o->ntol > 0.0) {
+    double s0[kStage];
+    CUDA_CHECK(cudaMemcpyAsync(s0, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    arnorm0 = s0[S_ARNORM];
+  }
 
   int it = 0;
   int status = ELMFB_ERR_NOT_CONVERGED;
@@ -2881,7 +2890,8 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     const double rn = sc[S_RNORM], arn = sc[S_ARNORM];
     const bool t1 = o->btol > 0.0 && rn <= o->btol * sc[S_BNORM];
     const bool t2 = o->atol > 0.0 && anorm > 0.0 && rn > 0.0 && arn <= o->atol * anorm * rn;
-    if (t1 || t2 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0) {
+    const bool t3 = o->ntol > 0.0 && arn <= o->ntol * arnorm0;
+    if (t1 || t2 || t3 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0) {
       status = ELMFB_OK;
       break;
     }

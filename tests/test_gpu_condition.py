@@ -69,14 +69,17 @@ def test_extreme_singular_values_of_bidiagonal():
 
 def test_condition_estimate_grows_towards_kappa_of_M():
     """On the full-rank 16-column system, kappa(B_k) never exceeds kappa(M)
-    (NumPy SVD of the oracle's M), does not decrease with k, and after 16
-    steps is within 1% of it."""
+    (NumPy SVD of the oracle's M), does not decrease with k, and reaches it
+    (to 1e-6) by k = 64.  Without reorthogonalisation the Lanczos vectors lose
+    orthogonality, so 16 steps are not enough: the oracle's own
+    bidiagonalisation gives kappa(B_16) = 355 and kappa(B_32) = 8491.24 against
+    kappa(M) = 8491.25."""
     P = _small()
     M = OS.assemble(P, fmt="dense")["M"]
     sv = np.linalg.svd(M, compute_uv=False)
     kappa = sv[0] / sv[-1]
     prev = 0.0
-    for k in (2, 4, 8, 16):
+    for k in (2, 4, 8, 16, 32, 64):
         with E.Solver.from_problem(P, precision=E.FP64) as s:
             s.assemble_problem(P)
             info = s.solve(preconditioner=E.PREC_NONE, max_iter=k, atol=0.0, btol=0.0,
@@ -86,7 +89,7 @@ def test_condition_estimate_grows_towards_kappa_of_M():
         assert est <= kappa * (1 + 1e-8)
         assert est >= prev * (1 - 1e-12)
         prev = est
-    assert prev == pytest.approx(kappa, rel=1e-2)
+    assert prev == pytest.approx(kappa, rel=1e-6)
 
 
 def test_qr_rank_and_r11_match_oracle():
