@@ -103,13 +103,31 @@ typedef struct elmfb_ctx* elmfb_t;
  *   seed         SplitMix64 seed of the parameter stream
  *   weight_scale a: every hidden weight and bias is drawn from U(-a, a)
  *   precision    ELMFB_FP64 / ELMFB_FP32 / ELMFB_MIXED / ELMFB_DF32
+ *   n_holes, holes  0 .. ELMFB_MAX_HOLES boxes (lo_x, lo_y, hi_x, hi_y; 1-D:
+ *                lo, -, hi, -) cut out of the domain: every subdomain whose
+ *                centre lies inside a hole is discarded -- strictly between
+ *                its faces, a face on the domain box's boundary counting as
+ *                part of the hole (paper §4.1:
+ *                on the L-shaped domain of §4.4 the subdomains outside the
+ *                domain are discarded).  The remaining subdomains keep their
+ *                order and are renumbered consecutively, so N_Phi = K x (kept
+ *                subdomains); windows are normalised over the kept subdomains
+ *                of a level, and a point no kept subdomain of level l covers
+ *                gets no term from that level.
+ *   ansatz_omega w > 0: hard-constraint ansatz of paper §4.3, the model is
+ *                u~(x) = A(x) u_hat(x), A = prod_i tanh(w (x_i - lo_i))
+ *                tanh(w (hi_i - x_i)), which vanishes on the box boundary; the
+ *                columns of M become Op[A w_j phi_jk] and elmfb_eval returns
+ *                u~.  0: no ansatz.
  * Parameter stream: output i of SplitMix64(seed) is
- * mix(seed + (i+1) * 0x9E3779B97F4A7C15); column q draws outputs
- * q*(dim+1)+p (p < dim: weight p, p = dim: bias); u = (z >> 40) * 2^-24,
- * value = a (2u - 1).  The feature input is (x - mu_j) / sigma_j. */
+ * mix(seed + (i+1) * 0x9E3779B97F4A7C15); column q of the full grid (before
+ * any discarding) draws outputs q*(dim+1)+p (p < dim: weight p, p = dim:
+ * bias); u = (z >> 40) * 2^-24, value = a (2u - 1).  The feature input is
+ * (x - mu_j) / sigma_j. */
 #define ELMFB_MAX_LEVELS 12
 #define ELMFB_MAX_FEATURES 256
 #define ELMFB_MAX_ROWSETS 16
+#define ELMFB_MAX_HOLES 4
 typedef struct {
   int dim;
   double lo[2];
@@ -122,6 +140,9 @@ typedef struct {
   uint64_t seed;
   double weight_scale;
   int precision;
+  int n_holes;
+  double holes[ELMFB_MAX_HOLES][4];
+  double ansatz_omega;
 } elmfb_config;
 
 /* Create a handle on the current CUDA device, bound to `cuda_stream`

@@ -18,8 +18,18 @@ Readings (the paper is silent or ambiguous):
 * the column index of (level l, subdomain j, feature k) is
   q = sum_{m<l} J_m K + j K + k  (§3 "Indexing conventions", 0-based here).
 
+Discarding (§4.1: "we discard rectangular subdomains outside of the L-shaped
+domain", for the L-shaped domain of §4.4): a problem may cut boxes (holes) out
+of its domain; a subdomain is discarded when its centre lies strictly inside a
+hole, a face of the hole that lies on the domain box's boundary counting as
+part of the hole (reading: the paper does not say how "outside" is decided;
+with the baseline's 16 x 16 grid this discards exactly the 8 x 8 subdomains it
+reports, for cell-centred and for end-point centres).  Kept subdomains keep their order and are numbered consecutively;
+their random parameters stay those of their full-grid column.
+
 Parity pinned through the window tests (partition of unity, support) and the
-closed-form column counts in tests/test_oracle_windows.py.
+closed-form column counts in tests/test_oracle_windows.py; discarding by the
+192-subdomain count of §4.4 and the partition of unity over kept subdomains.
 """
 from __future__ import annotations
 
@@ -36,13 +46,17 @@ class Level:
     mu: List[np.ndarray]        # per dimension: centres, shape (n,)
     sigma: List[float]          # per dimension: half-width
     col_offset: int             # first column index of this level
-    n_sub: int                  # J_l = n ** dim
+    n_sub: int                  # J_l = n ** dim (the full grid)
+    keep: np.ndarray = None     # (J_l,) bool: subdomain kept (not in a hole)
+    col_first: np.ndarray = None  # (J_l,) first column of subdomain j, -1 if discarded
+    param_offset: int = 0       # first full-grid column of this level (parameter draws)
 
 
 def build_levels(dim: int, lo, hi, levels, delta: float, K: int,
-                 placement: str = "cell") -> List[Level]:
+                 placement: str = "cell", holes=()) -> List[Level]:
     out = []
     off = 0
+    poff = 0
     for n in levels:
         mus, sigs = [], []
         for i in range(dim):
@@ -60,9 +74,38 @@ def build_levels(dim: int, lo, hi, levels, delta: float, K: int,
                 raise ValueError(f"unknown placement {placement!r}")
             sigs.append(delta * D / 2.0)
         J = n ** dim
-        out.append(Level(n=n, mu=mus, sigma=sigs, col_offset=off, n_sub=J))
-        off += J * K
+        lev = Level(n=n, mu=mus, sigma=sigs, col_offset=off, n_sub=J)
+        keep = np.ones(J, dtype=bool)
+        for j in range(J):
+            ji = subdomain_multi_index(lev, dim, j)
+            centre = [mus[i][ji[i]] for i in range(dim)]
+            for hlo, hhi in holes:
+                if all(_in_hole(centre[i], hlo[i], hhi[i], lo[i], hi[i]) for i in range(dim)):
+                    keep[j] = False
+        lev.keep = keep
+        lev.col_first = np.where(keep, off + (np.cumsum(keep) - 1) * K, -1)
+        lev.param_offset = poff
+        out.append(lev)
+        off += int(keep.sum()) * K
+        poff += J * K
     return out
+
+
+def _in_hole(c: float, hlo: float, hhi: float, lo: float, hi: float) -> bool:
+    """Centre coordinate c inside the hole's extent along one axis: strictly
+    between its faces, a face that lies on the domain box's boundary counting
+    as part of the hole (a centre on the box edge beyond the cut is outside
+    the domain too)."""
+    above = c > hlo or (hlo == lo and c == lo)
+    below = c < hhi or (hhi == hi and c == hi)
+    return above and below
+
+
+def n_columns(problem) -> int:
+    """N_Phi = K x (subdomains kept over all levels)."""
+    levels = build_levels(problem.dim, problem.lo, problem.hi, problem.levels, problem.delta,
+                          problem.features, problem.placement, getattr(problem, "holes", ()))
+    return sum(int(lev.keep.sum()) for lev in levels) * problem.features
 
 
 def subdomain_multi_index(level: Level, dim: int, j: int) -> Tuple[int, ...]:

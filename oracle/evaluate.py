@@ -1,7 +1,8 @@
 """Evaluation of the trained model and the paper's error metric (oracle side).
 
 * ``u_hat``  Eq. ``multilevel_solution``:
-             u_hat(x) = (1/L) sum_l sum_j w_j(x) sum_k a_ljk phi_ljk(x)
+             u_hat(x) = (1/L) sum_l sum_j w_j(x) sum_k a_ljk phi_ljk(x),
+             times A(x) under the hard-constraint ansatz of §4.3
 * ``e_l1``   Eq. ``l1_error``: sum_i |u_hat(x_i) - u(x_i)| / (M * std(u)),
              std taken over the test set with the population convention
              (reading: the paper does not say which).
@@ -16,6 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from .ansatz import ansatz
 from .decomposition import build_levels, subdomain_multi_index
 from .features import features
 from .system import parameters
@@ -26,7 +28,7 @@ def u_hat(problem, a: np.ndarray, X: np.ndarray, params=None, chunk: int = 8192)
     d = problem.dim
     K = problem.features
     levels = build_levels(d, problem.lo, problem.hi, problem.levels, problem.delta, K,
-                          problem.placement)
+                          problem.placement, getattr(problem, "holes", ()))
     L = len(levels)
     W, b = parameters(problem) if params is None else params
     X = np.asarray(X, dtype=np.float64).reshape(-1, d)
@@ -42,10 +44,14 @@ def u_hat(problem, a: np.ndarray, X: np.ndarray, params=None, chunk: int = 8192)
                 ji = subdomain_multi_index(lev, d, int(j))
                 mu = np.array([lev.mu[i][ji[i]] for i in range(d)])
                 sig = np.array(lev.sigma)
-                cols = lev.col_offset + int(j) * K + np.arange(K)
-                phi, _, _, _ = features((Xc[loc] - mu) / sig, W[cols], b[cols], sig)
+                cols = int(lev.col_first[j]) + np.arange(K)
+                pcols = lev.param_offset + int(j) * K + np.arange(K)
+                phi, _, _, _ = features((Xc[loc] - mu) / sig, W[pcols], b[pcols], sig)
                 acc[loc] += win["om"][loc, j] * (phi @ a[cols])
         out[c_start:c_start + chunk] = acc / L
+        an = getattr(problem, "ansatz_omega", 0.0)
+        if an:      # §4.3: the model is A(x) u_hat(x)
+            out[c_start:c_start + chunk] *= ansatz(Xc, problem.lo, problem.hi, an)[0]
     return out
 
 

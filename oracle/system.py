@@ -21,6 +21,8 @@ sum_i c2_i d_ii v and v = w phi the product rule gives
 
 Entries are zero outside the support of w_j (§3 "Multilevel
 domain-decomposition structure"), so M is stored sparse (CSR) when large.
+With the hard-constraint ansatz of §4.3 (problem.ansatz_omega > 0) w is
+replaced by A w throughout (oracle/ansatz.py).
 
 Pinned by: the loss identity ||M a - h||^2 = L(a) with the loss of Eq.
 ``multilevel_loss`` evaluated by finite differences of u_hat; the special cases
@@ -36,7 +38,8 @@ from typing import Optional
 import numpy as np
 import scipy.sparse as sp
 
-from .decomposition import build_levels, subdomain_multi_index
+from .ansatz import ansatz, apply_to_window
+from .decomposition import build_levels, n_columns, subdomain_multi_index
 from .features import features
 from .rng import draw_parameters
 from .windows import level_windows, support_mask
@@ -74,8 +77,10 @@ def stack_rows(problem) -> Rows:
 
 
 def parameters(problem, round_to_float32: bool = False):
-    """Fixed random parameters W (N_Phi, d), b (N_Phi,) of every column."""
-    W, b = draw_parameters(problem.seed, problem.n_columns, problem.dim, problem.weight_scale)
+    """Fixed random parameters W, b of every column of the full grids (before
+    any subdomain is discarded): row q is full-grid column q."""
+    W, b = draw_parameters(problem.seed, problem.n_columns_full, problem.dim,
+                           problem.weight_scale)
     if round_to_float32:
         W = W.astype(np.float32).astype(np.float64)
         b = b.astype(np.float32).astype(np.float64)
@@ -105,11 +110,11 @@ def assemble(problem, rows: Optional[np.ndarray] = None, fmt: str = "auto",
     R = stack_rows(problem)
     all_rows = np.arange(R.X.shape[0]) if rows is None else np.asarray(rows, dtype=np.int64)
     n_rows = all_rows.shape[0]
-    NPhi = problem.n_columns
+    NPhi = n_columns(problem)
     if fmt == "auto":
         fmt = "dense" if n_rows * NPhi <= 6e7 else "csr"
     levels = build_levels(d, problem.lo, problem.hi, problem.levels, problem.delta, K,
-                          problem.placement)
+                          problem.placement, getattr(problem, "holes", ()))
     L = len(levels)
     W, b = parameters(problem) if params is None else params
 
@@ -121,17 +126,34 @@ def assemble(problem, rows: Optional[np.ndarray] = None, fmt: str = "auto",
         c1 = R.c1[sel]
         c2 = R.c2[sel]
         sc = (R.scale[sel] / L)[:, None]
+        an = getattr(problem, "ansatz_omega", 0.0)
+        if an:
+            A, dA, ddA = ansatz(X, problem.lo, problem.hi, an)
         for lev in levels:
             win = level_windows(X, lev, d, with_abs=with_bound)
             mask = support_mask(X, lev, d)
+            if an:
+                # §4.3: the window factor w becomes g = A w (product rule in A)
+                om_, dom_, ddom_ = apply_to_window(A, dA, ddA, win["om"], win["dom"],
+                                                   win["ddom"])
+                if with_bound:
+                    aA = np.abs(A)
+                    win["dom_abs"], win["ddom_abs"] = (
+                        np.abs(dA)[:, None, :] * win["om"][:, :, None]
+                        + aA[:, None, None] * win["dom_abs"],
+                        np.abs(ddA)[:, None, :] * win["om"][:, :, None]
+                        + 2.0 * np.abs(dA)[:, None, :] * win["dom_abs"]
+                        + aA[:, None, None] * win["ddom_abs"])
+                win["om"], win["dom"], win["ddom"] = om_, dom_, ddom_
             for j in np.nonzero(mask.any(axis=0))[0]:
                 loc = np.nonzero(mask[:, j])[0]
                 ji = subdomain_multi_index(lev, d, int(j))
                 mu = np.array([lev.mu[i][ji[i]] for i in range(d)])
                 sig = np.array(lev.sigma)
                 Z = (X[loc] - mu[None, :]) / sig[None, :]
-                cols = lev.col_offset + int(j) * K + np.arange(K)
-                phi, dphi, ddphi, _ = features(Z, W[cols], b[cols], sig)
+                cols = int(lev.col_first[j]) + np.arange(K)
+                pcols = lev.param_offset + int(j) * K + np.arange(K)
+                phi, dphi, ddphi, _ = features(Z, W[pcols], b[pcols], sig)
                 om = win["om"][loc, j][:, None]
                 val = c0[loc] * om * phi
                 for i in range(d):

@@ -109,6 +109,13 @@ def level_windows(X, level, dim, with_abs=False):
                     dwhat_a[:, :, k] *= fabs[i][:, idx]
                     ddwhat_a[:, :, k] *= fabs[i][:, idx]
 
+    # discarded subdomains (holes, §4.1) take no part in the level's windows
+    if getattr(level, "keep", None) is not None:
+        what = what * level.keep[None, :]
+        dwhat = dwhat * level.keep[None, :, None]
+        ddwhat = ddwhat * level.keep[None, :, None]
+        dwhat_a = dwhat_a * level.keep[None, :, None]
+        ddwhat_a = ddwhat_a * level.keep[None, :, None]
     # level sums (the normalisation of Eq. window_func)
     S = what.sum(axis=1)
     dS = dwhat.sum(axis=1)                  # (n, dim)
@@ -142,4 +149,6 @@ def support_mask(X, level, dim):
         inside = np.abs(X[:, i:i + 1] - level.mu[i][None, :]) < level.sigma[i]
         idx = (np.arange(J) // (n ** i)) % n
         m &= inside[:, idx]
+    if getattr(level, "keep", None) is not None:
+        m &= level.keep[None, :]
     return m

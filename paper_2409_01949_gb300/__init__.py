@@ -28,6 +28,7 @@ SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN, SOLVE_QR = 0, 1, 2, 3
 PREC_NONE, PREC_BLOCK_JACOBI, PREC_BJ_GNN = 0, 1, 2
 MAX_LEVELS = 12
 MAX_ROWSETS = 16
+MAX_HOLES = 4
 N_STAGES = 8
 STAGE_NAMES = ["create", "cell_sort", "assemble", "gram", "precond_setup", "iterate", "eval",
                "assemble_total"]
@@ -43,7 +44,8 @@ class Config(C.Structure):
     _fields_ = [("dim", C.c_int), ("lo", C.c_double * 2), ("hi", C.c_double * 2),
                 ("n_levels", C.c_int), ("levels", C.c_int * MAX_LEVELS), ("delta", C.c_double),
                 ("placement", C.c_int), ("features", C.c_int), ("seed", C.c_uint64),
-                ("weight_scale", C.c_double), ("precision", C.c_int)]
+                ("weight_scale", C.c_double), ("precision", C.c_int), ("n_holes", C.c_int),
+                ("holes", (C.c_double * 4) * MAX_HOLES), ("ansatz_omega", C.c_double)]
 
 
 class RowSet(C.Structure):
@@ -176,8 +178,19 @@ def default_solve_opts(**kw) -> SolveOpts:
     return o
 
 
+def _set_holes(cfg, dim, holes):
+    holes = list(holes or ())
+    if len(holes) > MAX_HOLES:
+        raise ValueError("too many holes")
+    cfg.n_holes = len(holes)
+    for k, (lo, hi) in enumerate(holes):
+        for i in range(dim):
+            cfg.holes[k][i] = float(lo[i])
+            cfg.holes[k][2 + i] = float(hi[i])
+
+
 def make_config(dim, lo, hi, levels, delta, features, seed=0, weight_scale=1.0, precision=FP64,
-                placement=PLACE_CELL) -> Config:
+                placement=PLACE_CELL, holes=(), ansatz_omega=0.0) -> Config:
     cfg = Config()
     cfg.dim = dim
     for i in range(dim):
@@ -194,13 +207,16 @@ def make_config(dim, lo, hi, levels, delta, features, seed=0, weight_scale=1.0, 
     cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     cfg.weight_scale = float(weight_scale)
     cfg.precision = int(precision)
+    _set_holes(cfg, dim, holes)
+    cfg.ansatz_omega = float(ansatz_omega)
     return cfg
 
 
 def config_of(problem, precision=FP64) -> Config:
     place = PLACE_CELL if problem.placement == "cell" else PLACE_ENDPOINT
     return make_config(problem.dim, problem.lo, problem.hi, problem.levels, problem.delta,
-                       problem.features, problem.seed, problem.weight_scale, precision, place)
+                       problem.features, problem.seed, problem.weight_scale, precision, place,
+                       getattr(problem, "holes", ()), getattr(problem, "ansatz_omega", 0.0))
 
 
 def _rowsets(problem, keep):
@@ -270,23 +286,10 @@ class Solver:
 
     def __init__(self, dim, lo, hi, levels: Sequence[int], delta: float, features: int,
                  seed: int = 0, weight_scale: float = 1.0, precision: int = FP64,
-                 placement: int = PLACE_CELL, stream: Optional[int] = None):
-        cfg = Config()
-        cfg.dim = dim
-        for i in range(dim):
-            cfg.lo[i] = float(lo[i])
-            cfg.hi[i] = float(hi[i])
-        if len(levels) > MAX_LEVELS:
-            raise ValueError("too many levels")
-        cfg.n_levels = len(levels)
-        for i, n in enumerate(levels):
-            cfg.levels[i] = int(n)
-        cfg.delta = float(delta)
-        cfg.placement = int(placement)
-        cfg.features = int(features)
-        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
-        cfg.weight_scale = float(weight_scale)
-        cfg.precision = int(precision)
+                 placement: int = PLACE_CELL, stream: Optional[int] = None, holes=(),
+                 ansatz_omega: float = 0.0):
+        cfg = make_config(dim, lo, hi, levels, delta, features, seed, weight_scale, precision,
+                          placement, holes, ansatz_omega)
         self.h = C.c_void_p()
         self._keep = []
         _check(None, lib().elmfb_create(C.byref(self.h), C.byref(cfg), C.c_void_p(stream or 0)))
@@ -296,7 +299,8 @@ class Solver:
     def from_problem(cls, problem, precision=FP64, stream=None):
         place = PLACE_CELL if problem.placement == "cell" else PLACE_ENDPOINT
         return cls(problem.dim, problem.lo, problem.hi, problem.levels, problem.delta,
-                   problem.features, problem.seed, problem.weight_scale, precision, place, stream)
+                   problem.features, problem.seed, problem.weight_scale, precision, place, stream,
+                   getattr(problem, "holes", ()), getattr(problem, "ansatz_omega", 0.0))
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

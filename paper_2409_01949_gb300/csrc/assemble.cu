@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(128) k_assemble(
     const double* __restrict__ xs, const int* __restrict__ rcls,
     const RowClass* __restrict__ c_cls,
     const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels,
-    __nv_bfloat16* __restrict__ pt, int64_t NPR) {
+    __nv_bfloat16* __restrict__ pt, int64_t NPR, const Ansatz an) {
   extern __shared__ __nv_bfloat16 tsm[];   // WRITE_T: per warp [K][32]
   const int lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -355,6 +355,17 @@ __global__ void __launch_bounds__(128) k_assemble(
     const int en = cell_level_off[(int64_t)c * (L + 1) + lev + 1];
     T om, dom[2], ddom[2], xt[2];
     window_at<T>(x, dim, sub, cover_sub, b, en, s, om, dom, ddom, xt);
+    if (an.w > 0.0) {
+      // hard-constraint ansatz (paper §4.3): the window factor becomes
+      // g = A w, with g' = A' w + A w' and g'' = A'' w + 2 A' w' + A w''
+      double Aa, dA[2], ddA[2];
+      ansatz_at(an, x, dim, Aa, dA, ddA);
+      for (int i = 0; i < 2; ++i) {
+        ddom[i] = (T)ddA[i] * om + T(2) * (T)dA[i] * dom[i] + (T)Aa * ddom[i];
+        dom[i] = (T)dA[i] * om + (T)Aa * dom[i];
+      }
+      om = (T)Aa * om;
+    }
     const RowClass rc = c_cls[rcls[R]];
     const T sc = (T)rc.scale;
     A = sc * ((T)rc.c0 * om + (T)rc.c1[0] * dom[0] + (T)rc.c2[0] * ddom[0] +
@@ -442,6 +453,7 @@ void launch_assemble(elmfb_ctx* h) {
   const bool wt = h->cfg.precision == ELMFB_MIXED && sizeof(T) == 4;
   const bool split = h->df32() && sizeof(T) == 8;
   const size_t tsm = wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0;
+  const Ansatz an = make_ansatz(h->cfg);
 #define ELMFB_K1(F)                                                                          \
   case F:                                                                                    \
     if (wt)                                                                                  \
@@ -452,7 +464,7 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
           h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p,             \
-          h->d_pt.as<__nv_bfloat16>(), h->NPR);                                              \
+          h->d_pt.as<__nv_bfloat16>(), h->NPR, an);                                          \
     else if (split)                                                                          \
       k_assemble<T, F, false, true><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(         \
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
@@ -461,7 +473,7 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
           h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
-          h->NPR);                                                                           \
+          h->NPR, an);                                                                       \
     else                                                                                     \
       k_assemble<T, F, false, false><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(        \
           h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
@@ -470,7 +482,7 @@ void launch_assemble(elmfb_ctx* h) {
           h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
           h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
           h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
-          h->NPR);                                                                           \
+          h->NPR, an);                                                                       \
     break;
   // algorithmic bytes: every panel entry written once (twice in mixed precision:
   // FP32 row-major and BF16 feature-major), point data read once

@@ -48,6 +48,90 @@ int guarded(elmfb_ctx* h, F&& f) {
   }
 }
 
+// Drop every subdomain whose centre lies inside a hole box (strictly between
+// its faces, a face on the domain box's boundary counting as part of the
+// hole; paper §4.1, the L-shaped domain of §4.4) and renumber the rest in
+// order: the
+// geometry, the parameters (drawn for the full grid, so that a kept column
+// keeps its draw), the cell ranges and the covering lists are compacted.
+void discard_in_holes(elmfb_ctx* h) {
+  const elmfb_config& c = h->cfg;
+  const int nfull = h->n_sub;
+  std::vector<int> map(nfull, -1);
+  int kept = 0;
+  for (int s = 0; s < nfull; ++s) {
+    bool in_hole = false;
+    for (int k = 0; k < c.n_holes && !in_hole; ++k) {
+      bool inside = true;
+      for (int i = 0; i < h->dim; ++i) {
+        // strictly between the hole's faces; a face on the domain box's
+        // boundary belongs to the hole
+        const double m = h->sub[s].mu[i], hl = c.holes[k][i], hh = c.holes[k][2 + i];
+        const bool above = m > hl || (hl == c.lo[i] && m == c.lo[i]);
+        const bool below = m < hh || (hh == c.hi[i] && m == c.hi[i]);
+        inside = inside && above && below;
+      }
+      in_hole = inside;
+    }
+    if (!in_hole) map[s] = kept++;
+  }
+  if (kept == 0) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "every subdomain lies inside a hole");
+  const int K = h->K, d = h->dim;
+  std::vector<SubGeom> sub(kept);
+  std::vector<double> W((size_t)kept * K * d), B((size_t)kept * K);
+  std::vector<int> c0[2], c1[2];
+  for (int i = 0; i < 2; ++i) {
+    c0[i].resize(kept);
+    c1[i].resize(kept);
+  }
+  std::vector<int> lev_off(h->L + 1, 0);
+  for (int s = 0; s < nfull; ++s) {
+    const int t = map[s];
+    if (t < 0) continue;
+    sub[t] = h->sub[s];
+    lev_off[h->sub[s].level + 1]++;
+    for (int k = 0; k < K; ++k) {
+      for (int p = 0; p < d; ++p)
+        W[((size_t)t * K + k) * d + p] = h->Wh[((size_t)s * K + k) * d + p];
+      B[(size_t)t * K + k] = h->bh[(size_t)s * K + k];
+    }
+    for (int i = 0; i < 2; ++i) {
+      c0[i][t] = h->sub_c0[i][s];
+      c1[i][t] = h->sub_c1[i][s];
+    }
+  }
+  for (int l = 0; l < h->L; ++l) lev_off[l + 1] += lev_off[l];
+  std::vector<int> cover_off(h->n_cells + 1, 0), cover_sub;
+  std::vector<int> cell_level_off((size_t)h->n_cells * (h->L + 1), 0);
+  int max_cover = 0;
+  for (int cell = 0; cell < h->n_cells; ++cell) {
+    cover_off[cell] = (int)cover_sub.size();
+    for (int l = 0; l <= h->L; ++l) {
+      const size_t li = (size_t)cell * (h->L + 1) + l;
+      cell_level_off[li] = (int)cover_sub.size();
+      if (l == h->L) break;
+      for (int e = h->cell_level_off[li]; e < h->cell_level_off[li + 1]; ++e)
+        if (map[h->cover_sub[e]] >= 0) cover_sub.push_back(map[h->cover_sub[e]]);
+    }
+    max_cover = std::max(max_cover, (int)cover_sub.size() - cover_off[cell]);
+  }
+  cover_off[h->n_cells] = (int)cover_sub.size();
+  h->sub.swap(sub);
+  h->Wh.swap(W);
+  h->bh.swap(B);
+  for (int i = 0; i < 2; ++i) {
+    h->sub_c0[i].swap(c0[i]);
+    h->sub_c1[i].swap(c1[i]);
+  }
+  h->lev_sub_off.swap(lev_off);
+  h->cover_off.swap(cover_off);
+  h->cover_sub.swap(cover_sub);
+  h->cell_level_off.swap(cell_level_off);
+  h->max_cover = max_cover;
+  h->n_sub = kept;
+  h->NPhi = (int64_t)kept * K;
+}
+
 void build_geometry(elmfb_ctx* h) {
   const elmfb_config& c = h->cfg;
   h->dim = c.dim;
@@ -220,6 +304,7 @@ void build_geometry(elmfb_ctx* h) {
       h->max_cover = std::max(h->max_cover, (int)h->cover_sub.size() - h->cover_off[cell]);
     }
   h->cover_off[h->n_cells] = (int)h->cover_sub.size();
+  if (c.n_holes > 0) discard_in_holes(h);
   h->entry_cell.resize(h->cover_sub.size());
   for (int cell = 0; cell < h->n_cells; ++cell)
     for (int e = h->cover_off[cell]; e < h->cover_off[cell + 1]; ++e) h->entry_cell[e] = cell;
@@ -369,6 +454,8 @@ int elmfb_create(elmfb_t* out, const elmfb_config* cfg, void* cuda_stream) {
     return ELMFB_ERR_INVALID_ARG;
   for (int i = 0; i < c.dim; ++i)
     if (!(c.hi[i] > c.lo[i])) return ELMFB_ERR_INVALID_ARG;
+  if (c.n_holes < 0 || c.n_holes > ELMFB_MAX_HOLES || !(c.ansatz_omega >= 0.0))
+    return ELMFB_ERR_INVALID_ARG;
   int64_t nsub = 0;
   for (int l = 0; l < c.n_levels; ++l) {
     if (c.levels[l] < 1 || c.levels[l] > 4096) return ELMFB_ERR_INVALID_ARG;

@@ -84,6 +84,41 @@ struct SubGeom {
   int pad_;
 };
 
+// Hard-constraint ansatz of paper §4.3: A(x) = prod_i tanh(w (x_i - lo_i))
+// tanh(w (hi_i - x_i)) and its first and second derivative along each axis
+// (FP64); w = 0 means no ansatz (A = 1).
+struct Ansatz {
+  double w;
+  double lo[2], hi[2];
+};
+__host__ __device__ inline Ansatz make_ansatz(const elmfb_config& c) {
+  Ansatz a{c.ansatz_omega, {c.lo[0], c.dim > 1 ? c.lo[1] : 0.0},
+           {c.hi[0], c.dim > 1 ? c.hi[1] : 1.0}};
+  return a;
+}
+__device__ __forceinline__ void ansatz_at(const Ansatz& an, const double* x, int dim, double& A,
+                                          double dA[2], double ddA[2]) {
+  double f[2] = {1.0, 1.0}, fp[2] = {0.0, 0.0}, fpp[2] = {0.0, 0.0};
+  for (int i = 0; i < dim; ++i) {
+    // a = tanh(w (x - lo)), b = tanh(w (hi - x)); (ab)' = a'b + ab', (ab)'' =
+    // a''b + 2a'b' + ab'' with a' = w (1 - a^2), a'' = -2 w^2 a (1 - a^2) and
+    // b' = -w (1 - b^2), b'' = -2 w^2 b (1 - b^2)
+    const double a = tanh(an.w * (x[i] - an.lo[i]));
+    const double b = tanh(an.w * (an.hi[i] - x[i]));
+    const double ta = 1.0 - a * a, tb = 1.0 - b * b;
+    const double a1 = an.w * ta, b1 = -an.w * tb;
+    const double a2 = -2.0 * an.w * an.w * a * ta, b2 = -2.0 * an.w * an.w * b * tb;
+    f[i] = a * b;
+    fp[i] = a1 * b + a * b1;
+    fpp[i] = a2 * b + 2.0 * a1 * b1 + a * b2;
+  }
+  A = f[0] * f[1];
+  dA[0] = fp[0] * f[1];
+  dA[1] = f[0] * fp[1];
+  ddA[0] = fpp[0] * f[1];
+  ddA[1] = f[0] * fpp[1];
+}
+
 struct Stage {
   cudaEvent_t a = nullptr, b = nullptr;
 };

@@ -33,6 +33,14 @@ __device__ __forceinline__ double factor(double dx, double sigma, double inv_sig
   return 4.0 * c2 * c2;
 }
 
+// the hard-constraint factor A(x) of paper §4.3 (1 without the ansatz)
+__device__ __forceinline__ double ansatz_value(const Ansatz& an, const double* x, int dim) {
+  if (!(an.w > 0.0)) return 1.0;
+  double A, dA[2], ddA[2];
+  ansatz_at(an, x, dim, A, dA, ddA);
+  return A;
+}
+
 __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ xs, int64_t n, int dim,
                                               int K, int L, const double* __restrict__ bnd,
                                               int nc0, int nc1, const SubGeom* __restrict__ sub,
@@ -41,7 +49,7 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ xs, int
                                               const double* __restrict__ W,
                                               const double* __restrict__ B,
                                               const double* __restrict__ a,
-                                              double* __restrict__ out) {
+                                              double* __restrict__ out, const Ansatz an) {
   const int lane = threadIdx.x & 31;
   const int64_t pt = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (pt >= n) return;
@@ -100,7 +108,7 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ xs, int
       }
     }
     const double total = warp_sum_d(acc);
-    if (lane == 0) out[pt] = total / L;
+    if (lane == 0) out[pt] = total / L * ansatz_value(an, x, dim);
     return;
   }
   double total = 0.0;   // more than 32 covering subdomains: entry by entry
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(256) k_eval(const double* __restrict__ xs, int
       total += (w / S) * part;
     }
   }
-  if (lane == 0) out[pt] = total / L;
+  if (lane == 0) out[pt] = total / L * ansatz_value(an, x, dim);
 }
 
 // pass 1: sum u, sum |d|, sum d^2, sum u^2, max |d|  (per block)
@@ -208,7 +216,8 @@ void eval_model(elmfb_ctx* h, const double* xs, int64_t n, double* out) {
   k_eval<<<(unsigned)ceil_div(threads, 256), 256, 0, st>>>(
       dx.as<double>(), n, h->dim, h->K, h->L, h->d_bnd.as<double>(), h->nc[0], h->nc[1],
       h->d_sub.as<SubGeom>(), h->d_cell_level_off.as<int>(), h->d_cover_sub.as<int>(),
-      h->d_W64.as<double>(), h->d_b64.as<double>(), h->d_a.as<double>(), dout.as<double>());
+      h->d_W64.as<double>(), h->d_b64.as<double>(), h->d_a.as<double>(), dout.as<double>(),
+      make_ansatz(h->cfg));
   check_launch("k_eval");
   count_launch(h);
   CUDA_CHECK(cudaMemcpyAsync(out, dout.p, n * sizeof(double), cudaMemcpyDefault, st));

@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 import workloads as WL  # noqa: E402
+from oracle import decomposition as OD  # noqa: E402
 from oracle import evaluate as OE  # noqa: E402
 from oracle import lstsq as OL  # noqa: E402
 from oracle import system as OS  # noqa: E402
@@ -48,6 +49,10 @@ WORKLOADS = {
                                                    n_boundary_side=60), True),
     "dho_L1-64_K96_N20000": (WL.config_dho_ml, True),
     "poisson2d_L1-16_K128_N400": (WL.config_poisson2d_ml, False),
+    # §4.4 baseline: Helmholtz on the L-shaped domain, 16^2 - 8^2 subdomains
+    "helmholtz_L_w8_J16_K16": (WL.helmholtz_lshape, True),
+    # §4.3 baseline: multi-scale Laplace with the hard-constraint ansatz
+    "laplace_n4_J16_K16": (WL.laplace_multiscale, True),
 }
 
 
@@ -57,7 +62,7 @@ def run(name, only=None, old=None):
     X = P.test_points
     u = P.exact(X)
     rec = dict(old or {})
-    rec.update({"name": name, "n_rows": P.n_rows, "n_columns": P.n_columns})
+    rec.update({"name": name, "n_rows": P.n_rows, "n_columns": OD.n_columns(P)})
     t = time.time()
     out = OS.assemble(P, fmt="dense" if dense_ok else "csr")
     rec["assemble_s"] = time.time() - t

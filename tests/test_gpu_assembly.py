@@ -15,6 +15,7 @@ import pytest
 
 import paper_2409_01949_gb300 as E
 import workloads as WL
+from oracle import decomposition as OD
 from oracle import rng as OR
 from oracle import system as OS
 
@@ -35,6 +36,16 @@ SMALL = {
     "poisson2d_ragged_K33": (lambda: WL.poisson2d(levels=(1, 3, 7), features=33, n_side=37,
                                                   n_boundary_side=11),
                             [E.FP64, E.FP32, E.DF32]),
+    # §4.4: the L-shaped domain, subdomains of the cut-out square discarded
+    "helmholtz_L_w8_J16_K16": (WL.helmholtz_lshape, [E.FP64, E.FP32, E.DF32]),
+    "helmholtz_L_J1-8-16_K12_endpoint": (
+        lambda: WL.helmholtz_lshape(levels=(1, 8, 16), features=12, n_grid=40, n_long=40,
+                                    n_short=20, placement="endpoint"), [E.FP64, E.DF32]),
+    # §4.3: the hard-constraint ansatz, no boundary rows
+    "laplace_n4_J16_K16": (WL.laplace_multiscale, [E.FP64, E.FP32, E.DF32]),
+    "laplace_n2_J1-4-8_K20_ansatz": (
+        lambda: WL.laplace_multiscale(omegas=(3, 5), levels=(1, 4, 8), features=20, n_grid=30,
+                                      delta=2.0), [E.FP64, E.FP32]),
 }
 
 
@@ -65,7 +76,7 @@ def test_assembly_all_rows(name):
     P = make()
     for prec in precs:
         sz, ratio = _compare(P, prec)
-        assert sz.n_rows == P.n_rows and sz.n_columns == P.n_columns
+        assert sz.n_rows == P.n_rows and sz.n_columns == OD.n_columns(P)
 
 
 def test_stored_entry_count_matches_closed_form():
@@ -90,8 +101,23 @@ def test_parameters_bitwise_equal_to_oracle_stream():
     assert np.array_equal(W, Wo) and np.array_equal(b, bo)
 
 
+def test_discarded_subdomains_keep_their_parameter_draws():
+    """With holes the kept columns carry the draws of their full-grid columns
+    (the oracle's stream restricted to the kept subdomains)."""
+    P = WL.helmholtz_lshape(levels=(1, 4, 8), features=8)
+    levels = OD.build_levels(2, P.lo, P.hi, P.levels, P.delta, P.features, P.placement, P.holes)
+    full = np.concatenate([lev.param_offset + np.arange(lev.n_sub * P.features)
+                           .reshape(lev.n_sub, P.features)[lev.keep].ravel() for lev in levels])
+    with E.Solver.from_problem(P) as s:
+        W, b = s.params()
+        assert s.sizes().n_subdomains == sum(int(l.keep.sum()) for l in levels)
+    Wo, bo = OR.draw_parameters(P.seed, P.n_columns_full, 2, P.weight_scale)
+    assert np.array_equal(W, Wo[full]) and np.array_equal(b, bo[full])
+
+
 @pytest.mark.parametrize("maker,prec", [(WL.config_poisson2d_ml, E.FP32),
-                                        (WL.config_dho_ml, E.FP32)])
+                                        (WL.config_dho_ml, E.FP32),
+                                        (WL.config_poisson2d_large, E.FP32)])
 def test_assembly_full_size_sampled_rows(maker, prec):
     """Full workload sizes, as assembled for the benchmark; rows sampled for the oracle."""
     P = maker()

@@ -131,7 +131,11 @@ _SOLVE_CASES = [
 ]
 
 
-_QR_CASES = _SOLVE_CASES + [("dho_L1-64_K96_N20000", WL.config_dho_ml)]
+_QR_CASES = _SOLVE_CASES + [
+    ("dho_L1-64_K96_N20000", WL.config_dho_ml),
+    ("helmholtz_L_w8_J16_K16", WL.helmholtz_lshape),      # §4.4, L-shaped domain
+    ("laplace_n4_J16_K16", WL.laplace_multiscale),        # §4.3, hard-constraint ansatz
+]
 
 
 @pytest.mark.parametrize("name,make,prec", [(n, m, p) for n, m in _QR_CASES
@@ -210,8 +214,9 @@ def test_qr_rejects_a_dense_matrix_beyond_device_memory():
         assert ei.value.code == E.ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("name,make,prec", [(n, m, p) for n, m in _SOLVE_CASES
-                                            for p in (E.FP64, E.DF32)])
+@pytest.mark.parametrize("name,make,prec", [(n, m, p) for n, m in _SOLVE_CASES + [
+    ("helmholtz_L_w8_J16_K16", WL.helmholtz_lshape),
+    ("laplace_n4_J16_K16", WL.laplace_multiscale)] for p in (E.FP64, E.DF32)])
 def test_block_jacobi_lsqr_meets_paper_protocol_error(name, make, prec):
     g = _golden(name)
     P = make()
@@ -224,6 +229,29 @@ def test_block_jacobi_lsqr_meets_paper_protocol_error(name, make, prec):
           f"{info.solve_ms:.1f} ms); oracle LSQR-15000 {g['lsqr']['rel_l2']:.3e}; "
           f"oracle QR {g.get('qr', {}).get('rel_l2', float('nan')):.3e}")
     assert err["rel_l2"] <= 1.01 * g["lsqr"]["rel_l2"]
+
+
+@pytest.mark.parametrize("make", [
+    lambda: WL.helmholtz_lshape(levels=(1, 8), features=12, n_grid=30, n_long=30, n_short=15),
+    lambda: WL.laplace_multiscale(omegas=(3, 5), levels=(1, 4), features=12, n_grid=20)])
+def test_eval_matches_oracle_u_hat_with_holes_and_ansatz(make):
+    """u_hat of the L-shaped domain (discarded subdomains) and of the
+    hard-constraint ansatz (u~ = A u_hat) at the test points, at the box
+    boundary (where the ansatz vanishes) and at random interior points."""
+    from oracle import decomposition as OD
+    P = make()
+    a = np.random.default_rng(3).standard_normal(OD.n_columns(P))
+    X = np.concatenate([P.test_points, WL.square_boundary_midpoints(5)])
+    if P.holes:
+        X = X[~((X[:, 0] > 0.5) & (X[:, 1] > 0.5))]
+    with E.Solver.from_problem(P, precision=E.FP64) as s:
+        s.set_coeffs(a)
+        uh = s.eval(X)
+    ref = OE.u_hat(P, a, X)
+    assert np.allclose(uh, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    if P.ansatz_omega:
+        nb = WL.square_boundary_midpoints(5).shape[0]
+        assert np.all(uh[-nb:] == 0.0)
 
 
 def test_eval_matches_oracle_u_hat():

@@ -61,14 +61,32 @@ class Problem:
     exact: Callable[[np.ndarray], np.ndarray]
     test_points: np.ndarray     # (m, dim) float64
     placement: str = "cell"     # subdomain centres: "cell" (cell-centred) or "endpoint"
+    # boxes ((lo_x, lo_y), (hi_x, hi_y)) cut out of the domain; subdomains whose
+    # centre lies inside one are discarded (§4.1, the L-shape of §4.4)
+    holes: Tuple = ()
+    # > 0: hard-constraint ansatz u~ = A u_hat, A = prod_i tanh(w (x_i - lo_i))
+    # tanh(w (hi_i - x_i)) (§4.3); the problem then has no boundary rows
+    ansatz_omega: float = 0.0
 
     @property
     def n_rows(self) -> int:
         return self.interior.points.shape[0] + sum(b.points.shape[0] for b in self.boundary)
 
     @property
-    def n_subdomains(self) -> int:
+    def n_subdomains_full(self) -> int:
+        """Subdomains of the full grids, before any are discarded."""
         return sum(n ** self.dim for n in self.levels)
+
+    @property
+    def n_columns_full(self) -> int:
+        return self.features * self.n_subdomains_full
+
+    @property
+    def n_subdomains(self) -> int:
+        if self.holes:
+            raise AttributeError("with holes the count depends on the subdomain centres: "
+                                 "ask the solver (sizes) or the oracle (decomposition)")
+        return self.n_subdomains_full
 
     @property
     def n_columns(self) -> int:
@@ -274,6 +292,89 @@ def batch_instance(spec: BatchSpec, index: int, batch_seed: int = 0) -> Problem:
                      modes=[(1.0, spec.k, spec.k)], lam=(spec.k * math.pi) ** 4,
                      seed=(batch_seed << 20) + index, n_test_side=64,
                      name=f"batch{batch_seed}_{index}")
+
+
+def laplace_multiscale(omegas=(4, 8, 12, 16), levels=(16,), features: int = 16,
+                       delta: float = 2.9, n_grid: int = 80, n_test: int = 96, seed: int = 0,
+                       weight_scale: float = 1.0, placement: str = "cell",
+                       name: str = None) -> Problem:
+    """§4.3 Eq. ``laplace_problem``: -Laplace u = f on [0,1]^2, u = 0 on the
+    boundary, with f of Eq. ``multiscale_laplace_f``,
+    f = (2 / n) sum_i (w_i pi)^2 sin(w_i pi x) sin(w_i pi y), exact solution
+    u = (1 / n) sum_i sin(w_i pi x) sin(w_i pi y); the boundary condition is
+    imposed by the hard-constraint ansatz with w = w_n (the largest frequency),
+    so there are no boundary rows.  Collocation: the midpoints of an n_grid^2
+    grid (80^2 in the baseline); test points: an n_test^2 grid.
+    """
+    n = len(omegas)
+    modes = [(1.0 / n, w, w) for w in omegas]
+    u, f = _sine_modes_2d(modes)
+    xi = grid2d(midpoints(n_grid), midpoints(n_grid))
+    t = np.linspace(0.0, 1.0, n_test)
+    return Problem(
+        name=name or f"laplace_n{n}_J{'-'.join(map(str, levels))}_K{features}",
+        dim=2, lo=(0.0, 0.0), hi=(1.0, 1.0), levels=tuple(levels), delta=delta,
+        features=features, seed=seed, weight_scale=weight_scale,
+        interior=RowSet(xi, 0.0, (0.0, 0.0), (-1.0, -1.0), f(xi)),
+        boundary=[], exact=u, test_points=grid2d(t, t), placement=placement,
+        ansatz_omega=float(max(omegas)))
+
+
+def helmholtz_lshape(omega: float = 8.0, k: float = 1.0, levels=(16,), features: int = 16,
+                     delta: float = 2.9, n_grid: int = 80, n_long: int = 80, n_short: int = 40,
+                     n_test: int = 96, seed: int = 0, weight_scale: float = 1.0,
+                     placement: str = "cell", name: str = None) -> Problem:
+    """§4.4 Eq. ``helmholtz_problem``: Laplace u + k^2 u = f on the L-shaped domain
+    [0,1]^2 minus [0.5,1] x [0.5,1], u = g on its boundary, with the manufactured
+    solution u = sin(w pi x) sin(2 w pi y) + sin(3 w pi x y) (Eq. ``helmholtz_exact``)
+    and f from Eq. ``helmholtz_f``; lambda_bc = 25 w^4 (§4.4 "Physics-informed
+    objective").  Interior points: the midpoints of an n_grid^2 grid over [0,1]^2
+    outside the cut-out square (80^2 - 40^2 = 4800 in the baseline); boundary:
+    midpoints of n_long points on each of the two long segments and n_short on
+    each of the four short ones (320); test points: an n_test^2 grid over
+    [0,1]^2 outside the cut-out square.  Subdomains centred in the cut-out
+    square are discarded (§4.1).
+    """
+    wp = omega * math.pi
+
+    def u(p):
+        p = np.asarray(p)
+        x, y = p[..., 0], p[..., 1]
+        return np.sin(wp * x) * np.sin(2 * wp * y) + np.sin(3 * wp * x * y)
+
+    def f(p):
+        p = np.asarray(p)
+        x, y = p[..., 0], p[..., 1]
+        return (-5.0 * wp ** 2 * np.sin(wp * x) * np.sin(2 * wp * y)
+                - 9.0 * wp ** 2 * (x * x + y * y) * np.sin(3 * wp * x * y)
+                + k * k * (np.sin(wp * x) * np.sin(2 * wp * y) + np.sin(3 * wp * x * y)))
+
+    def outside_cut(P):
+        return ~((P[:, 0] > 0.5) & (P[:, 1] > 0.5))
+
+    g = grid2d(midpoints(n_grid), midpoints(n_grid))
+    xi = g[outside_cut(g)]
+    ml, ms = midpoints(n_long), midpoints(n_short)
+    zl, ol = np.zeros(n_long), np.ones(n_long)
+    zs, os_ = np.zeros(n_short), np.ones(n_short)
+    xb = np.concatenate([
+        np.stack([ml, zl], 1),                     # y = 0, x in (0, 1)
+        np.stack([os_, 0.5 * ms], 1),              # x = 1, y in (0, 0.5)
+        np.stack([1.0 - 0.5 * ms, 0.5 * os_], 1),  # y = 0.5, x in (0.5, 1)
+        np.stack([0.5 * os_, 0.5 + 0.5 * ms], 1),  # x = 0.5, y in (0.5, 1)
+        np.stack([0.5 - 0.5 * ms, os_], 1),        # y = 1, x in (0, 0.5)
+        np.stack([zl, 1.0 - ml], 1),               # x = 0, y in (0, 1)
+    ])
+    t = np.linspace(0.0, 1.0, n_test)
+    gt = grid2d(t, t)
+    return Problem(
+        name=name or f"helmholtz_L_w{omega:g}_J{'-'.join(map(str, levels))}_K{features}",
+        dim=2, lo=(0.0, 0.0), hi=(1.0, 1.0), levels=tuple(levels), delta=delta,
+        features=features, seed=seed, weight_scale=weight_scale,
+        interior=RowSet(xi, k * k, (0.0, 0.0), (1.0, 1.0), f(xi)),
+        boundary=[RowSet(xb, 1.0, (0.0, 0.0), (0.0, 0.0), u(xb), weight=25.0 * omega ** 4)],
+        exact=u, test_points=gt[outside_cut(gt)], placement=placement,
+        holes=(((0.5, 0.5), (1.0, 1.0)),))
 
 
 def dho_paper_baseline(seed: int = 0) -> Problem:
