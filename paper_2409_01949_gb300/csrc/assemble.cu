@@ -235,208 +235,237 @@ __device__ __forceinline__ void tanh_pair(T s, T* phi, T* t) {
   *phi = copysign(p, s);
   *t = T(4) * (e + T(1)) * r * r;
 }
+// FP32 panels: with r = 1 / (e^{2s} + 1), tanh s = 1 - 2 r and 1 - tanh^2 s =
+// 4 r (1 - r), from the hardware exp2 and reciprocal (relative errors below
+// 2^-22).  Their absolute errors in phi and t stay near 1e-7, which the FP32
+// entries' tolerance (1e-6 of the largest term magnitude of their K-feature
+// block) absorbs; e = inf (s > 44) gives r = 0, phi = 1, t = 0, and e = 0
+// gives r = 1, phi = -1, t = 0.
+__device__ __forceinline__ void tanh_pair_fast(float s, float* phi, float* t) {
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(s * 2.8853900817779268f));   // 2 log2(e)
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
+  *phi = fmaf(-2.0f, r, 1.0f);
+  *t = 4.0f * r * (1.0f - r);
+}
 
-// Normalised window of subdomain `own` and its derivatives at one point, from
-// the covering subdomains of its level (list [b, e) of cover_sub).
+// Window factor of one subdomain at one point: w = prod_i f_i(x_i) with
+// f = 4 c^4 (half-angle form, see the file header), its first and second
+// derivative along each axis, and the scaled coordinate xt = (x - mu)/sigma.
+// The support test |x - mu| < sigma and the edge distance are FP64.
 template <class T>
-__device__ __forceinline__ void window_at(const double* x, int dim, const SubGeom* __restrict__ sub,
-                                          const int* __restrict__ cover_sub, int b, int e, int own,
-                                          T& om, T dom[2], T ddom[2], T xt_own[2]) {
-  T S = 0, dS[2] = {0, 0}, ddS[2] = {0, 0};
-  T wo = 0, dwo[2] = {0, 0}, ddwo[2] = {0, 0};
-  xt_own[0] = xt_own[1] = 0;
-  for (int k = b; k < e; ++k) {
-    int t = cover_sub[k];
-    const SubGeom g = sub[t];
-    T f[2], fp[2], fpp[2];
-    for (int i = 0; i < 2; ++i) {
-      f[i] = 1;
+__device__ __forceinline__ void window_factor(const double* x, int dim, const SubGeom& g, T& w,
+                                              T dw[2], T ddw[2], T xt[2]) {
+  T f[2] = {1, 1}, fp[2] = {0, 0}, fpp[2] = {0, 0};
+  xt[0] = xt[1] = 0;
+  for (int i = 0; i < dim; ++i) {
+    const double dx = x[i] - g.mu[i];
+    const double adx = fabs(dx);
+    const T inv_s = sizeof(T) == 8 ? (T)g.inv_sigma_d[i] : (T)g.inv_sigma[i];
+    xt[i] = (T)dx * inv_s;
+    if (adx < g.sigma_d[i]) {
+      // half angle theta/2 = pi xt / 2: (sh, ch) = (sin, cos)(theta/2).  Near the
+      // edge use u = 1 - |xt| = (sigma - |dx|)/sigma formed in FP64, so
+      // ch = sin(pi u / 2) keeps its relative accuracy as ch -> 0.
+      T sh, ch;
+      const double ud = (g.sigma_d[i] - adx) * g.inv_sigma_d[i];
+      if (ud < 0.5) {
+        T su, cu;
+        Math<T>::sincospi(T(0.5) * (T)ud, &su, &cu);
+        ch = su;
+        sh = dx < 0.0 ? -cu : cu;
+      } else {
+        Math<T>::sincospi(T(0.5) * xt[i], &sh, &ch);
+      }
+      const T gg = Math<T>::pi() * inv_s;
+      const T c2 = ch * ch;
+      f[i] = T(4) * c2 * c2;
+      fp[i] = T(-8) * c2 * ch * sh * gg;
+      fpp[i] = T(4) * c2 * (T(3) * sh * sh - c2) * gg * gg;
+    } else {
+      f[i] = 0;
       fp[i] = 0;
       fpp[i] = 0;
     }
-    for (int i = 0; i < dim; ++i) {
-      // support test and edge distance in FP64, exactly as |x - mu| < sigma
-      const double dx = x[i] - g.mu[i];
-      const double adx = fabs(dx);
-      const T inv_s = sizeof(T) == 8 ? (T)g.inv_sigma_d[i] : (T)g.inv_sigma[i];
-      const T xt = (T)dx * inv_s;
-      if (t == own) xt_own[i] = xt;
-      if (adx < g.sigma_d[i]) {
-        // half angle theta/2 = pi xt / 2: (sh, ch) = (sin, cos)(theta/2).  Near the
-        // edge use u = 1 - |xt| = (sigma - |dx|)/sigma formed in FP64, so
-        // ch = sin(pi u / 2) keeps its relative accuracy as ch -> 0.
-        T sh, ch;
-        const double ud = (g.sigma_d[i] - adx) * g.inv_sigma_d[i];
-        if (ud < 0.5) {
-          T su, cu;
-          Math<T>::sincospi(T(0.5) * (T)ud, &su, &cu);
-          ch = su;
-          sh = dx < 0.0 ? -cu : cu;
-        } else {
-          Math<T>::sincospi(T(0.5) * xt, &sh, &ch);
-        }
-        const T gg = Math<T>::pi() * inv_s;
-        const T c2 = ch * ch;
-        f[i] = T(4) * c2 * c2;
-        fp[i] = T(-8) * c2 * ch * sh * gg;
-        fpp[i] = T(4) * c2 * (T(3) * sh * sh - c2) * gg * gg;
-      } else {
-        f[i] = 0;
-        fp[i] = 0;
-        fpp[i] = 0;
-      }
-    }
-    T w = f[0] * f[1];
-    T dw[2], ddw[2];
-    dw[0] = fp[0] * f[1];
-    ddw[0] = fpp[0] * f[1];
-    dw[1] = f[0] * fp[1];
-    ddw[1] = f[0] * fpp[1];
-    S += w;
-    for (int i = 0; i < 2; ++i) {
-      dS[i] += dw[i];
-      ddS[i] += ddw[i];
-    }
-    if (t == own) {
-      wo = w;
-      for (int i = 0; i < 2; ++i) {
-        dwo[i] = dw[i];
-        ddwo[i] = ddw[i];
-      }
-    }
   }
-  T iS = T(1) / S;
-  om = wo * iS;
-  for (int i = 0; i < 2; ++i) {
-    T a = dS[i] * iS;
-    dom[i] = (dwo[i] - wo * a) * iS;
-    ddom[i] = (ddwo[i] - T(2) * dwo[i] * a - wo * ddS[i] * iS + T(2) * wo * a * a) * iS;
-  }
+  w = f[0] * f[1];
+  dw[0] = fp[0] * f[1];
+  ddw[0] = fpp[0] * f[1];
+  dw[1] = f[0] * fp[1];
+  ddw[1] = f[0] * fpp[1];
 }
 
-// SPLIT (T = double): store each entry as an FP32 pair hi + lo (ELMFB_DF32).
+constexpr int kFacVals = 7;   // w, dw[2], ddw[2], xt[2] per (row, covering subdomain)
+
+// K1: one warp per tile (first covering entry e0 of one level's group in one
+// cell, nl entries, 32 rows from p0).  Phase 1: lane = row; the window factors
+// of the level's nl covering subdomains are formed once (kept in the warp's
+// shared memory, each lane reading back only its own column) together with
+// their level sums S, dS, ddS.  Then per covering panel: the normalised window
+// by the quotient rule (and the ansatz factor), the per-row terms A, beta_i,
+// gamma_i, and phase 2, which broadcasts one row at a time while every lane
+// evaluates its own features, so that the K entries of a row are stored
+// contiguously.  SPLIT (T = double): entries stored as FP32 pairs (ELMFB_DF32).
 template <class T, int FPL, bool WRITE_T, bool SPLIT>
 __global__ void __launch_bounds__(128) k_assemble(
-    const int2* __restrict__ tiles, int64_t n_tiles, int dim, int K, int L,
+    const int4* __restrict__ tiles, int64_t n_tiles, int dim, int K, int nl_max,
     const SubGeom* __restrict__ sub, const int* __restrict__ cover_sub,
     const int* __restrict__ cover_start, const int* __restrict__ entry_cell,
-    const int* __restrict__ cell_level_off, const int* __restrict__ cell_count,
-    const int* __restrict__ cell_pstart, const int64_t* __restrict__ panel_off,
-    const int64_t* __restrict__ entry_base, const int* __restrict__ cover_off,
-    const double* __restrict__ xs, const int* __restrict__ rcls,
-    const RowClass* __restrict__ c_cls,
-    const T* __restrict__ W, const T* __restrict__ Bias, T* __restrict__ panels,
-    __nv_bfloat16* __restrict__ pt, int64_t NPR, const Ansatz an) {
-  extern __shared__ __nv_bfloat16 tsm[];   // WRITE_T: per warp [K][32]
-  const int lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int* __restrict__ cell_count, const int* __restrict__ cell_pstart,
+    const int64_t* __restrict__ panel_off, const int64_t* __restrict__ entry_base,
+    const int* __restrict__ cover_off, const double* __restrict__ xs, const int* __restrict__ rcls,
+    const RowClass* __restrict__ c_cls, const T* __restrict__ W, const T* __restrict__ Bias,
+    T* __restrict__ panels, __nv_bfloat16* __restrict__ pt, int64_t NPR, const Ansatz an) {
+  extern __shared__ __align__(16) unsigned char k1_smem[];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wq;
   if (t >= n_tiles) return;
-  const int2 tile = tiles[t];
-  const int e = tile.x, p0 = tile.y;
-  const int c = entry_cell[e];
-  const int s = cover_sub[e];
-  const SubGeom gs = sub[s];
-  const int lev = gs.level;
+  T* fac = reinterpret_cast<T*>(k1_smem) + (size_t)wq * nl_max * kFacVals * 32;
+  __nv_bfloat16* tsm =
+      reinterpret_cast<__nv_bfloat16*>(k1_smem + (size_t)(blockDim.x >> 5) * nl_max * kFacVals *
+                                                     32 * sizeof(T)) +
+      (size_t)wq * K * 32;
+  const int4 tile = tiles[t];
+  const int e0 = tile.x, nl = tile.y, p0 = tile.z;
+  const int c = entry_cell[e0];
   const int cnt = cell_count[c];
   const int pad = cell_pstart[c + 1] - cell_pstart[c];
   const int nrows = min(32, pad - p0);
   const int64_t R0 = cell_pstart[c] + p0;
   // cell-interleaved storage: row p of entry e at element row entry_base[e] + p m_c
   const int64_t rstride = (int64_t)(cover_off[c + 1] - cover_off[c]) * K;
-  T* out = panels + entry_base[e] * (int64_t)K + (int64_t)p0 * rstride;
-
-  // phase 1: lane = row
-  T A = 0, be0 = 0, be1 = 0, ga0 = 0, ga1 = 0, xt0 = 0, xt1 = 0;
   const int p = p0 + lane;
-  if (lane < nrows && p < cnt) {
-    const int64_t R = R0 + lane;
-    double x[2] = {xs[R * dim], dim == 2 ? xs[R * dim + 1] : 0.0};
-    const int b = cell_level_off[(int64_t)c * (L + 1) + lev];
-    const int en = cell_level_off[(int64_t)c * (L + 1) + lev + 1];
-    T om, dom[2], ddom[2], xt[2];
-    window_at<T>(x, dim, sub, cover_sub, b, en, s, om, dom, ddom, xt);
+  const bool valid = lane < nrows && p < cnt;
+  const int64_t R = R0 + lane;
+  double x[2] = {0.0, 0.0};
+  if (valid) {
+    x[0] = xs[R * dim];
+    if (dim == 2) x[1] = xs[R * dim + 1];
+  }
+
+  // phase 1a: the level's window factors and their sums
+  T S = 0, dS[2] = {0, 0}, ddS[2] = {0, 0};
+  for (int k = 0; k < nl; ++k) {
+    T w = 0, dw[2] = {0, 0}, ddw[2] = {0, 0}, xt[2] = {0, 0};
+    if (valid) window_factor<T>(x, dim, sub[cover_sub[e0 + k]], w, dw, ddw, xt);
+    S += w;
+    for (int i = 0; i < 2; ++i) {
+      dS[i] += dw[i];
+      ddS[i] += ddw[i];
+    }
+    T* fk = fac + (size_t)k * kFacVals * 32 + lane;
+    fk[0] = w;
+    fk[32] = dw[0];
+    fk[64] = dw[1];
+    fk[96] = ddw[0];
+    fk[128] = ddw[1];
+    fk[160] = xt[0];
+    fk[192] = xt[1];
+  }
+  const T iS = S > T(0) ? T(1) / S : T(0);
+  RowClass rc{};
+  double Aa = 1.0, dA[2] = {0.0, 0.0}, ddA[2] = {0.0, 0.0};
+  if (valid) {
+    rc = c_cls[rcls[R]];
+    if (an.w > 0.0) ansatz_at(an, x, dim, Aa, dA, ddA);
+  }
+
+  for (int k = 0; k < nl; ++k) {
+    const int e = e0 + k;
+    const int s = cover_sub[e];
+    const SubGeom gs = sub[s];
+    // phase 1b: this panel's normalised window (quotient rule over the level)
+    const T* fk = fac + (size_t)k * kFacVals * 32 + lane;
+    const T wo = fk[0], dwo[2] = {fk[32], fk[64]}, ddwo[2] = {fk[96], fk[128]};
+    T om = wo * iS, dom[2], ddom[2];
+    for (int i = 0; i < 2; ++i) {
+      const T a = dS[i] * iS;
+      dom[i] = (dwo[i] - wo * a) * iS;
+      ddom[i] = (ddwo[i] - T(2) * dwo[i] * a - wo * ddS[i] * iS + T(2) * wo * a * a) * iS;
+    }
     if (an.w > 0.0) {
       // hard-constraint ansatz (paper §4.3): the window factor becomes
       // g = A w, with g' = A' w + A w' and g'' = A'' w + 2 A' w' + A w''
-      double Aa, dA[2], ddA[2];
-      ansatz_at(an, x, dim, Aa, dA, ddA);
       for (int i = 0; i < 2; ++i) {
         ddom[i] = (T)ddA[i] * om + T(2) * (T)dA[i] * dom[i] + (T)Aa * ddom[i];
         dom[i] = (T)dA[i] * om + (T)Aa * dom[i];
       }
       om = (T)Aa * om;
     }
-    const RowClass rc = c_cls[rcls[R]];
-    const T sc = (T)rc.scale;
-    A = sc * ((T)rc.c0 * om + (T)rc.c1[0] * dom[0] + (T)rc.c2[0] * ddom[0] +
-              (T)rc.c1[1] * dom[1] + (T)rc.c2[1] * ddom[1]);
-    be0 = sc * ((T)rc.c1[0] * om + T(2) * (T)rc.c2[0] * dom[0]);
-    be1 = sc * ((T)rc.c1[1] * om + T(2) * (T)rc.c2[1] * dom[1]);
-    ga0 = sc * (T)rc.c2[0] * om;
-    ga1 = sc * (T)rc.c2[1] * om;
-    xt0 = xt[0];
-    xt1 = xt[1];
-  }
-
-  // per-lane feature constants: features k = lane + 32 i
-  T w0[FPL], w1[FPL], bb[FPL], d0[FPL], d1[FPL];
-  const T is0 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[0] : (T)gs.inv_sigma[0];
-  const T is1 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[1] : (T)gs.inv_sigma[1];
-#pragma unroll
-  for (int i = 0; i < FPL; ++i) {
-    int k = lane + 32 * i;
-    if (k < K) {
-      int64_t q = (int64_t)s * K + k;
-      w0[i] = W[q * dim];
-      w1[i] = dim == 2 ? W[q * dim + 1] : T(0);
-      bb[i] = Bias[q];
-    } else {
-      w0[i] = w1[i] = bb[i] = 0;
+    T A = 0, be0 = 0, be1 = 0, ga0 = 0, ga1 = 0;
+    const T xt0 = fk[160], xt1 = fk[192];
+    if (valid) {
+      const T sc = (T)rc.scale;
+      A = sc * ((T)rc.c0 * om + (T)rc.c1[0] * dom[0] + (T)rc.c2[0] * ddom[0] +
+                (T)rc.c1[1] * dom[1] + (T)rc.c2[1] * ddom[1]);
+      be0 = sc * ((T)rc.c1[0] * om + T(2) * (T)rc.c2[0] * dom[0]);
+      be1 = sc * ((T)rc.c1[1] * om + T(2) * (T)rc.c2[1] * dom[1]);
+      ga0 = sc * (T)rc.c2[0] * om;
+      ga1 = sc * (T)rc.c2[1] * om;
     }
-    d0[i] = w0[i] * is0;
-    d1[i] = w1[i] * is1;
-  }
 
-  // phase 2: broadcast one row at a time
-  for (int r = 0; r < nrows; ++r) {
-    const T rA = __shfl_sync(0xffffffffu, A, r);
-    const T rb0 = __shfl_sync(0xffffffffu, be0, r);
-    const T rb1 = __shfl_sync(0xffffffffu, be1, r);
-    const T rg0 = __shfl_sync(0xffffffffu, ga0, r);
-    const T rg1 = __shfl_sync(0xffffffffu, ga1, r);
-    const T rx0 = __shfl_sync(0xffffffffu, xt0, r);
-    const T rx1 = __shfl_sync(0xffffffffu, xt1, r);
-    T* orow = out + (int64_t)r * rstride;
+    // per-lane feature constants: features f = lane + 32 i
+    T w0[FPL], w1[FPL], bb[FPL], d0[FPL], d1[FPL];
+    const T is0 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[0] : (T)gs.inv_sigma[0];
+    const T is1 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[1] : (T)gs.inv_sigma[1];
 #pragma unroll
     for (int i = 0; i < FPL; ++i) {
-      int k = lane + 32 * i;
-      if (k < K) {
-        T sarg = w0[i] * rx0 + w1[i] * rx1 + bb[i];
-        T phi, tt;
-        tanh_pair<T>(sarg, &phi, &tt);
-        T v = phi * rA + tt * (rb0 * d0[i] + rb1 * d1[i]) -
-              T(2) * phi * tt * (rg0 * d0[i] * d0[i] + rg1 * d1[i] * d1[i]);
-        if (SPLIT) {
-          const float hi = __double2float_rn((double)v);
-          reinterpret_cast<float2*>(orow)[k] =
-              make_float2(hi, __double2float_rn((double)v - (double)hi));
-        } else {
-          orow[k] = v;
+      const int f = lane + 32 * i;
+      if (f < K) {
+        const int64_t q = (int64_t)s * K + f;
+        w0[i] = W[q * dim];
+        w1[i] = dim == 2 ? W[q * dim + 1] : T(0);
+        bb[i] = Bias[q];
+      } else {
+        w0[i] = w1[i] = bb[i] = 0;
+      }
+      d0[i] = w0[i] * is0;
+      d1[i] = w1[i] * is1;
+    }
+
+    // phase 2: broadcast one row at a time
+    T* out = panels + entry_base[e] * (int64_t)K + (int64_t)p0 * rstride;
+    if (WRITE_T) __syncwarp();   // the previous panel's BF16 staging has been read
+    for (int r = 0; r < nrows; ++r) {
+      const T rA = __shfl_sync(0xffffffffu, A, r);
+      const T rb0 = __shfl_sync(0xffffffffu, be0, r);
+      const T rb1 = __shfl_sync(0xffffffffu, be1, r);
+      const T rg0 = __shfl_sync(0xffffffffu, ga0, r);
+      const T rg1 = __shfl_sync(0xffffffffu, ga1, r);
+      const T rx0 = __shfl_sync(0xffffffffu, xt0, r);
+      const T rx1 = __shfl_sync(0xffffffffu, xt1, r);
+      T* orow = out + (int64_t)r * rstride;
+#pragma unroll
+      for (int i = 0; i < FPL; ++i) {
+        const int f = lane + 32 * i;
+        if (f < K) {
+          const T sarg = w0[i] * rx0 + w1[i] * rx1 + bb[i];
+          T phi, tt;
+          if constexpr (sizeof(T) == 4) tanh_pair_fast(sarg, &phi, &tt);
+          else tanh_pair<T>(sarg, &phi, &tt);
+          const T v = phi * rA + tt * (rb0 * d0[i] + rb1 * d1[i]) -
+                      T(2) * phi * tt * (rg0 * d0[i] * d0[i] + rg1 * d1[i] * d1[i]);
+          if (SPLIT) {
+            const float hi = __double2float_rn((double)v);
+            reinterpret_cast<float2*>(orow)[f] =
+                make_float2(hi, __double2float_rn((double)v - (double)hi));
+          } else {
+            orow[f] = v;
+          }
+          if (WRITE_T) tsm[(size_t)f * 32 + r] = __float2bfloat16_rn((float)v);
         }
-        if (WRITE_T) tsm[((threadIdx.x >> 5) * K + k) * 32 + r] = __float2bfloat16_rn((float)v);
       }
     }
-  }
-  if (WRITE_T) {
-    // feature-major BF16 copy: feature k, rows rho0 .. rho0+nrows in 16-byte pieces
-    __syncwarp();
-    const __nv_bfloat16* wt = tsm + (threadIdx.x >> 5) * K * 32;
-    const int64_t rho0 = panel_off[s] + cover_start[e] + p0;
-    const int pieces = nrows / 8;   // nrows is 16 or 32
-    for (int idx = lane; idx < K * pieces; idx += 32) {
-      const int k = idx / pieces, q = idx - k * pieces;
-      const uint4 val = *reinterpret_cast<const uint4*>(wt + k * 32 + q * 8);
-      *reinterpret_cast<uint4*>(pt + (int64_t)k * NPR + rho0 + q * 8) = val;
+    if (WRITE_T) {
+      // feature-major BF16 copy: feature f, rows rho0 .. rho0+nrows in 16-byte pieces
+      __syncwarp();
+      const int64_t rho0 = panel_off[s] + cover_start[e] + p0;
+      const int pieces = nrows / 8;   // nrows is 16 or 32
+      for (int idx = lane; idx < K * pieces; idx += 32) {
+        const int f = idx / pieces, q = idx - f * pieces;
+        const uint4 val = *reinterpret_cast<const uint4*>(tsm + (size_t)f * 32 + q * 8);
+        *reinterpret_cast<uint4*>(pt + (int64_t)f * NPR + rho0 + q * 8) = val;
+      }
     }
   }
 }
@@ -446,58 +475,51 @@ void launch_assemble(elmfb_ctx* h) {
   const int K = h->K;
   const int fpl = (K + 31) / 32;
   const int warps = 4;
-  const int64_t blocks = ceil_div(h->n_tiles, warps);
+  const int64_t blocks = ceil_div(h->n_ltiles, warps);
   if (blocks == 0) return;
   const T* W = sizeof(T) == 8 ? (const T*)h->d_W64.p : (const T*)h->d_W32.p;
   const T* B = sizeof(T) == 8 ? (const T*)h->d_b64.p : (const T*)h->d_b32.p;
   const bool wt = h->cfg.precision == ELMFB_MIXED && sizeof(T) == 4;
   const bool split = h->df32() && sizeof(T) == 8;
-  const size_t tsm = wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0;
+  const size_t smem = (size_t)warps * h->nl_max * kFacVals * 32 * sizeof(T) +
+                      (wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0);
+  if (wt && K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "mixed precision supports K <= 128");
+  if (smem > 220 * 1024)
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "assembly: too many covering subdomains per level");
   const Ansatz an = make_ansatz(h->cfg);
+#define ELMFB_K1_ARGS                                                                        \
+  h->d_ltiles.as<int4>(), h->n_ltiles, h->dim, K, h->nl_max, h->d_sub.as<SubGeom>(),         \
+      h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),       \
+      h->d_cell_count.as<int>(), h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),   \
+      h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),          \
+      h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p
 #define ELMFB_K1(F)                                                                          \
   case F:                                                                                    \
-    if (wt)                                                                                  \
-      k_assemble<T, F, true, false><<<(unsigned)blocks, warps * 32, tsm, h->stream>>>(       \
-          h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
-          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
-          h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
-          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
-          h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
-          h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p,             \
-          h->d_pt.as<__nv_bfloat16>(), h->NPR, an);                                          \
-    else if (split)                                                                          \
-      k_assemble<T, F, false, true><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(         \
-          h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
-          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
-          h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
-          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
-          h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
-          h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
-          h->NPR, an);                                                                       \
-    else                                                                                     \
-      k_assemble<T, F, false, false><<<(unsigned)blocks, warps * 32, 0, h->stream>>>(        \
-          h->d_tiles.as<int2>(), h->n_tiles, h->dim, K, h->L, h->d_sub.as<SubGeom>(),        \
-          h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),   \
-          h->d_cell_level_off.as<int>(), h->d_cell_count.as<int>(),                          \
-          h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),                          \
-          h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),      \
-          h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p, nullptr,     \
-          h->NPR, an);                                                                       \
+    if (wt) {                                                                                \
+      ensure_dyn_smem((const void*)k_assemble<T, F, true, false>, smem);                     \
+      k_assemble<T, F, true, false><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(      \
+          ELMFB_K1_ARGS, h->d_pt.as<__nv_bfloat16>(), h->NPR, an);                           \
+    } else if (split) {                                                                      \
+      ensure_dyn_smem((const void*)k_assemble<T, F, false, true>, smem);                     \
+      k_assemble<T, F, false, true><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(      \
+          ELMFB_K1_ARGS, nullptr, h->NPR, an);                                               \
+    } else {                                                                                 \
+      ensure_dyn_smem((const void*)k_assemble<T, F, false, false>, smem);                    \
+      k_assemble<T, F, false, false><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(     \
+          ELMFB_K1_ARGS, nullptr, h->NPR, an);                                               \
+    }                                                                                        \
     break;
   // algorithmic bytes: every panel entry written once (twice in mixed precision:
   // FP32 row-major and BF16 feature-major), point data read once
   prof_begin(h, KID_ASSEMBLE,
              (double)h->NPR * K * (sizeof(T) + (wt ? 2.0 : 0.0)) +
                  (double)h->NR * (h->dim * 8.0 + 4.0));
-  if (tsm > 48 * 1024) {
-    if (wt)
-      ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "mixed precision supports K <= 128");
-  }
   switch (fpl) {
     ELMFB_K1(1) ELMFB_K1(2) ELMFB_K1(3) ELMFB_K1(4) ELMFB_K1(5) ELMFB_K1(6) ELMFB_K1(7) ELMFB_K1(8)
     default: ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "features > 256");
   }
 #undef ELMFB_K1
+#undef ELMFB_K1_ARGS
   prof_end(h, KID_ASSEMBLE);
   check_launch("k_assemble");
   count_launch(h);
@@ -656,6 +678,20 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
     for (int p = 0; p < pad; p += 32) tiles.push_back(make_int2(e, p));
   }
   h->n_tiles = (int64_t)tiles.size();
+  // assembly tiles: one per (cell, level group of covering entries, 32 rows)
+  std::vector<int4> ltiles;
+  h->nl_max = 1;
+  for (int c = 0; c < nc; ++c) {
+    const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
+    for (int l = 0; l < h->L; ++l) {
+      const int b = h->cell_level_off[(size_t)c * (h->L + 1) + l];
+      const int en = h->cell_level_off[(size_t)c * (h->L + 1) + l + 1];
+      if (en <= b) continue;
+      h->nl_max = std::max(h->nl_max, en - b);
+      for (int p = 0; p < pad; p += 32) ltiles.push_back(make_int4(b, en - b, p, 0));
+    }
+  }
+  h->n_ltiles = (int64_t)ltiles.size();
   // Gram pair count: subdomain pairs (i <= j) that share a cell with points,
   // and the algorithmic Gram flops 2 K^2 per shared row and pair
   h->gram_flops = 0.0;
@@ -675,6 +711,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   up(h->d_cell_eoff, h->cell_eoff.data(), (nc + 1) * sizeof(int64_t));
   up(h->d_entry_base, h->entry_base.data(), ne * sizeof(int64_t));
   up(h->d_tiles, tiles.data(), tiles.size() * sizeof(int2));
+  up(h->d_ltiles, ltiles.data(), ltiles.size() * sizeof(int4));
 
   // K0: scatter into cells, deterministic order inside each cell, gather row data
   const int64_t NR = h->NR;

@@ -190,8 +190,11 @@ struct elmfb_ctx {
   std::vector<int64_t> cell_eoff, entry_base;
   DevBuf d_cell_eoff, d_entry_base;
   DevBuf d_panels;      // [NPR*K] FP64, FP32 or FP32 pairs
-  DevBuf d_tiles;       // assembly / transpose-product tiles: (entry, first row)
+  DevBuf d_tiles;       // per-panel tiles: (entry, first row) of 32 rows
   int64_t n_tiles = 0;
+  DevBuf d_ltiles;      // assembly tiles: (first entry of a level group, entries, first row)
+  int64_t n_ltiles = 0;
+  int nl_max = 1;       // most covering entries of one level in one cell
   std::vector<int> entry_cell;   // [n_entries]
   DevBuf d_entry_cell;
   DevBuf d_flags;       // device status flags (int[4])

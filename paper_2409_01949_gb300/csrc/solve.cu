@@ -2599,7 +2599,8 @@ __device__ int gk_sturm_count(const double* __restrict__ gk, int k, double lam, 
 }
 
 // Extreme singular values of B_k by multisection of the Sturm count (one warp,
-// 32 trial points per round; geometric spacing once the interval is off 0):
+// 32 trial points per round; geometric spacing once the interval is off 0;
+// to 1e-10 relative):
 // out[0] = sigma_max (the point where the count reaches 2k+1), out[1] =
 // sigma_min (where it reaches k+2).  k = 0: zeros.
 __global__ void k_bidiag_extremes(const double* __restrict__ gk, int k, double* __restrict__ out) {
@@ -2621,7 +2622,7 @@ __global__ void k_bidiag_extremes(const double* __restrict__ gk, int k, double* 
   for (int which = 0; which < 2; ++which) {
     const int target = which == 0 ? 2 * k + 1 : k + 2;
     double lo = 0.0, hi = bound;
-    for (int round = 0; round < 200 && hi > lo * (1.0 + 4e-16); ++round) {
+    for (int round = 0; round < 200 && hi > lo * (1.0 + 1e-10); ++round) {
       const double f = (double)(lane + 1) / 33.0;
       const double lam = lo > 0.0 ? lo * pow(hi / lo, f) : hi * f;
       const bool below = gk_sturm_count(gk, k, lam, pivmin) < target;
