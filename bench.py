@@ -378,11 +378,44 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clk,
     }
+    if not args.no_gram:
+        line["gram_tc"] = gram_measure(P, stream)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(P, args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def gram_measure(P, stream, reps=3):
+    """The tensor-core Gram blocks (tcgen05, BF16 products, FP32 accumulation
+    in TMEM) of every subdomain pair sharing rows, on the same workload in
+    mixed precision: CUDA events around each launch (untimed for the step),
+    TFLOP/s of the algorithmic 2 K^2 flops per shared row and pair against the
+    measured dense BF16 peak."""
+    import paper_2409_01949_gb300 as E
+    s = E.Solver.from_problem(P, precision=E.MIXED, stream=stream.cuda_stream)
+    try:
+        s.assemble_problem(P)
+        flops = float(s.sizes().gram_flops)
+        s.compute_gram()                       # warm-up (pair lists, TMEM, descriptors)
+        s.set_profiling_only("gram_tc")
+        for _ in range(reps):
+            s.compute_gram()
+        ms, n, by = s.kernel_stats()["gram_tc"]
+    finally:
+        s.close()
+    avg = ms / n
+    tf = flops / (avg * 1e-3) / 1e12
+    peak = None
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peak = json.load(open(pp)).get("bf16_tflops")
+    return {"kernel": "gram_tc", "flops_per_launch": flops, "avg_ms": round(avg, 4),
+            "tflops": round(tf, 1), "peak_bf16_tflops": peak,
+            "frac": round(tf / peak, 4) if peak else None, "launches": n,
+            "note": "BF16 panels, FP32 accumulation; 2 K^2 flops per shared row and subdomain "
+                    "pair (i <= j); measured after the timed steps"}
 
 
 def run_batch(args):
@@ -495,6 +528,8 @@ def main():
                     help="oracle sample: every n-th row (default: about 40k rows)")
     ap.add_argument("--cpu-lsqr-its", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gram", action="store_true",
+                    help="skip the tensor-core Gram measurement after the timed steps")
     ap.add_argument("--roofline-stride", type=int, default=8,
                     help="time every n-th launch of the roofline kernel in the timed steps")
     ap.add_argument("--batch-n", type=int, default=512)

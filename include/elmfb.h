@@ -57,11 +57,18 @@ enum {
   ELMFB_FP64 = 0,   /* panels, Gram and solver vectors in FP64                  */
   ELMFB_FP32 = 1,   /* panels FP32, FP64 solver vectors and reductions          */
   ELMFB_MIXED = 2,  /* FP32 panels + BF16 copy for tensor-core Gram blocks       */
-  ELMFB_DF32 = 3    /* panels as FP32 pairs (hi + lo, ~48-bit significand, same
+  ELMFB_DF32 = 3,   /* panels as FP32 pairs (hi + lo, ~48-bit significand, same
                        8 bytes as FP64), products and sums in float-float
                        arithmetic on the FP32 pipes; entries evaluated in FP64.
                        The solvers need K a multiple of 4, K <= 128 and <= 30
                        covering panels per cell (else UNSUPPORTED)            */
+  ELMFB_FP32_DF32 = 4 /* mixed precision with refinement: FP32 panels for the
+                       iterations plus FP32-pair (ELMFB_DF32) panels of the
+                       same entries (12 bytes per entry) for FP64-accurate
+                       residuals; elmfb_solve's `refine` outer steps of LSQR
+                       each solve min ||M_fp32 d - r|| for r = h - M a formed
+                       from the pair panels, then a += d.  Same limits as
+                       ELMFB_DF32                                             */
 };
 
 /* ---- subdomain centre placement (paper §4.1 "Domain decomposition") -------- */
@@ -102,7 +109,8 @@ typedef struct elmfb_ctx* elmfb_t;
  *   features     K >= 1 random features per subdomain, at most ELMFB_MAX_FEATURES
  *   seed         SplitMix64 seed of the parameter stream
  *   weight_scale a: every hidden weight and bias is drawn from U(-a, a)
- *   precision    ELMFB_FP64 / ELMFB_FP32 / ELMFB_MIXED / ELMFB_DF32
+ *   precision    ELMFB_FP64 / ELMFB_FP32 / ELMFB_MIXED / ELMFB_DF32 /
+ *                ELMFB_FP32_DF32
  *   n_holes, holes  0 .. ELMFB_MAX_HOLES boxes (lo_x, lo_y, hi_x, hi_y; 1-D:
  *                lo, -, hi, -) cut out of the domain: every subdomain whose
  *                centre lies inside a hole is discarded -- strictly between
@@ -239,9 +247,13 @@ typedef struct {
   double shift;        /* Cholesky shift eps: G_jj + eps tr(G_jj)/K I          */
   int check_every;     /* host checks convergence every this many iterations  */
   int warm_start;      /* nonzero: start from the handle's current coefficients */
-  int refine;          /* PCG: outer refinement steps (>= 1); each recomputes
+  int refine;          /* outer refinement steps (>= 1).  PCG: each recomputes
                           g = M^T (h - M a) from the panels and runs max_iter
-                          PCG iterations on the tensor-core Gram for the update */
+                          PCG iterations on the tensor-core Gram for the
+                          update.  LSQR with ELMFB_FP32_DF32 panels: each
+                          forms r = h - M a from the pair panels and runs
+                          LSQR (max_iter, atol/btol/ntol) on the FP32 panels
+                          for the update d of min ||M d - r||            */
   double gram_shift;   /* PCG: Tikhonov shift mu, as a fraction of the mean
                           Gram diagonal, added to the Gram operator          */
   double rcond;        /* QR: rank cut, a column is dropped once the largest

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libelmfb.so")
 # status codes (elmfb.h)
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_BREAKDOWN, \
     ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(10)
-FP64, FP32, MIXED, DF32 = 0, 1, 2, 3
+FP64, FP32, MIXED, DF32, FP32_DF32 = 0, 1, 2, 3, 4
 PLACE_CELL, PLACE_ENDPOINT = 0, 1
 SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN, SOLVE_QR = 0, 1, 2, 3
 PREC_NONE, PREC_BLOCK_JACOBI, PREC_BJ_GNN = 0, 1, 2

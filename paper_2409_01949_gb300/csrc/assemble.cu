@@ -306,7 +306,7 @@ constexpr int kFacVals = 7;   // w, dw[2], ddw[2], xt[2] per (row, covering subd
 // gamma_i, and phase 2, which broadcasts one row at a time while every lane
 // evaluates its own features, so that the K entries of a row are stored
 // contiguously.  SPLIT (T = double): entries stored as FP32 pairs (ELMFB_DF32).
-template <class T, int FPL, bool WRITE_T, bool SPLIT>
+template <class T, int FPL, bool WRITE_T, bool SPLIT, bool kVec>
 __global__ void __launch_bounds__(128) k_assemble(
     const int4* __restrict__ tiles, int64_t n_tiles, int dim, int K, int nl_max,
     const SubGeom* __restrict__ sub, const int* __restrict__ cover_sub,
@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(128) k_assemble(
     const int64_t* __restrict__ panel_off, const int64_t* __restrict__ entry_base,
     const int* __restrict__ cover_off, const double* __restrict__ xs, const int* __restrict__ rcls,
     const RowClass* __restrict__ c_cls, const T* __restrict__ W, const T* __restrict__ Bias,
-    T* __restrict__ panels, __nv_bfloat16* __restrict__ pt, int64_t NPR, const Ansatz an) {
+    T* __restrict__ panels, __nv_bfloat16* __restrict__ pt, int64_t NPR, const Ansatz an,
+    float* __restrict__ panels32) {
   extern __shared__ __align__(16) unsigned char k1_smem[];
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wq;
@@ -325,6 +326,15 @@ __global__ void __launch_bounds__(128) k_assemble(
       reinterpret_cast<__nv_bfloat16*>(k1_smem + (size_t)(blockDim.x >> 5) * nl_max * kFacVals *
                                                      32 * sizeof(T)) +
       (size_t)wq * K * 32;
+  T* rowt = reinterpret_cast<T*>(k1_smem + (size_t)(blockDim.x >> 5) * nl_max * kFacVals * 32 *
+                                                 sizeof(T) +
+                                 (WRITE_T ? (size_t)(blockDim.x >> 5) * K * 32 *
+                                                sizeof(__nv_bfloat16)
+                                          : 0)) +
+            (size_t)wq * 32 * 8;
+  // lanes own consecutive features where a row leaves as vector stores;
+  // elsewhere f = lane + 32 i keeps every scalar store coalesced
+  constexpr bool kConsec = kVec;
   const int4 tile = tiles[t];
   const int e0 = tile.x, nl = tile.y, p0 = tile.z;
   const int c = entry_cell[e0];
@@ -404,13 +414,14 @@ __global__ void __launch_bounds__(128) k_assemble(
       ga1 = sc * (T)rc.c2[1] * om;
     }
 
-    // per-lane feature constants: features f = lane + 32 i
-    T w0[FPL], w1[FPL], bb[FPL], d0[FPL], d1[FPL];
+    // per-lane feature constants: with vector stores lanes own FPL
+    // consecutive features (f = lane FPL + i), else f = lane + 32 i
+    T w0[FPL], w1[FPL], bb[FPL], d0[FPL], d1[FPL], e0[FPL], e1[FPL];
     const T is0 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[0] : (T)gs.inv_sigma[0];
     const T is1 = sizeof(T) == 8 ? (T)gs.inv_sigma_d[1] : (T)gs.inv_sigma[1];
 #pragma unroll
     for (int i = 0; i < FPL; ++i) {
-      const int f = lane + 32 * i;
+      const int f = kConsec ? lane * FPL + i : lane + 32 * i;
       if (f < K) {
         const int64_t q = (int64_t)s * K + f;
         w0[i] = W[q * dim];
@@ -421,38 +432,66 @@ __global__ void __launch_bounds__(128) k_assemble(
       }
       d0[i] = w0[i] * is0;
       d1[i] = w1[i] * is1;
+      e0[i] = d0[i] * d0[i];
+      e1[i] = d1[i] * d1[i];
     }
 
-    // phase 2: broadcast one row at a time
+    // phase 2: the per-row terms go to shared memory, then each row's are
+    // read back by every lane (broadcast) while the lanes form its features:
+    // Op[w phi] = phi A + t (B - 2 phi C), B = sum_i beta_i d_i,
+    // C = sum_i gamma_i d_i^2
     T* out = panels + entry_base[e] * (int64_t)K + (int64_t)p0 * rstride;
-    if (WRITE_T) __syncwarp();   // the previous panel's BF16 staging has been read
+    __syncwarp();   // the previous panel's row terms (and BF16 staging) have been read
+    {
+      T* rt = rowt + lane * 8;
+      rt[0] = A;
+      rt[1] = be0;
+      rt[2] = be1;
+      rt[3] = ga0;
+      rt[4] = ga1;
+      rt[5] = xt0;
+      rt[6] = xt1;
+    }
+    __syncwarp();
     for (int r = 0; r < nrows; ++r) {
-      const T rA = __shfl_sync(0xffffffffu, A, r);
-      const T rb0 = __shfl_sync(0xffffffffu, be0, r);
-      const T rb1 = __shfl_sync(0xffffffffu, be1, r);
-      const T rg0 = __shfl_sync(0xffffffffu, ga0, r);
-      const T rg1 = __shfl_sync(0xffffffffu, ga1, r);
-      const T rx0 = __shfl_sync(0xffffffffu, xt0, r);
-      const T rx1 = __shfl_sync(0xffffffffu, xt1, r);
+      const T* rt = rowt + r * 8;
+      const T rA = rt[0], rb0 = rt[1], rb1 = rt[2], rg0 = rt[3], rg1 = rt[4], rx0 = rt[5],
+              rx1 = rt[6];
       T* orow = out + (int64_t)r * rstride;
+      T vals[FPL];
 #pragma unroll
       for (int i = 0; i < FPL; ++i) {
-        const int f = lane + 32 * i;
-        if (f < K) {
-          const T sarg = w0[i] * rx0 + w1[i] * rx1 + bb[i];
-          T phi, tt;
-          if constexpr (sizeof(T) == 4) tanh_pair_fast(sarg, &phi, &tt);
-          else tanh_pair<T>(sarg, &phi, &tt);
-          const T v = phi * rA + tt * (rb0 * d0[i] + rb1 * d1[i]) -
-                      T(2) * phi * tt * (rg0 * d0[i] * d0[i] + rg1 * d1[i] * d1[i]);
-          if (SPLIT) {
-            const float hi = __double2float_rn((double)v);
-            reinterpret_cast<float2*>(orow)[f] =
-                make_float2(hi, __double2float_rn((double)v - (double)hi));
-          } else {
-            orow[f] = v;
+        const T sarg = w0[i] * rx0 + w1[i] * rx1 + bb[i];
+        T phi, tt;
+        if constexpr (sizeof(T) == 4) tanh_pair_fast(sarg, &phi, &tt);
+        else tanh_pair<T>(sarg, &phi, &tt);
+        const T B = rb0 * d0[i] + rb1 * d1[i];
+        const T Cc = rg0 * e0[i] + rg1 * e1[i];
+        vals[i] = tt * (B - T(2) * phi * Cc) + phi * rA;
+      }
+      if constexpr (kVec) {
+        // K = 32 FPL and FP32 entries: one 8- or 16-byte store per lane
+        if constexpr (FPL == 4)
+          reinterpret_cast<float4*>(orow)[lane] = make_float4(vals[0], vals[1], vals[2], vals[3]);
+        else
+          reinterpret_cast<float2*>(orow)[lane] = make_float2(vals[0], vals[1]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < FPL; ++i) {
+          const int f = kConsec ? lane * FPL + i : lane + 32 * i;
+          if (f < K) {
+            const T v = vals[i];
+            if (SPLIT) {
+              const float hi = __double2float_rn((double)v);
+              reinterpret_cast<float2*>(orow)[f] =
+                  make_float2(hi, __double2float_rn((double)v - (double)hi));
+              // ELMFB_FP32_DF32: the FP32 panels hold the rounded entries
+              if (panels32) panels32[(orow - panels) + f] = hi;
+            } else {
+              orow[f] = v;
+            }
+            if (WRITE_T) tsm[(size_t)f * 32 + r] = __float2bfloat16_rn((float)v);
           }
-          if (WRITE_T) tsm[(size_t)f * 32 + r] = __float2bfloat16_rn((float)v);
         }
       }
     }
@@ -480,9 +519,15 @@ void launch_assemble(elmfb_ctx* h) {
   const T* W = sizeof(T) == 8 ? (const T*)h->d_W64.p : (const T*)h->d_W32.p;
   const T* B = sizeof(T) == 8 ? (const T*)h->d_b64.p : (const T*)h->d_b32.p;
   const bool wt = h->cfg.precision == ELMFB_MIXED && sizeof(T) == 4;
-  const bool split = h->df32() && sizeof(T) == 8;
+  const bool split = (h->df32() || h->dual()) && sizeof(T) == 8;
+  // ELMFB_FP32_DF32: pairs into d_panels_df, their FP32 rounding into d_panels
+  T* const pout = h->dual() ? (T*)h->d_panels_df.p : (T*)h->d_panels.p;
+  float* const p32 = h->dual() && sizeof(T) == 8 ? (float*)h->d_panels.p : nullptr;
   const size_t smem = (size_t)warps * h->nl_max * kFacVals * 32 * sizeof(T) +
-                      (wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0);
+                      (wt ? (size_t)warps * K * 32 * sizeof(__nv_bfloat16) : 0) +
+                      (size_t)warps * 32 * 8 * sizeof(T);
+  // FP32 entries with K = 64 or 128: vector stores of a lane's features
+  const bool vec = !wt && !split && sizeof(T) == 4 && (K == 64 || K == 128);
   if (wt && K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "mixed precision supports K <= 128");
   if (smem > 220 * 1024)
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "assembly: too many covering subdomains per level");
@@ -492,33 +537,31 @@ void launch_assemble(elmfb_ctx* h) {
       h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_cell.as<int>(),       \
       h->d_cell_count.as<int>(), h->d_cell_pstart.as<int>(), h->d_panel_off.as<int64_t>(),   \
       h->d_entry_base.as<int64_t>(), h->d_cover_off.as<int>(), h->d_x.as<double>(),          \
-      h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, (T*)h->d_panels.p
+      h->d_rcls.as<int>(), h->d_cls.as<RowClass>(), W, B, pout
+#define ELMFB_K1_LAUNCH(F, WT, SP, VEC, PT, P32)                                                \
+  do {                                                                                       \
+    ensure_dyn_smem((const void*)k_assemble<T, F, WT, SP, VEC>, smem);                       \
+    k_assemble<T, F, WT, SP, VEC><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(        \
+        ELMFB_K1_ARGS, PT, h->NPR, an, P32);                                                 \
+  } while (0)
 #define ELMFB_K1(F)                                                                          \
   case F:                                                                                    \
-    if (wt) {                                                                                \
-      ensure_dyn_smem((const void*)k_assemble<T, F, true, false>, smem);                     \
-      k_assemble<T, F, true, false><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(      \
-          ELMFB_K1_ARGS, h->d_pt.as<__nv_bfloat16>(), h->NPR, an);                           \
-    } else if (split) {                                                                      \
-      ensure_dyn_smem((const void*)k_assemble<T, F, false, true>, smem);                     \
-      k_assemble<T, F, false, true><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(      \
-          ELMFB_K1_ARGS, nullptr, h->NPR, an);                                               \
-    } else {                                                                                 \
-      ensure_dyn_smem((const void*)k_assemble<T, F, false, false>, smem);                    \
-      k_assemble<T, F, false, false><<<(unsigned)blocks, warps * 32, smem, h->stream>>>(     \
-          ELMFB_K1_ARGS, nullptr, h->NPR, an);                                               \
-    }                                                                                        \
+    if (wt) ELMFB_K1_LAUNCH(F, true, false, false, h->d_pt.as<__nv_bfloat16>(), nullptr);    \
+    else if (split) ELMFB_K1_LAUNCH(F, false, true, false, nullptr, p32);                    \
+    else if (vec) ELMFB_K1_LAUNCH(F, false, false, (F == 2 || F == 4), nullptr, nullptr);    \
+    else ELMFB_K1_LAUNCH(F, false, false, false, nullptr, nullptr);                          \
     break;
   // algorithmic bytes: every panel entry written once (twice in mixed precision:
   // FP32 row-major and BF16 feature-major), point data read once
   prof_begin(h, KID_ASSEMBLE,
-             (double)h->NPR * K * (sizeof(T) + (wt ? 2.0 : 0.0)) +
+             (double)h->NPR * K * (sizeof(T) + (wt ? 2.0 : 0.0) + (p32 ? 4.0 : 0.0)) +
                  (double)h->NR * (h->dim * 8.0 + 4.0));
   switch (fpl) {
     ELMFB_K1(1) ELMFB_K1(2) ELMFB_K1(3) ELMFB_K1(4) ELMFB_K1(5) ELMFB_K1(6) ELMFB_K1(7) ELMFB_K1(8)
     default: ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "features > 256");
   }
 #undef ELMFB_K1
+#undef ELMFB_K1_LAUNCH
 #undef ELMFB_K1_ARGS
   prof_end(h, KID_ASSEMBLE);
   check_launch("k_assemble");
@@ -774,6 +817,8 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   // K1: panels
   stage_begin(h, 2);
   h->d_panels.alloc(h->NPR * h->K * h->panel_elem(), st);
+  if (h->dual()) h->d_panels_df.alloc(h->NPR * h->K * sizeof(df2), st);
+  h->bj_reuse = false;
   h->gram_pair_ij.clear();
   h->have_gram = false;
   h->gnn_off.clear();
@@ -784,7 +829,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
     // padding tail of 16-row tiles is written by the kernel; clear once for safety
     CUDA_CHECK(cudaMemsetAsync(h->d_pt.p, 0, h->NPR * h->K * 2, st));
   }
-  if (h->eval64()) launch_assemble<double>(h);
+  if (h->eval64() || h->dual()) launch_assemble<double>(h);
   else launch_assemble<float>(h);
   stage_end(h, 2);
   stage_end(h, 7);

@@ -450,7 +450,7 @@ int elmfb_create(elmfb_t* out, const elmfb_config* cfg, void* cuda_stream) {
   if (c.dim < 1 || c.dim > 2 || c.n_levels < 1 || c.n_levels > ELMFB_MAX_LEVELS ||
       c.features < 1 || c.features > ELMFB_MAX_FEATURES || !(c.delta > 1.0) ||
       (c.placement != ELMFB_PLACE_CELL && c.placement != ELMFB_PLACE_ENDPOINT) ||
-      c.precision < ELMFB_FP64 || c.precision > ELMFB_DF32 || !(c.weight_scale >= 0.0))
+      c.precision < ELMFB_FP64 || c.precision > ELMFB_FP32_DF32 || !(c.weight_scale >= 0.0))
     return ELMFB_ERR_INVALID_ARG;
   for (int i = 0; i < c.dim; ++i)
     if (!(c.hi[i] > c.lo[i])) return ELMFB_ERR_INVALID_ARG;

@@ -350,13 +350,13 @@ __global__ void k_qr_iota(int* __restrict__ perm, int n) {
 }
 
 template <class T>
-void densify(elmfb_ctx* h, double* A, int64_t ld) {
+void densify(elmfb_ctx* h, const void* panels, double* A, int64_t ld) {
   const int64_t blocks = ceil_div(h->n_tiles, 4);
   if (blocks > 0)
     k_qr_densify<T><<<(unsigned)blocks, 128, 0, h->stream>>>(
         h->d_tiles.as<int2>(), h->n_tiles, h->K, h->d_entry_cell.as<int>(),
         h->d_cover_sub.as<int>(), h->d_cover_off.as<int>(), h->d_cell_pstart.as<int>(),
-        h->d_entry_base.as<int64_t>(), (const T*)h->d_panels.p, A, ld);
+        h->d_entry_base.as<int64_t>(), (const T*)panels, A, ld);
   check_launch("k_qr_densify");
   count_launch(h);
 }
@@ -384,9 +384,10 @@ void qr_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   dA.alloc((size_t)bytes, st);
   double* A = dA.as<double>();
   CUDA_CHECK(cudaMemsetAsync(A, 0, (size_t)bytes, st));
-  if (h->df32()) densify<df2>(h, A, ld);
-  else if (h->fp64()) densify<double>(h, A, ld);
-  else densify<float>(h, A, ld);
+  if (h->df32()) densify<df2>(h, h->d_panels.p, A, ld);
+  else if (h->dual()) densify<df2>(h, h->d_panels_df.p, A, ld);   // the pair panels
+  else if (h->fp64()) densify<double>(h, h->d_panels.p, A, ld);
+  else densify<float>(h, h->d_panels.p, A, ld);
   k_qr_copy_h<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1024), 256, 0, st>>>(
       h->d_h.as<double>(), m, A + (int64_t)n * ld);
   count_launch(h);

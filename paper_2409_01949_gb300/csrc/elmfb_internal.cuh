@@ -239,6 +239,10 @@ struct elmfb_ctx {
   int64_t prof_seen[KID_COUNT] = {0};   // launches seen while profiling
   bool prof_now[KID_COUNT] = {false};   // the current launch carries events
 
+  // ELMFB_FP32_DF32: d_panels holds the FP32 panels, d_panels_df the pairs
+  DevBuf d_panels_df;
+  bool bj_reuse = false;   // LSQR refinement: keep the block-Jacobi factors of the last set-up
+  bool dual() const { return cfg.precision == ELMFB_FP32_DF32; }
   bool fp64() const { return cfg.precision == ELMFB_FP64; }
   bool df32() const { return cfg.precision == ELMFB_DF32; }
   // entries evaluated in FP64 (FP64 panels, or FP32 pairs split from FP64)

@@ -2657,7 +2657,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const bool identity = o->preconditioner == ELMFB_PREC_NONE;
 
   stage_begin(h, 4);
-  block_jacobi_setup<T>(h, o->shift, identity);
+  if (!h->bj_reuse) block_jacobi_setup<T>(h, o->shift, identity);
   stage_end(h, 4);
   info->setup_ms = h->stage_ms[4];
   info->precond_retries = h->bj_retries;
@@ -3225,6 +3225,105 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
 
 }  // namespace
 
+namespace {
+
+// r = h - M a from the FP32-pair panels of ELMFB_FP32_DF32 (the fused pass in
+// mode 1 on the pair panels: float-float products and sums, FP64-accurate),
+// into h->d_u (padded sorted rows).
+void residual_pairs(elmfb_ctx* h, const double* a) {
+  struct Swap {   // the pair panels and ELMFB_DF32 for the duration of the pass
+    elmfb_ctx* h;
+    explicit Swap(elmfb_ctx* hh) : h(hh) {
+      std::swap(h->d_panels.p, h->d_panels_df.p);
+      std::swap(h->d_panels.bytes, h->d_panels_df.bytes);
+      h->cfg.precision = ELMFB_DF32;
+    }
+    ~Swap() {
+      std::swap(h->d_panels.p, h->d_panels_df.p);
+      std::swap(h->d_panels.bytes, h->d_panels_df.bytes);
+      h->cfg.precision = ELMFB_FP32_DF32;
+    }
+  } swap(h);
+  cudaStream_t st = h->stream;
+  FusedPlan fp;
+  if (!build_fused_plan(h, fp))
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "refinement: the pair panels need the fused pass");
+  DevBuf sc, gp;
+  sc.alloc(2 * kScal * sizeof(double), st);
+  gp.alloc((size_t)(std::max(kGatherBlocks, fp.n_units) + h->n_sub + 8) * sizeof(double), st);
+  CUDA_CHECK(cudaMemsetAsync(sc.p, 0, 2 * kScal * sizeof(double), st));
+  h->d_u.alloc(h->NR * sizeof(double), st);
+  launch_fused<df2>(h, fp, a, 1, sc.as<double>(), gp.as<double>());
+  check_launch("refinement residual");
+  CUDA_CHECK(cudaStreamSynchronize(st));   // fp's buffers are released on return
+}
+
+// Mixed-precision LSQR with refinement (ELMFB_FP32_DF32): `refine` outer
+// steps; step 0 solves min ||M a - h|| on the FP32 panels, every later step
+// forms r = h - M a from the pair panels and solves min ||M d - r|| on the FP32
+// panels (LSQR from zero, the block-Jacobi factors of step 0 reused), a += d.
+void lsqr_refine(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
+  cudaStream_t st = h->stream;
+  const int64_t N = h->NPhi;
+  elmfb_solve_opts oi = *o;
+  DevBuf acc, rbuf;
+  acc.alloc(N * sizeof(double), st);
+  int total = 0;
+  double solve_ms = 0.0;
+  int status = ELMFB_OK;
+  struct Reset {   // the next solve sets up its own preconditioner again
+    elmfb_ctx* h;
+    ~Reset() { h->bj_reuse = false; }
+  } reset{h};
+  for (int k = 0; k < o->refine; ++k) {
+    elmfb_solve_info ii{};
+    if (k == 0) {
+      lsqr<float>(h, &oi, &ii);
+      CUDA_CHECK(cudaMemcpyAsync(acc.p, h->d_a.p, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 st));
+      info->setup_ms = ii.setup_ms;
+      info->precond_retries = ii.precond_retries;
+    } else {
+      residual_pairs(h, acc.as<double>());
+      // the residual becomes the right-hand side of the correction solve
+      rbuf.alloc(h->NR * sizeof(double), st);
+      CUDA_CHECK(cudaMemcpyAsync(rbuf.p, h->d_u.p, h->NR * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+      std::swap(h->d_h.p, rbuf.p);
+      std::swap(h->d_h.bytes, rbuf.bytes);
+      h->bj_reuse = true;
+      oi.warm_start = 0;
+      try {
+        lsqr<float>(h, &oi, &ii);
+      } catch (...) {
+        std::swap(h->d_h.p, rbuf.p);
+        std::swap(h->d_h.bytes, rbuf.bytes);
+        throw;
+      }
+      std::swap(h->d_h.p, rbuf.p);
+      std::swap(h->d_h.bytes, rbuf.bytes);
+      const int ub = (int)std::min<int64_t>(ceil_div(N, 256), 1216);
+      k_add_to<<<ub, 256, 0, st>>>(acc.as<double>(), h->d_a.as<double>(), N);
+      count_launch(h);
+      check_launch("refinement update");
+    }
+    total += ii.iterations;
+    solve_ms += ii.solve_ms;
+    if (ii.status != ELMFB_OK) status = ii.status;
+    info->residual_norm = ii.residual_norm;
+    info->normal_residual_norm = ii.normal_residual_norm;
+    info->sigma_max = ii.sigma_max;
+    info->sigma_min = ii.sigma_min;
+  }
+  CUDA_CHECK(cudaMemcpyAsync(h->d_a.p, acc.p, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  info->status = status;
+  info->iterations = total;
+  info->solve_ms = solve_ms;
+}
+
+}  // namespace
+
 void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   if (o->method == ELMFB_SOLVE_PCG) {
     pcg_solve<float>(h, o, info);
@@ -3242,7 +3341,10 @@ void solve_system(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* inf
     ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "solver method not available in this build");
   if (o->preconditioner != ELMFB_PREC_NONE && o->preconditioner != ELMFB_PREC_BLOCK_JACOBI)
     ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "LSQR takes no or block-Jacobi preconditioning");
-  if (h->df32()) lsqr<df2>(h, o, info);
+  if (h->dual()) {
+    if (o->warm_start) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "refinement starts from a = 0");
+    lsqr_refine(h, o, info);
+  } else if (h->df32()) lsqr<df2>(h, o, info);
   else if (h->fp64()) lsqr<double>(h, o, info);
   else lsqr<float>(h, o, info);
 }
