@@ -380,11 +380,61 @@ def run_ours(args):
     }
     if not args.no_gram:
         line["gram_tc"] = gram_measure(P, stream)
+    if not args.no_compare_fp64 and prec != E.FP64:
+        line["precision_comparison"] = compare_fp64(P, stream, opts, ms, float(err["rel_l2"]),
+                                                    info.iterations, args)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(P, args)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def compare_fp64(P, stream, opts32, ms32, err32, its32, args, reps=2):
+    """The same step with FP64 panels (the plain FP64 GPU form: FP64 entries,
+    FP64 products and sums) under the same stopping rule, timed the same way
+    (CUDA events around whole steps, after one warm-up step): its error and
+    time beside the FP32-panel form's (FP32 storage and products, FP64
+    accumulation of the scalars and vectors)."""
+    import torch
+
+    import paper_2409_01949_gb300 as E
+    opts = E.default_solve_opts(max_iter=opts32.max_iter, atol=0.0, btol=0.0, ntol=opts32.ntol,
+                                shift=1e-12, check_every=opts32.check_every)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sets = _sets(P, dev)
+    xs = torch.as_tensor(P.test_points).to(dev)
+    u = torch.as_tensor(P.exact(P.test_points)).to(dev)
+    uh = torch.empty(xs.shape[0], dtype=torch.float64, device=dev)
+    res = {}
+
+    def step():
+        s = E.Solver.from_problem(P, precision=E.FP64, stream=stream.cuda_stream)
+        s.assemble(sets)
+        info = s.solve(opts)
+        s.eval(xs, out=uh)
+        e = s.error_norms(uh, u)
+        s.close()
+        res.update(info=info, err=e)
+
+    step()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(reps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = t0.elapsed_time(t1) / reps
+    e64 = float(res["err"]["rel_l2"])
+    return {"fp64_form": {"ms_per_step": round(ms64, 3), "rel_l2": e64,
+                          "iterations": res["info"].iterations, "shift": 1e-12},
+            "fp32_form": {"ms_per_step": round(ms32, 3), "rel_l2": err32, "iterations": its32},
+            "speedup_fp32_over_fp64": round(ms64 / ms32, 2),
+            "error_ratio_fp32_over_fp64": round(err32 / e64, 3),
+            "note": "same workload and stopping rule (||(MP)^T r|| <= ntol ||(MP)^T h||); the "
+                    "learned preconditioner applies to FCG only and is not part of either form"}
 
 
 def gram_measure(P, stream, reps=3):
@@ -427,8 +477,8 @@ def run_batch(args):
     torch.cuda.set_device(local)
     specs = WL.batch_specs(args.batch_n, 0)
     probs = [WL.batch_instance(sp, i, 0) for i, sp in enumerate(specs)]
-    opts = E.default_solve_opts(max_iter=args.batch_iters, atol=0.0, btol=0.0, shift=1e-10,
-                                check_every=args.batch_iters)
+    opts = E.default_solve_opts(max_iter=args.batch_iters, atol=0.0, btol=0.0, ntol=args.ntol,
+                                shift=1e-6, check_every=10)
     for _ in range(args.warmup):
         E.batch_solve(probs[:16], precision=E.FP32, n_workers=args.batch_workers, opts=opts)
     torch.cuda.synchronize()
@@ -447,11 +497,15 @@ def run_batch(args):
             "config": {"workload": f"batch{args.batch_n}_uneven_poisson2d",
                        "instances": len(probs), "rows": int(sum(P.n_rows for P in probs)),
                        "columns": int(sum(P.n_columns for P in probs)),
-                       "solver": f"LSQR + block-Jacobi, {args.batch_iters} iterations each",
+                       "solver": f"LSQR + block-Jacobi, stopped at ||(MP)^T r|| <= "
+                                 f"{args.ntol:g} ||(MP)^T h|| (cap {args.batch_iters})",
                        "workers": args.batch_workers},
             "instances_per_s": round(len(probs) / dt, 2),
             "rel_l2": {"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
                        "max": float(errs.max())},
+            "iterations": {"median": float(np.median([r.iterations for r in res])),
+                           "max": int(max(r.iterations for r in res)),
+                           "capped": int(sum(r.iterations >= args.batch_iters for r in res))},
             "gpu_launches": int(sum(r.launches for r in res)),
             "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -530,10 +584,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gram", action="store_true",
                     help="skip the tensor-core Gram measurement after the timed steps")
+    ap.add_argument("--no-compare-fp64", action="store_true",
+                    help="skip timing the same step with FP64 panels (the plain FP64 form)")
     ap.add_argument("--roofline-stride", type=int, default=8,
                     help="time every n-th launch of the roofline kernel in the timed steps")
     ap.add_argument("--batch-n", type=int, default=512)
-    ap.add_argument("--batch-iters", type=int, default=300)
+    ap.add_argument("--batch-iters", type=int, default=5000)
     ap.add_argument("--batch-workers", type=int, default=8)
     args = ap.parse_args()
     if args.workload == "batch":
