@@ -102,7 +102,12 @@ def _rhs_rows(P, seed):
     return np.concatenate([Q.interior.rhs, Q.boundary[0].rhs])
 
 
-def test_training_lowers_loss_and_reports_gain():
+def test_training_lowers_loss_but_the_network_does_not_beat_block_jacobi():
+    """The learned preconditioner's measured effect (a negative result): training
+    on pairs from the method's own FCG solves lowers the loss, but FCG with the
+    trained network ends at a larger error than FCG with block-Jacobi alone
+    after the same iteration cap (measured: rel. L2 0.99 against 0.12).  The
+    test holds that relation; a network that helps must change it."""
     P = WL.poisson2d(levels=(1, 2, 4), features=32, n_side=40, n_boundary_side=40)
     rhs = np.stack([_rhs_rows(P, s) for s in range(1, 5)])
     tol = 1e-6
@@ -113,6 +118,7 @@ def test_training_lowers_loss_and_reports_gain():
           f"block-Jacobi {i_bj.iterations} (rel L2 {e_bj:.2e}), with the network "
           f"{i_gnn.iterations} (rel L2 {e_gnn:.2e})")
     assert loss[1] < loss[0]
+    assert e_gnn >= e_bj and i_gnn.iterations >= i_bj.iterations
 
 
 def test_fcg_block_jacobi_matches_paper_protocol_error():
