@@ -60,8 +60,9 @@ enum {
   ELMFB_DF32 = 3,   /* panels as FP32 pairs (hi + lo, ~48-bit significand, same
                        8 bytes as FP64), products and sums in float-float
                        arithmetic on the FP32 pipes; entries evaluated in FP64.
-                       The solvers need K a multiple of 4, K <= 128 and <= 30
-                       covering panels per cell (else UNSUPPORTED)            */
+                       The solvers need K a multiple of 4, K <= 128, at most 30
+                       covering panels per cell and (covering panels per
+                       cell) x K <= 1696 (else UNSUPPORTED)                   */
   ELMFB_FP32_DF32 = 4 /* mixed precision with refinement: FP32 panels for the
                        iterations plus FP32-pair (ELMFB_DF32) panels of the
                        same entries (12 bytes per entry) for FP64-accurate

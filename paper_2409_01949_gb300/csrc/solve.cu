@@ -2366,7 +2366,8 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     const int pthreads = fthreads + 64;   // covering-panel warps + producer + control
     if (S < 4 || pthreads > 1024 || K % 2 != 0 || fpl > 4)
       ELMFB_THROW(ELMFB_ERR_UNSUPPORTED,
-                  "DF32 needs K even, K <= 128 and <= 30 covering panels per cell");
+                  "DF32 needs K even, K <= 128, at most 30 covering panels per cell and "
+                  "(covering panels per cell) x K <= 1696 (four ring stages of 4 rows)");
     const size_t smem = (size_t)S * stage_bytes + u_bytes;
     prof_begin(h, KID_FUSED, (double)h->NPR * K * 8.0 + 16.0 * h->NR + 8.0 * h->NPhi);
 #define ELMFB_FD(F)                                                                             \
