@@ -94,7 +94,11 @@ enum {
   ELMFB_PREC_NONE = 0,      /* plain LSQR, the paper's protocol                  */
   ELMFB_PREC_BLOCK_JACOBI = 1,/* per-subdomain Cholesky of the shifted diagonal
                                Gram block (not in the paper)                      */
-  ELMFB_PREC_BJ_GNN = 2     /* FCG only: block-Jacobi plus the learned correction */
+  ELMFB_PREC_BJ_GNN = 2,    /* FCG only: block-Jacobi plus the learned correction */
+  ELMFB_PREC_BJ_COARSE = 3  /* FCG only: block-Jacobi on the subdomains of the finer
+                               levels and, on all columns of levels 1..coarse_levels
+                               together, the inverse of their shifted joint Gram
+                               block (a coarse-level correction; not in the paper) */
 };
 
 typedef struct elmfb_ctx* elmfb_t;
@@ -262,6 +266,9 @@ typedef struct {
   double ntol;         /* LSQR: also stop when ||(M P)^T r|| <= ntol ||(M P)^T h||
                           (the preconditioned normal-equations residual
                           relative to its start, LSQR's estimate); 0 disables */
+  int coarse_levels;   /* ELMFB_PREC_BJ_COARSE: the coarse block holds the columns
+                          of levels 1..coarse_levels (at most 4096 of them);
+                          its shift is `shift` x tr / (its columns)          */
 } elmfb_solve_opts;
 
 typedef struct {
@@ -285,7 +292,7 @@ typedef struct {
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
  * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
- * gram_shift 0, rcond 1e-13, ntol 0. */
+ * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the

@@ -25,7 +25,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_BREAKD
 FP64, FP32, MIXED, DF32, FP32_DF32 = 0, 1, 2, 3, 4
 PLACE_CELL, PLACE_ENDPOINT = 0, 1
 SOLVE_LSQR, SOLVE_PCG, SOLVE_FCG_GNN, SOLVE_QR = 0, 1, 2, 3
-PREC_NONE, PREC_BLOCK_JACOBI, PREC_BJ_GNN = 0, 1, 2
+PREC_NONE, PREC_BLOCK_JACOBI, PREC_BJ_GNN, PREC_BJ_COARSE = 0, 1, 2, 3
 MAX_LEVELS = 12
 MAX_ROWSETS = 16
 MAX_HOLES = 4
@@ -66,7 +66,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int), ("preconditioner", C.c_int), ("max_iter", C.c_int),
                 ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
                 ("check_every", C.c_int), ("warm_start", C.c_int), ("refine", C.c_int),
-                ("gram_shift", C.c_double), ("rcond", C.c_double), ("ntol", C.c_double)]
+                ("gram_shift", C.c_double), ("rcond", C.c_double), ("ntol", C.c_double),
+                ("coarse_levels", C.c_int)]
 
 
 class BatchItem(C.Structure):

@@ -562,6 +562,7 @@ void elmfb_default_solve_opts(elmfb_solve_opts* o) {
   o->gram_shift = 0.0;
   o->rcond = 1e-13;
   o->ntol = 0.0;
+  o->coarse_levels = 2;
 }
 
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -310,6 +311,14 @@ void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part);  // z
 
 // learned preconditioner (gnn.cu)
 void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
+
+// coarse-level correction of block-Jacobi (coarse.cu): the joint block of the
+// columns of levels 1..levels
+int coarse_columns(const elmfb_ctx* h, int levels);
+void coarse_setup(elmfb_ctx* h, int levels, double shift,
+                  const std::function<void(const double*, double*)>& normal_op, DevBuf& X,
+                  int* retries);
+void coarse_apply(elmfb_ctx* h, const DevBuf& X, int n, const double* r, double* z, DevBuf& tmp);
 
 // eval (eval.cu)
 void eval_model(elmfb_ctx* h, const double* xs, int64_t n, double* out);

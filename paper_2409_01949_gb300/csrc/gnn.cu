@@ -386,6 +386,8 @@ struct Fcg {
   elmfb_ctx* h;
   FusedPlan fp;
   DevBuf vec, part, sc, xin, yout, gpart;
+  DevBuf Xc, ctmp;   // coarse-level correction: X_c = L_c^{-1} of the joint coarse block
+  int nc = 0;        // its columns (0: plain block-Jacobi)
   double *x, *r, *z, *p, *q, *g;
   int64_t N;
   void init() {
@@ -423,6 +425,7 @@ struct Fcg {
   // z = B r (+ sigma N(B r / sigma))
   void precond(bool use_gnn) {
     bj_apply(h, r, z, part.as<double>());
+    if (nc > 0) coarse_apply(h, Xc, nc, r, z, ctmp);
     if (!use_gnn) return;
     const double s2 = dot(h, z, z, N, part);
     const double sigma = std::sqrt(s2);
@@ -502,6 +505,17 @@ void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   if (use_gnn) gnn_alloc(h);
   Fcg f{h};
   f.init();
+  if (o->preconditioner == ELMFB_PREC_BJ_COARSE) {
+    // the coarse block from the same normal operator the iteration applies
+    stage_begin(h, 4);
+    int cr = 0;
+    coarse_setup(h, o->coarse_levels, o->shift,
+                 [&](const double* v, double* y) { f.normal_op(v, y); }, f.Xc, &cr);
+    f.nc = coarse_columns(h, o->coarse_levels);
+    stage_end(h, 4);
+    info->setup_ms += h->stage_ms[4];
+    info->precond_retries += cr;
+  }
   stage_begin(h, 5);
   CUDA_CHECK(cudaMemsetAsync(f.x, 0, f.N * sizeof(double), h->stream));
   f.rhs();

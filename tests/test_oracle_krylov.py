@@ -1,0 +1,46 @@
+"""Pins of the oracle's preconditioned CG and block preconditioner."""
+import numpy as np
+
+from oracle import krylov as KR
+
+
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q @ np.diag(np.linspace(1.0, 50.0, n)) @ Q.T
+
+
+def test_cg_solves_spd_system_in_n_steps():
+    A = _spd(12, 0)
+    b = np.random.default_rng(1).standard_normal(12)
+    x = KR.pcg(lambda v: A @ v, b, lambda r: r, 12)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
+
+
+def test_exact_preconditioner_solves_in_one_step():
+    A = _spd(10, 2)
+    b = np.random.default_rng(3).standard_normal(10)
+    Ai = np.linalg.inv(A)
+    x = KR.pcg(lambda v: A @ v, b, lambda r: Ai @ r, 1)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+def test_joint_block_over_every_column_is_the_inverse():
+    A = _spd(9, 4)
+    P = KR.block_preconditioner(A, K=3, shift=0.0, n_coarse=9)
+    r = np.random.default_rng(5).standard_normal(9)
+    assert np.allclose(P(r), np.linalg.solve(A, r), rtol=1e-10)
+
+
+def test_block_jacobi_blocks_and_shift():
+    """Without a coarse block: each K-block is inverted on its own, shifted by
+    eps tr/K (written out for a 2 x 2 block)."""
+    A = _spd(6, 6)
+    eps = 0.1
+    P = KR.block_preconditioner(A, K=2, shift=eps)
+    r = np.zeros(6)
+    r[2] = 1.0
+    B = A[2:4, 2:4] + eps * np.trace(A[2:4, 2:4]) / 2 * np.eye(2)
+    z = P(r)
+    assert np.allclose(z[2:4], np.linalg.solve(B, [1.0, 0.0]))
+    assert np.all(z[:2] == 0.0) and np.all(z[4:] == 0.0)
