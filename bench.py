@@ -478,7 +478,7 @@ def run_batch(args):
     specs = WL.batch_specs(args.batch_n, 0)
     probs = [WL.batch_instance(sp, i, 0) for i, sp in enumerate(specs)]
     opts = E.default_solve_opts(max_iter=args.batch_iters, atol=0.0, btol=0.0, ntol=args.ntol,
-                                shift=1e-6, check_every=10)
+                                shift=1e-6, check_every=10, graph=0 if args.no_graph else 1)
     for _ in range(args.warmup):
         E.batch_solve(probs[:16], precision=E.FP32, n_workers=args.batch_workers, opts=opts)
     torch.cuda.synchronize()
@@ -499,7 +499,8 @@ def run_batch(args):
                        "columns": int(sum(P.n_columns for P in probs)),
                        "solver": f"LSQR + block-Jacobi, stopped at ||(MP)^T r|| <= "
                                  f"{args.ntol:g} ||(MP)^T h|| (cap {args.batch_iters})",
-                       "workers": args.batch_workers},
+                       "workers": args.batch_workers,
+                       "graphs": not args.no_graph},
             "instances_per_s": round(len(probs) / dt, 2),
             "rel_l2": {"median": float(np.median(errs)), "p90": float(np.percentile(errs, 90)),
                        "max": float(errs.max())},
@@ -591,6 +592,9 @@ def main():
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-iters", type=int, default=5000)
     ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batched workload: launch LSQR kernels one by one instead of replaying "
+                         "each check interval as a CUDA graph")
     args = ap.parse_args()
     if args.workload == "batch":
         run_batch(args)

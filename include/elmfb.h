@@ -269,6 +269,11 @@ typedef struct {
   int coarse_levels;   /* ELMFB_PREC_BJ_COARSE: the coarse block holds the columns
                           of levels 1..coarse_levels (at most 4096 of them);
                           its shift is `shift` x tr / (its columns)          */
+  int graph;           /* LSQR: nonzero captures the kernels of one check
+                          interval as a CUDA graph and replays it (one launch
+                          per check_every iterations); needs a handle stream
+                          other than the legacy default stream and profiling
+                          off, else the kernels are launched one by one     */
 } elmfb_solve_opts;
 
 typedef struct {
@@ -292,7 +297,7 @@ typedef struct {
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
  * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
- * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2. */
+ * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2, graph 0. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the

@@ -67,7 +67,7 @@ class SolveOpts(C.Structure):
                 ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
                 ("check_every", C.c_int), ("warm_start", C.c_int), ("refine", C.c_int),
                 ("gram_shift", C.c_double), ("rcond", C.c_double), ("ntol", C.c_double),
-                ("coarse_levels", C.c_int)]
+                ("coarse_levels", C.c_int), ("graph", C.c_int)]
 
 
 class BatchItem(C.Structure):

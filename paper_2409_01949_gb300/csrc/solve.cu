@@ -2858,9 +2858,50 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   int status = ELMFB_ERR_NOT_CONVERGED;
   double sc[kScal];
   const int max_it = o->max_iter;
+  // Graph mode: the kernels of one check interval (all device-resident, no
+  // host values between them) are captured once as a CUDA graph and replayed,
+  // one launch per interval.  Needs a stream other than the legacy default
+  // stream and profiling off.
+  const bool use_graph = o->graph && fused && st != nullptr && !h->prof;
+  struct GraphExec {
+    cudaGraphExec_t e = nullptr;
+    ~GraphExec() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } gx;
+  int g_batch = 0;
+  int64_t g_launches = 0;
   while (it < max_it) {
     int batch = std::min(o->check_every, max_it - it);
-    for (int b = 0; b < batch; ++b) {
+    if (use_graph) {
+      if (!gx.e || batch != g_batch) {
+        if (gx.e) CUDA_CHECK(cudaGraphExecDestroy(gx.e));
+        gx.e = nullptr;
+        const int64_t l0 = h->launches;
+        cudaGraph_t g = nullptr;
+        CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+          for (int b = 0; b < batch; ++b) {
+            fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);
+            fused_tail(0);
+          }
+        } catch (...) {
+          cudaStreamEndCapture(st, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        CUDA_CHECK(cudaStreamEndCapture(st, &g));
+        const cudaError_t ie = cudaGraphInstantiate(&gx.e, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_CHECK(ie);
+        g_batch = batch;
+        g_launches = h->launches - l0;   // kernels that count themselves, per replay
+        h->launches = l0;
+      }
+      CUDA_CHECK(cudaGraphLaunch(gx.e, st));
+      h->launches += g_launches;
+    }
+    for (int b = 0; b < batch && !use_graph; ++b) {
       if (fused) {
         // t (and its low-precision copy) come from the previous iteration's tail
         fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);

@@ -97,3 +97,24 @@ def test_sixteen_uncapped_instances_meet_their_oracle():
                   f"oracle {o['rel_l2']:.4e}")
             assert r.status == E.OK
             assert r.rel_l2 <= bar
+
+
+@pytest.mark.parametrize("prec", [E.FP32, E.DF32])
+def test_graph_replay_equals_launch_by_launch(prec):
+    """LSQR with `graph` (each check interval captured once as a CUDA graph and
+    replayed) on a stream of the caller's runs the same kernels in the same
+    order: bitwise the same coefficients and iteration count as launching them
+    one by one, including a last interval shorter than check_every."""
+    torch = pytest.importorskip("torch")
+    P = WL.poisson2d(levels=(1, 2, 4), features=32, n_side=50, n_boundary_side=50)
+    stream = torch.cuda.Stream()
+    out = {}
+    for graph in (0, 1):
+        with E.Solver.from_problem(P, precision=prec, stream=stream.cuda_stream) as s:
+            s.assemble_problem(P)
+            info = s.solve(max_iter=57, atol=0.0, btol=0.0, shift=1e-6, check_every=10,
+                           graph=graph)
+            out[graph] = (s.coeffs(), info.iterations, s.kernel_launches())
+    assert out[0][1] == out[1][1] == 57
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][2] == out[1][2]
