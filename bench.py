@@ -478,7 +478,8 @@ def run_batch(args):
     specs = WL.batch_specs(args.batch_n, 0)
     probs = [WL.batch_instance(sp, i, 0) for i, sp in enumerate(specs)]
     opts = E.default_solve_opts(max_iter=args.batch_iters, atol=0.0, btol=0.0, ntol=args.ntol,
-                                shift=1e-6, check_every=10, graph=0 if args.no_graph else 1)
+                                shift=1e-6, check_every=10, graph=0 if args.no_graph else 1,
+                                autotune=1)
     for _ in range(args.warmup):
         E.batch_solve(probs[:16], precision=E.FP32, n_workers=args.batch_workers, opts=opts)
     torch.cuda.synchronize()
@@ -508,6 +509,7 @@ def run_batch(args):
                            "max": int(max(r.iterations for r in res)),
                            "capped": int(sum(r.iterations >= args.batch_iters for r in res))},
             "gpu_launches": int(sum(r.launches for r in res)),
+            "autotuner": E.tuning_table(),
             "clocks": clk}
     print(json.dumps(line), flush=True)
 

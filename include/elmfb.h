@@ -269,6 +269,9 @@ typedef struct {
   int coarse_levels;   /* ELMFB_PREC_BJ_COARSE: the coarse block holds the columns
                           of levels 1..coarse_levels (at most 4096 of them);
                           its shift is `shift` x tr / (its columns)          */
+  int autotune;        /* LSQR: nonzero picks the fused pass's work-unit size by
+                          timing (elmfb_tuning_table); the choice is kept per
+                          shape class for the life of the process           */
   int graph;           /* LSQR: nonzero captures the kernels of one check
                           interval as a CUDA graph and replays it (one launch
                           per check_every iterations); needs a handle stream
@@ -297,7 +300,7 @@ typedef struct {
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
  * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
- * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2, graph 0. */
+ * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2, autotune 0, graph 0. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the
@@ -382,6 +385,20 @@ typedef struct {
 } elmfb_batch_result;
 int elmfb_batch_solve(int n, const elmfb_batch_item* items, const elmfb_solve_opts* opts,
                       int n_workers, elmfb_batch_result* results);
+
+/* The autotuner's record (not in the paper).  A shape class is (panel
+ * precision, K, most covering panels of a cell, floor(log2 padded rows)); for
+ * each class seen by a solve with `autotune`, the fused LSQR pass was timed at
+ * three work-unit sizes (the heuristic size, half and twice it) and the
+ * fastest is used from then on.  Writes up to `max` entries and returns the
+ * number of classes (negative status on a bad argument). */
+typedef struct {
+  int precision, features, covering_panels, rows_log2;
+  int unit_rows;        /* the choice                          */
+  int candidates[3];    /* the unit sizes timed                */
+  double ms[3];         /* their average pass time (CUDA events) */
+} elmfb_tuning_entry;
+int elmfb_tuning_table(int max, elmfb_tuning_entry* out);
 
 /* Copy the coefficients a [N_Phi] out of / into the handle. */
 int elmfb_get_coeffs(elmfb_t h, double* a);

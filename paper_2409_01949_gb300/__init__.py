@@ -67,7 +67,7 @@ class SolveOpts(C.Structure):
                 ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
                 ("check_every", C.c_int), ("warm_start", C.c_int), ("refine", C.c_int),
                 ("gram_shift", C.c_double), ("rcond", C.c_double), ("ntol", C.c_double),
-                ("coarse_levels", C.c_int), ("graph", C.c_int)]
+                ("coarse_levels", C.c_int), ("autotune", C.c_int), ("graph", C.c_int)]
 
 
 class BatchItem(C.Structure):
@@ -87,6 +87,12 @@ class SolveInfo(C.Structure):
                 ("normal_residual_norm", C.c_double), ("setup_ms", C.c_double),
                 ("solve_ms", C.c_double), ("precond_retries", C.c_int), ("rank", C.c_int),
                 ("sigma_max", C.c_double), ("sigma_min", C.c_double)]
+
+
+class TuningEntry(C.Structure):
+    _fields_ = [("precision", C.c_int), ("features", C.c_int), ("covering_panels", C.c_int),
+                ("rows_log2", C.c_int), ("unit_rows", C.c_int), ("candidates", C.c_int * 3),
+                ("ms", C.c_double * 3)]
 
 
 _lib = None
@@ -129,6 +135,7 @@ _SIGNATURES = {
     "elmfb_gnn_train": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                   C.c_uint64, C.c_void_p]),
     "elmfb_get_gram": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "elmfb_tuning_table": (C.c_int, [C.c_int, C.c_void_p]),
 }
 
 
@@ -236,6 +243,18 @@ def _rowsets(problem, keep):
         arr[i].weight = float(rs.weight or 0.0)
     keep.append(arr)
     return arr
+
+
+def tuning_table():
+    """The autotuner's choices so far: a list of dicts, one per shape class."""
+    n = lib().elmfb_tuning_table(0, None)
+    if n < 0:
+        raise ElmfbError(-n, "tuning table")
+    arr = (TuningEntry * max(n, 1))()
+    n = lib().elmfb_tuning_table(n, arr)
+    return [dict(precision=e.precision, features=e.features, covering_panels=e.covering_panels,
+                 rows_log2=e.rows_log2, unit_rows=e.unit_rows, candidates=list(e.candidates),
+                 ms=list(e.ms)) for e in arr[:n]]
 
 
 def trim_memory(device: int = -1):

@@ -563,6 +563,7 @@ void elmfb_default_solve_opts(elmfb_solve_opts* o) {
   o->rcond = 1e-13;
   o->ntol = 0.0;
   o->coarse_levels = 2;
+  o->autotune = 0;
   o->graph = 0;
 }
 

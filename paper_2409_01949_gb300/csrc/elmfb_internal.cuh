@@ -288,7 +288,9 @@ struct FusedPlan {
   int threads = 0;
   bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
 };
-bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp);
+// unit_rows >= 8 forces the rows per work unit (the autotuner's choice)
+bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp, int unit_rows = 0);
+int64_t fused_unit_target(const elmfb_ctx* h);
 // mode 0: u' = M t - (alpha/beta) u (staged alpha, beta); mode 1: u' = h - M t;
 // mode 2: u' = (M t) s - (alpha/beta) u with s the staged 1/alpha (t = P v',
 // v' = alpha v not yet normalised).

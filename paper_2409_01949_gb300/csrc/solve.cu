@@ -26,9 +26,12 @@
 // Every reduction is a fixed-order sum, so results are bitwise reproducible
 // from run to run.
 #include <algorithm>
-#include <cstdlib>
-#include <type_traits>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
 
 #include "elmfb_internal.cuh"
 #include "sm100_ptx.cuh"
@@ -2247,7 +2250,16 @@ struct SolveLayout {
 
 }  // namespace
 
-bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
+// Heuristic rows per fused-pass work unit (see build_fused_plan).
+int64_t fused_unit_target(const elmfb_ctx* h) {
+  const double row_bytes =
+      (double)h->NPR / (double)std::max<int64_t>(h->NR, 1) * h->K * (double)h->panel_elem();
+  const int64_t by_bytes = (int64_t)((2.0 * 1024 * 1024) / std::max(row_bytes, 1.0));
+  return std::min<int64_t>(
+      kMaxUnitRows, std::max<int64_t>(8, std::max(h->NR / 608, by_bytes) & ~int64_t(7)));
+}
+
+bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp, int unit_rows) {
   const int K = h->K;
   if (h->max_cover > 32 || K > 128) return false;
   cudaStream_t st = h->stream;
@@ -2269,6 +2281,7 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp) {
     const long v = atol(e);
     if (v >= 8 && v <= kMaxUnitRows) target = v & ~7L;
   }
+  if (unit_rows >= 8) target = std::min<int64_t>(kMaxUnitRows, unit_rows & ~7);
   std::vector<int4> units;
   std::vector<std::vector<int>> plist(h->n_sub);
   int pbase = 0;
@@ -2649,6 +2662,88 @@ void bidiag_extremes(elmfb_ctx* h, const double* gk, int k, double* out2) {
 
 namespace {
 
+// ---- autotuner of the fused pass's work-unit size --------------------------
+// Shape class: panel precision, K, covering panels per cell, log2 of the
+// padded rows.  The first solve of a class with `autotune` times the fused
+// pass (mode 1, t = 0, CUDA events on the handle's stream, one warm-up and
+// three timed launches each) at the heuristic unit size and at half and twice
+// it, keeps the fastest for the class for the life of the process, and
+// records the candidates and their times (elmfb_tuning_table).
+struct TuneKey {
+  int prec, K, cover, rows_log2;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(prec, K, cover, rows_log2) < std::tie(o.prec, o.K, o.cover, o.rows_log2);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, elmfb_tuning_entry> g_tune;
+
+template <class T>
+int autotune_unit_rows(elmfb_ctx* h) {
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= h->NR) ++lg;
+  const TuneKey key{h->cfg.precision, h->K, h->max_cover, lg};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second.unit_rows;
+  }
+  cudaStream_t st = h->stream;
+  const int64_t t0 = fused_unit_target(h);
+  int cand[3] = {(int)std::max<int64_t>(8, (t0 / 2) & ~7), (int)t0,
+                 (int)std::min<int64_t>(kMaxUnitRows, t0 * 2)};
+  DevBuf zero, sc, gp;
+  zero.alloc(std::max<int64_t>(h->NPhi, 1) * sizeof(double), st);
+  sc.alloc(2 * kScal * sizeof(double), st);
+  CUDA_CHECK(cudaMemsetAsync(zero.p, 0, h->NPhi * sizeof(double), st));
+  CUDA_CHECK(cudaMemsetAsync(sc.p, 0, 2 * kScal * sizeof(double), st));
+  h->d_u.alloc(h->NR * sizeof(double), st);
+  cudaEvent_t a, b;
+  CUDA_CHECK(cudaEventCreate(&a));
+  CUDA_CHECK(cudaEventCreate(&b));
+  elmfb_tuning_entry e{};
+  e.precision = key.prec;
+  e.features = key.K;
+  e.covering_panels = key.cover;
+  e.rows_log2 = key.rows_log2;
+  double best = 1e300;
+  try {
+    for (int c = 0; c < 3; ++c) {
+      e.candidates[c] = cand[c];
+      if (c > 0 && cand[c] == cand[c - 1]) {
+        e.ms[c] = e.ms[c - 1];
+        continue;
+      }
+      FusedPlan fp;
+      if (!build_fused_plan(h, fp, cand[c])) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "no fused plan");
+      gp.alloc((size_t)(std::max(kGatherBlocks, fp.n_units) + h->n_sub + 8) * sizeof(double), st);
+      launch_fused<T>(h, fp, zero.as<double>(), 1, sc.as<double>(), gp.as<double>());
+      CUDA_CHECK(cudaEventRecord(a, st));
+      for (int r = 0; r < 3; ++r)
+        launch_fused<T>(h, fp, zero.as<double>(), 1, sc.as<double>(), gp.as<double>());
+      CUDA_CHECK(cudaEventRecord(b, st));
+      CUDA_CHECK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      CUDA_CHECK(cudaEventElapsedTime(&ms, a, b));
+      e.ms[c] = ms / 3.0;
+      if (e.ms[c] < best) {
+        best = e.ms[c];
+        e.unit_rows = cand[c];
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    throw;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  check_launch("autotune");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.emplace(key, e);
+  return g_tune.at(key).unit_rows;
+}
+
 template <class T>
 void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   cudaStream_t st = h->stream;
@@ -2748,7 +2843,9 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
 
   // fused single-pass iteration (M t and M^T u' in one read of the panels)
   FusedPlan fp;
-  const bool fused = build_fused_plan(h, fp);
+  const int tuned_rows = o->autotune && h->max_cover <= 32 && K <= 128
+                             ? autotune_unit_rows<T>(h) : 0;
+  const bool fused = build_fused_plan(h, fp, tuned_rows);
   DevBuf& dunits = fp.units;
   DevBuf& dfo = fp.fo;
   DevBuf& dfe = fp.fe;
@@ -3429,4 +3526,15 @@ void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part) {
       h->d_R.as<double>(), h->d_R.as<double>() + h->n_sub * KK, K, r, z, dot_part);
   check_launch("k_bj_apply");
   count_launch(h);
+}
+
+extern "C" int elmfb_tuning_table(int max, elmfb_tuning_entry* out) {
+  if (max < 0 || (max > 0 && !out)) return -ELMFB_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  int n = 0;
+  for (const auto& kv : g_tune) {
+    if (n < max) out[n] = kv.second;
+    ++n;
+  }
+  return n;
 }

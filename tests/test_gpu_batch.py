@@ -118,3 +118,35 @@ def test_graph_replay_equals_launch_by_launch(prec):
     assert out[0][1] == out[1][1] == 57
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][2] == out[1][2]
+
+
+def test_autotuner_keeps_one_choice_per_shape_class():
+    """`autotune` times the fused pass at three work-unit sizes on the first
+    solve of a shape class and keeps the fastest: the table gains one entry
+    for the class, whose choice is one of its candidates, a second solve of
+    the same class adds none, and the tuned solve still meets the solution
+    bar of the untuned one (the unit size only regroups partial sums)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "oracle_errors.json")))["poisson2d_L1-4_K64_N60"]
+    P = WL.poisson2d(levels=(1, 2, 4), features=64, n_side=60, n_boundary_side=60)
+    before = E.tuning_table()
+    errs = []
+    for _ in range(2):
+        with E.Solver.from_problem(P, precision=E.FP32) as s:
+            s.assemble_problem(P)
+            s.solve(max_iter=4000, atol=0.0, btol=0.0, ntol=1e-6, shift=1e-6, autotune=1)
+            errs.append(s.error_norms(s.eval(P.test_points), P.exact(P.test_points))["rel_l2"])
+        if _ == 0:
+            after_first = E.tuning_table()
+    after = E.tuning_table()
+    new = [e for e in after_first if e not in before]
+    print("tuning entries:", new, "errors:", errs)
+    assert len(after_first) == len(before) + 1 and len(after) == len(after_first)
+    e = new[0]
+    assert e["features"] == 64 and e["precision"] == E.FP32
+    assert e["unit_rows"] in e["candidates"]
+    assert e["ms"][e["candidates"].index(e["unit_rows"])] == min(e["ms"])
+    assert errs[0] == errs[1]
+    assert errs[0] <= 1.01 * g["lsqr"]["rel_l2"]
