@@ -243,6 +243,11 @@ struct elmfb_ctx {
   // ELMFB_FP32_DF32: d_panels holds the FP32 panels, d_panels_df the pairs
   DevBuf d_panels_df;
   bool bj_reuse = false;   // LSQR refinement: keep the block-Jacobi factors of the last set-up
+  // batched graphs: a device flag the LSQR loop's kernels read first (nonzero:
+  // return at once); null outside a batched graph
+  const int* skip = nullptr;
+  struct GraphRound* round = nullptr;   // the batch's coordinator (batch.cu), or null
+  int round_slot = -1;
   bool dual() const { return cfg.precision == ELMFB_FP32_DF32; }
   bool fp64() const { return cfg.precision == ELMFB_FP64; }
   bool df32() const { return cfg.precision == ELMFB_DF32; }
@@ -310,6 +315,19 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial = 
                       int n_beta = 0, double* scal = nullptr);
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials
 void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part);  // z = X^T X r
+
+// Batched graphs (batch.cu): the instances of elmfb_batch_solve in graph mode
+// each capture one check interval of their LSQR loop as a CUDA graph; one
+// parent graph holding all of them as independent child nodes is launched
+// once per interval, and an instance that has finished sets its skip flag so
+// that its nodes return at once.
+struct GraphRound;
+// join the rounds with this interval's graph (ownership passes); then step()
+// once per interval; leave() when done (sets the skip flag)
+void round_join(GraphRound* r, int slot, cudaGraph_t g);
+void round_step(GraphRound* r, int slot);
+void round_leave(GraphRound* r, int slot);
+const int* round_skip_flag(GraphRound* r, int slot);
 
 // learned preconditioner (gnn.cu)
 void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);

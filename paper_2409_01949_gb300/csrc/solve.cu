@@ -958,10 +958,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
     const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
-    double* __restrict__ partial, double* __restrict__ norm_partial) {
+    double* __restrict__ partial, double* __restrict__ norm_partial,
+    const int* __restrict__ skip) {
   __shared__ double sd[32][kFusedRows];
   __shared__ double su[kFusedRows];
   __shared__ double red[33];
+  if (skip && *skip) return;   // a finished instance of a batched graph
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
   const int c = un.x;
@@ -1163,7 +1165,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
-    int* __restrict__ flags) {
+    int* __restrict__ flags, const int* __restrict__ skip) {
+  if (skip && *skip) return;   // a finished instance of a batched graph
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
   __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
@@ -1383,7 +1386,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
-    int* __restrict__ flags) {
+    int* __restrict__ flags, const int* __restrict__ skip) {
+  if (skip && *skip) return;   // a finished instance of a batched graph
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
   __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
@@ -1575,7 +1579,8 @@ constexpr int kPanelChunk = 32;
 __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __restrict__ fe,
                                const int2* __restrict__ pch, int K, double* __restrict__ csum,
                                int pairs, const double* __restrict__ beta_partial, int n_beta,
-                               double* __restrict__ scal) {
+                               double* __restrict__ scal, const int* __restrict__ skip) {
+  if (skip && *skip) return;   // a finished instance of a batched graph
   __shared__ int ent[kPanelChunk];
   // block 0, LSQR: commit the scalars staged by the previous update (no kernel
   // of the iteration reads the committed slots before this point), then
@@ -2183,8 +2188,9 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
     int K, double* __restrict__ v, double* __restrict__ w, double* __restrict__ x,
     double* __restrict__ scal, int init, double* __restrict__ norm_partial,
     double* __restrict__ t, void* __restrict__ tlow, int low_kind,
-    unsigned int* __restrict__ counter, int* __restrict__ flags) {
+    unsigned int* __restrict__ counter, int* __restrict__ flags, const int* __restrict__ skip) {
   extern __shared__ __align__(16) unsigned char trsm[];
+  if (skip && *skip) return;   // a finished instance of a batched graph
   __shared__ double red[33];
   __shared__ int last;
   TriSmem sm(trsm, K);
@@ -2391,7 +2397,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
         h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), h->d_cover_off.as<int>(),        \
         h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(),    \
         scal, h->d_u.as<double>(), h->d_h.as<double>(), mode, fp.part.as<double>(), gpart, S,   \
-        mmax, h->d_flags.as<int>());                                                            \
+        mmax, h->d_flags.as<int>(), h->skip);                                                            \
   }
     ELMFB_FD(1) ELMFB_FD(2) ELMFB_FD(3) ELMFB_FD(4)
 #undef ELMFB_FD
@@ -2443,7 +2449,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
         h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
-        fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>());                           \
+        fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>(), h->skip);                           \
   } else
 #define ELMFB_FT(F) ELMFB_FTR(F, 4) ELMFB_FTR(F, 8)
     ELMFB_FT(1) ELMFB_FT(2) ELMFB_FT(3) ELMFB_FT(4)
@@ -2457,7 +2463,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),      \
         h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
-        fp.part.as<double>(), gpart);                                                        \
+        fp.part.as<double>(), gpart, h->skip);                                               \
   } else
 #define ELMFB_FU4(F) ELMFB_FU(F, 256) ELMFB_FU(F, 512) ELMFB_FU(F, 640) ELMFB_FU(F, 1024)
   ELMFB_FU4(1) ELMFB_FU4(2) ELMFB_FU4(3) ELMFB_FU4(4)
@@ -2897,7 +2903,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
           fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(),
           h->d_w.as<double>(), h->d_x_sol.as<double>(), scal, init, vpart,
           h->d_tmp.as<double>(), fp.tf.p, low_kind, dcount.as<unsigned int>(),
-          h->d_flags.as<int>());
+          h->d_flags.as<int>(), h->skip);
       prof_end(h, KID_UPDATE);
       return;
     }
@@ -2968,37 +2974,94 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   } gx;
   int g_batch = 0;
   int64_t g_launches = 0;
-  while (it < max_it) {
+  auto capture_interval = [&](int batch_len) {
+    const int64_t l0 = h->launches;
+    cudaGraph_t g = nullptr;
+    CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int b = 0; b < batch_len; ++b) {
+        fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);
+        fused_tail(0);
+      }
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    CUDA_CHECK(cudaStreamEndCapture(st, &g));
+    g_launches = h->launches - l0;   // kernels that count themselves, per replay
+    h->launches = l0;
+    return g;
+  };
+  auto check_scalars = [&]() -> bool {   // true: converged
+    CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    int dflags[4];
+    CUDA_CHECK(cudaMemcpyAsync(dflags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (dflags[3])
+      ELMFB_THROW(ELMFB_ERR_TIMEOUT,
+                  "LSQR iteration: an on-device wait (bulk copy) timed out");
+    if (sc[S_BAD] != 0.0) ELMFB_THROW(ELMFB_ERR_NONFINITE, "non-finite LSQR scalar");
+    const double anorm = std::sqrt(sc[S_ANORM2]);
+    const double rn = sc[S_RNORM], arn = sc[S_ARNORM];
+    const bool t1 = o->btol > 0.0 && rn <= o->btol * sc[S_BNORM];
+    const bool t2 = o->atol > 0.0 && anorm > 0.0 && rn > 0.0 && arn <= o->atol * anorm * rn;
+    const bool t3 = o->ntol > 0.0 && arn <= o->ntol * arnorm0;
+    return t1 || t2 || t3 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0;
+  };
+  // Batched graph: full intervals in the batch's shared rounds, then leave
+  // (the skip flag turns this instance's nodes into no-ops) and finish any
+  // remainder below launch by launch.  Only the FP32-pair tail, whose kernels
+  // all take the skip flag, joins the rounds.
+  const bool in_rounds = use_graph && h->round && xpairs && o->check_every <= max_it;
+  if (in_rounds) {
+    struct Leave {   // leave the rounds on every exit, errors included
+      elmfb_ctx* h;
+      bool joined = false;
+      ~Leave() {
+        if (joined) round_leave(h->round, h->round_slot);
+        h->skip = nullptr;
+      }
+    } lv{h};
+    h->skip = round_skip_flag(h->round, h->round_slot);
+    cudaGraph_t g = capture_interval(o->check_every);
+    // the rounds run on the batch's own stream: the start-up work on st first
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (se != cudaSuccess) {
+      cudaGraphDestroy(g);
+      CUDA_CHECK(se);
+    }
+    round_join(h->round, h->round_slot, g);
+    lv.joined = true;
+    while (it + o->check_every <= max_it) {
+      round_step(h->round, h->round_slot);
+      h->launches += g_launches;
+      count_launch(h, tail_launches * o->check_every);
+      it += o->check_every;
+      if (check_scalars()) {
+        status = ELMFB_OK;
+        break;
+      }
+    }
+  }
+  while (it < max_it && status != ELMFB_OK) {
     int batch = std::min(o->check_every, max_it - it);
-    if (use_graph) {
+    if (use_graph && !in_rounds) {
       if (!gx.e || batch != g_batch) {
         if (gx.e) CUDA_CHECK(cudaGraphExecDestroy(gx.e));
         gx.e = nullptr;
-        const int64_t l0 = h->launches;
-        cudaGraph_t g = nullptr;
-        CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        try {
-          for (int b = 0; b < batch; ++b) {
-            fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);
-            fused_tail(0);
-          }
-        } catch (...) {
-          cudaStreamEndCapture(st, &g);
-          if (g) cudaGraphDestroy(g);
-          throw;
-        }
-        CUDA_CHECK(cudaStreamEndCapture(st, &g));
+        cudaGraph_t g = capture_interval(batch);
         const cudaError_t ie = cudaGraphInstantiate(&gx.e, g, 0);
         cudaGraphDestroy(g);
         CUDA_CHECK(ie);
         g_batch = batch;
-        g_launches = h->launches - l0;   // kernels that count themselves, per replay
-        h->launches = l0;
       }
       CUDA_CHECK(cudaGraphLaunch(gx.e, st));
       h->launches += g_launches;
     }
-    for (int b = 0; b < batch && !use_graph; ++b) {
+    const bool graphed = use_graph && !in_rounds;
+    for (int b = 0; b < batch && !graphed; ++b) {
       if (fused) {
         // t (and its low-precision copy) come from the previous iteration's tail
         fused_step(h->d_tmp.as<double>(), fmode, low_kind ? fp.tf.p : nullptr);
@@ -3017,21 +3080,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     count_launch(h, (fused ? tail_launches : 5) * batch);
     it += batch;
     check_launch("lsqr iteration");
-    CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
-                               st));
-    int dflags[4];
-    CUDA_CHECK(cudaMemcpyAsync(dflags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
-    if (dflags[3])
-      ELMFB_THROW(ELMFB_ERR_TIMEOUT,
-                  "LSQR iteration: an on-device wait (bulk copy or grid barrier) timed out");
-    if (sc[S_BAD] != 0.0) ELMFB_THROW(ELMFB_ERR_NONFINITE, "non-finite LSQR scalar");
-    const double anorm = std::sqrt(sc[S_ANORM2]);
-    const double rn = sc[S_RNORM], arn = sc[S_ARNORM];
-    const bool t1 = o->btol > 0.0 && rn <= o->btol * sc[S_BNORM];
-    const bool t2 = o->atol > 0.0 && anorm > 0.0 && rn > 0.0 && arn <= o->atol * anorm * rn;
-    const bool t3 = o->ntol > 0.0 && arn <= o->ntol * arnorm0;
-    if (t1 || t2 || t3 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0) {
+    if (check_scalars()) {
       status = ELMFB_OK;
       break;
     }
@@ -3504,7 +3553,7 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, i
   const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
   k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(
       fp.part.as<double>(), fp.fe.as<int>(), fp.pch.as<int2>(), h->K, fp.csum.as<double>(),
-      fp.pairs ? 1 : 0, beta_partial, n_beta, scal);
+      fp.pairs ? 1 : 0, beta_partial, n_beta, scal, h->skip);
   check_launch("k_panel_chunks");
   count_launch(h);
 }

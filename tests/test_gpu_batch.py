@@ -55,8 +55,9 @@ def test_batch_errors_match_paper_protocol_on_small_instances():
         assert r.rel_l2 <= 1.01 * e_or
 
 
-def test_sixteen_uncapped_instances_meet_their_oracle():
-    """16 instances of the seed-0 draw of the batched workload, uncapped:
+def test_uncapped_instances_meet_their_oracle():
+    """The instances of the seed-0 draw of the batched workload, uncapped,
+    that tests/golden/batch_errors.json holds (up to 16):
     n_sub 2..32, K 32/64/128, grid sides 64..511 (tests/golden/batch_errors.json,
     written by tests/golden/make_batch_errors.py from the oracle alone).
     Instances the oracle solves by QR (at most 4096 columns) go through
@@ -76,8 +77,6 @@ def test_sixteen_uncapped_instances_meet_their_oracle():
     for key, rec in sorted(gold.items(), key=lambda kv: int(kv[0])):
         i = int(key)
         groups[rec["oracle"]["kind"]].append((i, WL.batch_instance(specs[i], i, 0), rec))
-    if sum(len(v) for v in groups.values()) < 16:
-        pytest.skip("batch_errors.json holds fewer than 16 instances (still being written)")
     runs = {
         "qr": (E.FP64, E.default_solve_opts(method=E.SOLVE_QR)),
         "lsqr15000": (E.FP32, E.default_solve_opts(max_iter=20000, atol=0.0, btol=0.0, ntol=1e-6,
@@ -118,6 +117,35 @@ def test_graph_replay_equals_launch_by_launch(prec):
     assert out[0][1] == out[1][1] == 57
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("prec", [E.FP32, E.DF32])
+def test_batched_graph_rounds_equal_one_by_one(prec):
+    """elmfb_batch_solve with `graph`: the members' check intervals run as the
+    child nodes of one parent graph launch per round, finished members turned
+    into no-ops by their skip flags, and a worker's next instance joining its
+    old slot after a rebuild.  Every instance still runs its own kernels in
+    its own order: bitwise the coefficients, u_hat and iteration counts of
+    launching them one by one, with instances that stop at different rounds
+    (the normal-residual test) and a last interval shorter than check_every."""
+    probs = _instances(9, cap_side=64, cap_sub=5, seed=1)
+    if prec == E.DF32:
+        probs = [P for P in probs if P.features <= 64][:5]
+    out = {}
+    for graph in (0, 1):
+        opts = E.default_solve_opts(max_iter=157, atol=0.0, btol=0.0, ntol=3e-3, shift=1e-6,
+                                    check_every=10, graph=graph)
+        res, uh, co = E.batch_solve(probs, precision=prec, n_workers=3, opts=opts, coeffs=True)
+        assert all(r.status == E.OK for r in res)
+        out[graph] = ([r.iterations for r in res], uh, co)
+    its = out[0][0]
+    print("iterations per instance:", its)
+    assert its == out[1][0]
+    assert len(set(its)) > 1     # members leave at different rounds
+    for a0, a1 in zip(out[0][2], out[1][2]):
+        assert np.array_equal(a0, a1)
+    for u0, u1 in zip(out[0][1], out[1][1]):
+        assert np.array_equal(u0, u1)
 
 
 def test_autotuner_keeps_one_choice_per_shape_class():
