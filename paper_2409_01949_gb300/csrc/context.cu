@@ -340,7 +340,7 @@ cudaMemPool_t library_pool() {
   return pool;
 }
 
-void ensure_dyn_smem(const void* func, size_t bytes) {
+void ensure_dyn_smem(const void* func, size_t bytes, bool max_carveout) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> limit;
   int dev = 0;
@@ -350,6 +350,9 @@ void ensure_dyn_smem(const void* func, size_t bytes) {
   // least 48 KB of dynamic memory whenever a kernel asks
   const size_t want = std::max<size_t>(bytes, 48 * 1024);
   size_t& cur = limit[{dev, func}];
+  if (cur == 0 && max_carveout)   // several CTAs of it share an SM's shared memory
+    CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
   if (want <= cur) return;
   CUDA_CHECK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want));
   cur = want;

@@ -290,6 +290,7 @@ struct FusedPlan {
   DevBuf pch, pco, csum;   // per-panel slices of the partial list and their sums
   int n_pchunks = 0;
   int n_units = 0;
+  int max_unit_rows = 0;   // rows of the largest unit (its u values are staged in smem)
   int threads = 0;
   bool pairs = false;   // partials are FP32 (hi, lo) pairs, value hi - lo
 };
@@ -357,4 +358,4 @@ int64_t count_gram_pairs(const elmfb_ctx* h);   // pairs (i <= j) sharing a cell
 // Raise, never lower, a kernel's dynamic shared-memory limit on the current
 // device.  The attribute is process-wide, so handles solving concurrently in
 // other threads only ever see it grow.
-void ensure_dyn_smem(const void* func, size_t bytes);
+void ensure_dyn_smem(const void* func, size_t bytes, bool max_carveout = false);

@@ -2304,6 +2304,8 @@ bool build_fused_plan(elmfb_ctx* h, FusedPlan& fp, int unit_rows) {
     }
   }
   fp.n_units = (int)units.size();
+  fp.max_unit_rows = 0;
+  for (const int4& u4 : units) fp.max_unit_rows = std::max(fp.max_unit_rows, u4.z - u4.y);
   std::vector<int> fo(h->n_sub + 1, 0), fe;
   fe.reserve(pbase);
   for (int s2 = 0; s2 < h->n_sub; ++s2) {
@@ -2360,6 +2362,31 @@ static size_t fused_ring_budget() {
     return (size_t)(v >= 64 && v <= 220 ? v : 220);
   }();
   return kb * 1024;
+}
+
+// Shared memory per CTA of k_fused_pipe when several CTAs share an SM.  A
+// CTA's chunk chain (copy in, the per-row dots, u', the M^T u' update) is
+// latency-bound and one chunk carries the rows of all m covering panels, so a
+// CTA streams about m times faster with m panels: with few panels per cell,
+// several CTAs per SM, each keeping four 8-row stages (2-D single-level cells,
+// 4 panels of K = 128 FP32: 2.98 TB/s at one CTA per SM, 5.3 TB/s at three);
+// the multilevel workloads' 17 panels stay at one.  ELMFB_FUSED_SMEM_KB fixes
+// the one-CTA budget instead, ELMFB_FUSED_CTAS the number of CTAs (tuning
+// knobs: both change timing only).
+constexpr size_t kSmemPerSM = 228 * 1024;
+constexpr size_t kCtaSmemReserve = 4096;   // the kernel's static arrays and the per-CTA reserve
+static size_t fused_pipe_budget(int mmax, int K, size_t elem, size_t u_bytes, int threads) {
+  if (getenv("ELMFB_FUSED_SMEM_KB")) return fused_ring_budget();
+  const char* e = getenv("ELMFB_FUSED_CTAS");
+  const int force = e ? atoi(e) : 0;
+  if (force == 1) return fused_ring_budget();
+  const size_t stage8 = std::max<size_t>((size_t)mmax * 8 * K * elem, 1);
+  for (int n = 4; n >= 2; --n) {
+    if ((force && n != force) || threads * n > 2048) continue;
+    const size_t b = kSmemPerSM / n - kCtaSmemReserve;
+    if (b > u_bytes && (b - u_bytes) / stage8 >= 4) return b;
+  }
+  return fused_ring_budget();
 }
 
 template <class T>
@@ -2421,10 +2448,14 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
   prof_begin(h, KID_FUSED, (double)h->NPR * K * sizeof(T) + 16.0 * h->NR + 8.0 * h->NPhi);
   // bulk-copy ring: S stages of (covering panels x kPipeRows rows x K) elements
   const int mmax = std::max(1, h->max_cover);
-  const size_t u_bytes = kMaxUnitRows * sizeof(double);
+  // the unit's u values, staged after the ring (16-byte aligned for the copy)
+  const size_t u_bytes =
+      ((size_t)std::max(8, std::min(fp.max_unit_rows, kMaxUnitRows)) * sizeof(double) + 15) &
+      ~size_t(15);
+  const size_t budget = fused_pipe_budget(mmax, K, sizeof(T), u_bytes, fthreads + 64);
   auto stages_for = [&](int r) {
     const size_t sb = std::max<size_t>((size_t)mmax * r * K * sizeof(T), 1);
-    return (int)std::min<size_t>(kPipeMaxStages, (fused_ring_budget() - u_bytes) / sb);
+    return (int)std::min<size_t>(kPipeMaxStages, (budget - u_bytes) / sb);
   };
   // rows per chunk: 8 while the ring still holds three such stages (fewer,
   // larger copies and half the per-chunk synchronisation; on the 2-D
@@ -2444,7 +2475,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     const size_t smem = (size_t)S * stage_bytes + u_bytes;
 #define ELMFB_FTR(F, R)                                                                        \
   if (fpl == F && rows == R) {                                                                 \
-    ensure_dyn_smem((const void*)k_fused_pipe<T, F, R>, smem);                                \
+    ensure_dyn_smem((const void*)k_fused_pipe<T, F, R>, smem, true);                          \
     k_fused_pipe<T, F, R><<<fp.n_units, pthreads, smem, st>>>(                                 \
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
