@@ -277,6 +277,20 @@ typedef struct {
                           per check_every iterations); needs a handle stream
                           other than the legacy default stream and profiling
                           off, else the kernels are launched one by one     */
+  int batch_shared;    /* elmfb_batch_solve, LSQR on FP32 panels with
+                          block-Jacobi: nonzero (the default) runs the
+                          instances' iterations in shared multi-instance
+                          launches; 0 launches each instance's kernels alone.
+                          Results are the same either way               */
+  double drop_tol;     /* block-Jacobi: 0 (the default) keeps every column;
+                          > 0 drops a column of a block whose Cholesky pivot
+                          (its Schur complement) is at most drop_tol times its
+                          shifted diagonal, i.e. one numerically dependent on
+                          the block's earlier columns; its coefficient stays 0
+                          (info->precond_dropped counts them).  For FP32
+                          panels on under-resolved subdomains (fewer
+                          collocation points than features), whose Gram
+                          blocks are singular up to FP32 rounding        */
 } elmfb_solve_opts;
 
 typedef struct {
@@ -296,11 +310,13 @@ typedef struct {
                                  below, sigma_min from above: kappa(B_k) <=
                                  kappa(M P)); QR, |R_11| and |R_rr|; else 0  */
   double sigma_min;
+  int precond_dropped;        /* block-Jacobi with drop_tol: columns dropped  */
 } elmfb_solve_info;
 
 /* Fill opts with the defaults: LSQR, block-Jacobi, max_iter 15000,
  * atol = btol = 1e-10, shift 1e-12, check_every 50, cold start, refine 1,
- * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2, autotune 0, graph 0. */
+ * gram_shift 0, rcond 1e-13, ntol 0, coarse_levels 2, autotune 0, graph 0,
+ * batch_shared 1, drop_tol 0. */
 void elmfb_default_solve_opts(elmfb_solve_opts* opts);
 
 /* Solve min ||M a - h|| for the coefficients a (paper Eq. multilevel_ls; the
@@ -359,12 +375,18 @@ int elmfb_gnn_train(elmfb_t h, int n_rhs, const double* rhs, int solve_iters, in
 /* ---- batched solves (not in the paper) ---------------------------------------
  * Solve many independent instances: each item is a full problem (create
  * config + row sets), optionally with evaluation points, an output buffer
- * for u_hat and reference values for the error norms.  n_workers host
- * threads, each with its own non-blocking stream, take the instances in
- * decreasing order of estimated work; all use the same solver options.
- * Results are identical to solving the instances one by one.  Returns the
- * first non-OK instance status (NOT_CONVERGED counts as OK), else ELMFB_OK.
- * Pointers may be host or device memory, as elsewhere. */
+ * for u_hat and reference values for the error norms.  n_workers (1..256)
+ * host threads, each with its own non-blocking stream, take the instances in
+ * decreasing order of estimated work; each uses its item's solver options,
+ * else the batch's (opts->batch_shared is taken from the batch's).  With
+ * opts->batch_shared, the LSQR iterations of the instances that are
+ * iterating at the same time (FP32 panels, block-Jacobi) run as shared
+ * launches: one fused pass, one slice-sum and one tail launch per iteration
+ * and launch shape over all of them, every check_every iterations a check of
+ * each instance's own stopping tests.  Results are identical to solving the
+ * instances one by one.  Returns the first non-OK instance status
+ * (NOT_CONVERGED counts as OK), else ELMFB_OK.  Pointers may be host or
+ * device memory, as elsewhere. */
 typedef struct {
   elmfb_config cfg;
   int n_sets;
@@ -374,6 +396,8 @@ typedef struct {
   double* eval_out;           /* [n_eval] u_hat                          */
   const double* eval_ref;     /* [n_eval] reference values, or NULL      */
   double* coeffs_out;         /* [N_Phi] coefficients, or NULL           */
+  const elmfb_solve_opts* opts;  /* this instance's solver options, or NULL
+                                    for the batch's                      */
 } elmfb_batch_item;
 typedef struct {
   int status;

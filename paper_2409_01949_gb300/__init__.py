@@ -67,13 +67,14 @@ class SolveOpts(C.Structure):
                 ("atol", C.c_double), ("btol", C.c_double), ("shift", C.c_double),
                 ("check_every", C.c_int), ("warm_start", C.c_int), ("refine", C.c_int),
                 ("gram_shift", C.c_double), ("rcond", C.c_double), ("ntol", C.c_double),
-                ("coarse_levels", C.c_int), ("autotune", C.c_int), ("graph", C.c_int)]
+                ("coarse_levels", C.c_int), ("autotune", C.c_int), ("graph", C.c_int),
+                ("batch_shared", C.c_int), ("drop_tol", C.c_double)]
 
 
 class BatchItem(C.Structure):
     _fields_ = [("cfg", Config), ("n_sets", C.c_int), ("sets", C.c_void_p), ("n_eval", C.c_int64),
                 ("eval_points", C.c_void_p), ("eval_out", C.c_void_p), ("eval_ref", C.c_void_p),
-                ("coeffs_out", C.c_void_p)]
+                ("coeffs_out", C.c_void_p), ("opts", C.c_void_p)]
 
 
 class BatchResult(C.Structure):
@@ -86,7 +87,8 @@ class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("residual_norm", C.c_double),
                 ("normal_residual_norm", C.c_double), ("setup_ms", C.c_double),
                 ("solve_ms", C.c_double), ("precond_retries", C.c_int), ("rank", C.c_int),
-                ("sigma_max", C.c_double), ("sigma_min", C.c_double)]
+                ("sigma_max", C.c_double), ("sigma_min", C.c_double),
+                ("precond_dropped", C.c_int)]
 
 
 class TuningEntry(C.Structure):
@@ -264,8 +266,10 @@ def trim_memory(device: int = -1):
         raise ElmfbError(rc, "trim_memory failed")
 
 
-def batch_solve(problems, precision=FP32, n_workers=8, opts=None, evaluate=True, coeffs=False):
-    """Solve independent problems with elmfb_batch_solve.
+def batch_solve(problems, precision=FP32, n_workers=8, opts=None, evaluate=True, coeffs=False,
+                item_opts=None):
+    """Solve independent problems with elmfb_batch_solve; item_opts (a list
+    with a SolveOpts or None per problem) overrides `opts` per instance.
 
     Returns (results, u_hat list, coefficient list)."""
     n = len(problems)
@@ -291,6 +295,9 @@ def batch_solve(problems, precision=FP32, n_workers=8, opts=None, evaluate=True,
             a = np.zeros(P.n_columns)
             items[i].coeffs_out = a.ctypes.data
             cos.append(a)
+        if item_opts is not None and item_opts[i] is not None:
+            keep.append(item_opts[i])
+            items[i].opts = C.cast(C.pointer(item_opts[i]), C.c_void_p)
     res = (BatchResult * n)()
     o = opts if opts is not None else default_solve_opts()
     rc = lib().elmfb_batch_solve(n, items, C.byref(o), n_workers, res)

@@ -5,78 +5,140 @@
 // owning a non-blocking CUDA stream, takes instances from a shared counter in
 // decreasing order of estimated work (rows x covering panels x K), so the
 // GPU is kept busy by several instances at once and the long instances start
-// first.  Results are independent of the schedule: every instance's kernels
-// are deterministic and touch only that instance's buffers.
+// first.
 //
-// Graph mode (opts->graph): besides capturing its check intervals, every
-// instance in its LSQR loop joins shared rounds.  Each round is ONE launch of
-// a parent graph whose independent child nodes are the current members'
-// captured intervals, so the GPU runs the members' small kernels side by
-// side instead of one instance's launches at a time.  A member reads its
-// scalars after every round and leaves on convergence, at its iteration cap
-// or on an error; its device skip flag then turns its nodes into no-ops (every
-// kernel of the interval reads the flag first), so the parent is rebuilt only
-// when a new member joins.  A rebuild keeps only the members' nodes, so a
-// slot is reused by the next instance of the same worker only after the old
-// nodes are gone.
+// Multi-instance launches: an instance that iterates on FP32 panels with the
+// FP32-pair tail joins shared rounds once its start-up step is done.  A
+// round runs check_every LSQR iterations of every member, each iteration as
+// three launches per launch shape (members of different K run on their own
+// streams side by side): the fused pass over all members' units, the slice
+// sums over all their slices, the tail over all their panels.  So the many
+// small per-instance kernels become a few large ones that fill the GPU.  The
+// last member to arrive at a round launches it; each member then reads its
+// own scalars and leaves on convergence, at its iteration cap or on an
+// error, after which the next round's maps are rebuilt without it.
+//
+// Results are independent of the schedule: every block of a shared launch
+// does what it does in the instance's own launch, on that instance's arrays
+// only, and each instance's kernels run in the same order.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 
 #include "elmfb_internal.cuh"
 
-struct GraphRound {
+struct BatchRound {
+  struct Member {
+    BatchInst inst{};
+    BatchShape shape;
+    int64_t launches = 0;   // shared launches attributed to this member, not yet reported
+  };
+  // one launch shape's members and their block maps
+  struct Class {
+    BatchShape shape;
+    cudaStream_t stream = nullptr;
+    std::vector<BatchInst> h_inst;
+    std::vector<int2> h_fmap, h_cmap, h_tmap;
+    DevBuf inst, fmap, cmap, tmap;
+    int first_slot = -1;
+  };
   std::mutex m;
   std::condition_variable cv;
-  int n_slots = 0;
-  cudaStream_t stream = nullptr;
-  int* d_skip = nullptr;              // one flag per slot, on the device
-  std::vector<cudaGraph_t> child;     // slot -> its member's interval (owned)
-  std::vector<char> member;           // slot joined and not yet left
-  std::vector<char> in_exec;          // slot's nodes are in the instantiated parent
-  bool dirty = false;                 // membership grew since the last build
+  int check_every = 1;
+  std::vector<Member> slot;
+  std::vector<char> member;
+  std::vector<cudaStream_t> streams;   // one per class in use, kept across rebuilds
+  std::vector<std::unique_ptr<Class>> classes;
+  bool dirty = false;
   int members = 0, arrived = 0;
-  uint64_t gen = 0;                   // rounds completed
-  cudaGraphExec_t exec = nullptr;
-  cudaError_t err = cudaSuccess;
-  int64_t rounds = 0, builds = 0;
+  uint64_t gen = 0;
+  int err = ELMFB_OK;
+  std::string msg;
+  int64_t rounds = 0, rebuilds = 0;
 
-  // Rebuild if needed, launch, wait; then release the waiting members.
-  // Called with the lock held by the last member to arrive.
-  void run_locked() {
-    if (err == cudaSuccess) {
-      cudaError_t e = cudaSuccess;
-      if (dirty) {
-        if (exec) cudaGraphExecDestroy(exec);
-        exec = nullptr;
-        cudaGraph_t parent = nullptr;
-        e = cudaGraphCreate(&parent, 0);
-        for (int s = 0; s < n_slots && e == cudaSuccess; ++s) {
-          if (!member[s]) continue;
-          cudaGraphNode_t nd;
-          e = cudaGraphAddChildGraphNode(&nd, parent, nullptr, 0, child[s]);
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, 0);
-        if (parent) cudaGraphDestroy(parent);
-        std::vector<int> flags(n_slots);
-        for (int s = 0; s < n_slots; ++s) {
-          in_exec[s] = member[s] && e == cudaSuccess;
-          flags[s] = member[s] ? 0 : 1;
-        }
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(d_skip, flags.data(), n_slots * sizeof(int), cudaMemcpyHostToDevice,
-                              stream);
-        dirty = false;
-        ++builds;
+  void rebuild() {
+    // members by launch shape, each shape's members dealt round-robin to up
+    // to kGroups groups on their own streams, so that one group's tail (a
+    // latency-bound kernel) overlaps another's fused pass
+    constexpr int kGroups = 4;
+    std::map<BatchShape, std::vector<int>> by_shape;
+    for (int q = 0; q < (int)slot.size(); ++q)
+      if (member[q]) by_shape[slot[q].shape].push_back(q);
+    std::vector<std::pair<BatchShape, std::vector<int>>> groups;
+    for (auto& g : by_shape) {
+      const int ng = std::min<int>(kGroups, (int)g.second.size());
+      for (int a = 0; a < ng; ++a) {
+        std::vector<int> part;
+        for (int j = a; j < (int)g.second.size(); j += ng) part.push_back(g.second[j]);
+        groups.emplace_back(g.first, std::move(part));
       }
-      if (e == cudaSuccess) e = cudaGraphLaunch(exec, stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-      err = e;
-      ++rounds;
+    }
+    // drop the old maps only after the streams are idle (they are: rounds
+    // end with a synchronisation)
+    classes.clear();
+    int c = 0;
+    for (auto& g : groups) {
+      if ((int)streams.size() <= c) {
+        cudaStream_t st = nullptr;
+        CUDA_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        streams.push_back(st);
+      }
+      classes.push_back(std::make_unique<Class>());
+      Class& k = *classes.back();
+      k.shape = g.first;
+      k.stream = streams[c];
+      k.first_slot = g.second.front();
+      for (int j = 0; j < (int)g.second.size(); ++j) {
+        const BatchInst& bi = slot[g.second[j]].inst;
+        k.h_inst.push_back(bi);
+        for (int u = 0; u < bi.n_units; ++u) k.h_fmap.push_back(make_int2(j, u));
+        for (int q = 0; q < bi.n_pchunks; ++q) k.h_cmap.push_back(make_int2(j, q));
+        for (int p = 0; p < bi.n_sub; ++p) k.h_tmap.push_back(make_int2(j, p));
+      }
+      auto put = [&](DevBuf& d, const void* src, size_t bytes) {
+        d.alloc(bytes, k.stream);
+        CUDA_CHECK(cudaMemcpyAsync(d.p, src, bytes, cudaMemcpyHostToDevice, k.stream));
+      };
+      put(k.inst, k.h_inst.data(), k.h_inst.size() * sizeof(BatchInst));
+      put(k.fmap, k.h_fmap.data(), k.h_fmap.size() * sizeof(int2));
+      put(k.cmap, k.h_cmap.data(), k.h_cmap.size() * sizeof(int2));
+      put(k.tmap, k.h_tmap.data(), k.h_tmap.size() * sizeof(int2));
+      ++c;
+    }
+    dirty = false;
+    ++rebuilds;
+  }
+
+  // Launch one round and wait for it; then release the waiting members.
+  // Called with the lock held by the last member to arrive (or to leave).
+  void run_locked() {
+    if (err == ELMFB_OK) {
+      try {
+        if (dirty) rebuild();
+        for (int i = 0; i < check_every; ++i)
+          for (auto& k : classes)
+            launch_batch_iteration(k->shape, k->inst.as<BatchInst>(), k->fmap.as<int2>(),
+                                   (int)k->h_fmap.size(), k->cmap.as<int2>(),
+                                   (int)k->h_cmap.size(), k->tmap.as<int2>(),
+                                   (int)k->h_tmap.size(), k->stream);
+        for (auto& k : classes) {
+          CUDA_CHECK(cudaStreamSynchronize(k->stream));
+          slot[k->first_slot].launches += 3 * (int64_t)check_every;
+        }
+        ++rounds;
+      } catch (const elmfb_error& e) {
+        err = e.code;
+        msg = e.msg;
+      } catch (...) {
+        err = ELMFB_ERR_CUDA;
+        msg = "unexpected error";
+      }
     }
     arrived = 0;
     ++gen;
@@ -84,20 +146,19 @@ struct GraphRound {
   }
 };
 
-void round_join(GraphRound* r, int slot, cudaGraph_t g) {
+void round_join(BatchRound* r, int q, const BatchInst& inst, const BatchShape& shape) {
   std::lock_guard<std::mutex> lk(r->m);
-  if (r->child[slot]) cudaGraphDestroy(r->child[slot]);
-  r->child[slot] = g;
-  r->member[slot] = 1;
+  r->slot[q].inst = inst;
+  r->slot[q].shape = shape;
+  r->slot[q].launches = 0;
+  r->member[q] = 1;
   ++r->members;
   r->dirty = true;
 }
 
-void round_step(GraphRound* r, int slot) {
-  (void)slot;
+int64_t round_step(BatchRound* r, int q) {
   std::unique_lock<std::mutex> lk(r->m);
-  if (r->err != cudaSuccess)
-    ELMFB_THROW(ELMFB_ERR_CUDA, std::string("batched graph round: ") + cudaGetErrorString(r->err));
+  if (r->err != ELMFB_OK) ELMFB_THROW(r->err, "multi-instance round: " + r->msg);
   ++r->arrived;
   if (r->arrived == r->members) {
     r->run_locked();
@@ -107,37 +168,30 @@ void round_step(GraphRound* r, int slot) {
     // round; the bound only turns a host-side fault into an error
     if (!r->cv.wait_for(lk, std::chrono::seconds(600), [&] { return r->gen != g0; })) {
       --r->arrived;
-      ELMFB_THROW(ELMFB_ERR_TIMEOUT, "batched graph round: the other members did not arrive");
+      ELMFB_THROW(ELMFB_ERR_TIMEOUT, "multi-instance round: the other members did not arrive");
     }
   }
-  if (r->err != cudaSuccess)
-    ELMFB_THROW(ELMFB_ERR_CUDA, std::string("batched graph round: ") + cudaGetErrorString(r->err));
+  if (r->err != ELMFB_OK) ELMFB_THROW(r->err, "multi-instance round: " + r->msg);
+  const int64_t n = r->slot[q].launches;
+  r->slot[q].launches = 0;
+  return n;
 }
 
-void round_leave(GraphRound* r, int slot) {
+int round_interval(const BatchRound* r) { return r->check_every; }
+
+void round_leave(BatchRound* r, int q) {
   std::lock_guard<std::mutex> lk(r->m);
-  if (!r->member[slot]) return;
-  r->member[slot] = 0;
+  if (!r->member[q]) return;
+  r->member[q] = 0;
   --r->members;
-  if (r->child[slot]) cudaGraphDestroy(r->child[slot]);   // the parent holds its own copy
-  r->child[slot] = nullptr;
-  if (r->in_exec[slot] && r->err == cudaSuccess) {
-    // no round runs while the lock is held: the flag is set before the next one
-    static const int one = 1;
-    cudaError_t e = cudaMemcpyAsync(r->d_skip + slot, &one, sizeof(int), cudaMemcpyHostToDevice,
-                                    r->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
-    if (e != cudaSuccess) r->err = e;
-  }
+  r->dirty = true;
   if (r->members > 0 && r->arrived == r->members) r->run_locked();
 }
-
-const int* round_skip_flag(GraphRound* r, int slot) { return r->d_skip + slot; }
 
 extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
                                  const elmfb_solve_opts* opts, int n_workers,
                                  elmfb_batch_result* results) {
-  if (n < 0 || (n > 0 && (!items || !results)) || n_workers < 1 || n_workers > 64)
+  if (n < 0 || (n > 0 && (!items || !results)) || n_workers < 1 || n_workers > 256)
     return ELMFB_ERR_INVALID_ARG;
   if (n == 0) return ELMFB_OK;
   int device = 0;
@@ -155,21 +209,11 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
   std::atomic<int> next{0};
   const int w = std::min(n_workers, n);
-  // graph mode: the shared rounds, one slot per worker
-  GraphRound round;
-  const bool rounds = opts && opts->graph;
-  if (rounds) {
-    round.n_slots = w;
-    round.child.assign(w, nullptr);
-    round.member.assign(w, 0);
-    round.in_exec.assign(w, 0);
-    if (cudaStreamCreateWithFlags(&round.stream, cudaStreamNonBlocking) != cudaSuccess)
-      return ELMFB_ERR_CUDA;
-    if (cudaMalloc(&round.d_skip, w * sizeof(int)) != cudaSuccess) {
-      cudaStreamDestroy(round.stream);
-      return ELMFB_ERR_CUDA;
-    }
-  }
+  // the shared rounds, one slot per worker
+  BatchRound round;
+  round.check_every = std::max(1, opts ? opts->check_every : 10);
+  round.slot.resize(w);
+  round.member.assign(w, 0);
   auto worker = [&](int slot) {
     cudaSetDevice(device);
     cudaStream_t st = nullptr;
@@ -189,11 +233,11 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
       if (rc == ELMFB_OK) rc = elmfb_assemble(h, it.n_sets, it.sets);
       elmfb_solve_info info{};
       if (rc == ELMFB_OK) {
-        if (rounds) {
+        if (opts && opts->batch_shared) {
           h->round = &round;
           h->round_slot = slot;
         }
-        rc = elmfb_solve(h, opts, &info);
+        rc = elmfb_solve(h, it.opts ? it.opts : opts, &info);
         h->round = nullptr;
         h->round_slot = -1;
         if (rc == ELMFB_ERR_NOT_CONVERGED) rc = ELMFB_OK;
@@ -229,13 +273,10 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
   std::vector<std::thread> pool;
   for (int t = 0; t < w; ++t) pool.emplace_back(worker, t);
   for (auto& t : pool) t.join();
-  if (rounds) {
-    if (round.exec) cudaGraphExecDestroy(round.exec);
-    for (cudaGraph_t g : round.child)
-      if (g) cudaGraphDestroy(g);
-    cudaStreamSynchronize(round.stream);
-    cudaFree(round.d_skip);
-    cudaStreamDestroy(round.stream);
+  round.classes.clear();
+  for (cudaStream_t st : round.streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
   }
   for (int i = 0; i < n; ++i)
     if (results[i].status != ELMFB_OK) return results[i].status;

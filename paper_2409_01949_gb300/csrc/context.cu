@@ -568,6 +568,8 @@ void elmfb_default_solve_opts(elmfb_solve_opts* o) {
   o->coarse_levels = 2;
   o->autotune = 0;
   o->graph = 0;
+  o->batch_shared = 1;
+  o->drop_tol = 0.0;
 }
 
 int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info) {
@@ -578,7 +580,8 @@ int elmfb_solve(elmfb_t h, const elmfb_solve_opts* opts, elmfb_solve_info* info)
     elmfb_default_solve_opts(&o);
     if (opts) o = *opts;
     if (o.max_iter < 0 || o.check_every < 1 || !(o.shift >= 0.0) || o.refine < 1 ||
-        !(o.gram_shift >= 0.0) || !(o.rcond >= 0.0) || !(o.ntol >= 0.0))
+        !(o.gram_shift >= 0.0) || !(o.rcond >= 0.0) || !(o.ntol >= 0.0) ||
+        !(o.drop_tol >= 0.0 && o.drop_tol < 1.0))
       ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "bad solver options");
     elmfb_solve_info inf{};
     h->gk_alpha.clear();

@@ -237,6 +237,7 @@ struct elmfb_ctx {
   double prof_bytes[KID_COUNT] = {0};   // algorithmic bytes per launch (last launch)
   int prof_stride = 1;                  // time every prof_stride-th launch of a kernel
   int bj_retries = 0;                   // block-Jacobi factorisations redone with a larger shift
+  int bj_dropped = 0;                   // block-Jacobi columns dropped as dependent
   int64_t prof_seen[KID_COUNT] = {0};   // launches seen while profiling
   bool prof_now[KID_COUNT] = {false};   // the current launch carries events
 
@@ -245,8 +246,7 @@ struct elmfb_ctx {
   bool bj_reuse = false;   // LSQR refinement: keep the block-Jacobi factors of the last set-up
   // batched graphs: a device flag the LSQR loop's kernels read first (nonzero:
   // return at once); null outside a batched graph
-  const int* skip = nullptr;
-  struct GraphRound* round = nullptr;   // the batch's coordinator (batch.cu), or null
+  struct BatchRound* round = nullptr;   // the batch's coordinator (batch.cu), or null
   int round_slot = -1;
   bool dual() const { return cfg.precision == ELMFB_FP32_DF32; }
   bool fp64() const { return cfg.precision == ELMFB_FP64; }
@@ -308,7 +308,8 @@ template <class T>
 void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t, int mode, double* scal,
                   double* gpart, const void* tf = nullptr);
 template <class T>
-void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0);
+void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift = 0.0,
+                        double drop = 0.0);
 // fixed slices of each panel's partials; with beta_partial (LSQR) also the
 // commit of the staged scalars and beta^2 into the staged slot that the panel
 // kernels read
@@ -317,18 +318,73 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial = 
 void panel_sum(elmfb_ctx* h, FusedPlan& fp, double* g);               // g_s = sum of partials
 void bj_apply(elmfb_ctx* h, const double* r, double* z, double* dot_part);  // z = X^T X r
 
-// Batched graphs (batch.cu): the instances of elmfb_batch_solve in graph mode
-// each capture one check interval of their LSQR loop as a CUDA graph; one
-// parent graph holding all of them as independent child nodes is launched
-// once per interval, and an instance that has finished sets its skip flag so
-// that its nodes return at once.
-struct GraphRound;
-// join the rounds with this interval's graph (ownership passes); then step()
-// once per interval; leave() when done (sets the skip flag)
-void round_join(GraphRound* r, int slot, cudaGraph_t g);
-void round_step(GraphRound* r, int slot);
-void round_leave(GraphRound* r, int slot);
-const int* round_skip_flag(GraphRound* r, int slot);
+// Multi-instance LSQR launches (batch.cu): the instances of
+// elmfb_batch_solve that iterate on FP32 panels with the FP32-pair tail join
+// shared rounds; one round runs check_every LSQR iterations of every member,
+// each iteration as three launches per launch shape (the fused pass, the
+// slice sums, the tail) whose blocks map to (member, local unit / slice /
+// panel) and read that member's arrays from its BatchInst.  Every block does
+// exactly what it does in the instance's own launch, so each instance's
+// iterates are bitwise those of solving it alone.
+struct BatchInst {
+  // fused pass
+  const float* panels;
+  const float* tlow;   // FP32 copy of t
+  const int4* units;
+  const int* cell_pstart;
+  const int* cell_count;
+  const int* cover_off;
+  const int* cover_sub;
+  const int64_t* entry_base;
+  double* scal;
+  double* u;
+  const double* hvec;
+  double* part;
+  double* gpart;   // per-unit ||u'||^2 partials
+  int* flags;
+  // slice sums
+  const int* fe;
+  const int2* pch;
+  double* csum;
+  // tail
+  const int* pco;
+  const float2* Xt;
+  double* v;
+  double* w;
+  double* x;
+  double* vpart;   // per-panel ||v'||^2 partials
+  double* t;
+  unsigned int* counter;
+  int n_units, n_pchunks, n_sub, pad_;
+};
+// What the members of one multi-instance launch must share.
+struct BatchShape {
+  int K = 0, fpl = 0, rows = 0, S = 0, mmax = 0, pthreads = 0, chunk_threads = 0, low_kind = 0,
+      mode = 0;
+  size_t smem = 0, tsmem = 0;
+  bool operator<(const BatchShape& o) const {
+    const int a[9] = {K, fpl, rows, S, mmax, pthreads, chunk_threads, low_kind, mode};
+    const int b[9] = {o.K, o.fpl, o.rows, o.S, o.mmax, o.pthreads, o.chunk_threads, o.low_kind,
+                      o.mode};
+    for (int i = 0; i < 9; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    if (smem != o.smem) return smem < o.smem;
+    return tsmem < o.tsmem;
+  }
+};
+struct BatchRound;
+// join with the instance's arrays; then round_step() once per check interval
+// (returns the shared launches attributed to this member, each launch to one
+// member); round_leave() when done
+void round_join(BatchRound* r, int slot, const BatchInst& inst, const BatchShape& shape);
+int64_t round_step(BatchRound* r, int slot);
+void round_leave(BatchRound* r, int slot);
+int round_interval(const BatchRound* r);   // iterations per round
+// one LSQR iteration of a launch shape's members: n_f units, n_c slices, n_t
+// panels over all of them (solve.cu)
+void launch_batch_iteration(const BatchShape& sh, const BatchInst* d_inst, const int2* d_fmap,
+                            int n_f, const int2* d_cmap, int n_c, const int2* d_tmap, int n_t,
+                            cudaStream_t st);
 
 // learned preconditioner (gnn.cu)
 void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);

@@ -613,7 +613,13 @@ __device__ __forceinline__ int trirow(int i) { return i * (i + 1) / 2; }
 // four warp-uniform slices of the sum over m, the slice sums added in a fixed
 // order.  A non-positive pivot starts again from a fresh copy of G_s with the
 // shift raised 100-fold (at most 8 times; each retry counted in flags[4]),
-// then raises flags[1].
+// then raises flags[1].  With drop > 0 a column whose pivot (its Schur
+// complement) is at most drop times its shifted diagonal is numerically
+// dependent on the columns before it: it is dropped (its row and column of X
+// are zero, so its coefficient stays 0), counted in flags[5], and never
+// triggers a retry.  On FP32 panels the Gram carries rounding of about 1e-7
+// of its entries, so directions below that are noise that the factors would
+// otherwise amplify by 1 / shift.
 // The factorisation is FP64 (the blocks are as ill-conditioned as the shift
 // allows); with three blocks per SM it keeps GB300's FP64 pipe (1/64 of the
 // FP32 FMA rate) about 80% busy.  kDfInv (FP32 and DF32 panels, whose solvers
@@ -623,7 +629,7 @@ __device__ __forceinline__ int trirow(int i) { return i * (i + 1) / 2; }
 template <bool kDfInv>
 __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __restrict__ Gp,
                                                                  int K, double shift,
-                                                                 double abs_shift,
+                                                                 double abs_shift, double drop,
                                                                  double* __restrict__ Xr,
                                                                  double* __restrict__ Xc,
                                                                  int* __restrict__ flags,
@@ -634,7 +640,8 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
   __shared__ double colk[128];       // scaled column k of L
   __shared__ double xpart[4][128];   // slice sums of a row of the inverse (pairs with kDfInv)
   __shared__ float2 lrow2[128];      // kDfInv: row i of L as pairs
-  __shared__ int fail;
+  __shared__ double gdiag[128];      // the shifted diagonal (drop test)
+  __shared__ int fail, ndrop;
   const int64_t PT = tri_pairs(K);
   double* P = reinterpret_cast<double*>(chsm);   // packed lower triangle
   float2* X2 = reinterpret_cast<float2*>(chsm);  // kDfInv: rows of X as pairs
@@ -671,6 +678,12 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
   // pivot k: L_kk = sqrt(G_kk), 1 / L_kk (one thread: FP64 sqrt / division are costly)
   auto pivot = [&](int k) {
     const double d = P[trirow(k) + k];
+    if (drop > 0.0 && !(d > drop * gdiag[k])) {   // dependent column: dropped
+      P[trirow(k) + k] = 1.0;
+      rpiv[k] = 0.0;
+      ++ndrop;
+      return;
+    }
     if (!(d > 0.0)) fail = 1;
     const double l = sqrt(d > 0.0 ? d : 1.0);
     P[trirow(k) + k] = l;
@@ -684,8 +697,14 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
       eps = eps > 0.0 ? eps * 100.0 : 1e-14;
     }
     const double add = eps * tr / K + abs_shift + (tr == 0.0 && abs_shift == 0.0 ? 1.0 : 0.0);
-    if (tid == 0) fail = 0;
-    for (int i = tid; i < K; i += nt) P[trirow(i) + i] += add;
+    if (tid == 0) {
+      fail = 0;
+      ndrop = 0;
+    }
+    for (int i = tid; i < K; i += nt) {
+      P[trirow(i) + i] += add;
+      gdiag[i] = P[trirow(i) + i];
+    }
     __syncthreads();
     if (tid == 0) pivot(0);
     __syncthreads();
@@ -720,6 +739,7 @@ __global__ void __launch_bounds__(kCholThreads, 3) k_block_chol(const double* __
     if (tid == 0) atomicOr(&flags[1], 1);
     return;
   }
+  if (tid == 0 && ndrop) atomicAdd(&flags[5], ndrop);
   // X = L^{-1} in place: X_ii = 1/L_ii; X_ij = -(sum_{m=j}^{i-1} L_im X_mj) / L_ii.
   // Row i of L is read while row i of X is formed, then overwritten.
   // Thread (p, j): column j, slice p of [0, i); rows m < j hold no X_mj.
@@ -958,12 +978,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     const int* __restrict__ cover_sub, const int* __restrict__ cover_start,
     const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
-    double* __restrict__ partial, double* __restrict__ norm_partial,
-    const int* __restrict__ skip) {
+    double* __restrict__ partial, double* __restrict__ norm_partial) {
   __shared__ double sd[32][kFusedRows];
   __shared__ double su[kFusedRows];
   __shared__ double red[33];
-  if (skip && *skip) return;   // a finished instance of a batched graph
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
   const int c = un.x;
@@ -1156,7 +1174,7 @@ __device__ __forceinline__ void load_slice(const T* p, T (&x)[FPL], bool whole, 
   }
 }
 
-template <class T, int FPL, int kRows>
+template <class T, int FPL, int kRows, bool kBatch = false>
 __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     const T* __restrict__ panels, const T* __restrict__ tvec, int K,
     const int4* __restrict__ units, const int* __restrict__ cell_pstart,
@@ -1165,8 +1183,28 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
-    int* __restrict__ flags, const int* __restrict__ skip) {
-  if (skip && *skip) return;   // a finished instance of a batched graph
+    int* __restrict__ flags, const BatchInst* __restrict__ bi, const int2* __restrict__ bmap) {
+  int ub = blockIdx.x;   // this CTA's unit
+  if constexpr (kBatch) {
+    // a multi-instance launch: the unit's instance supplies every array
+    const int2 bm = bmap[blockIdx.x];
+    const BatchInst& I = bi[bm.x];
+    panels = reinterpret_cast<const T*>(I.panels);
+    tvec = reinterpret_cast<const T*>(I.tlow);
+    units = I.units;
+    cell_pstart = I.cell_pstart;
+    cell_count = I.cell_count;
+    cover_off = I.cover_off;
+    cover_sub = I.cover_sub;
+    entry_base = I.entry_base;
+    scal = I.scal;
+    u = I.u;
+    hvec = I.hvec;
+    partial = I.part;
+    norm_partial = I.gpart;
+    flags = I.flags;
+    ub = bm.y;
+  }
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
   __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
@@ -1181,7 +1219,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cw = (blockDim.x >> 5) - 1;   // control warp: u', norms
   const int pw = cw - 1;                  // producer warp: the ring's copies
-  const int4 un = units[blockIdx.x];      // (cell, first row, end row, first partial)
+  const int4 un = units[ub];              // (cell, first row, end row, first partial)
   const int c = un.x;
   const int m = cover_off[c + 1] - cover_off[c];
   const int cnt = cell_count[c];
@@ -1279,7 +1317,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     }
     if (!ok && lane == 0) atomicOr(&flags[3], 1);
     const double tot = warp_sum<double>(nrm);
-    if (lane == 0) norm_partial[blockIdx.x] = tot;
+    if (lane == 0) norm_partial[ub] = tot;
     return;
   }
   if (!active) return;
@@ -1386,8 +1424,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     const int64_t* __restrict__ entry_base, const double* __restrict__ scal,
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
-    int* __restrict__ flags, const int* __restrict__ skip) {
-  if (skip && *skip) return;   // a finished instance of a batched graph
+    int* __restrict__ flags) {
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
   __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
@@ -1579,29 +1616,42 @@ constexpr int kPanelChunk = 32;
 __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __restrict__ fe,
                                const int2* __restrict__ pch, int K, double* __restrict__ csum,
                                int pairs, const double* __restrict__ beta_partial, int n_beta,
-                               double* __restrict__ scal, const int* __restrict__ skip) {
-  if (skip && *skip) return;   // a finished instance of a batched graph
+                               double* __restrict__ scal, const BatchInst* __restrict__ bi,
+                               const int2* __restrict__ bmap) {
   __shared__ int ent[kPanelChunk];
+  int cb = blockIdx.x;   // this block's slice
+  if (bi) {   // a multi-instance launch: the slice's instance supplies every array
+    const int2 bm = bmap[blockIdx.x];
+    const BatchInst& I = bi[bm.x];
+    partial = I.part;
+    fe = I.fe;
+    pch = I.pch;
+    csum = I.csum;
+    beta_partial = I.gpart;
+    n_beta = I.n_units;
+    scal = I.scal;
+    cb = bm.y;
+  }
   // block 0, LSQR: commit the scalars staged by the previous update (no kernel
   // of the iteration reads the committed slots before this point), then
   // warp 0 forms beta^2 = sum of the norm partials, once for every panel block
   // of the next kernel (a fixed order)
-  if (beta_partial && blockIdx.x == 0 && threadIdx.x < kStage && threadIdx.x != S_BSQ)
+  if (beta_partial && cb == 0 && threadIdx.x < kStage && threadIdx.x != S_BSQ)
     scal[threadIdx.x] = scal[kStage + threadIdx.x];
-  if (beta_partial && blockIdx.x == 0 && threadIdx.x < 32) {
+  if (beta_partial && cb == 0 && threadIdx.x < 32) {
     double v = 0.0;
     for (int i = threadIdx.x; i < n_beta; i += 32) v += beta_partial[i];
     v = warp_sum<double>(v);
     if (threadIdx.x == 0) scal[kStage + S_BSQ] = v;
   }
-  const int2 ch = pch[blockIdx.x];
+  const int2 ch = pch[cb];
   const int n = ch.y - ch.x;
   if ((int)threadIdx.x < n) ent[threadIdx.x] = fe[ch.x + threadIdx.x];
   __syncthreads();
   // every load of the slice is issued before the first add (one round of L2
   // latency instead of one per few partials); the adds keep the slice order
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const int64_t out = (int64_t)blockIdx.x * K + k;
+    const int64_t out = (int64_t)cb * K + k;
     if (pairs) {
       float2 pr[kPanelChunk];
 #pragma unroll
@@ -1795,11 +1845,10 @@ __device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags)
 __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restrict__ pco,
                              int K, double* __restrict__ v, double* __restrict__ scal, int init,
                              const float2* Xs, float2* zs, float2* part, uint64_t* bar,
-                             int* __restrict__ flags) {
+                             int* __restrict__ flags, int s) {
   __shared__ double red[33];
   __shared__ double sh_beta;
   __shared__ float2 sh_ib;
-  const int s = blockIdx.x;
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, k = threadIdx.x - g * Kp;
@@ -1868,7 +1917,7 @@ __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restr
 // in shared memory), those with i > m idle; then one pass adds the group sums
 // in order.
 __device__ void tail_t_tri(int K, const float2* Xs, const float2* vs, float2* part,
-                           double* __restrict__ t, void* __restrict__ tlow, int low_kind) {
+                           double* __restrict__ t, void* __restrict__ tlow, int low_kind, int s) {
   const int Kp = (K + 31) & ~31;
   const int G = blockDim.x / Kp;
   const int g = threadIdx.x / Kp, i = threadIdx.x - g * Kp;
@@ -1885,7 +1934,7 @@ __device__ void tail_t_tri(int K, const float2* Xs, const float2* vs, float2* pa
     part[g * K + i] = make_float2(S, C);
   }
   __syncthreads();
-  const int64_t o = (int64_t)blockIdx.x * K;
+  const int64_t o = (int64_t)s * K;
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
     float2 a = part[j];
     for (int q = 1; q < G; ++q) a = df_add(a, part[q * K + j]);
@@ -2188,14 +2237,33 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
     int K, double* __restrict__ v, double* __restrict__ w, double* __restrict__ x,
     double* __restrict__ scal, int init, double* __restrict__ norm_partial,
     double* __restrict__ t, void* __restrict__ tlow, int low_kind,
-    unsigned int* __restrict__ counter, int* __restrict__ flags, const int* __restrict__ skip) {
+    unsigned int* __restrict__ counter, int* __restrict__ flags, const BatchInst* __restrict__ bi,
+    const int2* __restrict__ bmap) {
   extern __shared__ __align__(16) unsigned char trsm[];
-  if (skip && *skip) return;   // a finished instance of a batched graph
   __shared__ double red[33];
   __shared__ int last;
+  int s = blockIdx.x, nblk = gridDim.x;   // this block's panel, the instance's panels
+  if (bi) {   // a multi-instance launch: the panel's instance supplies every array
+    const int2 bm = bmap[blockIdx.x];
+    const BatchInst& I = bi[bm.x];
+    csum = I.csum;
+    pco = I.pco;
+    Xt = I.Xt;
+    v = I.v;
+    w = I.w;
+    x = I.x;
+    scal = I.scal;
+    norm_partial = I.vpart;
+    t = I.t;
+    tlow = const_cast<float*>(I.tlow);
+    counter = I.counter;
+    flags = I.flags;
+    s = bm.y;
+    nblk = I.n_sub;
+  }
   TriSmem sm(trsm, K);
-  tri_fetch(sm.Xs, Xt, blockIdx.x, K, sm.bar);
-  const int64_t o = (int64_t)blockIdx.x * K;
+  tri_fetch(sm.Xs, Xt, s, K, sm.bar);
+  const int64_t o = (int64_t)s * K;
   if (!init) {
     const double ia = scal[S_TSCALE], pr = scal[S_PHI_RHO], tr = scal[S_THETA_RHO];
     for (int i = threadIdx.x; i < K; i += blockDim.x) {
@@ -2207,19 +2275,19 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
     }
   }
   const double nrm = tail_v_tri(csum, pco, K, v, scal, init, sm.Xs, sm.vec, sm.part, sm.bar,
-                                flags);
-  if (threadIdx.x == 0) norm_partial[blockIdx.x] = nrm;
+                                flags, s);
+  if (threadIdx.x == 0) norm_partial[s] = nrm;
   __syncthreads();
-  tail_t_tri(K, sm.Xs, sm.vec, sm.part, t, tlow, low_kind);
+  tail_t_tri(K, sm.Xs, sm.vec, sm.part, t, tlow, low_kind, s);
   // the last block: alpha, the recurrence, the staged scalars
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)nblk - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
   double a2 = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) a2 += __ldcg(norm_partial + i);
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) a2 += __ldcg(norm_partial + i);
   a2 = block_sum(a2, red);
   if (threadIdx.x == 0) {
     lsqr_recurrence(scal, a2, sqrt(scal[kStage + S_BSQ]), init, true);
@@ -2389,6 +2457,41 @@ static size_t fused_pipe_budget(int mmax, int K, size_t elem, size_t u_bytes, in
   return fused_ring_budget();
 }
 
+// The launch shape of k_fused_pipe for T panels: rows per chunk, ring stages,
+// dynamic shared memory, threads.  False when the pass takes the register
+// kernel k_fused instead.
+template <class T>
+static bool fused_pipe_shape(const elmfb_ctx* h, const FusedPlan& fp, int& rows, int& S,
+                             size_t& smem, int& pthreads) {
+  const int K = h->K;
+  // bulk-copy ring: S stages of (covering panels x rows x K) elements
+  const int mmax = std::max(1, h->max_cover);
+  // the unit's u values, staged after the ring (16-byte aligned for the copy)
+  const size_t u_bytes =
+      ((size_t)std::max(8, std::min(fp.max_unit_rows, kMaxUnitRows)) * sizeof(double) + 15) &
+      ~size_t(15);
+  pthreads = fp.threads + 64;   // covering-panel warps + producer + control
+  const size_t budget = fused_pipe_budget(mmax, K, sizeof(T), u_bytes, pthreads);
+  auto stages_for = [&](int r) {
+    const size_t sb = std::max<size_t>((size_t)mmax * r * K * sizeof(T), 1);
+    return (int)std::min<size_t>(kPipeMaxStages, (budget - u_bytes) / sb);
+  };
+  // rows per chunk: 8 while the ring still holds three such stages (fewer,
+  // larger copies and half the per-chunk synchronisation; on the 2-D
+  // workload's 17 covering panels a pass drops from 0.26 to 0.20 ms), else 4.
+  // ELMFB_FUSED_ROWS=4 forces 4 (it changes the grouping of the compensated
+  // sums, not the order of the terms within a row).
+  const char* erows = getenv("ELMFB_FUSED_ROWS");
+  rows = ((erows && atoi(erows) == 4) || stages_for(8) < 3) ? 4 : 8;
+  S = stages_for(rows);
+  smem = (size_t)S * mmax * rows * K * sizeof(T) + u_bytes;
+  const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
+  // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
+  // ring needs the two stages in use plus at least one in flight
+  return S >= 3 && pthreads <= 1024 && (K * sizeof(T)) % 16 == 0 &&
+         !(force_regs && force_regs[0] == '1');
+}
+
 template <class T>
 void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, double* scal,
                   double* gpart, const void* tlow) {
@@ -2424,7 +2527,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
         h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), h->d_cover_off.as<int>(),        \
         h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(), h->d_entry_base.as<int64_t>(),    \
         scal, h->d_u.as<double>(), h->d_h.as<double>(), mode, fp.part.as<double>(), gpart, S,   \
-        mmax, h->d_flags.as<int>(), h->skip);                                                            \
+        mmax, h->d_flags.as<int>());                                                            \
   }
     ELMFB_FD(1) ELMFB_FD(2) ELMFB_FD(3) ELMFB_FD(4)
 #undef ELMFB_FD
@@ -2446,33 +2549,10 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
     t = reinterpret_cast<const T*>(tf);
   }
   prof_begin(h, KID_FUSED, (double)h->NPR * K * sizeof(T) + 16.0 * h->NR + 8.0 * h->NPhi);
-  // bulk-copy ring: S stages of (covering panels x kPipeRows rows x K) elements
   const int mmax = std::max(1, h->max_cover);
-  // the unit's u values, staged after the ring (16-byte aligned for the copy)
-  const size_t u_bytes =
-      ((size_t)std::max(8, std::min(fp.max_unit_rows, kMaxUnitRows)) * sizeof(double) + 15) &
-      ~size_t(15);
-  const size_t budget = fused_pipe_budget(mmax, K, sizeof(T), u_bytes, fthreads + 64);
-  auto stages_for = [&](int r) {
-    const size_t sb = std::max<size_t>((size_t)mmax * r * K * sizeof(T), 1);
-    return (int)std::min<size_t>(kPipeMaxStages, (budget - u_bytes) / sb);
-  };
-  // rows per chunk: 8 while the ring still holds three such stages (fewer,
-  // larger copies and half the per-chunk synchronisation; on the 2-D
-  // workload's 17 covering panels a pass drops from 0.26 to 0.20 ms), else 4.
-  // ELMFB_FUSED_ROWS=4 forces 4 (it changes the grouping of the compensated
-  // sums, not the order of the terms within a row).
-  const char* erows = getenv("ELMFB_FUSED_ROWS");
-  const int rows = ((erows && atoi(erows) == 4) || stages_for(8) < 3) ? 4 : 8;
-  const size_t stage_bytes = (size_t)mmax * rows * K * sizeof(T);
-  const int S = stages_for(rows);
-  const char* force_regs = getenv("ELMFB_FUSED_REGISTERS");
-  // bulk copies need 16-byte aligned rows (K sizeof(T) a multiple of 16); the
-  // ring needs the two stages in use plus at least one in flight
-  const int pthreads = fthreads + 64;   // covering-panel warps + producer + control
-  if (S >= 3 && pthreads <= 1024 && (K * sizeof(T)) % 16 == 0 &&
-      !(force_regs && force_regs[0] == '1')) {
-    const size_t smem = (size_t)S * stage_bytes + u_bytes;
+  int rows = 8, S = 0, pthreads = 0;
+  size_t smem = 0;
+  if (fused_pipe_shape<T>(h, fp, rows, S, smem, pthreads)) {
 #define ELMFB_FTR(F, R)                                                                        \
   if (fpl == F && rows == R) {                                                                 \
     ensure_dyn_smem((const void*)k_fused_pipe<T, F, R>, smem, true);                          \
@@ -2480,7 +2560,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(),   \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),        \
         h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,    \
-        fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>(), h->skip);                           \
+        fp.part.as<double>(), gpart, S, mmax, h->d_flags.as<int>(), nullptr, nullptr);          \
   } else
 #define ELMFB_FT(F) ELMFB_FTR(F, 4) ELMFB_FTR(F, 8)
     ELMFB_FT(1) ELMFB_FT(2) ELMFB_FT(3) ELMFB_FT(4)
@@ -2494,7 +2574,7 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
         P, t, K, fp.units.as<int4>(), h->d_cell_pstart.as<int>(), h->d_cell_count.as<int>(), \
         h->d_cover_off.as<int>(), h->d_cover_sub.as<int>(), h->d_cover_start.as<int>(),      \
         h->d_entry_base.as<int64_t>(), scal, h->d_u.as<double>(), h->d_h.as<double>(), mode,  \
-        fp.part.as<double>(), gpart, h->skip);                                               \
+        fp.part.as<double>(), gpart);                                                        \
   } else
 #define ELMFB_FU4(F) ELMFB_FU(F, 256) ELMFB_FU(F, 512) ELMFB_FU(F, 640) ELMFB_FU(F, 1024)
   ELMFB_FU4(1) ELMFB_FU4(2) ELMFB_FU4(3) ELMFB_FU4(4)
@@ -2512,12 +2592,14 @@ void launch_fused(elmfb_ctx* h, FusedPlan& fp, const double* t64, int mode, doub
 constexpr int kDiagChunk = 2048;
 
 template <class T>
-void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift) {
+void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_shift,
+                        double drop) {
   cudaStream_t st = h->stream;
   const int K = h->K;
   const int64_t KK = (int64_t)K * K;
   h->d_R.alloc(2 * h->n_sub * KK * sizeof(double), st);
   h->bj_retries = 0;
+  h->bj_dropped = 0;
   if (identity) return;
   if (K > 128) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up supports K <= 128");
   // chunks of at most 2048 rows of one panel, as 16-row steps (entry, first
@@ -2612,19 +2694,20 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   if (pairs_x) h->d_R2.alloc(h->n_sub * tri_pairs(K) * sizeof(float2), st);
   if (pairs_x)
     k_block_chol<true><<<h->n_sub, kCholThreads, csm, st>>>(
-        dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
+        dG.as<double>(), K, shift, abs_shift, drop, h->d_R.as<double>(),
         h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), h->d_R2.as<float2>());
   else
     k_block_chol<false><<<h->n_sub, kCholThreads, csm, st>>>(
-        dG.as<double>(), K, shift, abs_shift, h->d_R.as<double>(),
+        dG.as<double>(), K, shift, abs_shift, drop, h->d_R.as<double>(),
         h->d_R.as<double>() + h->n_sub * KK, h->d_flags.as<int>(), nullptr);
   prof_end(h, KID_BLOCK_CHOL);
   check_launch("k_block_chol");
   count_launch(h);
-  int flags[5];
-  CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int flags[6];
+  CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaStreamSynchronize(st));
   h->bj_retries = flags[4];
+  h->bj_dropped = flags[5];
   if (flags[3]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "block-Jacobi set-up: a copy wait timed out");
   if (flags[1]) ELMFB_THROW(ELMFB_ERR_BREAKDOWN, "block Cholesky failed after shift increases");
 }
@@ -2790,10 +2873,11 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const bool identity = o->preconditioner == ELMFB_PREC_NONE;
 
   stage_begin(h, 4);
-  if (!h->bj_reuse) block_jacobi_setup<T>(h, o->shift, identity);
+  if (!h->bj_reuse) block_jacobi_setup<T>(h, o->shift, identity, 0.0, o->drop_tol);
   stage_end(h, 4);
   info->setup_ms = h->stage_ms[4];
   info->precond_retries = h->bj_retries;
+  info->precond_dropped = h->bj_dropped;
 
   // panel -> entries (cell order)
   const int ne = (int)h->cover_sub.size();
@@ -2934,7 +3018,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
           fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(),
           h->d_w.as<double>(), h->d_x_sol.as<double>(), scal, init, vpart,
           h->d_tmp.as<double>(), fp.tf.p, low_kind, dcount.as<unsigned int>(),
-          h->d_flags.as<int>(), h->skip);
+          h->d_flags.as<int>(), nullptr, nullptr);
       prof_end(h, KID_UPDATE);
       return;
     }
@@ -3041,34 +3125,66 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     const bool t3 = o->ntol > 0.0 && arn <= o->ntol * arnorm0;
     return t1 || t2 || t3 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0;
   };
-  // Batched graph: full intervals in the batch's shared rounds, then leave
-  // (the skip flag turns this instance's nodes into no-ops) and finish any
-  // remainder below launch by launch.  Only the FP32-pair tail, whose kernels
-  // all take the skip flag, joins the rounds.
-  const bool in_rounds = use_graph && h->round && xpairs && o->check_every <= max_it;
+  // Multi-instance launches: full check intervals in the batch's shared
+  // rounds, then leave and finish any remainder below.  FP32 panels with the
+  // FP32-pair tail and the bulk-copy fused pass only.
+  bool in_rounds = false;
+  BatchShape bsh;
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->round && round_interval(h->round) == o->check_every && xpairs && fused &&
+        fp.n_pchunks > 0 && o->check_every <= max_it)
+      in_rounds = fused_pipe_shape<T>(h, fp, bsh.rows, bsh.S, bsh.smem, bsh.pthreads);
+  }
   if (in_rounds) {
+    bsh.K = K;
+    bsh.fpl = (K + 31) / 32;
+    bsh.mmax = std::max(1, h->max_cover);
+    bsh.chunk_threads = std::min(std::max(32, ((K + 31) / 32) * 32), 128);   // as panel_chunk_sums
+    bsh.low_kind = low_kind;
+    bsh.mode = fmode;
+    bsh.tsmem = tsmem;
+    BatchInst bi{};
+    bi.panels = reinterpret_cast<const float*>(P);
+    bi.tlow = fp.tf.as<float>();
+    bi.units = fp.units.as<int4>();
+    bi.cell_pstart = h->d_cell_pstart.as<int>();
+    bi.cell_count = h->d_cell_count.as<int>();
+    bi.cover_off = h->d_cover_off.as<int>();
+    bi.cover_sub = h->d_cover_sub.as<int>();
+    bi.entry_base = h->d_entry_base.as<int64_t>();
+    bi.scal = scal;
+    bi.u = h->d_u.as<double>();
+    bi.hvec = h->d_h.as<double>();
+    bi.part = fp.part.as<double>();
+    bi.gpart = gpart;
+    bi.flags = h->d_flags.as<int>();
+    bi.fe = fp.fe.as<int>();
+    bi.pch = fp.pch.as<int2>();
+    bi.csum = fp.csum.as<double>();
+    bi.pco = fp.pco.as<int>();
+    bi.Xt = Xt;
+    bi.v = h->d_v.as<double>();
+    bi.w = h->d_w.as<double>();
+    bi.x = h->d_x_sol.as<double>();
+    bi.vpart = vpart;
+    bi.t = h->d_tmp.as<double>();
+    bi.counter = dcount.as<unsigned int>();
+    bi.n_units = n_units;
+    bi.n_pchunks = fp.n_pchunks;
+    bi.n_sub = h->n_sub;
+    // the rounds run on the batch's own streams: the start-up work on st first
+    CUDA_CHECK(cudaStreamSynchronize(st));
     struct Leave {   // leave the rounds on every exit, errors included
       elmfb_ctx* h;
       bool joined = false;
       ~Leave() {
         if (joined) round_leave(h->round, h->round_slot);
-        h->skip = nullptr;
       }
     } lv{h};
-    h->skip = round_skip_flag(h->round, h->round_slot);
-    cudaGraph_t g = capture_interval(o->check_every);
-    // the rounds run on the batch's own stream: the start-up work on st first
-    const cudaError_t se = cudaStreamSynchronize(st);
-    if (se != cudaSuccess) {
-      cudaGraphDestroy(g);
-      CUDA_CHECK(se);
-    }
-    round_join(h->round, h->round_slot, g);
+    round_join(h->round, h->round_slot, bi, bsh);
     lv.joined = true;
     while (it + o->check_every <= max_it) {
-      round_step(h->round, h->round_slot);
-      h->launches += g_launches;
-      count_launch(h, tail_launches * o->check_every);
+      h->launches += round_step(h->round, h->round_slot);
       it += o->check_every;
       if (check_scalars()) {
         status = ELMFB_OK;
@@ -3574,9 +3690,37 @@ template void launch_fused<double>(elmfb_ctx*, FusedPlan&, const double*, int, d
                                    const void*);
 template void launch_fused<df2>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
                                 const void*);
-template void block_jacobi_setup<float>(elmfb_ctx*, double, bool, double);
-template void block_jacobi_setup<double>(elmfb_ctx*, double, bool, double);
-template void block_jacobi_setup<df2>(elmfb_ctx*, double, bool, double);
+
+void launch_batch_iteration(const BatchShape& sh, const BatchInst* d_inst, const int2* d_fmap,
+                            int n_f, const int2* d_cmap, int n_c, const int2* d_tmap, int n_t,
+                            cudaStream_t st) {
+  if (n_f <= 0 || n_c <= 0 || n_t <= 0) return;
+  // the fused pass: every array from the unit's instance
+#define ELMFB_FB(F, R)                                                                         \
+  if (sh.fpl == F && sh.rows == R) {                                                           \
+    ensure_dyn_smem((const void*)k_fused_pipe<float, F, R, true>, sh.smem, true);             \
+    k_fused_pipe<float, F, R, true><<<n_f, sh.pthreads, sh.smem, st>>>(                        \
+        nullptr, nullptr, sh.K, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, \
+        nullptr, nullptr, nullptr, sh.mode, nullptr, nullptr, sh.S, sh.mmax, nullptr, d_inst,  \
+        d_fmap);                                                                               \
+  } else
+  ELMFB_FB(1, 4) ELMFB_FB(1, 8) ELMFB_FB(2, 4) ELMFB_FB(2, 8) ELMFB_FB(3, 4) ELMFB_FB(3, 8)
+  ELMFB_FB(4, 4) ELMFB_FB(4, 8)
+  ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "multi-instance fused pass needs K <= 128");
+#undef ELMFB_FB
+  // the slice sums (the first slice of each instance commits its scalars)
+  k_panel_chunks<<<n_c, sh.chunk_threads, 0, st>>>(nullptr, nullptr, nullptr, sh.K, nullptr, 1,
+                                                   nullptr, 0, nullptr, d_inst, d_cmap);
+  // the tail (the last block of each instance runs its recurrence)
+  ensure_dyn_smem((const void*)k_lsqr_tail_tri, sh.tsmem);
+  k_lsqr_tail_tri<<<n_t, kTriThreads, sh.tsmem, st>>>(
+      nullptr, nullptr, nullptr, sh.K, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
+      nullptr, sh.low_kind, nullptr, nullptr, d_inst, d_tmap);
+  check_launch("multi-instance LSQR iteration");
+}
+template void block_jacobi_setup<float>(elmfb_ctx*, double, bool, double, double);
+template void block_jacobi_setup<double>(elmfb_ctx*, double, bool, double, double);
+template void block_jacobi_setup<df2>(elmfb_ctx*, double, bool, double, double);
 
 void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, int n_beta,
                       double* scal) {
@@ -3584,7 +3728,7 @@ void panel_chunk_sums(elmfb_ctx* h, FusedPlan& fp, const double* beta_partial, i
   const int tb = std::min(std::max(32, ((h->K + 31) / 32) * 32), 128);
   k_panel_chunks<<<fp.n_pchunks, tb, 0, h->stream>>>(
       fp.part.as<double>(), fp.fe.as<int>(), fp.pch.as<int2>(), h->K, fp.csum.as<double>(),
-      fp.pairs ? 1 : 0, beta_partial, n_beta, scal, h->skip);
+      fp.pairs ? 1 : 0, beta_partial, n_beta, scal, nullptr, nullptr);
   check_launch("k_panel_chunks");
   count_launch(h);
 }

@@ -286,6 +286,16 @@ def batch_specs(n_instances: int = 512, seed: int = 0) -> List[BatchSpec]:
     return out
 
 
+def support_points_per_feature(P: Problem) -> float:
+    """Interior collocation points that one interior subdomain of the finest
+    level holds in its support, per feature: the support covers (delta / n)^dim
+    of the domain box (n subdomains per dimension), for uniformly spread
+    points.  Below a few, the subdomain's features are under-resolved and its
+    Gram block is singular or nearly so."""
+    n = P.levels[-1]
+    return P.interior.points.shape[0] * min(1.0, P.delta / n) ** P.dim / P.features
+
+
 def batch_instance(spec: BatchSpec, index: int, batch_seed: int = 0) -> Problem:
     """One single-level 2D Poisson instance u = sin(k pi x) sin(k pi y)."""
     return poisson2d(levels=(spec.n_sub,), features=spec.features, n_side=spec.n_side,
