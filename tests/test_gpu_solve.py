@@ -142,9 +142,12 @@ _QR_CASES = _SOLVE_CASES + [
                                             for p in (E.FP64, E.DF32)])
 def test_solution_matches_oracle_qr_minimiser(name, make, prec):
     """The GPU's column-pivoted QR on the assembled system reaches the
-    oracle's QR error (1.01x its largest value over row orders), with a
-    numerical rank within the oracle's range over those orders (+-2: a pivot
-    near the rank cut may fall either side of it)."""
+    oracle's QR error (1.01x its largest value over row orders, plus the
+    spread of those values: on the full DHO the minimiser's error is FP64
+    rounding, 1.7e-14 to 2.4e-14 over three row orders, so 1% of it is below
+    what reordering alone changes; elsewhere the spread is about 1e-12 of the
+    error), with a numerical rank within the oracle's range over those orders
+    (+-2: a pivot near the rank cut may fall either side of it)."""
     g = _golden(name)
     if "qr" not in g or "rel_l2_max_over_orders" not in g["qr"]:
         pytest.skip(f"{name}: no QR entry over row orders in oracle_errors.json")
@@ -160,7 +163,8 @@ def test_solution_matches_oracle_qr_minimiser(name, make, prec):
           f"({info.solve_ms:.1f} ms, residual {info.residual_norm:.4e}); oracle QR "
           f"{q['rel_l2']:.4e}, max over orders {q['rel_l2_max_over_orders']:.4e}, "
           f"ranks {ranks}, residual {q['residual']:.4e}")
-    assert err["rel_l2"] <= 1.01 * q["rel_l2_max_over_orders"]
+    errs = [q["rel_l2"]] + [o["rel_l2"] for o in q["orders"]]
+    assert err["rel_l2"] <= 1.01 * q["rel_l2_max_over_orders"] + (max(errs) - min(errs))
     assert min(ranks) - 2 <= info.rank <= max(ranks) + 2
     assert info.residual_norm <= 1.01 * max([q["residual"]] + [o["residual"] for o in q["orders"]])
 
