@@ -17,9 +17,17 @@ diagonal block of G = M^T M, shifted by eps tr/K), optionally with the first
 n_coarse columns (the coarse levels) treated as one joint block shifted by
 eps tr/n_coarse -- the coarse-level correction.
 
+``cholesky_dropping`` is the block factorisation with dependent columns
+dropped (the GPU's block-Jacobi option drop_tol): an unpivoted Cholesky of
+B + eps tr(B)/dim I in column order, where a column whose pivot (its Schur
+complement after the earlier kept columns) is at most drop times its shifted
+diagonal is dropped -- it takes no part in the factorisation and its
+coefficient is fixed at zero.
+
 Pinned by: CG with P = I solves an SPD system in n steps; P = A^{-1} solves it
-in one; the joint block over all columns with no shift is A^{-1}
-(tests/test_oracle_krylov.py).
+in one; the joint block over all columns with no shift is A^{-1}; with
+drop = 0 the factor is NumPy's Cholesky; a repeated column is dropped and a
+Gram of rank r keeps exactly r columns (tests/test_oracle_krylov.py).
 """
 from __future__ import annotations
 
@@ -72,3 +80,29 @@ def block_preconditioner(G: np.ndarray, K: int, shift: float, n_coarse: int = 0)
             z[a:b] = Bi @ r[a:b]
         return z
     return apply
+
+
+def cholesky_dropping(B: np.ndarray, shift: float, drop: float):
+    """(L, kept, ratio): L lower triangular with L L^T = the shifted block
+    restricted to the kept columns (rows and columns of dropped ones zero),
+    kept a bool mask, ratio[k] the pivot of column k over its shifted
+    diagonal when its turn came."""
+    n = B.shape[0]
+    S = 0.5 * (B + B.T) + shift * np.trace(B) / n * np.eye(n)
+    g = np.diag(S).copy()          # the shifted diagonal, the drop test's scale
+    L = np.zeros((n, n))
+    kept = np.ones(n, dtype=bool)
+    ratio = np.zeros(n)
+    for k in range(n):
+        d = S[k, k]
+        ratio[k] = d / g[k]
+        if drop > 0.0 and not d > drop * g[k]:
+            kept[k] = False        # dependent on the kept columns before it
+            continue
+        if not d > 0.0:
+            raise np.linalg.LinAlgError("non-positive pivot")
+        col = S[k:, k] / np.sqrt(d)
+        L[k:, k] = col
+        S[k + 1:, k + 1:] -= np.outer(col[1:], col[1:])
+    L[~kept, :] = 0.0              # a dropped row takes no part either
+    return L, kept, ratio

@@ -154,6 +154,27 @@ def test_shared_launches_equal_one_by_one():
         assert np.array_equal(u0, u1)
 
 
+def test_per_instance_options_equal_one_by_one():
+    """Per-item solver options in elmfb_batch_solve (here the paper's
+    unpreconditioned LSQR for two of four instances, block-Jacobi for the
+    rest, with shared launches): each instance gets bitwise the coefficients
+    and iteration count of solving it alone with its own options."""
+    probs = _instances(4, cap_side=48, cap_sub=4, seed=2)
+    base = E.default_solve_opts(max_iter=120, atol=0.0, btol=0.0, ntol=1e-3, shift=1e-6,
+                                check_every=10)
+    plain = E.default_solve_opts(max_iter=120, atol=0.0, btol=0.0, ntol=1e-3, check_every=10,
+                                 preconditioner=E.PREC_NONE)
+    item_opts = [plain, None, plain, None]
+    res, _, co = E.batch_solve(probs, precision=E.FP32, n_workers=2, opts=base, coeffs=True,
+                               item_opts=item_opts)
+    for P, r, a_b, o in zip(probs, res, co, item_opts):
+        with E.Solver.from_problem(P, precision=E.FP32) as s:
+            s.assemble_problem(P)
+            info = s.solve(o if o is not None else base)
+            assert np.array_equal(s.coeffs(), a_b)
+        assert r.iterations == info.iterations
+
+
 def test_autotuner_keeps_one_choice_per_shape_class():
     """`autotune` times the fused pass at three work-unit sizes on the first
     solve of a shape class and keeps the fastest: the table gains one entry

@@ -123,6 +123,39 @@ def test_block_cholesky_retries_with_a_larger_shift(prec):
     assert np.all(np.isfinite(a))
 
 
+@pytest.mark.parametrize("prec", [E.FP32, E.FP64])
+def test_block_cholesky_drops_the_oracles_dependent_columns(prec):
+    """drop_tol on under-resolved subdomains (8 x 8 single-level, K = 32, about
+    50 collocation points per support): the columns the GPU drops (their
+    coefficients exactly 0, counted in precond_dropped) are those the oracle's
+    Cholesky with dropping drops on the Gram blocks of the panels' own entries,
+    except columns whose pivot ratio lies within a factor 2 of the threshold
+    (the GPU's Gram rounds differently there)."""
+    from oracle import krylov as KR
+    K, drop, shift = 32, 1e-4, 1e-6
+    P = WL.poisson2d(levels=(8,), features=K, n_side=20, n_boundary_side=20)
+    with E.Solver.from_problem(P, precision=prec) as s:
+        s.assemble_problem(P)
+        M, _ = s.get_rows(np.arange(P.n_rows))
+        info = s.solve(max_iter=5, atol=0.0, btol=0.0, shift=shift, drop_tol=drop,
+                       check_every=5)
+        a = s.coeffs()
+    gpu_dropped = a == 0.0
+    oracle_dropped = np.zeros_like(gpu_dropped)
+    borderline = np.zeros_like(gpu_dropped)
+    for j in range(M.shape[1] // K):
+        Mj = M[:, j * K:(j + 1) * K]
+        _, kept, ratio = KR.cholesky_dropping(Mj.T @ Mj, shift, drop)
+        oracle_dropped[j * K:(j + 1) * K] = ~kept
+        borderline[j * K:(j + 1) * K] = (ratio > 0.5 * drop) & (ratio < 2.0 * drop)
+    print(f"dropped: gpu {gpu_dropped.sum()} (info {info.precond_dropped}), oracle "
+          f"{oracle_dropped.sum()}, borderline {borderline.sum()} of {a.size}")
+    assert info.precond_dropped == gpu_dropped.sum()
+    assert oracle_dropped.sum() > a.size // 4          # the case is under-resolved
+    assert np.all((gpu_dropped == oracle_dropped) | borderline)
+    assert np.all(np.isfinite(a))
+
+
 _SOLVE_CASES = [
     ("poisson1d_J16_K64_N2000", WL.config_poisson1d),
     ("dho_L1-8_K24_N1000", lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000)),
