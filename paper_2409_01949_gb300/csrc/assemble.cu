@@ -209,6 +209,35 @@ __global__ void k_fill_cell_of_R(const int* __restrict__ cell_pstart, int n_cell
     cell_of_R[p] = c;
 }
 
+// Work lists written on the device from one record per group (a group's
+// items are consecutive in the output, off[g] .. off[g + 1]).
+// Entry steps: item t of group g is (ent[g], rows t).
+__global__ void k_expand_steps(const int* __restrict__ ent, const int64_t* __restrict__ off,
+                               int n_groups, int rows, int2* __restrict__ out) {
+  const int g = blockIdx.x;
+  if (g >= n_groups) return;
+  const int64_t o = off[g], n = off[g + 1] - o;
+  const int e = ent[g];
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) out[o + t] = make_int2(e, (int)(rows * t));
+}
+
+// Assembly tiles: item t of group g = (first entry, entries, 32 t, 0).
+__global__ void k_expand_ltiles(const int2* __restrict__ grp, const int64_t* __restrict__ off,
+                                int n_groups, int4* __restrict__ out) {
+  const int g = blockIdx.x;
+  if (g >= n_groups) return;
+  const int64_t o = off[g], n = off[g + 1] - o;
+  const int2 b = grp[g];
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x)
+    out[o + t] = make_int4(b.x, b.y, (int)(32 * t), 0);
+}
+
+__global__ void k_fill_int(int* __restrict__ p, int64_t n, int v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
 // ------------------------------------------------------------------ K1 ------
 template <class T> struct Math;
 template <> struct Math<float> {
@@ -642,7 +671,6 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   h->d_pts_user.alloc(n * dim * sizeof(double), st);
   h->d_rhs_user.alloc(n * sizeof(double), st);
   h->d_cls_user.alloc(n * sizeof(int), st);
-  std::vector<int> cls_user(n);
   {
     int64_t off = 0;
     for (int b = 0; b < n_sets; ++b) {
@@ -652,12 +680,13 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
                                  m * dim * sizeof(double), cudaMemcpyDefault, st));
       CUDA_CHECK(cudaMemcpyAsync(h->d_rhs_user.as<double>() + off, sets[b].rhs, m * sizeof(double),
                                  cudaMemcpyDefault, st));
-      std::fill(cls_user.begin() + off, cls_user.begin() + off + m, b);
+      k_fill_int<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1216), 256, 0, st>>>(
+          h->d_cls_user.as<int>() + off, m, b);
+      count_launch(h);
       off += m;
     }
+    check_launch("k_fill_int");
   }
-  CUDA_CHECK(cudaMemcpyAsync(h->d_cls_user.p, cls_user.data(), n * sizeof(int),
-                             cudaMemcpyHostToDevice, st));
 
   // K0: cells
   const int nc = h->n_cells;
@@ -713,16 +742,12 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   }
   if (h->NPR >= (int64_t)1 << 31) ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "more than 2^31 panel rows");
   h->nnz = 0;
-  std::vector<int2> tiles;
-  for (int e = 0; e < ne; ++e) {
-    int c = h->entry_cell[e];
-    int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
-    h->nnz += (int64_t)h->cell_count[c] * h->K;
-    for (int p = 0; p < pad; p += 32) tiles.push_back(make_int2(e, p));
-  }
-  h->n_tiles = (int64_t)tiles.size();
-  // assembly tiles: one per (cell, level group of covering entries, 32 rows)
-  std::vector<int4> ltiles;
+  for (int e = 0; e < ne; ++e) h->nnz += (int64_t)h->cell_count[h->entry_cell[e]] * h->K;
+  h->n_tiles = -1;   // the QR's tiles, made when it runs (ensure_qr_tiles)
+  // assembly tiles: one per (cell, level group of covering entries, 32 rows),
+  // written on the device from one record per group
+  std::vector<int2> lgrp;
+  std::vector<int64_t> lgoff(1, 0);
   h->nl_max = 1;
   for (int c = 0; c < nc; ++c) {
     const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
@@ -731,10 +756,12 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
       const int en = h->cell_level_off[(size_t)c * (h->L + 1) + l + 1];
       if (en <= b) continue;
       h->nl_max = std::max(h->nl_max, en - b);
-      for (int p = 0; p < pad; p += 32) ltiles.push_back(make_int4(b, en - b, p, 0));
+      if (pad == 0) continue;
+      lgrp.push_back(make_int2(b, en - b));
+      lgoff.push_back(lgoff.back() + ceil_div(pad, 32));
     }
   }
-  h->n_ltiles = (int64_t)ltiles.size();
+  h->n_ltiles = lgoff.back();
   // Gram pair count: subdomain pairs (i <= j) that share a cell with points,
   // and the algorithmic Gram flops 2 K^2 per shared row and pair
   h->gram_flops = 0.0;
@@ -753,8 +780,18 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   up(h->d_panel_off, h->panel_off.data(), (h->n_sub + 1) * sizeof(int64_t));
   up(h->d_cell_eoff, h->cell_eoff.data(), (nc + 1) * sizeof(int64_t));
   up(h->d_entry_base, h->entry_base.data(), ne * sizeof(int64_t));
-  up(h->d_tiles, tiles.data(), tiles.size() * sizeof(int2));
-  up(h->d_ltiles, ltiles.data(), ltiles.size() * sizeof(int4));
+  {
+    DevBuf dg, dgo;
+    up(dg, lgrp.data(), lgrp.size() * sizeof(int2));
+    up(dgo, lgoff.data(), lgoff.size() * sizeof(int64_t));
+    h->d_ltiles.alloc(std::max<int64_t>(h->n_ltiles, 1) * sizeof(int4), st);
+    if (!lgrp.empty()) {
+      k_expand_ltiles<<<(unsigned)lgrp.size(), 128, 0, st>>>(dg.as<int2>(), dgo.as<int64_t>(),
+                                                             (int)lgrp.size(), h->d_ltiles.as<int4>());
+      check_launch("k_expand_ltiles");
+      count_launch(h);
+    }
+  }
 
   // K0: scatter into cells, deterministic order inside each cell, gather row data
   const int64_t NR = h->NR;
@@ -891,4 +928,38 @@ void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, doub
   CUDA_CHECK(cudaMemcpyAsync(out, dout.p, n * h->NPhi * sizeof(double), cudaMemcpyDefault, st));
   if (h_out) CUDA_CHECK(cudaMemcpyAsync(h_out, dh.p, n * sizeof(double), cudaMemcpyDefault, st));
   CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+// Per-entry 32-row tiles of the panels, (entry, first row), for the QR's
+// densification: made on the first call after an assembly.
+void ensure_qr_tiles(elmfb_ctx* h) {
+  if (h->n_tiles >= 0) return;
+  const int ne = (int)h->cover_sub.size();
+  std::vector<int> ent(ne);
+  std::vector<int64_t> off(ne + 1, 0);
+  for (int e = 0; e < ne; ++e) {
+    const int c = h->entry_cell[e];
+    ent[e] = e;
+    off[e + 1] = off[e] + ceil_div(h->cell_pstart[c + 1] - h->cell_pstart[c], 32);
+  }
+  expand_entry_steps(h, ent, off, 32, h->d_tiles);
+  h->n_tiles = off[ne];
+}
+
+void expand_entry_steps(elmfb_ctx* h, const std::vector<int>& ent, const std::vector<int64_t>& off,
+                        int rows, DevBuf& out) {
+  cudaStream_t st = h->stream;
+  const int ng = (int)ent.size();
+  out.alloc(std::max<int64_t>(off.back(), 1) * sizeof(int2), st);
+  if (ng == 0) return;
+  DevBuf de, doff;
+  de.alloc(ng * sizeof(int), st);
+  doff.alloc((ng + 1) * sizeof(int64_t), st);
+  CUDA_CHECK(cudaMemcpyAsync(de.p, ent.data(), ng * sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_CHECK(cudaMemcpyAsync(doff.p, off.data(), (ng + 1) * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, st));
+  k_expand_steps<<<(unsigned)ng, 128, 0, st>>>(de.as<int>(), doff.as<int64_t>(), ng, rows,
+                                               out.as<int2>());
+  check_launch("k_expand_steps");
+  count_launch(h);
 }

@@ -351,6 +351,7 @@ __global__ void k_qr_iota(int* __restrict__ perm, int n) {
 
 template <class T>
 void densify(elmfb_ctx* h, const void* panels, double* A, int64_t ld) {
+  ensure_qr_tiles(h);
   const int64_t blocks = ceil_div(h->n_tiles, 4);
   if (blocks > 0)
     k_qr_densify<T><<<(unsigned)blocks, 128, 0, h->stream>>>(

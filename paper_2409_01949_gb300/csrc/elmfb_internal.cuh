@@ -192,7 +192,7 @@ struct elmfb_ctx {
   DevBuf d_cell_eoff, d_entry_base;
   DevBuf d_panels;      // [NPR*K] FP64, FP32 or FP32 pairs
   DevBuf d_tiles;       // per-panel tiles: (entry, first row) of 32 rows
-  int64_t n_tiles = 0;
+  int64_t n_tiles = -1;  // -1 until the QR needs them (ensure_qr_tiles)
   DevBuf d_ltiles;      // assembly tiles: (first entry of a level group, entries, first row)
   int64_t n_ltiles = 0;
   int nl_max = 1;       // most covering entries of one level in one cell
@@ -263,6 +263,11 @@ void stage_collect(elmfb_ctx* h);
 
 // assembly (assemble.cu)
 void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets);
+// out = the items (ent[g], rows t), t < off[g + 1] - off[g], of every group g in
+// order, written on the device (int2; off[0] = 0)
+void expand_entry_steps(elmfb_ctx* h, const std::vector<int>& ent, const std::vector<int64_t>& off,
+                        int rows, DevBuf& out);
+void ensure_qr_tiles(elmfb_ctx* h);   // h->d_tiles / n_tiles for the QR's densification
 void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, double* h_out);
 
 // tensor-core Gram (gram_tc.cu)

@@ -2605,40 +2605,40 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   // chunks of at most 2048 rows of one panel, as 16-row steps (entry, first
   // row) taken cell by cell in the cell-interleaved storage
   const int ne = (int)h->cover_sub.size();
-  std::vector<std::vector<int>> pent(h->n_sub);
-  for (int e = 0; e < ne; ++e) pent[h->cover_sub[e]].push_back(e);
+  // entries panel by panel (each panel's in cell order), with the global
+  // index of each entry's first step; the steps themselves are written on
+  // the device (k_expand_steps), the chunks here from the step counts
+  std::vector<int> pent_off(h->n_sub + 1, 0), pent(ne);
+  for (int e = 0; e < ne; ++e) pent_off[h->cover_sub[e] + 1]++;
+  for (int s2 = 0; s2 < h->n_sub; ++s2) pent_off[s2 + 1] += pent_off[s2];
+  {
+    std::vector<int> fill(pent_off.begin(), pent_off.end() - 1);
+    for (int e = 0; e < ne; ++e) pent[fill[h->cover_sub[e]]++] = e;
+  }
+  std::vector<int64_t> step_off(ne + 1, 0);
+  for (int q = 0; q < ne; ++q) {
+    const int c = h->entry_cell[pent[q]];
+    step_off[q + 1] = step_off[q] + ceil_div(h->cell_pstart[c + 1] - h->cell_pstart[c], 16);
+  }
+  if (step_off[ne] >= ((int64_t)1 << 31))
+    ELMFB_THROW(ELMFB_ERR_UNSUPPORTED, "block-Jacobi set-up: more than 2^31 row steps");
   std::vector<int4> chunks;
-  std::vector<int2> steps;
   std::vector<int> chunk_off(h->n_sub + 1, 0);
   constexpr int kStepsPerChunk = kDiagChunk / 16;
-  for (int s = 0; s < h->n_sub; ++s) {
-    chunk_off[s] = (int)chunks.size();
-    int first = (int)steps.size();
-    for (int e : pent[s]) {
-      const int c = h->entry_cell[e];
-      const int pad = h->cell_pstart[c + 1] - h->cell_pstart[c];
-      for (int p0 = 0; p0 < pad; p0 += 16) {
-        steps.push_back(make_int2(e, p0));
-        if ((int)steps.size() - first == kStepsPerChunk) {
-          chunks.push_back(make_int4(s, first, kStepsPerChunk, 0));
-          first = (int)steps.size();
-        }
-      }
-    }
-    if ((int)steps.size() > first)
-      chunks.push_back(make_int4(s, first, (int)steps.size() - first, 0));
+  for (int s2 = 0; s2 < h->n_sub; ++s2) {
+    chunk_off[s2] = (int)chunks.size();
+    const int64_t f0 = step_off[pent_off[s2]], f1 = step_off[pent_off[s2 + 1]];
+    for (int64_t f = f0; f < f1; f += kStepsPerChunk)
+      chunks.push_back(make_int4(s2, (int)f, (int)std::min<int64_t>(kStepsPerChunk, f1 - f), 0));
   }
   chunk_off[h->n_sub] = (int)chunks.size();
   const int KT = K * (K + 1) / 2;
   DevBuf dch, dcoff, dsteps;
   dch.alloc(std::max<size_t>(chunks.size(), 1) * sizeof(int4), st);
   dcoff.alloc(chunk_off.size() * sizeof(int), st);
-  dsteps.alloc(std::max<size_t>(steps.size(), 1) * sizeof(int2), st);
   CUDA_CHECK(cudaMemcpyAsync(dch.p, chunks.data(), chunks.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, st));
-  if (!steps.empty())
-    CUDA_CHECK(cudaMemcpyAsync(dsteps.p, steps.data(), steps.size() * sizeof(int2),
-                               cudaMemcpyHostToDevice, st));
+  expand_entry_steps(h, pent, step_off, 16, dsteps);
   CUDA_CHECK(cudaMemcpyAsync(dcoff.p, chunk_off.data(), chunk_off.size() * sizeof(int),
                              cudaMemcpyHostToDevice, st));
   h->d_gpart.alloc(std::max<size_t>(chunks.size(), 1) * KT * sizeof(double), st);
