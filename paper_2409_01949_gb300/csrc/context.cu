@@ -22,13 +22,39 @@
 
 namespace {
 
-inline uint64_t splitmix64_mix(uint64_t z) {
+__host__ __device__ inline uint64_t splitmix64_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
 }
-inline uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+__host__ __device__ inline uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return splitmix64_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+// The random parameters of every column, on the device: column q (of kept
+// subdomain q / K) takes the draws of its full-grid column qf, outputs
+// qf (d + 1) + p of the stream, u = the top 24 bits / 2^24, value a (2u - 1);
+// W and b in FP64 and FP32.
+__global__ void k_params(uint64_t seed, double a, int d, int K, int64_t n_cols,
+                         const int* __restrict__ param_sub, double* __restrict__ W64,
+                         double* __restrict__ b64, float* __restrict__ W32,
+                         float* __restrict__ b32) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_cols;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t qf = (int64_t)param_sub[q / K] * K + q % K;
+    for (int p = 0; p <= d; ++p) {
+      const uint64_t z = splitmix64_at(seed, (uint64_t)qf * (d + 1) + p);
+      const double u = (double)(z >> 40) * (1.0 / 16777216.0);
+      const double v = a * (2.0 * u - 1.0);
+      if (p < d) {
+        W64[q * d + p] = v;
+        W32[q * d + p] = (float)v;
+      } else {
+        b64[q] = v;
+        b32[q] = (float)v;
+      }
+    }
+  }
 }
 
 template <class F>
@@ -51,9 +77,9 @@ int guarded(elmfb_ctx* h, F&& f) {
 // Drop every subdomain whose centre lies inside a hole box (strictly between
 // its faces, a face on the domain box's boundary counting as part of the
 // hole; paper §4.1, the L-shaped domain of §4.4) and renumber the rest in
-// order: the
-// geometry, the parameters (drawn for the full grid, so that a kept column
-// keeps its draw), the cell ranges and the covering lists are compacted.
+// order: the geometry, the parameter sources (the full-grid subdomain whose
+// draws a kept one keeps), the cell ranges and the covering lists are
+// compacted.
 void discard_in_holes(elmfb_ctx* h) {
   const elmfb_config& c = h->cfg;
   const int nfull = h->n_sub;
@@ -76,9 +102,9 @@ void discard_in_holes(elmfb_ctx* h) {
     if (!in_hole) map[s] = kept++;
   }
   if (kept == 0) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "every subdomain lies inside a hole");
-  const int K = h->K, d = h->dim;
+  const int K = h->K;
   std::vector<SubGeom> sub(kept);
-  std::vector<double> W((size_t)kept * K * d), B((size_t)kept * K);
+  std::vector<int> psub(kept);
   std::vector<int> c0[2], c1[2];
   for (int i = 0; i < 2; ++i) {
     c0[i].resize(kept);
@@ -89,12 +115,8 @@ void discard_in_holes(elmfb_ctx* h) {
     const int t = map[s];
     if (t < 0) continue;
     sub[t] = h->sub[s];
+    psub[t] = h->param_sub[s];
     lev_off[h->sub[s].level + 1]++;
-    for (int k = 0; k < K; ++k) {
-      for (int p = 0; p < d; ++p)
-        W[((size_t)t * K + k) * d + p] = h->Wh[((size_t)s * K + k) * d + p];
-      B[(size_t)t * K + k] = h->bh[(size_t)s * K + k];
-    }
     for (int i = 0; i < 2; ++i) {
       c0[i][t] = h->sub_c0[i][s];
       c1[i][t] = h->sub_c1[i][s];
@@ -117,8 +139,7 @@ void discard_in_holes(elmfb_ctx* h) {
   }
   cover_off[h->n_cells] = (int)cover_sub.size();
   h->sub.swap(sub);
-  h->Wh.swap(W);
-  h->bh.swap(B);
+  h->param_sub.swap(psub);
   for (int i = 0; i < 2; ++i) {
     h->sub_c0[i].swap(c0[i]);
     h->sub_c1[i].swap(c1[i]);
@@ -196,20 +217,11 @@ void build_geometry(elmfb_ctx* h) {
     }
   }
 
-  // random parameters: column q draws outputs q*(d+1)+p
-  const int d = h->dim;
-  h->Wh.resize((size_t)h->NPhi * d);
-  h->bh.resize(h->NPhi);
-  const double a = c.weight_scale;
-  for (int64_t q = 0; q < h->NPhi; ++q) {
-    for (int p = 0; p <= d; ++p) {
-      uint64_t z = splitmix64_at(c.seed, (uint64_t)q * (d + 1) + p);
-      double u = (double)(z >> 40) * (1.0 / 16777216.0);
-      double v = a * (2.0 * u - 1.0);
-      if (p < d) h->Wh[q * d + p] = v;
-      else h->bh[q] = v;
-    }
-  }
+  // random parameters (drawn on the device, k_params): column q draws
+  // outputs q*(d+1)+p of the stream; each subdomain is its own source until
+  // subdomains in holes are discarded
+  h->param_sub.resize(h->n_sub);
+  for (int s = 0; s < h->n_sub; ++s) h->param_sub[s] = s;
 
   // cells: common refinement of all supports, per dimension
   for (int i = 0; i < 2; ++i) {
@@ -426,11 +438,21 @@ void prof_harvest(elmfb_ctx* h) {
 
 void upload_geometry(elmfb_ctx* h) {
   upload(h, h->d_sub, h->sub);
-  std::vector<float> W32(h->Wh.begin(), h->Wh.end()), b32(h->bh.begin(), h->bh.end());
-  upload(h, h->d_W32, W32);
-  upload(h, h->d_b32, b32);
-  upload(h, h->d_W64, h->Wh);
-  upload(h, h->d_b64, h->bh);
+  {
+    cudaStream_t st = h->stream;
+    const int d = h->dim;
+    DevBuf dps;
+    upload(h, dps, h->param_sub);
+    h->d_W64.alloc(std::max<int64_t>(h->NPhi * d, 1) * sizeof(double), st);
+    h->d_b64.alloc(std::max<int64_t>(h->NPhi, 1) * sizeof(double), st);
+    h->d_W32.alloc(std::max<int64_t>(h->NPhi * d, 1) * sizeof(float), st);
+    h->d_b32.alloc(std::max<int64_t>(h->NPhi, 1) * sizeof(float), st);
+    k_params<<<(unsigned)std::min<int64_t>(ceil_div(h->NPhi, 256), 1216), 256, 0, st>>>(
+        h->cfg.seed, h->cfg.weight_scale, d, h->K, h->NPhi, dps.as<int>(), h->d_W64.as<double>(),
+        h->d_b64.as<double>(), h->d_W32.as<float>(), h->d_b32.as<float>());
+    check_launch("k_params");
+    count_launch(h);
+  }
   std::vector<double> bnd(h->bnd[0]);
   bnd.insert(bnd.end(), h->bnd[1].begin(), h->bnd[1].end());
   upload(h, h->d_bnd, bnd);
@@ -537,9 +559,12 @@ int elmfb_get_sizes(elmfb_t h, elmfb_sizes* o) {
 int elmfb_get_params(elmfb_t h, double* W, double* b) {
   return guarded(h, [&] {
     if (W)
-      CUDA_CHECK(cudaMemcpy(W, h->Wh.data(), h->Wh.size() * sizeof(double), cudaMemcpyDefault));
+      CUDA_CHECK(cudaMemcpyAsync(W, h->d_W64.p, h->NPhi * h->dim * sizeof(double),
+                                 cudaMemcpyDefault, h->stream));
     if (b)
-      CUDA_CHECK(cudaMemcpy(b, h->bh.data(), h->bh.size() * sizeof(double), cudaMemcpyDefault));
+      CUDA_CHECK(cudaMemcpyAsync(b, h->d_b64.p, h->NPhi * sizeof(double), cudaMemcpyDefault,
+                                 h->stream));
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
   });
 }
 

@@ -146,7 +146,7 @@ struct elmfb_ctx {
   int64_t NPhi = 0;
   std::vector<int> lev_n, lev_sub_off;  // [L], [L+1]
   std::vector<SubGeom> sub;             // [n_sub]
-  std::vector<double> Wh, bh;           // [NPhi*dim], [NPhi]
+  std::vector<int> param_sub;           // per subdomain: the full-grid subdomain whose draws it takes
   std::vector<double> bnd[2];           // cell boundaries per dimension
   int nc[2] = {1, 1};
   int n_cells = 0;

@@ -1797,16 +1797,23 @@ __global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ 
   }
 }
 
-// Block size of the kernels that apply the packed pair triangle: 512 threads
-// and about 70 KB of shared memory at K = 128, three blocks per SM, so that
-// every panel of the 2-D workloads (a few hundred) runs in one wave.
+// Block size of the kernels that apply the packed pair triangle: four groups
+// of K (rounded up to 32) threads, 128 to 512 -- at K = 128, 512 threads and
+// about 70 KB of shared memory, three blocks per SM, so that every panel of
+// the 2-D workloads (a few hundred) runs in one wave; at K = 64, 256 threads,
+// so that the thousands of small panels of the large 2-D workload run with
+// more blocks per SM rather than more idle threads per block.
 constexpr int kTriThreads = 512;
+static int tri_threads(int K) {
+  const int Kp = (K + 31) & ~31;
+  return std::min(kTriThreads, std::max(128, 4 * Kp));
+}
 
 // Shared memory of those kernels: the triangle, a K-vector of pairs, G x K
 // group partials and the copy's mbarrier.
 static size_t tri_smem_bytes(int K) {
   const int Kp = (K + 31) & ~31;
-  const int G = kTriThreads / Kp;
+  const int G = tri_threads(K) / Kp;
   return (size_t)(tri_pairs(K) + K + (int64_t)G * K) * sizeof(float2) + 16;
 }
 
@@ -3014,7 +3021,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       panel_chunk_sums(h, fp, gpart, n_units, scal);
       prof_end(h, KID_PANEL_T);
       prof_begin(h, KID_UPDATE, csum_bytes + tri_bytes + 72.0 * N);
-      k_lsqr_tail_tri<<<h->n_sub, kTriThreads, tsmem, st>>>(
+      k_lsqr_tail_tri<<<h->n_sub, tri_threads(K), tsmem, st>>>(
           fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(),
           h->d_w.as<double>(), h->d_x_sol.as<double>(), scal, init, vpart,
           h->d_tmp.as<double>(), fp.tf.p, low_kind, dcount.as<unsigned int>(),
@@ -3713,7 +3720,7 @@ void launch_batch_iteration(const BatchShape& sh, const BatchInst* d_inst, const
                                                    nullptr, 0, nullptr, d_inst, d_cmap);
   // the tail (the last block of each instance runs its recurrence)
   ensure_dyn_smem((const void*)k_lsqr_tail_tri, sh.tsmem);
-  k_lsqr_tail_tri<<<n_t, kTriThreads, sh.tsmem, st>>>(
+  k_lsqr_tail_tri<<<n_t, tri_threads(sh.K), sh.tsmem, st>>>(
       nullptr, nullptr, nullptr, sh.K, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
       nullptr, sh.low_kind, nullptr, nullptr, d_inst, d_tmap);
   check_launch("multi-instance LSQR iteration");
