@@ -705,7 +705,7 @@ void assemble_system(elmfb_ctx* h, int n_sets, const elmfb_rowset* sets) {
   CUDA_CHECK(cudaMemcpyAsync(h->cell_count.data(), h->d_cell_count.p, nc * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   if (flags[0]) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "a collocation point lies outside the domain box");
 
   // host: padded cell layout, panel offsets, tiles
@@ -898,7 +898,7 @@ void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, doub
   {
     std::vector<int64_t> hr(n);
     CUDA_CHECK(cudaMemcpyAsync(hr.data(), drows.p, n * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     for (int64_t v : hr)
       if (v < 0 || v >= h->n_rows) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "row index out of range");
   }
@@ -927,7 +927,7 @@ void export_rows(elmfb_ctx* h, const int64_t* rows, int64_t n, double* out, doub
   count_launch(h);
   CUDA_CHECK(cudaMemcpyAsync(out, dout.p, n * h->NPhi * sizeof(double), cudaMemcpyDefault, st));
   if (h_out) CUDA_CHECK(cudaMemcpyAsync(h_out, dh.p, n * sizeof(double), cudaMemcpyDefault, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
 }
 
 // Per-entry 32-row tiles of the panels, (entry, first row), for the QR's

@@ -38,11 +38,13 @@ struct BatchRound {
     BatchInst inst{};
     BatchShape shape;
     int64_t launches = 0;   // shared launches attributed to this member, not yet reported
+    double rec[kRoundRecord];   // its scalars and flags after the last round
   };
   // one launch shape's members and their block maps
   struct Class {
     BatchShape shape;
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;   // blocking-sync event: the launcher sleeps while the round runs
     std::vector<BatchInst> h_inst;
     std::vector<int2> h_fmap, h_cmap, h_tmap;
     DevBuf inst, fmap, cmap, tmap;
@@ -54,6 +56,15 @@ struct BatchRound {
   std::vector<Member> slot;
   std::vector<char> member;
   std::vector<cudaStream_t> streams;   // one per class in use, kept across rebuilds
+  std::vector<cudaEvent_t> events;     // and its blocking-sync event
+  // every member's record gathered after a round by one kernel and one copy
+  // (rather than a copy and a wait in every member's thread)
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gdone = nullptr;
+  DevBuf all_inst, d_rec;
+  std::vector<BatchInst> h_all;
+  std::vector<int> all_slot;
+  double* h_rec = nullptr;   // pinned, n_slots records
   std::vector<std::unique_ptr<Class>> classes;
   bool dirty = false;
   int members = 0, arrived = 0;
@@ -61,8 +72,31 @@ struct BatchRound {
   int err = ELMFB_OK;
   std::string msg;
   int64_t rounds = 0, rebuilds = 0;
+  // ELMFB_BATCH_TRACE=<file>: one line per round (start and length in ms
+  // since the batch began, the wait since the previous round ended, members,
+  // fused-pass units), written when the batch ends
+  struct Trace {
+    double t0, ms, gap;
+    int members, units;
+  };
+  bool trace = false;
+  std::vector<Trace> log;
+  std::chrono::steady_clock::time_point start = std::chrono::steady_clock::now(),
+                                        last_end = start;
 
   void rebuild() {
+    h_all.clear();
+    all_slot.clear();
+    for (int q = 0; q < (int)slot.size(); ++q)
+      if (member[q]) {
+        h_all.push_back(slot[q].inst);
+        all_slot.push_back(q);
+      }
+    if (!h_all.empty()) {
+      all_inst.alloc(h_all.size() * sizeof(BatchInst), gstream);
+      CUDA_CHECK(cudaMemcpyAsync(all_inst.p, h_all.data(), h_all.size() * sizeof(BatchInst),
+                                 cudaMemcpyHostToDevice, gstream));
+    }
     // members by launch shape, each shape's members dealt round-robin to up
     // to kGroups groups on their own streams, so that one group's tail (a
     // latency-bound kernel) overlaps another's fused pass
@@ -88,11 +122,15 @@ struct BatchRound {
         cudaStream_t st = nullptr;
         CUDA_CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         streams.push_back(st);
+        cudaEvent_t ev = nullptr;
+        CUDA_CHECK(cudaEventCreateWithFlags(&ev, cudaEventBlockingSync | cudaEventDisableTiming));
+        events.push_back(ev);
       }
       classes.push_back(std::make_unique<Class>());
       Class& k = *classes.back();
       k.shape = g.first;
       k.stream = streams[c];
+      k.done = events[c];
       k.first_slot = g.second.front();
       for (int j = 0; j < (int)g.second.size(); ++j) {
         const BatchInst& bi = slot[g.second[j]].inst;
@@ -118,6 +156,7 @@ struct BatchRound {
   // Launch one round and wait for it; then release the waiting members.
   // Called with the lock held by the last member to arrive (or to leave).
   void run_locked() {
+    const auto t0 = std::chrono::steady_clock::now();
     if (err == ELMFB_OK) {
       try {
         if (dirty) rebuild();
@@ -128,10 +167,30 @@ struct BatchRound {
                                    (int)k->h_cmap.size(), k->tmap.as<int2>(),
                                    (int)k->h_tmap.size(), k->stream);
         for (auto& k : classes) {
-          CUDA_CHECK(cudaStreamSynchronize(k->stream));
+          CUDA_CHECK(cudaEventRecord(k->done, k->stream));
+          CUDA_CHECK(cudaStreamWaitEvent(gstream, k->done, 0));
           slot[k->first_slot].launches += 3 * (int64_t)check_every;
         }
+        const int n = (int)all_slot.size();
+        launch_gather_records(all_inst.as<BatchInst>(), n, d_rec.as<double>(), gstream);
+        CUDA_CHECK(cudaMemcpyAsync(h_rec, d_rec.p, (size_t)n * kRoundRecord * sizeof(double),
+                                   cudaMemcpyDeviceToHost, gstream));
+        CUDA_CHECK(cudaEventRecord(gdone, gstream));
+        CUDA_CHECK(cudaEventSynchronize(gdone));   // sleeps (blocking-sync event)
+        if (n > 0) slot[all_slot[0]].launches += 1;
+        for (int j = 0; j < n; ++j)
+          std::copy(h_rec + (size_t)j * kRoundRecord, h_rec + (size_t)(j + 1) * kRoundRecord,
+                    slot[all_slot[j]].rec);
         ++rounds;
+        if (trace) {
+          const auto t1 = std::chrono::steady_clock::now();
+          using ms = std::chrono::duration<double, std::milli>;
+          int units = 0;
+          for (auto& k : classes) units += (int)k->h_fmap.size();
+          log.push_back({ms(t0 - start).count(), ms(t1 - t0).count(), ms(t0 - last_end).count(),
+                         members, units});
+          last_end = t1;
+        }
       } catch (const elmfb_error& e) {
         err = e.code;
         msg = e.msg;
@@ -156,7 +215,7 @@ void round_join(BatchRound* r, int q, const BatchInst& inst, const BatchShape& s
   r->dirty = true;
 }
 
-int64_t round_step(BatchRound* r, int q) {
+int64_t round_step(BatchRound* r, int q, double* rec) {
   std::unique_lock<std::mutex> lk(r->m);
   if (r->err != ELMFB_OK) ELMFB_THROW(r->err, "multi-instance round: " + r->msg);
   ++r->arrived;
@@ -172,6 +231,7 @@ int64_t round_step(BatchRound* r, int q) {
     }
   }
   if (r->err != ELMFB_OK) ELMFB_THROW(r->err, "multi-instance round: " + r->msg);
+  std::copy(r->slot[q].rec, r->slot[q].rec + kRoundRecord, rec);
   const int64_t n = r->slot[q].launches;
   r->slot[q].launches = 0;
   return n;
@@ -214,6 +274,18 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
   round.check_every = std::max(1, opts ? opts->check_every : 10);
   round.slot.resize(w);
   round.member.assign(w, 0);
+  if (cudaStreamCreateWithFlags(&round.gstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&round.gdone, cudaEventBlockingSync | cudaEventDisableTiming) !=
+          cudaSuccess ||
+      cudaMallocHost(&round.h_rec, (size_t)w * kRoundRecord * sizeof(double)) != cudaSuccess)
+    return ELMFB_ERR_CUDA;
+  try {
+    round.d_rec.alloc((size_t)w * kRoundRecord * sizeof(double), round.gstream);
+  } catch (...) {
+    return ELMFB_ERR_CUDA;
+  }
+  const char* trace_path = getenv("ELMFB_BATCH_TRACE");
+  round.trace = trace_path && trace_path[0];
   auto worker = [&](int slot) {
     cudaSetDevice(device);
     cudaStream_t st = nullptr;
@@ -230,6 +302,8 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
       elmfb_t h = nullptr;
       int rc = elmfb_create(&h, &it.cfg, st);
       if (rc != ELMFB_OK) std::snprintf(res.message, sizeof(res.message), "create failed");
+      // more worker threads than host cores: waits sleep instead of spinning
+      if (h) h->blocking_sync = true;
       if (rc == ELMFB_OK) rc = elmfb_assemble(h, it.n_sets, it.sets);
       elmfb_solve_info info{};
       if (rc == ELMFB_OK) {
@@ -273,11 +347,26 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
   std::vector<std::thread> pool;
   for (int t = 0; t < w; ++t) pool.emplace_back(worker, t);
   for (auto& t : pool) t.join();
+  if (round.trace) {
+    if (FILE* f = std::fopen(trace_path, "w")) {
+      std::fprintf(f, "t0_ms,ms,gap_ms,members,units\n");
+      for (const auto& r : round.log)
+        std::fprintf(f, "%.3f,%.3f,%.3f,%d,%d\n", r.t0, r.ms, r.gap, r.members, r.units);
+      std::fclose(f);
+    }
+  }
   round.classes.clear();
+  round.all_inst.release();
+  round.d_rec.release();
+  cudaStreamSynchronize(round.gstream);
+  cudaStreamDestroy(round.gstream);
+  cudaEventDestroy(round.gdone);
+  cudaFreeHost(round.h_rec);
   for (cudaStream_t st : round.streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
+  for (cudaEvent_t ev : round.events) cudaEventDestroy(ev);
   for (int i = 0; i < n; ++i)
     if (results[i].status != ELMFB_OK) return results[i].status;
   return ELMFB_OK;

@@ -172,7 +172,7 @@ void coarse_setup(elmfb_ctx* h, int levels, double shift,
   check_launch("k_coarse_chol_inv");
   int flags[2];
   CUDA_CHECK(cudaMemcpyAsync(flags, fl.p, sizeof(flags), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   if (flags[0]) ELMFB_THROW(ELMFB_ERR_BREAKDOWN, "coarse block Cholesky failed after shift increases");
   if (retries) *retries = flags[1];
 }

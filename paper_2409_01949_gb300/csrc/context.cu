@@ -370,6 +370,18 @@ void ensure_dyn_smem(const void* func, size_t bytes, bool max_carveout) {
   cur = want;
 }
 
+void stream_sync(elmfb_ctx* h) {
+  if (!h->blocking_sync) {
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    return;
+  }
+  if (!h->sync_ev)
+    CUDA_CHECK(cudaEventCreateWithFlags(&h->sync_ev,
+                                        cudaEventBlockingSync | cudaEventDisableTiming));
+  CUDA_CHECK(cudaEventRecord(h->sync_ev, h->stream));
+  CUDA_CHECK(cudaEventSynchronize(h->sync_ev));
+}
+
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
@@ -379,7 +391,7 @@ void check_launch(const char* what) {
 void stage_begin(elmfb_ctx* h, int s) { CUDA_CHECK(cudaEventRecord(h->st[s].a, h->stream)); }
 void stage_end(elmfb_ctx* h, int s) {
   CUDA_CHECK(cudaEventRecord(h->st[s].b, h->stream));
-  CUDA_CHECK(cudaEventSynchronize(h->st[s].b));
+  stream_sync(h);
   float ms = 0.f;
   CUDA_CHECK(cudaEventElapsedTime(&ms, h->st[s].a, h->st[s].b));
   h->stage_ms[s] = ms;
@@ -424,7 +436,7 @@ void prof_end(elmfb_ctx* h, int kid) {
 
 void prof_harvest(elmfb_ctx* h) {
   if (h->prof_live.empty()) return;
-  CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  stream_sync(h);
   for (auto& r : h->prof_live) {
     float ms = 0.f;
     CUDA_CHECK(cudaEventElapsedTime(&ms, r.a, r.b));
@@ -523,6 +535,7 @@ void elmfb_destroy(elmfb_t h) {
     cudaEventDestroy(r.b);
   }
   for (auto e : h->prof_pool) cudaEventDestroy(e);
+  if (h->sync_ev) cudaEventDestroy(h->sync_ev);
   delete h;  // DevBuf destructors free device memory, ordered on the handle's stream
   cudaStreamSynchronize(st);
 }
@@ -564,7 +577,7 @@ int elmfb_get_params(elmfb_t h, double* W, double* b) {
     if (b)
       CUDA_CHECK(cudaMemcpyAsync(b, h->d_b64.p, h->NPhi * sizeof(double), cudaMemcpyDefault,
                                  h->stream));
-    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    stream_sync(h);
   });
 }
 
@@ -638,7 +651,7 @@ int elmfb_get_coeffs(elmfb_t h, double* a) {
     if (!a) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null output");
     CUDA_CHECK(cudaMemcpyAsync(a, h->d_a.p, h->NPhi * sizeof(double), cudaMemcpyDefault,
                                h->stream));
-    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    stream_sync(h);
   });
 }
 
@@ -647,7 +660,7 @@ int elmfb_set_coeffs(elmfb_t h, const double* a) {
     if (!a) ELMFB_THROW(ELMFB_ERR_INVALID_ARG, "null input");
     CUDA_CHECK(cudaMemcpyAsync(h->d_a.p, a, h->NPhi * sizeof(double), cudaMemcpyDefault,
                                h->stream));
-    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    stream_sync(h);
     h->have_coeffs = true;
   });
 }

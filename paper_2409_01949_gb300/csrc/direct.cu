@@ -431,7 +431,7 @@ void qr_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     count_launch(h, 2 * batch);
     check_launch("qr step");
     CUDA_CHECK(cudaMemcpyAsync(&hs, S, sizeof(QrState), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     if (hs.bad != 0.0) ELMFB_THROW(ELMFB_ERR_NONFINITE, "QR: non-finite column norm");
     if (hs.stop) break;
   }
@@ -451,7 +451,7 @@ void qr_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   if (rank > 0)
     CUDA_CHECK(cudaMemcpyAsync(&rrr, A + (int64_t)(rank - 1) * ld + (rank - 1), sizeof(double),
                                cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   stage_end(h, 5);
   info->status = ELMFB_OK;
   info->iterations = rank;

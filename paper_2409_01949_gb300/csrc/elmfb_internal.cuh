@@ -247,6 +247,8 @@ struct elmfb_ctx {
   // batched graphs: a device flag the LSQR loop's kernels read first (nonzero:
   // return at once); null outside a batched graph
   struct BatchRound* round = nullptr;   // the batch's coordinator (batch.cu), or null
+  bool blocking_sync = false;   // waits sleep on an event (batch workers) instead of spinning
+  cudaEvent_t sync_ev = nullptr;
   int round_slot = -1;
   bool dual() const { return cfg.precision == ELMFB_FP32_DF32; }
   bool fp64() const { return cfg.precision == ELMFB_FP64; }
@@ -378,11 +380,14 @@ struct BatchShape {
   }
 };
 struct BatchRound;
+// The staged LSQR scalars and the first four flags of one member after a
+// round, as the coordinator gathers them for all members at once.
+constexpr int kRoundRecord = 20;   // 16 staged scalars, 4 flags
 // join with the instance's arrays; then round_step() once per check interval
-// (returns the shared launches attributed to this member, each launch to one
-// member); round_leave() when done
+// (fills rec with this member's record; returns the shared launches
+// attributed to it, each launch to one member); round_leave() when done
 void round_join(BatchRound* r, int slot, const BatchInst& inst, const BatchShape& shape);
-int64_t round_step(BatchRound* r, int slot);
+int64_t round_step(BatchRound* r, int slot, double* rec);
 void round_leave(BatchRound* r, int slot);
 int round_interval(const BatchRound* r);   // iterations per round
 // one LSQR iteration of a launch shape's members: n_f units, n_c slices, n_t
@@ -390,6 +395,8 @@ int round_interval(const BatchRound* r);   // iterations per round
 void launch_batch_iteration(const BatchShape& sh, const BatchInst* d_inst, const int2* d_fmap,
                             int n_f, const int2* d_cmap, int n_c, const int2* d_tmap, int n_t,
                             cudaStream_t st);
+// out[j] = member j's record (kRoundRecord doubles) from its scal and flags
+void launch_gather_records(const BatchInst* d_inst, int n, double* out, cudaStream_t st);
 
 // learned preconditioner (gnn.cu)
 void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info);
@@ -420,3 +427,8 @@ int64_t count_gram_pairs(const elmfb_ctx* h);   // pairs (i <= j) sharing a cell
 // device.  The attribute is process-wide, so handles solving concurrently in
 // other threads only ever see it grow.
 void ensure_dyn_smem(const void* func, size_t bytes, bool max_carveout = false);
+// Wait for the handle's stream: cudaStreamSynchronize, or with blocking_sync
+// an event recorded on it and waited on with blocking synchronisation (the
+// thread sleeps: a batch runs more host threads than cores, and spinning
+// waiters starve the threads with work to do).
+void stream_sync(elmfb_ctx* h);

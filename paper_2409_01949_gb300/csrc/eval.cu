@@ -241,7 +241,7 @@ void error_norms(elmfb_ctx* h, const double* uh, const double* ur, int64_t n, do
   std::vector<double> a(nb * 5), b(nb);
   CUDA_CHECK(cudaMemcpyAsync(a.data(), p1.p, nb * 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaMemcpyAsync(b.data(), p2.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   double sad = 0, sd2 = 0, su2 = 0, mx = 0, var = 0;
   for (int i = 0; i < nb; ++i) {
     sad += a[i * 5 + 1];

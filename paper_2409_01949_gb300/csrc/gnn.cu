@@ -361,7 +361,7 @@ double gnn_pass(elmfb_ctx* h, int B, const float* X, const float* T, const float
     std::vector<double> lp(kDotBlocks);
     CUDA_CHECK(cudaMemcpyAsync(lp.data(), h->d_gnn_lp.p, kDotBlocks * sizeof(double),
                                cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     for (double v : lp) loss += v;
   }
   check_launch("gnn pass");
@@ -375,7 +375,7 @@ double dot(elmfb_ctx* h, const double* a, const double* b, int64_t n, DevBuf& pa
   std::vector<double> p(kDotBlocks);
   CUDA_CHECK(cudaMemcpyAsync(p.data(), part.p, kDotBlocks * sizeof(double), cudaMemcpyDeviceToHost,
                              h->stream));
-  CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  stream_sync(h);
   double s = 0.0;
   for (double v : p) s += v;
   return s;
@@ -458,7 +458,7 @@ struct Fcg {
                                    h->stream));
         CUDA_CHECK(cudaMemcpyAsync(hx.data(), x, N * sizeof(double), cudaMemcpyDeviceToHost,
                                    h->stream));
-        CUDA_CHECK(cudaStreamSynchronize(h->stream));
+        stream_sync(h);
         rec_r->insert(rec_r->end(), hr.begin(), hr.end());
         rec_x->insert(rec_x->end(), hx.begin(), hx.end());
       }
@@ -610,7 +610,7 @@ int elmfb_gnn_eval(elmfb_t h, int batch, const float* x, const float* t, const f
     if (t && grad)
       CUDA_CHECK(cudaMemcpyAsync(grad, dg.p, gnn_weight_count(h->K) * sizeof(float),
                                  cudaMemcpyDefault, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     if (loss) *loss = L;
     return ELMFB_OK;
   } catch (const elmfb_error& e) {

@@ -241,7 +241,7 @@ void gram_compute(elmfb_ctx* h) {
   stage_end(h, 3);
   int flags[4];
   CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   if (flags[2]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "tensor-core Gram: a pipeline wait timed out");
   h->have_gram = true;
 }

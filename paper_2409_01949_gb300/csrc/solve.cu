@@ -1852,7 +1852,7 @@ __device__ __forceinline__ void tri_wait(uint64_t* bar, int* __restrict__ flags)
 __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restrict__ pco,
                              int K, double* __restrict__ v, double* __restrict__ scal, int init,
                              const float2* Xs, float2* zs, float2* part, uint64_t* bar,
-                             int* __restrict__ flags, int s) {
+                             int* __restrict__ flags, int s, bool ident) {
   __shared__ double red[33];
   __shared__ double sh_beta;
   __shared__ float2 sh_ib;
@@ -1884,10 +1884,10 @@ __device__ double tail_v_tri(const double* __restrict__ csum, const int* __restr
     zs[i] = make_float2(S, C);
   }
   __syncthreads();
-  tri_wait(bar, flags);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  float2* ys = part;   // the group partials are consumed
-  for (int k0 = wid; k0 < K; k0 += 4 * nw) {
+  float2* ys = ident ? zs : part;   // the group partials are consumed
+  if (!ident) tri_wait(bar, flags);
+  for (int k0 = wid; k0 < K && !ident; k0 += 4 * nw) {
     float2 acc[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -2268,8 +2268,9 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
     s = bm.y;
     nblk = I.n_sub;
   }
+  const bool ident = Xt == nullptr;   // no preconditioner: X = I
   TriSmem sm(trsm, K);
-  tri_fetch(sm.Xs, Xt, s, K, sm.bar);
+  if (!ident) tri_fetch(sm.Xs, Xt, s, K, sm.bar);
   const int64_t o = (int64_t)s * K;
   if (!init) {
     const double ia = scal[S_TSCALE], pr = scal[S_PHI_RHO], tr = scal[S_THETA_RHO];
@@ -2282,10 +2283,18 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
     }
   }
   const double nrm = tail_v_tri(csum, pco, K, v, scal, init, sm.Xs, sm.vec, sm.part, sm.bar,
-                                flags, s);
+                                flags, s, ident);
   if (threadIdx.x == 0) norm_partial[s] = nrm;
   __syncthreads();
-  tail_t_tri(K, sm.Xs, sm.vec, sm.part, t, tlow, low_kind, s);
+  if (ident) {   // t' = v'
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+      const double vn = v[o + j];
+      t[o + j] = vn;
+      store_low(tlow, low_kind, o + j, vn);
+    }
+  } else {
+    tail_t_tri(K, sm.Xs, sm.vec, sm.part, t, tlow, low_kind, s);
+  }
   // the last block: alpha, the recurrence, the staged scalars
   __threadfence();
   __syncthreads();
@@ -2712,7 +2721,7 @@ void block_jacobi_setup(elmfb_ctx* h, double shift, bool identity, double abs_sh
   count_launch(h);
   int flags[6];
   CUDA_CHECK(cudaMemcpyAsync(flags, h->d_flags.p, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   h->bj_retries = flags[4];
   h->bj_dropped = flags[5];
   if (flags[3]) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "block-Jacobi set-up: a copy wait timed out");
@@ -2992,11 +3001,12 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     launch_fused<T>(h, fp, t, mode, scal, gpart, tf);
   };
   // FP32 and DF32 panels apply X_j as FP32 pairs (block_jacobi_setup keeps a
-  // pair copy); the fused path's partials are then pairs too
-  const bool xpairs = !std::is_same<T, double>::value && fused && fp.pairs && !identity;
-  const float2* Xt = xpairs ? h->d_R2.as<float2>() : nullptr;
+  // pair copy), or no X at all without a preconditioner (the tail's identity
+  // form); the fused path's partials are then pairs too
+  const bool xpairs = !std::is_same<T, double>::value && fused && fp.pairs;
+  const float2* Xt = xpairs && !identity ? h->d_R2.as<float2>() : nullptr;
   const size_t tsmem = tri_smem_bytes(K);
-  const double tri_bytes = 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
+  const double tri_bytes = identity ? 0.0 : 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
   // FP32 / DF32 panels: the whole tail in k_lsqr_tail_tri (the update deferred
@@ -3075,7 +3085,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     double s0[kStage];
     CUDA_CHECK(cudaMemcpyAsync(s0, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
                                st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     arnorm0 = s0[S_ARNORM];
   }
 
@@ -3115,12 +3125,23 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     h->launches = l0;
     return g;
   };
-  auto check_scalars = [&]() -> bool {   // true: converged
-    CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double), cudaMemcpyDeviceToHost,
-                               st));
+  // true: converged; rec = the staged scalars and the first four flags as
+  // the batch's coordinator gathered them, else read here
+  auto check_scalars = [&](const double* rec = nullptr) -> bool {
     int dflags[4];
-    CUDA_CHECK(cudaMemcpyAsync(dflags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (rec) {
+      for (int i = 0; i < kStage; ++i) sc[i] = rec[i];
+      for (int i = 0; i < 4; ++i) dflags[i] = (int)rec[kStage + i];
+    } else {
+      // with blocking waits, sleep until the interval is done: the copies
+      // into pageable memory below would otherwise wait for it in a spin
+      if (h->blocking_sync) stream_sync(h);
+      CUDA_CHECK(cudaMemcpyAsync(sc, scal + kStage, kStage * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaMemcpyAsync(dflags, h->d_flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                                 st));
+      stream_sync(h);
+    }
     if (dflags[3])
       ELMFB_THROW(ELMFB_ERR_TIMEOUT,
                   "LSQR iteration: an on-device wait (bulk copy) timed out");
@@ -3180,7 +3201,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     bi.n_pchunks = fp.n_pchunks;
     bi.n_sub = h->n_sub;
     // the rounds run on the batch's own streams: the start-up work on st first
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     struct Leave {   // leave the rounds on every exit, errors included
       elmfb_ctx* h;
       bool joined = false;
@@ -3190,10 +3211,11 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     } lv{h};
     round_join(h->round, h->round_slot, bi, bsh);
     lv.joined = true;
+    double rec[kRoundRecord];
     while (it + o->check_every <= max_it) {
-      h->launches += round_step(h->round, h->round_slot);
+      h->launches += round_step(h->round, h->round_slot, rec);
       it += o->check_every;
-      if (check_scalars()) {
+      if (check_scalars(rec)) {
         status = ELMFB_OK;
         break;
       }
@@ -3275,7 +3297,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     CUDA_CHECK(cudaMemcpyAsync(rec.data(), scal + 2 * kScal, rec.size() * sizeof(double),
                                cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaMemcpyAsync(sv, dsv.p, sizeof(sv), cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
+    stream_sync(h);
     for (int i = 0; i <= gk_k; ++i) {
       h->gk_alpha[i] = rec[2 * i];
       h->gk_beta[i] = rec[2 * i + 1];
@@ -3554,7 +3576,7 @@ void pcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   std::vector<double> gp(fp.n_units);
   CUDA_CHECK(cudaMemcpyAsync(gp.data(), gpart, fp.n_units * sizeof(double),
                              cudaMemcpyDeviceToHost, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   stage_end(h, 5);
   double rn = 0.0;
   for (double v : gp) rn += v;
@@ -3597,7 +3619,7 @@ void residual_pairs(elmfb_ctx* h, const double* a) {
   h->d_u.alloc(h->NR * sizeof(double), st);
   launch_fused<df2>(h, fp, a, 1, sc.as<double>(), gp.as<double>());
   check_launch("refinement residual");
-  CUDA_CHECK(cudaStreamSynchronize(st));   // fp's buffers are released on return
+  stream_sync(h);   // fp's buffers are released on return
 }
 
 // Mixed-precision LSQR with refinement (ELMFB_FP32_DF32): `refine` outer
@@ -3658,7 +3680,7 @@ void lsqr_refine(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info
     info->sigma_min = ii.sigma_min;
   }
   CUDA_CHECK(cudaMemcpyAsync(h->d_a.p, acc.p, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CUDA_CHECK(cudaStreamSynchronize(st));
+  stream_sync(h);
   info->status = status;
   info->iterations = total;
   info->solve_ms = solve_ms;
@@ -3697,6 +3719,25 @@ template void launch_fused<double>(elmfb_ctx*, FusedPlan&, const double*, int, d
                                    const void*);
 template void launch_fused<df2>(elmfb_ctx*, FusedPlan&, const double*, int, double*, double*,
                                 const void*);
+
+namespace {
+__global__ void k_gather_records(const BatchInst* __restrict__ inst, int n,
+                                 double* __restrict__ out) {
+  const int j = blockIdx.x;
+  if (j >= n) return;
+  const BatchInst& I = inst[j];
+  const int t = threadIdx.x;
+  if (t < kStage) out[(int64_t)j * kRoundRecord + t] = I.scal[kStage + t];
+  else if (t < kRoundRecord) out[(int64_t)j * kRoundRecord + t] = (double)I.flags[t - kStage];
+}
+}  // namespace
+
+void launch_gather_records(const BatchInst* d_inst, int n, double* out, cudaStream_t st) {
+  static_assert(kRoundRecord == kStage + 4, "a record is the staged scalars and four flags");
+  if (n <= 0) return;
+  k_gather_records<<<n, 32, 0, st>>>(d_inst, n, out);
+  check_launch("k_gather_records");
+}
 
 void launch_batch_iteration(const BatchShape& sh, const BatchInst* d_inst, const int2* d_fmap,
                             int n_f, const int2* d_cmap, int n_c, const int2* d_tmap, int n_t,
