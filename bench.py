@@ -604,7 +604,7 @@ def main():
                     help="time every n-th launch of the roofline kernel in the timed steps")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-iters", type=int, default=5000)
-    ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--batch-workers", type=int, default=32)
     ap.add_argument("--no-shared", action="store_true",
                     help="batched workload: launch each instance's LSQR kernels alone instead of "
                          "in shared multi-instance launches")
