@@ -2748,50 +2748,74 @@ __device__ int gk_sturm_count(const double* __restrict__ gk, int k, double lam, 
   return cnt;
 }
 
-// Extreme singular values of B_k by multisection of the Sturm count (one warp,
-// 32 trial points per round; geometric spacing once the interval is off 0;
-// to 1e-10 relative):
+// Extreme singular values of B_k by multisection of the Sturm count (one
+// block: 256 trial points per round for each extreme, the two searched side
+// by side; geometric spacing once the interval is off 0; to 1e-10 relative):
 // out[0] = sigma_max (the point where the count reaches 2k+1), out[1] =
 // sigma_min (where it reaches k+2).  k = 0: zeros.
-__global__ void k_bidiag_extremes(const double* __restrict__ gk, int k, double* __restrict__ out) {
-  const int lane = threadIdx.x;
+__global__ void __launch_bounds__(512) k_bidiag_extremes(const double* __restrict__ gk, int k,
+                                                        double* __restrict__ out) {
+  // two groups of 256 threads, one per extreme: each round every thread
+  // counts at one of 256 points spread geometrically over the group's
+  // interval, and the interval shrinks to the pair of points where the count
+  // crosses the target
+  constexpr int kPts = 256;
+  __shared__ double lam_s[2][kPts];
+  __shared__ int nb_w[16];
+  __shared__ double lo_s[2], hi_s[2];
+  __shared__ int done_s[2];
+  const int g = threadIdx.x / kPts, i = threadIdx.x % kPts;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k <= 0) {
-    if (lane < 2) out[lane] = 0.0;
+    if (threadIdx.x < 2) out[threadIdx.x] = 0.0;
     return;
   }
   double bound = 0.0, emax2 = 0.0, eprev = 0.0;
-  for (int i = 0; i < 2 * k; ++i) {
-    const int j = i >> 1;
-    const double e = fabs((i & 1) ? gk[2 * (j + 1) + 1] : gk[2 * j]);
+  for (int q = 0; q < 2 * k; ++q) {
+    const int j = q >> 1;
+    const double e = fabs((q & 1) ? gk[2 * (j + 1) + 1] : gk[2 * j]);
     bound = fmax(bound, eprev + e);
     eprev = e;
     emax2 = fmax(emax2, e * e);
   }
   bound = fmax(bound, eprev) * (1.0 + 1e-12) + 1e-300;
   const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
-  for (int which = 0; which < 2; ++which) {
-    const int target = which == 0 ? 2 * k + 1 : k + 2;
-    double lo = 0.0, hi = bound;
-    for (int round = 0; round < 200 && hi > lo * (1.0 + 1e-10); ++round) {
-      const double f = (double)(lane + 1) / 33.0;
-      const double lam = lo > 0.0 ? lo * pow(hi / lo, f) : hi * f;
-      const bool below = gk_sturm_count(gk, k, lam, pivmin) < target;
-      const unsigned m = __ballot_sync(0xffffffffu, below);
-      // lanes 0..n-1 lie below the point; the new interval is [lam_{n-1}, lam_n]
-      const int nb = __popc(m);
-      const double l_lo = __shfl_sync(0xffffffffu, lam, nb > 0 ? nb - 1 : 0);
-      const double l_hi = __shfl_sync(0xffffffffu, lam, nb < 32 ? nb : 31);
-      if (nb > 0) lo = l_lo;
-      if (nb < 32) hi = l_hi;
-    }
-    if (lane == 0) out[which] = 0.5 * (lo + hi);
+  const int target = g == 0 ? 2 * k + 1 : k + 2;   // sigma_max, sigma_min
+  if (threadIdx.x < 2) {
+    lo_s[threadIdx.x] = 0.0;
+    hi_s[threadIdx.x] = bound;
+    done_s[threadIdx.x] = 0;
   }
+  __syncthreads();
+  for (int round = 0; round < 200 && !(done_s[0] && done_s[1]); ++round) {
+    const double lo = lo_s[g], hi = hi_s[g];
+    const double f = (double)(i + 1) / (kPts + 1);
+    const double lam = lo > 0.0 ? lo * pow(hi / lo, f) : hi * f;
+    lam_s[g][i] = lam;
+    const bool below = !done_s[g] && gk_sturm_count(gk, k, lam, pivmin) < target;
+    const unsigned m = __ballot_sync(0xffffffffu, below);
+    if (lane == 0) nb_w[warp] = __popc(m);
+    __syncthreads();
+    if (i == 0 && !done_s[g]) {
+      // points 0..nb-1 lie below the crossing; the new interval is [lam_{nb-1}, lam_nb]
+      int nb = 0;
+      for (int w = 0; w < kPts / 32; ++w) nb += nb_w[g * (kPts / 32) + w];
+      double nlo = lo, nhi = hi;
+      if (nb > 0) nlo = lam_s[g][nb - 1];
+      if (nb < kPts) nhi = lam_s[g][nb];
+      lo_s[g] = nlo;
+      hi_s[g] = nhi;
+      done_s[g] = !(nhi > nlo * (1.0 + 1e-10));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) out[threadIdx.x] = 0.5 * (lo_s[threadIdx.x] + hi_s[threadIdx.x]);
 }
 
 }  // namespace
 
 void bidiag_extremes(elmfb_ctx* h, const double* gk, int k, double* out2) {
-  k_bidiag_extremes<<<1, 32, 0, h->stream>>>(gk, k, out2);
+  k_bidiag_extremes<<<1, 512, 0, h->stream>>>(gk, k, out2);
   check_launch("k_bidiag_extremes");
   count_launch(h);
 }
