@@ -382,7 +382,7 @@ struct BatchShape {
 struct BatchRound;
 // The staged LSQR scalars and the first four flags of one member after a
 // round, as the coordinator gathers them for all members at once.
-constexpr int kRoundRecord = 20;   // 16 staged scalars, 4 flags
+constexpr int kRoundRecord = 28;   // 24 staged scalars, 4 flags
 // join with the instance's arrays; then round_step() once per check interval
 // (fills rec with this member's record; returns the shared launches
 // attributed to it, each launch to one member); round_leave() when done

@@ -40,21 +40,26 @@ namespace {
 
 constexpr int kGatherBlocks = 1216;   // 152 SMs x 8
 constexpr int kGatherThreads = 256;
-constexpr int kScal = 32;             // device scalar slots
+constexpr int kScal = 48;             // device scalar slots
 
-// scalar slots in d_scal: [0, 16) committed values read by the kernels of an
-// iteration, [16, 32) staged values written by the kernel that runs the
+// scalar slots in d_scal: [0, 24) committed values read by the kernels of an
+// iteration, [24, 48) staged values written by the kernel that runs the
 // recurrence; the next iteration's first reader of committed values
 // (k_panel_chunks, or k_precond without the fused plan) commits staged ->
 // committed.
-constexpr int kStage = 16;
+constexpr int kStage = 24;
 enum {
   S_ALPHA = 0, S_BETA, S_RHOBAR, S_PHIBAR, S_ANORM2, S_RNORM, S_ARNORM, S_ITER, S_BNORM,
   S_XNORM2, S_BAD, S_PHI_RHO, S_THETA_RHO,
-  S_BSQ,    // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
-  S_TSCALE, // 1/alpha: the fused pass's factor on M t' (mode 2, t' = P v' unnormalised)
-  S_GKCAP   // capacity (entries) of the Golub-Kahan record after the 2 kScal slots
+  S_BSQ,     // staged: sum of the fused pass's ||u'||^2 partials (beta^2), formed once
+  S_TSCALE,  // 1/alpha: the fused pass's factor on M t' (mode 2, t' = P v' unnormalised)
+  S_GKCAP,   // capacity (entries) of the Golub-Kahan record after the 2 kScal slots
+  // the stopping tests on the device (LSQR with the pair tail, S_STOP_ON):
+  S_DONE,    // set by the recurrence once a test is met; the next iterations' kernels return
+  S_ARN0,    // ||(M P)^T h|| = alpha_1 beta_1, staged at the start
+  S_STOP_ON, S_NTOL, S_BTOL, S_ATOL   // set by the host, both copies
 };
+static_assert(S_ATOL < kStage, "scalar slots");
 
 // Record alpha_{i+1}, beta_{i+1} of LSQR step i (i = the new iteration count;
 // 0 = the start: alpha_1, beta_1) after the scalar slots, while it fits: the
@@ -982,6 +987,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
   __shared__ double sd[32][kFusedRows];
   __shared__ double su[kFusedRows];
   __shared__ double red[33];
+  if (mode == 2 && scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
   const int c = un.x;
@@ -1205,6 +1211,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe(
     flags = I.flags;
     ub = bm.y;
   }
+  if (mode == 2 && scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
   __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
@@ -1425,6 +1432,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused_pipe_df(
     double* __restrict__ u, const double* __restrict__ hvec, int mode,
     double* __restrict__ partial, double* __restrict__ norm_partial, int S, int mmax,
     int* __restrict__ flags) {
+  if (mode == 2 && scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   extern __shared__ __align__(128) unsigned char ring_raw[];
   __shared__ __align__(8) uint64_t full[kPipeMaxStages];    // chunk copied in
   __shared__ __align__(8) uint64_t empty[kPipeMaxStages];   // stage free again
@@ -1632,6 +1640,7 @@ __global__ void k_panel_chunks(const double* __restrict__ partial, const int* __
     scal = I.scal;
     cb = bm.y;
   }
+  if (beta_partial && scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   // block 0, LSQR: commit the scalars staged by the previous update (no kernel
   // of the iteration reads the committed slots before this point), then
   // warp 0 forms beta^2 = sum of the norm partials, once for every panel block
@@ -2127,6 +2136,24 @@ __device__ LsqrStep lsqr_recurrence(double* __restrict__ scal, double a2, double
     sg[S_THETA_RHO] = r.theta_rho;
     sg[S_TSCALE] = r.ia;
     record_bidiagonal(scal, sg[S_ITER], alpha, beta);
+    // the host's stopping tests (Paige & Saunders' btol / atol, and ntol on
+    // the normal residual relative to its start), taken here after every
+    // iteration: once one is met the next iterations' kernels return at once,
+    // so the solve stops at this iteration whatever the host's check interval
+    if (scal[kStage + S_STOP_ON] != 0.0) {
+      bool done = !(alpha > 0.0) || !(beta > 0.0) || sg[S_BAD] != 0.0;
+      if (init) {
+        sg[S_ARN0] = arnorm;
+      } else {
+        const double anorm = sqrt(anorm2), rn = phibar_new;
+        const double btol = scal[kStage + S_BTOL], atol = scal[kStage + S_ATOL];
+        const double ntol = scal[kStage + S_NTOL];
+        done = done || (btol > 0.0 && rn <= btol * sg[S_BNORM]) ||
+               (atol > 0.0 && anorm > 0.0 && rn > 0.0 && arnorm <= atol * anorm * rn) ||
+               (ntol > 0.0 && arnorm <= ntol * scal[kStage + S_ARN0]);
+      }
+      sg[S_DONE] = done ? 1.0 : 0.0;
+    }
   }
   return r;
 }
@@ -2268,6 +2295,7 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
     s = bm.y;
     nblk = I.n_sub;
   }
+  if (scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   const bool ident = Xt == nullptr;   // no preconditioner: X = I
   TriSmem sm(trsm, K);
   if (!ident) tri_fetch(sm.Xs, Xt, s, K, sm.bar);
@@ -3045,6 +3073,12 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     CUDA_CHECK(cudaMemsetAsync(h->d_x_sol.p, 0, N * sizeof(double), st));
   }
   const int fmode = xpairs ? 2 : 0;              // the loop's fused-pass mode
+  if (xpairs) {   // the stopping tests run on the device too (lsqr_recurrence)
+    const double sp[4] = {1.0, o->ntol, o->btol, o->atol};   // S_STOP_ON .. S_ATOL
+    CUDA_CHECK(cudaMemcpyAsync(scal + S_STOP_ON, sp, sizeof(sp), cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(scal + kStage + S_STOP_ON, sp, sizeof(sp), cudaMemcpyHostToDevice,
+                               st));
+  }
   const int tail_launches = xpairs ? 1 : 2;      // besides the slice sums (counted by themselves)
   auto fused_tail = [&](int init) {
     if (xpairs) {
@@ -3175,7 +3209,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     const bool t1 = o->btol > 0.0 && rn <= o->btol * sc[S_BNORM];
     const bool t2 = o->atol > 0.0 && anorm > 0.0 && rn > 0.0 && arn <= o->atol * anorm * rn;
     const bool t3 = o->ntol > 0.0 && arn <= o->ntol * arnorm0;
-    return t1 || t2 || t3 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0;
+    return t1 || t2 || t3 || sc[S_ALPHA] == 0.0 || sc[S_BETA] == 0.0 || sc[S_DONE] != 0.0;
   };
   // Multi-instance launches: full check intervals in the batch's shared
   // rounds, then leave and finish any remainder below.  FP32 panels with the
@@ -3308,6 +3342,8 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   check_launch("lsqr finish");
   CUDA_CHECK(cudaMemcpyAsync(sc, scal, kStage * sizeof(double), cudaMemcpyDeviceToHost, st));
   stage_end(h, 5);
+  // with the tests on the device the iterations stop where a test was met
+  if (xpairs) it = (int)sc[S_ITER];
   // the Golub-Kahan record and its extreme singular values (B_k, k = it)
   const int gk_k = std::min(it, gk_cap - 1);
   h->gk_alpha.assign(gk_k + 1, 0.0);

@@ -41,7 +41,9 @@ def test_refinement_gets_below_the_fp32_floor_on_the_oscillator():
     g = json.load(open(GOLDEN))["dho_L1-64_K96_N20000"]
     P = WL.config_dho_ml()
     a32, e32, i32 = _solve(P, E.FP32, 1, 1e-6)
-    aref, eref, iref = _solve(P, E.FP32_DF32, 3, 1e-2)
+    # inner solves to ntol 3e-3: LSQR stops at the iteration where its test is
+    # met, so looser inner solves leave the correction short
+    aref, eref, iref = _solve(P, E.FP32_DF32, 3, 3e-3)
     print(f"FP32 panels: rel L2 {e32:.3e} ({i32.iterations} its); FP32 + pair refinement x3: "
           f"{eref:.3e} ({iref.iterations} its); oracle LSQR-15000 {g['lsqr']['rel_l2']:.3e}")
     assert eref <= 1.01 * g["lsqr"]["rel_l2"]
