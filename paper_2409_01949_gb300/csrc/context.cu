@@ -416,9 +416,10 @@ const char* kKernelNames[KID_COUNT] = {"assemble_panels", "gather_Mv",    "entry
 
 void prof_begin(elmfb_ctx* h, int kid, double bytes) {
   if (!h->prof || !((h->prof_mask >> kid) & 1)) return;
-  h->prof_now[kid] = h->prof_seen[kid]++ % h->prof_stride == 0;
+  const int64_t seq = h->prof_seen[kid]++;
+  h->prof_now[kid] = seq % h->prof_stride == 0;
   if (!h->prof_now[kid]) return;
-  ProfRec r{kid, prof_event(h), prof_event(h)};
+  ProfRec r{kid, prof_event(h), prof_event(h), seq};
   CUDA_CHECK(cudaEventRecord(r.a, h->stream));
   h->prof_live.push_back(r);
   h->prof_bytes[kid] = bytes;
@@ -431,13 +432,16 @@ void prof_end(elmfb_ctx* h, int kid) {
       CUDA_CHECK(cudaEventRecord(it->b, h->stream));
       break;
     }
-  if (h->prof_live.size() > 4096) prof_harvest(h);
+  // the most recent records stay live: a solve may still drop them
+  if (h->prof_live.size() > 4096) prof_harvest(h, 256);
 }
 
-void prof_harvest(elmfb_ctx* h) {
-  if (h->prof_live.empty()) return;
+void prof_harvest(elmfb_ctx* h, size_t keep) {
+  if (h->prof_live.size() <= keep) return;
+  const size_t n = h->prof_live.size() - keep;
   stream_sync(h);
-  for (auto& r : h->prof_live) {
+  for (size_t i = 0; i < n; ++i) {
+    const ProfRec& r = h->prof_live[i];
     float ms = 0.f;
     CUDA_CHECK(cudaEventElapsedTime(&ms, r.a, r.b));
     h->prof_ms[r.kid] += ms;
@@ -445,7 +449,21 @@ void prof_harvest(elmfb_ctx* h) {
     h->prof_pool.push_back(r.a);
     h->prof_pool.push_back(r.b);
   }
-  h->prof_live.clear();
+  h->prof_live.erase(h->prof_live.begin(), h->prof_live.begin() + n);
+}
+
+void prof_drop_from(elmfb_ctx* h, int kid, int64_t from) {
+  auto& v = h->prof_live;
+  size_t w = 0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    if (v[i].kid == kid && v[i].seq >= from) {
+      h->prof_pool.push_back(v[i].a);
+      h->prof_pool.push_back(v[i].b);
+    } else {
+      v[w++] = v[i];
+    }
+  }
+  v.resize(w);
 }
 
 void upload_geometry(elmfb_ctx* h) {

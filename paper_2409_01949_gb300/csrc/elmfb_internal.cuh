@@ -132,6 +132,7 @@ enum KernelId {
 struct ProfRec {
   int kid;
   cudaEvent_t a, b;
+  int64_t seq;   // the kernel's launch ordinal (prof_seen before this launch)
 };
 
 struct elmfb_ctx {
@@ -416,7 +417,10 @@ void error_norms(elmfb_ctx* h, const double* uh, const double* ur, int64_t n, do
 // per-kernel profiling (no-ops when h->prof is false)
 void prof_begin(elmfb_ctx* h, int kid, double bytes);
 void prof_end(elmfb_ctx* h, int kid);
-void prof_harvest(elmfb_ctx* h);
+void prof_harvest(elmfb_ctx* h, size_t keep = 0);   // all but the last `keep` records
+// forget the timed launches of kernel kid from ordinal `from` on (launches
+// that returned at once after LSQR stopped on the device)
+void prof_drop_from(elmfb_ctx* h, int kid, int64_t from);
 
 // helpers
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -3342,8 +3342,16 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   check_launch("lsqr finish");
   CUDA_CHECK(cudaMemcpyAsync(sc, scal, kStage * sizeof(double), cudaMemcpyDeviceToHost, st));
   stage_end(h, 5);
-  // with the tests on the device the iterations stop where a test was met
-  if (xpairs) it = (int)sc[S_ITER];
+  // with the tests on the device the iterations stop where a test was met;
+  // the launches after it returned at once and are no part of the kernels'
+  // timings
+  if (xpairs) {
+    const int ran = (int)sc[S_ITER];
+    if (ran < it && h->prof)
+      for (int kid : {(int)KID_FUSED, (int)KID_PANEL_T, (int)KID_UPDATE})
+        prof_drop_from(h, kid, h->prof_seen[kid] - (it - ran));
+    it = ran;
+  }
   // the Golub-Kahan record and its extreme singular values (B_k, k = it)
   const int gk_k = std::min(it, gk_cap - 1);
   h->gk_alpha.assign(gk_k + 1, 0.0);
