@@ -67,6 +67,7 @@ struct BatchRound {
   double* h_rec = nullptr;   // pinned, n_slots records
   std::vector<std::unique_ptr<Class>> classes;
   bool dirty = false;
+  bool running = false;   // a round is on the GPU (the lock is free meanwhile)
   int members = 0, arrived = 0;
   uint64_t gen = 0;
   int err = ELMFB_OK;
@@ -154,12 +155,30 @@ struct BatchRound {
   }
 
   // Launch one round and wait for it; then release the waiting members.
-  // Called with the lock held by the last member to arrive (or to leave).
-  void run_locked() {
+  // Called with the lock held (lk) once every member has arrived and no round
+  // runs.  The lock is released while the GPU works, so that instances can
+  // join (their arrivals count towards the next round) and leave meanwhile;
+  // the round's own arrays (classes, all_inst, all_slot) change only in
+  // rebuild(), which runs here before the lock is released.
+  void run_round(std::unique_lock<std::mutex>& lk) {
     const auto t0 = std::chrono::steady_clock::now();
-    if (err == ELMFB_OK) {
+    running = true;
+    arrived = 0;
+    const int participants = members;
+    int e_code = err;
+    std::string e_msg;
+    if (e_code == ELMFB_OK) {
       try {
         if (dirty) rebuild();
+      } catch (const elmfb_error& e) {
+        e_code = e.code;
+        e_msg = e.msg;
+      }
+    }
+    const int n = (int)all_slot.size();
+    if (e_code == ELMFB_OK) {
+      lk.unlock();
+      try {
         for (int i = 0; i < check_every; ++i)
           for (auto& k : classes)
             launch_batch_iteration(k->shape, k->inst.as<BatchInst>(), k->fmap.as<int2>(),
@@ -169,37 +188,42 @@ struct BatchRound {
         for (auto& k : classes) {
           CUDA_CHECK(cudaEventRecord(k->done, k->stream));
           CUDA_CHECK(cudaStreamWaitEvent(gstream, k->done, 0));
-          slot[k->first_slot].launches += 3 * (int64_t)check_every;
         }
-        const int n = (int)all_slot.size();
         launch_gather_records(all_inst.as<BatchInst>(), n, d_rec.as<double>(), gstream);
         CUDA_CHECK(cudaMemcpyAsync(h_rec, d_rec.p, (size_t)n * kRoundRecord * sizeof(double),
                                    cudaMemcpyDeviceToHost, gstream));
         CUDA_CHECK(cudaEventRecord(gdone, gstream));
         CUDA_CHECK(cudaEventSynchronize(gdone));   // sleeps (blocking-sync event)
-        if (n > 0) slot[all_slot[0]].launches += 1;
-        for (int j = 0; j < n; ++j)
-          std::copy(h_rec + (size_t)j * kRoundRecord, h_rec + (size_t)(j + 1) * kRoundRecord,
-                    slot[all_slot[j]].rec);
-        ++rounds;
-        if (trace) {
-          const auto t1 = std::chrono::steady_clock::now();
-          using ms = std::chrono::duration<double, std::milli>;
-          int units = 0;
-          for (auto& k : classes) units += (int)k->h_fmap.size();
-          log.push_back({ms(t0 - start).count(), ms(t1 - t0).count(), ms(t0 - last_end).count(),
-                         members, units});
-          last_end = t1;
-        }
       } catch (const elmfb_error& e) {
-        err = e.code;
-        msg = e.msg;
+        e_code = e.code;
+        e_msg = e.msg;
       } catch (...) {
-        err = ELMFB_ERR_CUDA;
-        msg = "unexpected error";
+        e_code = ELMFB_ERR_CUDA;
+        e_msg = "unexpected error";
       }
+      lk.lock();
     }
-    arrived = 0;
+    if (e_code == ELMFB_OK) {
+      for (auto& k : classes) slot[k->first_slot].launches += 3 * (int64_t)check_every;
+      if (n > 0) slot[all_slot[0]].launches += 1;
+      for (int j = 0; j < n; ++j)
+        std::copy(h_rec + (size_t)j * kRoundRecord, h_rec + (size_t)(j + 1) * kRoundRecord,
+                  slot[all_slot[j]].rec);
+      ++rounds;
+      if (trace) {
+        const auto t1 = std::chrono::steady_clock::now();
+        using ms = std::chrono::duration<double, std::milli>;
+        int units = 0;
+        for (auto& k : classes) units += (int)k->h_fmap.size();
+        log.push_back({ms(t0 - start).count(), ms(t1 - t0).count(), ms(t0 - last_end).count(),
+                       participants, units});
+        last_end = t1;
+      }
+    } else if (err == ELMFB_OK) {
+      err = e_code;
+      msg = e_msg;
+    }
+    running = false;
     ++gen;
     cv.notify_all();
   }
@@ -218,17 +242,16 @@ void round_join(BatchRound* r, int q, const BatchInst& inst, const BatchShape& s
 int64_t round_step(BatchRound* r, int q, double* rec) {
   std::unique_lock<std::mutex> lk(r->m);
   if (r->err != ELMFB_OK) ELMFB_THROW(r->err, "multi-instance round: " + r->msg);
+  // the round this arrival takes part in: the next one to start (after the
+  // running one, if a round runs now)
+  const uint64_t target = r->gen + (r->running ? 2 : 1);
   ++r->arrived;
-  if (r->arrived == r->members) {
-    r->run_locked();
-  } else {
-    const uint64_t g0 = r->gen;
-    // every member either arrives or leaves, and the last of them runs the
-    // round; the bound only turns a host-side fault into an error
-    if (!r->cv.wait_for(lk, std::chrono::seconds(600), [&] { return r->gen != g0; })) {
-      --r->arrived;
-      ELMFB_THROW(ELMFB_ERR_TIMEOUT, "multi-instance round: the other members did not arrive");
-    }
+  if (!r->running && r->arrived == r->members) r->run_round(lk);
+  // every member either arrives or leaves, and the last of them runs the
+  // round; the bound only turns a host-side fault into an error
+  if (!r->cv.wait_for(lk, std::chrono::seconds(600), [&] { return r->gen >= target; })) {
+    if (r->gen + 1 == target && !r->running) --r->arrived;
+    ELMFB_THROW(ELMFB_ERR_TIMEOUT, "multi-instance round: the other members did not arrive");
   }
   if (r->err != ELMFB_OK) ELMFB_THROW(r->err, "multi-instance round: " + r->msg);
   std::copy(r->slot[q].rec, r->slot[q].rec + kRoundRecord, rec);
@@ -240,12 +263,12 @@ int64_t round_step(BatchRound* r, int q, double* rec) {
 int round_interval(const BatchRound* r) { return r->check_every; }
 
 void round_leave(BatchRound* r, int q) {
-  std::lock_guard<std::mutex> lk(r->m);
+  std::unique_lock<std::mutex> lk(r->m);
   if (!r->member[q]) return;
   r->member[q] = 0;
   --r->members;
   r->dirty = true;
-  if (r->members > 0 && r->arrived == r->members) r->run_locked();
+  if (!r->running && r->members > 0 && r->arrived == r->members) r->run_round(lk);
 }
 
 extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
