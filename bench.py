@@ -487,6 +487,18 @@ def run_batch(args):
     plain = E.default_solve_opts(max_iter=args.batch_iters, atol=0.0, btol=0.0, ntol=args.ntol,
                                  check_every=10, preconditioner=E.PREC_NONE)
     item_opts = [plain if WL.support_points_per_feature(P) < 4.0 else None for P in probs]
+    # autotuning, one worker (each shape class timed alone on the GPU): one
+    # instance per (K, log2 rows), the largest of its group; the timed batch
+    # looks the choices up
+    reps = {}
+    for P, o in zip(probs, item_opts):
+        if o is None:
+            key = (P.features, int(np.log2(P.n_rows)))
+            if key not in reps or P.n_rows > reps[key].n_rows:
+                reps[key] = P
+    tune = E.default_solve_opts(max_iter=10, atol=0.0, btol=0.0, shift=1e-6, check_every=10,
+                                autotune=1)
+    E.batch_solve(list(reps.values()), precision=E.FP32, n_workers=1, opts=tune)
     for _ in range(args.warmup):
         E.batch_solve(probs[:16], precision=E.FP32, n_workers=args.batch_workers, opts=opts,
                       item_opts=item_opts[:16])

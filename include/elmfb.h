@@ -271,7 +271,11 @@ typedef struct {
                           its shift is `shift` x tr / (its columns)          */
   int autotune;        /* LSQR: nonzero picks the fused pass's work-unit size by
                           timing (elmfb_tuning_table); the choice is kept per
-                          shape class for the life of the process           */
+                          shape class for the life of the process.  In
+                          elmfb_batch_solve with more than one worker it only
+                          uses classes tuned before (a timing beside other
+                          instances would measure them too): tune a batch's
+                          classes with one worker first                   */
   int graph;           /* LSQR: nonzero captures the kernels of one check
                           interval as a CUDA graph and replays it (one launch
                           per check_every iterations); needs a handle stream

@@ -325,8 +325,12 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
       elmfb_t h = nullptr;
       int rc = elmfb_create(&h, &it.cfg, st);
       if (rc != ELMFB_OK) std::snprintf(res.message, sizeof(res.message), "create failed");
-      // more worker threads than host cores: waits sleep instead of spinning
-      if (h) h->blocking_sync = true;
+      // more worker threads than host cores: waits sleep instead of spinning;
+      // with other instances on the GPU the autotuner cannot time in isolation
+      if (h) {
+        h->blocking_sync = true;
+        h->tune_lookup_only = w > 1;
+      }
       if (rc == ELMFB_OK) rc = elmfb_assemble(h, it.n_sets, it.sets);
       elmfb_solve_info info{};
       if (rc == ELMFB_OK) {

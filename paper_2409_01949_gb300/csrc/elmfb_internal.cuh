@@ -249,6 +249,7 @@ struct elmfb_ctx {
   // return at once); null outside a batched graph
   struct BatchRound* round = nullptr;   // the batch's coordinator (batch.cu), or null
   bool blocking_sync = false;   // waits sleep on an event (batch workers) instead of spinning
+  bool tune_lookup_only = false;   // autotune: use recorded choices only (concurrent batch)
   cudaEvent_t sync_ev = nullptr;
   int round_slot = -1;
   bool dual() const { return cfg.precision == ELMFB_FP32_DF32; }

@@ -2855,8 +2855,10 @@ namespace {
 // padded rows.  The first solve of a class with `autotune` times the fused
 // pass (mode 1, t = 0, CUDA events on the handle's stream, one warm-up and
 // three timed launches each) at the heuristic unit size and at half and twice
-// it, keeps the fastest for the class for the life of the process, and
-// records the candidates and their times (elmfb_tuning_table).
+// it (half and a quarter where twice would pass the 1024-row cap), keeps the
+// fastest for the class for the life of the process, and records the
+// candidates and their times (elmfb_tuning_table).  Handles of a batch of
+// several workers only look the choices up (tune_lookup_only).
 struct TuneKey {
   int prec, K, cover, rows_log2;
   bool operator<(const TuneKey& o) const {
@@ -2876,10 +2878,18 @@ int autotune_unit_rows(elmfb_ctx* h) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second.unit_rows;
   }
+  // beside other instances on the GPU a timing measures them too: keep the
+  // heuristic for classes not tuned before
+  if (h->tune_lookup_only) return 0;
   cudaStream_t st = h->stream;
+  // half the heuristic, the heuristic, twice it; at the cap a quarter instead of twice
   const int64_t t0 = fused_unit_target(h);
-  int cand[3] = {(int)std::max<int64_t>(8, (t0 / 2) & ~7), (int)t0,
-                 (int)std::min<int64_t>(kMaxUnitRows, t0 * 2)};
+  const int64_t t_hi = 2 * t0 <= kMaxUnitRows ? 2 * t0 : t0;
+  const int64_t t_lo = 2 * t0 <= kMaxUnitRows ? t0 / 2 : t0 / 4;
+  int cand[3] = {(int)std::max<int64_t>(8, t_lo & ~7), (int)std::max<int64_t>(8, (t0 / 2) & ~7),
+                 (int)t_hi};
+  if (2 * t0 <= kMaxUnitRows) cand[1] = (int)t0;
+  std::sort(cand, cand + 3);
   DevBuf zero, sc, gp;
   zero.alloc(std::max<int64_t>(h->NPhi, 1) * sizeof(double), st);
   sc.alloc(2 * kScal * sizeof(double), st);

@@ -175,6 +175,26 @@ def test_per_instance_options_equal_one_by_one():
         assert r.iterations == info.iterations
 
 
+def test_batch_autotunes_only_with_one_worker():
+    """Beside other instances on the GPU a timing measures them too, so a batch
+    of several workers only looks up recorded choices: a new shape class (K =
+    44) gets no entry from a 3-worker batch, and one entry from a 1-worker
+    batch of the same instances."""
+    probs = [WL.poisson2d(levels=(3,), features=44, n_side=40 + 2 * i, n_boundary_side=40,
+                          seed=i) for i in range(3)]
+    keys = lambda: {(e["features"], e["covering_panels"], e["rows_log2"])
+                    for e in E.tuning_table()}
+    before = keys()
+    opts = E.default_solve_opts(max_iter=20, atol=0.0, btol=0.0, shift=1e-6, check_every=10,
+                                autotune=1)
+    res, _, _ = E.batch_solve(probs, precision=E.FP32, n_workers=3, opts=opts)
+    assert all(r.status == E.OK for r in res)
+    assert {k for k in keys() - before if k[0] == 44} == set()
+    res, _, _ = E.batch_solve(probs, precision=E.FP32, n_workers=1, opts=opts)
+    assert all(r.status == E.OK for r in res)
+    assert len({k for k in keys() - before if k[0] == 44}) >= 1
+
+
 def test_autotuner_keeps_one_choice_per_shape_class():
     """`autotune` times the fused pass at three work-unit sizes on the first
     solve of a shape class and keeps the fastest: the table gains one entry

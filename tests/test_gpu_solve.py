@@ -156,6 +156,27 @@ def test_block_cholesky_drops_the_oracles_dependent_columns(prec):
     assert np.all(np.isfinite(a))
 
 
+@pytest.mark.parametrize("prec", [E.FP32, E.DF32])
+def test_device_stop_makes_iterations_independent_of_check_interval(prec):
+    """With the pair tail the stopping tests run on the device after every
+    iteration and the kernels of later iterations return at once: check
+    intervals of 1, 7 and 10 give the same iteration count and bitwise the
+    same coefficients (the count equals the first iteration whose test is met,
+    which check_every = 1 finds directly)."""
+    P = WL.poisson2d(levels=(1, 2, 4), features=32, n_side=50, n_boundary_side=50)
+    out = []
+    for ce in (1, 7, 10):
+        with E.Solver.from_problem(P, precision=prec) as s:
+            s.assemble_problem(P)
+            info = s.solve(max_iter=3000, atol=0.0, btol=0.0, ntol=1e-2, shift=1e-6,
+                           check_every=ce)
+            out.append((info.iterations, s.coeffs()))
+    print("iterations:", [o[0] for o in out])
+    assert out[0][0] == out[1][0] == out[2][0] < 3000
+    assert out[0][0] % 7 != 0 or out[0][0] % 10 != 0   # not both multiples of the intervals
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][1], out[2][1])
+
+
 _SOLVE_CASES = [
     ("poisson1d_J16_K64_N2000", WL.config_poisson1d),
     ("dho_L1-8_K24_N1000", lambda: WL.dho(levels=(1, 2, 4, 8), features=24, n_interior=1000)),
