@@ -41,6 +41,12 @@ SMALL = {
     "helmholtz_L_J1-8-16_K12_endpoint": (
         lambda: WL.helmholtz_lshape(levels=(1, 8, 16), features=12, n_grid=40, n_long=40,
                                     n_short=20, placement="endpoint"), [E.FP64, E.DF32]),
+    # the largest feature counts: K = 256 (the library's maximum), K = 160 (past
+    # the fused pass's 128, ragged against 32-lane slices)
+    "poisson1d_Kmax256": (lambda: WL.poisson1d(levels=(2, 4), features=256, n_interior=90),
+                          [E.FP64, E.FP32, E.DF32]),
+    "poisson2d_K160": (lambda: WL.poisson2d(levels=(2,), features=160, n_side=26,
+                                            n_boundary_side=9), [E.FP64, E.FP32]),
     # §4.3: the hard-constraint ansatz, no boundary rows
     "laplace_n4_J16_K16": (WL.laplace_multiscale, [E.FP64, E.FP32, E.DF32]),
     "laplace_n2_J1-4-8_K20_ansatz": (
