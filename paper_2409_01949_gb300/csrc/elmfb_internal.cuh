@@ -369,13 +369,13 @@ struct BatchInst {
 // What the members of one multi-instance launch must share.
 struct BatchShape {
   int K = 0, fpl = 0, rows = 0, S = 0, mmax = 0, pthreads = 0, chunk_threads = 0, low_kind = 0,
-      mode = 0;
+      mode = 0, tthreads = 0;
   size_t smem = 0, tsmem = 0;
   bool operator<(const BatchShape& o) const {
-    const int a[9] = {K, fpl, rows, S, mmax, pthreads, chunk_threads, low_kind, mode};
-    const int b[9] = {o.K, o.fpl, o.rows, o.S, o.mmax, o.pthreads, o.chunk_threads, o.low_kind,
-                      o.mode};
-    for (int i = 0; i < 9; ++i)
+    const int a[10] = {K, fpl, rows, S, mmax, pthreads, chunk_threads, low_kind, mode, tthreads};
+    const int b[10] = {o.K, o.fpl, o.rows, o.S, o.mmax, o.pthreads, o.chunk_threads, o.low_kind,
+                       o.mode, o.tthreads};
+    for (int i = 0; i < 10; ++i)
       if (a[i] != b[i]) return a[i] < b[i];
     if (smem != o.smem) return smem < o.smem;
     return tsmem < o.tsmem;

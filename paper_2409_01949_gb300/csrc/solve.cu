@@ -1811,19 +1811,23 @@ __global__ void __launch_bounds__(1024) k_precond_df(const float2* __restrict__ 
 // about 70 KB of shared memory, three blocks per SM, so that every panel of
 // the 2-D workloads (a few hundred) runs in one wave; at K = 64, 256 threads,
 // so that the thousands of small panels of the large 2-D workload run with
-// more blocks per SM rather than more idle threads per block.
+// more blocks per SM rather than more idle threads per block.  Without a
+// preconditioner (X = I, no triangle) the tail's products vanish and one
+// group of at least 128 threads does the rest, with no triangle in shared
+// memory, so that many blocks share an SM.
 constexpr int kTriThreads = 512;
-static int tri_threads(int K) {
+static int tri_threads(int K, bool ident = false) {
   const int Kp = (K + 31) & ~31;
+  if (ident) return std::max(128, Kp);
   return std::min(kTriThreads, std::max(128, 4 * Kp));
 }
 
-// Shared memory of those kernels: the triangle, a K-vector of pairs, G x K
-// group partials and the copy's mbarrier.
-static size_t tri_smem_bytes(int K) {
+// Shared memory of those kernels: the triangle (none for X = I), a K-vector of
+// pairs, G x K group partials and the copy's mbarrier.
+static size_t tri_smem_bytes(int K, bool ident = false) {
   const int Kp = (K + 31) & ~31;
-  const int G = tri_threads(K) / Kp;
-  return (size_t)(tri_pairs(K) + K + (int64_t)G * K) * sizeof(float2) + 16;
+  const int G = tri_threads(K, ident) / Kp;
+  return (size_t)((ident ? 0 : tri_pairs(K)) + K + (int64_t)G * K) * sizeof(float2) + 16;
 }
 
 // One bulk copy of panel s's triangle into shared memory (thread 0 issues it;
@@ -1967,10 +1971,10 @@ struct TriSmem {
   float2* vec;
   float2* part;
   uint64_t* bar;
-  __device__ TriSmem(unsigned char* raw, int K) {
+  __device__ TriSmem(unsigned char* raw, int K, bool ident = false) {
     const int G = blockDim.x / ((K + 31) & ~31);
     Xs = reinterpret_cast<float2*>(raw);
-    vec = Xs + tri_pairs(K);
+    vec = Xs + (ident ? 0 : tri_pairs(K));
     part = vec + K;
     bar = reinterpret_cast<uint64_t*>(part + (int64_t)G * K);
   }
@@ -2297,7 +2301,7 @@ __global__ void __launch_bounds__(kTriThreads, 3) k_lsqr_tail_tri(
   }
   if (scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   const bool ident = Xt == nullptr;   // no preconditioner: X = I
-  TriSmem sm(trsm, K);
+  TriSmem sm(trsm, K, ident);
   if (!ident) tri_fetch(sm.Xs, Xt, s, K, sm.bar);
   const int64_t o = (int64_t)s * K;
   if (!init) {
@@ -3067,7 +3071,8 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   // form); the fused path's partials are then pairs too
   const bool xpairs = !std::is_same<T, double>::value && fused && fp.pairs;
   const float2* Xt = xpairs && !identity ? h->d_R2.as<float2>() : nullptr;
-  const size_t tsmem = tri_smem_bytes(K);
+  const size_t tsmem = tri_smem_bytes(K, identity);
+  const int tthreads = tri_threads(K, identity);
   const double tri_bytes = identity ? 0.0 : 8.0 * h->n_sub * ((double)K * (K + 1) / 2);
   // k_precond also writes the fused pass's low-precision copy of t
   const int low_kind = !fused ? 0 : (std::is_same<T, df2>::value ? 2 : (fp.pairs ? 1 : 0));
@@ -3099,7 +3104,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
       panel_chunk_sums(h, fp, gpart, n_units, scal);
       prof_end(h, KID_PANEL_T);
       prof_begin(h, KID_UPDATE, csum_bytes + tri_bytes + 72.0 * N);
-      k_lsqr_tail_tri<<<h->n_sub, tri_threads(K), tsmem, st>>>(
+      k_lsqr_tail_tri<<<h->n_sub, tthreads, tsmem, st>>>(
           fp.csum.as<double>(), fp.pco.as<int>(), Xt, K, h->d_v.as<double>(),
           h->d_w.as<double>(), h->d_x_sol.as<double>(), scal, init, vpart,
           h->d_tmp.as<double>(), fp.tf.p, low_kind, dcount.as<unsigned int>(),
@@ -3239,6 +3244,7 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
     bsh.low_kind = low_kind;
     bsh.mode = fmode;
     bsh.tsmem = tsmem;
+    bsh.tthreads = tthreads;
     BatchInst bi{};
     bi.panels = reinterpret_cast<const float*>(P);
     bi.tlow = fp.tf.as<float>();
@@ -3839,7 +3845,7 @@ void launch_batch_iteration(const BatchShape& sh, const BatchInst* d_inst, const
                                                    nullptr, 0, nullptr, d_inst, d_cmap);
   // the tail (the last block of each instance runs its recurrence)
   ensure_dyn_smem((const void*)k_lsqr_tail_tri, sh.tsmem);
-  k_lsqr_tail_tri<<<n_t, tri_threads(sh.K), sh.tsmem, st>>>(
+  k_lsqr_tail_tri<<<n_t, sh.tthreads, sh.tsmem, st>>>(
       nullptr, nullptr, nullptr, sh.K, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
       nullptr, sh.low_kind, nullptr, nullptr, d_inst, d_tmap);
   check_launch("multi-instance LSQR iteration");
