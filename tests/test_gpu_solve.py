@@ -348,6 +348,34 @@ def test_eval_matches_oracle_u_hat():
     assert np.allclose(uh, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
 
 
+def test_full_size_large_2d_solution_evaluates_as_the_oracle_model():
+    """The large 2-D multilevel workload (4.2M rows, 349,504 columns: beyond
+    any oracle solve) solved as the bench does; the oracle evaluates the model
+    with the GPU's coefficients at 256 sampled test points, one by one, and
+    the GPU's u_hat agrees to FP64 rounding of the terms (the windows of a
+    level sum to 1 and |tanh| <= 1, so a point's terms add up in magnitude to
+    at most max_j ||a_j||_1).  The GPU's error norms against the closed form
+    equal the oracle's on the same u_hat."""
+    P = WL.config_poisson2d_large()
+    rng = np.random.default_rng(5)
+    X = P.test_points[rng.choice(P.test_points.shape[0], 256, replace=False)]
+    with E.Solver.from_problem(P, precision=E.FP32) as s:
+        s.assemble_problem(P)
+        info = s.solve(max_iter=5000, atol=0.0, btol=0.0, ntol=1e-4, shift=1e-6, check_every=10)
+        a = s.coeffs()
+        uh = s.eval(X)
+        u = P.exact(X)
+        norms = s.error_norms(uh, u)
+    ref = OE.u_hat(P, a, X)
+    scale = np.abs(a).reshape(-1, P.features).sum(axis=1).max()
+    diff = np.abs(uh - ref).max()
+    print(f"{info.iterations} its; sampled rel L2 {norms['rel_l2']:.3e}; |gpu - oracle| {diff:.3e}"
+          f" (term scale {scale:.3e})")
+    assert diff <= 1e-13 * scale + 1e-12 * np.abs(ref).max()
+    assert norms["rel_l2"] == pytest.approx(OE.rel_l2(uh, u), rel=1e-12)
+    assert norms["e_l1"] == pytest.approx(OE.e_l1(uh, u), rel=1e-12)
+
+
 def test_error_norms_match_oracle():
     rng = np.random.default_rng(2)
     u = rng.standard_normal(10007)
