@@ -250,7 +250,10 @@ typedef struct {
   double atol;         /* stop when ||M^T r|| <= atol ||M|| ||r|| (estimates) */
   double btol;         /* stop when ||r|| <= btol ||h||; 0 disables both tests */
   double shift;        /* Cholesky shift eps: G_jj + eps tr(G_jj)/K I          */
-  int check_every;     /* host checks convergence every this many iterations  */
+  int check_every;     /* host checks convergence every this many iterations;
+                          with FP32 and FP32-pair panels the stopping tests
+                          also run on the device after every iteration, so
+                          the iteration count does not depend on it       */
   int warm_start;      /* nonzero: start from the handle's current coefficients */
   int refine;          /* outer refinement steps (>= 1).  PCG: each recomputes
                           g = M^T (h - M a) from the panels and runs max_iter
@@ -280,7 +283,9 @@ typedef struct {
                           interval as a CUDA graph and replays it (one launch
                           per check_every iterations); needs a handle stream
                           other than the legacy default stream and profiling
-                          off, else the kernels are launched one by one     */
+                          off, else the kernels are launched one by one.
+                          Instances of elmfb_batch_solve that share launches
+                          (batch_shared) run in the batch's rounds instead  */
   int batch_shared;    /* elmfb_batch_solve, LSQR on FP32 panels with
                           block-Jacobi: nonzero (the default) runs the
                           instances' iterations in shared multi-instance
