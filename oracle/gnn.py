@@ -18,8 +18,11 @@ Weight vector layout (the C ABI's): W_in (H x K), b_in (H), then for l = 1..3
 W_self_l (H x H), W_nb_l (H x H), b_l (H), then W_out (K x H), b_out (K), all
 row-major.
 
-Pinned by central finite differences of the loss (tests/test_oracle_gnn.py);
-parity unpinned against the paper, which has no such network.
+Pinned in tests/test_oracle_gnn.py by a forward pass computed by hand on a
+3-node path with distinct inputs and integer weights (a swap of W_self and
+W_nb, a sum in place of the mean or a dropped ReLU each change it), by the
+zero-weight and equal-input special cases, and by central finite differences
+of the loss.  The paper defines no such network, so nothing it prints pins it.
 """
 from __future__ import annotations
 
