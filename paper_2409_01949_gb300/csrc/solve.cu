@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(544) k_gram_diag_partial(const T* __restrict__
                                                             const int* __restrict__ entry_cell,
                                                             const int* __restrict__ cover_off,
                                                             double* __restrict__ partial) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);   // [16][Kp]
   const int4 ch = chunks[blockIdx.x];     // (panel, first step, steps, -)
   const int Kp = (K + 3) & ~3;
@@ -935,7 +935,6 @@ __global__ void __launch_bounds__(128) k_entry_T(const T* __restrict__ panels,
   const int c = entry_cell[e];
   const int cnt = cell_count[c];
   const int64_t R0 = cell_pstart[c];
-  const int s = cover_sub[e];
   const T* base = panels + entry_base[e] * (int64_t)K;
   const int64_t rs = (int64_t)(cover_off[c + 1] - cover_off[c]) * K;   // row stride
   double* out = partial + (int64_t)e * K;
@@ -986,7 +985,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_fused(
     double* __restrict__ partial, double* __restrict__ norm_partial) {
   __shared__ double sd[32][kFusedRows];
   __shared__ double su[kFusedRows];
-  __shared__ double red[33];
   if (mode == 2 && scal[kStage + S_DONE] != 0.0) return;   // LSQR stopped on the device
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int4 un = units[blockIdx.x];   // (cell, first row, end row, first partial)
@@ -3049,12 +3047,8 @@ void lsqr(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) {
   const int tuned_rows = o->autotune && h->max_cover <= 32 && K <= 128
                              ? autotune_unit_rows<T>(h) : 0;
   const bool fused = build_fused_plan(h, fp, tuned_rows);
-  DevBuf& dunits = fp.units;
-  DevBuf& dfo = fp.fo;
-  DevBuf& dfe = fp.fe;
   DevBuf& dfpart = fp.part;
   const int n_units = fp.n_units;
-  const int fthreads = fp.threads;
   if (fused) {
     h->d_ptile.alloc((std::max(kGatherBlocks, n_units) + h->n_sub + 8) * sizeof(double), st);
     gpart = h->d_ptile.as<double>();
