@@ -394,8 +394,11 @@ int elmfb_gnn_train(elmfb_t h, int n_rhs, const double* rhs, int solve_iters, in
  * and launch shape over all of them, every check_every iterations a check of
  * each instance's own stopping tests.  Results are identical to solving the
  * instances one by one.  Returns the first non-OK instance status
- * (NOT_CONVERGED counts as OK), else ELMFB_OK.  Pointers may be host or
- * device memory, as elsewhere. */
+ * (NOT_CONVERGED counts as OK), else ELMFB_OK; ELMFB_ERR_CUDA without
+ * touching `results` if the batch's own stream, event or buffers cannot be
+ * made.  An instance that no worker took (none could create its stream)
+ * reports ELMFB_ERR_CUDA in its result.  Pointers may be host or device
+ * memory, as elsewhere. */
 typedef struct {
   elmfb_config cfg;
   int n_sets;

@@ -85,6 +85,25 @@ struct BatchRound {
   std::chrono::steady_clock::time_point start = std::chrono::steady_clock::now(),
                                         last_end = start;
 
+  // Device buffers are freed on the streams they were allocated on, before
+  // those streams go; every exit of the batch (errors included) passes here.
+  ~BatchRound() {
+    classes.clear();
+    all_inst.release();
+    d_rec.release();
+    if (gstream) {
+      cudaStreamSynchronize(gstream);
+      cudaStreamDestroy(gstream);
+    }
+    if (gdone) cudaEventDestroy(gdone);
+    if (h_rec) cudaFreeHost(h_rec);
+    for (cudaStream_t st : streams) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+  }
+
   void rebuild() {
     h_all.clear();
     all_slot.clear();
@@ -307,6 +326,14 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
   } catch (...) {
     return ELMFB_ERR_CUDA;
   }
+  // an item no worker takes (no worker could start) reports that
+  for (int i = 0; i < n; ++i) {
+    results[i] = elmfb_batch_result{};
+    results[i].status = ELMFB_ERR_CUDA;
+    results[i].rel_l2 = results[i].e_l1 = results[i].max_abs = NAN;
+    std::snprintf(results[i].message, sizeof(results[i].message),
+                  "not run: no batch worker could start");
+  }
   const char* trace_path = getenv("ELMFB_BATCH_TRACE");
   round.trace = trace_path && trace_path[0];
   auto worker = [&](int slot) {
@@ -382,18 +409,6 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
       std::fclose(f);
     }
   }
-  round.classes.clear();
-  round.all_inst.release();
-  round.d_rec.release();
-  cudaStreamSynchronize(round.gstream);
-  cudaStreamDestroy(round.gstream);
-  cudaEventDestroy(round.gdone);
-  cudaFreeHost(round.h_rec);
-  for (cudaStream_t st : round.streams) {
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
-  }
-  for (cudaEvent_t ev : round.events) cudaEventDestroy(ev);
   for (int i = 0; i < n; ++i)
     if (results[i].status != ELMFB_OK) return results[i].status;
   return ELMFB_OK;
