@@ -42,7 +42,7 @@ extern "C" {
 enum {
   ELMFB_OK = 0,
   ELMFB_ERR_INVALID_ARG = 1,  /* bad size, pointer, or option                   */
-  ELMFB_ERR_OOM = 2,          /* device allocation failed                        */
+  ELMFB_ERR_OOM = 2,          /* allocation failed (device, or the host handle)  */
   ELMFB_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has details) */
   ELMFB_ERR_STATE = 4,        /* call out of order (e.g. solve before assemble)   */
   ELMFB_ERR_NOT_CONVERGED = 5,/* iteration cap reached; coefficients still valid  */

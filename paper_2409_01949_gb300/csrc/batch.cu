@@ -29,6 +29,8 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <system_error>
 #include <thread>
 
 #include "elmfb_internal.cuh"
@@ -290,9 +292,8 @@ void round_leave(BatchRound* r, int q) {
   if (!r->running && r->members > 0 && r->arrived == r->members) r->run_round(lk);
 }
 
-extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
-                                 const elmfb_solve_opts* opts, int n_workers,
-                                 elmfb_batch_result* results) {
+static int batch_solve(int n, const elmfb_batch_item* items, const elmfb_solve_opts* opts,
+                       int n_workers, elmfb_batch_result* results) {
   if (n < 0 || (n > 0 && (!items || !results)) || n_workers < 1 || n_workers > 256)
     return ELMFB_ERR_INVALID_ARG;
   if (n == 0) return ELMFB_OK;
@@ -398,8 +399,18 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   };
+  // a thread that cannot be started leaves its share to the others; with none
+  // started, this thread does the work
   std::vector<std::thread> pool;
-  for (int t = 0; t < w; ++t) pool.emplace_back(worker, t);
+  pool.reserve(w);
+  for (int t = 0; t < w; ++t) {
+    try {
+      pool.emplace_back(worker, t);
+    } catch (const std::system_error&) {
+      break;
+    }
+  }
+  if (pool.empty()) worker(0);
   for (auto& t : pool) t.join();
   if (round.trace) {
     if (FILE* f = std::fopen(trace_path, "w")) {
@@ -412,4 +423,17 @@ extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
   for (int i = 0; i < n; ++i)
     if (results[i].status != ELMFB_OK) return results[i].status;
   return ELMFB_OK;
+}
+
+// no exception crosses the C ABI
+extern "C" int elmfb_batch_solve(int n, const elmfb_batch_item* items,
+                                 const elmfb_solve_opts* opts, int n_workers,
+                                 elmfb_batch_result* results) {
+  try {
+    return batch_solve(n, items, opts, n_workers, results);
+  } catch (const std::bad_alloc&) {
+    return ELMFB_ERR_OOM;
+  } catch (...) {
+    return ELMFB_ERR_CUDA;
+  }
 }

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <utility>
 
 #include "elmfb_internal.cuh"
@@ -68,6 +69,9 @@ int guarded(elmfb_ctx* h, F&& f) {
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
   } catch (const std::exception& e) {
     h->err = e.what();
     return ELMFB_ERR_CUDA;
@@ -517,7 +521,8 @@ int elmfb_create(elmfb_t* out, const elmfb_config* cfg, void* cuda_stream) {
     nsub += c.dim == 2 ? (int64_t)c.levels[l] * c.levels[l] : c.levels[l];
   }
   if (nsub * c.features > (int64_t)1 << 30) return ELMFB_ERR_UNSUPPORTED;
-  elmfb_ctx* h = new elmfb_ctx();
+  elmfb_ctx* h = new (std::nothrow) elmfb_ctx();   // no exception crosses the C ABI
+  if (!h) return ELMFB_ERR_OOM;
   h->cfg = c;
   h->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&h->device);

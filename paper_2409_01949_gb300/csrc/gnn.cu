@@ -21,6 +21,9 @@
 #include <algorithm>
 #include <cmath>
 
+#include <new>
+#include <stdexcept>
+
 #include "elmfb_internal.cuh"
 
 namespace {
@@ -551,6 +554,12 @@ int elmfb_gnn_graph(elmfb_t h, int* off, int* nb, int64_t* n_edges) {
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 
@@ -567,6 +576,12 @@ int elmfb_gnn_set_weights(elmfb_t h, const float* w) {
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 
@@ -581,6 +596,12 @@ int elmfb_gnn_get_weights(elmfb_t h, float* w) {
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 
@@ -616,6 +637,12 @@ int elmfb_gnn_eval(elmfb_t h, int batch, const float* x, const float* t, const f
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 
@@ -765,6 +792,12 @@ int elmfb_gnn_train(elmfb_t h, int n_rhs, const double* rhs, int solve_iters, in
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 

@@ -25,6 +25,9 @@
 
 #include <cudaTypedefs.h>
 
+#include <new>
+#include <stdexcept>
+
 #include "elmfb_internal.cuh"
 #include "sm100_ptx.cuh"
 
@@ -258,6 +261,12 @@ int elmfb_compute_gram(elmfb_t h) {
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 
@@ -291,6 +300,12 @@ int elmfb_get_gram(elmfb_t h, int64_t n, const int* ij, double* out) {
   } catch (const elmfb_error& e) {
     h->err = e.msg;
     return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
   }
 }
 
