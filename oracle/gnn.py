@@ -18,6 +18,13 @@ Weight vector layout (the C ABI's): W_in (H x K), b_in (H), then for l = 1..3
 W_self_l (H x H), W_nb_l (H x H), b_l (H), then W_out (K x H), b_out (K), all
 row-major.
 
+forward_bf16 is the same network with every layer's operands rounded to
+bfloat16 where the GPU's tensor-core inference rounds them (the neighbour
+mean formed in FP32 first); bf16_round is pinned by round-half-even cases
+worked out by hand, forward_bf16 by the hand-computed case below (every
+value there is exact in bfloat16) and by inputs, weights and activations
+whose rounding that case exposes.
+
 Pinned in tests/test_oracle_gnn.py by a forward pass computed by hand on a
 3-node path with distinct inputs and integer weights (a swap of W_self and
 W_nb, a sum in place of the mean or a dropped ReLU each change it), by the
@@ -64,6 +71,45 @@ def forward(w, X, nbrs, K: int, H: int = 64):
                         for nb in nbrs], axis=1)
         A = np.maximum(A @ P[f"W_self{l}"].T + agg @ P[f"W_nb{l}"].T + P[f"b{l}"], 0.0)
     return A @ P["W_out"].T + P["b_out"]
+
+
+def bf16_round(x) -> np.ndarray:
+    """FP32 values rounded to bfloat16 (8 significant bits: the upper 16 bits
+    of the FP32 pattern), to nearest with ties to even, returned as FP32.
+    Written from the definition of round-half-even on the bit pattern: add
+    half a unit of the last kept bit, less one unless that bit is odd, then
+    clear the 16 dropped bits."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def _mean_f32(A32, nb):
+    """Neighbour mean as the network's inference kernel forms it: FP32 sums in
+    the neighbour list's order, then one FP32 division by the degree."""
+    acc = np.zeros((A32.shape[0], A32.shape[2]), dtype=np.float32)
+    for t in nb:
+        acc = acc + A32[:, t, :]
+    return acc / np.float32(len(nb)) if len(nb) else acc
+
+
+def forward_bf16(w, X, nbrs, K: int, H: int = 64):
+    """forward() with the operands of every layer rounded to bfloat16, as the
+    learned preconditioner applies the network on the tensor cores: the
+    weights (given as FP32), the FP32 input, each layer's FP32 activations
+    (the FP64 result of the layer stored as FP32, then rounded) and the FP32
+    neighbour means.  Products and sums are then exact or FP64."""
+    P = unpack(np.asarray(w, dtype=np.float32), K, H)
+    q = lambda M: bf16_round(np.asarray(M, dtype=np.float32)).astype(np.float64)
+    A32 = np.asarray(X, dtype=np.float32)
+    A = np.maximum(q(A32) @ q(P["W_in"]).T + P["b_in"], 0.0)
+    for l in range(N_LAYERS):
+        A32 = A.astype(np.float32)
+        agg = np.stack([_mean_f32(A32, nb) for nb in nbrs], axis=1)
+        A = np.maximum(q(A32) @ q(P[f"W_self{l}"]).T + q(agg) @ q(P[f"W_nb{l}"]).T + P[f"b{l}"],
+                       0.0)
+    A32 = A.astype(np.float32)
+    return q(A32) @ q(P["W_out"]).T + P["b_out"]
 
 
 def loss(w, X, T, wb, nbrs, K: int, H: int = 64) -> float:

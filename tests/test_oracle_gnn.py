@@ -82,3 +82,65 @@ def test_hand_computed_forward_on_three_node_path():
     nbrs = [np.array([1]), np.array([0, 2]), np.array([1])]
     Y = G.forward(w, X, nbrs, K, H)
     assert np.array_equal(Y[0, :, 0], [29.5, -46.5, 31.5])
+
+
+def test_bf16_round_half_even_by_hand():
+    """bfloat16 keeps 8 significant bits.  Worked by hand: 255 (8 bits) and
+    powers of two are kept; 1 + 2^-9 is below half a unit (2^-8) and goes to
+    1; 1 + 2^-8 and 257 are ties that go to the even neighbour (1, 256);
+    1 + 3 2^-8 and 259 are ties whose lower neighbour is odd (1.015625, 260)."""
+    x = np.array([255.0, 0.5, -3.0, 1 + 2**-9, 1 + 2**-8, 257.0, 1 + 3 * 2**-8, 259.0, -259.0],
+                 dtype=np.float32)
+    want = [255.0, 0.5, -3.0, 1.0, 1.0, 256.0, 1.015625, 260.0, -260.0]
+    assert np.array_equal(G.bf16_round(x), np.array(want, dtype=np.float32))
+
+
+def _hand_case():
+    K, H = 1, 2
+    w = np.zeros(G.n_weights(K, H))
+    P = G.unpack(w, K, H)
+    P["W_in"][:] = [[1.0], [-1.0]]
+    P["b_in"][:] = [0.0, 1.0]
+    for l in range(3):
+        P[f"W_self{l}"][:] = [[1.0, 0.0], [0.0, 2.0]]
+        P[f"W_nb{l}"][:] = [[0.0, 1.0], [1.0, 0.0]]
+        P[f"b{l}"][:] = [0.0, -1.0]
+    P["W_out"][:] = [[1.0, -1.0]]
+    P["b_out"][:] = [0.5]
+    X = np.array([[[1.0], [-2.0], [3.0]]])
+    nbrs = [np.array([1]), np.array([0, 2]), np.array([1])]
+    return w, P, X, nbrs, K, H
+
+
+def test_bf16_forward_on_the_hand_case():
+    """Every value of the hand-computed case is exact in bfloat16, so the
+    rounded network gives the same Y = (29.5, -46.5, 31.5)."""
+    w, P, X, nbrs, K, H = _hand_case()
+    Y = G.forward_bf16(w, X, nbrs, K, H)
+    assert np.array_equal(Y[0, :, 0], [29.5, -46.5, 31.5])
+
+
+def test_bf16_forward_rounds_input_weights_and_activations():
+    """Perturbations below half a bfloat16 unit vanish where the kernel
+    rounds: in the input (x_0 = 1 + 2^-9), in a weight (W_in[0] = 1 + 2^-9)
+    and in an activation (b_in[0] = 2^-9 makes A0 of node 0 equal 1 + 2^-9,
+    which the first message-passing layer reads rounded to 1).  The rounded
+    network still gives the hand-computed Y; the unrounded one does not."""
+    w, P, X, nbrs, K, H = _hand_case()
+    X = X.copy()
+    X[0, 0, 0] = 1 + 2**-9
+    P["W_in"][0, 0] = 1 + 2**-9
+    P["b_in"][0] = 2**-9
+    Y = G.forward_bf16(w, X, nbrs, K, H)
+    assert np.array_equal(Y[0, :, 0], [29.5, -46.5, 31.5])
+    assert not np.array_equal(G.forward(w, X, nbrs, K, H)[0, :, 0], [29.5, -46.5, 31.5])
+
+
+def test_bf16_forward_close_to_forward():
+    """On a random network the rounded forward stays within the error that
+    bfloat16 operands allow (relative unit 2^-8 per operand) of the exact one."""
+    w, X, T, wb, nbrs, K, H = _setup(4)
+    Y = G.forward(w, X, nbrs, K, H)
+    Yb = G.forward_bf16(w, X, nbrs, K, H)
+    assert not np.array_equal(Y, Yb)
+    assert np.abs(Yb - Y).max() <= 0.05 * np.abs(Y).max()
