@@ -372,6 +372,14 @@ int elmfb_gnn_get_weights(elmfb_t h, float* w);
  * and, if grad != NULL, its gradient w.r.t. the weights (for checking). */
 int elmfb_gnn_eval(elmfb_t h, int batch, const float* x, const float* t, const float* wb,
                    float* y, float* grad, double* loss);
+/* The forward pass as FCG's learned preconditioner applies it: every layer's
+ * operands (weights, input, activations, neighbour means formed in FP32) are
+ * rounded to bfloat16 (to nearest, ties to even) and multiplied on the tensor
+ * cores with FP32 accumulation; bias and ReLU in FP32.  x, y [batch][n_subdomains][K]
+ * (host or device).  Needs K a multiple of 16 up to 128 (else
+ * ELMFB_ERR_UNSUPPORTED; FCG then applies elmfb_gnn_eval's FP32 forward), and
+ * weights (ELMFB_ERR_STATE before elmfb_gnn_set_weights / elmfb_gnn_train). */
+int elmfb_gnn_infer(elmfb_t h, int batch, const float* x, float* y);
 /* Train on pairs from block-Jacobi FCG solves of this system with n_rhs other
  * right-hand sides rhs [n_rhs][n_rows] (unscaled, row order of assemble):
  * solve_iters recorded iterations per solve (errors against the iterate

@@ -134,6 +134,7 @@ _SIGNATURES = {
     "elmfb_gnn_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "elmfb_gnn_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p]),
+    "elmfb_gnn_infer": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "elmfb_gnn_train": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                   C.c_uint64, C.c_void_p]),
     "elmfb_get_gram": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -494,6 +495,14 @@ class Solver:
                                             y.ctypes.data, g.ctypes.data if g is not None else None,
                                             C.byref(loss)))
         return y, g, loss.value
+
+    def gnn_infer(self, x):
+        """The network's forward pass as FCG applies it (bfloat16 operands on
+        the tensor cores, FP32 accumulation); x [batch][n_subdomains][K]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros_like(x)
+        _check(self.h, lib().elmfb_gnn_infer(self.h, x.shape[0], x.ctypes.data, y.ctypes.data))
+        return y
 
     def gnn_train(self, rhs_list, solve_iters=30, epochs=20, lr=1e-3, seed=0):
         R = np.ascontiguousarray(np.asarray(rhs_list, dtype=np.float64))

@@ -24,7 +24,10 @@
 #include <new>
 #include <stdexcept>
 
+#include <cuda_bf16.h>
+
 #include "elmfb_internal.cuh"
+#include "sm100_ptx.cuh"
 
 namespace {
 
@@ -219,6 +222,145 @@ __global__ void k_permute_rhs(const int* __restrict__ sorted, const int* __restr
   out[R] = r < 0 ? 0.0 : rhs[r] * hscale[rcls[R]];
 }
 
+// ---- the network on the tensor cores (inference in FCG's preconditioner) ---
+//
+// One dense layer, 128 rows r = (sample b, node s) per CTA:
+//   out[r][o] = act(sum_c in[r][c] W[o][c] + bias[o])
+// with the contraction c over the D1 channels of in1 (weights W1 [Dout][D1])
+// and, for the message-passing layers, the H channels of the neighbour mean of
+// in2 (weights W2 [Dout][H]): mean over t in N(s) of row (b, t), FP32 sums in
+// the neighbour list's order, then one FP32 division by the degree.  Every
+// operand is rounded to bfloat16 (to nearest, ties to even) as the threads
+// write it into shared memory, in the K-major layout with 128-byte swizzle
+// that a TMA SWIZZLE_128B load produces: 64 channels (128 B) per row and
+// block, element c of row m at block c / 64, byte
+//   m * 128 + ((((c % 64) / 8) ^ (m % 8)) * 16) + (c % 8) * 2.
+// One thread issues (D1 + D2) / 16 tcgen05.mma (kind::f16, BF16 x BF16, FP32
+// accumulation, M = 128, N = Dout) into TMEM; the four warps read the
+// accumulator back (warp w: TMEM lanes = rows 32w .. 32w + 31), add the bias,
+// apply the ReLU and store FP32.  Limits: D1 + D2 <= 128 and Dout <= 128, all
+// multiples of 16.  The completion wait is bounded: on a timeout flags[6] is
+// raised and the block waits once more (bounded) before freeing TMEM.
+constexpr int kTcRows = 128;
+constexpr int kTcBlock = 128 * 128;                    // bytes: 128 rows x 64 BF16
+constexpr size_t kTcSmem = 4 * (size_t)kTcBlock + 1024;   // A and B, 2 blocks each; alignment
+
+// 8 consecutive channels c .. c + 7 (c % 8 == 0) of row m, rounded to bfloat16
+__device__ __forceinline__ void tc_store8(uint8_t* tile, int m, int c, const float (&v)[8]) {
+  uint32_t p[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    p[j] = *reinterpret_cast<const uint32_t*>(&b2);
+  }
+  const int chunk = ((c & 63) >> 3) ^ (m & 7);
+  *reinterpret_cast<uint4*>(tile + (size_t)(c >> 6) * kTcBlock + (size_t)m * 128 + chunk * 16) =
+      make_uint4(p[0], p[1], p[2], p[3]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_gnn_layer_tc(const float* __restrict__ in1, int D1, const float* __restrict__ W1,
+                   const float* __restrict__ in2, const float* __restrict__ W2,
+                   const int* __restrict__ off, const int* __restrict__ nb, int n_nodes,
+                   const float* __restrict__ bias, int Dout, int64_t R, int act,
+                   float* __restrict__ out, int* __restrict__ flags) {
+  extern __shared__ uint8_t smraw[];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_slot;
+  uint8_t* At = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* Bt = At + 2 * kTcBlock;
+  const int D2 = W2 ? kH : 0;
+  const int Dk = D1 + D2;
+  const int warp = threadIdx.x >> 5;
+  const int m = threadIdx.x;   // this thread's row of A and of B
+  const int64_t r = (int64_t)blockIdx.x * kTcRows + m;
+  if (threadIdx.x == 0) {
+    sm100::mbar_init(&done, 1);
+    sm100::fence_mbar_init();
+  }
+  if (warp == 0) sm100::tmem_alloc(&tmem_slot, 128);
+  // A: row r of in1, then the neighbour mean of in2 (zeros past R)
+  for (int c = 0; c < Dk; c += 8) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = 0.f;
+    if (r < R) {
+      if (c < D1) {
+        const float4* p = reinterpret_cast<const float4*>(in1 + r * D1 + c);
+        const float4 a = p[0], b = p[1];
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+        v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+      } else {
+        const int s = (int)(r % n_nodes);
+        const int64_t row0 = r - s;   // node 0 of this sample
+        const int e0 = off[s], e1 = off[s + 1];
+        for (int e = e0; e < e1; ++e) {
+          const float4* p = reinterpret_cast<const float4*>(in2 + (row0 + nb[e]) * kH + (c - D1));
+          const float4 a = p[0], b = p[1];
+          v[0] += a.x, v[1] += a.y, v[2] += a.z, v[3] += a.w;
+          v[4] += b.x, v[5] += b.y, v[6] += b.z, v[7] += b.w;
+        }
+        if (e1 > e0) {
+          const float deg = (float)(e1 - e0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = v[j] / deg;
+        }
+      }
+    }
+    tc_store8(At, m, c, v);
+  }
+  // B: row m of [W1 | W2]
+  if (m < Dout) {
+    for (int c = 0; c < Dk; c += 8) {
+      const float* w = c < D1 ? W1 + (int64_t)m * D1 + c : W2 + (int64_t)m * kH + (c - D1);
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = w[j];
+      tc_store8(Bt, m, c, v);
+    }
+  }
+  sm100::fence_proxy_async_smem();   // generic-proxy writes -> the tensor core's reads
+  sm100::tc_fence_before();
+  __syncthreads();
+  sm100::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = sm100::idesc_bf16_f32(128, (uint32_t)Dout);
+    for (int k = 0; k < Dk / 16; ++k) {
+      // 16 channels (32 B) per instruction, inside block k / 4
+      const uint32_t blk = (uint32_t)(k >> 2) * kTcBlock;
+      const uint64_t ad = sm100::sdesc_k_sw128(sm100::smem_u32(At + blk)) + 2 * (k & 3);
+      const uint64_t bd = sm100::sdesc_k_sw128(sm100::smem_u32(Bt + blk)) + 2 * (k & 3);
+      sm100::mma_bf16(tmem, ad, bd, idesc, k > 0 ? 1u : 0u);
+    }
+    sm100::mma_commit(&done);
+  }
+  __syncwarp();
+  const bool got = sm100::mbar_wait(&done, 0);
+  if (!got) {
+    if (threadIdx.x == 0) atomicOr(&flags[6], 1);
+    sm100::mbar_wait(&done, 0);   // let the MMAs finish before TMEM is read or freed
+  }
+  sm100::tc_fence_after();
+  for (int c0 = 0; c0 < Dout; c0 += 16) {
+    uint32_t v[16];
+    sm100::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+    sm100::tmem_ld_wait();
+    if (r < R && got) {
+      float* o = out + r * Dout + c0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float x = __uint_as_float(v[j]) + bias[c0 + j];
+        o[j] = act ? relu(x) : x;
+      }
+    }
+  }
+  sm100::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) sm100::tmem_dealloc(tmem, 128);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host ----
@@ -371,6 +513,44 @@ double gnn_pass(elmfb_ctx* h, int B, const float* X, const float* T, const float
   return loss;
 }
 
+// The forward pass as FCG applies it: bfloat16 operands on the tensor cores,
+// one k_gnn_layer_tc launch per layer (the neighbour means formed inside the
+// message-passing layers).  X, Y: [B][n][K] float on the device.  K must be a
+// multiple of 16 up to 128; other K take gnn_pass's FP32 forward.  A timed-out
+// completion wait raises flags[6] (cleared by the caller).
+bool gnn_tc_supported(int K) { return K >= 16 && K <= 128 && K % 16 == 0; }
+
+void gnn_infer(elmfb_ctx* h, int B, const float* X, float* Y) {
+  const int K = h->K, n = h->n_sub;
+  if (!gnn_tc_supported(K)) {
+    gnn_pass(h, B, X, nullptr, nullptr, Y, nullptr);
+    return;
+  }
+  cudaStream_t st = h->stream;
+  const int64_t R = (int64_t)B * n;
+  Gnn g{h, K, n, gnn_weight_count(K)};
+  g.bind(h->d_gnn_w.as<float>());
+  h->d_gnn_act.alloc((size_t)R * kH * 2 * sizeof(float), st);
+  float* cur = h->d_gnn_act.as<float>();
+  float* nxt = cur + R * kH;
+  ensure_dyn_smem((const void*)k_gnn_layer_tc, kTcSmem);
+  const unsigned grid = (unsigned)ceil_div(R, kTcRows);
+  const int* off = h->d_gnn_off.as<int>();
+  const int* nb = h->d_gnn_nb.as<int>();
+  int* flags = h->d_flags.as<int>();
+  k_gnn_layer_tc<<<grid, 128, kTcSmem, st>>>(X, K, g.W_in, nullptr, nullptr, off, nb, n, g.b_in,
+                                              kH, R, 1, cur, flags);
+  for (int l = 0; l < kLayers; ++l) {
+    k_gnn_layer_tc<<<grid, 128, kTcSmem, st>>>(cur, kH, g.W_self[l], cur, g.W_nb[l], off, nb, n,
+                                                g.b_l[l], kH, R, 1, nxt, flags);
+    std::swap(cur, nxt);
+  }
+  k_gnn_layer_tc<<<grid, 128, kTcSmem, st>>>(cur, kH, g.W_out, nullptr, nullptr, off, nb, n,
+                                              g.b_out, K, R, 0, Y, flags);
+  count_launch(h, kLayers + 2);
+  check_launch("gnn inference");
+}
+
 double dot(elmfb_ctx* h, const double* a, const double* b, int64_t n, DevBuf& part) {
   part.alloc(kDotBlocks * sizeof(double), h->stream);
   k_dot_part<<<kDotBlocks, 256, 0, h->stream>>>(a, b, n, part.as<double>());
@@ -437,7 +617,7 @@ struct Fcg {
     yout.alloc(N * sizeof(float), h->stream);
     const unsigned nb = (unsigned)ceil_div(N, 256);
     k_scale_to_float<<<nb, 256, 0, h->stream>>>(z, 1.0 / sigma, xin.as<float>(), N);
-    gnn_pass(h, 1, xin.as<float>(), nullptr, nullptr, yout.as<float>(), nullptr);
+    gnn_infer(h, 1, xin.as<float>(), yout.as<float>());
     k_add_scaled_float<<<nb, 256, 0, h->stream>>>(z, yout.as<float>(), sigma, N);
     count_launch(h, 2);
   }
@@ -530,6 +710,14 @@ void fcg_solve(elmfb_ctx* h, const elmfb_solve_opts* o, elmfb_solve_info* info) 
   CUDA_CHECK(cudaMemcpyAsync(h->d_a.p, f.x, f.N * sizeof(double), cudaMemcpyDeviceToDevice,
                              h->stream));
   stage_end(h, 5);
+  if (use_gnn && gnn_tc_supported(h->K)) {
+    int timed_out = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&timed_out, h->d_flags.as<int>() + 6, sizeof(int),
+                               cudaMemcpyDeviceToHost, h->stream));
+    stream_sync(h);
+    if (timed_out)
+      ELMFB_THROW(ELMFB_ERR_TIMEOUT, "learned preconditioner: a tensor-core wait timed out");
+  }
   info->status = rel <= o->btol ? ELMFB_OK : ELMFB_ERR_NOT_CONVERGED;
   info->iterations = its;
   info->residual_norm = NAN;
@@ -592,6 +780,41 @@ int elmfb_gnn_get_weights(elmfb_t h, float* w) {
     if (!h->d_gnn_w.p) ELMFB_THROW(ELMFB_ERR_STATE, "no network weights yet");
     CUDA_CHECK(cudaMemcpy(w, h->d_gnn_w.p, gnn_weight_count(h->K) * sizeof(float),
                           cudaMemcpyDefault));
+    return ELMFB_OK;
+  } catch (const elmfb_error& e) {
+    h->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    h->err = "host allocation failed";
+    return ELMFB_ERR_OOM;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return ELMFB_ERR_CUDA;
+  }
+}
+
+int elmfb_gnn_infer(elmfb_t h, int batch, const float* x, float* y) {
+  if (!h || batch < 1 || !x || !y) return ELMFB_ERR_INVALID_ARG;
+  try {
+    CUDA_CHECK(cudaSetDevice(h->device));
+    if (!h->d_gnn_w.p) ELMFB_THROW(ELMFB_ERR_STATE, "no network weights yet");
+    if (!gnn_tc_supported(h->K))
+      ELMFB_THROW(ELMFB_ERR_UNSUPPORTED,
+                  "tensor-core inference needs K a multiple of 16, at most 128");
+    cudaStream_t st = h->stream;
+    const int64_t n = (int64_t)batch * h->n_sub * h->K;
+    DevBuf dx, dy;
+    dx.alloc(n * sizeof(float), st);
+    dy.alloc(n * sizeof(float), st);
+    CUDA_CHECK(cudaMemcpyAsync(dx.p, x, n * sizeof(float), cudaMemcpyDefault, st));
+    CUDA_CHECK(cudaMemsetAsync(h->d_flags.as<int>() + 6, 0, sizeof(int), st));
+    gnn_infer(h, batch, dx.as<float>(), dy.as<float>());
+    int timed_out = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&timed_out, h->d_flags.as<int>() + 6, sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(y, dy.p, n * sizeof(float), cudaMemcpyDefault, st));
+    stream_sync(h);
+    if (timed_out) ELMFB_THROW(ELMFB_ERR_TIMEOUT, "network inference: a tensor-core wait timed out");
     return ELMFB_OK;
   } catch (const elmfb_error& e) {
     h->err = e.msg;

@@ -3,6 +3,8 @@
 * the GPU network's forward pass and hand-written gradients against the
   oracle's FP64 definition (oracle/gnn.py) with central finite differences,
   on the subdomain graph derived by the oracle from its own M;
+* the tensor-core forward that FCG applies (bfloat16 operands, FP32
+  accumulation) against the oracle's forward with the same rounding points;
 * a network whose output layer is zero leaves FCG identical to block-Jacobi
   FCG (the correction is exactly zero);
 * training on pairs from the method's own solves lowers the loss, and the
@@ -63,6 +65,46 @@ def test_gnn_forward_and_gradient_match_oracle():
                          nbrs, K, idx, H)
     scale = max(np.abs(gfd).max(), 1e-12)
     assert np.allclose(grad[idx], gfd, rtol=2e-3, atol=2e-3 * scale)
+
+
+def test_tensor_core_inference_matches_bf16_oracle():
+    """FCG applies the network with bfloat16 operands on the tensor cores
+    (elmfb_gnn_infer).  Against the oracle's forward with the same rounding
+    points (forward_bf16), on 3 samples of an 85-node graph (255 rows: two
+    128-row tiles, the second ragged), K = 32: almost every output agrees to
+    FP32 accumulation order; an activation whose FP32 value sits at a
+    bfloat16 rounding boundary may round the other way, which moves the
+    outputs by about one bfloat16 unit of one operand, so the bar on the
+    largest difference is 4e-3 of the output scale.  The unrounded network is
+    further away (the bfloat16 error itself); K = 8 is not a multiple of 16
+    and is refused."""
+    P = WL.poisson2d(levels=(1, 2, 4, 8), features=32, n_side=40, n_boundary_side=40)
+    K, H = P.features, 64
+    nbrs = _oracle_graph(P)
+    rng = np.random.default_rng(5)
+    w = (0.2 * rng.standard_normal(OG.n_weights(K, H))).astype(np.float32)
+    X = rng.standard_normal((3, P.n_subdomains, K)).astype(np.float32)
+    with E.Solver.from_problem(P, precision=E.FP32) as s:
+        s.assemble_problem(P)
+        assert all(np.array_equal(a, b) for a, b in zip(s.gnn_graph(), nbrs))
+        s.gnn_set_weights(w)
+        Y = s.gnn_infer(X)
+    Yb = OG.forward_bf16(w, X, nbrs, K, H)
+    Yo = OG.forward(w.astype(np.float64), X.astype(np.float64), nbrs, K, H)
+    scale = np.abs(Yb).max()
+    d_b, d_o = np.abs(Y - Yb), np.abs(Y - Yo)
+    print(f"tensor-core inference: max |Y - Y_bf16| {d_b.max() / scale:.2e}, median "
+          f"{np.median(d_b) / scale:.2e}; max |Y - Y_fp64| {d_o.max() / scale:.2e} (of scale)")
+    assert d_b.max() <= 4e-3 * scale
+    assert np.median(d_b) <= 1e-5 * scale
+    assert d_b.max() < 0.5 * d_o.max()
+    Q = _small()
+    with E.Solver.from_problem(Q, precision=E.FP32) as s:
+        s.assemble_problem(Q)
+        s.gnn_set_weights(np.zeros(s.gnn_num_weights(), dtype=np.float32))
+        with pytest.raises(E.ElmfbError) as ei:
+            s.gnn_infer(np.zeros((1, Q.n_subdomains, Q.features), dtype=np.float32))
+        assert ei.value.code == E.ERR_UNSUPPORTED
 
 
 def _fcg(P, prec, precond, iters, tol=0.0, weights=None, train=None):
