@@ -273,30 +273,46 @@ __global__ void __launch_bounds__(128, 1)
   const int D2 = W2 ? kH : 0;
   const int Dk = D1 + D2;
   const int warp = threadIdx.x >> 5;
-  const int m = threadIdx.x;   // this thread's row of A and of B
+  const int m = threadIdx.x;   // this thread's row of B and of the output
   const int64_t r = (int64_t)blockIdx.x * kTcRows + m;
   if (threadIdx.x == 0) {
     sm100::mbar_init(&done, 1);
     sm100::fence_mbar_init();
   }
   if (warp == 0) sm100::tmem_alloc(&tmem_slot, 128);
-  // A: row r of in1, then the neighbour mean of in2 (zeros past R)
-  for (int c = 0; c < Dk; c += 8) {
+  // A: the tile's rows of in1, then the neighbour means of in2 (zeros past R),
+  // as tasks (row, 8-channel chunk) spread over all threads.  A coarse node's
+  // long neighbour list is shared by the 8 threads of its chunks; each chunk
+  // sums its neighbours in list order.
+  const int64_t tile0 = (int64_t)blockIdx.x * kTcRows;
+  const int n1 = D1 / 8;
+  for (int task = threadIdx.x; task < kTcRows * n1; task += blockDim.x) {
+    const int mt = task / n1, c = (task - mt * n1) * 8;
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = 0.f;
-    if (r < R) {
-      if (c < D1) {
-        const float4* p = reinterpret_cast<const float4*>(in1 + r * D1 + c);
-        const float4 a = p[0], b = p[1];
-        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
-        v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
-      } else {
-        const int s = (int)(r % n_nodes);
-        const int64_t row0 = r - s;   // node 0 of this sample
+    if (tile0 + mt < R) {
+      const float4* p = reinterpret_cast<const float4*>(in1 + (tile0 + mt) * D1 + c);
+      const float4 a = p[0], b = p[1];
+      v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+      v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    }
+    tc_store8(At, mt, c, v);
+  }
+  if (D2 > 0) {
+    for (int task = threadIdx.x; task < kTcRows * (kH / 8); task += blockDim.x) {
+      const int mt = task >> 3, c = (task & 7) * 8;
+      const int64_t rt = tile0 + mt;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = 0.f;
+      if (rt < R) {
+        const int s = (int)(rt % n_nodes);
+        const int64_t row0 = rt - s;   // node 0 of this sample
         const int e0 = off[s], e1 = off[s + 1];
+#pragma unroll 4
         for (int e = e0; e < e1; ++e) {
-          const float4* p = reinterpret_cast<const float4*>(in2 + (row0 + nb[e]) * kH + (c - D1));
+          const float4* p = reinterpret_cast<const float4*>(in2 + (row0 + nb[e]) * kH + c);
           const float4 a = p[0], b = p[1];
           v[0] += a.x, v[1] += a.y, v[2] += a.z, v[3] += a.w;
           v[4] += b.x, v[5] += b.y, v[6] += b.z, v[7] += b.w;
@@ -307,8 +323,8 @@ __global__ void __launch_bounds__(128, 1)
           for (int j = 0; j < 8; ++j) v[j] = v[j] / deg;
         }
       }
+      tc_store8(At, mt, D1 + c, v);
     }
-    tc_store8(At, m, c, v);
   }
   // B: row m of [W1 | W2]
   if (m < Dout) {
