@@ -537,11 +537,17 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(P, args):
-    """The FP64 oracle as it stands on a bounded sample, projected to the full paper protocol."""
+def cpu_baseline(P, args, n_samples=1):
+    """The FP64 oracle as it stands on a bounded sample, projected to the full paper protocol.
+
+    One sample assembles about 30,000 rows (about 30 s of the host's time on the large 2-D
+    workload); a run of n_samples of them (the reference arm's warm-up and timed steps) takes
+    proportionally smaller samples, at least 3,000 rows, so that the whole run stays near two
+    minutes."""
     from oracle import lstsq as OL
     from oracle import system as OS
-    frac = args.cpu_row_stride or max(1, P.n_rows // 40000)
+    target = max(3000, int(30000 * min(1.0, 4.0 / max(1, n_samples))))
+    frac = args.cpu_row_stride or max(1, P.n_rows // target)
     its = args.cpu_lsqr_its
     rows = np.arange(0, P.n_rows, frac)
     c0 = time.process_time()
@@ -570,7 +576,7 @@ def run_reference(args):
     P = make()
     vals = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(P, args)
+        cb = cpu_baseline(P, args, args.warmup + args.steps)
         if i >= args.warmup:
             vals.append(cb)
     v = statistics.mean(c["value"] for c in vals)
