@@ -44,13 +44,12 @@ import workloads as WL  # noqa: E402
 
 METRIC = "ELM-FBPINN time-to-solution (s) at oracle-matched L2 error; assembly HBM GB/s"
 DOMINANT = "fused_Mt_MTu"   # the LSQR pass: the largest share of a step
-# DRAM bytes (read + write) per algorithmic byte of the FP32-panel fused pass,
-# from the ncu capture summarised in profiles/k_fused_pipe_poisson2d_L1-16_K128_N200.md
-# (a quarter-size case of the same kernel; its traffic grows with the panel bytes)
-FUSED_FP32_TRAFFIC_PER_BYTE = (346.5 + 7.7) / 346.4
-# the same for the DF32-panel pass (k_fused_pipe_df), from the full-size DHO
-# capture in profiles/k_fused_pipe_df_dho_L1-64_K96_N20000.md
-FUSED_DF32_TRAFFIC_PER_BYTE = 192.5 / 189.4
+# roofline.traffic is null: the fused pass has changed (the device-side stopping
+# test, the CTAs-per-SM budget, the multi-instance variant) since its DRAM bytes
+# were last captured with ncu
+TRAFFIC_NOTE = ("null: the fused pass changed after its last ncu DRAM capture (then 1.022x the "
+                "algorithmic bytes for FP32 panels on the 200x200 2-D case, 1.016x for FP32-pair "
+                "panels on the DHO workload)")
 # workload -> (problem, oracle golden name, panel precision)
 WORKLOADS = {
     "poisson2d_large": (WL.config_poisson2d_large, "poisson2d_L1-64_K64_N2048_f0", "fp32"),
@@ -354,14 +353,8 @@ def run_ours(args):
                      "oracle_qr_rel_l2": (g or {}).get("qr", {}).get("rel_l2")},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(ach / hbm, 4),
-                     "traffic": (round(kstats[dom][2] * FUSED_FP32_TRAFFIC_PER_BYTE)
-                                 if prec == E.FP32 else
-                                 round(kstats[dom][2] * FUSED_DF32_TRAFFIC_PER_BYTE)
-                                 if prec == E.DF32 else None),
-                     "traffic_note": ("DRAM bytes per launch scaled from the ncu capture of the "
-                                      "200x200 case" if prec == E.FP32 else
-                                      "DRAM bytes per launch from the ncu capture of the DHO "
-                                      "workload" if prec == E.DF32 else None),
+                     "traffic": None,
+                     "traffic_note": TRAFFIC_NOTE,
                      "peak_kind": peak_kind,
                      "timed_launches": int(kstats[dom][1]),
                      "timed_every": args.roofline_stride},
